@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark of the PI batch path on GB300: Mqueries/s and the HBM roofline fraction.
+
+Default workload: the skewed configuration -- 2^27 distinct uniform uint64 keys with
+value = splitmix64(key), promotion p = 1/4, batches of 2^22 queries with Zipf(0.99)
+keys over the key set, 90% search / 5% insert / 5% delete, index layer rebuilt after
+every batch that changes it. One "step" = one pi_execute_batch: pack + sort, descent,
+ownership + apply, merge, layout, rebuild.
+
+Inputs are synthetic and seeded (paper_1601_00159_gb300/workloads.py), generated on
+the host outside the timed region and resident in HBM before it starts. The storage
+layer (2 GB) and the cycled batch inputs (32 x 71 MB) are larger than L2, so no L2
+flush is inserted between steps.
+
+Output: one JSON line (rank 0). `--impl reference` times the CPU oracle instead (the
+paper ships no code; the oracle is the only reference implementation here).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1601_00159_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "Mqueries/s and % of HBM roofline on 1 GB300; p50/p99 latency in serving loop"
+UNIT = "Mqueries/s"
+KERNELS_PER_STEP = 15  # pack, plan, 8 radix passes, descend, apply, merge, layout, rebuild
+
+WORKLOADS = {
+    "skewed": dict(fn=wl.skewed, n=1 << 27, q=1 << 22,
+                   desc="plain PI, skewed: 2^27 uint64 keys/values, p=1/4, batches of 2^22 Zipf(0.99) "
+                        "queries, 90% search / 5% insert / 5% delete, rebuild after each batch"),
+    "mid": dict(fn=wl.mid, n=1 << 24, q=1 << 20,
+                desc="plain PI, mid: 2^24 uint64 keys, p=1/4, batches of 2^20 queries, 50% search / "
+                     "50% insert of new uniform keys, rebuild after each batch"),
+    "tiny": dict(fn=wl.tiny, n=1 << 16, q=1 << 14,
+                 desc="plain PI, tiny: 2^16 uint64 keys, p=1/2, one batch of 2^14 searches (half hits)"),
+}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------
+# Algorithmic bytes (the method's own traffic, counted per batch from its inputs and
+# the index sizes; one 32-byte sector per random access).
+def algorithmic_bytes(q, q_ins, distinct, hits, writes, size_after, level_sizes, l2_bytes, sort_passes):
+    io = q * (1 + 8 + 16) + q_ins * 8
+    trav = 0
+    for l, n_l in enumerate(level_sizes):
+        if l >= 2 and n_l and 12 * n_l > l2_bytes / 2:
+            trav += distinct * 64
+    store = distinct * 32 + hits * 32 + writes * 96
+    n_index = sum(level_sizes[2:])
+    rebuild = 9 * size_after + 12 * n_index
+    sort = sort_passes * 24 * q + q * (9 + 12)
+    return dict(io=io, traversal=trav, storage=store, rebuild=rebuild, sort=sort,
+                total=io + trav + store + rebuild)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", f"-lms={self.period}"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = np.array([float(r[1]) for r in rows])
+        mx = float(rows[0][2])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = sm[sm > 0.5 * mx] if (sm > 0.5 * mx).any() else sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("", "[N/A]"))}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------------
+def cpu_baseline(w, batch0, budget_s: float = 20.0):
+    """Time the oracle (single-threaded, as it stands) on a bounded sample: build over the
+    full initial key set (untimed), then apply the first queries of the first batch."""
+    import oracle
+    oracle.build()
+    t0 = time.time()
+    orc = oracle.Oracle(w.keys, w.vals, w.promote_p, w.hash_seed)
+    build_s = time.time() - t0
+    q = len(batch0)
+    done, elapsed, chunk = 0, 0.0, 1 << 14
+    while done < q and elapsed < budget_s:
+        c = min(chunk, q - done)
+        t = time.perf_counter()
+        orc.execute(batch0.ops[done:done + c], batch0.keys[done:done + c], batch0.vals[done:done + c])
+        elapsed += time.perf_counter() - t
+        done += c
+        chunk = min(chunk * 2, 1 << 20)
+    orc.close()
+    return {"value": done / elapsed / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} queries of batch 0 on the full {len(w.keys)}-key index "
+                      f"({elapsed:.1f} s timed; oracle build {build_s:.1f} s untimed)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    spec = WORKLOADS[args.workload]
+    w = spec["fn"]()
+    batches = list(w.batches()) if callable(w.batches) else list(w.batches)
+    import oracle
+    oracle.build()
+    orc = oracle.Oracle(w.keys, w.vals, w.promote_p, w.hash_seed)
+    per_step = min(len(batches[0]), 1 << 18)  # bounded sample per step
+    for s in range(args.warmup):
+        b = batches[s % len(batches)]
+        orc.execute(b.ops[:per_step], b.keys[:per_step], b.vals[:per_step])
+    t = time.perf_counter()
+    for s in range(args.steps):
+        b = batches[(args.warmup + s) % len(batches)]
+        orc.execute(b.ops[:per_step], b.keys[:per_step], b.vals[:per_step])
+    el = time.perf_counter() - t
+    v = args.steps * per_step / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": spec["desc"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} queries of each batch, applied in arrival order"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_1601_00159_gb300 import Index, build, load_library
+    build.build()
+    load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = WORKLOADS[args.workload]
+    t_gen = time.time()
+    w = spec["fn"]()
+    n_distinct_batches = 1 if args.workload == "tiny" else min(args.steps + args.warmup, args.batches)
+    gen = w.batches() if callable(w.batches) else iter(w.batches)
+    host_batches = [next(gen) for _ in range(n_distinct_batches)]
+    gen_s = time.time() - t_gen
+    q = len(host_batches[0])
+
+    def dev_batch(b):
+        return (torch.from_numpy(b.ops).to(dev), torch.from_numpy(b.keys.view(np.int64)).to(dev),
+                torch.from_numpy(b.vals.view(np.int64)).to(dev))
+
+    dbatches = [dev_batch(b) for b in host_batches]
+    results = torch.empty((q, 2), dtype=torch.int64, device=dev)
+    keys_d = torch.from_numpy(w.keys.view(np.int64)).to(dev)
+    vals_d = torch.from_numpy(w.vals.view(np.int64)).to(dev)
+    total_steps = args.warmup + args.steps
+    cfg = {"storage_capacity": len(w.keys) + q * (total_steps + 4) if args.workload == "mid" else 0}
+    cfg = {k: v for k, v in cfg.items() if v}
+    torch.cuda.synchronize()
+    t = time.time()
+    idx = Index(keys_d, vals_d, w.promote_p, w.hash_seed, cfg or None)
+    create_s = time.time() - t
+    del keys_d, vals_d
+    stream = torch.cuda.current_stream()
+    l2_bytes = torch.cuda.get_device_properties(dev).L2_cache_size
+
+    for s in range(args.warmup):
+        o, k, v = dbatches[s % len(dbatches)]
+        idx.execute(o, k, v, results)
+    torch.cuda.synchronize()
+    info0 = idx.info()
+    idx.profile(True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for s in range(args.steps):
+            o, k, v = dbatches[(args.warmup + s) % len(dbatches)]
+            idx.execute(o, k, v, results)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    ms_total = ev0.elapsed_time(ev1)
+    stage_ms, nb = idx.profile_read()
+    idx.profile(False)
+    info1 = idx.info()
+    assert idx.status() == 0, "device error status after the timed region"
+    ms_total = reduce_max(ms_total, ws)
+    ms_step = ms_total / args.steps
+    value = ws * q * args.steps / (ms_total * 1e-3) / 1e6
+
+    # e2e: host (pinned) buffers through pi_execute_batch_host, copies inside the timed region
+    e2e_steps = max(3, min(args.steps, 200))
+    hp = []
+    for b in host_batches[: min(len(host_batches), 8)]:
+        hp.append((torch.from_numpy(b.ops.copy()).pin_memory(),
+                   torch.from_numpy(b.keys.view(np.int64).copy()).pin_memory(),
+                   torch.from_numpy(b.vals.view(np.int64).copy()).pin_memory()))
+    hres = torch.empty((q, 2), dtype=torch.int64).pin_memory()
+    for s in range(2):
+        o, k, v = hp[s % len(hp)]
+        idx.execute_host(o, k, v, hres)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(e2e_steps):
+        o, k, v = hp[s % len(hp)]
+        idx.execute_host(o, k, v, hres)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(e0.elapsed_time(e1), ws)
+    e2e_value = ws * q * e2e_steps / (e2e_ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (largest share of the step), from live CUDA events
+    hbm, peak_kind = measured_peaks()
+    per_stage = {k: v / max(nb, 1) for k, v in stage_ms.items()}
+    hb = host_batches[0]
+    ins = int((hb.ops == wl.OP_INSERT).sum())
+    uk, inv = np.unique(hb.keys, return_inverse=True)
+    distinct = len(uk)
+    live_before = info0["live"]
+    sizes = info1["level_size"]
+    size_after = info1["size"]
+    writes = distinct  # upper bound: every distinct key may be written once
+    ab = algorithmic_bytes(q, ins, distinct, distinct, writes, size_after, sizes, l2_bytes, 8)
+    stage_bytes = {"sort": ab["sort"] / 8, "rebuild": ab["rebuild"],
+                   "descend": ab["traversal"] + ab["storage"] + q * 12, "apply": ab["io"]}
+    dom = max(per_stage, key=lambda s: per_stage[s])
+    if dom == "sort":
+        launches = 8
+        per_launch_ms = per_stage["sort"] / 8
+        dom_bytes = stage_bytes["sort"]
+        kname = "k_sort_pass"
+    else:
+        launches = 1
+        per_launch_ms = per_stage[dom]
+        dom_bytes = stage_bytes.get(dom, 0.0)
+        kname = {"rebuild": "k_rebuild", "descend": "k_descend", "apply": "k_apply",
+                 "merge": "k_merge", "layout": "k_level_bases"}[dom]
+    achieved = dom_bytes / (per_launch_ms * 1e-3) / 1e9
+    rebuild_gbs = stage_bytes["rebuild"] / (per_stage["rebuild"] * 1e-3) / 1e9 if per_stage["rebuild"] > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"], "keys": len(w.keys), "batch": q,
+                   "distinct_batches_cycled": len(dbatches), "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "l2_flush": "none: storage layer and cycled batch inputs exceed L2"},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_source": peak_kind, "traffic": None,
+                     "launches_per_step": launches, "ms_per_launch": per_launch_ms,
+                     "algorithmic_bytes_per_launch": dom_bytes},
+        "batch_roofline": {"algorithmic_bytes": ab["total"], "achieved_gbs": ab["total"] / (ms_step * 1e-3) / 1e9,
+                           "frac": ab["total"] / (ms_step * 1e-3) / 1e9 / hbm,
+                           "rebuild_gbs": rebuild_gbs},
+        "stages_ms": per_stage,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": q * 17, "d2h_bytes_per_step": q * 16,
+                "steps": e2e_steps},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": clk.summary(),
+        "index": {"size": info1["size"], "live": info1["live"], "tombstones": info1["tombstones"],
+                  "top_level": info1["top_level"], "rebuilds_in_region": info1["rebuilds"] - info0["rebuilds"],
+                  "create_s": create_s, "gen_s": gen_s, "distinct_keys_batch0": distinct},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, host_batches[0], args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    idx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="skewed", choices=sorted(WORKLOADS))
+    ap.add_argument("--batches", type=int, default=32, help="distinct batches generated and cycled")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * pi.h -- C ABI of the GB300 (sm_103a) implementation of PI's batch hot path.
+ *
+ * PI ("a Parallel in-memory skip list based Index", arXiv:1601.00159) keeps a
+ * sorted storage layer of data nodes (key, value, height, delete flag; Definition 1
+ * and Section 3.2.3) under an index layer of sorted levels (Section 3.1). It answers
+ * a whole batch of point queries at once (Algorithm 1): sort the batch by key,
+ * descend the index layer to each query's interception (Algorithm 2, Definition 4),
+ * give every storage node a single owner (Algorithm 3 and Section 3.2.4), execute
+ * the queries against the storage layer (Algorithm 4), and rebuild the index layer
+ * from the storage layer (Sections 4.1 and 4.4.4).
+ *
+ * All array arguments are DEVICE pointers unless a name ends in _host. They are owned
+ * by the caller and must stay valid until the work that reads them has completed on
+ * the stream passed in. Keys and values are unsigned 64-bit integers compared as
+ * unsigned; the key 2^64-1 is reserved (it is the sentinel that ends every level).
+ *
+ * Threading: a pi_index_t must not be used from two host threads, or from two
+ * streams, at the same time; the caller serialises its calls.
+ */
+#ifndef PI_H_
+#define PI_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-identical to cudaStream_t; NULL means the legacy default stream. */
+typedef struct CUstream_st* pi_stream_t;
+
+typedef struct pi_index pi_index_t; /* opaque, library-owned device state */
+
+/* One result per query, in arrival order (16 bytes). */
+typedef struct {
+    uint64_t value;    /* the key's value just before this query, or 0 if it was absent */
+    uint32_t status;   /* PI_R_* */
+    uint32_t reserved; /* always 0 */
+} pi_result_t;
+
+/* Query types (Definition 2: a query is (type, key, [value])). */
+enum { PI_OP_SEARCH = 0, PI_OP_INSERT = 1, PI_OP_DELETE = 2 };
+
+/* Per-query status. */
+enum {
+    PI_R_ABSENT = 0,  /* the key was not present before this query */
+    PI_R_PRESENT = 1, /* the key was present; value holds its value */
+    PI_R_INVALID = 2  /* op code not 0/1/2, or key == 2^64-1: the query had no effect */
+};
+
+/* Return codes. */
+enum {
+    PI_OK = 0,
+    PI_ERR_INVALID_ARG = -1, /* NULL pointer, size over a limit, bad promote_p, reserved key */
+    PI_ERR_OOM = -2,         /* device allocation failed; the index is unchanged */
+    PI_ERR_CUDA = -3,        /* a CUDA call failed (launch error or an earlier fault) */
+    PI_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up; the index is unusable */
+    PI_ERR_NOT_BUILT = -5    /* pi_export_level: that level is not materialised */
+};
+
+#define PI_MAX_BATCH (1u << 28)          /* queries per pi_execute_batch call */
+#define PI_MAX_KEYS ((1u << 30) - 2u)    /* storage-layer nodes */
+
+/* Optional tuning for pi_create_ex. Zero means "default" for every field. */
+typedef struct {
+    uint32_t struct_size;        /* sizeof(pi_config_t) */
+    uint32_t rebuild_policy;     /* 0: rebuild the index layer after every batch that
+                                    changed it (default). 1: deferred, as in Section 6's
+                                    setup: rebuild only when the storage layer was
+                                    re-laid-out or the updates since the last rebuild
+                                    exceed rebuild_threshold_pct percent of its size. */
+    uint32_t rebuild_threshold_pct; /* policy 1 only; default 15 (Section 6) */
+    uint32_t smem_top_entries;   /* index entries staged in shared memory (<= 4096) */
+    uint64_t storage_capacity;   /* initial storage-layer capacity, in nodes */
+    uint64_t index_capacity;     /* initial index-layer capacity, in entries */
+} pi_config_t;
+
+/*
+ * pi_create -- bulk-build an index from n (key, value) pairs (Section 3.1: the index
+ * layer is built bottom-up by one scan of the storage layer).
+ *   keys, values: device arrays of n entries. A key that appears several times keeps
+ *     its LAST value, as if the pairs were inserted in order.
+ *   promote_p: the promotion probability P of Definition 1; must be 1/2, 1/4, 1/8 or
+ *     1/16. A key's tower height is 1 + min(ctz(h) / b, Hmax - 1) with p = 2^-b,
+ *     h = splitmix64(key ^ splitmix64(seed)), Hmax = min(32, 64 / b), ctz(0) = 64.
+ *   seed: seeds the height hash; the structure is a pure function of keys and seed.
+ * Synchronous. Returns NULL on error; pi_last_error() then gives the code
+ * (PI_ERR_INVALID_ARG for n > PI_MAX_KEYS, a bad promote_p or a reserved key).
+ */
+pi_index_t* pi_create(const uint64_t* keys, const uint64_t* values, uint64_t n,
+                      double promote_p, uint64_t seed);
+pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t n,
+                         double promote_p, uint64_t seed, const pi_config_t* config);
+
+/*
+ * pi_execute_batch -- process one query set Q (Definition 3; Algorithm 1).
+ *   ops[n] (uint8), keys[n], values[n] (values read only where ops[i] == PI_OP_INSERT),
+ *   results[n]: device arrays. Results are in arrival order: query i reports the
+ *   state of its key just before query i, as if the batch were applied one query at
+ *   a time in arrival order (the batch is serializable, Section 4.2). Insert sets the
+ *   key's value and clears its delete flag (Algorithm 4); delete sets the flag; search
+ *   changes nothing. For a search this is Algorithm 4's result; for a delete PRESENT
+ *   is the paper's "return 1"; for an insert the paper returns null and this library
+ *   reports the prior state instead.
+ * Stream-ordered and asynchronous: results are complete when `stream` completes.
+ * No host synchronisation happens except, rarely, when a capacity must grow.
+ * n == 0 is a no-op. Returns PI_ERR_INVALID_ARG for NULL pointers or n > PI_MAX_BATCH,
+ * PI_ERR_OOM if a capacity could not grow (index unchanged), PI_ERR_CUDA on a launch
+ * failure, PI_ERR_TIMEOUT if an earlier batch reported a device-side timeout.
+ */
+int pi_execute_batch(pi_index_t* idx, const uint8_t* ops, const uint64_t* keys,
+                     const uint64_t* values, uint64_t n, pi_result_t* results,
+                     pi_stream_t stream);
+
+/*
+ * pi_execute_batch_host -- the same, with HOST arrays. The library copies the inputs
+ * to device staging it owns, runs pi_execute_batch and copies the results back, all
+ * on `stream`; results_host is complete when `stream` completes. Pinned host memory
+ * makes the copies asynchronous; pageable memory works but serialises them.
+ */
+int pi_execute_batch_host(pi_index_t* idx, const uint8_t* ops_host, const uint64_t* keys_host,
+                          const uint64_t* values_host, uint64_t n, pi_result_t* results_host,
+                          pi_stream_t stream);
+
+/* Releases every device allocation of the index after its pending work. NULL-safe. */
+void pi_destroy(pi_index_t* idx);
+
+/* Error code of the last failing pi_create / pi_create_ex on this host thread. */
+int pi_last_error(void);
+
+/* Synchronises `stream` and returns PI_OK, or the sticky device-side error
+ * (PI_ERR_TIMEOUT / PI_ERR_CUDA) recorded by any batch so far. */
+int pi_status(pi_index_t* idx, pi_stream_t stream);
+
+/* Snapshot of the index's shape (synchronises `stream`). */
+typedef struct {
+    uint64_t size;           /* storage-layer nodes, delete-flagged ones included */
+    uint64_t live;           /* live keys */
+    uint64_t tombstones;     /* delete-flagged nodes still in the storage layer */
+    uint32_t top_level;      /* H: highest level holding a key (1 if only storage) */
+    uint32_t bottom_built;   /* lowest materialised index level (2 unless it overflowed) */
+    uint32_t smem_low_level; /* lowest level staged in shared memory by the descent */
+    uint32_t promote_shift;  /* b, with P = 2^-b */
+    uint64_t level_size[34]; /* level_size[l] = live keys with height >= l, l = 1..33 */
+    uint64_t storage_capacity;
+    uint64_t index_capacity;
+    uint64_t batches;        /* batches executed */
+    uint64_t rebuilds;       /* index-layer rebuilds run (counts only when known) */
+} pi_info_t;
+int pi_info(pi_index_t* idx, pi_info_t* out_host, pi_stream_t stream);
+
+/* Live keys (level 1). *n_out_host = live count; up to cap pairs are written, in key
+ * order, to the device arrays keys_out / vals_out. Synchronises `stream`. */
+int pi_export(pi_index_t* idx, uint64_t* keys_out, uint64_t* vals_out, uint64_t cap,
+              uint64_t* n_out_host, pi_stream_t stream);
+
+/* Level `level` (>= 2) of the index layer as last rebuilt: its keys and, if down_out
+ * is not NULL, each key's position in the level below (for the lowest materialised
+ * level: its storage-layer position). Device arrays; *n_out_host = the level's size.
+ * PI_ERR_NOT_BUILT if the level is not materialised. Synchronises `stream`. */
+int pi_export_level(pi_index_t* idx, int level, uint64_t* keys_out, uint32_t* down_out,
+                    uint64_t cap, uint64_t* n_out_host, pi_stream_t stream);
+
+/*
+ * Stage timing, for measurement (no counterpart in the paper). While enabled, each
+ * pi_execute_batch records CUDA events on its stream between the pipeline's stages:
+ *   0 pack + radix sort (K0, K1)        3 storage merge (K6a)
+ *   1 descent + storage locate (K2, K3) 4 level layout (K6b)
+ *   2 ownership + apply (K4, K5)        5 index-layer rebuild (K6c)
+ * pi_profile(idx, 1) starts (and clears) the accumulation; pi_profile(idx, 0) stops it.
+ * pi_profile_read synchronises `stream` and writes the summed milliseconds per stage to
+ * stage_ms_host[PI_NUM_STAGES] and the number of batches they cover to *batches_host.
+ */
+#define PI_NUM_STAGES 6
+int pi_profile(pi_index_t* idx, int enable);
+int pi_profile_read(pi_index_t* idx, double* stage_ms_host, uint64_t* batches_host, pi_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PI_H_ */

@@ -1,0 +1,213 @@
+"""Python binding of the PI batch library (include/pi.h), for tests and benchmarks.
+
+Argument marshalling only: every step of the batch path runs in the CUDA library
+(paper_1601_00159_gb300/_build/libpi.so). PyTorch supplies device memory and streams.
+uint64 keys and values travel as torch.int64 tensors holding the same bits.
+There is no fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpi.so")
+
+PI_OP_SEARCH, PI_OP_INSERT, PI_OP_DELETE = 0, 1, 2
+PI_R_ABSENT, PI_R_PRESENT, PI_R_INVALID = 0, 1, 2
+PI_OK, PI_ERR_INVALID_ARG, PI_ERR_OOM, PI_ERR_CUDA, PI_ERR_TIMEOUT, PI_ERR_NOT_BUILT = 0, -1, -2, -3, -4, -5
+PI_MAX_BATCH = 1 << 28
+PI_MAX_KEYS = (1 << 30) - 2
+
+EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
+            "pi_last_error", "pi_status", "pi_info", "pi_export", "pi_export_level", "pi_profile",
+            "pi_profile_read"]
+STAGES = ["sort", "descend", "apply", "merge", "layout", "rebuild"]
+
+
+class PiError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what} failed with code {code}")
+        self.code = code
+
+
+class PiConfig(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("rebuild_policy", ctypes.c_uint32),
+                ("rebuild_threshold_pct", ctypes.c_uint32), ("smem_top_entries", ctypes.c_uint32),
+                ("storage_capacity", ctypes.c_uint64), ("index_capacity", ctypes.c_uint64)]
+
+
+class PiInfo(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_uint64), ("live", ctypes.c_uint64), ("tombstones", ctypes.c_uint64),
+                ("top_level", ctypes.c_uint32), ("bottom_built", ctypes.c_uint32),
+                ("smem_low_level", ctypes.c_uint32), ("promote_shift", ctypes.c_uint32),
+                ("level_size", ctypes.c_uint64 * 34), ("storage_capacity", ctypes.c_uint64),
+                ("index_capacity", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("rebuilds", ctypes.c_uint64)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "level_size"}
+        d["level_size"] = list(self.level_size)
+        return d
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpi.so and declare its signatures. Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"PI CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, u64, i32, dbl = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    lib.pi_create.restype = vp
+    lib.pi_create.argtypes = [vp, vp, u64, dbl, u64]
+    lib.pi_create_ex.restype = vp
+    lib.pi_create_ex.argtypes = [vp, vp, u64, dbl, u64, ctypes.POINTER(PiConfig)]
+    lib.pi_execute_batch.restype = i32
+    lib.pi_execute_batch.argtypes = [vp, vp, vp, vp, u64, vp, vp]
+    lib.pi_execute_batch_host.restype = i32
+    lib.pi_execute_batch_host.argtypes = [vp, vp, vp, vp, u64, vp, vp]
+    lib.pi_destroy.restype = None
+    lib.pi_destroy.argtypes = [vp]
+    lib.pi_last_error.restype = i32
+    lib.pi_last_error.argtypes = []
+    lib.pi_status.restype = i32
+    lib.pi_status.argtypes = [vp, vp]
+    lib.pi_info.restype = i32
+    lib.pi_info.argtypes = [vp, ctypes.POINTER(PiInfo), vp]
+    lib.pi_export.restype = i32
+    lib.pi_export.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64), vp]
+    lib.pi_export_level.restype = i32
+    lib.pi_export_level.argtypes = [vp, i32, vp, vp, u64, ctypes.POINTER(u64), vp]
+    lib.pi_profile.restype = i32
+    lib.pi_profile.argtypes = [vp, i32]
+    lib.pi_profile_read.restype = i32
+    lib.pi_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), vp]
+    _lib = lib
+    return lib
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_dev(t, dtype, name):
+    import torch
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+
+
+def _chk(rc: int, what: str):
+    if rc != PI_OK:
+        raise PiError(rc, what)
+
+
+class Index:
+    """One PI index resident on the current CUDA device (pi_create ... pi_destroy)."""
+
+    def __init__(self, keys, vals, promote_p: float, seed: int, config: dict | None = None):
+        import torch
+        lib = load_library()
+        _check_dev(keys, torch.int64, "keys")
+        _check_dev(vals, torch.int64, "vals")
+        if keys.numel() != vals.numel():
+            raise ValueError("keys and vals differ in length")
+        torch.cuda.current_stream().synchronize()
+        if config:
+            cfg = PiConfig(ctypes.sizeof(PiConfig), 0, 0, 0, 0, 0)
+            for k, v in config.items():
+                setattr(cfg, k, v)
+            h = lib.pi_create_ex(keys.data_ptr(), vals.data_ptr(), keys.numel(), float(promote_p),
+                                 seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(cfg))
+        else:
+            h = lib.pi_create(keys.data_ptr(), vals.data_ptr(), keys.numel(), float(promote_p),
+                              seed & 0xFFFFFFFFFFFFFFFF)
+        if not h:
+            raise PiError(lib.pi_last_error(), "pi_create")
+        self._h = ctypes.c_void_p(h)
+        self.lib = lib
+
+    def execute(self, ops, keys, vals, results=None, stream=None):
+        """pi_execute_batch on device tensors; returns results as int64 [n, 2]:
+        column 0 = value bits, column 1 = status (low 32 bits)."""
+        import torch
+        n = ops.numel()
+        _check_dev(ops, torch.uint8, "ops")
+        _check_dev(keys, torch.int64, "keys")
+        _check_dev(vals, torch.int64, "vals")
+        if keys.numel() != n or vals.numel() != n:
+            raise ValueError("ops, keys and vals differ in length")
+        if results is None:
+            results = torch.empty((n, 2), dtype=torch.int64, device=ops.device)
+        rc = self.lib.pi_execute_batch(self._h, ops.data_ptr(), keys.data_ptr(), vals.data_ptr(), n,
+                                       results.data_ptr(), _stream_handle(stream))
+        _chk(rc, "pi_execute_batch")
+        return results
+
+    def execute_host(self, ops, keys, vals, results, stream=None):
+        """pi_execute_batch_host on host (ideally pinned) CPU tensors."""
+        n = ops.numel()
+        rc = self.lib.pi_execute_batch_host(self._h, ops.data_ptr(), keys.data_ptr(), vals.data_ptr(), n,
+                                            results.data_ptr(), _stream_handle(stream))
+        _chk(rc, "pi_execute_batch_host")
+        return results
+
+    def status(self, stream=None) -> int:
+        return self.lib.pi_status(self._h, _stream_handle(stream))
+
+    def info(self, stream=None) -> dict:
+        out = PiInfo()
+        _chk(self.lib.pi_info(self._h, ctypes.byref(out), _stream_handle(stream)), "pi_info")
+        return out.as_dict()
+
+    def export(self, stream=None):
+        """Live (keys, vals) in key order as int64 CUDA tensors."""
+        import torch
+        n = ctypes.c_uint64(0)
+        _chk(self.lib.pi_export(self._h, None, None, 0, ctypes.byref(n), _stream_handle(stream)), "pi_export")
+        k = torch.empty(max(n.value, 1), dtype=torch.int64, device="cuda")
+        v = torch.empty(max(n.value, 1), dtype=torch.int64, device="cuda")
+        _chk(self.lib.pi_export(self._h, k.data_ptr(), v.data_ptr(), n.value, ctypes.byref(n),
+                                _stream_handle(stream)), "pi_export")
+        return k[: n.value], v[: n.value]
+
+    def export_level(self, level: int, stream=None):
+        """(keys int64, down int32) of built level `level` >= 2, or None if not built."""
+        import torch
+        n = ctypes.c_uint64(0)
+        rc = self.lib.pi_export_level(self._h, level, None, None, 0, ctypes.byref(n), _stream_handle(stream))
+        if rc == PI_ERR_NOT_BUILT:
+            return None
+        _chk(rc, "pi_export_level")
+        k = torch.empty(max(n.value, 1), dtype=torch.int64, device="cuda")
+        d = torch.empty(max(n.value, 1), dtype=torch.int32, device="cuda")
+        _chk(self.lib.pi_export_level(self._h, level, k.data_ptr(), d.data_ptr(), n.value, ctypes.byref(n),
+                                      _stream_handle(stream)), "pi_export_level")
+        return k[: n.value], d[: n.value]
+
+    def profile(self, enable: bool):
+        _chk(self.lib.pi_profile(self._h, 1 if enable else 0), "pi_profile")
+
+    def profile_read(self, stream=None):
+        """(dict stage -> summed ms, batches covered)."""
+        ms = (ctypes.c_double * len(STAGES))()
+        nb = ctypes.c_uint64(0)
+        _chk(self.lib.pi_profile_read(self._h, ms, ctypes.byref(nb), _stream_handle(stream)), "pi_profile_read")
+        return dict(zip(STAGES, list(ms))), nb.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.pi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,220 @@
+// K4 + K5: single ownership and query execution (Algorithms 3 and 4, Section 3.2.4).
+//
+// In the paper each execution thread owns the storage nodes between its first
+// interception and the next thread's, handing queries over to its neighbour so that
+// no node has two writers; within a thread the queries run in order. Here the whole
+// sorted batch is one array and ownership is computed, not negotiated:
+//  * a key run is a maximal stretch of equal keys in the sorted batch (its queries are
+//    in arrival order, by the stable sort);
+//  * every query reports the state of its key just before it: that is the effect of
+//    the last insert/delete before it in its run, or, if there is none, the state the
+//    descent found in the storage layer. An inclusive max-scan over
+//        e_i = 2i+3 if query i writes, 2i+2 if it heads a run, 0 otherwise
+//    gives, at i-1, either the index of that last write (odd) or the run head (even);
+//  * the LAST query of each run is the run's only owner: it writes the run's final
+//    state to the storage node (value, delete flag), or emits a new node when the key
+//    is not in the storage layer and ends up present (Algorithm 4, insertNode).
+// Two decoupled look-backs carry the max-scan and the new-node count across tiles.
+
+#include "common.cuh"
+
+namespace pi {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 8;
+constexpr int kTile = kThreads * kItems;  // 2048 sorted queries per tile
+constexpr uint32_t kSeqMask = (1u << 30) - 1u;
+constexpr uint32_t kCtrApply = 8;
+
+__device__ __forceinline__ void store_result(pi_result_t* res, uint32_t seq, uint64_t v, uint32_t st) {
+    uint4 w;
+    w.x = (uint32_t)v;
+    w.y = (uint32_t)(v >> 32);
+    w.z = st;
+    w.w = 0u;
+    *reinterpret_cast<uint4*>(res + seq) = w;
+}
+
+__global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a, uint32_t epoch_max, uint32_t epoch_cnt) {
+    __shared__ uint32_t s_tmp[33];
+    __shared__ int32_t s_delta[kLevelSlots];
+    __shared__ int32_t s_tomb;
+    __shared__ uint32_t s_changes, s_dirty, s_new_total;
+    __shared__ uint32_t s_tile, s_excl_max, s_excl_cnt;
+    __shared__ int s_ok;
+
+    const int tid = threadIdx.x;
+    if (block_sees_error(&a.m->error)) return;
+    const uint32_t n = a.n;
+    const uint32_t qv = n - a.bm->invalid;
+    const uint32_t cur = a.m->cur;
+    uint64_t* SV = a.st.vals[cur];
+    uint8_t* SM = a.st.meta[cur];
+    const uint32_t ntiles = (n + kTile - 1) / kTile;
+    uint64_t* desc_max = a.desc;
+    uint64_t* desc_cnt = a.desc + ntiles;
+
+    if (tid < kLevelSlots) s_delta[tid] = 0;
+    if (tid == 0) {
+        s_tomb = 0;
+        s_changes = 0;
+        s_dirty = 0;
+        s_new_total = 0;
+        s_ok = 1;
+    }
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_tile = atomicAdd(&a.bm->tile_ctr[kCtrApply], 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint32_t base = tile * kTile + tid * kItems;
+
+        uint64_t key[kItems];
+        uint32_t pay[kItems];
+        uint32_t e[kItems];
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const uint32_t i = base + k;
+            key[k] = i < qv ? a.sk[i] : kMaxKey;
+            pay[k] = i < n ? a.sp[i] : 0u;
+        }
+        const uint64_t kprev = (base > 0 && base - 1 < qv) ? a.sk[base - 1] : kMaxKey;
+        const uint64_t knext = (base + kItems < qv) ? a.sk[base + kItems] : kMaxKey;
+        uint32_t agg = 0;
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const uint32_t i = base + k;
+            const bool valid = i < qv;
+            const uint64_t prev = k ? key[k - 1] : kprev;
+            const bool head = valid && (i == 0 || key[k] != prev);
+            const uint32_t op = pay[k] >> 30;
+            const bool write = valid && (op == 1u || op == 2u);
+            e[k] = write ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
+            agg = max(agg, e[k]);
+        }
+        uint32_t tile_max;
+        const uint32_t texcl = block_excl_max<kThreads>(agg, s_tmp, &tile_max);
+        if (tid == 0) {
+            bool ok;
+            s_excl_max = lookback<true>(desc_max, 1, tile, epoch_max, tile_max, a.err, &ok);
+            if (!ok) s_ok = 0;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+
+        uint32_t M = max(s_excl_max, texcl);
+        uint32_t new_here = 0;
+        uint32_t new_mask = 0;
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const uint32_t i = base + k;
+            const uint32_t mex = M;
+            const uint32_t minc = max(M, e[k]);
+            M = minc;
+            e[k] = minc;  // keep the inclusive value for the new-node pass
+            if (i >= n) continue;
+            const uint32_t seq = pay[k] & kSeqMask;
+            if (i >= qv) {
+                store_result(a.results, seq, 0ull, PI_R_INVALID);
+                continue;
+            }
+            const uint64_t prev = k ? key[k - 1] : kprev;
+            const bool head = (i == 0 || key[k] != prev);
+            const uint8_t fl = a.flags[i];
+            const bool exists = fl & 1u, live0 = (fl & 2u) != 0;
+            bool pl;
+            uint64_t pv;
+            if (!head && (mex & 1u)) {
+                const uint32_t j = (mex - 3u) >> 1;
+                const uint32_t pj = a.sp[j];
+                pl = (pj >> 30) == 1u;
+                pv = pl ? a.uvals[pj & kSeqMask] : 0ull;
+            } else {
+                pl = live0;
+                pv = live0 ? a.val0[i] : 0ull;
+            }
+            store_result(a.results, seq, pv, pl ? PI_R_PRESENT : PI_R_ABSENT);
+
+            const uint64_t next = (k + 1 < kItems) ? key[k + 1] : knext;
+            const bool last = next != key[k];
+            if (!last || !(minc & 1u)) continue;  // not the owner, or the run never writes
+            const uint32_t jw = (minc - 3u) >> 1;
+            const uint32_t pw = (jw == i) ? pay[k] : a.sp[jw];
+            const bool fin_live = (pw >> 30) == 1u;
+            if (exists) {
+                const uint32_t r = a.loc[i] - 1u;
+                const uint8_t mt = SM[r];
+                const uint32_t h = mt & kHeightMask;
+                if (fin_live) {
+                    SV[r] = a.uvals[pw & kSeqMask];
+                    SM[r] = (uint8_t)h;
+                } else {
+                    SM[r] = (uint8_t)(h | kTomb);
+                }
+                if (fin_live != live0) {
+                    atomicAdd(&s_tomb, fin_live ? -1 : 1);
+                    atomicAdd(&s_changes, 1u);
+                    atomicAdd(&s_delta[1], fin_live ? 1 : -1);
+                    for (uint32_t l = 2; l <= h; ++l) atomicAdd(&s_delta[l], fin_live ? 1 : -1);
+                    if (h >= 2) s_dirty = 1;
+                }
+            } else if (fin_live) {
+                new_here++;
+                new_mask |= 1u << k;
+            }
+        }
+        // New nodes: compact slots in key order.
+        uint32_t tile_new;
+        const uint32_t nexcl = block_excl_sum<kThreads>(new_here, s_tmp, &tile_new);
+        if (tid == 0) {
+            bool ok;
+            s_excl_cnt = lookback<false>(desc_cnt, 1, tile, epoch_cnt, tile_new, a.err, &ok);
+            if (!ok) s_ok = 0;
+            s_new_total += tile_new;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        uint32_t slot = s_excl_cnt + nexcl;
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            if (!(new_mask & (1u << k))) continue;
+            const uint32_t i = base + k;
+            const uint32_t jw = (e[k] - 3u) >> 1;
+            const uint32_t pw = (jw == i) ? pay[k] : a.sp[jw];
+            const uint32_t h = tower_height(key[k], a.hp);
+            a.nn.keys[slot] = key[k];
+            a.nn.vals[slot] = a.uvals[pw & kSeqMask];
+            a.nn.loc[slot] = a.loc[i];
+            a.nn.height[slot] = (uint8_t)h;
+            ++slot;
+            atomicAdd(&s_changes, 1u);
+            atomicAdd(&s_delta[1], 1);
+            for (uint32_t l = 2; l <= h; ++l) atomicAdd(&s_delta[l], 1);
+            if (h >= 2) s_dirty = 1;
+        }
+    }
+    __syncthreads();
+    if (tid < kLevelSlots && s_delta[tid]) atomicAdd(&a.bm->delta[tid], s_delta[tid]);
+    if (tid == 0) {
+        if (s_tomb) atomicAdd(&a.bm->tomb_delta, s_tomb);
+        if (s_changes) atomicAdd(&a.bm->changes, s_changes);
+        if (s_dirty) atomicOr(&a.bm->index_dirty, 1u);
+        if (s_new_total) atomicAdd(&a.bm->new_count, s_new_total);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_apply(const ApplyArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
+    if (a.n == 0) return cudaSuccess;
+    const uint32_t tiles = (a.n + kTile - 1) / kTile;
+    const uint32_t cap = (uint32_t)num_sms * 4u;
+    const int grid = (int)(tiles < cap ? tiles : cap);
+    const uint32_t e1 = ++epoch, e2 = ++epoch;
+    k_apply<<<grid, kThreads, 0, s>>>(a, e1, e2);
+    return cudaGetLastError();
+}
+
+}  // namespace pi

@@ -1,0 +1,391 @@
+// Shared device-side definitions of the PI batch path (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pi.h"
+
+namespace pi {
+
+constexpr uint64_t kMaxKey = ~0ull;  // reserved key: level and storage sentinel
+constexpr int kLevelSlots = 34;      // per-level arrays are indexed by level 0..33
+constexpr uint8_t kTomb = 0x80;      // meta bit 7: the delete flag F_del (Algorithm 4)
+constexpr uint8_t kHeightMask = 0x3F;
+constexpr uint32_t kSmemTopMax = 4096;  // index entries staged in shared memory
+constexpr uint32_t kPad = 64;           // readable entries past every array's end
+
+// Sticky error bits in DevMeta::error.
+constexpr uint32_t kErrTimeout = 1u;  // a bounded wait gave up
+constexpr uint32_t kErrBounds = 2u;   // an internal bound check refused an access
+
+// Bounded spins: a look-back or barrier wait gives up after this many polls (about
+// half a second with the back-off below) and records kErrTimeout instead of hanging.
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Persistent device state of one index (one allocation, lives with the index).
+struct DevMeta {
+    uint32_t cur;          // which of the two storage buffers is current
+    uint32_t size;         // storage-layer nodes (delete-flagged ones included)
+    uint32_t tombs;        // delete-flagged nodes
+    uint32_t error;        // sticky kErr* bits
+    // layout of the index layer as last built
+    uint32_t H;            // top built level (1: no index level)
+    uint32_t Lb;           // lowest materialised index level
+    uint32_t Ls;           // lowest level staged in shared memory (> H: none)
+    uint32_t smem_entries; // entries [0, smem_entries) are staged
+    uint32_t index_total;  // entries in use (sentinels included)
+    uint32_t index_need;   // entries a full build needs
+    uint32_t grow_request; // 1 when levels were dropped for lack of capacity
+    uint32_t updates;      // node changes since the last rebuild
+    uint32_t rebuilds;     // rebuilds run
+    uint32_t batches;      // batches run
+    uint32_t pad_[2];
+    uint32_t cnt[kLevelSlots];   // live keys with height >= l, kept current every batch
+    uint32_t n[kLevelSlots];     // n[l]: size of built level l
+    uint32_t base[kLevelSlots];  // built level l occupies [base[l], base[l] + n[l]] (+ sentinel)
+};
+
+struct SortPlan {
+    uint32_t npass;
+    uint32_t digit[8];
+    uint32_t src[8];  // 0 = packed input, 1 = buffer A, 2 = buffer B
+    uint32_t dst[8];
+};
+
+// Per-batch scratch counters, cleared by one memset at the start of every batch.
+struct BatchMeta {
+    uint32_t tile_ctr[24];       // dynamic tile counters, one per look-back kernel
+    int32_t delta[kLevelSlots];  // change of n[l] in this batch
+    int32_t tomb_delta;
+    uint32_t invalid;            // invalid queries
+    uint32_t new_count;          // new storage nodes
+    uint32_t merged;             // storage layer re-laid-out
+    uint32_t index_dirty;        // level membership changed
+    uint32_t rebuild;            // the rebuild runs in this batch
+    uint32_t changes;            // storage nodes whose liveness changed or that were added
+    uint32_t pad_[1];
+    uint32_t hist[8][256];       // radix digit histograms
+    SortPlan plan;
+};
+
+// Storage layer, double buffered: [0] and [1]; DevMeta::cur picks the current one.
+struct Storage {
+    uint64_t* keys[2];
+    uint64_t* vals[2];
+    uint8_t* meta[2];
+};
+
+struct NewNodes {
+    uint64_t* keys;
+    uint64_t* vals;
+    uint32_t* loc;  // storage position + 1 of the largest stored key below it (0: front)
+    uint8_t* height;
+};
+
+struct HashParams {
+    uint64_t seed_mix;  // splitmix64(seed)
+    int b;              // P = 2^-b
+    int hmax;           // min(32, 64 / b)
+};
+
+// ---------------------------------------------------------------------------------
+// Tower height (Definition 1 with the geometric draw replaced by a seeded key hash).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint32_t tower_height(uint64_t key, const HashParams& hp) {
+    uint64_t h = splitmix64(key ^ hp.seed_mix);
+    int tz = h ? (__ffsll((long long)h) - 1) : 64;
+    int lvl = tz / hp.b;
+    if (lvl > hp.hmax - 1) lvl = hp.hmax - 1;
+    return 1u + (uint32_t)lvl;
+}
+
+// ---------------------------------------------------------------------------------
+// Memory helpers.
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ uint32_t lanemask_le() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------------
+// Decoupled look-back (Merrill and Garland, "Single-pass parallel prefix scan with
+// decoupled look-back", 2016). Descriptor word: epoch (32) | flag (2) | value (30).
+// The epoch is unique per launch, so descriptors never need clearing between
+// launches: a word from an older launch reads as "not yet published".
+constexpr uint64_t kFlagAgg = 1ull << 30;
+constexpr uint64_t kFlagPrefix = 2ull << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+
+template <bool kMax>
+__device__ __forceinline__ uint32_t lb_op(uint32_t a, uint32_t b) {
+    return kMax ? (a > b ? a : b) : a + b;
+}
+
+// Publishes `agg` for tile `tile` and returns the exclusive prefix of the tiles before
+// it (identity 0 for both sum and max). Sets *ok = false and records kErrTimeout if a
+// predecessor never published within the spin bound.
+template <bool kMax>
+__device__ uint32_t lookback(uint64_t* desc, size_t stride, uint32_t tile, uint32_t epoch,
+                             uint32_t agg, uint32_t* err, bool* ok) {
+    const uint64_t tag = (uint64_t)epoch << 32;
+    *ok = true;
+    if (tile == 0) {
+        st_relaxed(desc, tag | kFlagPrefix | (agg & kValMask));
+        return 0;
+    }
+    st_relaxed(desc + (size_t)tile * stride, tag | kFlagAgg | (agg & kValMask));
+    uint32_t excl = 0;
+    int64_t t = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (t >= 0) {
+        uint64_t d = ld_relaxed(desc + (size_t)t * stride);
+        uint64_t flag = d & (3ull << 30);
+        if ((uint32_t)(d >> 32) != epoch || flag == 0) {
+            ++spins;
+            if (spins > kSpinLimit) {
+                atomicOr(err, kErrTimeout);
+                *ok = false;
+                return 0;
+            }
+            if ((spins & 1023u) == 0 && *(volatile uint32_t*)err) {  // another wait gave up
+                *ok = false;
+                return 0;
+            }
+            if (spins > 32) __nanosleep(100);
+            continue;
+        }
+        excl = lb_op<kMax>(excl, (uint32_t)(d & kValMask));
+        if (flag == kFlagPrefix) break;
+        --t;
+    }
+    st_relaxed(desc + (size_t)tile * stride, tag | kFlagPrefix | (lb_op<kMax>(excl, agg) & kValMask));
+    return excl;
+}
+
+// ---------------------------------------------------------------------------------
+// TMA bulk copies (cp.async.bulk, global -> shared) completing on an mbarrier.
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Requires 16-byte aligned addresses and a size that is a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for one phase. On timeout records kErrTimeout and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, uint32_t* err) {
+    for (uint32_t i = 0; i < (1u << 20); ++i) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if (i > 16) __nanosleep(64);
+    }
+    atomicOr(err, kErrTimeout);
+    return false;
+}
+
+// Block-uniform test of the sticky error word (every thread gets the same answer).
+__device__ __forceinline__ bool block_sees_error(const uint32_t* err) {
+    return __syncthreads_or(threadIdx.x == 0 && *(volatile const uint32_t*)err) != 0;
+}
+
+// ---------------------------------------------------------------------------------
+// Block-wide exclusive sum over one value per thread (blockDim.x a multiple of 32).
+template <int kThreads>
+__device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t* warp_tmp, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < kThreads / 32) ? warp_tmp[lane] : 0;
+        uint32_t s = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kThreads / 32) warp_tmp[lane] = s - w;
+        if (lane == kThreads / 32 - 1) warp_tmp[32] = s;
+    }
+    __syncthreads();
+    uint32_t r = warp_tmp[warp] + x - v;
+    if (total) *total = warp_tmp[32];
+    __syncthreads();
+    return r;
+}
+
+// Block-wide inclusive max over one value per thread; returns the exclusive max.
+template <int kThreads>
+__device__ __forceinline__ uint32_t block_excl_max(uint32_t v, uint32_t* warp_tmp, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x = max(x, y);
+    }
+    uint32_t ex = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) ex = 0;
+    if (lane == 31) warp_tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < kThreads / 32) ? warp_tmp[lane] : 0;
+        uint32_t s = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s = max(s, y);
+        }
+        uint32_t e = __shfl_up_sync(0xffffffffu, s, 1);
+        if (lane == 0) e = 0;
+        if (lane < kThreads / 32) warp_tmp[lane] = e;
+        if (lane == kThreads / 32 - 1) warp_tmp[32] = s;
+    }
+    __syncthreads();
+    uint32_t r = max(warp_tmp[warp], ex);
+    if (total) *total = warp_tmp[32];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------------
+// Host-side launch wrappers (defined in the .cu files).
+struct SortBuffers {
+    uint64_t* in_k;  // packed keys (written by the pack kernel)
+    uint32_t* in_p;  // packed payload: op << 30 | arrival index
+    uint64_t* a_k;
+    uint32_t* a_p;
+    uint64_t* b_k;
+    uint32_t* b_p;
+    uint32_t* dofs;  // [8][256] digit offsets
+    uint64_t* desc;  // [tiles][256] look-back descriptors
+};
+
+// Radix sort of (key, payload) pairs: result in a_k / a_p, stable, by key.
+// ops may be NULL (all searches). Counts invalid queries into bm->invalid.
+cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, const SortBuffers& sb,
+                        BatchMeta* bm, uint32_t* err, uint32_t& epoch, cudaStream_t s, int num_sms);
+
+struct DescendArgs {
+    const uint64_t* sk;  // sorted keys
+    const DevMeta* m;
+    const BatchMeta* bm;
+    const uint64_t* lkeys;
+    const uint32_t* ldown;
+    Storage st;
+    uint32_t* loc;
+    uint8_t* flags;
+    uint64_t* val0;
+    uint32_t n;
+    uint32_t* err;
+};
+cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms);
+
+struct ApplyArgs {
+    const uint64_t* sk;
+    const uint32_t* sp;
+    const uint32_t* loc;
+    const uint8_t* flags;
+    const uint64_t* val0;
+    const uint64_t* uvals;
+    pi_result_t* results;
+    Storage st;
+    NewNodes nn;
+    DevMeta* m;
+    BatchMeta* bm;
+    uint64_t* desc;  // 2 * tiles words
+    uint32_t n;
+    HashParams hp;
+    uint32_t* err;
+};
+cudaError_t launch_apply(const ApplyArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
+
+struct RebuildArgs {
+    Storage st;
+    NewNodes nn;
+    DevMeta* m;
+    BatchMeta* bm;
+    uint64_t* lkeys;
+    uint32_t* ldown;
+    uint64_t* desc;       // look-back descriptors: max(tiles_merge, tiles_rebuild * 32)
+    uint32_t* tile_live;  // scratch
+    uint32_t index_cap;   // entries (without padding)
+    uint32_t size_ub;     // upper bound of the storage size after the batch
+    uint32_t rebuild_policy;
+    uint32_t threshold_pct;
+    uint32_t force_rebuild;  // 1: rebuild regardless; 2: initial build (not a batch)
+    uint32_t st_cap;         // storage capacity (nodes, padding excluded)
+    uint32_t* err;
+};
+cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
+cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s);
+cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
+
+// Bulk build: sorted (key, payload) -> storage layer (last duplicate wins) + counts.
+struct CreateArgs {
+    const uint64_t* sk;
+    const uint32_t* sp;
+    const uint64_t* uvals;
+    uint32_t n;
+    Storage st;
+    DevMeta* m;
+    BatchMeta* bm;
+    uint64_t* desc;
+    HashParams hp;
+    uint32_t st_cap;
+    uint32_t* err;
+};
+cudaError_t launch_create_storage(const CreateArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
+
+// Test-support compactions.
+cudaError_t launch_export_live(const Storage& st, const DevMeta* m, uint64_t* keys_out,
+                               uint64_t* vals_out, uint64_t cap, uint32_t* count, uint64_t* desc,
+                               uint32_t* tile_ctr, uint32_t& epoch, uint32_t* err, cudaStream_t s,
+                               int num_sms, uint32_t size_ub);
+
+}  // namespace pi

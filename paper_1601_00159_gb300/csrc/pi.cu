@@ -1,0 +1,728 @@
+// Host side of the C ABI (include/pi.h): owns the device state of an index and
+// enqueues the batch pipeline of Algorithm 1 on the caller's stream:
+//   K0/K1 pack + radix sort  ->  K2/K3 descent + locate  ->  K4/K5 ownership + apply
+//   ->  K6 merge + level layout + rebuild  ->  async copy of the small device meta to
+//   a pinned mailbox (used only to tighten capacity bounds; never waited on, except
+//   when a bound could be exceeded).
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+using namespace pi;
+
+namespace {
+
+thread_local int g_last_error = PI_OK;
+
+constexpr uint64_t kMinStorage = 1u << 16;
+
+struct Scratch {
+    uint64_t cap = 0;  // queries
+    uint64_t* in_k = nullptr;
+    uint32_t* in_p = nullptr;
+    uint64_t* a_k = nullptr;
+    uint32_t* a_p = nullptr;
+    uint64_t* b_k = nullptr;
+    uint32_t* b_p = nullptr;
+    uint32_t* loc = nullptr;
+    uint8_t* flags = nullptr;
+    uint64_t* val0 = nullptr;
+    NewNodes nn{};
+};
+
+struct Staging {
+    uint64_t cap = 0;
+    uint8_t* ops = nullptr;
+    uint64_t* keys = nullptr;
+    uint64_t* vals = nullptr;
+    pi_result_t* res = nullptr;
+};
+
+}  // namespace
+
+struct pi_index {
+    int device = 0;
+    int num_sms = 0;
+    HashParams hp{};
+    uint32_t rebuild_policy = 0, threshold_pct = 15;
+    DevMeta* d_meta = nullptr;
+    BatchMeta* d_bm = nullptr;
+    uint32_t* d_dofs = nullptr;
+    uint32_t* d_count = nullptr;
+    Storage st{};
+    uint64_t st_cap = 0;  // nodes per buffer, padding excluded
+    uint64_t* lkeys = nullptr;
+    uint32_t* ldown = nullptr;
+    uint64_t idx_cap = 0;  // entries, padding excluded
+    Scratch sc;
+    Staging stg;
+    uint64_t* desc = nullptr;
+    uint64_t desc_words = 0;
+    uint32_t epoch = 1;
+    // Ring of mailboxes: batch b copies the device meta to slot b % kRing and records
+    // ev[b % kRing]; the newest completed slot bounds the host's view of the sizes.
+    DevMeta* h_mbox = nullptr;  // pinned, kRing slots
+    cudaEvent_t ev[64] = {};
+    uint64_t ring_n[64] = {};   // queries of the batch in each slot
+    uint64_t issued = 0;        // batches issued
+    uint64_t seen = 0;          // batches whose mailbox has been read (a prefix)
+    DevMeta known{};       // last mailbox snapshot
+    uint64_t pending_n = 0;  // queries issued after that snapshot
+    bool force_rebuild = false;
+    // stage timing (pi_profile): events recorded between the pipeline's kernels
+    bool prof = false;
+    cudaEvent_t* pev = nullptr;  // kProfSlots batches x (PI_NUM_STAGES + 1) events
+    uint32_t pused = 0;          // batches recorded but not folded yet
+    double pms[PI_NUM_STAGES] = {};
+    uint64_t pbatches = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T** p, uint64_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+uint64_t host_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int shift_of(double p) {
+    for (int b = 1; b <= 4; ++b)
+        if (p == 1.0 / (double)(1u << b)) return b;
+    return 0;
+}
+
+int map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return PI_OK;
+    if (e == cudaErrorMemoryAllocation) return PI_ERR_OOM;
+    return PI_ERR_CUDA;
+}
+
+// Look-back descriptors needed for q queries and a storage capacity of s nodes.
+uint64_t desc_need(uint64_t q, uint64_t s) {
+    uint64_t a = ((q + 4095) / 4096) * 256;  // sort passes
+    uint64_t b = 2 * ((q + 2047) / 2048);    // apply
+    uint64_t c = (s / 4096 + 2) * 32;        // rebuild (and merge, export)
+    uint64_t m = a > b ? a : b;
+    return (m > c ? m : c) + 64;
+}
+
+cudaError_t ensure_desc(pi_index* x, uint64_t words) {
+    if (words <= x->desc_words) return cudaSuccess;
+    dfree(x->desc);
+    cudaError_t e = dalloc(&x->desc, words);
+    if (e != cudaSuccess) {
+        x->desc_words = 0;
+        return e;
+    }
+    e = cudaMemset(x->desc, 0, words * sizeof(uint64_t));
+    x->desc_words = words;
+    return e;
+}
+
+uint32_t next_epochs(pi_index* x, uint32_t count, cudaStream_t s) {
+    // Epochs tag look-back descriptors; on wrap-around clear them so no stale word can
+    // carry a reused epoch.
+    if (x->epoch > 0xFFFFFFFFu - count - 64u) {
+        cudaMemsetAsync(x->desc, 0, x->desc_words * sizeof(uint64_t), s);
+        x->epoch = 1;
+    }
+    return x->epoch;
+}
+
+void free_scratch(Scratch& s) {
+    dfree(s.in_k); dfree(s.in_p); dfree(s.a_k); dfree(s.a_p); dfree(s.b_k); dfree(s.b_p);
+    dfree(s.loc); dfree(s.flags); dfree(s.val0);
+    dfree(s.nn.keys); dfree(s.nn.vals); dfree(s.nn.loc); dfree(s.nn.height);
+    s.cap = 0;
+}
+
+cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
+    cudaError_t e = cudaSuccess;
+    const uint64_t c = q + kPad;
+#define PI_TRY(expr) do { e = (expr); if (e != cudaSuccess) { free_scratch(s); return e; } } while (0)
+    PI_TRY(dalloc(&s.in_k, c)); PI_TRY(dalloc(&s.in_p, c));
+    PI_TRY(dalloc(&s.a_k, c)); PI_TRY(dalloc(&s.a_p, c));
+    PI_TRY(dalloc(&s.b_k, c)); PI_TRY(dalloc(&s.b_p, c));
+    PI_TRY(dalloc(&s.loc, c)); PI_TRY(dalloc(&s.flags, c)); PI_TRY(dalloc(&s.val0, c));
+    PI_TRY(dalloc(&s.nn.keys, c)); PI_TRY(dalloc(&s.nn.vals, c));
+    PI_TRY(dalloc(&s.nn.loc, c)); PI_TRY(dalloc(&s.nn.height, c));
+#undef PI_TRY
+    s.cap = q;
+    return cudaSuccess;
+}
+
+void free_storage(Storage& st) {
+    for (int i = 0; i < 2; ++i) {
+        dfree(st.keys[i]); dfree(st.vals[i]); dfree(st.meta[i]);
+    }
+}
+
+cudaError_t alloc_storage(Storage& st, uint64_t cap) {
+    cudaError_t e;
+    for (int i = 0; i < 2; ++i) {
+        if ((e = dalloc(&st.keys[i], cap + kPad)) != cudaSuccess) break;
+        if ((e = dalloc(&st.vals[i], cap + kPad)) != cudaSuccess) break;
+        if ((e = dalloc(&st.meta[i], cap + kPad)) != cudaSuccess) break;
+        cudaMemset(st.meta[i], 0, cap + kPad);
+    }
+    if (e != cudaSuccess) free_storage(st);
+    return e;
+}
+
+constexpr uint32_t kProfSlots = 4096;
+
+void prof_fold(pi_index* x) {
+    for (uint32_t b = 0; b < x->pused; ++b) {
+        cudaEvent_t* e = x->pev + (size_t)b * (PI_NUM_STAGES + 1);
+        cudaEventSynchronize(e[PI_NUM_STAGES]);
+        for (int st = 0; st < PI_NUM_STAGES; ++st) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, e[st], e[st + 1]) == cudaSuccess) x->pms[st] += ms;
+        }
+        x->pbatches++;
+    }
+    x->pused = 0;
+}
+
+// Event for stage boundary k of the batch being enqueued (nullptr when not profiling).
+cudaEvent_t prof_event(pi_index* x, int k) {
+    if (!x->prof) return nullptr;
+    return x->pev[(size_t)x->pused * (PI_NUM_STAGES + 1) + k];
+}
+
+void prof_mark(pi_index* x, int k, cudaStream_t s) {
+    if (cudaEvent_t e = prof_event(x, k)) cudaEventRecord(e, s);
+}
+
+void destroy(pi_index* x) {
+    if (!x) return;
+    cudaSetDevice(x->device);
+    cudaDeviceSynchronize();
+    if (x->pev) {
+        for (size_t i = 0; i < (size_t)kProfSlots * (PI_NUM_STAGES + 1); ++i) cudaEventDestroy(x->pev[i]);
+        delete[] x->pev;
+    }
+    free_scratch(x->sc);
+    dfree(x->stg.ops); dfree(x->stg.keys); dfree(x->stg.vals); dfree(x->stg.res);
+    free_storage(x->st);
+    dfree(x->lkeys); dfree(x->ldown);
+    dfree(x->desc); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
+    if (x->h_mbox) cudaFreeHost(x->h_mbox);
+    for (auto& e : x->ev)
+        if (e) cudaEventDestroy(e);
+    delete x;
+}
+
+SortBuffers sort_buffers(pi_index* x, const Scratch& s) {
+    SortBuffers sb;
+    sb.in_k = s.in_k; sb.in_p = s.in_p; sb.a_k = s.a_k; sb.a_p = s.a_p; sb.b_k = s.b_k; sb.b_p = s.b_p;
+    sb.dofs = x->d_dofs;
+    sb.desc = x->desc;
+    return sb;
+}
+
+// Read the device meta synchronously (after a stream sync).
+cudaError_t read_meta(pi_index* x, cudaStream_t s, DevMeta* out) {
+    cudaError_t e = cudaMemcpyAsync(out, x->d_meta, sizeof(DevMeta), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
+constexpr uint64_t kRing = 64;
+
+// Non-blocking: adopt the newest completed batch's mailbox.
+void refresh_known(pi_index* x) {
+    uint64_t newest = x->seen;
+    for (uint64_t b = x->issued; b > x->seen; --b) {
+        if (cudaEventQuery(x->ev[(b - 1) % kRing]) == cudaSuccess) {
+            newest = b;
+            break;
+        }
+    }
+    if (newest == x->seen) return;
+    x->known = x->h_mbox[(newest - 1) % kRing];
+    x->seen = newest;
+    uint64_t p = 0;
+    for (uint64_t b = newest; b < x->issued; ++b) p += x->ring_n[b % kRing];
+    x->pending_n = p;
+}
+
+cudaError_t sync_known(pi_index* x, cudaStream_t s) {
+    cudaError_t e = read_meta(x, s, &x->known);
+    if (e == cudaSuccess) {
+        for (uint64_t b = x->seen; b < x->issued; ++b) cudaEventSynchronize(x->ev[b % kRing]);
+        x->seen = x->issued;
+        x->pending_n = 0;
+    }
+    return e;
+}
+
+int sticky_error(const DevMeta& m) {
+    if (m.error & kErrTimeout) return PI_ERR_TIMEOUT;
+    if (m.error) return PI_ERR_CUDA;
+    return PI_OK;
+}
+
+cudaError_t grow_storage(pi_index* x, uint64_t need, cudaStream_t s) {
+    uint64_t cap = need + need / 2 + kMinStorage;
+    if (cap > PI_MAX_KEYS) cap = PI_MAX_KEYS;
+    Storage ns{};
+    cudaError_t e = alloc_storage(ns, cap);
+    if (e != cudaSuccess) return e;
+    const uint32_t cur = x->known.cur;
+    const uint64_t cnt = (uint64_t)x->known.size + 1;  // with the sentinel
+    cudaMemcpyAsync(ns.keys[0], x->st.keys[cur], cnt * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(ns.vals[0], x->st.vals[cur], cnt * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(ns.meta[0], x->st.meta[cur], cnt, cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(&x->d_meta->cur, 0, sizeof(uint32_t), s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free_storage(ns);
+        return e;
+    }
+    free_storage(x->st);
+    x->st = ns;
+    x->st_cap = cap;
+    x->known.cur = 0;
+    return ensure_desc(x, desc_need(x->sc.cap, cap));
+}
+
+cudaError_t grow_index(pi_index* x, uint64_t need, cudaStream_t s) {
+    uint64_t cap = need + need / 4 + 4096;
+    uint64_t* nk = nullptr;
+    uint32_t* nd = nullptr;
+    cudaError_t e = dalloc(&nk, cap + kPad);
+    if (e == cudaSuccess) e = dalloc(&nd, cap + kPad);
+    if (e != cudaSuccess) {
+        dfree(nk);
+        dfree(nd);
+        return e;
+    }
+    const uint64_t used = x->known.index_total;
+    if (x->lkeys && used) {
+        cudaMemcpyAsync(nk, x->lkeys, used * 8, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(nd, x->ldown, used * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        dfree(nk);
+        dfree(nd);
+        return e;
+    }
+    dfree(x->lkeys);
+    dfree(x->ldown);
+    x->lkeys = nk;
+    x->ldown = nd;
+    x->idx_cap = cap;
+    x->force_rebuild = true;
+    return cudaSuccess;
+}
+
+RebuildArgs rebuild_args(pi_index* x, uint32_t size_ub, uint32_t force) {
+    RebuildArgs r{};
+    r.st = x->st;
+    r.nn = x->sc.nn;
+    r.m = x->d_meta;
+    r.bm = x->d_bm;
+    r.lkeys = x->lkeys;
+    r.ldown = x->ldown;
+    r.desc = x->desc;
+    r.tile_live = nullptr;
+    r.index_cap = (uint32_t)(x->idx_cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : x->idx_cap);
+    r.size_ub = size_ub;
+    r.rebuild_policy = x->rebuild_policy;
+    r.threshold_pct = x->threshold_pct;
+    r.force_rebuild = force;
+    r.st_cap = (uint32_t)x->st_cap;
+    r.err = &x->d_meta->error;
+    return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pi_last_error(void) { return g_last_error; }
+
+pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t n, double promote_p,
+                         uint64_t seed, const pi_config_t* cfg) {
+    g_last_error = PI_OK;
+    const int b = shift_of(promote_p);
+    if (b == 0 || n > PI_MAX_KEYS || (n > 0 && (!keys || !values))) {
+        g_last_error = PI_ERR_INVALID_ARG;
+        return nullptr;
+    }
+    if (cfg && cfg->struct_size != 0 && cfg->struct_size < sizeof(pi_config_t)) {
+        g_last_error = PI_ERR_INVALID_ARG;
+        return nullptr;
+    }
+    pi_index* x = new (std::nothrow) pi_index();
+    if (!x) {
+        g_last_error = PI_ERR_OOM;
+        return nullptr;
+    }
+    cudaError_t e = cudaGetDevice(&x->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&x->num_sms, cudaDevAttrMultiProcessorCount, x->device);
+    if (e != cudaSuccess) {
+        g_last_error = PI_ERR_CUDA;
+        delete x;
+        return nullptr;
+    }
+    x->hp.b = b;
+    x->hp.hmax = (64 / b) < 32 ? (64 / b) : 32;
+    x->hp.seed_mix = host_splitmix64(seed);
+    if (cfg) {
+        x->rebuild_policy = cfg->rebuild_policy;
+        if (cfg->rebuild_threshold_pct) x->threshold_pct = cfg->rebuild_threshold_pct;
+    }
+    uint64_t st_cap = n + (n / 2 > kMinStorage ? n / 2 : kMinStorage);
+    if (cfg && cfg->storage_capacity > st_cap) st_cap = cfg->storage_capacity;
+    if (st_cap > PI_MAX_KEYS) st_cap = PI_MAX_KEYS;
+
+    cudaStream_t s = nullptr;
+    Scratch tmp{};
+    int rc = PI_OK;
+    do {
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) break;
+        for (auto& ev : x->ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) break;
+        if (e != cudaSuccess) break;
+        if ((e = cudaMallocHost(reinterpret_cast<void**>(&x->h_mbox), kRing * sizeof(DevMeta))) != cudaSuccess) break;
+        if ((e = dalloc(&x->d_meta, 1)) != cudaSuccess) break;
+        if ((e = dalloc(&x->d_bm, 1)) != cudaSuccess) break;
+        if ((e = dalloc(&x->d_dofs, 8 * 256)) != cudaSuccess) break;
+        if ((e = dalloc(&x->d_count, 1)) != cudaSuccess) break;
+        cudaMemsetAsync(x->d_meta, 0, sizeof(DevMeta), s);
+        cudaMemsetAsync(x->d_bm, 0, sizeof(BatchMeta), s);
+        if ((e = alloc_storage(x->st, st_cap)) != cudaSuccess) break;
+        x->st_cap = st_cap;
+        if ((e = ensure_desc(x, desc_need(n, st_cap))) != cudaSuccess) break;
+        // 1. sort (key, arrival) and keep the last of every key run
+        if (n > 0) {
+            if ((e = alloc_scratch(tmp, n)) != cudaSuccess) break;
+            SortBuffers sb = sort_buffers(x, tmp);
+            uint32_t ep = next_epochs(x, 16, s);
+            if ((e = launch_sort(nullptr, keys, (uint32_t)n, sb, x->d_bm, &x->d_meta->error, ep, s, x->num_sms)) !=
+                cudaSuccess)
+                break;
+            x->epoch = ep;
+            BatchMeta hbm;
+            if ((e = cudaMemcpyAsync(&hbm, x->d_bm, sizeof(BatchMeta), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+            if (hbm.invalid) {
+                rc = PI_ERR_INVALID_ARG;
+                break;
+            }
+            CreateArgs ca{};
+            ca.sk = tmp.a_k;
+            ca.sp = tmp.a_p;
+            ca.uvals = values;
+            ca.n = (uint32_t)n;
+            ca.st = x->st;
+            ca.m = x->d_meta;
+            ca.bm = x->d_bm;
+            ca.desc = x->desc;
+            ca.hp = x->hp;
+            ca.st_cap = (uint32_t)x->st_cap;
+            ca.err = &x->d_meta->error;
+            ep = next_epochs(x, 4, s);
+            if ((e = launch_create_storage(ca, ep, s, x->num_sms)) != cudaSuccess) break;
+            x->epoch = ep;
+        }
+        DevMeta hm;
+        if ((e = read_meta(x, s, &hm)) != cudaSuccess) break;
+        uint64_t need = 0;
+        for (int l = 2; l < kLevelSlots; ++l)
+            if (hm.cnt[l]) need += (uint64_t)hm.cnt[l] + 1;
+        uint64_t icap = need + need / 4 + 4096;
+        if (cfg && cfg->index_capacity) icap = cfg->index_capacity;
+        if ((e = dalloc(&x->lkeys, icap + kPad)) != cudaSuccess) break;
+        if ((e = dalloc(&x->ldown, icap + kPad)) != cudaSuccess) break;
+        x->idx_cap = icap;
+        // 2. lay out and build the index layer
+        cudaMemsetAsync(x->d_bm, 0, sizeof(BatchMeta), s);
+        RebuildArgs ra = rebuild_args(x, (uint32_t)hm.size, 2u);
+        uint32_t ep = next_epochs(x, 4, s);
+        if ((e = launch_merge(ra, ep, s, x->num_sms)) != cudaSuccess) break;
+        if ((e = launch_level_bases(ra, s)) != cudaSuccess) break;
+        if ((e = launch_rebuild(ra, ep, s, x->num_sms)) != cudaSuccess) break;
+        x->epoch = ep;
+        if ((e = read_meta(x, s, &x->known)) != cudaSuccess) break;
+        if (x->known.error) {
+            rc = sticky_error(x->known);
+            break;
+        }
+    } while (0);
+    free_scratch(tmp);
+    if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    if (rc == PI_OK && e != cudaSuccess) rc = map_cuda(e);
+    if (rc != PI_OK) {
+        g_last_error = rc;
+        destroy(x);
+        return nullptr;
+    }
+    return x;
+}
+
+pi_index_t* pi_create(const uint64_t* keys, const uint64_t* values, uint64_t n, double promote_p,
+                      uint64_t seed) {
+    return pi_create_ex(keys, values, n, promote_p, seed, nullptr);
+}
+
+int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, const uint64_t* values,
+                     uint64_t n, pi_result_t* results, pi_stream_t stream) {
+    if (!x) return PI_ERR_INVALID_ARG;
+    if (n == 0) return PI_OK;
+    if (!ops || !keys || !values || !results || n > PI_MAX_BATCH) return PI_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    refresh_known(x);
+    if (int rc = sticky_error(x->known)) return rc;
+    // capacities (grow rarely; growing synchronises the stream)
+    if (n > x->sc.cap) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
+        free_scratch(x->sc);
+        uint64_t q = n < 4096 ? 4096 : n;
+        if ((e = alloc_scratch(x->sc, q)) != cudaSuccess) return map_cuda(e);
+        if ((e = ensure_desc(x, desc_need(q, x->st_cap))) != cudaSuccess) return map_cuda(e);
+    }
+    uint64_t size_ub = (uint64_t)x->known.size + x->pending_n + n;
+    if (size_ub > x->st_cap) {
+        if ((e = sync_known(x, s)) != cudaSuccess) return map_cuda(e);
+        if (int rc = sticky_error(x->known)) return rc;
+        size_ub = (uint64_t)x->known.size + n;
+        if (size_ub > PI_MAX_KEYS) return PI_ERR_INVALID_ARG;
+        if (size_ub > x->st_cap && (e = grow_storage(x, size_ub, s)) != cudaSuccess) return map_cuda(e);
+    }
+    if (x->known.grow_request) {
+        if ((e = sync_known(x, s)) != cudaSuccess) return map_cuda(e);
+        if (x->known.grow_request && x->known.index_need + 64ull > x->idx_cap) {
+            if ((e = grow_index(x, x->known.index_need, s)) != cudaSuccess) return map_cuda(e);
+        }
+        x->known.grow_request = 0;
+    }
+    uint32_t ep = next_epochs(x, 16, s);
+    if (x->prof && x->pused == kProfSlots) prof_fold(x);
+    prof_mark(x, 0, s);
+    cudaMemsetAsync(x->d_bm, 0, sizeof(BatchMeta), s);
+    SortBuffers sb = sort_buffers(x, x->sc);
+    if ((e = launch_sort(ops, keys, (uint32_t)n, sb, x->d_bm, &x->d_meta->error, ep, s, x->num_sms)) != cudaSuccess)
+        return map_cuda(e);
+    DescendArgs da{};
+    da.sk = x->sc.a_k;
+    da.m = x->d_meta;
+    da.bm = x->d_bm;
+    da.lkeys = x->lkeys;
+    da.ldown = x->ldown;
+    da.st = x->st;
+    da.loc = x->sc.loc;
+    da.flags = x->sc.flags;
+    da.val0 = x->sc.val0;
+    da.n = (uint32_t)n;
+    da.err = &x->d_meta->error;
+    prof_mark(x, 1, s);
+    if ((e = launch_descend(da, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 2, s);
+    ApplyArgs aa{};
+    aa.sk = x->sc.a_k;
+    aa.sp = x->sc.a_p;
+    aa.loc = x->sc.loc;
+    aa.flags = x->sc.flags;
+    aa.val0 = x->sc.val0;
+    aa.uvals = values;
+    aa.results = results;
+    aa.st = x->st;
+    aa.nn = x->sc.nn;
+    aa.m = x->d_meta;
+    aa.bm = x->d_bm;
+    aa.desc = x->desc;
+    aa.n = (uint32_t)n;
+    aa.hp = x->hp;
+    aa.err = &x->d_meta->error;
+    if ((e = launch_apply(aa, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 3, s);
+    RebuildArgs ra = rebuild_args(x, (uint32_t)size_ub, x->force_rebuild ? 1u : 0u);
+    if ((e = launch_merge(ra, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 4, s);
+    if ((e = launch_level_bases(ra, s)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 5, s);
+    if ((e = launch_rebuild(ra, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 6, s);
+    if (x->prof) x->pused++;
+    x->epoch = ep;
+    x->force_rebuild = false;
+    const uint64_t slot = x->issued % kRing;
+    if (x->issued - x->seen >= kRing) {  // the slot is still unread: wait for its batch
+        cudaEventSynchronize(x->ev[slot]);
+        refresh_known(x);
+    }
+    cudaMemcpyAsync(&x->h_mbox[slot], x->d_meta, sizeof(DevMeta), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(x->ev[slot], s);
+    x->ring_n[slot] = n;
+    x->issued++;
+    x->pending_n += n;
+    return map_cuda(cudaGetLastError());
+}
+
+int pi_execute_batch_host(pi_index_t* x, const uint8_t* ops_host, const uint64_t* keys_host,
+                          const uint64_t* values_host, uint64_t n, pi_result_t* results_host,
+                          pi_stream_t stream) {
+    if (!x) return PI_ERR_INVALID_ARG;
+    if (n == 0) return PI_OK;
+    if (!ops_host || !keys_host || !values_host || !results_host || n > PI_MAX_BATCH) return PI_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    Staging& g = x->stg;
+    if (n > g.cap) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
+        dfree(g.ops); dfree(g.keys); dfree(g.vals); dfree(g.res);
+        g.cap = 0;
+        if ((e = dalloc(&g.ops, n)) != cudaSuccess || (e = dalloc(&g.keys, n)) != cudaSuccess ||
+            (e = dalloc(&g.vals, n)) != cudaSuccess || (e = dalloc(&g.res, n)) != cudaSuccess) {
+            dfree(g.ops); dfree(g.keys); dfree(g.vals); dfree(g.res);
+            return map_cuda(e);
+        }
+        g.cap = n;
+    }
+    cudaMemcpyAsync(g.ops, ops_host, n, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(g.keys, keys_host, n * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(g.vals, values_host, n * 8, cudaMemcpyHostToDevice, s);
+    int rc = pi_execute_batch(x, g.ops, g.keys, g.vals, n, g.res, stream);
+    if (rc != PI_OK) return rc;
+    e = cudaMemcpyAsync(results_host, g.res, n * sizeof(pi_result_t), cudaMemcpyDeviceToHost, s);
+    return map_cuda(e);
+}
+
+void pi_destroy(pi_index_t* x) { destroy(x); }
+
+int pi_profile(pi_index_t* x, int enable) {
+    if (!x) return PI_ERR_INVALID_ARG;
+    if (enable && !x->pev) {
+        const size_t cnt = (size_t)kProfSlots * (PI_NUM_STAGES + 1);
+        x->pev = new (std::nothrow) cudaEvent_t[cnt];
+        if (!x->pev) return PI_ERR_OOM;
+        for (size_t i = 0; i < cnt; ++i) {
+            if (cudaEventCreate(&x->pev[i]) != cudaSuccess) {
+                for (size_t j = 0; j < i; ++j) cudaEventDestroy(x->pev[j]);
+                delete[] x->pev;
+                x->pev = nullptr;
+                return PI_ERR_CUDA;
+            }
+        }
+    }
+    if (x->pused) prof_fold(x);
+    x->prof = enable != 0;
+    for (int st = 0; st < PI_NUM_STAGES; ++st) x->pms[st] = 0.0;
+    x->pbatches = 0;
+    return PI_OK;
+}
+
+int pi_profile_read(pi_index_t* x, double* stage_ms_host, uint64_t* batches_host, pi_stream_t stream) {
+    if (!x || !stage_ms_host || !batches_host) return PI_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return map_cuda(e);
+    prof_fold(x);
+    for (int st = 0; st < PI_NUM_STAGES; ++st) stage_ms_host[st] = x->pms[st];
+    *batches_host = x->pbatches;
+    return PI_OK;
+}
+
+int pi_status(pi_index_t* x, pi_stream_t stream) {
+    if (!x) return PI_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = sync_known(x, s);
+    if (e != cudaSuccess) return map_cuda(e);
+    return sticky_error(x->known);
+}
+
+int pi_info(pi_index_t* x, pi_info_t* out, pi_stream_t stream) {
+    if (!x || !out) return PI_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = sync_known(x, s);
+    if (e != cudaSuccess) return map_cuda(e);
+    const DevMeta& m = x->known;
+    std::memset(out, 0, sizeof(*out));
+    out->size = m.size;
+    out->live = m.cnt[1];
+    out->tombstones = m.tombs;
+    out->top_level = m.H;
+    out->bottom_built = m.Lb;
+    out->smem_low_level = m.Ls;
+    out->promote_shift = (uint32_t)x->hp.b;
+    for (int l = 1; l < kLevelSlots; ++l) out->level_size[l] = m.cnt[l];
+    out->storage_capacity = x->st_cap;
+    out->index_capacity = x->idx_cap;
+    out->batches = m.batches;
+    out->rebuilds = m.rebuilds;
+    return sticky_error(m);
+}
+
+int pi_export(pi_index_t* x, uint64_t* keys_out, uint64_t* vals_out, uint64_t cap, uint64_t* n_out_host,
+              pi_stream_t stream) {
+    if (!x || !n_out_host || (cap > 0 && (!keys_out || !vals_out))) return PI_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = sync_known(x, s);
+    if (e != cudaSuccess) return map_cuda(e);
+    if (int rc = sticky_error(x->known)) return rc;
+    cudaMemsetAsync(x->d_count, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(&x->d_bm->tile_ctr[12], 0, sizeof(uint32_t), s);
+    uint32_t ep = next_epochs(x, 2, s);
+    e = launch_export_live(x->st, x->d_meta, keys_out, vals_out, cap, x->d_count, x->desc, &x->d_bm->tile_ctr[12], ep,
+                           &x->d_meta->error, s, x->num_sms, x->known.size);
+    x->epoch = ep;
+    if (e != cudaSuccess) return map_cuda(e);
+    uint32_t c = 0;
+    e = cudaMemcpyAsync(&c, x->d_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return map_cuda(e);
+    *n_out_host = c;
+    return PI_OK;
+}
+
+int pi_export_level(pi_index_t* x, int level, uint64_t* keys_out, uint32_t* down_out, uint64_t cap,
+                    uint64_t* n_out_host, pi_stream_t stream) {
+    if (!x || !n_out_host || level < 2 || level >= kLevelSlots || (cap > 0 && !keys_out)) return PI_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = sync_known(x, s);
+    if (e != cudaSuccess) return map_cuda(e);
+    const DevMeta& m = x->known;
+    if ((uint32_t)level > m.H) {
+        *n_out_host = 0;
+        return PI_OK;
+    }
+    if ((uint32_t)level < m.Lb) {
+        *n_out_host = 0;
+        return PI_ERR_NOT_BUILT;
+    }
+    const uint64_t cnt = m.n[level];
+    *n_out_host = cnt;
+    const uint64_t c = cnt < cap ? cnt : cap;
+    if (c) {
+        cudaMemcpyAsync(keys_out, x->lkeys + m.base[level], c * 8, cudaMemcpyDeviceToDevice, s);
+        if (down_out) cudaMemcpyAsync(down_out, x->ldown + m.base[level], c * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    e = cudaStreamSynchronize(s);
+    return map_cuda(e);
+}
+
+}  // extern "C"

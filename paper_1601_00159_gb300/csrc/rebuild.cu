@@ -1,0 +1,538 @@
+// K6: storage-layer merge and index-layer rebuild (Sections 4.1 and 4.4.4), plus the
+// bulk build of a new index (Section 3.1) and the test-support export.
+//
+// Storage layer: contiguous sorted arrays keys / vals / meta (meta = height | F_del),
+// double buffered. A delete only sets F_del (Algorithm 4), so a deleted node keeps its
+// place and a later insert of the same key revives it in place. The storage layer is
+// re-laid-out (merge) only when new nodes must be placed, or when delete-flagged nodes
+// exceed 1/8 of it; the merge drops every delete-flagged node.
+//
+// Rebuild: the paper's daemon scans the storage layer and puts the key of every
+// valid node of height > 1 into the index-layer arrays. Here one pass over the storage
+// layer does it for all levels at once: per tile of 4096 nodes, keys and meta arrive in
+// shared memory by TMA bulk copy; the tile counts its live nodes of height >= l for
+// every level l; one decoupled look-back per level (a warp, one lane per level) gives
+// the tile's offset in each level; then level by level the tile compacts its nodes of
+// height >= l (a prefix sum) and writes them with their down pointers.
+//
+// Level sizes are not counted by the rebuild: the apply kernel keeps them current as
+// deltas, so the layout (level bases, sentinels, staging split) is known before the
+// pass and the pass writes every entry exactly once.
+
+#include "common.cuh"
+
+namespace pi {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kNodes = 4096;             // storage nodes per tile
+constexpr int kPer = kNodes / kThreads;  // 16 per thread
+constexpr uint32_t kCtrMerge = 9, kCtrRebuild = 10, kCtrCreate = 11;
+
+__device__ __forceinline__ bool merge_needed(const DevMeta* m, const BatchMeta* bm) {
+    const uint32_t size = m->size;
+    const uint32_t tombs = (uint32_t)((int32_t)m->tombs + bm->tomb_delta);
+    return bm->new_count > 0 || (tombs > 0 && (uint64_t)tombs * 8u > size);
+}
+
+// Number of entries of a[0..n) that are < x (a sorted).
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t n, uint32_t x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------------
+// Merge: old live nodes + new nodes -> the other storage buffer, in key order.
+// A new node with loc = x goes right before old node x (after old node x - 1) and is
+// handled by the tile that holds position x; the tiles cover positions [0, size].
+__global__ void __launch_bounds__(kThreads) k_merge(RebuildArgs a, uint32_t epoch) {
+    __shared__ uint16_t s_lp[kNodes + 1];  // live old nodes in [ts, ts + k)
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_tile, s_prefix, s_jb, s_je;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    const DevMeta* m = a.m;
+    if (block_sees_error(&m->error)) return;
+    if (!merge_needed(m, a.bm)) return;
+    const uint32_t size = m->size, src = m->cur, dst = src ^ 1u;
+    const uint32_t newc = a.bm->new_count;
+    const uint32_t ntiles = size / kNodes + 1;
+    const uint64_t* K0 = a.st.keys[src];
+    const uint64_t* V0 = a.st.vals[src];
+    const uint8_t* M0 = a.st.meta[src];
+    uint64_t* K1 = a.st.keys[dst];
+    uint64_t* V1 = a.st.vals[dst];
+    uint8_t* M1 = a.st.meta[dst];
+    if (tid == 0) s_ok = 1;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_tile = atomicAdd(&a.bm->tile_ctr[kCtrMerge], 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint32_t ts = tile * kNodes;
+        const uint32_t cnt = (size > ts) ? min((uint32_t)kNodes, size - ts) : 0u;
+        const uint32_t b0 = tid * kPer;
+        uint32_t live_bits = 0, lc = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const uint32_t li = b0 + k;
+            const bool lv = li < cnt && !(M0[ts + li] & kTomb);
+            live_bits |= (lv ? 1u : 0u) << k;
+            lc += lv ? 1u : 0u;
+        }
+        uint32_t tile_live;
+        uint32_t excl = block_excl_sum<kThreads>(lc, s_tmp, &tile_live);
+        {
+            uint32_t run = excl;
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                s_lp[b0 + k] = (uint16_t)run;
+                run += (live_bits >> k) & 1u;
+            }
+            if (tid == kThreads - 1) s_lp[kNodes] = (uint16_t)run;
+        }
+        if (tid == 0) {
+            bool ok;
+            s_prefix = lookback<false>(a.desc, 1, tile, epoch, tile_live, a.err, &ok);
+            if (!ok) s_ok = 0;
+            s_jb = lower_bound_u32(a.nn.loc, newc, ts);
+            s_je = lower_bound_u32(a.nn.loc, newc, ts + kNodes);
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const uint32_t jb = s_jb, je = s_je;
+        const uint32_t out_base = s_prefix + jb;
+        // old live nodes
+        {
+            uint32_t ptr = jb + (je > jb ? lower_bound_u32(a.nn.loc + jb, je - jb, ts + b0 + 1) : 0u);
+            uint32_t run = excl;
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const uint32_t li = b0 + k;
+                if (li >= cnt) break;
+                while (ptr < je && a.nn.loc[ptr] <= ts + li) ++ptr;
+                if ((live_bits >> k) & 1u) {
+                    const uint32_t o = out_base + run + (ptr - jb);
+                    if (o >= a.st_cap) {
+                        atomicOr(a.err, kErrBounds);
+                        break;
+                    }
+                    K1[o] = K0[ts + li];
+                    V1[o] = V0[ts + li];
+                    M1[o] = M0[ts + li];
+                    ++run;
+                }
+            }
+        }
+        // new nodes of this tile
+        for (uint32_t j = jb + tid; j < je; j += kThreads) {
+            const uint32_t x = a.nn.loc[j] - ts;  // in [0, kNodes]
+            const uint32_t o = out_base + s_lp[x] + (j - jb);
+            if (x > (uint32_t)kNodes || o >= a.st_cap) {
+                atomicOr(a.err, kErrBounds);
+                continue;
+            }
+            K1[o] = a.nn.keys[j];
+            V1[o] = a.nn.vals[j];
+            M1[o] = a.nn.height[j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Layout: apply the batch's deltas, switch storage buffers after a merge, decide the
+// rebuild, and lay the index levels out top-first with their sentinels.
+__global__ void k_level_bases(RebuildArgs a) {
+    if (threadIdx.x != 0) return;
+    DevMeta* m = a.m;
+    BatchMeta* bm = a.bm;
+    if (*(volatile uint32_t*)&m->error) return;
+    const bool merged = merge_needed(m, bm);
+    uint32_t tombs = (uint32_t)((int32_t)m->tombs + bm->tomb_delta);
+    uint32_t size = m->size;
+    if (merged) {
+        size = size - tombs + bm->new_count;
+        tombs = 0;
+        m->cur ^= 1u;
+    }
+    if (size > a.st_cap) {  // cannot happen when the host reserved capacity
+        atomicOr(a.err, kErrBounds);
+        return;
+    }
+    m->size = size;
+    m->tombs = tombs;
+    bm->merged = merged ? 1u : 0u;
+    const uint32_t cur = m->cur;
+    a.st.keys[cur][size] = kMaxKey;
+    a.st.vals[cur][size] = 0;
+    a.st.meta[cur][size] = 0;
+    for (int l = 1; l < kLevelSlots; ++l) m->cnt[l] = (uint32_t)((int32_t)m->cnt[l] + bm->delta[l]);
+    m->updates += bm->changes;
+    if (a.force_rebuild != 2u) m->batches += 1;
+
+    bool rebuild = a.force_rebuild || merged;
+    if (!rebuild && bm->index_dirty) {
+        if (a.rebuild_policy == 0) rebuild = true;
+        else rebuild = (uint64_t)m->updates * 100u >= (uint64_t)a.threshold_pct * (uint64_t)(size ? size : 1u);
+    }
+    bm->rebuild = rebuild ? 1u : 0u;
+    if (!rebuild) return;
+    m->updates = 0;
+    m->rebuilds += 1;
+
+    uint32_t H = 1;
+    for (int l = 2; l < kLevelSlots; ++l)
+        if (m->cnt[l] > 0) H = (uint32_t)l;
+    // Lowest level that fits: drop bottom levels (the descent then scans longer storage
+    // gaps) rather than overrun the capacity; the host grows it later.
+    uint64_t need = 0;
+    for (uint32_t l = 2; l <= H; ++l) need += (uint64_t)m->cnt[l] + 1u;
+    uint32_t Lb = 2;
+    uint64_t fit = need;
+    while (Lb <= H && fit > a.index_cap) {
+        fit -= (uint64_t)m->cnt[Lb] + 1u;
+        ++Lb;
+    }
+    m->index_need = (uint32_t)need;
+    m->grow_request = (Lb > 2) ? 1u : 0u;
+    for (int l = 0; l < kLevelSlots; ++l) {
+        m->n[l] = 0;
+        m->base[l] = 0;
+    }
+    uint32_t off = 0;
+    for (int l = (int)H; l >= (int)Lb; --l) {
+        m->base[l] = off;
+        m->n[l] = m->cnt[l];
+        off += m->cnt[l] + 1u;
+    }
+    m->H = H;
+    m->Lb = Lb;
+    m->index_total = off;
+    uint32_t Ls = H + 1;
+    for (int l = (int)H; l >= (int)Lb; --l) {
+        if (m->base[l] + m->n[l] + 1u <= kSmemTopMax) Ls = (uint32_t)l;
+        else break;
+    }
+    m->Ls = Ls;
+    m->smem_entries = (Ls <= H) ? m->base[Ls] + m->n[Ls] + 1u : 0u;
+    for (int l = (int)H; l >= (int)Lb; --l) {
+        const uint32_t sidx = m->base[l] + m->n[l];
+        a.lkeys[sidx] = kMaxKey;
+        a.ldown[sidx] = (l > (int)Lb) ? m->n[l - 1] : size;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Index-layer rebuild: one pass over the storage layer, all levels.
+__global__ void __launch_bounds__(kThreads) k_rebuild(RebuildArgs a, uint32_t epoch) {
+    extern __shared__ __align__(16) uint8_t s_dyn[];
+    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);                        // kNodes + 2
+    uint8_t* s_meta = s_dyn + (kNodes + 2) * sizeof(uint64_t);                     // kNodes + 16
+    uint32_t* s_la = reinterpret_cast<uint32_t*>(s_meta + kNodes + 16);            // list (ping)
+    uint32_t* s_lb = s_la + kNodes;                                                // list (pong)
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_hist[kLevelSlots];
+    __shared__ uint32_t s_off[kLevelSlots];
+    __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
+    __shared__ uint32_t s_tile;
+    __shared__ int s_ok;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const DevMeta* m = a.m;
+    if (block_sees_error(&m->error)) return;
+    if (!a.bm->rebuild) return;
+    const uint32_t H = m->H, Lb = m->Lb, size = m->size, cur = m->cur;
+    if (H < Lb || size == 0) return;
+    const uint64_t* SK = a.st.keys[cur];
+    const uint8_t* SM = a.st.meta[cur];
+    const uint32_t ntiles = (size + kNodes - 1) / kNodes;
+    if (tid < kLevelSlots) {
+        s_base[tid] = m->base[tid];
+        s_n[tid] = m->n[tid];
+    }
+    if (tid == 0) {
+        s_ok = 1;
+        mbar_init(&s_bar, 1);
+    }
+    uint32_t phase = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_tile = atomicAdd(&a.bm->tile_ctr[kCtrRebuild], 1u);
+        if (tid < kLevelSlots) s_hist[tid] = 0;
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint32_t ts = tile * kNodes;
+        const uint32_t cnt = min((uint32_t)kNodes, size - ts);
+        if (tid == 0) {
+            const uint32_t bk = ((cnt * 8u + 15u) / 16u) * 16u;
+            const uint32_t bm_ = ((cnt + 15u) / 16u) * 16u;
+            mbar_arrive_expect_tx(&s_bar, bk + bm_);
+            bulk_g2s(s_keys, SK + ts, bk, &s_bar);
+            bulk_g2s(s_meta, SM + ts, bm_, &s_bar);
+        }
+        if (!mbar_wait_bounded(&s_bar, phase, a.err)) s_ok = 0;
+        phase ^= 1u;
+        __syncthreads();
+        if (!s_ok) {
+            if (tid == 0) mbar_wait_bounded(&s_bar, phase ^ 1u, a.err);
+            break;
+        }
+        // live heights of this tile
+        const uint32_t b0 = tid * kPer;
+        uint32_t hts[kPer];
+        uint32_t c_lb = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const uint32_t li = b0 + k;
+            const uint8_t mt = li < cnt ? s_meta[li] : (uint8_t)kTomb;
+            const uint32_t h = (mt & kTomb) ? 0u : (uint32_t)(mt & kHeightMask);
+            hts[k] = h;
+            if (h >= 2) atomicAdd(&s_hist[min(h, H)], 1u);
+            c_lb += (h >= Lb) ? 1u : 0u;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // per-level tile counts (suffix sums of the histogram), then one look-back
+            // per level: lane i handles level Lb + i.
+            const uint32_t l = Lb + (uint32_t)lane;
+            uint32_t c = 0;
+            if (l <= H)
+                for (uint32_t h = l; h <= H; ++h) c += s_hist[h];
+            bool ok = true;
+            uint32_t ex = 0;
+            if (l <= H) ex = lookback<false>(a.desc + lane, 32, tile, epoch, c, a.err, &ok);
+            if (!ok) s_ok = 0;
+            if (l <= H) s_off[l] = ex;
+        }
+        // level Lb: compact live nodes of height >= Lb
+        uint32_t tot;
+        const uint32_t ex0 = block_excl_sum<kThreads>(c_lb, s_tmp, &tot);
+        {
+            uint32_t w = ex0;
+#pragma unroll
+            for (int k = 0; k < kPer; ++k)
+                if (hts[k] >= Lb) s_la[w++] = b0 + k;  // node index (list entry of level Lb)
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        for (uint32_t j = tid; j < tot; j += kThreads) {
+            const uint32_t node = s_la[j] & 0xFFFFu;
+            const uint32_t g = s_base[Lb] + s_off[Lb] + j;
+            if (s_off[Lb] + j >= s_n[Lb]) {
+                atomicOr(a.err, kErrBounds);
+                break;
+            }
+            a.lkeys[g] = s_keys[node];
+            a.ldown[g] = ts + node;
+        }
+        // levels above: compact the previous level's list
+        uint32_t* prev = s_la;
+        uint32_t* next = s_lb;
+        uint32_t mprev = tot;
+        for (uint32_t l = Lb + 1; l <= H && mprev > 0; ++l) {
+            const uint32_t per = (mprev + kThreads - 1) / kThreads;
+            const uint32_t jb = min(tid * per, mprev), je = min(jb + per, mprev);
+            uint32_t c = 0;
+            for (uint32_t j = jb; j < je; ++j) c += (s_meta[prev[j] & 0xFFFFu] & kHeightMask) >= l ? 1u : 0u;
+            uint32_t mcur;
+            uint32_t w = block_excl_sum<kThreads>(c, s_tmp, &mcur);
+            for (uint32_t j = jb; j < je; ++j) {
+                const uint32_t node = prev[j] & 0xFFFFu;
+                if ((s_meta[node] & kHeightMask) >= l) next[w++] = node | (j << 16);
+            }
+            __syncthreads();
+            for (uint32_t j = tid; j < mcur; j += kThreads) {
+                const uint32_t e = next[j];
+                const uint32_t g = s_base[l] + s_off[l] + j;
+                if (s_off[l] + j >= s_n[l]) {
+                    atomicOr(a.err, kErrBounds);
+                    break;
+                }
+                a.lkeys[g] = s_keys[e & 0xFFFFu];
+                a.ldown[g] = s_off[l - 1] + (e >> 16);
+            }
+            __syncthreads();
+            uint32_t* t = prev;
+            prev = next;
+            next = t;
+            mprev = mcur;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Bulk build: keep the last query of every key run of the sorted input (the last
+// occurrence of a key wins), with its value and tower height; count level sizes.
+__global__ void __launch_bounds__(kThreads) k_create_storage(CreateArgs a, uint32_t epoch) {
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_hist[kLevelSlots];
+    __shared__ uint32_t s_tile, s_prefix, s_kept;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    const uint32_t n = a.n;
+    const uint32_t ntiles = (n + kNodes - 1) / kNodes;
+    if (tid < kLevelSlots) s_hist[tid] = 0;
+    if (tid == 0) {
+        s_ok = 1;
+        s_kept = 0;
+    }
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_tile = atomicAdd(&a.bm->tile_ctr[kCtrCreate], 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint32_t b0 = tile * kNodes + tid * kPer;
+        uint32_t keep_bits = 0, c = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const uint32_t i = b0 + k;
+            bool keep = false;
+            if (i < n) {
+                const uint64_t key = a.sk[i];
+                keep = key != kMaxKey && (i + 1 == n || a.sk[i + 1] != key);
+            }
+            keep_bits |= (keep ? 1u : 0u) << k;
+            c += keep ? 1u : 0u;
+        }
+        uint32_t tot;
+        const uint32_t ex = block_excl_sum<kThreads>(c, s_tmp, &tot);
+        if (tid == 0) {
+            bool ok;
+            s_prefix = lookback<false>(a.desc, 1, tile, epoch, tot, a.err, &ok);
+            if (!ok) s_ok = 0;
+            s_kept += tot;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        uint32_t o = s_prefix + ex;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            if (!((keep_bits >> k) & 1u)) continue;
+            const uint32_t i = b0 + k;
+            const uint64_t key = a.sk[i];
+            const uint32_t h = tower_height(key, a.hp);
+            if (o >= a.st_cap) {
+                atomicOr(a.err, kErrBounds);
+                break;
+            }
+            a.st.keys[0][o] = key;
+            a.st.vals[0][o] = a.uvals[a.sp[i] & ((1u << 30) - 1u)];
+            a.st.meta[0][o] = (uint8_t)h;
+            atomicAdd(&s_hist[h], 1u);
+            ++o;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_kept) atomicAdd(&a.m->size, s_kept);
+    // s_hist[h] = nodes of height exactly h; cnt[l] = nodes of height >= l
+    if (tid >= 1 && tid < kLevelSlots) {
+        uint32_t c = 0;
+        for (int h = tid; h < kLevelSlots; ++h) c += s_hist[h];
+        if (c) atomicAdd(&a.m->cnt[tid], c);
+    }
+}
+
+// Live pairs of the storage layer, in key order.
+__global__ void __launch_bounds__(kThreads) k_export_live(Storage st, const DevMeta* m, uint64_t* ko,
+                                                          uint64_t* vo, uint64_t cap, uint32_t* count,
+                                                          uint64_t* desc, uint32_t* tile_ctr, uint32_t epoch,
+                                                          uint32_t* err) {
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    const uint32_t size = m->size, cur = m->cur;
+    const uint32_t ntiles = (size + kNodes - 1) / kNodes;
+    if (tid == 0) s_ok = 1;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint32_t b0 = tile * kNodes + tid * kPer;
+        uint32_t bits = 0, c = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const uint32_t i = b0 + k;
+            const bool lv = i < size && !(st.meta[cur][i] & kTomb);
+            bits |= (lv ? 1u : 0u) << k;
+            c += lv ? 1u : 0u;
+        }
+        uint32_t tot;
+        const uint32_t ex = block_excl_sum<kThreads>(c, s_tmp, &tot);
+        if (tid == 0) {
+            bool ok;
+            s_prefix = lookback<false>(desc, 1, tile, epoch, tot, err, &ok);
+            if (!ok) s_ok = 0;
+            if (tile == ntiles - 1) *count = s_prefix + tot;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        uint64_t o = (uint64_t)s_prefix + ex;
+        for (int k = 0; k < kPer; ++k) {
+            if (!((bits >> k) & 1u)) continue;
+            if (o < cap) {
+                ko[o] = st.keys[cur][b0 + k];
+                vo[o] = st.vals[cur][b0 + k];
+            }
+            ++o;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
+    const uint32_t tiles = a.size_ub / kNodes + 1;
+    const uint32_t cap = (uint32_t)num_sms * 4u;
+    k_merge<<<(int)(tiles < cap ? tiles : cap), kThreads, 0, s>>>(a, ++epoch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s) {
+    k_level_bases<<<1, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
+    static bool attr_set = false;
+    const int dyn = (kNodes + 2) * 8 + kNodes + 16 + 2 * kNodes * 4;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_rebuild, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const uint32_t tiles = a.size_ub / kNodes + 1;
+    const uint32_t cap = (uint32_t)num_sms * 2u;
+    k_rebuild<<<(int)(tiles < cap ? tiles : cap), kThreads, dyn, s>>>(a, ++epoch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_create_storage(const CreateArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
+    if (a.n == 0) return cudaSuccess;
+    const uint32_t tiles = (a.n + kNodes - 1) / kNodes;
+    const uint32_t cap = (uint32_t)num_sms * 4u;
+    k_create_storage<<<(int)(tiles < cap ? tiles : cap), kThreads, 0, s>>>(a, ++epoch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_live(const Storage& st, const DevMeta* m, uint64_t* keys_out, uint64_t* vals_out,
+                               uint64_t cap, uint32_t* count, uint64_t* desc, uint32_t* tile_ctr,
+                               uint32_t& epoch, uint32_t* err, cudaStream_t s, int num_sms, uint32_t size_ub) {
+    const uint32_t tiles = size_ub / kNodes + 1;
+    const uint32_t c = (uint32_t)num_sms * 4u;
+    k_export_live<<<(int)(tiles < c ? tiles : c), kThreads, 0, s>>>(st, m, keys_out, vals_out, cap, count, desc,
+                                                                   tile_ctr, ++epoch, err);
+    return cudaGetLastError();
+}
+
+}  // namespace pi

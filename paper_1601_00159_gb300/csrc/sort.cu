@@ -1,0 +1,199 @@
+// K0 + K1: validate/pack the query set and sort it by key (Definition 3: the queries
+// of a query set are ordered by key; Section 4.2: the sort can use data parallelism).
+//
+// LSD radix sort with 8-bit digits, one kernel launch per digit, each a single pass
+// over the data with decoupled look-back (the "Onesweep" organisation of Adinets and
+// Merrill, 2022, written here from the published description). A pass whose digit is
+// the same for every key (found from the histograms) is skipped. The sort is stable,
+// so equal keys stay in arrival order: the order is (key, arrival index), the
+// reading of Definition 3 for duplicate keys.
+//
+// Payload word: op << 30 | arrival index. Invalid queries (op > 2 or the reserved key)
+// get the sort key 2^64-1 and so gather at the end of the sorted batch.
+
+#include "common.cuh"
+
+namespace pi {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // 4096
+constexpr int kWarps = kThreads / 32;
+constexpr int kWarpSpan = 32 * kItems;    // 512 consecutive elements per warp
+
+__global__ void __launch_bounds__(256) k_pack_hist(const uint8_t* __restrict__ ops,
+                                                   const uint64_t* __restrict__ keys, uint32_t n,
+                                                   uint64_t* __restrict__ sk, uint32_t* __restrict__ sp,
+                                                   BatchMeta* bm) {
+    __shared__ uint32_t h[8 * 256];
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    uint32_t invalid = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+        uint32_t op = ops ? ops[i] : 0u;
+        bool valid = op <= 2u && k != kMaxKey;
+        uint64_t s = valid ? k : kMaxKey;
+        invalid += valid ? 0u : 1u;
+        sk[i] = s;
+        sp[i] = ((op & 3u) << 30) | i;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) atomicAdd(&h[d * 256 + ((s >> (8 * d)) & 255u)], 1u);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) invalid += __shfl_xor_sync(0xffffffffu, invalid, o);
+    if ((threadIdx.x & 31) == 0 && invalid) atomicAdd(&bm->invalid, invalid);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&bm->hist[i >> 8][i & 255], h[i]);
+}
+
+// Digit offsets (exclusive scan of each histogram) and the pass plan.
+__global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, uint32_t* dofs) {
+    __shared__ uint32_t tmp[33];
+    __shared__ uint32_t skip[8];
+    const int b = threadIdx.x;
+    if (b < 8) skip[b] = 0;
+    __syncthreads();
+    for (int d = 0; d < 8; ++d) {
+        uint32_t c = bm->hist[d][b];
+        if (c == n) skip[d] = 1;
+        uint32_t ex = block_excl_sum<256>(c, tmp, nullptr);
+        dofs[d * 256 + b] = ex;
+    }
+    __syncthreads();
+    if (b == 0) {
+        SortPlan& P = bm->plan;
+        uint32_t r = 0;
+        uint32_t dig[8];
+        for (int d = 0; d < 8; ++d)
+            if (!skip[d]) dig[r++] = d;
+        if (r == 0) dig[r++] = 0;  // all keys equal: one pass (identity order)
+        P.npass = r;
+        for (uint32_t j = 0; j < r; ++j) {
+            P.digit[j] = dig[j];
+            P.src[j] = (j == 0) ? 0u : P.dst[j - 1];
+            P.dst[j] = ((r - 1 - j) % 2 == 0) ? 1u : 2u;  // the last pass writes buffer A
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sort_pass(uint32_t j, uint32_t n, SortBuffers sb,
+                                                        BatchMeta* bm, uint32_t epoch, uint32_t* err) {
+    const SortPlan& P = bm->plan;
+    if (j >= P.npass) return;
+    const uint32_t shift = 8u * P.digit[j];
+    const uint64_t* src_k = P.src[j] == 0 ? sb.in_k : (P.src[j] == 1 ? sb.a_k : sb.b_k);
+    const uint32_t* src_p = P.src[j] == 0 ? sb.in_p : (P.src[j] == 1 ? sb.a_p : sb.b_p);
+    uint64_t* dst_k = P.dst[j] == 1 ? sb.a_k : sb.b_k;
+    uint32_t* dst_p = P.dst[j] == 1 ? sb.a_p : sb.b_p;
+
+    extern __shared__ __align__(16) uint8_t s_dyn[];
+    uint64_t* s_key = reinterpret_cast<uint64_t*>(s_dyn);
+    uint32_t* s_pay = reinterpret_cast<uint32_t*>(s_dyn + kTile * sizeof(uint64_t));
+    __shared__ uint32_t s_whist[kWarps][256];
+    __shared__ uint32_t s_gbase[256];
+    __shared__ uint32_t s_tstart[256];
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_tile;
+    __shared__ int s_ok;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_tile = atomicAdd(&bm->tile_ctr[j], 1u);
+        s_ok = 1;
+    }
+    for (int i = tid; i < kWarps * 256; i += kThreads) (&s_whist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t tbase = tile * kTile;
+    const uint32_t tn = min((uint32_t)kTile, n - tbase);
+
+    uint64_t key[kItems];
+    uint32_t pay[kItems];
+    uint32_t dig[kItems];
+    uint32_t rank[kItems];
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        uint32_t li = warp * kWarpSpan + k * 32 + lane;
+        bool v = li < tn;
+        key[k] = v ? src_k[tbase + li] : 0ull;
+        pay[k] = v ? src_p[tbase + li] : 0u;
+        dig[k] = v ? (uint32_t)((key[k] >> shift) & 255u) : 256u;
+    }
+    // Rank within the warp: elements are visited in index order (k, then lane).
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        uint32_t d = dig[k];
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t lower = __popc(peers & lt);
+        uint32_t base = d < 256u ? s_whist[warp][d] : 0u;
+        rank[k] = base + lower;
+        __syncwarp();
+        if (d < 256u && lower == 0) s_whist[warp][d] = base + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // Thread tid owns digit tid: tile total and per-warp exclusive prefix.
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        uint32_t c = s_whist[w][tid];
+        s_whist[w][tid] = total;
+        total += c;
+    }
+    bool ok;
+    uint32_t excl = lookback<false>(sb.desc + tid, 256, tile, epoch, total, err, &ok);
+    if (!ok) s_ok = 0;
+    s_gbase[tid] = sb.dofs[P.digit[j] * 256 + tid] + excl;
+    s_tstart[tid] = block_excl_sum<kThreads>(total, s_tmp, nullptr);
+    __syncthreads();
+    if (!s_ok) return;  // a predecessor never published: write nothing
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        uint32_t d = dig[k];
+        if (d < 256u) {
+            uint32_t pos = s_tstart[d] + s_whist[warp][d] + rank[k];
+            s_key[pos] = key[k];
+            s_pay[pos] = pay[k];
+        }
+    }
+    __syncthreads();
+    for (uint32_t s = tid; s < tn; s += kThreads) {
+        uint64_t k = s_key[s];
+        uint32_t d = (uint32_t)((k >> shift) & 255u);
+        uint32_t g = s_gbase[d] + (s - s_tstart[d]);
+        if (g < n) {
+            dst_k[g] = k;
+            dst_p[g] = s_pay[s];
+        } else {
+            atomicOr(err, kErrBounds);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, const SortBuffers& sb,
+                        BatchMeta* bm, uint32_t* err, uint32_t& epoch, cudaStream_t s, int num_sms) {
+    if (n == 0) return cudaSuccess;
+    int grid = min((int)((n + 255) / 256), num_sms * 8);
+    k_pack_hist<<<grid, 256, 0, s>>>(ops, keys, n, sb.in_k, sb.in_p, bm);
+    k_sort_plan<<<1, 256, 0, s>>>(n, bm, sb.dofs);
+    static bool attr_set = false;
+    const int dyn = kTile * (int)(sizeof(uint64_t) + sizeof(uint32_t));
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    uint32_t tiles = (n + kTile - 1) / kTile;
+    for (uint32_t j = 0; j < 8; ++j) {
+        k_sort_pass<<<tiles, kThreads, dyn, s>>>(j, n, sb, bm, ++epoch, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pi

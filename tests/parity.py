@@ -1,0 +1,78 @@
+"""Shared harness of the GPU parity tests: run the same seeded batches through the
+CUDA path (via the C ABI binding) and through the oracle, and compare bit for bit."""
+from __future__ import annotations
+
+import numpy as np
+
+
+def to_dev(a: np.ndarray, dtype):
+    import torch
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def results_np(res):
+    r = res.cpu().numpy()
+    vals = r[:, 0].view(np.uint64)
+    status = (r[:, 1].view(np.uint64) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    reserved = (r[:, 1].view(np.uint64) >> np.uint64(32)).astype(np.uint32)
+    return vals, status, reserved
+
+
+def make_index(keys, vals, p, seed, config=None):
+    import torch
+    from paper_1601_00159_gb300 import Index
+    return Index(to_dev(keys, torch.int64), to_dev(vals, torch.int64), p, seed, config)
+
+
+def run_batch(idx, batch):
+    import torch
+    res = idx.execute(to_dev(batch.ops, torch.uint8), to_dev(batch.keys, torch.int64),
+                      to_dev(batch.vals, torch.int64))
+    return results_np(res)
+
+
+def assert_results_equal(got, expected, ctx=""):
+    gv, gs, gr = got
+    ev, es = expected
+    assert gs.shape == es.shape
+    bad = np.nonzero((gs != es) | (gv != ev))[0]
+    assert len(bad) == 0, (f"{ctx}: {len(bad)} of {len(es)} results differ; first at {bad[:5]}: "
+                           f"gpu {list(zip(gs[bad[:5]], gv[bad[:5]]))} oracle {list(zip(es[bad[:5]], ev[bad[:5]]))}")
+    assert not gr.any(), f"{ctx}: reserved field not zero"
+
+
+def assert_state_equal(idx, orc, ctx="", check_levels=True):
+    k, v = idx.export()
+    gk = k.cpu().numpy().view(np.uint64)
+    gv = v.cpu().numpy().view(np.uint64)
+    ok, ov = orc.export()
+    assert len(gk) == len(ok), f"{ctx}: {len(gk)} live keys on GPU, oracle {len(ok)}"
+    assert np.array_equal(gk, ok), f"{ctx}: live key sets differ"
+    assert np.array_equal(gv, ov), f"{ctx}: values differ"
+    info = idx.info()
+    assert info["live"] == len(ok)
+    assert idx.status() == 0, f"{ctx}: device error status {idx.status()}"
+    if not check_levels:
+        return info
+    top = orc.num_levels()
+    assert info["top_level"] == max(top, 1), f"{ctx}: top level {info['top_level']} vs {top}"
+    prev_keys = ok
+    for level in range(2, top + 1):
+        lv = idx.export_level(level)
+        exp = orc.level(level)
+        assert info["level_size"][level] == len(exp)
+        if lv is None:
+            assert level < info["bottom_built"], f"{ctx}: level {level} missing"
+            prev_keys = exp
+            continue
+        lk = lv[0].cpu().numpy().view(np.uint64)
+        ld = lv[1].cpu().numpy().astype(np.int64)
+        assert np.array_equal(lk, exp), f"{ctx}: level {level} differs"
+        if level > info["bottom_built"]:
+            assert np.array_equal(prev_keys[ld], lk), f"{ctx}: down pointers of level {level} wrong"
+        elif info["tombstones"] == 0:
+            assert np.array_equal(ok[ld], lk), f"{ctx}: storage down pointers of level {level} wrong"
+        prev_keys = exp
+    return info

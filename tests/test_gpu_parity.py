@@ -1,0 +1,174 @@
+"""GPU path vs oracle, bit for bit: per-query results (arrival order), final live
+(key, value) set, and every built index level with its down pointers.
+
+Integer work throughout, so the bar is exact equality. Sizes span several tiles of
+every kernel (sort 4096, apply 2048, rebuild 4096 queries or nodes) with ragged tails.
+"""
+import numpy as np
+import pytest
+
+from paper_1601_00159_gb300 import workloads as wl
+from tests.parity import (assert_results_equal, assert_state_equal, make_index, run_batch, to_dev,
+                          results_np)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def orc_mod():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    from paper_1601_00159_gb300 import build, load_library
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    return load_library()
+
+
+def run_workload(orc_mod, w, config=None, check_levels_every=1, batches=None, check_levels=True):
+    idx = make_index(w.keys, w.vals, w.promote_p, w.hash_seed, config)
+    orc = orc_mod.Oracle(w.keys, w.vals, w.promote_p, w.hash_seed)
+    assert_state_equal(idx, orc, f"{w.name} after create")
+    bl = w.batches() if callable(w.batches) else w.batches
+    for b, batch in enumerate(bl):
+        if batches is not None and b >= batches:
+            break
+        got = run_batch(idx, batch)
+        exp = orc.execute(batch.ops, batch.keys, batch.vals)
+        assert_results_equal(got, exp, f"{w.name} batch {b}")
+        if (b + 1) % check_levels_every == 0:
+            assert_state_equal(idx, orc, f"{w.name} batch {b}", check_levels)
+    info = assert_state_equal(idx, orc, f"{w.name} end", check_levels)
+    idx.close()
+    orc.close()
+    return info
+
+
+def test_tiny_config_full_size(orc_mod):
+    """2^16 keys, p = 1/2, one all-search batch of 2^14 (half hits, half misses)."""
+    w = wl.tiny()
+    info = run_workload(orc_mod, w)
+    assert info["rebuilds"] == 1  # only the initial build: a search batch changes nothing
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_small_dense(orc_mod, seed):
+    """Tiny key ranges: long same-key runs, revivals, delete/insert chains, invalid ops."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(0, 3000))
+    q = int(rng.integers(1, 9000))
+    kr = int(rng.choice([5, 64, 700, 5000, 1 << 40]))
+    p = float(rng.choice([0.5, 0.25, 0.125, 0.0625]))
+    w = wl.random_small(1000 + seed, n, q, kr, p=p, n_batches=4)
+    run_workload(orc_mod, w)
+
+
+def test_mid_shape_scaled(orc_mod):
+    w = wl.mid(seed=11, n0=1 << 18, q=1 << 15, n_batches=6)
+    run_workload(orc_mod, w)
+
+
+def test_skewed_shape_scaled(orc_mod):
+    w = wl.skewed(seed=12, n=1 << 20, q=1 << 17, n_batches=6)
+    info = run_workload(orc_mod, w)
+    assert info["tombstones"] > 0  # deletes keep flagged nodes in place
+
+
+@pytest.mark.parametrize("policy", [0, 1])
+def test_rebuild_policy_does_not_change_results(orc_mod, policy):
+    w = wl.random_small(77, 20000, 30000, 1 << 20, p=0.25, n_batches=5)
+    # levels are defined right after a rebuild; the deferred policy may leave them stale
+    run_workload(orc_mod, w, config={"rebuild_policy": policy, "rebuild_threshold_pct": 50},
+                 check_levels_every=1, check_levels=(policy == 0))
+
+
+def test_index_capacity_overflow_keeps_results_exact(orc_mod):
+    """An index layer that does not fit drops its lowest levels (the descent then walks
+    longer storage gaps); results stay exact and the capacity grows afterwards."""
+    w = wl.random_small(5, 50000, 20000, 1 << 30, p=0.5, n_batches=4)
+    idx = make_index(w.keys, w.vals, w.promote_p, w.hash_seed, {"index_capacity": 3000})
+    orc = orc_mod.Oracle(w.keys, w.vals, w.promote_p, w.hash_seed)
+    info0 = idx.info()
+    assert info0["bottom_built"] > 2
+    for b, batch in enumerate(w.batches):
+        assert_results_equal(run_batch(idx, batch), orc.execute(batch.ops, batch.keys, batch.vals), f"b{b}")
+    info = assert_state_equal(idx, orc, "overflow end")
+    assert info["bottom_built"] == 2 and info["index_capacity"] > 3000
+
+
+def test_edge_cases(orc_mod):
+    import torch
+    M = (1 << 64) - 1
+    # empty index, then inserts; empty batch; all-invalid batch; extreme keys
+    idx = make_index(np.zeros(0, np.uint64), np.zeros(0, np.uint64), 0.25, 3)
+    orc = orc_mod.Oracle(np.zeros(0, np.uint64), np.zeros(0, np.uint64), 0.25, 3)
+    assert_state_equal(idx, orc, "empty")
+    empty = torch.empty(0, dtype=torch.int64, device="cuda")
+    idx.execute(torch.empty(0, dtype=torch.uint8, device="cuda"), empty, empty)
+    cases = [
+        (np.array([0, 1, 0, 2, 0], np.uint8), np.array([0, 0, 0, 0, 0], np.uint64), np.arange(5, dtype=np.uint64)),
+        (np.array([1, 1, 0, 0], np.uint8), np.array([M - 1, 1 << 63, M - 1, M], np.uint64),
+         np.array([7, 8, 9, 10], np.uint64)),
+        (np.array([3, 200, 1], np.uint8), np.array([5, 5, M], np.uint64), np.array([1, 2, 3], np.uint64)),
+        (np.full(10000, 1, np.uint8), np.full(10000, 42, np.uint64), np.arange(10000, dtype=np.uint64)),
+        (np.array([2] * 5000 + [0] * 5000, np.uint8), np.full(10000, 42, np.uint64), np.zeros(10000, np.uint64)),
+    ]
+    for c, (ops, keys, vals) in enumerate(cases):
+        b = wl.Batch(ops, keys, vals)
+        assert_results_equal(run_batch(idx, b), orc.execute(ops, keys, vals), f"case {c}")
+        assert_state_equal(idx, orc, f"case {c}")
+
+
+def test_one_hot_key_spans_many_tiles(orc_mod):
+    """One key receives 2^18 interleaved queries (sort, scan and apply tiles all split
+    the run): the owner is the run's last query and every result sees the prior ones."""
+    n = 1 << 12
+    keys = wl.distinct_keys(3, np.arange(n))
+    vals = wl.splitmix64(keys)
+    idx = make_index(keys, vals, 0.25, 9)
+    orc = orc_mod.Oracle(keys, vals, 0.25, 9)
+    q = (1 << 18) + 123
+    s = wl.stream_seed(3, 9)
+    ops = wl.bounded(s, 0, q, 3).astype(np.uint8)
+    bkeys = np.where(wl.bounded(s, q, q, 4) == 0, keys[wl.bounded(s, 2 * q, q, n)], keys[17])
+    bvals = wl.u64_stream(s, 3 * q, q)
+    b = wl.Batch(ops, bkeys.astype(np.uint64), bvals)
+    assert_results_equal(run_batch(idx, b), orc.execute(b.ops, b.keys, b.vals), "hot")
+    assert_state_equal(idx, orc, "hot")
+
+
+def test_host_entry_point_matches_device_entry_point(orc_mod):
+    import torch
+    w = wl.random_small(31, 4000, 5000, 3000, p=0.25, n_batches=2)
+    a = make_index(w.keys, w.vals, w.promote_p, w.hash_seed)
+    b = make_index(w.keys, w.vals, w.promote_p, w.hash_seed)
+    for batch in w.batches:
+        ra = results_np(a.execute(to_dev(batch.ops, torch.uint8), to_dev(batch.keys, torch.int64),
+                                  to_dev(batch.vals, torch.int64)))
+        ops = torch.from_numpy(batch.ops.copy()).pin_memory()
+        ks = torch.from_numpy(batch.keys.view(np.int64).copy()).pin_memory()
+        vs = torch.from_numpy(batch.vals.view(np.int64).copy()).pin_memory()
+        out = torch.empty((len(batch), 2), dtype=torch.int64).pin_memory()
+        b.execute_host(ops, ks, vs, out)
+        torch.cuda.current_stream().synchronize()
+        rb = results_np(out)
+        assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
+
+
+def test_create_rejects_bad_arguments():
+    import torch
+    from paper_1601_00159_gb300 import Index, PiError, PI_ERR_INVALID_ARG
+    k = to_dev(np.array([1, (1 << 64) - 1], np.uint64), torch.int64)
+    v = to_dev(np.array([1, 2], np.uint64), torch.int64)
+    with pytest.raises(PiError) as e:
+        Index(k, v, 0.25, 1)
+    assert e.value.code == PI_ERR_INVALID_ARG
+    k2 = to_dev(np.array([1, 2], np.uint64), torch.int64)
+    with pytest.raises(PiError):
+        Index(k2, v, 0.3, 1)
