@@ -213,7 +213,12 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
     spec = WORKLOADS[args.workload]
     t_gen = time.time()
-    w = spec["fn"]()
+    kw = {}
+    if args.keys_log2:
+        kw["n" if args.workload != "mid" else "n0"] = 1 << args.keys_log2
+    if args.batch_log2:
+        kw["q"] = 1 << args.batch_log2
+    w = spec["fn"](**kw)
     n_distinct_batches = 1 if args.workload == "tiny" else min(args.steps + args.warmup, args.batches)
     gen = w.batches() if callable(w.batches) else iter(w.batches)
     host_batches = [next(gen) for _ in range(n_distinct_batches)]
@@ -321,7 +326,8 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": spec["desc"], "keys": len(w.keys), "batch": q,
+        "config": {"workload": args.workload if not (args.keys_log2 or args.batch_log2) else
+                   f"{args.workload}-keys{len(w.keys)}-batch{q}", "desc": spec["desc"], "keys": len(w.keys), "batch": q,
                    "distinct_batches_cycled": len(dbatches), "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2_flush": "none: storage layer and cycled batch inputs exceed L2"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -357,6 +363,8 @@ def main():
     ap.add_argument("--batches", type=int, default=32, help="distinct batches generated and cycled")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--keys-log2", type=int, default=0, help="override the index size (profiling runs)")
+    ap.add_argument("--batch-log2", type=int, default=0, help="override the batch size (profiling runs)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if ws > 1:

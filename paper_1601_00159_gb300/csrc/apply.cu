@@ -96,10 +96,13 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a, uint32_t epoch_
         }
         uint32_t tile_max;
         const uint32_t texcl = block_excl_max<kThreads>(agg, s_tmp, &tile_max);
-        if (tid == 0) {
+        if (tid < 32) {
             bool ok;
-            s_excl_max = lookback<true>(desc_max, 1, tile, epoch_max, tile_max, a.err, &ok);
-            if (!ok) s_ok = 0;
+            const uint32_t ex = lookback_warp<true>(desc_max, tile, epoch_max, tile_max, a.err, &ok);
+            if (tid == 0) {
+                s_excl_max = ex;
+                if (!ok) s_ok = 0;
+            }
         }
         __syncthreads();
         if (!s_ok) break;
@@ -168,11 +171,14 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a, uint32_t epoch_
         // New nodes: compact slots in key order.
         uint32_t tile_new;
         const uint32_t nexcl = block_excl_sum<kThreads>(new_here, s_tmp, &tile_new);
-        if (tid == 0) {
+        if (tid < 32) {
             bool ok;
-            s_excl_cnt = lookback<false>(desc_cnt, 1, tile, epoch_cnt, tile_new, a.err, &ok);
-            if (!ok) s_ok = 0;
-            s_new_total += tile_new;
+            const uint32_t ex = lookback_warp<false>(desc_cnt, tile, epoch_cnt, tile_new, a.err, &ok);
+            if (tid == 0) {
+                s_excl_cnt = ex;
+                if (!ok) s_ok = 0;
+                s_new_total += tile_new;
+            }
         }
         __syncthreads();
         if (!s_ok) break;

@@ -185,6 +185,114 @@ __device__ uint32_t lookback(uint64_t* desc, size_t stride, uint32_t tile, uint3
     return excl;
 }
 
+// Per-thread variant that keeps four predecessor reads in flight per round trip
+// (one thread per digit in the radix sort, descriptors strided by `stride`).
+__device__ __forceinline__ uint32_t lookback_sum4(uint64_t* desc, size_t stride, uint32_t tile, uint32_t epoch, uint32_t agg,
+                                  uint32_t* err, bool* ok) {
+    const uint64_t tag = (uint64_t)epoch << 32;
+    *ok = true;
+    if (tile == 0) {
+        st_relaxed(desc, tag | kFlagPrefix | (agg & kValMask));
+        return 0;
+    }
+    st_relaxed(desc + (size_t)tile * stride, tag | kFlagAgg | (agg & kValMask));
+    uint32_t excl = 0, spins = 0;
+    int64_t t = (int64_t)tile - 1;
+    while (t >= 0) {
+        uint64_t d[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[i] = (t - i >= 0) ? ld_relaxed(desc + (size_t)(t - i) * stride) : (tag | kFlagPrefix);
+        int used = 0;
+        bool stop = false, stall = false;
+        uint32_t add = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (stop || stall) continue;
+            const uint64_t flag = d[i] & (3ull << 30);
+            if ((uint32_t)(d[i] >> 32) != epoch || flag == 0) {
+                stall = true;
+                continue;
+            }
+            add += (uint32_t)(d[i] & kValMask);
+            ++used;
+            if (flag == kFlagPrefix) stop = true;
+        }
+        excl += add;
+        t -= used;
+        if (stop) break;
+        if (stall) {
+            ++spins;
+            if (spins > kSpinLimit) {
+                atomicOr(err, kErrTimeout);
+                *ok = false;
+                return 0;
+            }
+            if ((spins & 1023u) == 0 && *(volatile uint32_t*)err) {
+                *ok = false;
+                return 0;
+            }
+            if (spins > 32) __nanosleep(100);
+        }
+    }
+    st_relaxed(desc + (size_t)tile * stride, tag | kFlagPrefix | ((excl + agg) & kValMask));
+    return excl;
+}
+
+// Warp-wide variant, called by all 32 lanes of one warp: each round reads the
+// descriptors of 32 predecessors at once (lane i reads tile base - 1 - i), so a run of
+// predecessors that have published only their aggregates is crossed 32 tiles per
+// memory round trip instead of one. Returns the exclusive prefix in every lane.
+template <bool kMax>
+__device__ uint32_t lookback_warp(uint64_t* desc, uint32_t tile, uint32_t epoch, uint32_t agg, uint32_t* err,
+                                  bool* ok) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t tag = (uint64_t)epoch << 32;
+    *ok = true;
+    if (tile == 0) {
+        if (lane == 0) st_relaxed(desc, tag | kFlagPrefix | (agg & kValMask));
+        return 0;
+    }
+    if (lane == 0) st_relaxed(desc + tile, tag | kFlagAgg | (agg & kValMask));
+    uint32_t excl = 0;
+    int64_t base = (int64_t)tile;
+    uint32_t spins = 0;
+    for (;;) {
+        const int64_t t = base - 1 - (int64_t)lane;
+        uint64_t d = (t >= 0) ? ld_relaxed(desc + t) : (tag | kFlagPrefix);  // before tile 0: prefix 0
+        const uint64_t flag = d & (3ull << 30);
+        const bool valid = (uint32_t)(d >> 32) == epoch && flag != 0;
+        const uint32_t pref = __ballot_sync(0xffffffffu, valid && flag == kFlagPrefix);
+        const uint32_t inval = __ballot_sync(0xffffffffu, !valid);
+        const uint32_t stop = pref ? (uint32_t)(__ffs(pref) - 1) : 32u;
+        const uint32_t need = (stop >= 31u) ? 0xffffffffu : ((2u << stop) - 1u);  // lanes 0..stop
+        if (inval & need) {
+            ++spins;
+            if (spins > kSpinLimit) {
+                if (lane == 0) atomicOr(err, kErrTimeout);
+                *ok = false;
+                return 0;
+            }
+            if ((spins & 1023u) == 0 && *(volatile uint32_t*)err) {
+                *ok = false;
+                return 0;
+            }
+            if (spins > 32) __nanosleep(100);
+            continue;
+        }
+        uint32_t v = (lane <= stop) ? (uint32_t)(d & kValMask) : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint32_t y = __shfl_xor_sync(0xffffffffu, v, o);
+            v = lb_op<kMax>(v, y);
+        }
+        excl = lb_op<kMax>(excl, v);
+        if (stop < 32u) break;
+        base -= 32;
+    }
+    if (lane == 0) st_relaxed(desc + tile, tag | kFlagPrefix | (lb_op<kMax>(excl, agg) & kValMask));
+    return excl;
+}
+
 // ---------------------------------------------------------------------------------
 // TMA bulk copies (cp.async.bulk, global -> shared) completing on an mbarrier.
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -353,7 +461,7 @@ struct RebuildArgs {
     uint64_t* lkeys;
     uint32_t* ldown;
     uint64_t* desc;       // look-back descriptors: max(tiles_merge, tiles_rebuild * 32)
-    uint32_t* tile_live;  // scratch
+    uint32_t* tile_cnt;   // rebuild: per-level per-tile counts, then offsets
     uint32_t index_cap;   // entries (without padding)
     uint32_t size_ub;     // upper bound of the storage size after the batch
     uint32_t rebuild_policy;

@@ -15,8 +15,9 @@
 // key do not search: they take their leader's result at the end. Two search forms:
 //  * warp-cooperative (the SIMD-compare analogue of Section 3.2.1): when the leaders'
 //    start positions lie within 16 entries, the warp loads one 32-key segment with one
-//    coalesced access; for each leader, __ballot_sync(segment_key <= q) and the first
-//    zero bit give the rank of the largest key <= q in the segment;
+//    coalesced access, and every lane finds the rank of the largest segment key <= its
+//    query by a five-step binary search over the lanes (shuffles); __ballot_sync
+//    locates the level's sentinel inside the segment;
 //  * per lane: when the leaders are spread out (the lower levels), each lane scans its
 //    own gap from its start position, four keys (and their downs) per round.
 // Both end at the sentinel, so no bound check is needed on a well-formed level; a
@@ -92,29 +93,34 @@ __device__ __forceinline__ void warp_search(const uint64_t* K, const uint32_t* D
             }
             break;
         }
-        const uint64_t seg_k = K[s + lane];
+        // One coalesced 32-key segment for the whole warp (plus its downs).
+        uint64_t seg_k = K[s + lane];
         const uint32_t seg_d = kDown ? D[s + lane] : 0u;
-        uint32_t todo = pend;
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t lo_i = __shfl_sync(kFull, lo, src);
-            if (lo_i >= s + 32u) continue;  // uniform: this segment does not reach lane src
-            const uint64_t qi = __shfl_sync(kFull, q, src);
-            const uint32_t b = __ballot_sync(kFull, seg_k <= qi);
-            const uint32_t c = (b == kFull) ? 32u : (uint32_t)(__ffs(~b) - 1);
-            const int pick = c ? (int)c - 1 : 0;
-            const uint32_t dsel = __shfl_sync(kFull, seg_d, pick);
-            const uint64_t ksel = __shfl_sync(kFull, seg_k, pick);
-            if (lane == src) {
-                if (c == 32u) {
-                    lo = s + 31u;  // every key of the segment is <= q: continue from its end
-                } else {
-                    r = (int32_t)s + (int32_t)c - 1;
-                    dn = c ? dsel : 0u;
-                    kr = c ? ksel : 0ull;
-                    done = true;
-                }
+        // Past the level's sentinel the array holds the next level: clamp to keep the
+        // segment sorted.
+        const uint32_t sent = __ballot_sync(kFull, seg_k == kMaxKey);
+        if (sent && lane > __ffs(sent) - 1) seg_k = kMaxKey;
+        // Each lane counts the segment keys <= its query: binary search over lanes.
+        uint32_t c = 0;
+#pragma unroll
+        for (uint32_t step = 16; step >= 1; step >>= 1) {
+            const uint64_t kk = __shfl_sync(kFull, seg_k, (int)(c + step - 1));
+            if (kk <= q) c += step;
+        }
+        const uint64_t k31 = __shfl_sync(kFull, seg_k, 31);
+        if (c == 31 && k31 <= q) c = 32;
+        const int pick = c ? (int)c - 1 : 0;
+        const uint32_t dsel = __shfl_sync(kFull, seg_d, pick & 31);
+        const uint64_t ksel = __shfl_sync(kFull, seg_k, pick & 31);
+        const bool covered = !done && lo >= s && lo < s + 32u;
+        if (covered) {
+            if (c == 32u) {
+                lo = s + 31u;  // every key of the segment is <= q: continue from its end
+            } else {
+                r = (int32_t)s + (int32_t)c - 1;
+                dn = c ? dsel : 0u;
+                kr = c ? ksel : 0ull;
+                done = true;
             }
         }
         pend = __ballot_sync(kFull, !done);

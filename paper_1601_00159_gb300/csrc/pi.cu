@@ -61,6 +61,8 @@ struct pi_index {
     Staging stg;
     uint64_t* desc = nullptr;
     uint64_t desc_words = 0;
+    uint32_t* tile_cnt = nullptr;  // rebuild counts: (levels) x (storage tiles)
+    uint64_t tile_cnt_words = 0;
     uint32_t epoch = 1;
     // Ring of mailboxes: batch b copies the device meta to slot b % kRing and records
     // ev[b % kRing]; the newest completed slot bounds the host's view of the sizes.
@@ -136,6 +138,15 @@ cudaError_t ensure_desc(pi_index* x, uint64_t words) {
     return e;
 }
 
+cudaError_t ensure_tile_cnt(pi_index* x, uint64_t st_cap) {
+    const uint64_t words = 32 * (st_cap / 4096 + 2);
+    if (words <= x->tile_cnt_words) return cudaSuccess;
+    dfree(x->tile_cnt);
+    cudaError_t e = dalloc(&x->tile_cnt, words);
+    x->tile_cnt_words = (e == cudaSuccess) ? words : 0;
+    return e;
+}
+
 uint32_t next_epochs(pi_index* x, uint32_t count, cudaStream_t s) {
     // Epochs tag look-back descriptors; on wrap-around clear them so no stale word can
     // carry a reused epoch.
@@ -174,13 +185,18 @@ void free_storage(Storage& st) {
     }
 }
 
+// Storage arrays are padded by a whole 4096-node tile plus kPad entries, so that tile
+// loads of the last (partial) tile and read-ahead past the sentinel stay in bounds.
+uint64_t storage_alloc(uint64_t cap) { return cap + 4096 + kPad; }
+
 cudaError_t alloc_storage(Storage& st, uint64_t cap) {
     cudaError_t e;
+    const uint64_t c = storage_alloc(cap);
     for (int i = 0; i < 2; ++i) {
-        if ((e = dalloc(&st.keys[i], cap + kPad)) != cudaSuccess) break;
-        if ((e = dalloc(&st.vals[i], cap + kPad)) != cudaSuccess) break;
-        if ((e = dalloc(&st.meta[i], cap + kPad)) != cudaSuccess) break;
-        cudaMemset(st.meta[i], 0, cap + kPad);
+        if ((e = dalloc(&st.keys[i], c)) != cudaSuccess) break;
+        if ((e = dalloc(&st.vals[i], c)) != cudaSuccess) break;
+        if ((e = dalloc(&st.meta[i], c)) != cudaSuccess) break;
+        cudaMemset(st.meta[i], 0, c);
     }
     if (e != cudaSuccess) free_storage(st);
     return e;
@@ -223,7 +239,7 @@ void destroy(pi_index* x) {
     dfree(x->stg.ops); dfree(x->stg.keys); dfree(x->stg.vals); dfree(x->stg.res);
     free_storage(x->st);
     dfree(x->lkeys); dfree(x->ldown);
-    dfree(x->desc); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
+    dfree(x->desc); dfree(x->tile_cnt); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
     if (x->h_mbox) cudaFreeHost(x->h_mbox);
     for (auto& e : x->ev)
         if (e) cudaEventDestroy(e);
@@ -301,6 +317,7 @@ cudaError_t grow_storage(pi_index* x, uint64_t need, cudaStream_t s) {
     x->st = ns;
     x->st_cap = cap;
     x->known.cur = 0;
+    if ((e = ensure_tile_cnt(x, cap)) != cudaSuccess) return e;
     return ensure_desc(x, desc_need(x->sc.cap, cap));
 }
 
@@ -344,7 +361,7 @@ RebuildArgs rebuild_args(pi_index* x, uint32_t size_ub, uint32_t force) {
     r.lkeys = x->lkeys;
     r.ldown = x->ldown;
     r.desc = x->desc;
-    r.tile_live = nullptr;
+    r.tile_cnt = x->tile_cnt;
     r.index_cap = (uint32_t)(x->idx_cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : x->idx_cap);
     r.size_ub = size_ub;
     r.rebuild_policy = x->rebuild_policy;
@@ -413,6 +430,7 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
         cudaMemsetAsync(x->d_bm, 0, sizeof(BatchMeta), s);
         if ((e = alloc_storage(x->st, st_cap)) != cudaSuccess) break;
         x->st_cap = st_cap;
+        if ((e = ensure_tile_cnt(x, st_cap)) != cudaSuccess) break;
         if ((e = ensure_desc(x, desc_need(n, st_cap))) != cudaSuccess) break;
         // 1. sort (key, arrival) and keep the last of every key run
         if (n > 0) {

@@ -27,7 +27,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kNodes = 4096;             // storage nodes per tile
 constexpr int kPer = kNodes / kThreads;  // 16 per thread
-constexpr uint32_t kCtrMerge = 9, kCtrRebuild = 10, kCtrCreate = 11;
+constexpr uint32_t kCtrMerge = 9, kCtrCreate = 11;
 
 __device__ __forceinline__ bool merge_needed(const DevMeta* m, const BatchMeta* bm) {
     const uint32_t size = m->size;
@@ -96,12 +96,15 @@ __global__ void __launch_bounds__(kThreads) k_merge(RebuildArgs a, uint32_t epoc
             }
             if (tid == kThreads - 1) s_lp[kNodes] = (uint16_t)run;
         }
-        if (tid == 0) {
+        if (tid < 32) {
             bool ok;
-            s_prefix = lookback<false>(a.desc, 1, tile, epoch, tile_live, a.err, &ok);
-            if (!ok) s_ok = 0;
-            s_jb = lower_bound_u32(a.nn.loc, newc, ts);
-            s_je = lower_bound_u32(a.nn.loc, newc, ts + kNodes);
+            const uint32_t ex = lookback_warp<false>(a.desc, tile, epoch, tile_live, a.err, &ok);
+            if (tid == 0) {
+                s_prefix = ex;
+                if (!ok) s_ok = 0;
+                s_jb = lower_bound_u32(a.nn.loc, newc, ts);
+                s_je = lower_bound_u32(a.nn.loc, newc, ts + kNodes);
+            }
         }
         __syncthreads();
         if (!s_ok) break;
@@ -228,8 +231,75 @@ __global__ void k_level_bases(RebuildArgs a) {
 }
 
 // ---------------------------------------------------------------------------------
-// Index-layer rebuild: one pass over the storage layer, all levels.
-__global__ void __launch_bounds__(kThreads) k_rebuild(RebuildArgs a, uint32_t epoch) {
+// Index-layer rebuild, in three launches over tiles of 4096 storage nodes:
+//   count: per tile and level l, the live nodes of height >= l (reads meta only);
+//   scan:  per level, the exclusive prefix of those counts over tiles (one CTA/level);
+//   write: per tile, keys and meta arrive in shared memory by TMA bulk copy; level by
+//          level the tile compacts its nodes of height >= l (a block prefix sum over
+//          the previous level's list) and writes keys and down pointers.
+// Counts are laid out level-major: cnt[(l - Lb) * ntiles + tile].
+__global__ void __launch_bounds__(kThreads) k_rebuild_count(RebuildArgs a) {
+    __shared__ uint32_t s_hist[kLevelSlots];
+    const int tid = threadIdx.x;
+    const DevMeta* m = a.m;
+    if (block_sees_error(&m->error)) return;
+    if (!a.bm->rebuild) return;
+    const uint32_t H = m->H, Lb = m->Lb, size = m->size, cur = m->cur;
+    if (H < Lb || size == 0) return;
+    const uint32_t ntiles = (size + kNodes - 1) / kNodes;
+    const uint32_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    if (tid < kLevelSlots) s_hist[tid] = 0;
+    __syncthreads();
+    const uint32_t ts = tile * kNodes;
+    const uint32_t cnt = min((uint32_t)kNodes, size - ts);
+    const uint8_t* SM = a.st.meta[cur] + ts;
+    // 16 meta bytes per thread in one 128-bit load (the array is padded past its end)
+    const uint4 w = *reinterpret_cast<const uint4*>(SM + tid * kPer);
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const uint32_t li = tid * kPer + k;
+        const uint32_t mt = (words[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+        const uint32_t h = (li < cnt && !(mt & kTomb)) ? (mt & kHeightMask) : 0u;
+        if (h >= Lb) atomicAdd(&s_hist[min(h, H)], 1u);
+    }
+    __syncthreads();
+    if (tid >= (int)Lb && tid <= (int)H) {
+        uint32_t c = 0;
+        for (uint32_t h = tid; h <= H; ++h) c += s_hist[h];
+        a.tile_cnt[(size_t)(tid - Lb) * ntiles + tile] = c;
+    }
+}
+
+// One CTA per level: exclusive scan of the tile counts in place; checks the total.
+__global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_carry;
+    const DevMeta* m = a.m;
+    if (block_sees_error(&m->error)) return;
+    if (!a.bm->rebuild) return;
+    const uint32_t H = m->H, Lb = m->Lb, size = m->size;
+    const uint32_t l = Lb + blockIdx.x;
+    if (H < Lb || size == 0 || l > H) return;
+    const uint32_t ntiles = (size + kNodes - 1) / kNodes;
+    uint32_t* c = a.tile_cnt + (size_t)(l - Lb) * ntiles;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < ntiles; b0 += 1024) {
+        const uint32_t i = b0 + threadIdx.x;
+        const uint32_t v = i < ntiles ? c[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_sum<1024>(v, s_tmp, &tot);
+        if (i < ntiles) c[i] = s_carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && s_carry != m->n[l]) atomicOr(a.err, kErrBounds);  // counts disagree
+}
+
+__global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);                        // kNodes + 2
     uint8_t* s_meta = s_dyn + (kNodes + 2) * sizeof(uint64_t);                     // kNodes + 16
@@ -237,133 +307,99 @@ __global__ void __launch_bounds__(kThreads) k_rebuild(RebuildArgs a, uint32_t ep
     uint32_t* s_lb = s_la + kNodes;                                                // list (pong)
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmp[33];
-    __shared__ uint32_t s_hist[kLevelSlots];
-    __shared__ uint32_t s_off[kLevelSlots];
-    __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
-    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_off[kLevelSlots], s_base[kLevelSlots], s_n[kLevelSlots];
     __shared__ int s_ok;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const DevMeta* m = a.m;
     if (block_sees_error(&m->error)) return;
     if (!a.bm->rebuild) return;
     const uint32_t H = m->H, Lb = m->Lb, size = m->size, cur = m->cur;
     if (H < Lb || size == 0) return;
-    const uint64_t* SK = a.st.keys[cur];
-    const uint8_t* SM = a.st.meta[cur];
     const uint32_t ntiles = (size + kNodes - 1) / kNodes;
-    if (tid < kLevelSlots) {
-        s_base[tid] = m->base[tid];
-        s_n[tid] = m->n[tid];
-    }
+    const uint32_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    const uint32_t ts = tile * kNodes;
+    const uint32_t cnt = min((uint32_t)kNodes, size - ts);
     if (tid == 0) {
         s_ok = 1;
         mbar_init(&s_bar, 1);
+        const uint32_t bk = ((cnt * 8u + 15u) / 16u) * 16u;
+        const uint32_t bm_ = ((cnt + 15u) / 16u) * 16u;
+        mbar_arrive_expect_tx(&s_bar, bk + bm_);
+        bulk_g2s(s_keys, a.st.keys[cur] + ts, bk, &s_bar);
+        bulk_g2s(s_meta, a.st.meta[cur] + ts, bm_, &s_bar);
     }
-    uint32_t phase = 0;
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_tile = atomicAdd(&a.bm->tile_ctr[kCtrRebuild], 1u);
-        if (tid < kLevelSlots) s_hist[tid] = 0;
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const uint32_t ts = tile * kNodes;
-        const uint32_t cnt = min((uint32_t)kNodes, size - ts);
-        if (tid == 0) {
-            const uint32_t bk = ((cnt * 8u + 15u) / 16u) * 16u;
-            const uint32_t bm_ = ((cnt + 15u) / 16u) * 16u;
-            mbar_arrive_expect_tx(&s_bar, bk + bm_);
-            bulk_g2s(s_keys, SK + ts, bk, &s_bar);
-            bulk_g2s(s_meta, SM + ts, bm_, &s_bar);
-        }
-        if (!mbar_wait_bounded(&s_bar, phase, a.err)) s_ok = 0;
-        phase ^= 1u;
-        __syncthreads();
-        if (!s_ok) {
-            if (tid == 0) mbar_wait_bounded(&s_bar, phase ^ 1u, a.err);
+    if (tid < kLevelSlots) {
+        s_base[tid] = m->base[tid];
+        s_n[tid] = m->n[tid];
+        s_off[tid] = (tid >= (int)Lb && tid <= (int)H) ? a.tile_cnt[(size_t)(tid - Lb) * ntiles + tile] : 0u;
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&s_bar, 0, a.err)) s_ok = 0;
+    __syncthreads();
+    if (!s_ok) {
+        if (tid == 0) mbar_wait_bounded(&s_bar, 0, a.err);  // let the copy land
+        return;
+    }
+    // level Lb: live nodes of height >= Lb, in node order
+    const uint32_t b0 = tid * kPer;
+    uint32_t bits = 0, c_lb = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const uint32_t li = b0 + k;
+        const uint8_t mt = li < cnt ? s_meta[li] : (uint8_t)kTomb;
+        const bool in = !(mt & kTomb) && (uint32_t)(mt & kHeightMask) >= Lb;
+        bits |= (in ? 1u : 0u) << k;
+        c_lb += in ? 1u : 0u;
+    }
+    uint32_t tot;
+    uint32_t w = block_excl_sum<kThreads>(c_lb, s_tmp, &tot);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+        if ((bits >> k) & 1u) s_la[w++] = b0 + k;
+    __syncthreads();
+    for (uint32_t j = tid; j < tot; j += kThreads) {
+        const uint32_t node = s_la[j];
+        if (s_off[Lb] + j >= s_n[Lb]) {
+            atomicOr(a.err, kErrBounds);
             break;
         }
-        // live heights of this tile
-        const uint32_t b0 = tid * kPer;
-        uint32_t hts[kPer];
-        uint32_t c_lb = 0;
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const uint32_t li = b0 + k;
-            const uint8_t mt = li < cnt ? s_meta[li] : (uint8_t)kTomb;
-            const uint32_t h = (mt & kTomb) ? 0u : (uint32_t)(mt & kHeightMask);
-            hts[k] = h;
-            if (h >= 2) atomicAdd(&s_hist[min(h, H)], 1u);
-            c_lb += (h >= Lb) ? 1u : 0u;
+        const uint32_t g = s_base[Lb] + s_off[Lb] + j;
+        a.lkeys[g] = s_keys[node];
+        a.ldown[g] = ts + node;
+    }
+    // levels above: compact the previous level's list
+    uint32_t* prev = s_la;
+    uint32_t* next = s_lb;
+    uint32_t mprev = tot;
+    for (uint32_t l = Lb + 1; l <= H && mprev > 0; ++l) {
+        const uint32_t per = (mprev + kThreads - 1) / kThreads;
+        const uint32_t jb = min(tid * per, mprev), je = min(jb + per, mprev);
+        uint32_t c = 0;
+        for (uint32_t j = jb; j < je; ++j) c += (s_meta[prev[j] & 0xFFFFu] & kHeightMask) >= l ? 1u : 0u;
+        uint32_t mcur;
+        uint32_t wpos = block_excl_sum<kThreads>(c, s_tmp, &mcur);
+        for (uint32_t j = jb; j < je; ++j) {
+            const uint32_t node = prev[j] & 0xFFFFu;
+            if ((s_meta[node] & kHeightMask) >= l) next[wpos++] = node | (j << 16);
         }
         __syncthreads();
-        if (warp == 0) {
-            // per-level tile counts (suffix sums of the histogram), then one look-back
-            // per level: lane i handles level Lb + i.
-            const uint32_t l = Lb + (uint32_t)lane;
-            uint32_t c = 0;
-            if (l <= H)
-                for (uint32_t h = l; h <= H; ++h) c += s_hist[h];
-            bool ok = true;
-            uint32_t ex = 0;
-            if (l <= H) ex = lookback<false>(a.desc + lane, 32, tile, epoch, c, a.err, &ok);
-            if (!ok) s_ok = 0;
-            if (l <= H) s_off[l] = ex;
-        }
-        // level Lb: compact live nodes of height >= Lb
-        uint32_t tot;
-        const uint32_t ex0 = block_excl_sum<kThreads>(c_lb, s_tmp, &tot);
-        {
-            uint32_t w = ex0;
-#pragma unroll
-            for (int k = 0; k < kPer; ++k)
-                if (hts[k] >= Lb) s_la[w++] = b0 + k;  // node index (list entry of level Lb)
-        }
-        __syncthreads();
-        if (!s_ok) break;
-        for (uint32_t j = tid; j < tot; j += kThreads) {
-            const uint32_t node = s_la[j] & 0xFFFFu;
-            const uint32_t g = s_base[Lb] + s_off[Lb] + j;
-            if (s_off[Lb] + j >= s_n[Lb]) {
+        for (uint32_t j = tid; j < mcur; j += kThreads) {
+            const uint32_t e = next[j];
+            if (s_off[l] + j >= s_n[l]) {
                 atomicOr(a.err, kErrBounds);
                 break;
             }
-            a.lkeys[g] = s_keys[node];
-            a.ldown[g] = ts + node;
+            const uint32_t g = s_base[l] + s_off[l] + j;
+            a.lkeys[g] = s_keys[e & 0xFFFFu];
+            a.ldown[g] = s_off[l - 1] + (e >> 16);
         }
-        // levels above: compact the previous level's list
-        uint32_t* prev = s_la;
-        uint32_t* next = s_lb;
-        uint32_t mprev = tot;
-        for (uint32_t l = Lb + 1; l <= H && mprev > 0; ++l) {
-            const uint32_t per = (mprev + kThreads - 1) / kThreads;
-            const uint32_t jb = min(tid * per, mprev), je = min(jb + per, mprev);
-            uint32_t c = 0;
-            for (uint32_t j = jb; j < je; ++j) c += (s_meta[prev[j] & 0xFFFFu] & kHeightMask) >= l ? 1u : 0u;
-            uint32_t mcur;
-            uint32_t w = block_excl_sum<kThreads>(c, s_tmp, &mcur);
-            for (uint32_t j = jb; j < je; ++j) {
-                const uint32_t node = prev[j] & 0xFFFFu;
-                if ((s_meta[node] & kHeightMask) >= l) next[w++] = node | (j << 16);
-            }
-            __syncthreads();
-            for (uint32_t j = tid; j < mcur; j += kThreads) {
-                const uint32_t e = next[j];
-                const uint32_t g = s_base[l] + s_off[l] + j;
-                if (s_off[l] + j >= s_n[l]) {
-                    atomicOr(a.err, kErrBounds);
-                    break;
-                }
-                a.lkeys[g] = s_keys[e & 0xFFFFu];
-                a.ldown[g] = s_off[l - 1] + (e >> 16);
-            }
-            __syncthreads();
-            uint32_t* t = prev;
-            prev = next;
-            next = t;
-            mprev = mcur;
-        }
+        __syncthreads();
+        uint32_t* t = prev;
+        prev = next;
+        next = t;
+        mprev = mcur;
     }
 }
 
@@ -404,11 +440,14 @@ __global__ void __launch_bounds__(kThreads) k_create_storage(CreateArgs a, uint3
         }
         uint32_t tot;
         const uint32_t ex = block_excl_sum<kThreads>(c, s_tmp, &tot);
-        if (tid == 0) {
+        if (tid < 32) {
             bool ok;
-            s_prefix = lookback<false>(a.desc, 1, tile, epoch, tot, a.err, &ok);
-            if (!ok) s_ok = 0;
-            s_kept += tot;
+            const uint32_t ex = lookback_warp<false>(a.desc, tile, epoch, tot, a.err, &ok);
+            if (tid == 0) {
+                s_prefix = ex;
+                if (!ok) s_ok = 0;
+                s_kept += tot;
+            }
         }
         __syncthreads();
         if (!s_ok) break;
@@ -469,11 +508,14 @@ __global__ void __launch_bounds__(kThreads) k_export_live(Storage st, const DevM
         }
         uint32_t tot;
         const uint32_t ex = block_excl_sum<kThreads>(c, s_tmp, &tot);
-        if (tid == 0) {
+        if (tid < 32) {
             bool ok;
-            s_prefix = lookback<false>(desc, 1, tile, epoch, tot, err, &ok);
-            if (!ok) s_ok = 0;
-            if (tile == ntiles - 1) *count = s_prefix + tot;
+            const uint32_t ex = lookback_warp<false>(desc, tile, epoch, tot, err, &ok);
+            if (tid == 0) {
+                s_prefix = ex;
+                if (!ok) s_ok = 0;
+                if (tile == ntiles - 1) *count = ex + tot;
+            }
         }
         __syncthreads();
         if (!s_ok) break;
@@ -504,16 +546,19 @@ cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
+    (void)epoch;
+    (void)num_sms;
     static bool attr_set = false;
     const int dyn = (kNodes + 2) * 8 + kNodes + 16 + 2 * kNodes * 4;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_rebuild, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaError_t e = cudaFuncSetAttribute(k_rebuild_write, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const uint32_t tiles = a.size_ub / kNodes + 1;
-    const uint32_t cap = (uint32_t)num_sms * 2u;
-    k_rebuild<<<(int)(tiles < cap ? tiles : cap), kThreads, dyn, s>>>(a, ++epoch);
+    const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
+    k_rebuild_count<<<tiles, kThreads, 0, s>>>(a);
+    k_rebuild_scan<<<kLevelSlots - 2, 1024, 0, s>>>(a);
+    k_rebuild_write<<<tiles, kThreads, dyn, s>>>(a);
     return cudaGetLastError();
 }
 

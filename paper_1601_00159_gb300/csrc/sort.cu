@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(uint32_t j, uint32_t n, 
         total += c;
     }
     bool ok;
-    uint32_t excl = lookback<false>(sb.desc + tid, 256, tile, epoch, total, err, &ok);
+    uint32_t excl = lookback_sum4(sb.desc + tid, 256, tile, epoch, total, err, &ok);
     if (!ok) s_ok = 0;
     s_gbase[tid] = sb.dofs[P.digit[j] * 256 + tid] + excl;
     s_tstart[tid] = block_excl_sum<kThreads>(total, s_tmp, nullptr);
