@@ -36,7 +36,7 @@ from paper_1601_00159_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "Mqueries/s and % of HBM roofline on 1 GB300; p50/p99 latency in serving loop"
 UNIT = "Mqueries/s"
-KERNELS_PER_STEP = 15  # pack, plan, 8 radix passes, descend, apply, merge, layout, rebuild
+KERNELS_PER_STEP = 17  # pack, plan, 8 radix passes, descend, apply, merge, layout, rebuild count/scan/write
 
 WORKLOADS = {
     "skewed": dict(fn=wl.skewed, n=1 << 27, q=1 << 22,

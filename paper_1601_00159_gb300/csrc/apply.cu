@@ -160,7 +160,11 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a, uint32_t epoch_
                     atomicAdd(&s_tomb, fin_live ? -1 : 1);
                     atomicAdd(&s_changes, 1u);
                     atomicAdd(&s_delta[1], fin_live ? 1 : -1);
-                    for (uint32_t l = 2; l <= h; ++l) atomicAdd(&s_delta[l], fin_live ? 1 : -1);
+                    for (uint32_t l = 2; l <= h; ++l) {
+                        atomicAdd(&s_delta[l], fin_live ? 1 : -1);
+                        // the rebuild's per-tile count of the node's 4096-node tile
+                        atomicAdd(&a.lcnt[(size_t)(l - 2) * a.lstride + (r >> 12)], fin_live ? 1u : 0xFFFFFFFFu);
+                    }
                     if (h >= 2) s_dirty = 1;
                 }
             } else if (fin_live) {

@@ -14,6 +14,7 @@ constexpr uint8_t kTomb = 0x80;      // meta bit 7: the delete flag F_del (Algor
 constexpr uint8_t kHeightMask = 0x3F;
 constexpr uint32_t kSmemTopMax = 4096;  // index entries staged in shared memory
 constexpr uint32_t kPad = 64;           // readable entries past every array's end
+constexpr uint32_t kSortTile = 2048;    // elements per radix-sort tile
 
 // Sticky error bits in DevMeta::error.
 constexpr uint32_t kErrTimeout = 1u;  // a bounded wait gave up
@@ -447,6 +448,8 @@ struct ApplyArgs {
     DevMeta* m;
     BatchMeta* bm;
     uint64_t* desc;  // 2 * tiles words
+    uint32_t* lcnt;  // per-level per-tile live counts (see RebuildArgs)
+    uint32_t lstride;
     uint32_t n;
     HashParams hp;
     uint32_t* err;
@@ -461,7 +464,9 @@ struct RebuildArgs {
     uint64_t* lkeys;
     uint32_t* ldown;
     uint64_t* desc;       // look-back descriptors: max(tiles_merge, tiles_rebuild * 32)
-    uint32_t* tile_cnt;   // rebuild: per-level per-tile counts, then offsets
+    uint32_t* lcnt;       // per-level per-tile live counts, level-major, row stride lstride
+    uint32_t* loff;       // rebuild: per-level per-tile offsets (scan output)
+    uint32_t lstride;     // tiles per row of lcnt (storage capacity / 4096 + 2)
     uint32_t index_cap;   // entries (without padding)
     uint32_t size_ub;     // upper bound of the storage size after the batch
     uint32_t rebuild_policy;

@@ -67,41 +67,29 @@ __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, 
 }
 
 // Called by all 32 lanes. Lanes with `want` search level (K, D) from their `lo`.
+// When the searching lanes start within 8 entries of each other (the usual case on
+// the upper levels, since the batch is sorted), the warp loads one 32-key segment
+// with one coalesced access and each lane finds its rank in it by a five-step binary
+// search over the lanes; a lane whose answer lies past the segment, and every lane
+// when the starts are spread out (the lower levels), scans on its own.
 template <bool kDown>
 __device__ __forceinline__ void warp_search(const uint64_t* K, const uint32_t* D, uint32_t& lo, uint32_t lim,
                                             uint64_t q, bool want, int32_t& r, uint32_t& dn, uint64_t& kr,
                                             uint32_t* err) {
     const int lane = threadIdx.x & 31;
-    uint32_t pend = __ballot_sync(kFull, want);
-    if (!pend) return;
     const uint32_t lo_min = __reduce_min_sync(kFull, want ? lo : 0xffffffffu);
+    if (lo_min == 0xffffffffu) return;  // no lane searches this level
     const uint32_t lo_max = __reduce_max_sync(kFull, want ? lo : 0u);
-    if (lo_max - lo_min >= 16u) {
-        if (want) lane_scan<kDown>(K, D, lo, lim, q, r, dn, kr, err);
-        return;
-    }
-    bool done = !want;
-    for (uint32_t round = 0; pend; ++round) {
-        const uint32_t s = __reduce_min_sync(kFull, done ? 0xffffffffu : lo);
-        if (s > lim || round > (lim >> 4) + 4u) {  // cannot happen on a well-formed level
-            if (!done) {
-                atomicOr(err, kErrBounds);
-                r = -1;
-                dn = 0;
-                kr = 0;
-                done = true;
-            }
-            break;
-        }
-        // One coalesced 32-key segment for the whole warp (plus its downs).
+    bool scan = want;
+    if (lo_max - lo_min < 8u && lo_min <= lim) {
+        const uint32_t s = lo_min;
         uint64_t seg_k = K[s + lane];
         const uint32_t seg_d = kDown ? D[s + lane] : 0u;
-        // Past the level's sentinel the array holds the next level: clamp to keep the
-        // segment sorted.
+        // Past the level's sentinel the array holds the next level: clamp so the
+        // segment stays sorted.
         const uint32_t sent = __ballot_sync(kFull, seg_k == kMaxKey);
         if (sent && lane > __ffs(sent) - 1) seg_k = kMaxKey;
-        // Each lane counts the segment keys <= its query: binary search over lanes.
-        uint32_t c = 0;
+        uint32_t c = 0;  // segment keys <= q (keys before lo are <= q as well)
 #pragma unroll
         for (uint32_t step = 16; step >= 1; step >>= 1) {
             const uint64_t kk = __shfl_sync(kFull, seg_k, (int)(c + step - 1));
@@ -112,19 +100,33 @@ __device__ __forceinline__ void warp_search(const uint64_t* K, const uint32_t* D
         const int pick = c ? (int)c - 1 : 0;
         const uint32_t dsel = __shfl_sync(kFull, seg_d, pick & 31);
         const uint64_t ksel = __shfl_sync(kFull, seg_k, pick & 31);
-        const bool covered = !done && lo >= s && lo < s + 32u;
-        if (covered) {
-            if (c == 32u) {
-                lo = s + 31u;  // every key of the segment is <= q: continue from its end
-            } else {
+        if (want) {
+            if (c < 32u) {
                 r = (int32_t)s + (int32_t)c - 1;
                 dn = c ? dsel : 0u;
                 kr = c ? ksel : 0ull;
-                done = true;
+                scan = false;
+            } else {
+                lo = s + 31u;  // every segment key is <= q: continue from its end
             }
         }
-        pend = __ballot_sync(kFull, !done);
     }
+    if (scan) lane_scan<kDown>(K, D, lo, lim, q, r, dn, kr, err);
+}
+
+// Largest index of K[0..n) (sorted, in shared memory) with key <= q, or -1.
+__device__ __forceinline__ int32_t smem_rank(const uint64_t* K, uint32_t n, uint64_t q) {
+    uint32_t lo = 0, len = n;
+    while (len > 0) {
+        const uint32_t half = len >> 1;
+        if (K[lo + half] <= q) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return (int32_t)lo - 1;
 }
 
 __global__ void __launch_bounds__(kThreads) k_descend(DescendArgs a) {
@@ -180,14 +182,24 @@ __global__ void __launch_bounds__(kThreads) k_descend(DescendArgs a) {
         int32_t r = -1;
         uint32_t dn = 0;
         uint64_t kr = 0;
-        for (int l = (int)H; l >= (int)Lb; --l) {
-            const bool sm = (uint32_t)l >= Ls;
-            const uint64_t* K = sm ? s_k + s_base[l] : a.lkeys + s_base[l];
-            const uint32_t* D = sm ? s_d + s_base[l] : a.ldown + s_base[l];
+        int top = (int)H;
+        if (Ls <= H) {
+            // The pinned levels Ls..H are in shared memory. Level Ls holds every key of
+            // the levels above it, so the entry the walk down those levels would reach
+            // on level Ls -- its largest key <= q -- is found by one binary search.
+            if (leader) {
+                r = smem_rank(s_k + s_base[Ls], s_n[Ls], q);
+                lo = (r >= 0) ? s_d[s_base[Ls] + r] : 0u;
+            }
+            top = (int)Ls - 1;
+        }
+        for (int l = top; l >= (int)Lb; --l) {
+            const uint64_t* K = a.lkeys + s_base[l];
+            const uint32_t* D = a.ldown + s_base[l];
             r = -1;
             dn = 0;
             warp_search<true>(K, D, lo, s_n[l], q, leader, r, dn, kr, a.err);
-            lo = (r >= 0) ? dn : 0u;
+            if (leader) lo = (r >= 0) ? dn : 0u;
         }
         r = -1;
         kr = 0;

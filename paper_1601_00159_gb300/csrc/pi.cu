@@ -61,8 +61,9 @@ struct pi_index {
     Staging stg;
     uint64_t* desc = nullptr;
     uint64_t desc_words = 0;
-    uint32_t* tile_cnt = nullptr;  // rebuild counts: (levels) x (storage tiles)
-    uint64_t tile_cnt_words = 0;
+    uint32_t* lcnt = nullptr;  // per-level per-tile live counts: 32 rows x lstride
+    uint32_t* loff = nullptr;  // rebuild offsets, same shape
+    uint32_t lstride = 0;
     uint32_t epoch = 1;
     // Ring of mailboxes: batch b copies the device meta to slot b % kRing and records
     // ev[b % kRing]; the newest completed slot bounds the host's view of the sizes.
@@ -118,7 +119,7 @@ int map_cuda(cudaError_t e) {
 
 // Look-back descriptors needed for q queries and a storage capacity of s nodes.
 uint64_t desc_need(uint64_t q, uint64_t s) {
-    uint64_t a = ((q + 4095) / 4096) * 256;  // sort passes
+    uint64_t a = ((q + kSortTile - 1) / kSortTile) * 256;  // sort passes
     uint64_t b = 2 * ((q + 2047) / 2048);    // apply
     uint64_t c = (s / 4096 + 2) * 32;        // rebuild (and merge, export)
     uint64_t m = a > b ? a : b;
@@ -138,12 +139,18 @@ cudaError_t ensure_desc(pi_index* x, uint64_t words) {
     return e;
 }
 
+// Per-level per-tile counts are rows of (storage capacity / 4096 + 2) tiles; a new
+// capacity reallocates them and the next rebuild recounts (force_rebuild).
 cudaError_t ensure_tile_cnt(pi_index* x, uint64_t st_cap) {
-    const uint64_t words = 32 * (st_cap / 4096 + 2);
-    if (words <= x->tile_cnt_words) return cudaSuccess;
-    dfree(x->tile_cnt);
-    cudaError_t e = dalloc(&x->tile_cnt, words);
-    x->tile_cnt_words = (e == cudaSuccess) ? words : 0;
+    const uint64_t stride = st_cap / 4096 + 2;
+    if (stride <= x->lstride) return cudaSuccess;
+    dfree(x->lcnt);
+    dfree(x->loff);
+    cudaError_t e = dalloc(&x->lcnt, 32 * stride);
+    if (e == cudaSuccess) e = dalloc(&x->loff, 32 * stride);
+    if (e == cudaSuccess) e = cudaMemset(x->lcnt, 0, 32 * stride * sizeof(uint32_t));
+    x->lstride = (e == cudaSuccess) ? (uint32_t)stride : 0u;
+    x->force_rebuild = true;
     return e;
 }
 
@@ -239,7 +246,7 @@ void destroy(pi_index* x) {
     dfree(x->stg.ops); dfree(x->stg.keys); dfree(x->stg.vals); dfree(x->stg.res);
     free_storage(x->st);
     dfree(x->lkeys); dfree(x->ldown);
-    dfree(x->desc); dfree(x->tile_cnt); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
+    dfree(x->desc); dfree(x->lcnt); dfree(x->loff); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
     if (x->h_mbox) cudaFreeHost(x->h_mbox);
     for (auto& e : x->ev)
         if (e) cudaEventDestroy(e);
@@ -361,7 +368,9 @@ RebuildArgs rebuild_args(pi_index* x, uint32_t size_ub, uint32_t force) {
     r.lkeys = x->lkeys;
     r.ldown = x->ldown;
     r.desc = x->desc;
-    r.tile_cnt = x->tile_cnt;
+    r.lcnt = x->lcnt;
+    r.loff = x->loff;
+    r.lstride = x->lstride;
     r.index_cap = (uint32_t)(x->idx_cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : x->idx_cap);
     r.size_ub = size_ub;
     r.rebuild_policy = x->rebuild_policy;
@@ -483,6 +492,7 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
         if ((e = launch_rebuild(ra, ep, s, x->num_sms)) != cudaSuccess) break;
         x->epoch = ep;
         if ((e = read_meta(x, s, &x->known)) != cudaSuccess) break;
+        x->force_rebuild = false;
         if (x->known.error) {
             rc = sticky_error(x->known);
             break;
@@ -574,6 +584,8 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
     aa.m = x->d_meta;
     aa.bm = x->d_bm;
     aa.desc = x->desc;
+    aa.lcnt = x->lcnt;
+    aa.lstride = x->lstride;
     aa.n = (uint32_t)n;
     aa.hp = x->hp;
     aa.err = &x->d_meta->error;

@@ -231,48 +231,57 @@ __global__ void k_level_bases(RebuildArgs a) {
 }
 
 // ---------------------------------------------------------------------------------
-// Index-layer rebuild, in three launches over tiles of 4096 storage nodes:
-//   count: per tile and level l, the live nodes of height >= l (reads meta only);
-//   scan:  per level, the exclusive prefix of those counts over tiles (one CTA/level);
-//   write: per tile, keys and meta arrive in shared memory by TMA bulk copy; level by
-//          level the tile compacts its nodes of height >= l (a block prefix sum over
-//          the previous level's list) and writes keys and down pointers.
-// Counts are laid out level-major: cnt[(l - Lb) * ntiles + tile].
-__global__ void __launch_bounds__(kThreads) k_rebuild_count(RebuildArgs a) {
-    __shared__ uint32_t s_hist[kLevelSlots];
-    const int tid = threadIdx.x;
+// Index-layer rebuild over tiles of 4096 storage nodes.
+//   lcnt[(l - 2) * stride + tile] = live nodes of height >= l in the tile, for every
+//   level l >= 2. The apply kernel keeps these counts current (its owners add or
+//   remove one node per liveness change), so they are recounted from meta only after
+//   the storage layer was re-laid-out (merge), at create, or after a capacity change.
+//   scan:  per level, the exclusive prefix of the counts over tiles (one CTA/level)
+//          into loff[(l - Lb) * ntiles + tile];
+//   write: per tile, keys and meta arrive in shared memory by TMA bulk copy. Warp w
+//          owns nodes [512 w, 512 w + 512) of the tile: it counts its nodes per level
+//          (one ballot per level per 32 nodes), the warps' counts are prefixed across
+//          the tile (one barrier), then the warp sweeps its nodes again and every node
+//          of height >= l writes its key and down pointer to level l at the position
+//          given by the same ballots.
+__global__ void __launch_bounds__(256) k_rebuild_count(RebuildArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const DevMeta* m = a.m;
-    if (block_sees_error(&m->error)) return;
-    if (!a.bm->rebuild) return;
-    const uint32_t H = m->H, Lb = m->Lb, size = m->size, cur = m->cur;
-    if (H < Lb || size == 0) return;
+    if (*(volatile const uint32_t*)&m->error) return;  // no barrier in this kernel
+    if (!a.bm->rebuild || !(a.bm->merged || a.force_rebuild)) return;
+    const uint32_t size = m->size, cur = m->cur;
     const uint32_t ntiles = (size + kNodes - 1) / kNodes;
-    const uint32_t tile = blockIdx.x;
+    const uint32_t tile = blockIdx.x * 8u + (uint32_t)warp;
     if (tile >= ntiles) return;
-    if (tid < kLevelSlots) s_hist[tid] = 0;
-    __syncthreads();
     const uint32_t ts = tile * kNodes;
     const uint32_t cnt = min((uint32_t)kNodes, size - ts);
     const uint8_t* SM = a.st.meta[cur] + ts;
-    // 16 meta bytes per thread in one 128-bit load (the array is padded past its end)
-    const uint4 w = *reinterpret_cast<const uint4*>(SM + tid * kPer);
-    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+    uint32_t c = 0;  // lane i: nodes of height >= 2 + i
+    for (uint32_t it = 0; it < kNodes / 512; ++it) {
+        const uint32_t off = it * 512u + (uint32_t)lane * 16u;
+        const uint4 w = *reinterpret_cast<const uint4*>(SM + off);  // padded past the end
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+        uint32_t hs[16];
+        uint32_t hm = 0;
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const uint32_t li = tid * kPer + k;
-        const uint32_t mt = (words[k >> 2] >> (8 * (k & 3))) & 0xFFu;
-        const uint32_t h = (li < cnt && !(mt & kTomb)) ? (mt & kHeightMask) : 0u;
-        if (h >= Lb) atomicAdd(&s_hist[min(h, H)], 1u);
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t mt = (words[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+            hs[k] = (off + k < cnt && !(mt & kTomb)) ? (mt & kHeightMask) : 0u;
+            hm = max(hm, hs[k]);
+        }
+        const uint32_t wm = __reduce_max_sync(0xffffffffu, hm);
+        for (uint32_t l = 2; l <= wm; ++l) {
+            uint32_t loc = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) loc += hs[k] >= l ? 1u : 0u;
+            const uint32_t tot = __reduce_add_sync(0xffffffffu, loc);
+            if ((uint32_t)lane == l - 2) c += tot;
+        }
     }
-    __syncthreads();
-    if (tid >= (int)Lb && tid <= (int)H) {
-        uint32_t c = 0;
-        for (uint32_t h = tid; h <= H; ++h) c += s_hist[h];
-        a.tile_cnt[(size_t)(tid - Lb) * ntiles + tile] = c;
-    }
+    if (lane < 32 && lane + 2 < kLevelSlots) a.lcnt[(size_t)lane * a.lstride + tile] = c;
 }
 
-// One CTA per level: exclusive scan of the tile counts in place; checks the total.
+// One CTA per built level: exclusive scan of the tile counts; checks the total.
 __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
     __shared__ uint32_t s_tmp[33];
     __shared__ uint32_t s_carry;
@@ -283,7 +292,8 @@ __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
     const uint32_t l = Lb + blockIdx.x;
     if (H < Lb || size == 0 || l > H) return;
     const uint32_t ntiles = (size + kNodes - 1) / kNodes;
-    uint32_t* c = a.tile_cnt + (size_t)(l - Lb) * ntiles;
+    const uint32_t* c = a.lcnt + (size_t)(l - 2) * a.lstride;
+    uint32_t* o = a.loff + (size_t)(l - Lb) * ntiles;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     for (uint32_t b0 = 0; b0 < ntiles; b0 += 1024) {
@@ -291,7 +301,7 @@ __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
         const uint32_t v = i < ntiles ? c[i] : 0u;
         uint32_t tot;
         const uint32_t ex = block_excl_sum<1024>(v, s_tmp, &tot);
-        if (i < ntiles) c[i] = s_carry + ex;
+        if (i < ntiles) o[i] = s_carry + ex;
         __syncthreads();
         if (threadIdx.x == 0) s_carry += tot;
         __syncthreads();
@@ -301,16 +311,14 @@ __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
 
 __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
-    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);                        // kNodes + 2
-    uint8_t* s_meta = s_dyn + (kNodes + 2) * sizeof(uint64_t);                     // kNodes + 16
-    uint32_t* s_la = reinterpret_cast<uint32_t*>(s_meta + kNodes + 16);            // list (ping)
-    uint32_t* s_lb = s_la + kNodes;                                                // list (pong)
+    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);     // kNodes + 2
+    uint8_t* s_meta = s_dyn + (kNodes + 2) * sizeof(uint64_t);  // kNodes + 16
     __shared__ __align__(8) uint64_t s_bar;
-    __shared__ uint32_t s_tmp[33];
-    __shared__ uint32_t s_off[kLevelSlots], s_base[kLevelSlots], s_n[kLevelSlots];
+    __shared__ uint32_t s_wcnt[8][32];
+    __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
     __shared__ int s_ok;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const DevMeta* m = a.m;
     if (block_sees_error(&m->error)) return;
     if (!a.bm->rebuild) return;
@@ -333,73 +341,61 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     if (tid < kLevelSlots) {
         s_base[tid] = m->base[tid];
         s_n[tid] = m->n[tid];
-        s_off[tid] = (tid >= (int)Lb && tid <= (int)H) ? a.tile_cnt[(size_t)(tid - Lb) * ntiles + tile] : 0u;
     }
     __syncthreads();
     if (!mbar_wait_bounded(&s_bar, 0, a.err)) s_ok = 0;
+    // this warp's nodes: [w0, w0 + 512), 16 chunks of 32 (lane = node)
+    const uint32_t w0 = (uint32_t)warp * 512u;
+    const uint32_t lt = lanemask_lt();
+    uint32_t c = 0;  // lane i: this warp's nodes of height >= Lb + i
+    for (uint32_t ch = 0; ch < 16; ++ch) {
+        const uint32_t node = w0 + ch * 32u + (uint32_t)lane;
+        const uint8_t mt = node < cnt ? s_meta[node] : (uint8_t)kTomb;
+        const uint32_t h = (mt & kTomb) ? 0u : (uint32_t)(mt & kHeightMask);
+        const uint32_t wm = __reduce_max_sync(0xffffffffu, h);
+        for (uint32_t l = Lb; l <= wm; ++l) {
+            const uint32_t b = __ballot_sync(0xffffffffu, h >= l);
+            if ((uint32_t)lane == l - Lb) c += __popc(b);
+        }
+    }
+    s_wcnt[warp][lane] = c;
     __syncthreads();
     if (!s_ok) {
         if (tid == 0) mbar_wait_bounded(&s_bar, 0, a.err);  // let the copy land
         return;
     }
-    // level Lb: live nodes of height >= Lb, in node order
-    const uint32_t b0 = tid * kPer;
-    uint32_t bits = 0, c_lb = 0;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const uint32_t li = b0 + k;
-        const uint8_t mt = li < cnt ? s_meta[li] : (uint8_t)kTomb;
-        const bool in = !(mt & kTomb) && (uint32_t)(mt & kHeightMask) >= Lb;
-        bits |= (in ? 1u : 0u) << k;
-        c_lb += in ? 1u : 0u;
+    // running position of this warp in level Lb + lane
+    const uint32_t lv = Lb + (uint32_t)lane;
+    uint32_t run = 0;
+    if (lv <= H) {
+        run = a.loff[(size_t)lane * ntiles + tile];
+        for (int w = 0; w < warp; ++w) run += s_wcnt[w][lane];
     }
-    uint32_t tot;
-    uint32_t w = block_excl_sum<kThreads>(c_lb, s_tmp, &tot);
-#pragma unroll
-    for (int k = 0; k < kPer; ++k)
-        if ((bits >> k) & 1u) s_la[w++] = b0 + k;
-    __syncthreads();
-    for (uint32_t j = tid; j < tot; j += kThreads) {
-        const uint32_t node = s_la[j];
-        if (s_off[Lb] + j >= s_n[Lb]) {
-            atomicOr(a.err, kErrBounds);
-            break;
-        }
-        const uint32_t g = s_base[Lb] + s_off[Lb] + j;
-        a.lkeys[g] = s_keys[node];
-        a.ldown[g] = ts + node;
-    }
-    // levels above: compact the previous level's list
-    uint32_t* prev = s_la;
-    uint32_t* next = s_lb;
-    uint32_t mprev = tot;
-    for (uint32_t l = Lb + 1; l <= H && mprev > 0; ++l) {
-        const uint32_t per = (mprev + kThreads - 1) / kThreads;
-        const uint32_t jb = min(tid * per, mprev), je = min(jb + per, mprev);
-        uint32_t c = 0;
-        for (uint32_t j = jb; j < je; ++j) c += (s_meta[prev[j] & 0xFFFFu] & kHeightMask) >= l ? 1u : 0u;
-        uint32_t mcur;
-        uint32_t wpos = block_excl_sum<kThreads>(c, s_tmp, &mcur);
-        for (uint32_t j = jb; j < je; ++j) {
-            const uint32_t node = prev[j] & 0xFFFFu;
-            if ((s_meta[node] & kHeightMask) >= l) next[wpos++] = node | (j << 16);
-        }
-        __syncthreads();
-        for (uint32_t j = tid; j < mcur; j += kThreads) {
-            const uint32_t e = next[j];
-            if (s_off[l] + j >= s_n[l]) {
-                atomicOr(a.err, kErrBounds);
-                break;
+    for (uint32_t ch = 0; ch < 16; ++ch) {
+        const uint32_t node = w0 + ch * 32u + (uint32_t)lane;
+        const uint8_t mt = node < cnt ? s_meta[node] : (uint8_t)kTomb;
+        const uint32_t h = (mt & kTomb) ? 0u : (uint32_t)(mt & kHeightMask);
+        const uint32_t wm = __reduce_max_sync(0xffffffffu, h);
+        if (wm < Lb) continue;
+        const uint64_t key = s_keys[node];
+        uint32_t prev_base = 0, prev_mask = 0;
+        for (uint32_t l = Lb; l <= wm; ++l) {
+            const uint32_t b = __ballot_sync(0xffffffffu, h >= l);
+            const uint32_t base = __shfl_sync(0xffffffffu, run, (int)(l - Lb));
+            if (h >= l) {
+                const uint32_t pos = base + __popc(b & lt);
+                if (pos < s_n[l]) {
+                    const uint32_t g = s_base[l] + pos;
+                    a.lkeys[g] = key;
+                    a.ldown[g] = (l == Lb) ? ts + node : prev_base + __popc(prev_mask & lt);
+                } else {
+                    atomicOr(a.err, kErrBounds);
+                }
             }
-            const uint32_t g = s_base[l] + s_off[l] + j;
-            a.lkeys[g] = s_keys[e & 0xFFFFu];
-            a.ldown[g] = s_off[l - 1] + (e >> 16);
+            if ((uint32_t)lane == l - Lb) run += __popc(b);
+            prev_base = base;
+            prev_mask = b;
         }
-        __syncthreads();
-        uint32_t* t = prev;
-        prev = next;
-        next = t;
-        mprev = mcur;
     }
 }
 
@@ -549,14 +545,14 @@ cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s
     (void)epoch;
     (void)num_sms;
     static bool attr_set = false;
-    const int dyn = (kNodes + 2) * 8 + kNodes + 16 + 2 * kNodes * 4;
+    const int dyn = (kNodes + 2) * 8 + kNodes + 16;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_rebuild_write, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
-    k_rebuild_count<<<tiles, kThreads, 0, s>>>(a);
+    k_rebuild_count<<<(tiles + 7) / 8, 256, 0, s>>>(a);
     k_rebuild_scan<<<kLevelSlots - 2, 1024, 0, s>>>(a);
     k_rebuild_write<<<tiles, kThreads, dyn, s>>>(a);
     return cudaGetLastError();

@@ -17,10 +17,11 @@ namespace pi {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;  // 4096
+constexpr int kItems = 8;
+constexpr int kTile = kThreads * kItems;  // kSortTile
 constexpr int kWarps = kThreads / 32;
-constexpr int kWarpSpan = 32 * kItems;    // 512 consecutive elements per warp
+constexpr int kWarpSpan = 32 * kItems;    // 256 consecutive elements per warp
+static_assert(kTile == kSortTile, "tile size shared with the host's descriptor sizing");
 
 __global__ void __launch_bounds__(256) k_pack_hist(const uint8_t* __restrict__ ops,
                                                    const uint64_t* __restrict__ keys, uint32_t n,
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, ui
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_sort_pass(uint32_t j, uint32_t n, SortBuffers sb,
+__global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t n, SortBuffers sb,
                                                         BatchMeta* bm, uint32_t epoch, uint32_t* err) {
     const SortPlan& P = bm->plan;
     if (j >= P.npass) return;
@@ -122,19 +123,32 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(uint32_t j, uint32_t n, 
         pay[k] = v ? src_p[tbase + li] : 0u;
         dig[k] = v ? (uint32_t)((key[k] >> shift) & 255u) : 256u;
     }
-    // Rank within the warp: elements are visited in index order (k, then lane).
+    // Rank within the warp: elements are visited in index order (k, then lane). The
+    // lanes holding the same digit are found with nine ballots (validity + 8 bits);
+    // the lowest of them adds the group's size to the warp's counter for that digit
+    // with one shared-memory atomic, whose old value is the group's base. The
+    // __syncwarp orders the atomics of consecutive items, so equal digits keep index
+    // order (stability); the bases are gathered only after the loop.
     const uint32_t lt = lanemask_lt();
+    uint32_t lower[kItems], old[kItems], lead[kItems];
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
-        uint32_t d = dig[k];
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t lower = __popc(peers & lt);
-        uint32_t base = d < 256u ? s_whist[warp][d] : 0u;
-        rank[k] = base + lower;
-        __syncwarp();
-        if (d < 256u && lower == 0) s_whist[warp][d] = base + __popc(peers);
+        const uint32_t d = dig[k];
+        uint32_t peers = __ballot_sync(0xffffffffu, d < 256u);
+        if (d >= 256u) peers = ~peers;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? m : ~m;
+        }
+        lead[k] = (uint32_t)(__ffs(peers) - 1);
+        lower[k] = __popc(peers & lt);
+        old[k] = 0;
+        if (lower[k] == 0 && d < 256u) old[k] = atomicAdd(&s_whist[warp][d], (uint32_t)__popc(peers));
         __syncwarp();
     }
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) rank[k] = __shfl_sync(0xffffffffu, old[k], (int)lead[k]) + lower[k];
     __syncthreads();
     // Thread tid owns digit tid: tile total and per-warp exclusive prefix.
     uint32_t total = 0;
