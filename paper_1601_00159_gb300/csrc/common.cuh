@@ -12,7 +12,7 @@ constexpr uint64_t kMaxKey = ~0ull;  // reserved key: level and storage sentinel
 constexpr int kLevelSlots = 34;      // per-level arrays are indexed by level 0..33
 constexpr uint8_t kTomb = 0x80;      // meta bit 7: the delete flag F_del (Algorithm 4)
 constexpr uint8_t kHeightMask = 0x3F;
-constexpr uint32_t kSmemTopMax = 4096;  // index entries staged in shared memory
+constexpr uint32_t kSmemTopMax = 2048;  // index entries staged in shared memory
 constexpr uint32_t kPad = 64;           // readable entries past every array's end
 constexpr uint32_t kSortTile = 2048;    // elements per radix-sort tile
 
@@ -186,9 +186,10 @@ __device__ uint32_t lookback(uint64_t* desc, size_t stride, uint32_t tile, uint3
     return excl;
 }
 
-// Per-thread variant that keeps four predecessor reads in flight per round trip
+// Per-thread variant that keeps kWin predecessor reads in flight per round trip
 // (one thread per digit in the radix sort, descriptors strided by `stride`).
-__device__ __forceinline__ uint32_t lookback_sum4(uint64_t* desc, size_t stride, uint32_t tile, uint32_t epoch, uint32_t agg,
+template <int kWin>
+__device__ __forceinline__ uint32_t lookback_sum_win(uint64_t* desc, size_t stride, uint32_t tile, uint32_t epoch, uint32_t agg,
                                   uint32_t* err, bool* ok) {
     const uint64_t tag = (uint64_t)epoch << 32;
     *ok = true;
@@ -200,14 +201,14 @@ __device__ __forceinline__ uint32_t lookback_sum4(uint64_t* desc, size_t stride,
     uint32_t excl = 0, spins = 0;
     int64_t t = (int64_t)tile - 1;
     while (t >= 0) {
-        uint64_t d[4];
+        uint64_t d[kWin];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) d[i] = (t - i >= 0) ? ld_relaxed(desc + (size_t)(t - i) * stride) : (tag | kFlagPrefix);
+        for (int i = 0; i < kWin; ++i) d[i] = (t - i >= 0) ? ld_relaxed(desc + (size_t)(t - i) * stride) : (tag | kFlagPrefix);
         int used = 0;
         bool stop = false, stall = false;
         uint32_t add = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < kWin; ++i) {
             if (stop || stall) continue;
             const uint64_t flag = d[i] & (3ull << 30);
             if ((uint32_t)(d[i] >> 32) != epoch || flag == 0) {

@@ -129,7 +129,7 @@ __device__ __forceinline__ int32_t smem_rank(const uint64_t* K, uint32_t n, uint
     return (int32_t)lo - 1;
 }
 
-__global__ void __launch_bounds__(kThreads) k_descend(DescendArgs a) {
+__global__ void __launch_bounds__(kThreads, 6) k_descend(DescendArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
     uint32_t* s_d = reinterpret_cast<uint32_t*>(s_dyn + (kSmemTopMax + kPad) * sizeof(uint64_t));
@@ -232,7 +232,7 @@ cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
     }
     if (a.n == 0) return cudaSuccess;
     uint32_t warps_needed = (a.n + 31) / 32;
-    uint32_t blocks = (warps_needed + kWarps - 1) / kWarps, cap = (uint32_t)num_sms * 4u;
+    uint32_t blocks = (warps_needed + kWarps - 1) / kWarps, cap = (uint32_t)num_sms * 6u;
     int grid = (int)(blocks < cap ? blocks : cap);
     k_descend<<<grid, kThreads, dyn, s>>>(a);
     return cudaGetLastError();

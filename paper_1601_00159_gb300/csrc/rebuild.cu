@@ -309,12 +309,25 @@ __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
     if (threadIdx.x == 0 && s_carry != m->n[l]) atomicOr(a.err, kErrBounds);  // counts disagree
 }
 
+// Byte-wise (SIMD within a register) helpers: a meta word holds four nodes.
+__device__ __forceinline__ uint32_t live_heights(uint32_t metaw) {
+    // bytes with the delete flag (bit 7) clear keep their height, the others become 0
+    return metaw & __vcmpltu4(metaw, 0x80808080u);
+}
+__device__ __forceinline__ uint32_t bytes_ge(uint32_t hw, uint32_t l) {  // 0xFF per byte >= l
+    return __vcmpgeu4(hw, l * 0x01010101u);
+}
+
+constexpr int kStage = 128;  // entries staged per warp per round (4 nodes x 32 lanes)
+
 __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);     // kNodes + 2
     uint8_t* s_meta = s_dyn + (kNodes + 2) * sizeof(uint64_t);  // kNodes + 16
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_wcnt[8][32];
+    __shared__ uint64_t s_sk[8][kStage];  // per-warp staging of one round's entries
+    __shared__ uint32_t s_sd[8][kStage];
     __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
     __shared__ int s_ok;
 
@@ -344,19 +357,36 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     }
     __syncthreads();
     if (!mbar_wait_bounded(&s_bar, 0, a.err)) s_ok = 0;
-    // this warp's nodes: [w0, w0 + 512), 16 chunks of 32 (lane = node)
+    // Warp w owns nodes [w0, w0 + 512). Phase 1: its node count per level, lane i
+    // holding level Lb + i; lane t reads nodes [w0 + 16 t, w0 + 16 t + 16).
     const uint32_t w0 = (uint32_t)warp * 512u;
-    const uint32_t lt = lanemask_lt();
-    uint32_t c = 0;  // lane i: this warp's nodes of height >= Lb + i
-    for (uint32_t ch = 0; ch < 16; ++ch) {
-        const uint32_t node = w0 + ch * 32u + (uint32_t)lane;
-        const uint8_t mt = node < cnt ? s_meta[node] : (uint8_t)kTomb;
-        const uint32_t h = (mt & kTomb) ? 0u : (uint32_t)(mt & kHeightMask);
-        const uint32_t wm = __reduce_max_sync(0xffffffffu, h);
-        for (uint32_t l = Lb; l <= wm; ++l) {
-            const uint32_t b = __ballot_sync(0xffffffffu, h >= l);
-            if ((uint32_t)lane == l - Lb) c += __popc(b);
+    uint32_t hw[4];
+    {
+        const uint32_t nb = w0 + (uint32_t)lane * 16u;
+        const uint4 v = *reinterpret_cast<const uint4*>(s_meta + nb);
+        const uint32_t raw[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t h = live_heights(raw[k]);
+            // nodes past the end of the storage layer count as absent
+            const uint32_t first = nb + 4u * k;
+            if (first + 4u > cnt) {
+                const uint32_t keep = first >= cnt ? 0u : (cnt - first);  // 0..3 bytes
+                h &= keep ? (0xFFFFFFFFu >> (8u * (4u - keep))) : 0u;
+            }
+            hw[k] = h;
         }
+    }
+    uint32_t hmax = __vmaxu4(__vmaxu4(hw[0], hw[1]), __vmaxu4(hw[2], hw[3]));
+    hmax = max(max(hmax & 0xFFu, (hmax >> 8) & 0xFFu), max((hmax >> 16) & 0xFFu, hmax >> 24));
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, hmax);
+    uint32_t c = 0;
+    for (uint32_t l = Lb; l <= wm; ++l) {
+        uint32_t n_l = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) n_l += __popc(bytes_ge(hw[k], l));
+        const uint32_t tot = __reduce_add_sync(0xffffffffu, n_l >> 3);
+        if ((uint32_t)lane == l - Lb) c = tot;
     }
     s_wcnt[warp][lane] = c;
     __syncthreads();
@@ -365,36 +395,76 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
         return;
     }
     // running position of this warp in level Lb + lane
-    const uint32_t lv = Lb + (uint32_t)lane;
     uint32_t run = 0;
-    if (lv <= H) {
+    if (Lb + (uint32_t)lane <= H) {
         run = a.loff[(size_t)lane * ntiles + tile];
         for (int w = 0; w < warp; ++w) run += s_wcnt[w][lane];
     }
-    for (uint32_t ch = 0; ch < 16; ++ch) {
-        const uint32_t node = w0 + ch * 32u + (uint32_t)lane;
-        const uint8_t mt = node < cnt ? s_meta[node] : (uint8_t)kTomb;
-        const uint32_t h = (mt & kTomb) ? 0u : (uint32_t)(mt & kHeightMask);
-        const uint32_t wm = __reduce_max_sync(0xffffffffu, h);
-        if (wm < Lb) continue;
-        const uint64_t key = s_keys[node];
-        uint32_t prev_base = 0, prev_mask = 0;
-        for (uint32_t l = Lb; l <= wm; ++l) {
-            const uint32_t b = __ballot_sync(0xffffffffu, h >= l);
+    // Phase 2: four rounds of 128 nodes; lane t holds nodes w0 + 128 r + 4 t .. + 3
+    // (one meta word). Per level, a warp prefix sum of the lanes' counts places the
+    // entries; they are staged in shared memory and written out coalesced.
+    uint64_t* stk = s_sk[warp];
+    uint32_t* std_ = s_sd[warp];
+    const uint32_t lt = lanemask_lt();
+    (void)lt;
+    for (uint32_t rnd = 0; rnd < 4; ++rnd) {
+        const uint32_t nb = w0 + rnd * 128u + (uint32_t)lane * 4u;
+        uint32_t h = live_heights(*reinterpret_cast<const uint32_t*>(s_meta + nb));
+        if (nb + 4u > cnt) {
+            const uint32_t keep = nb >= cnt ? 0u : (cnt - nb);
+            h &= keep ? (0xFFFFFFFFu >> (8u * (4u - keep))) : 0u;
+        }
+        uint32_t hm = __vmaxu4(h, h >> 16);
+        hm = max(hm & 0xFFu, (hm >> 8) & 0xFFu);
+        const uint32_t rm = __reduce_max_sync(0xffffffffu, hm);
+        uint32_t prev_mask = 0, prev_first = 0;
+        for (uint32_t l = Lb; l <= rm; ++l) {
+            const uint32_t mk = bytes_ge(h, l);
+            const uint32_t cl = __popc(mk) >> 3;
+            uint32_t incl = cl;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t excl = incl - cl;
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
             const uint32_t base = __shfl_sync(0xffffffffu, run, (int)(l - Lb));
-            if (h >= l) {
-                const uint32_t pos = base + __popc(b & lt);
+            // stage this lane's entries of level l (in node order)
+            uint32_t j = 0;
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+                if ((mk >> (8 * bb)) & 1u) {
+                    const uint32_t node = nb + (uint32_t)bb;
+                    uint32_t down;
+                    if (l == Lb) {
+                        down = ts + node;
+                    } else {
+                        // position of the node in level l - 1: that level's first slot
+                        // for this lane plus the lane's level-(l-1) nodes before it
+                        const uint32_t below = bb ? (prev_mask & ((1u << (8 * bb)) - 1u)) : 0u;
+                        down = prev_first + (__popc(below) >> 3);
+                    }
+                    stk[excl + j] = s_keys[node];
+                    std_[excl + j] = down;
+                    ++j;
+                }
+            }
+            __syncwarp();
+            for (uint32_t e = (uint32_t)lane; e < total; e += 32u) {
+                const uint32_t pos = base + e;
                 if (pos < s_n[l]) {
                     const uint32_t g = s_base[l] + pos;
-                    a.lkeys[g] = key;
-                    a.ldown[g] = (l == Lb) ? ts + node : prev_base + __popc(prev_mask & lt);
+                    a.lkeys[g] = stk[e];
+                    a.ldown[g] = std_[e];
                 } else {
                     atomicOr(a.err, kErrBounds);
                 }
             }
-            if ((uint32_t)lane == l - Lb) run += __popc(b);
-            prev_base = base;
-            prev_mask = b;
+            __syncwarp();
+            if ((uint32_t)lane == l - Lb) run += total;
+            prev_mask = mk;
+            prev_first = base + excl;
         }
     }
 }

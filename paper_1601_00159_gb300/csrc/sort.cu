@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
         total += c;
     }
     bool ok;
-    uint32_t excl = lookback_sum4(sb.desc + tid, 256, tile, epoch, total, err, &ok);
+    uint32_t excl = lookback_sum_win<8>(sb.desc + tid, 256, tile, epoch, total, err, &ok);
     if (!ok) s_ok = 0;
     s_gbase[tid] = sb.dofs[P.digit[j] * 256 + tid] + excl;
     s_tstart[tid] = block_excl_sum<kThreads>(total, s_tmp, nullptr);
