@@ -14,7 +14,12 @@
 //  * the LAST query of each run is the run's only owner: it writes the run's final
 //    state to the storage node (value, delete flag), or emits a new node when the key
 //    is not in the storage layer and ends up present (Algorithm 4, insertNode).
-// Two decoupled look-backs carry the max-scan and the new-node count across tiles.
+//
+// The max-scan is split across kernels so no tile ever waits on another: the descent
+// already walks the sorted batch and leaves each 2048-query tile's maximum e in
+// tile_max (one atomicMax per warp); k_apply_scan turns those into exclusive tile
+// prefixes; k_apply is then fully data-parallel. New nodes are staged per tile and
+// packed in key order by k_new_scan + k_new_pack.
 
 #include "common.cuh"
 
@@ -22,10 +27,8 @@ namespace pi {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 8;
-constexpr int kTile = kThreads * kItems;  // 2048 sorted queries per tile
+constexpr int kItems = kApplyTile / kThreads;  // 8 sorted queries per thread
 constexpr uint32_t kSeqMask = (1u << 30) - 1u;
-constexpr uint32_t kCtrApply = 8;
 
 __device__ __forceinline__ void store_result(pi_result_t* res, uint32_t seq, uint64_t v, uint32_t st) {
     uint4 w;
@@ -36,13 +39,31 @@ __device__ __forceinline__ void store_result(pi_result_t* res, uint32_t seq, uin
     *reinterpret_cast<uint4*>(res + seq) = w;
 }
 
-__global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a, uint32_t epoch_max, uint32_t epoch_cnt) {
+// Exclusive max over tiles of tile_max -> tile_pref (one CTA).
+__global__ void __launch_bounds__(1024) k_apply_scan(ApplyArgs a) {
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_carry;
+    if (block_sees_error(&a.m->error)) return;
+    const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < ntiles; b0 += 1024) {
+        const uint32_t i = b0 + threadIdx.x;
+        const uint32_t v = i < ntiles ? a.tile_max[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_max<1024>(v, s_tmp, &tot);
+        if (i < ntiles) a.tile_pref[i] = max(s_carry, ex);
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = max(s_carry, tot);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
     __shared__ uint32_t s_tmp[33];
     __shared__ int32_t s_delta[kLevelSlots];
     __shared__ int32_t s_tomb;
-    __shared__ uint32_t s_changes, s_dirty, s_new_total;
-    __shared__ uint32_t s_tile, s_excl_max, s_excl_cnt;
-    __shared__ int s_ok;
+    __shared__ uint32_t s_changes, s_dirty;
 
     const int tid = threadIdx.x;
     if (block_sees_error(&a.m->error)) return;
@@ -51,142 +72,108 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a, uint32_t epoch_
     const uint32_t cur = a.m->cur;
     uint64_t* SV = a.st.vals[cur];
     uint8_t* SM = a.st.meta[cur];
-    const uint32_t ntiles = (n + kTile - 1) / kTile;
-    uint64_t* desc_max = a.desc;
-    uint64_t* desc_cnt = a.desc + ntiles;
-
+    const uint32_t tile = blockIdx.x;
     if (tid < kLevelSlots) s_delta[tid] = 0;
     if (tid == 0) {
         s_tomb = 0;
         s_changes = 0;
         s_dirty = 0;
-        s_new_total = 0;
-        s_ok = 1;
     }
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_tile = atomicAdd(&a.bm->tile_ctr[kCtrApply], 1u);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const uint32_t base = tile * kTile + tid * kItems;
+    const uint32_t base = tile * kApplyTile + tid * kItems;
 
-        uint64_t key[kItems];
-        uint32_t pay[kItems];
-        uint32_t e[kItems];
+    uint64_t key[kItems];
+    uint32_t pay[kItems];
+    uint32_t e[kItems];
 #pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            const uint32_t i = base + k;
-            key[k] = i < qv ? a.sk[i] : kMaxKey;
-            pay[k] = i < n ? a.sp[i] : 0u;
-        }
-        const uint64_t kprev = (base > 0 && base - 1 < qv) ? a.sk[base - 1] : kMaxKey;
-        const uint64_t knext = (base + kItems < qv) ? a.sk[base + kItems] : kMaxKey;
-        uint32_t agg = 0;
+    for (int k = 0; k < kItems; ++k) {
+        const uint32_t i = base + k;
+        key[k] = i < qv ? a.sk[i] : kMaxKey;
+        pay[k] = i < n ? a.sp[i] : 0u;
+    }
+    const uint64_t kprev = (base > 0 && base - 1 < qv) ? a.sk[base - 1] : kMaxKey;
+    const uint64_t knext = (base + kItems < qv) ? a.sk[base + kItems] : kMaxKey;
+    uint32_t agg = 0;
 #pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            const uint32_t i = base + k;
-            const bool valid = i < qv;
-            const uint64_t prev = k ? key[k - 1] : kprev;
-            const bool head = valid && (i == 0 || key[k] != prev);
-            const uint32_t op = pay[k] >> 30;
-            const bool write = valid && (op == 1u || op == 2u);
-            e[k] = write ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
-            agg = max(agg, e[k]);
+    for (int k = 0; k < kItems; ++k) {
+        const uint32_t i = base + k;
+        const bool valid = i < qv;
+        const uint64_t prev = k ? key[k - 1] : kprev;
+        const bool head = valid && (i == 0 || key[k] != prev);
+        const uint32_t op = pay[k] >> 30;
+        const bool write = valid && (op == 1u || op == 2u);
+        e[k] = write ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
+        agg = max(agg, e[k]);
+    }
+    const uint32_t texcl = block_excl_max<kThreads>(agg, s_tmp, nullptr);
+    uint32_t M = max(a.tile_pref[tile], texcl);
+    uint32_t new_here = 0, new_mask = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint32_t i = base + k;
+        const uint32_t mex = M;
+        const uint32_t minc = max(M, e[k]);
+        M = minc;
+        e[k] = minc;  // keep the inclusive value for the new-node pass
+        if (i >= n) continue;
+        const uint32_t seq = pay[k] & kSeqMask;
+        if (i >= qv) {
+            store_result(a.results, seq, 0ull, PI_R_INVALID);
+            continue;
         }
-        uint32_t tile_max;
-        const uint32_t texcl = block_excl_max<kThreads>(agg, s_tmp, &tile_max);
-        if (tid < 32) {
-            bool ok;
-            const uint32_t ex = lookback_warp<true>(desc_max, tile, epoch_max, tile_max, a.err, &ok);
-            if (tid == 0) {
-                s_excl_max = ex;
-                if (!ok) s_ok = 0;
-            }
+        const uint64_t prev = k ? key[k - 1] : kprev;
+        const bool head = (i == 0 || key[k] != prev);
+        const uint8_t fl = a.flags[i];
+        const bool exists = fl & 1u, live0 = (fl & 2u) != 0;
+        bool pl;
+        uint64_t pv;
+        if (!head && (mex & 1u)) {
+            const uint32_t j = (mex - 3u) >> 1;
+            const uint32_t pj = a.sp[j];
+            pl = (pj >> 30) == 1u;
+            pv = pl ? a.uvals[pj & kSeqMask] : 0ull;
+        } else {
+            pl = live0;
+            pv = live0 ? a.val0[i] : 0ull;
         }
-        __syncthreads();
-        if (!s_ok) break;
+        store_result(a.results, seq, pv, pl ? PI_R_PRESENT : PI_R_ABSENT);
 
-        uint32_t M = max(s_excl_max, texcl);
-        uint32_t new_here = 0;
-        uint32_t new_mask = 0;
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            const uint32_t i = base + k;
-            const uint32_t mex = M;
-            const uint32_t minc = max(M, e[k]);
-            M = minc;
-            e[k] = minc;  // keep the inclusive value for the new-node pass
-            if (i >= n) continue;
-            const uint32_t seq = pay[k] & kSeqMask;
-            if (i >= qv) {
-                store_result(a.results, seq, 0ull, PI_R_INVALID);
-                continue;
-            }
-            const uint64_t prev = k ? key[k - 1] : kprev;
-            const bool head = (i == 0 || key[k] != prev);
-            const uint8_t fl = a.flags[i];
-            const bool exists = fl & 1u, live0 = (fl & 2u) != 0;
-            bool pl;
-            uint64_t pv;
-            if (!head && (mex & 1u)) {
-                const uint32_t j = (mex - 3u) >> 1;
-                const uint32_t pj = a.sp[j];
-                pl = (pj >> 30) == 1u;
-                pv = pl ? a.uvals[pj & kSeqMask] : 0ull;
+        const uint64_t next = (k + 1 < kItems) ? key[k + 1] : knext;
+        const bool last = next != key[k];
+        if (!last || !(minc & 1u)) continue;  // not the owner, or the run never writes
+        const uint32_t jw = (minc - 3u) >> 1;
+        const uint32_t pw = (jw == i) ? pay[k] : a.sp[jw];
+        const bool fin_live = (pw >> 30) == 1u;
+        if (exists) {
+            const uint32_t r = a.loc[i] - 1u;
+            const uint8_t mt = SM[r];
+            const uint32_t h = mt & kHeightMask;
+            if (fin_live) {
+                SV[r] = a.uvals[pw & kSeqMask];
+                SM[r] = (uint8_t)h;
             } else {
-                pl = live0;
-                pv = live0 ? a.val0[i] : 0ull;
+                SM[r] = (uint8_t)(h | kTomb);
             }
-            store_result(a.results, seq, pv, pl ? PI_R_PRESENT : PI_R_ABSENT);
-
-            const uint64_t next = (k + 1 < kItems) ? key[k + 1] : knext;
-            const bool last = next != key[k];
-            if (!last || !(minc & 1u)) continue;  // not the owner, or the run never writes
-            const uint32_t jw = (minc - 3u) >> 1;
-            const uint32_t pw = (jw == i) ? pay[k] : a.sp[jw];
-            const bool fin_live = (pw >> 30) == 1u;
-            if (exists) {
-                const uint32_t r = a.loc[i] - 1u;
-                const uint8_t mt = SM[r];
-                const uint32_t h = mt & kHeightMask;
-                if (fin_live) {
-                    SV[r] = a.uvals[pw & kSeqMask];
-                    SM[r] = (uint8_t)h;
-                } else {
-                    SM[r] = (uint8_t)(h | kTomb);
+            if (fin_live != live0) {
+                atomicAdd(&s_tomb, fin_live ? -1 : 1);
+                atomicAdd(&s_changes, 1u);
+                atomicAdd(&s_delta[1], fin_live ? 1 : -1);
+                for (uint32_t l = 2; l <= h; ++l) {
+                    atomicAdd(&s_delta[l], fin_live ? 1 : -1);
+                    // the rebuild's per-tile count of the node's 4096-node tile
+                    atomicAdd(&a.lcnt[(size_t)(l - 2) * a.lstride + (r >> 12)], fin_live ? 1u : 0xFFFFFFFFu);
                 }
-                if (fin_live != live0) {
-                    atomicAdd(&s_tomb, fin_live ? -1 : 1);
-                    atomicAdd(&s_changes, 1u);
-                    atomicAdd(&s_delta[1], fin_live ? 1 : -1);
-                    for (uint32_t l = 2; l <= h; ++l) {
-                        atomicAdd(&s_delta[l], fin_live ? 1 : -1);
-                        // the rebuild's per-tile count of the node's 4096-node tile
-                        atomicAdd(&a.lcnt[(size_t)(l - 2) * a.lstride + (r >> 12)], fin_live ? 1u : 0xFFFFFFFFu);
-                    }
-                    if (h >= 2) s_dirty = 1;
-                }
-            } else if (fin_live) {
-                new_here++;
-                new_mask |= 1u << k;
+                if (h >= 2) s_dirty = 1;
             }
+        } else if (fin_live) {
+            new_here++;
+            new_mask |= 1u << k;
         }
-        // New nodes: compact slots in key order.
-        uint32_t tile_new;
-        const uint32_t nexcl = block_excl_sum<kThreads>(new_here, s_tmp, &tile_new);
-        if (tid < 32) {
-            bool ok;
-            const uint32_t ex = lookback_warp<false>(desc_cnt, tile, epoch_cnt, tile_new, a.err, &ok);
-            if (tid == 0) {
-                s_excl_cnt = ex;
-                if (!ok) s_ok = 0;
-                s_new_total += tile_new;
-            }
-        }
-        __syncthreads();
-        if (!s_ok) break;
-        uint32_t slot = s_excl_cnt + nexcl;
+    }
+    // New nodes: staged in this tile's slice of the staging arrays, in key order.
+    uint32_t tile_new;
+    uint32_t slot = block_excl_sum<kThreads>(new_here, s_tmp, &tile_new);
+    if (new_mask) {
+        const uint32_t so = tile * kApplyTile;
 #pragma unroll
         for (int k = 0; k < kItems; ++k) {
             if (!(new_mask & (1u << k))) continue;
@@ -194,10 +181,10 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a, uint32_t epoch_
             const uint32_t jw = (e[k] - 3u) >> 1;
             const uint32_t pw = (jw == i) ? pay[k] : a.sp[jw];
             const uint32_t h = tower_height(key[k], a.hp);
-            a.nn.keys[slot] = key[k];
-            a.nn.vals[slot] = a.uvals[pw & kSeqMask];
-            a.nn.loc[slot] = a.loc[i];
-            a.nn.height[slot] = (uint8_t)h;
+            a.stage.keys[so + slot] = key[k];
+            a.stage.vals[so + slot] = a.uvals[pw & kSeqMask];
+            a.stage.loc[so + slot] = a.loc[i];
+            a.stage.height[so + slot] = (uint8_t)h;
             ++slot;
             atomicAdd(&s_changes, 1u);
             atomicAdd(&s_delta[1], 1);
@@ -206,24 +193,63 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a, uint32_t epoch_
         }
     }
     __syncthreads();
+    if (tid == 0) a.tile_new[tile] = tile_new;
     if (tid < kLevelSlots && s_delta[tid]) atomicAdd(&a.bm->delta[tid], s_delta[tid]);
     if (tid == 0) {
         if (s_tomb) atomicAdd(&a.bm->tomb_delta, s_tomb);
         if (s_changes) atomicAdd(&a.bm->changes, s_changes);
         if (s_dirty) atomicOr(&a.bm->index_dirty, 1u);
-        if (s_new_total) atomicAdd(&a.bm->new_count, s_new_total);
+    }
+}
+
+// Exclusive sum of the per-tile new-node counts (one CTA); total -> bm->new_count.
+__global__ void __launch_bounds__(1024) k_new_scan(ApplyArgs a) {
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_carry;
+    if (block_sees_error(&a.m->error)) return;
+    const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < ntiles; b0 += 1024) {
+        const uint32_t i = b0 + threadIdx.x;
+        const uint32_t v = i < ntiles ? a.tile_new[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_sum<1024>(v, s_tmp, &tot);
+        if (i < ntiles) a.tile_pref[i] = s_carry + ex;  // tile_pref is free again
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.bm->new_count = s_carry;
+}
+
+// Packs each tile's staged new nodes to their place in key order.
+__global__ void __launch_bounds__(kThreads) k_new_pack(ApplyArgs a) {
+    if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
+    const uint32_t tile = blockIdx.x;
+    const uint32_t c = a.tile_new[tile];
+    if (c == 0) return;
+    const uint32_t dst = a.tile_pref[tile];
+    const uint32_t so = tile * kApplyTile;
+    for (uint32_t j = threadIdx.x; j < c; j += kThreads) {
+        a.nn.keys[dst + j] = a.stage.keys[so + j];
+        a.nn.vals[dst + j] = a.stage.vals[so + j];
+        a.nn.loc[dst + j] = a.stage.loc[so + j];
+        a.nn.height[dst + j] = a.stage.height[so + j];
     }
 }
 
 }  // namespace
 
 cudaError_t launch_apply(const ApplyArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
+    (void)epoch;
+    (void)num_sms;
     if (a.n == 0) return cudaSuccess;
-    const uint32_t tiles = (a.n + kTile - 1) / kTile;
-    const uint32_t cap = (uint32_t)num_sms * 4u;
-    const int grid = (int)(tiles < cap ? tiles : cap);
-    const uint32_t e1 = ++epoch, e2 = ++epoch;
-    k_apply<<<grid, kThreads, 0, s>>>(a, e1, e2);
+    const uint32_t tiles = (a.n + kApplyTile - 1) / kApplyTile;
+    k_apply_scan<<<1, 1024, 0, s>>>(a);
+    k_apply<<<tiles, kThreads, 0, s>>>(a);
+    k_new_scan<<<1, 1024, 0, s>>>(a);
+    k_new_pack<<<tiles, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

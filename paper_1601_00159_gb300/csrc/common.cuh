@@ -15,6 +15,7 @@ constexpr uint8_t kHeightMask = 0x3F;
 constexpr uint32_t kSmemTopMax = 2048;  // index entries staged in shared memory
 constexpr uint32_t kPad = 64;           // readable entries past every array's end
 constexpr uint32_t kSortTile = 2048;    // elements per radix-sort tile
+constexpr uint32_t kApplyTile = 2048;   // sorted queries per apply tile
 
 // Sticky error bits in DevMeta::error.
 constexpr uint32_t kErrTimeout = 1u;  // a bounded wait gave up
@@ -414,6 +415,9 @@ struct SortBuffers {
     uint32_t* b_p;
     uint32_t* dofs;  // [8][256] digit offsets
     uint64_t* desc;  // [tiles][256] look-back descriptors
+    uint32_t* tile_max;  // per-apply-tile max run marker, cleared by the plan kernel (may be null)
+    uint32_t* tcnt;      // [tiles][256] per-tile digit counts of the current pass
+    uint32_t* toff;      // [tiles][256] per-tile digit offsets of the current pass
 };
 
 // Radix sort of (key, payload) pairs: result in a_k / a_p, stable, by key.
@@ -423,6 +427,8 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
 
 struct DescendArgs {
     const uint64_t* sk;  // sorted keys
+    const uint32_t* sp;  // sorted payload (op << 30 | arrival index)
+    uint32_t* tile_max;  // per-apply-tile max of the run markers e_i (atomicMax)
     const DevMeta* m;
     const BatchMeta* bm;
     const uint64_t* lkeys;
@@ -448,7 +454,11 @@ struct ApplyArgs {
     NewNodes nn;
     DevMeta* m;
     BatchMeta* bm;
-    uint64_t* desc;  // 2 * tiles words
+    uint64_t* desc;  // unused
+    uint32_t* tile_max;   // per-tile max run marker (from the descent)
+    uint32_t* tile_pref;  // per-tile exclusive prefix (max, then reused for new-node sums)
+    uint32_t* tile_new;   // per-tile new-node count
+    NewNodes stage;       // per-tile staging of new nodes (kApplyTile slots per tile)
     uint32_t* lcnt;  // per-level per-tile live counts (see RebuildArgs)
     uint32_t lstride;
     uint32_t n;

@@ -178,6 +178,16 @@ __global__ void __launch_bounds__(kThreads, 6) k_descend(DescendArgs a) {
         const uint64_t qp = __shfl_up_sync(kFull, q, 1);
         const bool leader = active && (lane == 0 || qp != q);
         const uint32_t lead = __ballot_sync(kFull, leader);
+        {
+            // run markers for the ownership scan: e = 2i+3 for a write, 2i+2 for a run
+            // head, else 0; the tile's maximum feeds the scan across apply tiles
+            const uint32_t op = active ? (a.sp[i] >> 30) : 0u;
+            const uint64_t before = (lane == 0) ? (i > 0 ? a.sk[i - 1] : kMaxKey) : qp;
+            const bool head = active && (i == 0 || before != q);
+            const uint32_t e = (active && (op == 1u || op == 2u)) ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
+            const uint32_t wmax = __reduce_max_sync(kFull, e);
+            if (lane == 0 && wmax) atomicMax(&a.tile_max[i / kApplyTile], wmax);
+        }
         uint32_t lo = 0;
         int32_t r = -1;
         uint32_t dn = 0;

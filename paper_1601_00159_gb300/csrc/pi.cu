@@ -31,6 +31,12 @@ struct Scratch {
     uint8_t* flags = nullptr;
     uint64_t* val0 = nullptr;
     NewNodes nn{};
+    NewNodes stage{};
+    uint32_t* tile_max = nullptr;
+    uint32_t* tile_pref = nullptr;
+    uint32_t* tile_new = nullptr;
+    uint32_t* tcnt = nullptr;  // radix sort: per-tile digit counts
+    uint32_t* toff = nullptr;  // radix sort: per-tile digit offsets
 };
 
 struct Staging {
@@ -119,7 +125,7 @@ int map_cuda(cudaError_t e) {
 
 // Look-back descriptors needed for q queries and a storage capacity of s nodes.
 uint64_t desc_need(uint64_t q, uint64_t s) {
-    uint64_t a = ((q + kSortTile - 1) / kSortTile) * 256;  // sort passes
+    uint64_t a = 0;                                    // (the sort needs none)
     uint64_t b = 2 * ((q + 2047) / 2048);    // apply
     uint64_t c = (s / 4096 + 2) * 32;        // rebuild (and merge, export)
     uint64_t m = a > b ? a : b;
@@ -168,6 +174,9 @@ void free_scratch(Scratch& s) {
     dfree(s.in_k); dfree(s.in_p); dfree(s.a_k); dfree(s.a_p); dfree(s.b_k); dfree(s.b_p);
     dfree(s.loc); dfree(s.flags); dfree(s.val0);
     dfree(s.nn.keys); dfree(s.nn.vals); dfree(s.nn.loc); dfree(s.nn.height);
+    dfree(s.stage.keys); dfree(s.stage.vals); dfree(s.stage.loc); dfree(s.stage.height);
+    dfree(s.tile_max); dfree(s.tile_pref); dfree(s.tile_new);
+    dfree(s.tcnt); dfree(s.toff);
     s.cap = 0;
 }
 
@@ -181,6 +190,13 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     PI_TRY(dalloc(&s.loc, c)); PI_TRY(dalloc(&s.flags, c)); PI_TRY(dalloc(&s.val0, c));
     PI_TRY(dalloc(&s.nn.keys, c)); PI_TRY(dalloc(&s.nn.vals, c));
     PI_TRY(dalloc(&s.nn.loc, c)); PI_TRY(dalloc(&s.nn.height, c));
+    const uint64_t tiles = (q + kApplyTile - 1) / kApplyTile + 1;
+    const uint64_t cs = tiles * kApplyTile;
+    PI_TRY(dalloc(&s.stage.keys, cs)); PI_TRY(dalloc(&s.stage.vals, cs));
+    PI_TRY(dalloc(&s.stage.loc, cs)); PI_TRY(dalloc(&s.stage.height, cs));
+    PI_TRY(dalloc(&s.tile_max, tiles)); PI_TRY(dalloc(&s.tile_pref, tiles)); PI_TRY(dalloc(&s.tile_new, tiles));
+    const uint64_t stiles = (q + kSortTile - 1) / kSortTile + 1;
+    PI_TRY(dalloc(&s.tcnt, stiles * 256)); PI_TRY(dalloc(&s.toff, stiles * 256));
 #undef PI_TRY
     s.cap = q;
     return cudaSuccess;
@@ -258,6 +274,9 @@ SortBuffers sort_buffers(pi_index* x, const Scratch& s) {
     sb.in_k = s.in_k; sb.in_p = s.in_p; sb.a_k = s.a_k; sb.a_p = s.a_p; sb.b_k = s.b_k; sb.b_p = s.b_p;
     sb.dofs = x->d_dofs;
     sb.desc = x->desc;
+    sb.tile_max = s.tile_max;
+    sb.tcnt = s.tcnt;
+    sb.toff = s.toff;
     return sb;
 }
 
@@ -558,6 +577,8 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
         return map_cuda(e);
     DescendArgs da{};
     da.sk = x->sc.a_k;
+    da.sp = x->sc.a_p;
+    da.tile_max = x->sc.tile_max;
     da.m = x->d_meta;
     da.bm = x->d_bm;
     da.lkeys = x->lkeys;
@@ -584,6 +605,10 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
     aa.m = x->d_meta;
     aa.bm = x->d_bm;
     aa.desc = x->desc;
+    aa.tile_max = x->sc.tile_max;
+    aa.tile_pref = x->sc.tile_pref;
+    aa.tile_new = x->sc.tile_new;
+    aa.stage = x->sc.stage;
     aa.lcnt = x->lcnt;
     aa.lstride = x->lstride;
     aa.n = (uint32_t)n;

@@ -309,25 +309,31 @@ __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
     if (threadIdx.x == 0 && s_carry != m->n[l]) atomicOr(a.err, kErrBounds);  // counts disagree
 }
 
-// Byte-wise (SIMD within a register) helpers: a meta word holds four nodes.
+// Byte-wise arithmetic on a meta word holding four nodes (height in bits 0-5, delete
+// flag in bit 7). live_heights clears the bytes of delete-flagged nodes; members(h, l)
+// leaves bit 7 set in exactly the bytes whose height is >= l: 0x80 + h - l is >= 0x80
+// iff h >= l, and never borrows from the next byte because h - l >= -33.
 __device__ __forceinline__ uint32_t live_heights(uint32_t metaw) {
-    // bytes with the delete flag (bit 7) clear keep their height, the others become 0
-    return metaw & __vcmpltu4(metaw, 0x80808080u);
+    const uint32_t t = (metaw >> 7) & 0x01010101u;  // 1 in the low bit of flagged bytes
+    return metaw & ~(t * 0xFFu);
 }
-__device__ __forceinline__ uint32_t bytes_ge(uint32_t hw, uint32_t l) {  // 0xFF per byte >= l
-    return __vcmpgeu4(hw, l * 0x01010101u);
+__device__ __forceinline__ uint32_t members(uint32_t hw, uint32_t l) {
+    return ((hw | 0x80808080u) - l * 0x01010101u) & 0x80808080u;
 }
 
-constexpr int kStage = 128;  // entries staged per warp per round (4 nodes x 32 lanes)
+constexpr int kList = 1024;  // per-warp list capacity (the warp owns 512 nodes)
+constexpr uint32_t kKeyBytes = (kNodes + 2) * sizeof(uint64_t);
+constexpr uint32_t kMetaBytes = kNodes + 16;
+constexpr uint32_t kBufBytes = kKeyBytes + kMetaBytes;  // one tile: keys then meta
 
+// Persistent CTAs, tiles assigned statically (tile = blockIdx.x + k * gridDim.x); two
+// shared-memory buffers, so the TMA bulk copy of the CTA's next tile lands while the
+// current one is processed.
 __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
-    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);     // kNodes + 2
-    uint8_t* s_meta = s_dyn + (kNodes + 2) * sizeof(uint64_t);  // kNodes + 16
-    __shared__ __align__(8) uint64_t s_bar;
+    uint32_t* s_list = reinterpret_cast<uint32_t*>(s_dyn + 2 * kBufBytes);  // 8 warps x kList
+    __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_wcnt[8][32];
-    __shared__ uint64_t s_sk[8][kStage];  // per-warp staging of one round's entries
-    __shared__ uint32_t s_sd[8][kStage];
     __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
     __shared__ int s_ok;
 
@@ -338,134 +344,144 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     const uint32_t H = m->H, Lb = m->Lb, size = m->size, cur = m->cur;
     if (H < Lb || size == 0) return;
     const uint32_t ntiles = (size + kNodes - 1) / kNodes;
-    const uint32_t tile = blockIdx.x;
-    if (tile >= ntiles) return;
-    const uint32_t ts = tile * kNodes;
-    const uint32_t cnt = min((uint32_t)kNodes, size - ts);
+    if (blockIdx.x >= ntiles) return;
+    const uint64_t* SK = a.st.keys[cur];
+    const uint8_t* SMt = a.st.meta[cur];
+    auto issue = [&](uint32_t t, uint32_t b) {  // thread 0 only
+        const uint32_t c = min((uint32_t)kNodes, size - t * kNodes);
+        const uint32_t bk = ((c * 8u + 15u) / 16u) * 16u;
+        const uint32_t bm_ = ((c + 15u) / 16u) * 16u;
+        uint8_t* buf = s_dyn + b * kBufBytes;
+        mbar_arrive_expect_tx(&s_bar[b], bk + bm_);
+        bulk_g2s(buf, SK + (size_t)t * kNodes, bk, &s_bar[b]);
+        bulk_g2s(buf + kKeyBytes, SMt + (size_t)t * kNodes, bm_, &s_bar[b]);
+    };
     if (tid == 0) {
         s_ok = 1;
-        mbar_init(&s_bar, 1);
-        const uint32_t bk = ((cnt * 8u + 15u) / 16u) * 16u;
-        const uint32_t bm_ = ((cnt + 15u) / 16u) * 16u;
-        mbar_arrive_expect_tx(&s_bar, bk + bm_);
-        bulk_g2s(s_keys, a.st.keys[cur] + ts, bk, &s_bar);
-        bulk_g2s(s_meta, a.st.meta[cur] + ts, bm_, &s_bar);
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        issue(blockIdx.x, 0);
     }
     if (tid < kLevelSlots) {
         s_base[tid] = m->base[tid];
         s_n[tid] = m->n[tid];
     }
     __syncthreads();
-    if (!mbar_wait_bounded(&s_bar, 0, a.err)) s_ok = 0;
-    // Warp w owns nodes [w0, w0 + 512). Phase 1: its node count per level, lane i
-    // holding level Lb + i; lane t reads nodes [w0 + 16 t, w0 + 16 t + 16).
-    const uint32_t w0 = (uint32_t)warp * 512u;
-    uint32_t hw[4];
-    {
-        const uint32_t nb = w0 + (uint32_t)lane * 16u;
-        const uint4 v = *reinterpret_cast<const uint4*>(s_meta + nb);
-        const uint32_t raw[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint32_t h = live_heights(raw[k]);
-            // nodes past the end of the storage layer count as absent
-            const uint32_t first = nb + 4u * k;
-            if (first + 4u > cnt) {
-                const uint32_t keep = first >= cnt ? 0u : (cnt - first);  // 0..3 bytes
-                h &= keep ? (0xFFFFFFFFu >> (8u * (4u - keep))) : 0u;
-            }
-            hw[k] = h;
-        }
-    }
-    uint32_t hmax = __vmaxu4(__vmaxu4(hw[0], hw[1]), __vmaxu4(hw[2], hw[3]));
-    hmax = max(max(hmax & 0xFFu, (hmax >> 8) & 0xFFu), max((hmax >> 16) & 0xFFu, hmax >> 24));
-    const uint32_t wm = __reduce_max_sync(0xffffffffu, hmax);
-    uint32_t c = 0;
-    for (uint32_t l = Lb; l <= wm; ++l) {
-        uint32_t n_l = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) n_l += __popc(bytes_ge(hw[k], l));
-        const uint32_t tot = __reduce_add_sync(0xffffffffu, n_l >> 3);
-        if ((uint32_t)lane == l - Lb) c = tot;
-    }
-    s_wcnt[warp][lane] = c;
-    __syncthreads();
-    if (!s_ok) {
-        if (tid == 0) mbar_wait_bounded(&s_bar, 0, a.err);  // let the copy land
-        return;
-    }
-    // running position of this warp in level Lb + lane
-    uint32_t run = 0;
-    if (Lb + (uint32_t)lane <= H) {
-        run = a.loff[(size_t)lane * ntiles + tile];
-        for (int w = 0; w < warp; ++w) run += s_wcnt[w][lane];
-    }
-    // Phase 2: four rounds of 128 nodes; lane t holds nodes w0 + 128 r + 4 t .. + 3
-    // (one meta word). Per level, a warp prefix sum of the lanes' counts places the
-    // entries; they are staged in shared memory and written out coalesced.
-    uint64_t* stk = s_sk[warp];
-    uint32_t* std_ = s_sd[warp];
     const uint32_t lt = lanemask_lt();
-    (void)lt;
-    for (uint32_t rnd = 0; rnd < 4; ++rnd) {
-        const uint32_t nb = w0 + rnd * 128u + (uint32_t)lane * 4u;
-        uint32_t h = live_heights(*reinterpret_cast<const uint32_t*>(s_meta + nb));
-        if (nb + 4u > cnt) {
-            const uint32_t keep = nb >= cnt ? 0u : (cnt - nb);
-            h &= keep ? (0xFFFFFFFFu >> (8u * (4u - keep))) : 0u;
-        }
-        uint32_t hm = __vmaxu4(h, h >> 16);
-        hm = max(hm & 0xFFu, (hm >> 8) & 0xFFu);
-        const uint32_t rm = __reduce_max_sync(0xffffffffu, hm);
-        uint32_t prev_mask = 0, prev_first = 0;
-        for (uint32_t l = Lb; l <= rm; ++l) {
-            const uint32_t mk = bytes_ge(h, l);
-            const uint32_t cl = __popc(mk) >> 3;
-            uint32_t incl = cl;
+    const uint32_t w0 = (uint32_t)warp * 512u;
+    uint32_t it = 0;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const uint32_t b = it & 1u;
+        if (tid == 0 && tile + gridDim.x < ntiles) issue(tile + gridDim.x, b ^ 1u);  // buffer b^1 is free
+        const uint64_t* s_keys = reinterpret_cast<const uint64_t*>(s_dyn + b * kBufBytes);
+        const uint8_t* s_meta = s_dyn + b * kBufBytes + kKeyBytes;
+        const uint32_t ts = tile * kNodes;
+        const uint32_t cnt = min((uint32_t)kNodes, size - ts);
+        if (!mbar_wait_bounded(&s_bar[b], (it >> 1) & 1u, a.err)) s_ok = 0;
+        // Phase 1: the warp's node count per level (lane i holds level Lb + i); lane t
+        // looks at nodes [w0 + 16 t, w0 + 16 t + 16) of the tile.
+        {
+            const uint32_t nb = w0 + (uint32_t)lane * 16u;
+            const uint4 v = *reinterpret_cast<const uint4*>(s_meta + nb);
+            const uint32_t raw[4] = {v.x, v.y, v.z, v.w};
+            uint32_t hw[4];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const uint32_t excl = incl - cl;
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            const uint32_t base = __shfl_sync(0xffffffffu, run, (int)(l - Lb));
-            // stage this lane's entries of level l (in node order)
-            uint32_t j = 0;
-#pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-                if ((mk >> (8 * bb)) & 1u) {
-                    const uint32_t node = nb + (uint32_t)bb;
-                    uint32_t down;
-                    if (l == Lb) {
-                        down = ts + node;
-                    } else {
-                        // position of the node in level l - 1: that level's first slot
-                        // for this lane plus the lane's level-(l-1) nodes before it
-                        const uint32_t below = bb ? (prev_mask & ((1u << (8 * bb)) - 1u)) : 0u;
-                        down = prev_first + (__popc(below) >> 3);
-                    }
-                    stk[excl + j] = s_keys[node];
-                    std_[excl + j] = down;
-                    ++j;
+            for (int k = 0; k < 4; ++k) {
+                uint32_t h = live_heights(raw[k]);
+                const uint32_t first = nb + 4u * k;  // nodes past the storage layer's end are absent
+                if (first + 4u > cnt) {
+                    const uint32_t keep = first >= cnt ? 0u : (cnt - first);
+                    h &= keep ? (0xFFFFFFFFu >> (8u * (4u - keep))) : 0u;
                 }
+                hw[k] = h;
             }
-            __syncwarp();
-            for (uint32_t e = (uint32_t)lane; e < total; e += 32u) {
-                const uint32_t pos = base + e;
-                if (pos < s_n[l]) {
-                    const uint32_t g = s_base[l] + pos;
-                    a.lkeys[g] = stk[e];
-                    a.ldown[g] = std_[e];
+            uint32_t c = 0;
+            for (uint32_t l = Lb; l <= H; ++l) {
+                uint32_t nl = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) nl += __popc(members(hw[k], l));
+                const uint32_t tot = __reduce_add_sync(0xffffffffu, nl);
+                if ((uint32_t)lane == l - Lb) c = tot;
+                if (tot == 0) break;
+            }
+            s_wcnt[warp][lane] = c;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        // first position of this warp in level Lb + lane
+        uint32_t wbase = 0;
+        if (Lb + (uint32_t)lane <= H) {
+            wbase = a.loff[(size_t)lane * ntiles + tile];
+            for (int w = 0; w < warp; ++w) wbase += s_wcnt[w][lane];
+        }
+        uint32_t* la = s_list + warp * kList;  // entries: node (low 16) | index in level below (high 16)
+        uint32_t* lb = la + kList / 2;
+        // Level Lb: 16 chunks of 32 nodes, lane = node; members write consecutive
+        // slots. Nodes that reach level Lb + 1 too go to the warp's list with their
+        // index in level Lb (relative to the warp).
+        uint32_t base = __shfl_sync(0xffffffffu, wbase, 0);
+        uint32_t pos_in_level = 0, nlist = 0;
+        for (uint32_t ch = 0; ch < 16; ++ch) {
+            const uint32_t node = w0 + ch * 32u + (uint32_t)lane;
+            const uint8_t mt = node < cnt ? s_meta[node] : (uint8_t)kTomb;
+            const uint32_t h = (mt & kTomb) ? 0u : (uint32_t)(mt & kHeightMask);
+            const uint32_t b0 = __ballot_sync(0xffffffffu, h >= Lb);
+            if (!b0) continue;
+            const uint32_t b1 = __ballot_sync(0xffffffffu, h > Lb);
+            if (h >= Lb) {
+                const uint32_t idx = pos_in_level + __popc(b0 & lt);
+                const uint32_t p = base + idx;
+                if (p < s_n[Lb]) {
+                    const uint32_t g = s_base[Lb] + p;
+                    a.lkeys[g] = s_keys[node];
+                    a.ldown[g] = ts + node;
                 } else {
                     atomicOr(a.err, kErrBounds);
                 }
+                if (h > Lb) la[nlist + __popc(b1 & lt)] = node | (idx << 16);
+            }
+            pos_in_level += __popc(b0);
+            nlist += __popc(b1);
+        }
+        __syncwarp();
+        // Levels above: walk the previous level's list, 32 entries per step.
+        uint32_t prev_base = base;
+        for (uint32_t l = Lb + 1; l <= H && nlist > 0; ++l) {
+            base = __shfl_sync(0xffffffffu, wbase, (int)(l - Lb));
+            uint32_t nnext = 0;
+            for (uint32_t j0 = 0; j0 < nlist; j0 += 32u) {
+                const uint32_t j = j0 + (uint32_t)lane;
+                const bool in = j < nlist;
+                const uint32_t e = in ? la[j] : 0u;
+                const uint32_t node = e & 0xFFFFu;
+                const uint32_t h = in ? (uint32_t)(s_meta[node] & kHeightMask) : 0u;
+                const uint32_t b1 = __ballot_sync(0xffffffffu, in && h > l);
+                if (in) {
+                    const uint32_t p = base + j;
+                    if (p < s_n[l]) {
+                        const uint32_t g = s_base[l] + p;
+                        a.lkeys[g] = s_keys[node];
+                        a.ldown[g] = prev_base + (e >> 16);
+                    } else {
+                        atomicOr(a.err, kErrBounds);
+                    }
+                    if (h > l) lb[nnext + __popc(b1 & lt)] = node | (j << 16);
+                }
+                nnext += __popc(b1);
             }
             __syncwarp();
-            if ((uint32_t)lane == l - Lb) run += total;
-            prev_mask = mk;
-            prev_first = base + excl;
+            uint32_t* t = la;
+            la = lb;
+            lb = t;
+            nlist = nnext;
+            prev_base = base;
         }
+        __syncthreads();  // buffer b and the lists are reused next
+    }
+    if (!s_ok && tid == 0) {
+        // a wait gave up: let any copy still in flight land before the CTA exits
+        mbar_wait_bounded(&s_bar[0], 0, a.err);
+        mbar_wait_bounded(&s_bar[1], 0, a.err);
     }
 }
 
@@ -613,9 +629,8 @@ cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s) {
 
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
     (void)epoch;
-    (void)num_sms;
     static bool attr_set = false;
-    const int dyn = (kNodes + 2) * 8 + kNodes + 16;
+    const int dyn = (int)(2 * kBufBytes + 8 * kList * 4);
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_rebuild_write, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
@@ -624,7 +639,8 @@ cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s
     const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
     k_rebuild_count<<<(tiles + 7) / 8, 256, 0, s>>>(a);
     k_rebuild_scan<<<kLevelSlots - 2, 1024, 0, s>>>(a);
-    k_rebuild_write<<<tiles, kThreads, dyn, s>>>(a);
+    const uint32_t cap = 2u * (uint32_t)num_sms;
+    k_rebuild_write<<<(int)(tiles < cap ? tiles : cap), kThreads, dyn, s>>>(a);
     return cudaGetLastError();
 }
 

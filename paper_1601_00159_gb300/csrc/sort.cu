@@ -1,11 +1,17 @@
 // K0 + K1: validate/pack the query set and sort it by key (Definition 3: the queries
 // of a query set are ordered by key; Section 4.2: the sort can use data parallelism).
 //
-// LSD radix sort with 8-bit digits, one kernel launch per digit, each a single pass
-// over the data with decoupled look-back (the "Onesweep" organisation of Adinets and
-// Merrill, 2022, written here from the published description). A pass whose digit is
-// the same for every key (found from the histograms) is skipped. The sort is stable,
-// so equal keys stay in arrival order: the order is (key, arrival index), the
+// LSD radix sort with 8-bit digits. Every pass is three launches over tiles of 2048
+// elements, so no tile ever waits for another:
+//   count:   the tile's digit histogram (tile-major rows of 256 counters);
+//   scan:    one CTA per digit turns that digit's column into global offsets
+//            (digit base from the up-front histograms + prefix over tiles);
+//   scatter: ranks the tile's elements stably within the tile and writes them to
+//            offset + rank, staged in shared memory so each digit's run is written
+//            contiguously.
+// The up-front histograms of all eight digits (one read of the keys) give the digit
+// bases and let a pass whose digit is the same for every key be skipped. The sort is
+// stable, so equal keys stay in arrival order: the order is (key, arrival index), the
 // reading of Definition 3 for duplicate keys.
 //
 // Payload word: op << 30 | arrival index. Invalid queries (op > 2 or the reserved key)
@@ -51,10 +57,12 @@ __global__ void __launch_bounds__(256) k_pack_hist(const uint8_t* __restrict__ o
 }
 
 // Digit offsets (exclusive scan of each histogram) and the pass plan.
-__global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, uint32_t* dofs) {
+__global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, uint32_t* dofs, uint32_t* tile_max) {
     __shared__ uint32_t tmp[33];
     __shared__ uint32_t skip[8];
     const int b = threadIdx.x;
+    if (tile_max)
+        for (uint32_t t = b; t < (n + kApplyTile - 1) / kApplyTile; t += 256) tile_max[t] = 0;
     if (b < 8) skip[b] = 0;
     __syncthreads();
     for (int d = 0; d < 8; ++d) {
@@ -80,8 +88,50 @@ __global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, ui
     }
 }
 
+__device__ __forceinline__ const uint64_t* pass_src_keys(const SortPlan& P, uint32_t j, const SortBuffers& sb) {
+    return P.src[j] == 0 ? sb.in_k : (P.src[j] == 1 ? sb.a_k : sb.b_k);
+}
+
+// Digit histogram of every tile for pass j, over that pass's input.
+__global__ void __launch_bounds__(kThreads) k_sort_count(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
+    __shared__ uint32_t h[256];
+    const SortPlan& P = bm->plan;
+    if (j >= P.npass) return;
+    const uint32_t shift = 8u * P.digit[j];
+    const uint64_t* src = pass_src_keys(P, j, sb);
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t tbase = blockIdx.x * kTile;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint32_t i = tbase + k * kThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(uint32_t)(src[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    sb.tcnt[(size_t)blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
+}
+
+// One CTA per digit: that digit's offset in every tile for pass j.
+__global__ void __launch_bounds__(kThreads) k_sort_scan(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
+    __shared__ uint32_t s_tmp[33];
+    const SortPlan& P = bm->plan;
+    if (j >= P.npass) return;
+    const uint32_t d = blockIdx.x;
+    const uint32_t ntiles = (n + kTile - 1) / kTile;
+    const uint32_t per = (ntiles + kThreads - 1) / kThreads;
+    const uint32_t t0 = min(threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
+    uint32_t sum = 0;
+    for (uint32_t t = t0; t < t1; ++t) sum += sb.tcnt[(size_t)t * 256 + d];
+    uint32_t run = sb.dofs[P.digit[j] * 256 + d] + block_excl_sum<kThreads>(sum, s_tmp, nullptr);
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t c = sb.tcnt[(size_t)t * 256 + d];
+        sb.toff[(size_t)t * 256 + d] = run;
+        run += c;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t n, SortBuffers sb,
-                                                        BatchMeta* bm, uint32_t epoch, uint32_t* err) {
+                                                           BatchMeta* bm, uint32_t* err) {
     const SortPlan& P = bm->plan;
     if (j >= P.npass) return;
     const uint32_t shift = 8u * P.digit[j];
@@ -97,17 +147,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
     __shared__ uint32_t s_gbase[256];
     __shared__ uint32_t s_tstart[256];
     __shared__ uint32_t s_tmp[33];
-    __shared__ uint32_t s_tile;
-    __shared__ int s_ok;
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        s_tile = atomicAdd(&bm->tile_ctr[j], 1u);
-        s_ok = 1;
-    }
     for (int i = tid; i < kWarps * 256; i += kThreads) (&s_whist[0][0])[i] = 0;
     __syncthreads();
-    const uint32_t tile = s_tile;
+    const uint32_t tile = blockIdx.x;
     const uint32_t tbase = tile * kTile;
     const uint32_t tn = min((uint32_t)kTile, n - tbase);
 
@@ -158,13 +201,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
         s_whist[w][tid] = total;
         total += c;
     }
-    bool ok;
-    uint32_t excl = lookback_sum_win<8>(sb.desc + tid, 256, tile, epoch, total, err, &ok);
-    if (!ok) s_ok = 0;
-    s_gbase[tid] = sb.dofs[P.digit[j] * 256 + tid] + excl;
+    s_gbase[tid] = sb.toff[(size_t)tile * 256 + tid];
     s_tstart[tid] = block_excl_sum<kThreads>(total, s_tmp, nullptr);
     __syncthreads();
-    if (!s_ok) return;  // a predecessor never published: write nothing
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         uint32_t d = dig[k];
@@ -195,7 +234,7 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
     if (n == 0) return cudaSuccess;
     int grid = min((int)((n + 255) / 256), num_sms * 8);
     k_pack_hist<<<grid, 256, 0, s>>>(ops, keys, n, sb.in_k, sb.in_p, bm);
-    k_sort_plan<<<1, 256, 0, s>>>(n, bm, sb.dofs);
+    k_sort_plan<<<1, 256, 0, s>>>(n, bm, sb.dofs, sb.tile_max);
     static bool attr_set = false;
     const int dyn = kTile * (int)(sizeof(uint64_t) + sizeof(uint32_t));
     if (!attr_set) {
@@ -203,10 +242,14 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    uint32_t tiles = (n + kTile - 1) / kTile;
+    const uint32_t tiles = (n + kTile - 1) / kTile;
+    k_sort_count<<<tiles, kThreads, 0, s>>>(0, n, sb, bm);
     for (uint32_t j = 0; j < 8; ++j) {
-        k_sort_pass<<<tiles, kThreads, dyn, s>>>(j, n, sb, bm, ++epoch, err);
+        k_sort_scan<<<256, kThreads, 0, s>>>(j, n, sb, bm);
+        k_sort_pass<<<tiles, kThreads, dyn, s>>>(j, n, sb, bm, err);
+        if (j + 1 < 8) k_sort_count<<<tiles, kThreads, 0, s>>>(j + 1, n, sb, bm);
     }
+    (void)epoch;
     return cudaGetLastError();
 }
 
