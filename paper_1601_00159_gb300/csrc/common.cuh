@@ -67,7 +67,8 @@ struct BatchMeta {
     uint32_t rebuild;            // the rebuild runs in this batch
     uint32_t changes;            // storage nodes whose liveness changed or that were added
     uint32_t pad_[1];
-    uint32_t hist[8][256];       // radix digit histograms
+    uint32_t bmax[8];            // per key byte: its maximum over the batch
+    uint32_t bnmin[8];           // per key byte: 255 - its minimum over the batch
     SortPlan plan;
 };
 
@@ -413,11 +414,12 @@ struct SortBuffers {
     uint32_t* a_p;
     uint64_t* b_k;
     uint32_t* b_p;
-    uint32_t* dofs;  // [8][256] digit offsets
+    uint32_t* dofs;  // [256] digit totals of the current pass
     uint64_t* desc;  // [tiles][256] look-back descriptors
     uint32_t* tile_max;  // per-apply-tile max run marker, cleared by the plan kernel (may be null)
     uint32_t* tcnt;      // [tiles][256] per-tile digit counts of the current pass
     uint32_t* toff;      // [tiles][256] per-tile digit offsets of the current pass
+    uint8_t* ndig;       // next pass's digit of every element, in the current pass's output order
 };
 
 // Radix sort of (key, payload) pairs: result in a_k / a_p, stable, by key.

@@ -37,6 +37,7 @@ struct Scratch {
     uint32_t* tile_new = nullptr;
     uint32_t* tcnt = nullptr;  // radix sort: per-tile digit counts
     uint32_t* toff = nullptr;  // radix sort: per-tile digit offsets
+    uint8_t* ndig = nullptr;   // radix sort: next pass's digits
 };
 
 struct Staging {
@@ -176,7 +177,7 @@ void free_scratch(Scratch& s) {
     dfree(s.nn.keys); dfree(s.nn.vals); dfree(s.nn.loc); dfree(s.nn.height);
     dfree(s.stage.keys); dfree(s.stage.vals); dfree(s.stage.loc); dfree(s.stage.height);
     dfree(s.tile_max); dfree(s.tile_pref); dfree(s.tile_new);
-    dfree(s.tcnt); dfree(s.toff);
+    dfree(s.tcnt); dfree(s.toff); dfree(s.ndig);
     s.cap = 0;
 }
 
@@ -197,6 +198,7 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     PI_TRY(dalloc(&s.tile_max, tiles)); PI_TRY(dalloc(&s.tile_pref, tiles)); PI_TRY(dalloc(&s.tile_new, tiles));
     const uint64_t stiles = (q + kSortTile - 1) / kSortTile + 1;
     PI_TRY(dalloc(&s.tcnt, stiles * 256)); PI_TRY(dalloc(&s.toff, stiles * 256));
+    PI_TRY(dalloc(&s.ndig, stiles * kSortTile + 16));
 #undef PI_TRY
     s.cap = q;
     return cudaSuccess;
@@ -277,6 +279,7 @@ SortBuffers sort_buffers(pi_index* x, const Scratch& s) {
     sb.tile_max = s.tile_max;
     sb.tcnt = s.tcnt;
     sb.toff = s.toff;
+    sb.ndig = s.ndig;
     return sb;
 }
 

@@ -321,17 +321,20 @@ __device__ __forceinline__ uint32_t members(uint32_t hw, uint32_t l) {
     return ((hw | 0x80808080u) - l * 0x01010101u) & 0x80808080u;
 }
 
-constexpr int kList = 1024;  // per-warp list capacity (the warp owns 512 nodes)
 constexpr uint32_t kKeyBytes = (kNodes + 2) * sizeof(uint64_t);
 constexpr uint32_t kMetaBytes = kNodes + 16;
 constexpr uint32_t kBufBytes = kKeyBytes + kMetaBytes;  // one tile: keys then meta
 
 // Persistent CTAs, tiles assigned statically (tile = blockIdx.x + k * gridDim.x); two
 // shared-memory buffers, so the TMA bulk copy of the CTA's next tile lands while the
-// current one is processed.
+// current one is processed. Warp w owns nodes [512 w, 512 w + 512) of a tile and walks
+// them in four chunks of 128: lane t holds nodes 4t..4t+3 of the chunk (one meta
+// word). Per level, a byte-wise membership test, one warp prefix sum of the lanes'
+// counts and stores at consecutive positions place the chunk's entries; a node's
+// position in the level below (its down pointer) is that level's position of the
+// lane's first member plus the lane's members before it.
 __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
-    uint32_t* s_list = reinterpret_cast<uint32_t*>(s_dyn + 2 * kBufBytes);  // 8 warps x kList
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_wcnt[8][32];
     __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
@@ -367,7 +370,6 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
         s_n[tid] = m->n[tid];
     }
     __syncthreads();
-    const uint32_t lt = lanemask_lt();
     const uint32_t w0 = (uint32_t)warp * 512u;
     uint32_t it = 0;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -378,23 +380,20 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
         const uint32_t ts = tile * kNodes;
         const uint32_t cnt = min((uint32_t)kNodes, size - ts);
         if (!mbar_wait_bounded(&s_bar[b], (it >> 1) & 1u, a.err)) s_ok = 0;
-        // Phase 1: the warp's node count per level (lane i holds level Lb + i); lane t
-        // looks at nodes [w0 + 16 t, w0 + 16 t + 16) of the tile.
-        {
-            const uint32_t nb = w0 + (uint32_t)lane * 16u;
-            const uint4 v = *reinterpret_cast<const uint4*>(s_meta + nb);
-            const uint32_t raw[4] = {v.x, v.y, v.z, v.w};
-            uint32_t hw[4];
+        // Live heights of the lane's nodes in the four chunks (one word per chunk).
+        uint32_t hw[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint32_t h = live_heights(raw[k]);
-                const uint32_t first = nb + 4u * k;  // nodes past the storage layer's end are absent
-                if (first + 4u > cnt) {
-                    const uint32_t keep = first >= cnt ? 0u : (cnt - first);
-                    h &= keep ? (0xFFFFFFFFu >> (8u * (4u - keep))) : 0u;
-                }
-                hw[k] = h;
+        for (int c4 = 0; c4 < 4; ++c4) {
+            const uint32_t nb = w0 + (uint32_t)c4 * 128u + (uint32_t)lane * 4u;
+            uint32_t h = live_heights(*reinterpret_cast<const uint32_t*>(s_meta + nb));
+            if (nb + 4u > cnt) {  // nodes past the storage layer's end are absent
+                const uint32_t keep = nb >= cnt ? 0u : (cnt - nb);
+                h &= keep ? (0xFFFFFFFFu >> (8u * (4u - keep))) : 0u;
             }
+            hw[c4] = h;
+        }
+        // Phase 1: the warp's node count per level (lane i holds level Lb + i).
+        {
             uint32_t c = 0;
             for (uint32_t l = Lb; l <= H; ++l) {
                 uint32_t nl = 0;
@@ -409,74 +408,52 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
         __syncthreads();
         if (!s_ok) break;
         // first position of this warp in level Lb + lane
-        uint32_t wbase = 0;
+        uint32_t run = 0;
         if (Lb + (uint32_t)lane <= H) {
-            wbase = a.loff[(size_t)lane * ntiles + tile];
-            for (int w = 0; w < warp; ++w) wbase += s_wcnt[w][lane];
+            run = a.loff[(size_t)lane * ntiles + tile];
+            for (int w = 0; w < warp; ++w) run += s_wcnt[w][lane];
         }
-        uint32_t* la = s_list + warp * kList;  // entries: node (low 16) | index in level below (high 16)
-        uint32_t* lb = la + kList / 2;
-        // Level Lb: 16 chunks of 32 nodes, lane = node; members write consecutive
-        // slots. Nodes that reach level Lb + 1 too go to the warp's list with their
-        // index in level Lb (relative to the warp).
-        uint32_t base = __shfl_sync(0xffffffffu, wbase, 0);
-        uint32_t pos_in_level = 0, nlist = 0;
-        for (uint32_t ch = 0; ch < 16; ++ch) {
-            const uint32_t node = w0 + ch * 32u + (uint32_t)lane;
-            const uint8_t mt = node < cnt ? s_meta[node] : (uint8_t)kTomb;
-            const uint32_t h = (mt & kTomb) ? 0u : (uint32_t)(mt & kHeightMask);
-            const uint32_t b0 = __ballot_sync(0xffffffffu, h >= Lb);
-            if (!b0) continue;
-            const uint32_t b1 = __ballot_sync(0xffffffffu, h > Lb);
-            if (h >= Lb) {
-                const uint32_t idx = pos_in_level + __popc(b0 & lt);
-                const uint32_t p = base + idx;
-                if (p < s_n[Lb]) {
-                    const uint32_t g = s_base[Lb] + p;
-                    a.lkeys[g] = s_keys[node];
-                    a.ldown[g] = ts + node;
-                } else {
-                    atomicOr(a.err, kErrBounds);
+        // Phase 2: per chunk, level by level until the chunk has no member.
+#pragma unroll 1
+        for (int c4 = 0; c4 < 4; ++c4) {
+            const uint32_t h = hw[c4];
+            const uint32_t nb = w0 + (uint32_t)c4 * 128u + (uint32_t)lane * 4u;
+            uint32_t prev_mk = 0, prev_first = 0;
+            for (uint32_t l = Lb; l <= H; ++l) {
+                const uint32_t mk = members(h, l);  // bit 8k+7 set: node nb+k is in level l
+                const uint32_t cl = __popc(mk);
+                uint32_t incl = cl;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
                 }
-                if (h > Lb) la[nlist + __popc(b1 & lt)] = node | (idx << 16);
-            }
-            pos_in_level += __popc(b0);
-            nlist += __popc(b1);
-        }
-        __syncwarp();
-        // Levels above: walk the previous level's list, 32 entries per step.
-        uint32_t prev_base = base;
-        for (uint32_t l = Lb + 1; l <= H && nlist > 0; ++l) {
-            base = __shfl_sync(0xffffffffu, wbase, (int)(l - Lb));
-            uint32_t nnext = 0;
-            for (uint32_t j0 = 0; j0 < nlist; j0 += 32u) {
-                const uint32_t j = j0 + (uint32_t)lane;
-                const bool in = j < nlist;
-                const uint32_t e = in ? la[j] : 0u;
-                const uint32_t node = e & 0xFFFFu;
-                const uint32_t h = in ? (uint32_t)(s_meta[node] & kHeightMask) : 0u;
-                const uint32_t b1 = __ballot_sync(0xffffffffu, in && h > l);
-                if (in) {
-                    const uint32_t p = base + j;
-                    if (p < s_n[l]) {
-                        const uint32_t g = s_base[l] + p;
-                        a.lkeys[g] = s_keys[node];
-                        a.ldown[g] = prev_base + (e >> 16);
-                    } else {
-                        atomicOr(a.err, kErrBounds);
+                const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                if (total == 0) break;
+                const uint32_t first = __shfl_sync(0xffffffffu, run, (int)(l - Lb)) + incl - cl;
+                uint32_t j = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if ((mk >> (8 * k + 7)) & 1u) {
+                        const uint32_t p = first + j;
+                        const uint32_t node = nb + (uint32_t)k;
+                        if (p < s_n[l]) {
+                            const uint32_t g = s_base[l] + p;
+                            a.lkeys[g] = s_keys[node];
+                            a.ldown[g] = (l == Lb) ? ts + node
+                                                   : prev_first + __popc(prev_mk & ((1u << (8 * k)) - 1u));
+                        } else {
+                            atomicOr(a.err, kErrBounds);
+                        }
+                        ++j;
                     }
-                    if (h > l) lb[nnext + __popc(b1 & lt)] = node | (j << 16);
                 }
-                nnext += __popc(b1);
+                if ((uint32_t)lane == l - Lb) run += total;
+                prev_mk = mk;
+                prev_first = first;
             }
-            __syncwarp();
-            uint32_t* t = la;
-            la = lb;
-            lb = t;
-            nlist = nnext;
-            prev_base = base;
         }
-        __syncthreads();  // buffer b and the lists are reused next
+        __syncthreads();  // buffer b is reused two tiles later
     }
     if (!s_ok && tid == 0) {
         // a wait gave up: let any copy still in flight land before the CTA exits
@@ -630,7 +607,7 @@ cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s) {
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
     (void)epoch;
     static bool attr_set = false;
-    const int dyn = (int)(2 * kBufBytes + 8 * kList * 4);
+    const int dyn = (int)(2 * kBufBytes);
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_rebuild_write, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
@@ -639,7 +616,7 @@ cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s
     const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
     k_rebuild_count<<<(tiles + 7) / 8, 256, 0, s>>>(a);
     k_rebuild_scan<<<kLevelSlots - 2, 1024, 0, s>>>(a);
-    const uint32_t cap = 2u * (uint32_t)num_sms;
+    const uint32_t cap = 3u * (uint32_t)num_sms;
     k_rebuild_write<<<(int)(tiles < cap ? tiles : cap), kThreads, dyn, s>>>(a);
     return cudaGetLastError();
 }

@@ -29,55 +29,61 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kWarpSpan = 32 * kItems;    // 256 consecutive elements per warp
 static_assert(kTile == kSortTile, "tile size shared with the host's descriptor sizing");
 
-__global__ void __launch_bounds__(256) k_pack_hist(const uint8_t* __restrict__ ops,
-                                                   const uint64_t* __restrict__ keys, uint32_t n,
-                                                   uint64_t* __restrict__ sk, uint32_t* __restrict__ sp,
-                                                   BatchMeta* bm) {
-    __shared__ uint32_t h[8 * 256];
-    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) h[i] = 0;
-    __syncthreads();
+// K0: validate and pack. Also finds, per key byte, whether it is the same in every
+// key (byte-wise min and max), which decides the radix passes that can be skipped.
+__global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ ops, const uint64_t* __restrict__ keys,
+                                              uint32_t n, uint64_t* __restrict__ sk, uint32_t* __restrict__ sp,
+                                              BatchMeta* bm) {
     uint32_t invalid = 0;
+    uint32_t mx[8], mn[8];  // mn holds max of (255 - byte), so zero is the identity
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        mx[d] = 0;
+        mn[d] = 0;
+    }
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint64_t k = keys[i];
-        uint32_t op = ops ? ops[i] : 0u;
-        bool valid = op <= 2u && k != kMaxKey;
-        uint64_t s = valid ? k : kMaxKey;
+        const uint64_t k = keys[i];
+        const uint32_t op = ops ? ops[i] : 0u;
+        const bool valid = op <= 2u && k != kMaxKey;
+        const uint64_t s = valid ? k : kMaxKey;
         invalid += valid ? 0u : 1u;
         sk[i] = s;
         sp[i] = ((op & 3u) << 30) | i;
 #pragma unroll
-        for (int d = 0; d < 8; ++d) atomicAdd(&h[d * 256 + ((s >> (8 * d)) & 255u)], 1u);
+        for (int d = 0; d < 8; ++d) {
+            const uint32_t b = (uint32_t)(s >> (8 * d)) & 255u;
+            mx[d] = max(mx[d], b);
+            mn[d] = max(mn[d], 255u - b);
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) invalid += __shfl_xor_sync(0xffffffffu, invalid, o);
-    if ((threadIdx.x & 31) == 0 && invalid) atomicAdd(&bm->invalid, invalid);
-    __syncthreads();
-    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x)
-        if (h[i]) atomicAdd(&bm->hist[i >> 8][i & 255], h[i]);
+    for (int d = 0; d < 8; ++d) {
+        mx[d] = __reduce_max_sync(0xffffffffu, mx[d]);
+        mn[d] = __reduce_max_sync(0xffffffffu, mn[d]);
+    }
+    invalid = __reduce_add_sync(0xffffffffu, invalid);
+    if ((threadIdx.x & 31) == 0) {
+        if (invalid) atomicAdd(&bm->invalid, invalid);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            atomicMax(&bm->bmax[d], mx[d]);
+            atomicMax(&bm->bnmin[d], mn[d]);
+        }
+    }
 }
 
-// Digit offsets (exclusive scan of each histogram) and the pass plan.
-__global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, uint32_t* dofs, uint32_t* tile_max) {
-    __shared__ uint32_t tmp[33];
-    __shared__ uint32_t skip[8];
+// Pass plan: the passes whose byte varies (at least one), ping-ponging so the last
+// pass writes buffer A.
+__global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, uint32_t* tile_max) {
     const int b = threadIdx.x;
     if (tile_max)
         for (uint32_t t = b; t < (n + kApplyTile - 1) / kApplyTile; t += 256) tile_max[t] = 0;
-    if (b < 8) skip[b] = 0;
-    __syncthreads();
-    for (int d = 0; d < 8; ++d) {
-        uint32_t c = bm->hist[d][b];
-        if (c == n) skip[d] = 1;
-        uint32_t ex = block_excl_sum<256>(c, tmp, nullptr);
-        dofs[d * 256 + b] = ex;
-    }
-    __syncthreads();
     if (b == 0) {
         SortPlan& P = bm->plan;
         uint32_t r = 0;
         uint32_t dig[8];
         for (int d = 0; d < 8; ++d)
-            if (!skip[d]) dig[r++] = d;
+            if (bm->bmax[d] != 255u - bm->bnmin[d]) dig[r++] = d;  // max byte != min byte
         if (r == 0) dig[r++] = 0;  // all keys equal: one pass (identity order)
         P.npass = r;
         for (uint32_t j = 0; j < r; ++j) {
@@ -92,41 +98,78 @@ __device__ __forceinline__ const uint64_t* pass_src_keys(const SortPlan& P, uint
     return P.src[j] == 0 ? sb.in_k : (P.src[j] == 1 ? sb.a_k : sb.b_k);
 }
 
-// Digit histogram of every tile for pass j, over that pass's input.
+// Digit histogram of every tile for pass j. Pass 0 reads the packed keys; later
+// passes read the digit bytes the previous scatter wrote beside its output.
 __global__ void __launch_bounds__(kThreads) k_sort_count(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
     __shared__ uint32_t h[256];
     const SortPlan& P = bm->plan;
     if (j >= P.npass) return;
-    const uint32_t shift = 8u * P.digit[j];
-    const uint64_t* src = pass_src_keys(P, j, sb);
     h[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t tbase = blockIdx.x * kTile;
+    if (j == 0) {
+        const uint32_t shift = 8u * P.digit[0];
+        const uint64_t* src = pass_src_keys(P, 0, sb);
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const uint32_t i = tbase + k * kThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(uint32_t)(src[i] >> shift) & 255u], 1u);
+        for (int k = 0; k < kItems; ++k) {
+            const uint32_t i = tbase + k * kThreads + threadIdx.x;
+            if (i < n) atomicAdd(&h[(uint32_t)(src[i] >> shift) & 255u], 1u);
+        }
+    } else {
+        // 8 digit bytes per thread: one 8-byte load
+        const uint32_t i0 = tbase + threadIdx.x * 8u;
+        if (i0 + 8u <= n) {
+            const uint2 v = *reinterpret_cast<const uint2*>(sb.ndig + i0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(&h[(v.x >> (8 * k)) & 255u], 1u);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(&h[(v.y >> (8 * k)) & 255u], 1u);
+        } else {
+            for (uint32_t i = i0; i < n && i < i0 + 8u; ++i) atomicAdd(&h[sb.ndig[i]], 1u);
+        }
     }
     __syncthreads();
     sb.tcnt[(size_t)blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
 }
 
-// One CTA per digit: that digit's offset in every tile for pass j.
-__global__ void __launch_bounds__(kThreads) k_sort_scan(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
+// One CTA per digit: that digit's offset in every tile for pass j, relative to the
+// digit's first slot, and the digit's total (the scatter adds the digit bases).
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
     __shared__ uint32_t s_tmp[33];
     const SortPlan& P = bm->plan;
     if (j >= P.npass) return;
     const uint32_t d = blockIdx.x;
     const uint32_t ntiles = (n + kTile - 1) / kTile;
-    const uint32_t per = (ntiles + kThreads - 1) / kThreads;
+    const uint32_t per = (ntiles + 1023u) / 1024u;
     const uint32_t t0 = min(threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
+    uint32_t c[4];
     uint32_t sum = 0;
-    for (uint32_t t = t0; t < t1; ++t) sum += sb.tcnt[(size_t)t * 256 + d];
-    uint32_t run = sb.dofs[P.digit[j] * 256 + d] + block_excl_sum<kThreads>(sum, s_tmp, nullptr);
-    for (uint32_t t = t0; t < t1; ++t) {
-        const uint32_t c = sb.tcnt[(size_t)t * 256 + d];
-        sb.toff[(size_t)t * 256 + d] = run;
-        run += c;
+    if (per <= 4) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            c[k] = (t0 + k < t1) ? sb.tcnt[(size_t)(t0 + k) * 256 + d] : 0u;
+            sum += c[k];
+        }
+    } else {
+        for (uint32_t t = t0; t < t1; ++t) sum += sb.tcnt[(size_t)t * 256 + d];
+    }
+    uint32_t total;
+    uint32_t run = block_excl_sum<1024>(sum, s_tmp, &total);
+    if (threadIdx.x == 0) sb.dofs[d] = total;  // digit total of this pass
+    if (per <= 4) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (t0 + k < t1) {
+                sb.toff[(size_t)(t0 + k) * 256 + d] = run;
+                run += c[k];
+            }
+        }
+    } else {
+        for (uint32_t t = t0; t < t1; ++t) {
+            const uint32_t cc = sb.tcnt[(size_t)t * 256 + d];
+            sb.toff[(size_t)t * 256 + d] = run;
+            run += cc;
+        }
     }
 }
 
@@ -201,7 +244,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
         s_whist[w][tid] = total;
         total += c;
     }
-    s_gbase[tid] = sb.toff[(size_t)tile * 256 + tid];
+    const uint32_t dbase = block_excl_sum<kThreads>(sb.dofs[tid], s_tmp, nullptr);  // digit bases
+    s_gbase[tid] = dbase + sb.toff[(size_t)tile * 256 + tid];
     s_tstart[tid] = block_excl_sum<kThreads>(total, s_tmp, nullptr);
     __syncthreads();
 #pragma unroll
@@ -214,6 +258,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
         }
     }
     __syncthreads();
+    const bool next = j + 1 < P.npass;
+    const uint32_t nshift = next ? 8u * P.digit[j + 1] : 0u;
     for (uint32_t s = tid; s < tn; s += kThreads) {
         uint64_t k = s_key[s];
         uint32_t d = (uint32_t)((k >> shift) & 255u);
@@ -221,6 +267,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
         if (g < n) {
             dst_k[g] = k;
             dst_p[g] = s_pay[s];
+            if (next) sb.ndig[g] = (uint8_t)(k >> nshift);  // the next pass's digit
         } else {
             atomicOr(err, kErrBounds);
         }
@@ -233,8 +280,8 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
                         BatchMeta* bm, uint32_t* err, uint32_t& epoch, cudaStream_t s, int num_sms) {
     if (n == 0) return cudaSuccess;
     int grid = min((int)((n + 255) / 256), num_sms * 8);
-    k_pack_hist<<<grid, 256, 0, s>>>(ops, keys, n, sb.in_k, sb.in_p, bm);
-    k_sort_plan<<<1, 256, 0, s>>>(n, bm, sb.dofs, sb.tile_max);
+    k_pack<<<grid, 256, 0, s>>>(ops, keys, n, sb.in_k, sb.in_p, bm);
+    k_sort_plan<<<1, 256, 0, s>>>(n, bm, sb.tile_max);
     static bool attr_set = false;
     const int dyn = kTile * (int)(sizeof(uint64_t) + sizeof(uint32_t));
     if (!attr_set) {
@@ -245,7 +292,7 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
     const uint32_t tiles = (n + kTile - 1) / kTile;
     k_sort_count<<<tiles, kThreads, 0, s>>>(0, n, sb, bm);
     for (uint32_t j = 0; j < 8; ++j) {
-        k_sort_scan<<<256, kThreads, 0, s>>>(j, n, sb, bm);
+        k_sort_scan<<<256, 1024, 0, s>>>(j, n, sb, bm);
         k_sort_pass<<<tiles, kThreads, dyn, s>>>(j, n, sb, bm, err);
         if (j + 1 < 8) k_sort_count<<<tiles, kThreads, 0, s>>>(j + 1, n, sb, bm);
     }
