@@ -281,10 +281,11 @@ __global__ void __launch_bounds__(256) k_rebuild_count(RebuildArgs a) {
     if (lane < 32 && lane + 2 < kLevelSlots) a.lcnt[(size_t)lane * a.lstride + tile] = c;
 }
 
-// One CTA per built level: exclusive scan of the tile counts; checks the total.
+// One CTA per built level: exclusive scan of the tile counts; checks the total. Each
+// thread takes a contiguous run of tiles (independent loads), so the scan is one block
+// prefix sum per 1024 runs rather than one per 1024 tiles.
 __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
     __shared__ uint32_t s_tmp[33];
-    __shared__ uint32_t s_carry;
     const DevMeta* m = a.m;
     if (block_sees_error(&m->error)) return;
     if (!a.bm->rebuild) return;
@@ -294,19 +295,18 @@ __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
     const uint32_t ntiles = (size + kNodes - 1) / kNodes;
     const uint32_t* c = a.lcnt + (size_t)(l - 2) * a.lstride;
     uint32_t* o = a.loff + (size_t)(l - Lb) * ntiles;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (uint32_t b0 = 0; b0 < ntiles; b0 += 1024) {
-        const uint32_t i = b0 + threadIdx.x;
-        const uint32_t v = i < ntiles ? c[i] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_excl_sum<1024>(v, s_tmp, &tot);
-        if (i < ntiles) o[i] = s_carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += tot;
-        __syncthreads();
+    const uint32_t per = (ntiles + 1023u) / 1024u;
+    const uint32_t t0 = min(threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
+    uint32_t sum = 0;
+    for (uint32_t t = t0; t < t1; ++t) sum += c[t];
+    uint32_t tot;
+    uint32_t run = block_excl_sum<1024>(sum, s_tmp, &tot);
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t v = c[t];
+        o[t] = run;
+        run += v;
     }
-    if (threadIdx.x == 0 && s_carry != m->n[l]) atomicOr(a.err, kErrBounds);  // counts disagree
+    if (threadIdx.x == 0 && tot != m->n[l]) atomicOr(a.err, kErrBounds);  // counts disagree
 }
 
 // Byte-wise arithmetic on a meta word holding four nodes (height in bits 0-5, delete
@@ -323,19 +323,25 @@ __device__ __forceinline__ uint32_t members(uint32_t hw, uint32_t l) {
 
 constexpr uint32_t kKeyBytes = (kNodes + 2) * sizeof(uint64_t);
 constexpr uint32_t kMetaBytes = kNodes + 16;
-constexpr uint32_t kBufBytes = kKeyBytes + kMetaBytes;  // one tile: keys then meta
+constexpr uint32_t kWarpNodes = kNodes / 8;  // 512 nodes per warp
 
-// Persistent CTAs, tiles assigned statically (tile = blockIdx.x + k * gridDim.x); two
-// shared-memory buffers, so the TMA bulk copy of the CTA's next tile lands while the
-// current one is processed. Warp w owns nodes [512 w, 512 w + 512) of a tile and walks
-// them in four chunks of 128: lane t holds nodes 4t..4t+3 of the chunk (one meta
-// word). Per level, a byte-wise membership test, one warp prefix sum of the lanes'
-// counts and stores at consecutive positions place the chunk's entries; a node's
-// position in the level below (its down pointer) is that level's position of the
-// lane's first member plus the lane's members before it.
+// One tile of 4096 nodes per CTA: keys and meta arrive in shared memory by TMA bulk
+// copy. Warp w owns nodes [512 w, 512 w + 512); lane t holds nodes 16t..16t+15 of them.
+//  1. per lane, a byte-wise membership test of its nodes for every level gives the
+//     warp's count per level (lane i accumulates level Lb + i); the warps' counts are
+//     prefixed across the tile (one barrier);
+//  2. the lanes' level-Lb members (node indices) are placed in a per-warp list in
+//     node order by one warp prefix sum;
+//  3. the whole warp emits level Lb from the list, 32 consecutive entries per step
+//     (coalesced stores), and compacts the list in place to the members of level
+//     Lb + 1, keeping each one's index in level Lb for its down pointer; the next
+//     levels repeat step 3 on the shrinking list.
 __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
-    __shared__ __align__(8) uint64_t s_bar[2];
+    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);                   // kNodes + 2
+    uint8_t* s_meta = s_dyn + kKeyBytes;                                     // kNodes + 16
+    uint32_t* s_list = reinterpret_cast<uint32_t*>(s_dyn + kKeyBytes + kMetaBytes);  // 8 x 512
+    __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_wcnt[8][32];
     __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
     __shared__ int s_ok;
@@ -347,118 +353,119 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     const uint32_t H = m->H, Lb = m->Lb, size = m->size, cur = m->cur;
     if (H < Lb || size == 0) return;
     const uint32_t ntiles = (size + kNodes - 1) / kNodes;
-    if (blockIdx.x >= ntiles) return;
-    const uint64_t* SK = a.st.keys[cur];
-    const uint8_t* SMt = a.st.meta[cur];
-    auto issue = [&](uint32_t t, uint32_t b) {  // thread 0 only
-        const uint32_t c = min((uint32_t)kNodes, size - t * kNodes);
-        const uint32_t bk = ((c * 8u + 15u) / 16u) * 16u;
-        const uint32_t bm_ = ((c + 15u) / 16u) * 16u;
-        uint8_t* buf = s_dyn + b * kBufBytes;
-        mbar_arrive_expect_tx(&s_bar[b], bk + bm_);
-        bulk_g2s(buf, SK + (size_t)t * kNodes, bk, &s_bar[b]);
-        bulk_g2s(buf + kKeyBytes, SMt + (size_t)t * kNodes, bm_, &s_bar[b]);
-    };
+    const uint32_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    const uint32_t ts = tile * kNodes;
+    const uint32_t cnt = min((uint32_t)kNodes, size - ts);
     if (tid == 0) {
         s_ok = 1;
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        issue(blockIdx.x, 0);
+        mbar_init(&s_bar, 1);
+        const uint32_t bk = ((cnt * 8u + 15u) / 16u) * 16u;
+        const uint32_t bm_ = ((cnt + 15u) / 16u) * 16u;
+        mbar_arrive_expect_tx(&s_bar, bk + bm_);
+        bulk_g2s(s_keys, a.st.keys[cur] + ts, bk, &s_bar);
+        bulk_g2s(s_meta, a.st.meta[cur] + ts, bm_, &s_bar);
     }
     if (tid < kLevelSlots) {
         s_base[tid] = m->base[tid];
         s_n[tid] = m->n[tid];
     }
     __syncthreads();
-    const uint32_t w0 = (uint32_t)warp * 512u;
-    uint32_t it = 0;
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const uint32_t b = it & 1u;
-        if (tid == 0 && tile + gridDim.x < ntiles) issue(tile + gridDim.x, b ^ 1u);  // buffer b^1 is free
-        const uint64_t* s_keys = reinterpret_cast<const uint64_t*>(s_dyn + b * kBufBytes);
-        const uint8_t* s_meta = s_dyn + b * kBufBytes + kKeyBytes;
-        const uint32_t ts = tile * kNodes;
-        const uint32_t cnt = min((uint32_t)kNodes, size - ts);
-        if (!mbar_wait_bounded(&s_bar[b], (it >> 1) & 1u, a.err)) s_ok = 0;
-        // Live heights of the lane's nodes in the four chunks (one word per chunk).
-        uint32_t hw[4];
+    if (!mbar_wait_bounded(&s_bar, 0, a.err)) s_ok = 0;
+    const uint32_t w0 = (uint32_t)warp * kWarpNodes;
+    const uint32_t nb = w0 + (uint32_t)lane * 16u;
+    uint32_t hw[4];
+    {
+        const uint4 v = *reinterpret_cast<const uint4*>(s_meta + nb);
+        const uint32_t raw[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-            const uint32_t nb = w0 + (uint32_t)c4 * 128u + (uint32_t)lane * 4u;
-            uint32_t h = live_heights(*reinterpret_cast<const uint32_t*>(s_meta + nb));
-            if (nb + 4u > cnt) {  // nodes past the storage layer's end are absent
-                const uint32_t keep = nb >= cnt ? 0u : (cnt - nb);
+        for (int k = 0; k < 4; ++k) {
+            uint32_t h = live_heights(raw[k]);
+            const uint32_t first = nb + 4u * k;  // nodes past the storage layer's end are absent
+            if (first + 4u > cnt) {
+                const uint32_t keep = first >= cnt ? 0u : (cnt - first);
                 h &= keep ? (0xFFFFFFFFu >> (8u * (4u - keep))) : 0u;
             }
-            hw[c4] = h;
+            hw[k] = h;
         }
-        // Phase 1: the warp's node count per level (lane i holds level Lb + i).
-        {
-            uint32_t c = 0;
-            for (uint32_t l = Lb; l <= H; ++l) {
-                uint32_t nl = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) nl += __popc(members(hw[k], l));
-                const uint32_t tot = __reduce_add_sync(0xffffffffu, nl);
-                if ((uint32_t)lane == l - Lb) c = tot;
-                if (tot == 0) break;
-            }
-            s_wcnt[warp][lane] = c;
-        }
-        __syncthreads();
-        if (!s_ok) break;
-        // first position of this warp in level Lb + lane
-        uint32_t run = 0;
-        if (Lb + (uint32_t)lane <= H) {
-            run = a.loff[(size_t)lane * ntiles + tile];
-            for (int w = 0; w < warp; ++w) run += s_wcnt[w][lane];
-        }
-        // Phase 2: per chunk, level by level until the chunk has no member.
-#pragma unroll 1
-        for (int c4 = 0; c4 < 4; ++c4) {
-            const uint32_t h = hw[c4];
-            const uint32_t nb = w0 + (uint32_t)c4 * 128u + (uint32_t)lane * 4u;
-            uint32_t prev_mk = 0, prev_first = 0;
-            for (uint32_t l = Lb; l <= H; ++l) {
-                const uint32_t mk = members(h, l);  // bit 8k+7 set: node nb+k is in level l
-                const uint32_t cl = __popc(mk);
-                uint32_t incl = cl;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-                if (total == 0) break;
-                const uint32_t first = __shfl_sync(0xffffffffu, run, (int)(l - Lb)) + incl - cl;
-                uint32_t j = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if ((mk >> (8 * k + 7)) & 1u) {
-                        const uint32_t p = first + j;
-                        const uint32_t node = nb + (uint32_t)k;
-                        if (p < s_n[l]) {
-                            const uint32_t g = s_base[l] + p;
-                            a.lkeys[g] = s_keys[node];
-                            a.ldown[g] = (l == Lb) ? ts + node
-                                                   : prev_first + __popc(prev_mk & ((1u << (8 * k)) - 1u));
-                        } else {
-                            atomicOr(a.err, kErrBounds);
-                        }
-                        ++j;
-                    }
-                }
-                if ((uint32_t)lane == l - Lb) run += total;
-                prev_mk = mk;
-                prev_first = first;
-            }
-        }
-        __syncthreads();  // buffer b is reused two tiles later
     }
-    if (!s_ok && tid == 0) {
-        // a wait gave up: let any copy still in flight land before the CTA exits
-        mbar_wait_bounded(&s_bar[0], 0, a.err);
-        mbar_wait_bounded(&s_bar[1], 0, a.err);
+    // 1. the warp's count per level
+    uint32_t mine = 0;  // this lane's member count at level Lb
+    {
+        uint32_t c = 0;
+        for (uint32_t l = Lb; l <= H; ++l) {
+            uint32_t nl = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) nl += __popc(members(hw[k], l));
+            if (l == Lb) mine = nl;
+            const uint32_t tot = __reduce_add_sync(0xffffffffu, nl);
+            if ((uint32_t)lane == l - Lb) c = tot;
+            if (tot == 0) break;
+        }
+        s_wcnt[warp][lane] = c;
+    }
+    __syncthreads();
+    if (!s_ok) {
+        if (tid == 0) mbar_wait_bounded(&s_bar, 0, a.err);  // let the copy land
+        return;
+    }
+    uint32_t wbase = 0;  // first position of this warp in level Lb + lane
+    if (Lb + (uint32_t)lane <= H) {
+        wbase = a.loff[(size_t)lane * ntiles + tile];
+        for (int w = 0; w < warp; ++w) wbase += s_wcnt[w][lane];
+    }
+    // 2. level-Lb members in node order
+    uint32_t* list = s_list + warp * kWarpNodes;
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    uint32_t nlist = __shfl_sync(0xffffffffu, incl, 31);
+    {
+        uint32_t w = incl - mine;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t mk = members(hw[k], Lb);
+            while (mk) {
+                const uint32_t bit = __ffs(mk) - 1;
+                list[w++] = nb + 4u * k + (bit >> 3);  // node within the tile
+                mk &= mk - 1;
+            }
+        }
+    }
+    __syncwarp();
+    // 3. emit level after level from the list, compacting it in place
+    const uint32_t lt = lanemask_lt();
+    uint32_t prev_base = 0;
+    for (uint32_t l = Lb; l <= H && nlist > 0; ++l) {
+        const uint32_t base = __shfl_sync(0xffffffffu, wbase, (int)(l - Lb));
+        uint32_t nnext = 0;
+        for (uint32_t j0 = 0; j0 < nlist; j0 += 32u) {
+            const uint32_t j = j0 + (uint32_t)lane;
+            const bool in = j < nlist;
+            const uint32_t e = in ? list[j] : 0u;  // node | index in level l - 1 << 16
+            const uint32_t node = e & 0xFFFFu;
+            const uint32_t h = in ? (uint32_t)(s_meta[node] & kHeightMask) : 0u;
+            const uint32_t up = __ballot_sync(0xffffffffu, in && h > l);
+            __syncwarp();  // every lane has read its entry before the list is overwritten
+            if (in) {
+                const uint32_t p = base + j;
+                if (p < s_n[l]) {
+                    const uint32_t g = s_base[l] + p;
+                    a.lkeys[g] = s_keys[node];
+                    a.ldown[g] = (l == Lb) ? ts + node : prev_base + (e >> 16);
+                } else {
+                    atomicOr(a.err, kErrBounds);
+                }
+                if (h > l) list[nnext + __popc(up & lt)] = node | (j << 16);
+            }
+            nnext += __popc(up);
+            __syncwarp();
+        }
+        nlist = nnext;
+        prev_base = base;
     }
 }
 
@@ -606,8 +613,9 @@ cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s) {
 
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
     (void)epoch;
+    (void)num_sms;
     static bool attr_set = false;
-    const int dyn = (int)(2 * kBufBytes);
+    const int dyn = (int)(kKeyBytes + kMetaBytes + 8 * kWarpNodes * 4);
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_rebuild_write, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
@@ -616,8 +624,7 @@ cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s
     const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
     k_rebuild_count<<<(tiles + 7) / 8, 256, 0, s>>>(a);
     k_rebuild_scan<<<kLevelSlots - 2, 1024, 0, s>>>(a);
-    const uint32_t cap = 3u * (uint32_t)num_sms;
-    k_rebuild_write<<<(int)(tiles < cap ? tiles : cap), kThreads, dyn, s>>>(a);
+    k_rebuild_write<<<tiles, kThreads, dyn, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -56,6 +56,9 @@ __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ ops, c
             mn[d] = max(mn[d], 255u - b);
         }
     }
+    __shared__ uint32_t s_red[17];
+    if (threadIdx.x < 17) s_red[threadIdx.x] = 0;
+    __syncthreads();
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         mx[d] = __reduce_max_sync(0xffffffffu, mx[d]);
@@ -63,13 +66,18 @@ __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ ops, c
     }
     invalid = __reduce_add_sync(0xffffffffu, invalid);
     if ((threadIdx.x & 31) == 0) {
-        if (invalid) atomicAdd(&bm->invalid, invalid);
+        if (invalid) atomicAdd(&s_red[16], invalid);
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
-            atomicMax(&bm->bmax[d], mx[d]);
-            atomicMax(&bm->bnmin[d], mn[d]);
+            atomicMax(&s_red[d], mx[d]);
+            atomicMax(&s_red[8 + d], mn[d]);
         }
     }
+    __syncthreads();
+    // one global atomic per byte per CTA
+    if (threadIdx.x < 8) atomicMax(&bm->bmax[threadIdx.x], s_red[threadIdx.x]);
+    else if (threadIdx.x < 16) atomicMax(&bm->bnmin[threadIdx.x - 8], s_red[threadIdx.x]);
+    else if (threadIdx.x == 16 && s_red[16]) atomicAdd(&bm->invalid, s_red[16]);
 }
 
 // Pass plan: the passes whose byte varies (at least one), ping-ponging so the last
