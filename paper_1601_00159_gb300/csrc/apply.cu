@@ -17,9 +17,11 @@
 //
 // The max-scan is split across kernels so no tile ever waits on another: the descent
 // already walks the sorted batch and leaves each 2048-query tile's maximum e in
-// tile_max (one atomicMax per warp); k_apply_scan turns those into exclusive tile
-// prefixes; k_apply is then fully data-parallel. New nodes are staged per tile and
-// packed in key order by k_new_scan + k_new_pack.
+// tile_max; k_apply_scan turns those into exclusive tile prefixes; k_apply is then
+// fully data-parallel. The descent stored one result per local run head of the tile
+// (a query whose key differs from the previous one, and the tile's first query), so a
+// query's storage-layer state is found at its run head's index among those heads.
+// New nodes are staged per tile and packed in key order by k_new_scan + k_new_pack.
 
 #include "common.cuh"
 
@@ -84,6 +86,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
     uint64_t key[kItems];
     uint32_t pay[kItems];
     uint32_t e[kItems];
+    uint32_t dres[kItems];
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const uint32_t i = base + k;
@@ -106,6 +109,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
     }
     const uint32_t texcl = block_excl_max<kThreads>(agg, s_tmp, nullptr);
     uint32_t M = max(a.tile_pref[tile], texcl);
+    // index of each query's local run head among the tile's local heads
+    uint32_t lh = 0, nh = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint32_t i = base + k;
+        const uint64_t prev = k ? key[k - 1] : kprev;
+        const bool local = i < qv && (i == 0 || key[k] != prev || (tid == 0 && k == 0));
+        lh |= (local ? 1u : 0u) << k;
+        nh += local ? 1u : 0u;
+    }
+    uint32_t hidx = block_excl_sum<kThreads>(nh, s_tmp, nullptr) + tile * kApplyTile;  // next head's slot
     uint32_t new_here = 0, new_mask = 0;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
@@ -114,6 +128,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
         const uint32_t minc = max(M, e[k]);
         M = minc;
         e[k] = minc;  // keep the inclusive value for the new-node pass
+        const uint32_t dj = hidx + ((lh >> k) & 1u) - 1u;  // this query's run head's result
+        hidx += (lh >> k) & 1u;
+        dres[k] = dj;
         if (i >= n) continue;
         const uint32_t seq = pay[k] & kSeqMask;
         if (i >= qv) {
@@ -122,7 +139,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
         }
         const uint64_t prev = k ? key[k - 1] : kprev;
         const bool head = (i == 0 || key[k] != prev);
-        const uint8_t fl = a.flags[i];
+        const uint8_t fl = a.flags[dj];
         const bool exists = fl & 1u, live0 = (fl & 2u) != 0;
         bool pl;
         uint64_t pv;
@@ -133,7 +150,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
             pv = pl ? a.uvals[pj & kSeqMask] : 0ull;
         } else {
             pl = live0;
-            pv = live0 ? a.val0[i] : 0ull;
+            pv = live0 ? a.val0[dj] : 0ull;
         }
         store_result(a.results, seq, pv, pl ? PI_R_PRESENT : PI_R_ABSENT);
 
@@ -144,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
         const uint32_t pw = (jw == i) ? pay[k] : a.sp[jw];
         const bool fin_live = (pw >> 30) == 1u;
         if (exists) {
-            const uint32_t r = a.loc[i] - 1u;
+            const uint32_t r = a.loc[dj] - 1u;
             const uint8_t mt = SM[r];
             const uint32_t h = mt & kHeightMask;
             if (fin_live) {
@@ -183,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
             const uint32_t h = tower_height(key[k], a.hp);
             a.stage.keys[so + slot] = key[k];
             a.stage.vals[so + slot] = a.uvals[pw & kSeqMask];
-            a.stage.loc[so + slot] = a.loc[i];
+            a.stage.loc[so + slot] = a.loc[dres[k]];
             a.stage.height[so + slot] = (uint8_t)h;
             ++slot;
             atomicAdd(&s_changes, 1u);

@@ -129,12 +129,22 @@ __device__ __forceinline__ int32_t smem_rank(const uint64_t* K, uint32_t n, uint
     return (int32_t)lo - 1;
 }
 
-__global__ void __launch_bounds__(kThreads, 6) k_descend(DescendArgs a) {
+// Persistent CTAs over tiles of kApplyTile sorted queries (tile = blockIdx.x + k *
+// gridDim.x). Per tile, the CTA
+//  1. marks the tile's local run heads (a query whose key differs from the previous
+//     query's, and the tile's first query) and compacts their keys into shared
+//     memory -- equal keys are searched once per tile;
+//  2. computes the tile's maximum ownership marker e (see the apply kernel);
+//  3. descends the distinct keys with full warps (32 per step) and writes one result
+//     per distinct key at tile * kApplyTile + its index among the tile's local heads.
+__global__ void __launch_bounds__(kThreads, 4) k_descend(DescendArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
     uint32_t* s_d = reinterpret_cast<uint32_t*>(s_dyn + (kSmemTopMax + kPad) * sizeof(uint64_t));
+    uint64_t* s_q = reinterpret_cast<uint64_t*>(s_dyn + (kSmemTopMax + kPad) * 12);  // kApplyTile keys
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
+    __shared__ uint32_t s_tmp[33];
     __shared__ int s_fail;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -142,7 +152,9 @@ __global__ void __launch_bounds__(kThreads, 6) k_descend(DescendArgs a) {
     if (block_sees_error(&m->error)) return;
     const uint32_t H = m->H, Lb = m->Lb, Ls = m->Ls, E = m->smem_entries;
     const uint32_t size = m->size, cur = m->cur;
-    const uint32_t qv = a.n - a.bm->invalid;
+    const uint32_t n = a.n;
+    const uint32_t qv = n - a.bm->invalid;
+    const uint32_t ntiles = (n + kApplyTile - 1) / kApplyTile;
     if (tid < kLevelSlots) {
         s_base[tid] = m->base[tid];
         s_n[tid] = m->n[tid];
@@ -167,66 +179,79 @@ __global__ void __launch_bounds__(kThreads, 6) k_descend(DescendArgs a) {
     } else {
         __syncthreads();
     }
-
     const uint64_t* SK = a.st.keys[cur];
     const uint8_t* SM = a.st.meta[cur];
     const uint64_t* SV = a.st.vals[cur];
-    for (uint32_t chunk = blockIdx.x * kWarps + warp; chunk * 32u < qv; chunk += gridDim.x * kWarps) {
-        const uint32_t i = chunk * 32u + lane;
-        const bool active = i < qv;
-        const uint64_t q = active ? a.sk[i] : kMaxKey;
-        const uint64_t qp = __shfl_up_sync(kFull, q, 1);
-        const bool leader = active && (lane == 0 || qp != q);
-        const uint32_t lead = __ballot_sync(kFull, leader);
-        {
-            // run markers for the ownership scan: e = 2i+3 for a write, 2i+2 for a run
-            // head, else 0; the tile's maximum feeds the scan across apply tiles
-            const uint32_t op = active ? (a.sp[i] >> 30) : 0u;
-            const uint64_t before = (lane == 0) ? (i > 0 ? a.sk[i - 1] : kMaxKey) : qp;
-            const bool head = active && (i == 0 || before != q);
-            const uint32_t e = (active && (op == 1u || op == 2u)) ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
-            const uint32_t wmax = __reduce_max_sync(kFull, e);
-            if (lane == 0 && wmax) atomicMax(&a.tile_max[i / kApplyTile], wmax);
+    constexpr int kItems = kApplyTile / kThreads;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // 1 + 2: local heads and the ownership marker of this thread's 8 queries
+        const uint32_t base = tile * kApplyTile + tid * kItems;
+        uint64_t key[kItems];
+        uint32_t lh = 0, emax = 0, nh = 0;
+        const uint64_t kprev = (base > 0 && base - 1 < qv) ? a.sk[base - 1] : kMaxKey;
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const uint32_t i = base + k;
+            const bool valid = i < qv;
+            key[k] = valid ? a.sk[i] : kMaxKey;
+            const uint32_t op = valid ? (a.sp[i] >> 30) : 0u;
+            const uint64_t prev = k ? key[k - 1] : kprev;
+            const bool head = valid && (i == 0 || key[k] != prev);
+            const bool local = valid && (head || (tid == 0 && k == 0));
+            const uint32_t e = (valid && (op == 1u || op == 2u)) ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
+            emax = max(emax, e);
+            lh |= (local ? 1u : 0u) << k;
+            nh += local ? 1u : 0u;
         }
-        uint32_t lo = 0;
-        int32_t r = -1;
-        uint32_t dn = 0;
-        uint64_t kr = 0;
-        int top = (int)H;
-        if (Ls <= H) {
-            // The pinned levels Ls..H are in shared memory. Level Ls holds every key of
-            // the levels above it, so the entry the walk down those levels would reach
-            // on level Ls -- its largest key <= q -- is found by one binary search.
-            if (leader) {
-                r = smem_rank(s_k + s_base[Ls], s_n[Ls], q);
-                lo = (r >= 0) ? s_d[s_base[Ls] + r] : 0u;
+        uint32_t tmax;
+        block_excl_max<kThreads>(emax, s_tmp, &tmax);
+        if (tid == 0) a.tile_max[tile] = tmax;
+        uint32_t nq;
+        uint32_t w = block_excl_sum<kThreads>(nh, s_tmp, &nq);
+#pragma unroll
+        for (int k = 0; k < kItems; ++k)
+            if ((lh >> k) & 1u) s_q[w++] = key[k];
+        __syncthreads();
+        // 3. descend the tile's distinct keys, 32 per warp step
+        for (uint32_t c = (uint32_t)warp * 32u; c < nq; c += kThreads) {
+            const uint32_t j = c + (uint32_t)lane;
+            const bool active = j < nq;
+            const uint64_t q = active ? s_q[j] : kMaxKey;
+            uint32_t lo = 0;
+            int32_t r = -1;
+            uint32_t dn = 0;
+            uint64_t kr = 0;
+            int top = (int)H;
+            if (Ls <= H) {
+                // Pinned levels Ls..H are in shared memory; level Ls holds every key of
+                // the levels above it, so the entry the walk down those levels reaches
+                // on level Ls -- its largest key <= q -- is found by one binary search.
+                if (active) {
+                    r = smem_rank(s_k + s_base[Ls], s_n[Ls], q);
+                    lo = (r >= 0) ? s_d[s_base[Ls] + r] : 0u;
+                }
+                top = (int)Ls - 1;
             }
-            top = (int)Ls - 1;
-        }
-        for (int l = top; l >= (int)Lb; --l) {
-            const uint64_t* K = a.lkeys + s_base[l];
-            const uint32_t* D = a.ldown + s_base[l];
+            for (int l = top; l >= (int)Lb; --l) {
+                r = -1;
+                dn = 0;
+                warp_search<true>(a.lkeys + s_base[l], a.ldown + s_base[l], lo, s_n[l], q, active, r, dn, kr, a.err);
+                if (active) lo = (r >= 0) ? dn : 0u;
+            }
             r = -1;
-            dn = 0;
-            warp_search<true>(K, D, lo, s_n[l], q, leader, r, dn, kr, a.err);
-            if (leader) lo = (r >= 0) ? dn : 0u;
+            kr = 0;
+            warp_search<false>(SK, nullptr, lo, size, q, active, r, dn, kr, a.err);
+            if (active) {
+                const bool exists = r >= 0 && kr == q;
+                const uint8_t meta = exists ? SM[r] : (uint8_t)0;
+                const bool live = exists && !(meta & kTomb);
+                const uint32_t o = tile * kApplyTile + j;
+                a.loc[o] = (uint32_t)(r + 1);
+                a.flags[o] = (uint8_t)((exists ? 1u : 0u) | (live ? 2u : 0u));
+                a.val0[o] = live ? SV[r] : 0ull;
+            }
         }
-        r = -1;
-        kr = 0;
-        warp_search<false>(SK, nullptr, lo, size, q, leader, r, dn, kr, a.err);
-        const bool exists = leader && r >= 0 && kr == q;
-        const uint8_t meta = exists ? SM[r] : (uint8_t)0;
-        const bool live = exists && !(meta & kTomb);
-        const uint64_t v = live ? SV[r] : 0ull;
-        const int src = 31 - __clz(lead & lanemask_le());
-        const int32_t r_l = __shfl_sync(kFull, r, src);
-        const uint32_t f_l = __shfl_sync(kFull, (exists ? 1u : 0u) | (live ? 2u : 0u), src);
-        const uint64_t v_l = __shfl_sync(kFull, v, src);
-        if (active) {
-            a.loc[i] = (uint32_t)(r_l + 1);
-            a.flags[i] = (uint8_t)f_l;
-            a.val0[i] = v_l;
-        }
+        __syncthreads();  // s_q is reused by the next tile
     }
 }
 
@@ -234,17 +259,15 @@ __global__ void __launch_bounds__(kThreads, 6) k_descend(DescendArgs a) {
 
 cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
     static bool attr_set = false;
-    const int dyn = (int)((kSmemTopMax + kPad) * (sizeof(uint64_t) + sizeof(uint32_t)));
+    const int dyn = (int)((kSmemTopMax + kPad) * (sizeof(uint64_t) + sizeof(uint32_t)) + kApplyTile * sizeof(uint64_t));
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_descend, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (a.n == 0) return cudaSuccess;
-    uint32_t warps_needed = (a.n + 31) / 32;
-    uint32_t blocks = (warps_needed + kWarps - 1) / kWarps, cap = (uint32_t)num_sms * 6u;
-    int grid = (int)(blocks < cap ? blocks : cap);
-    k_descend<<<grid, kThreads, dyn, s>>>(a);
+    const uint32_t tiles = (a.n + kApplyTile - 1) / kApplyTile, cap = (uint32_t)num_sms * 4u;
+    k_descend<<<(int)(tiles < cap ? tiles : cap), kThreads, dyn, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -298,10 +298,29 @@ __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
     const uint32_t per = (ntiles + 1023u) / 1024u;
     const uint32_t t0 = min(threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
     uint32_t sum = 0;
-    for (uint32_t t = t0; t < t1; ++t) sum += c[t];
+    uint32_t t = t0;
+    for (; t + 8u <= t1; t += 8u) {  // eight independent loads per step
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = c[t + k];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sum += v[k];
+    }
+    for (; t < t1; ++t) sum += c[t];
     uint32_t tot;
     uint32_t run = block_excl_sum<1024>(sum, s_tmp, &tot);
-    for (uint32_t t = t0; t < t1; ++t) {
+    t = t0;
+    for (; t + 8u <= t1; t += 8u) {
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = c[t + k];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            o[t + k] = run;
+            run += v[k];
+        }
+    }
+    for (; t < t1; ++t) {
         const uint32_t v = c[t];
         o[t] = run;
         run += v;
