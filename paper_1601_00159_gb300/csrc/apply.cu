@@ -109,17 +109,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
     }
     const uint32_t texcl = block_excl_max<kThreads>(agg, s_tmp, nullptr);
     uint32_t M = max(a.tile_pref[tile], texcl);
-    // index of each query's local run head among the tile's local heads
+    // index of each query's local run head among its 256-query sub-tile's local heads
+    // (a warp's 8 x 32 queries are exactly one descent sub-tile)
     uint32_t lh = 0, nh = 0;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const uint32_t i = base + k;
         const uint64_t prev = k ? key[k - 1] : kprev;
-        const bool local = i < qv && (i == 0 || key[k] != prev || (tid == 0 && k == 0));
+        const bool local = i < qv && (i == 0 || key[k] != prev || (i % kSubTile) == 0);
         lh |= (local ? 1u : 0u) << k;
         nh += local ? 1u : 0u;
     }
-    uint32_t hidx = block_excl_sum<kThreads>(nh, s_tmp, nullptr) + tile * kApplyTile;  // next head's slot
+    uint32_t hidx;
+    {
+        const int lane = tid & 31;
+        uint32_t incl = nh;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        hidx = incl - nh + (base / kSubTile) * kSubTile;  // next head's slot
+    }
     uint32_t new_here = 0, new_mask = 0;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {

@@ -16,6 +16,7 @@ constexpr uint32_t kSmemTopMax = 2048;  // index entries staged in shared memory
 constexpr uint32_t kPad = 64;           // readable entries past every array's end
 constexpr uint32_t kSortTile = 2048;    // elements per radix-sort tile
 constexpr uint32_t kApplyTile = 2048;   // sorted queries per apply tile
+constexpr uint32_t kSubTile = 256;      // sorted queries per descent warp step (one apply warp)
 
 // Sticky error bits in DevMeta::error.
 constexpr uint32_t kErrTimeout = 1u;  // a bounded wait gave up

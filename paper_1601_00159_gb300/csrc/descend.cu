@@ -129,22 +129,23 @@ __device__ __forceinline__ int32_t smem_rank(const uint64_t* K, uint32_t n, uint
     return (int32_t)lo - 1;
 }
 
-// Persistent CTAs over tiles of kApplyTile sorted queries (tile = blockIdx.x + k *
-// gridDim.x). Per tile, the CTA
-//  1. marks the tile's local run heads (a query whose key differs from the previous
-//     query's, and the tile's first query) and compacts their keys into shared
-//     memory -- equal keys are searched once per tile;
-//  2. computes the tile's maximum ownership marker e (see the apply kernel);
-//  3. descends the distinct keys with full warps (32 per step) and writes one result
-//     per distinct key at tile * kApplyTile + its index among the tile's local heads.
-__global__ void __launch_bounds__(kThreads, 4) k_descend(DescendArgs a) {
+// Persistent warps over sub-tiles of kSubTile (256) sorted queries; warp-global index
+// gw = blockIdx.x * 8 + warp takes sub-tiles gw, gw + 8 * gridDim.x, ... Per sub-tile
+// the warp, without block barriers,
+//  1. marks the local run heads (a query whose key differs from the previous query's,
+//     and the sub-tile's first query) and compacts their keys, in order, into its own
+//     shared-memory list -- equal keys are searched once;
+//  2. folds the sub-tile's ownership markers e (see the apply kernel) into its apply
+//     tile's maximum;
+//  3. descends the list with full warps (32 keys per step) and writes one result per
+//     local head at sub_base + its index among the sub-tile's local heads.
+__global__ void __launch_bounds__(kThreads, 5) k_descend(DescendArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
     uint32_t* s_d = reinterpret_cast<uint32_t*>(s_dyn + (kSmemTopMax + kPad) * sizeof(uint64_t));
-    uint64_t* s_q = reinterpret_cast<uint64_t*>(s_dyn + (kSmemTopMax + kPad) * 12);  // kApplyTile keys
+    uint64_t* s_qall = reinterpret_cast<uint64_t*>(s_dyn + (kSmemTopMax + kPad) * 12);  // 8 x kSubTile keys
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
-    __shared__ uint32_t s_tmp[33];
     __shared__ int s_fail;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_descend(DescendArgs a) {
     const uint32_t size = m->size, cur = m->cur;
     const uint32_t n = a.n;
     const uint32_t qv = n - a.bm->invalid;
-    const uint32_t ntiles = (n + kApplyTile - 1) / kApplyTile;
+    const uint32_t nsub = (n + kSubTile - 1) / kSubTile;
     if (tid < kLevelSlots) {
         s_base[tid] = m->base[tid];
         s_n[tid] = m->n[tid];
@@ -182,38 +183,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_descend(DescendArgs a) {
     const uint64_t* SK = a.st.keys[cur];
     const uint8_t* SM = a.st.meta[cur];
     const uint64_t* SV = a.st.vals[cur];
-    constexpr int kItems = kApplyTile / kThreads;
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        // 1 + 2: local heads and the ownership marker of this thread's 8 queries
-        const uint32_t base = tile * kApplyTile + tid * kItems;
-        uint64_t key[kItems];
-        uint32_t lh = 0, emax = 0, nh = 0;
-        const uint64_t kprev = (base > 0 && base - 1 < qv) ? a.sk[base - 1] : kMaxKey;
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            const uint32_t i = base + k;
+    uint64_t* s_q = s_qall + warp * kSubTile;
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t sub = blockIdx.x * (kThreads / 32) + warp; sub < nsub; sub += gridDim.x * (kThreads / 32)) {
+        const uint32_t sb = sub * kSubTile;
+        // 1 + 2: striped over the sub-tile: element sb + 32 k + lane
+        uint32_t nq = 0, emax = 0;
+        uint64_t carry = (sb > 0 && sb - 1 < qv) ? a.sk[sb - 1] : kMaxKey;  // key before the element
+#pragma unroll 2
+        for (int k = 0; k < kSubTile / 32; ++k) {
+            const uint32_t i = sb + (uint32_t)k * 32u + (uint32_t)lane;
             const bool valid = i < qv;
-            key[k] = valid ? a.sk[i] : kMaxKey;
+            const uint64_t q = valid ? a.sk[i] : kMaxKey;
             const uint32_t op = valid ? (a.sp[i] >> 30) : 0u;
-            const uint64_t prev = k ? key[k - 1] : kprev;
-            const bool head = valid && (i == 0 || key[k] != prev);
-            const bool local = valid && (head || (tid == 0 && k == 0));
+            uint64_t prev = __shfl_up_sync(0xffffffffu, q, 1);
+            if (lane == 0) prev = carry;
+            carry = __shfl_sync(0xffffffffu, q, 31);
+            const bool head = valid && (i == 0 || q != prev);
+            const bool local = valid && (head || (k == 0 && lane == 0));
             const uint32_t e = (valid && (op == 1u || op == 2u)) ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
             emax = max(emax, e);
-            lh |= (local ? 1u : 0u) << k;
-            nh += local ? 1u : 0u;
+            const uint32_t b = __ballot_sync(0xffffffffu, local);
+            if (local) s_q[nq + __popc(b & lt)] = q;
+            nq += __popc(b);
         }
-        uint32_t tmax;
-        block_excl_max<kThreads>(emax, s_tmp, &tmax);
-        if (tid == 0) a.tile_max[tile] = tmax;
-        uint32_t nq;
-        uint32_t w = block_excl_sum<kThreads>(nh, s_tmp, &nq);
-#pragma unroll
-        for (int k = 0; k < kItems; ++k)
-            if ((lh >> k) & 1u) s_q[w++] = key[k];
-        __syncthreads();
-        // 3. descend the tile's distinct keys, 32 per warp step
-        for (uint32_t c = (uint32_t)warp * 32u; c < nq; c += kThreads) {
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        if (lane == 0 && emax) atomicMax(&a.tile_max[sb / kApplyTile], emax);
+        __syncwarp();
+        // 3. descend the sub-tile's distinct keys, 32 per step
+        for (uint32_t c = 0; c < nq; c += 32u) {
             const uint32_t j = c + (uint32_t)lane;
             const bool active = j < nq;
             const uint64_t q = active ? s_q[j] : kMaxKey;
@@ -245,13 +243,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_descend(DescendArgs a) {
                 const bool exists = r >= 0 && kr == q;
                 const uint8_t meta = exists ? SM[r] : (uint8_t)0;
                 const bool live = exists && !(meta & kTomb);
-                const uint32_t o = tile * kApplyTile + j;
+                const uint32_t o = sb + j;
                 a.loc[o] = (uint32_t)(r + 1);
                 a.flags[o] = (uint8_t)((exists ? 1u : 0u) | (live ? 2u : 0u));
                 a.val0[o] = live ? SV[r] : 0ull;
             }
         }
-        __syncthreads();  // s_q is reused by the next tile
+        __syncwarp();  // the list is reused by the next sub-tile
     }
 }
 
@@ -259,15 +257,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_descend(DescendArgs a) {
 
 cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
     static bool attr_set = false;
-    const int dyn = (int)((kSmemTopMax + kPad) * (sizeof(uint64_t) + sizeof(uint32_t)) + kApplyTile * sizeof(uint64_t));
+    const int dyn = (int)((kSmemTopMax + kPad) * (sizeof(uint64_t) + sizeof(uint32_t)) + 8 * kSubTile * sizeof(uint64_t));
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_descend, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (a.n == 0) return cudaSuccess;
-    const uint32_t tiles = (a.n + kApplyTile - 1) / kApplyTile, cap = (uint32_t)num_sms * 4u;
-    k_descend<<<(int)(tiles < cap ? tiles : cap), kThreads, dyn, s>>>(a);
+    const uint32_t blocks = ((a.n + kSubTile - 1) / kSubTile + 7) / 8, cap = (uint32_t)num_sms * 5u;
+    k_descend<<<(int)(blocks < cap ? blocks : cap), kThreads, dyn, s>>>(a);
     return cudaGetLastError();
 }
 
