@@ -71,10 +71,18 @@ typedef struct {
                                     re-laid-out or the updates since the last rebuild
                                     exceed rebuild_threshold_pct percent of its size. */
     uint32_t rebuild_threshold_pct; /* policy 1 only; default 15 (Section 6) */
-    uint32_t smem_top_entries;   /* index entries staged in shared memory (<= 4096) */
+    uint32_t smem_top_entries;   /* cap on the index entries staged in shared memory by the
+                                    descent (default and maximum 2048); smaller values
+                                    pin fewer top levels */
     uint64_t storage_capacity;   /* initial storage-layer capacity, in nodes */
     uint64_t index_capacity;     /* initial index-layer capacity, in entries */
+    uint32_t test_flags;         /* PI_TEST_*: alternative code paths for tests; 0 in use */
+    uint32_t reserved;
 } pi_config_t;
+
+/* test_flags bit: give only the lowest index level a launch of its own in the
+ * level-synchronous descent, so every other level takes the in-kernel walk. */
+#define PI_TEST_WALK_LEVELS 1u
 
 /*
  * pi_create -- bulk-build an index from n (key, value) pairs (Section 3.1: the index

@@ -16,11 +16,12 @@
 //    is not in the storage layer and ends up present (Algorithm 4, insertNode).
 //
 // The max-scan is split across kernels so no tile ever waits on another: the descent
-// already walks the sorted batch and leaves each 2048-query tile's maximum e in
-// tile_max; k_apply_scan turns those into exclusive tile prefixes; k_apply is then
-// fully data-parallel. The descent stored one result per local run head of the tile
-// (a query whose key differs from the previous one, and the tile's first query), so a
-// query's storage-layer state is found at its run head's index among those heads.
+// already walks the sorted batch, leaves each 2048-query tile's maximum e in tile_max
+// and turns those into exclusive tile prefixes (tile_pref); k_apply is then
+// fully data-parallel. The descent stored one result per distinct key -- per local
+// run head (a query whose key differs from the previous one, and the first query of
+// every 256-query sub-tile) in sorted order -- so a query's storage-layer state is
+// found at its run head's dense index.
 // New nodes are staged per tile and packed in key order by k_new_scan + k_new_pack.
 
 #include "common.cuh"
@@ -39,26 +40,6 @@ __device__ __forceinline__ void store_result(pi_result_t* res, uint32_t seq, uin
     w.z = st;
     w.w = 0u;
     *reinterpret_cast<uint4*>(res + seq) = w;
-}
-
-// Exclusive max over tiles of tile_max -> tile_pref (one CTA).
-__global__ void __launch_bounds__(1024) k_apply_scan(ApplyArgs a) {
-    __shared__ uint32_t s_tmp[33];
-    __shared__ uint32_t s_carry;
-    if (block_sees_error(&a.m->error)) return;
-    const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (uint32_t b0 = 0; b0 < ntiles; b0 += 1024) {
-        const uint32_t i = b0 + threadIdx.x;
-        const uint32_t v = i < ntiles ? a.tile_max[i] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_excl_max<1024>(v, s_tmp, &tot);
-        if (i < ntiles) a.tile_pref[i] = max(s_carry, ex);
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry = max(s_carry, tot);
-        __syncthreads();
-    }
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
@@ -129,7 +110,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        hidx = incl - nh + (base / kSubTile) * kSubTile;  // next head's slot
+        hidx = incl - nh + a.sub_pref[base / kSubTile];  // dense index of the next head
     }
     uint32_t new_here = 0, new_mask = 0;
 #pragma unroll
@@ -274,8 +255,7 @@ cudaError_t launch_apply(const ApplyArgs& a, uint32_t& epoch, cudaStream_t s, in
     (void)num_sms;
     if (a.n == 0) return cudaSuccess;
     const uint32_t tiles = (a.n + kApplyTile - 1) / kApplyTile;
-    k_apply_scan<<<1, 1024, 0, s>>>(a);
-    k_apply<<<tiles, kThreads, 0, s>>>(a);
+    k_apply<<<tiles, kThreads, 0, s>>>(a);  // tile prefixes come from the descent's scan
     k_new_scan<<<1, 1024, 0, s>>>(a);
     k_new_pack<<<tiles, kThreads, 0, s>>>(a);
     return cudaGetLastError();

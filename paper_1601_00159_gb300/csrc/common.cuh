@@ -67,7 +67,7 @@ struct BatchMeta {
     uint32_t index_dirty;        // level membership changed
     uint32_t rebuild;            // the rebuild runs in this batch
     uint32_t changes;            // storage nodes whose liveness changed or that were added
-    uint32_t pad_[1];
+    uint32_t distinct;           // distinct keys of the batch (local run heads)
     uint32_t bmax[8];            // per key byte: its maximum over the batch
     uint32_t bnmin[8];           // per key byte: 255 - its minimum over the batch
     SortPlan plan;
@@ -432,8 +432,15 @@ struct DescendArgs {
     const uint64_t* sk;  // sorted keys
     const uint32_t* sp;  // sorted payload (op << 30 | arrival index)
     uint32_t* tile_max;  // per-apply-tile max of the run markers e_i (atomicMax)
+    uint32_t* tile_pref; // per-apply-tile exclusive max prefix
+    uint64_t* hq;        // distinct keys per 256-query sub-tile (holey, sub * 256 + j)
+    uint32_t* sub_cnt;   // distinct keys per sub-tile
+    uint32_t* sub_pref;  // dense index of each sub-tile's first distinct key
+    uint64_t* dq;        // dense distinct keys
+    uint32_t* dlo;       // their current start position on the level being searched
+    int top_launched;    // highest index level given its own launch (see launch_descend)
     const DevMeta* m;
-    const BatchMeta* bm;
+    BatchMeta* bm;
     const uint64_t* lkeys;
     const uint32_t* ldown;
     Storage st;
@@ -461,6 +468,7 @@ struct ApplyArgs {
     uint32_t* tile_max;   // per-tile max run marker (from the descent)
     uint32_t* tile_pref;  // per-tile exclusive prefix (max, then reused for new-node sums)
     uint32_t* tile_new;   // per-tile new-node count
+    const uint32_t* sub_pref;  // dense index of each 256-query sub-tile's first distinct key
     NewNodes stage;       // per-tile staging of new nodes (kApplyTile slots per tile)
     uint32_t* lcnt;  // per-level per-tile live counts (see RebuildArgs)
     uint32_t lstride;
@@ -487,6 +495,7 @@ struct RebuildArgs {
     uint32_t threshold_pct;
     uint32_t force_rebuild;  // 1: rebuild regardless; 2: initial build (not a batch)
     uint32_t st_cap;         // storage capacity (nodes, padding excluded)
+    uint32_t smem_top;       // cap on pinned entries (<= kSmemTopMax)
     uint32_t* err;
 };
 cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);

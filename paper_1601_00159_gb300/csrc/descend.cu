@@ -1,27 +1,33 @@
 // K2 + K3: descend the index layer to each query's interception (Algorithm 2,
 // Definition 4), then locate the query's key in the storage layer (Algorithm 4's
-// getNode), for every query of the sorted batch.
+// getNode), for every distinct key of the sorted batch.
 //
 // Layout (built by the rebuild): all index levels live in one key array and one down
 // array, top level first; level l is [base[l], base[l] + n[l]) followed by a sentinel
 // entry with key 2^64-1. down[i] is the position of the same key in the level below
 // (for the lowest built level: its storage-layer position), so the keys of level l-1
 // that lie between two consecutive keys of level l are exactly
-// [down[r], down[r + 1]). The top levels are copied once per CTA into shared memory
-// with one TMA bulk copy each for keys and downs.
+// [down[r], down[r + 1]).
 //
-// Per level, a warp holds 32 consecutive sorted queries (the paper's query group,
-// Section 4.4.3, processed level by level). Lanes whose key equals the previous lane's
-// key do not search: they take their leader's result at the end. Two search forms:
-//  * warp-cooperative (the SIMD-compare analogue of Section 3.2.1): when the leaders'
-//    start positions lie within 16 entries, the warp loads one 32-key segment with one
-//    coalesced access, and every lane finds the rank of the largest segment key <= its
-//    query by a five-step binary search over the lanes (shuffles); __ballot_sync
-//    locates the level's sentinel inside the segment;
-//  * per lane: when the leaders are spread out (the lower levels), each lane scans its
-//    own gap from its start position, four keys (and their downs) per round.
-// Both end at the sentinel, so no bound check is needed on a well-formed level; a
-// defensive bound records kErrBounds instead of reading past it.
+// The descent is level-synchronous over the whole batch -- the paper's group query
+// processing (Section 4.4.3) with the group being every distinct key of the batch:
+//  k_distinct   per 256-query sub-tile, one warp compacts the distinct keys (run
+//               heads, plus the sub-tile's first query) and records their count; it
+//               also folds the ownership markers into the apply tiles' maxima;
+//  k_dscan      one CTA prefixes the sub-tile counts (dense index of every distinct
+//               key) and the apply tiles' maxima;
+//  k_top        the levels pinned in shared memory (copied once per CTA by TMA bulk
+//               copies) are resolved by one binary search of the lowest pinned level,
+//               which holds every key of the levels above it; writes the dense key and
+//               its start position on the next level;
+//  k_level      one launch per remaining index level: every key scans its gap;
+//  k_locate     the storage layer: the node with the largest key <= q, and its state.
+// Each launch is one independent gather per key, so hundreds of thousands of keys are
+// in flight at once. Within a warp, when the 32 keys' start positions lie within 8
+// entries (upper levels: the keys are sorted), the warp loads one 32-key segment with
+// one coalesced access and each lane ranks its key in it by a binary search over the
+// lanes (the SIMD-compare analogue of Section 3.2.1); otherwise each lane scans its own
+// gap four keys (and downs) per round. Both end at the level's sentinel.
 
 #include "common.cuh"
 
@@ -29,7 +35,6 @@ namespace pi {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kFull = 0xffffffffu;
 
 // r = largest index >= lo-1 with K[r] <= q (K[lo] <= q unless lo is the head, 0).
@@ -129,37 +134,91 @@ __device__ __forceinline__ int32_t smem_rank(const uint64_t* K, uint32_t n, uint
     return (int32_t)lo - 1;
 }
 
-// Persistent warps over sub-tiles of kSubTile (256) sorted queries; warp-global index
-// gw = blockIdx.x * 8 + warp takes sub-tiles gw, gw + 8 * gridDim.x, ... Per sub-tile
-// the warp, without block barriers,
-//  1. marks the local run heads (a query whose key differs from the previous query's,
-//     and the sub-tile's first query) and compacts their keys, in order, into its own
-//     shared-memory list -- equal keys are searched once;
-//  2. folds the sub-tile's ownership markers e (see the apply kernel) into its apply
-//     tile's maximum;
-//  3. descends the list with full warps (32 keys per step) and writes one result per
-//     local head at sub_base + its index among the sub-tile's local heads.
-__global__ void __launch_bounds__(kThreads, 5) k_descend(DescendArgs a) {
+// Per 256-query sub-tile (one warp each): local run heads -> holey key list, count,
+// and the apply tile's maximum ownership marker.
+__global__ void __launch_bounds__(kThreads) k_distinct(DescendArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
+    const uint32_t n = a.n;
+    const uint32_t qv = n - a.bm->invalid;
+    const uint32_t sub = blockIdx.x * (kThreads / 32) + warp;
+    const uint32_t nsub = (n + kSubTile - 1) / kSubTile;
+    if (sub >= nsub) return;
+    const uint32_t sb = sub * kSubTile;
+    const uint32_t lt = lanemask_lt();
+    uint32_t nq = 0, emax = 0;
+    uint64_t carry = (sb > 0 && sb - 1 < qv) ? a.sk[sb - 1] : kMaxKey;  // key before the element
+#pragma unroll 2
+    for (int k = 0; k < kSubTile / 32; ++k) {
+        const uint32_t i = sb + (uint32_t)k * 32u + (uint32_t)lane;
+        const bool valid = i < qv;
+        const uint64_t q = valid ? a.sk[i] : kMaxKey;
+        const uint32_t op = valid ? (a.sp[i] >> 30) : 0u;
+        uint64_t prev = __shfl_up_sync(0xffffffffu, q, 1);
+        if (lane == 0) prev = carry;
+        carry = __shfl_sync(0xffffffffu, q, 31);
+        const bool head = valid && (i == 0 || q != prev);
+        const bool local = valid && (head || (k == 0 && lane == 0));
+        const uint32_t e = (valid && (op == 1u || op == 2u)) ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
+        emax = max(emax, e);
+        const uint32_t b = __ballot_sync(0xffffffffu, local);
+        if (local) a.hq[sb + nq + __popc(b & lt)] = q;
+        nq += __popc(b);
+    }
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if (lane == 0) {
+        if (emax) atomicMax(&a.tile_max[sb / kApplyTile], emax);
+        a.sub_cnt[sub] = nq;
+    }
+}
+
+// One CTA: dense index of every sub-tile's first distinct key (exclusive sum of the
+// counts), the number of distinct keys, and the apply tiles' exclusive max prefixes.
+__global__ void __launch_bounds__(1024) k_dscan(DescendArgs a) {
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_carry;
+    if (block_sees_error(&a.m->error)) return;
+    const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < nsub; b0 += 1024) {
+        const uint32_t i = b0 + threadIdx.x;
+        const uint32_t v = i < nsub ? a.sub_cnt[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_sum<1024>(v, s_tmp, &tot);
+        if (i < nsub) a.sub_pref[i] = s_carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.bm->distinct = s_carry;
+    const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < ntiles; b0 += 1024) {
+        const uint32_t i = b0 + threadIdx.x;
+        const uint32_t v = i < ntiles ? a.tile_max[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_max<1024>(v, s_tmp, &tot);
+        if (i < ntiles) a.tile_pref[i] = max(s_carry, ex);
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = max(s_carry, tot);
+        __syncthreads();
+    }
+}
+
+// Dense keys and their start position below the pinned levels. One warp per sub-tile.
+__global__ void __launch_bounds__(kThreads) k_top(DescendArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
     uint32_t* s_d = reinterpret_cast<uint32_t*>(s_dyn + (kSmemTopMax + kPad) * sizeof(uint64_t));
-    uint64_t* s_qall = reinterpret_cast<uint64_t*>(s_dyn + (kSmemTopMax + kPad) * 12);  // 8 x kSubTile keys
     __shared__ __align__(8) uint64_t s_bar;
-    __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
     __shared__ int s_fail;
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const DevMeta* m = a.m;
     if (block_sees_error(&m->error)) return;
-    const uint32_t H = m->H, Lb = m->Lb, Ls = m->Ls, E = m->smem_entries;
-    const uint32_t size = m->size, cur = m->cur;
-    const uint32_t n = a.n;
-    const uint32_t qv = n - a.bm->invalid;
-    const uint32_t nsub = (n + kSubTile - 1) / kSubTile;
-    if (tid < kLevelSlots) {
-        s_base[tid] = m->base[tid];
-        s_n[tid] = m->n[tid];
-    }
+    const uint32_t H = m->H, Ls = m->Ls, Lb = m->Lb, E = m->smem_entries;
+    const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
     if (tid == 0) s_fail = 0;
     if (E > 0) {
         if (tid == 0) {
@@ -177,79 +236,82 @@ __global__ void __launch_bounds__(kThreads, 5) k_descend(DescendArgs a) {
             if (tid == 0) mbar_wait_bounded(&s_bar, 0, a.err);  // let the copy land
             return;
         }
-    } else {
-        __syncthreads();
     }
+    const uint32_t bL = m->base[Ls], nL = m->n[Ls];
+    for (uint32_t sub = blockIdx.x * (kThreads / 32) + warp; sub < nsub; sub += gridDim.x * (kThreads / 32)) {
+        const uint32_t c = a.sub_cnt[sub], d0 = a.sub_pref[sub];
+        for (uint32_t j = (uint32_t)lane; j < c; j += 32u) {
+            const uint64_t q = a.hq[sub * kSubTile + j];
+            uint32_t lo = 0;
+            if (Ls <= H) {
+                const int32_t r = smem_rank(s_k + bL, nL, q);
+                lo = (r >= 0) ? s_d[bL + r] : 0u;
+            }
+            // levels between the pinned ones and the top launched level (only when
+            // the index grew past the host's last view of it): walked here
+            for (int l = (Ls <= H ? (int)Ls - 1 : (int)H); l > a.top_launched && l >= (int)Lb; --l) {
+                int32_t r = -1;
+                uint32_t dn = 0;
+                uint64_t kr = 0;
+                lane_scan<true>(a.lkeys + m->base[l], a.ldown + m->base[l], lo, m->n[l], q, r, dn, kr, a.err);
+                lo = (r >= 0) ? dn : 0u;
+            }
+            a.dq[d0 + j] = q;
+            a.dlo[d0 + j] = lo;
+        }
+    }
+}
+
+// One global index level: every distinct key scans its gap from its start position.
+__global__ void __launch_bounds__(kThreads) k_level(DescendArgs a, int l) {
+    const DevMeta* m = a.m;
+    if (*(volatile const uint32_t*)&m->error) return;  // no barrier in this kernel
+    const uint32_t H = m->H, Lb = m->Lb, Ls = m->Ls;
+    const int top = (Ls <= H) ? (int)Ls - 1 : (int)H;
+    if (l > top || l < (int)Lb) return;  // this level is pinned or not built
+    const uint32_t D = a.bm->distinct;
+    const uint32_t base = m->base[l], lim = m->n[l];
+    const uint64_t* K = a.lkeys + base;
+    const uint32_t* Dn = a.ldown + base;
+    for (uint32_t d0 = blockIdx.x * kThreads; d0 < D; d0 += gridDim.x * kThreads) {
+        const uint32_t d = d0 + threadIdx.x;
+        const bool active = d < D;
+        const uint64_t q = active ? a.dq[d] : kMaxKey;
+        uint32_t lo = active ? a.dlo[d] : 0u;
+        int32_t r = -1;
+        uint32_t dn = 0;
+        uint64_t kr = 0;
+        warp_search<true>(K, Dn, lo, lim, q, active, r, dn, kr, a.err);
+        if (active) a.dlo[d] = (r >= 0) ? dn : 0u;
+    }
+}
+
+// The storage layer: node with the largest key <= q (exists if equal) and its state.
+__global__ void __launch_bounds__(kThreads) k_locate(DescendArgs a) {
+    const DevMeta* m = a.m;
+    if (*(volatile const uint32_t*)&m->error) return;  // no barrier in this kernel
+    const uint32_t size = m->size, cur = m->cur;
     const uint64_t* SK = a.st.keys[cur];
     const uint8_t* SM = a.st.meta[cur];
     const uint64_t* SV = a.st.vals[cur];
-    uint64_t* s_q = s_qall + warp * kSubTile;
-    const uint32_t lt = lanemask_lt();
-    for (uint32_t sub = blockIdx.x * (kThreads / 32) + warp; sub < nsub; sub += gridDim.x * (kThreads / 32)) {
-        const uint32_t sb = sub * kSubTile;
-        // 1 + 2: striped over the sub-tile: element sb + 32 k + lane
-        uint32_t nq = 0, emax = 0;
-        uint64_t carry = (sb > 0 && sb - 1 < qv) ? a.sk[sb - 1] : kMaxKey;  // key before the element
-#pragma unroll 2
-        for (int k = 0; k < kSubTile / 32; ++k) {
-            const uint32_t i = sb + (uint32_t)k * 32u + (uint32_t)lane;
-            const bool valid = i < qv;
-            const uint64_t q = valid ? a.sk[i] : kMaxKey;
-            const uint32_t op = valid ? (a.sp[i] >> 30) : 0u;
-            uint64_t prev = __shfl_up_sync(0xffffffffu, q, 1);
-            if (lane == 0) prev = carry;
-            carry = __shfl_sync(0xffffffffu, q, 31);
-            const bool head = valid && (i == 0 || q != prev);
-            const bool local = valid && (head || (k == 0 && lane == 0));
-            const uint32_t e = (valid && (op == 1u || op == 2u)) ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
-            emax = max(emax, e);
-            const uint32_t b = __ballot_sync(0xffffffffu, local);
-            if (local) s_q[nq + __popc(b & lt)] = q;
-            nq += __popc(b);
+    const uint32_t D = a.bm->distinct;
+    for (uint32_t d0 = blockIdx.x * kThreads; d0 < D; d0 += gridDim.x * kThreads) {
+        const uint32_t d = d0 + threadIdx.x;
+        const bool active = d < D;
+        const uint64_t q = active ? a.dq[d] : kMaxKey;
+        uint32_t lo = active ? a.dlo[d] : 0u;
+        int32_t r = -1;
+        uint32_t dn = 0;
+        uint64_t kr = 0;
+        warp_search<false>(SK, nullptr, lo, size, q, active, r, dn, kr, a.err);
+        if (active) {
+            const bool exists = r >= 0 && kr == q;
+            const uint8_t meta = exists ? SM[r] : (uint8_t)0;
+            const bool live = exists && !(meta & kTomb);
+            a.loc[d] = (uint32_t)(r + 1);
+            a.flags[d] = (uint8_t)((exists ? 1u : 0u) | (live ? 2u : 0u));
+            a.val0[d] = live ? SV[r] : 0ull;
         }
-        emax = __reduce_max_sync(0xffffffffu, emax);
-        if (lane == 0 && emax) atomicMax(&a.tile_max[sb / kApplyTile], emax);
-        __syncwarp();
-        // 3. descend the sub-tile's distinct keys, 32 per step
-        for (uint32_t c = 0; c < nq; c += 32u) {
-            const uint32_t j = c + (uint32_t)lane;
-            const bool active = j < nq;
-            const uint64_t q = active ? s_q[j] : kMaxKey;
-            uint32_t lo = 0;
-            int32_t r = -1;
-            uint32_t dn = 0;
-            uint64_t kr = 0;
-            int top = (int)H;
-            if (Ls <= H) {
-                // Pinned levels Ls..H are in shared memory; level Ls holds every key of
-                // the levels above it, so the entry the walk down those levels reaches
-                // on level Ls -- its largest key <= q -- is found by one binary search.
-                if (active) {
-                    r = smem_rank(s_k + s_base[Ls], s_n[Ls], q);
-                    lo = (r >= 0) ? s_d[s_base[Ls] + r] : 0u;
-                }
-                top = (int)Ls - 1;
-            }
-            for (int l = top; l >= (int)Lb; --l) {
-                r = -1;
-                dn = 0;
-                warp_search<true>(a.lkeys + s_base[l], a.ldown + s_base[l], lo, s_n[l], q, active, r, dn, kr, a.err);
-                if (active) lo = (r >= 0) ? dn : 0u;
-            }
-            r = -1;
-            kr = 0;
-            warp_search<false>(SK, nullptr, lo, size, q, active, r, dn, kr, a.err);
-            if (active) {
-                const bool exists = r >= 0 && kr == q;
-                const uint8_t meta = exists ? SM[r] : (uint8_t)0;
-                const bool live = exists && !(meta & kTomb);
-                const uint32_t o = sb + j;
-                a.loc[o] = (uint32_t)(r + 1);
-                a.flags[o] = (uint8_t)((exists ? 1u : 0u) | (live ? 2u : 0u));
-                a.val0[o] = live ? SV[r] : 0ull;
-            }
-        }
-        __syncwarp();  // the list is reused by the next sub-tile
     }
 }
 
@@ -257,15 +319,26 @@ __global__ void __launch_bounds__(kThreads, 5) k_descend(DescendArgs a) {
 
 cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
     static bool attr_set = false;
-    const int dyn = (int)((kSmemTopMax + kPad) * (sizeof(uint64_t) + sizeof(uint32_t)) + 8 * kSubTile * sizeof(uint64_t));
+    const int dyn = (int)((kSmemTopMax + kPad) * (sizeof(uint64_t) + sizeof(uint32_t)));
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_descend, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaError_t e = cudaFuncSetAttribute(k_top, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (a.n == 0) return cudaSuccess;
-    const uint32_t blocks = ((a.n + kSubTile - 1) / kSubTile + 7) / 8, cap = (uint32_t)num_sms * 5u;
-    k_descend<<<(int)(blocks < cap ? blocks : cap), kThreads, dyn, s>>>(a);
+    const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
+    const uint32_t blocks = (nsub + 7) / 8;
+    k_distinct<<<blocks, kThreads, 0, s>>>(a);
+    k_dscan<<<1, 1024, 0, s>>>(a);
+    const uint32_t capt = (uint32_t)num_sms * 8u;
+    k_top<<<(int)(blocks < capt ? blocks : capt), kThreads, dyn, s>>>(a);
+    // one launch per index level from top_launched down to 2; a launch whose level is
+    // pinned or not built exits at once, and levels above top_launched that are
+    // neither (the index grew) are walked by k_top
+    const uint32_t need = (a.n + kThreads - 1) / kThreads, capg = (uint32_t)num_sms * 16u;
+    const uint32_t gblocks = need < capg ? need : capg;  // grid-stride over the distinct keys
+    for (int l = a.top_launched; l >= 2; --l) k_level<<<gblocks, kThreads, 0, s>>>(a, l);
+    k_locate<<<gblocks, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,11 @@ struct Scratch {
     uint32_t* tcnt = nullptr;  // radix sort: per-tile digit counts
     uint32_t* toff = nullptr;  // radix sort: per-tile digit offsets
     uint8_t* ndig = nullptr;   // radix sort: next pass's digits
+    uint64_t* hq = nullptr;    // descent: distinct keys per sub-tile
+    uint32_t* sub_cnt = nullptr;
+    uint32_t* sub_pref = nullptr;
+    uint64_t* dq = nullptr;    // descent: dense distinct keys
+    uint32_t* dlo = nullptr;   // descent: per-key start position
 };
 
 struct Staging {
@@ -55,6 +60,8 @@ struct pi_index {
     int num_sms = 0;
     HashParams hp{};
     uint32_t rebuild_policy = 0, threshold_pct = 15;
+    uint32_t smem_top = kSmemTopMax;  // pinned-entry cap
+    uint32_t test_flags = 0;
     DevMeta* d_meta = nullptr;
     BatchMeta* d_bm = nullptr;
     uint32_t* d_dofs = nullptr;
@@ -178,6 +185,7 @@ void free_scratch(Scratch& s) {
     dfree(s.stage.keys); dfree(s.stage.vals); dfree(s.stage.loc); dfree(s.stage.height);
     dfree(s.tile_max); dfree(s.tile_pref); dfree(s.tile_new);
     dfree(s.tcnt); dfree(s.toff); dfree(s.ndig);
+    dfree(s.hq); dfree(s.sub_cnt); dfree(s.sub_pref); dfree(s.dq); dfree(s.dlo);
     s.cap = 0;
 }
 
@@ -199,6 +207,9 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     const uint64_t stiles = (q + kSortTile - 1) / kSortTile + 1;
     PI_TRY(dalloc(&s.tcnt, stiles * 256)); PI_TRY(dalloc(&s.toff, stiles * 256));
     PI_TRY(dalloc(&s.ndig, stiles * kSortTile + 16));
+    const uint64_t nsub = (q + kSubTile - 1) / kSubTile + 1;
+    PI_TRY(dalloc(&s.hq, nsub * kSubTile)); PI_TRY(dalloc(&s.sub_cnt, nsub)); PI_TRY(dalloc(&s.sub_pref, nsub));
+    PI_TRY(dalloc(&s.dq, c)); PI_TRY(dalloc(&s.dlo, c));
 #undef PI_TRY
     s.cap = q;
     return cudaSuccess;
@@ -399,6 +410,7 @@ RebuildArgs rebuild_args(pi_index* x, uint32_t size_ub, uint32_t force) {
     r.threshold_pct = x->threshold_pct;
     r.force_rebuild = force;
     r.st_cap = (uint32_t)x->st_cap;
+    r.smem_top = x->smem_top;
     r.err = &x->d_meta->error;
     return r;
 }
@@ -439,6 +451,8 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
     if (cfg) {
         x->rebuild_policy = cfg->rebuild_policy;
         if (cfg->rebuild_threshold_pct) x->threshold_pct = cfg->rebuild_threshold_pct;
+        if (cfg->smem_top_entries && cfg->smem_top_entries < kSmemTopMax) x->smem_top = cfg->smem_top_entries;
+        x->test_flags = cfg->test_flags;
     }
     uint64_t st_cap = n + (n / 2 > kMinStorage ? n / 2 : kMinStorage);
     if (cfg && cfg->storage_capacity > st_cap) st_cap = cfg->storage_capacity;
@@ -582,6 +596,18 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
     da.sk = x->sc.a_k;
     da.sp = x->sc.a_p;
     da.tile_max = x->sc.tile_max;
+    da.tile_pref = x->sc.tile_pref;
+    da.hq = x->sc.hq;
+    da.sub_cnt = x->sc.sub_cnt;
+    da.sub_pref = x->sc.sub_pref;
+    da.dq = x->sc.dq;
+    da.dlo = x->sc.dlo;
+    {
+        // levels below the pinned ones, as of the host's last view of the index
+        int t = (x->known.Ls >= 3 && x->known.Ls <= (uint32_t)x->hp.hmax + 1) ? (int)x->known.Ls - 1 : x->hp.hmax;
+        if (x->test_flags & PI_TEST_WALK_LEVELS) t = 2;
+        da.top_launched = t < 2 ? 2 : t;
+    }
     da.m = x->d_meta;
     da.bm = x->d_bm;
     da.lkeys = x->lkeys;
@@ -611,6 +637,7 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
     aa.tile_max = x->sc.tile_max;
     aa.tile_pref = x->sc.tile_pref;
     aa.tile_new = x->sc.tile_new;
+    aa.sub_pref = x->sc.sub_pref;
     aa.stage = x->sc.stage;
     aa.lcnt = x->lcnt;
     aa.lstride = x->lstride;

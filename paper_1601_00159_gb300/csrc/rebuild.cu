@@ -218,7 +218,7 @@ __global__ void k_level_bases(RebuildArgs a) {
     m->index_total = off;
     uint32_t Ls = H + 1;
     for (int l = (int)H; l >= (int)Lb; --l) {
-        if (m->base[l] + m->n[l] + 1u <= kSmemTopMax) Ls = (uint32_t)l;
+        if (m->base[l] + m->n[l] + 1u <= a.smem_top) Ls = (uint32_t)l;
         else break;
     }
     m->Ls = Ls;

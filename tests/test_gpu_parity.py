@@ -88,6 +88,17 @@ def test_rebuild_policy_does_not_change_results(orc_mod, policy):
                  check_levels_every=1, check_levels=(policy == 0))
 
 
+@pytest.mark.parametrize("cfg", [{"test_flags": 1}, {"smem_top_entries": 1}, {"smem_top_entries": 40},
+                                 {"test_flags": 1, "smem_top_entries": 200}])
+def test_descent_paths_give_identical_results(orc_mod, cfg):
+    """The in-kernel level walk, no pinned levels, and few pinned levels all reach
+    the same interceptions as the default launch plan."""
+    w = wl.random_small(88, 60000, 40000, 1 << 40, p=0.25, n_batches=3)
+    run_workload(orc_mod, w, config=cfg)
+    w2 = wl.skewed(seed=5, n=1 << 18, q=1 << 15, n_batches=3)
+    run_workload(orc_mod, w2, config=cfg)
+
+
 def test_index_capacity_overflow_keeps_results_exact(orc_mod):
     """An index layer that does not fit drops its lowest levels (the descent then walks
     longer storage gaps); results stay exact and the capacity grows afterwards."""
