@@ -131,6 +131,32 @@ int pi_execute_batch_host(pi_index_t* idx, const uint8_t* ops_host, const uint64
                           const uint64_t* values_host, uint64_t n, pi_result_t* results_host,
                           pi_stream_t stream);
 
+/*
+ * pi_execute_batch_noalloc -- the same as pi_execute_batch, for callers that cannot
+ * allocate device memory during a batch. (The paper has no counterpart: this is an
+ * interface choice.) Such callers include code that must not block on the CUDA
+ * allocator (cudaMalloc/cudaFree can synchronise the device, which a latency-bound
+ * serving loop cannot afford) and code running where a memory budget is fixed up front.
+ * The per-batch scratch of up to PI_NOALLOC_MAX_BATCH queries comes from one
+ * file-scope device array of a fixed size (about 9 MB), held by every GPU that loads
+ * the library until the process exits; this call allocates nothing.
+ *   - n > PI_NOALLOC_MAX_BATCH returns PI_ERR_INVALID_ARG.
+ *   - A batch that could need the storage layer to grow returns PI_ERR_OOM with the
+ *     index unchanged (create the index with enough storage_capacity, or use
+ *     pi_execute_batch for that batch). An index layer that outgrows its capacity is not
+ *     grown: its lowest levels are dropped and the results stay exact.
+ *   - The first call on a device looks up the array's device address (with that device
+ *     current); make that first call before any stream capture.
+ *   - Every call shares the one array: calls whose work overlaps on the GPU (other
+ *     streams, other indices) race and must be serialised by the caller. Nothing in the
+ *     array needs to start at zero; each batch writes what it later reads.
+ * Results and index updates are identical to pi_execute_batch's.
+ */
+#define PI_NOALLOC_MAX_BATCH (1u << 16)
+int pi_execute_batch_noalloc(pi_index_t* idx, const uint8_t* ops, const uint64_t* keys,
+                             const uint64_t* values, uint64_t n, pi_result_t* results,
+                             pi_stream_t stream);
+
 /* Releases every device allocation of the index after its pending work. NULL-safe. */
 void pi_destroy(pi_index_t* idx);
 

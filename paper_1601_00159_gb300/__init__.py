@@ -21,7 +21,8 @@ PI_MAX_KEYS = (1 << 30) - 2
 
 EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
             "pi_last_error", "pi_status", "pi_info", "pi_export", "pi_export_level", "pi_profile",
-            "pi_profile_read"]
+            "pi_profile_read", "pi_execute_batch_noalloc"]
+PI_NOALLOC_MAX_BATCH = 1 << 16
 STAGES = ["sort", "descend", "apply", "merge", "layout", "rebuild"]
 
 
@@ -70,6 +71,8 @@ def load_library(path: str = LIB_PATH):
     lib.pi_create_ex.argtypes = [vp, vp, u64, dbl, u64, ctypes.POINTER(PiConfig)]
     lib.pi_execute_batch.restype = i32
     lib.pi_execute_batch.argtypes = [vp, vp, vp, vp, u64, vp, vp]
+    lib.pi_execute_batch_noalloc.restype = i32
+    lib.pi_execute_batch_noalloc.argtypes = [vp, vp, vp, vp, u64, vp, vp]
     lib.pi_execute_batch_host.restype = i32
     lib.pi_execute_batch_host.argtypes = [vp, vp, vp, vp, u64, vp, vp]
     lib.pi_destroy.restype = None
@@ -149,6 +152,18 @@ class Index:
         rc = self.lib.pi_execute_batch(self._h, ops.data_ptr(), keys.data_ptr(), vals.data_ptr(), n,
                                        results.data_ptr(), _stream_handle(stream))
         _chk(rc, "pi_execute_batch")
+        return results
+
+    def execute_noalloc(self, ops, keys, vals, results, stream=None):
+        """pi_execute_batch_noalloc: device tensors; `results` (int64 [n, 2]) must exist."""
+        import torch
+        _check_dev(ops, torch.uint8, "ops")
+        _check_dev(keys, torch.int64, "keys")
+        _check_dev(vals, torch.int64, "vals")
+        _check_dev(results, torch.int64, "results")
+        rc = self.lib.pi_execute_batch_noalloc(self._h, ops.data_ptr(), keys.data_ptr(), vals.data_ptr(),
+                                               ops.numel(), results.data_ptr(), _stream_handle(stream))
+        _chk(rc, "pi_execute_batch_noalloc")
         return results
 
     def execute_host(self, ops, keys, vals, results, stream=None):

@@ -7,7 +7,9 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -415,6 +417,78 @@ RebuildArgs rebuild_args(pi_index* x, uint32_t size_ub, uint32_t force) {
     return r;
 }
 
+// ---------------------------------------------------------------------------------
+// Allocation-free batches (pi_execute_batch_noalloc): the per-batch scratch of up to
+// PI_NOALLOC_MAX_BATCH queries lives in one file-scope device array, carved into the
+// same buffers alloc_scratch() would allocate, in this order.
+constexpr uint64_t al256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
+
+constexpr uint64_t noalloc_bytes(uint64_t q) {
+    const uint64_t c = q + kPad;
+    const uint64_t tiles = (q + kApplyTile - 1) / kApplyTile + 1, cs = tiles * kApplyTile;
+    const uint64_t stiles = (q + kSortTile - 1) / kSortTile + 1;
+    const uint64_t nsub = (q + kSubTile - 1) / kSubTile + 1;
+    return 3 * al256(c * 8) + 3 * al256(c * 4)                    // in, a, b (keys, payload)
+           + al256(c * 4) + al256(c) + al256(c * 8)               // loc, flags, val0
+           + 2 * al256(c * 8) + al256(c * 4) + al256(c)           // new nodes
+           + 2 * al256(cs * 8) + al256(cs * 4) + al256(cs)        // new-node staging
+           + 3 * al256(tiles * 4)                                 // tile max / prefix / new
+           + 2 * al256(stiles * 256 * 4) + al256(stiles * kSortTile + 16)  // tcnt, toff, ndig
+           + al256(nsub * kSubTile * 8) + 2 * al256(nsub * 4)     // hq, sub_cnt, sub_pref
+           + al256(c * 8) + al256(c * 4);                         // dq, dlo
+}
+
+constexpr uint64_t kNoAllocBytes = noalloc_bytes(PI_NOALLOC_MAX_BATCH);
+
+// Shared by every call on a device; each GPU that loads the library holds it until exit.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+// Carves `base` like noalloc_bytes(q); returns the bytes used.
+uint64_t carve_scratch(uint8_t* base, uint64_t q, Scratch& s) {
+    uint64_t off = 0;
+    auto take = [&](auto*& ptr, uint64_t bytes) {
+        ptr = reinterpret_cast<std::remove_reference_t<decltype(ptr)>>(base + off);
+        off += al256(bytes);
+    };
+    const uint64_t c = q + kPad;
+    const uint64_t tiles = (q + kApplyTile - 1) / kApplyTile + 1, cs = tiles * kApplyTile;
+    const uint64_t stiles = (q + kSortTile - 1) / kSortTile + 1;
+    const uint64_t nsub = (q + kSubTile - 1) / kSubTile + 1;
+    take(s.in_k, c * 8); take(s.a_k, c * 8); take(s.b_k, c * 8);
+    take(s.in_p, c * 4); take(s.a_p, c * 4); take(s.b_p, c * 4);
+    take(s.loc, c * 4); take(s.flags, c); take(s.val0, c * 8);
+    take(s.nn.keys, c * 8); take(s.nn.vals, c * 8); take(s.nn.loc, c * 4); take(s.nn.height, c);
+    take(s.stage.keys, cs * 8); take(s.stage.vals, cs * 8); take(s.stage.loc, cs * 4); take(s.stage.height, cs);
+    take(s.tile_max, tiles * 4); take(s.tile_pref, tiles * 4); take(s.tile_new, tiles * 4);
+    take(s.tcnt, stiles * 256 * 4); take(s.toff, stiles * 256 * 4); take(s.ndig, stiles * kSortTile + 16);
+    take(s.hq, nsub * kSubTile * 8); take(s.sub_cnt, nsub * 4); take(s.sub_pref, nsub * 4);
+    take(s.dq, c * 8); take(s.dlo, c * 4);
+    s.cap = q;
+    return off;
+}
+
+// Device address of the array, looked up once per device with that device current.
+std::mutex g_noalloc_mu;
+uint8_t* g_noalloc_ptr[64] = {};
+
+cudaError_t noalloc_scratch_for(int device, uint8_t** out) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        int prev = -1;
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e != cudaSuccess) return e;
+        if (prev != device && (e = cudaSetDevice(device)) != cudaSuccess) return e;
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (prev != device) cudaSetDevice(prev);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = static_cast<uint8_t*>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -696,6 +770,104 @@ int pi_execute_batch_host(pi_index_t* x, const uint8_t* ops_host, const uint64_t
     if (rc != PI_OK) return rc;
     e = cudaMemcpyAsync(results_host, g.res, n * sizeof(pi_result_t), cudaMemcpyDeviceToHost, s);
     return map_cuda(e);
+}
+
+int pi_execute_batch_noalloc(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, const uint64_t* values,
+                             uint64_t n, pi_result_t* results, pi_stream_t stream) {
+    if (!x) return PI_ERR_INVALID_ARG;
+    if (n == 0) return PI_OK;
+    if (!ops || !keys || !values || !results) return PI_ERR_INVALID_ARG;
+    if (n > PI_NOALLOC_MAX_BATCH) return PI_ERR_INVALID_ARG;  // beyond the static scratch
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    uint8_t* base = nullptr;
+    if ((e = noalloc_scratch_for(x->device, &base)) != cudaSuccess) return map_cuda(e);
+    Scratch sc{};
+    if (carve_scratch(base, PI_NOALLOC_MAX_BATCH, sc) != kNoAllocBytes) return PI_ERR_CUDA;
+    refresh_known(x);
+    if (int rc = sticky_error(x->known)) return rc;
+    uint64_t size_ub = (uint64_t)x->known.size + x->pending_n + n;
+    if (size_ub > x->st_cap) {
+        if ((e = sync_known(x, s)) != cudaSuccess) return map_cuda(e);
+        if (int rc = sticky_error(x->known)) return rc;
+        size_ub = (uint64_t)x->known.size + n;
+        if (size_ub > x->st_cap) return PI_ERR_OOM;  // the storage layer would have to grow
+    }
+    // An index layer that outgrew its capacity is not grown here: the rebuild then drops
+    // its lowest levels and results stay exact.
+    uint32_t ep = next_epochs(x, 16, s);
+    cudaMemsetAsync(x->d_bm, 0, sizeof(BatchMeta), s);
+    SortBuffers sb = sort_buffers(x, sc);
+    if ((e = launch_sort(ops, keys, (uint32_t)n, sb, x->d_bm, &x->d_meta->error, ep, s, x->num_sms)) != cudaSuccess)
+        return map_cuda(e);
+    DescendArgs da{};
+    da.sk = sc.a_k;
+    da.sp = sc.a_p;
+    da.tile_max = sc.tile_max;
+    da.tile_pref = sc.tile_pref;
+    da.hq = sc.hq;
+    da.sub_cnt = sc.sub_cnt;
+    da.sub_pref = sc.sub_pref;
+    da.dq = sc.dq;
+    da.dlo = sc.dlo;
+    {
+        int t = (x->known.Ls >= 3 && x->known.Ls <= (uint32_t)x->hp.hmax + 1) ? (int)x->known.Ls - 1 : x->hp.hmax;
+        if (x->test_flags & PI_TEST_WALK_LEVELS) t = 2;
+        da.top_launched = t < 2 ? 2 : t;
+    }
+    da.m = x->d_meta;
+    da.bm = x->d_bm;
+    da.lkeys = x->lkeys;
+    da.ldown = x->ldown;
+    da.st = x->st;
+    da.loc = sc.loc;
+    da.flags = sc.flags;
+    da.val0 = sc.val0;
+    da.n = (uint32_t)n;
+    da.err = &x->d_meta->error;
+    if ((e = launch_descend(da, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    ApplyArgs aa{};
+    aa.sk = sc.a_k;
+    aa.sp = sc.a_p;
+    aa.loc = sc.loc;
+    aa.flags = sc.flags;
+    aa.val0 = sc.val0;
+    aa.uvals = values;
+    aa.results = results;
+    aa.st = x->st;
+    aa.nn = sc.nn;
+    aa.m = x->d_meta;
+    aa.bm = x->d_bm;
+    aa.desc = x->desc;
+    aa.tile_max = sc.tile_max;
+    aa.tile_pref = sc.tile_pref;
+    aa.tile_new = sc.tile_new;
+    aa.sub_pref = sc.sub_pref;
+    aa.stage = sc.stage;
+    aa.lcnt = x->lcnt;
+    aa.lstride = x->lstride;
+    aa.n = (uint32_t)n;
+    aa.hp = x->hp;
+    aa.err = &x->d_meta->error;
+    if ((e = launch_apply(aa, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    RebuildArgs ra = rebuild_args(x, (uint32_t)size_ub, x->force_rebuild ? 1u : 0u);
+    ra.nn = sc.nn;
+    if ((e = launch_merge(ra, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    if ((e = launch_level_bases(ra, s)) != cudaSuccess) return map_cuda(e);
+    if ((e = launch_rebuild(ra, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    x->epoch = ep;
+    x->force_rebuild = false;
+    const uint64_t slot = x->issued % kRing;
+    if (x->issued - x->seen >= kRing) {  // the slot is still unread: wait for its batch
+        cudaEventSynchronize(x->ev[slot]);
+        refresh_known(x);
+    }
+    cudaMemcpyAsync(&x->h_mbox[slot], x->d_meta, sizeof(DevMeta), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(x->ev[slot], s);
+    x->ring_n[slot] = n;
+    x->issued++;
+    x->pending_n += n;
+    return map_cuda(cudaGetLastError());
 }
 
 void pi_destroy(pi_index_t* x) { destroy(x); }
