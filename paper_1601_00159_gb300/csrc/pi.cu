@@ -137,7 +137,8 @@ int map_cuda(cudaError_t e) {
 uint64_t desc_need(uint64_t q, uint64_t s) {
     uint64_t a = 0;                                    // (the sort needs none)
     uint64_t b = 2 * ((q + 2047) / 2048);    // apply
-    uint64_t c = (s / 4096 + 2) * 32;        // rebuild (and merge, export)
+    uint64_t c = (s / 4096 + 2) * 32;        // merge, export
+    if (c < 32 * 64) c = 32 * 64;            // rebuild level scan: 64 chunks x 32 levels
     uint64_t m = a > b ? a : b;
     return (m > c ? m : c) + 64;
 }
@@ -392,6 +393,25 @@ cudaError_t grow_index(pi_index* x, uint64_t need, cudaStream_t s) {
     x->idx_cap = cap;
     x->force_rebuild = true;
     return cudaSuccess;
+}
+
+// The descent walks the levels below the pinned ones inside its top kernel, one key
+// per thread, as long as they are small (about 24 MB of entries: L2-resident); the
+// levels below get one launch each. Taken from the host's last view of the index; any
+// split gives the same result.
+constexpr uint64_t kWalkEntries = 2u << 20;
+
+int top_launched_for(const pi_index* x) {
+    const DevMeta& k = x->known;
+    if (x->test_flags & PI_TEST_WALK_LEVELS) return 2;
+    if (k.Ls < 3 || k.Ls > (uint32_t)x->hp.hmax + 1) return x->hp.hmax;
+    uint64_t cum = 0;
+    int l = (int)k.Ls - 1;
+    while (l >= 2 && cum + k.n[l] <= kWalkEntries) {
+        cum += k.n[l];
+        --l;
+    }
+    return l < 2 ? 2 : l;
 }
 
 RebuildArgs rebuild_args(pi_index* x, uint32_t size_ub, uint32_t force) {
@@ -676,12 +696,7 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
     da.sub_pref = x->sc.sub_pref;
     da.dq = x->sc.dq;
     da.dlo = x->sc.dlo;
-    {
-        // levels below the pinned ones, as of the host's last view of the index
-        int t = (x->known.Ls >= 3 && x->known.Ls <= (uint32_t)x->hp.hmax + 1) ? (int)x->known.Ls - 1 : x->hp.hmax;
-        if (x->test_flags & PI_TEST_WALK_LEVELS) t = 2;
-        da.top_launched = t < 2 ? 2 : t;
-    }
+    da.top_launched = top_launched_for(x);
     da.m = x->d_meta;
     da.bm = x->d_bm;
     da.lkeys = x->lkeys;
@@ -810,11 +825,7 @@ int pi_execute_batch_noalloc(pi_index_t* x, const uint8_t* ops, const uint64_t* 
     da.sub_pref = sc.sub_pref;
     da.dq = sc.dq;
     da.dlo = sc.dlo;
-    {
-        int t = (x->known.Ls >= 3 && x->known.Ls <= (uint32_t)x->hp.hmax + 1) ? (int)x->known.Ls - 1 : x->hp.hmax;
-        if (x->test_flags & PI_TEST_WALK_LEVELS) t = 2;
-        da.top_launched = t < 2 ? 2 : t;
-    }
+    da.top_launched = top_launched_for(x);
     da.m = x->d_meta;
     da.bm = x->d_bm;
     da.lkeys = x->lkeys;

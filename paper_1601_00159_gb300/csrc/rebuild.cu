@@ -150,11 +150,12 @@ __global__ void __launch_bounds__(kThreads) k_merge(RebuildArgs a, uint32_t epoc
 // ---------------------------------------------------------------------------------
 // Layout: apply the batch's deltas, switch storage buffers after a merge, decide the
 // rebuild, and lay the index levels out top-first with their sentinels.
-__global__ void k_level_bases(RebuildArgs a) {
-    if (threadIdx.x != 0) return;
+// Thread 0: sizes, re-layout switch, rebuild decision and level layout. Returns true
+// when the rebuild runs (the sentinels are then written by the caller's lanes).
+__device__ bool level_bases_body(RebuildArgs a) {
     DevMeta* m = a.m;
     BatchMeta* bm = a.bm;
-    if (*(volatile uint32_t*)&m->error) return;
+    if (*(volatile uint32_t*)&m->error) return false;
     const bool merged = merge_needed(m, bm);
     uint32_t tombs = (uint32_t)((int32_t)m->tombs + bm->tomb_delta);
     uint32_t size = m->size;
@@ -165,7 +166,7 @@ __global__ void k_level_bases(RebuildArgs a) {
     }
     if (size > a.st_cap) {  // cannot happen when the host reserved capacity
         atomicOr(a.err, kErrBounds);
-        return;
+        return false;
     }
     m->size = size;
     m->tombs = tombs;
@@ -184,7 +185,7 @@ __global__ void k_level_bases(RebuildArgs a) {
         else rebuild = (uint64_t)m->updates * 100u >= (uint64_t)a.threshold_pct * (uint64_t)(size ? size : 1u);
     }
     bm->rebuild = rebuild ? 1u : 0u;
-    if (!rebuild) return;
+    if (!rebuild) return false;
     m->updates = 0;
     m->rebuilds += 1;
 
@@ -223,10 +224,24 @@ __global__ void k_level_bases(RebuildArgs a) {
     }
     m->Ls = Ls;
     m->smem_entries = (Ls <= H) ? m->base[Ls] + m->n[Ls] + 1u : 0u;
-    for (int l = (int)H; l >= (int)Lb; --l) {
+    __threadfence_block();
+    return true;
+}
+
+__global__ void k_level_bases(RebuildArgs a) {
+    __shared__ int s_go;
+    if (threadIdx.x == 0) s_go = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) s_go = level_bases_body(a) ? 1 : 0;
+    __syncthreads();
+    if (!s_go) return;
+    // sentinels of the built levels, one lane per level
+    const DevMeta* m = a.m;
+    const int l = (int)m->Lb + (int)threadIdx.x;
+    if (l <= (int)m->H) {
         const uint32_t sidx = m->base[l] + m->n[l];
         a.lkeys[sidx] = kMaxKey;
-        a.ldown[sidx] = (l > (int)Lb) ? m->n[l - 1] : size;
+        a.ldown[sidx] = (l > (int)m->Lb) ? m->n[l - 1] : m->size;
     }
 }
 
@@ -251,8 +266,7 @@ __global__ void __launch_bounds__(256) k_rebuild_count(RebuildArgs a) {
     if (!a.bm->rebuild || !(a.bm->merged || a.force_rebuild)) return;
     const uint32_t size = m->size, cur = m->cur;
     const uint32_t ntiles = (size + kNodes - 1) / kNodes;
-    const uint32_t tile = blockIdx.x * 8u + (uint32_t)warp;
-    if (tile >= ntiles) return;
+    for (uint32_t tile = blockIdx.x * 8u + (uint32_t)warp; tile < ntiles; tile += gridDim.x * 8u) {
     const uint32_t ts = tile * kNodes;
     const uint32_t cnt = min((uint32_t)kNodes, size - ts);
     const uint8_t* SM = a.st.meta[cur] + ts;
@@ -279,53 +293,59 @@ __global__ void __launch_bounds__(256) k_rebuild_count(RebuildArgs a) {
         }
     }
     if (lane < 32 && lane + 2 < kLevelSlots) a.lcnt[(size_t)lane * a.lstride + tile] = c;
+    }
 }
 
-// One CTA per built level: exclusive scan of the tile counts; checks the total. Each
-// thread takes a contiguous run of tiles (independent loads), so the scan is one block
-// prefix sum per 1024 runs rather than one per 1024 tiles.
-__global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a) {
+// Per built level, exclusive scan of the tile counts over tiles. Grid: (chunks, levels);
+// each CTA scans kScanChunk tiles (4 per thread) and gets the prefix of the chunks
+// before it by a warp-wide decoupled look-back (the chain is a few chunks long). The
+// level's last chunk checks the total against the level size.
+constexpr uint32_t kScanChunk = 4096;
+
+__global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a, uint32_t epoch) {
     __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_prefix;
+    __shared__ int s_ok;
     const DevMeta* m = a.m;
     if (block_sees_error(&m->error)) return;
     if (!a.bm->rebuild) return;
     const uint32_t H = m->H, Lb = m->Lb, size = m->size;
-    const uint32_t l = Lb + blockIdx.x;
+    const uint32_t l = Lb + blockIdx.y;
     if (H < Lb || size == 0 || l > H) return;
     const uint32_t ntiles = (size + kNodes - 1) / kNodes;
+    const uint32_t nchunks = (ntiles + kScanChunk - 1) / kScanChunk;
+    const uint32_t chunk = blockIdx.x;
+    if (chunk >= nchunks) return;
     const uint32_t* c = a.lcnt + (size_t)(l - 2) * a.lstride;
     uint32_t* o = a.loff + (size_t)(l - Lb) * ntiles;
-    const uint32_t per = (ntiles + 1023u) / 1024u;
-    const uint32_t t0 = min(threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
-    uint32_t sum = 0;
-    uint32_t t = t0;
-    for (; t + 8u <= t1; t += 8u) {  // eight independent loads per step
-        uint32_t v[8];
+    const uint32_t t0 = chunk * kScanChunk + threadIdx.x * 4u;
+    uint32_t v[4], sum = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = c[t + k];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sum += v[k];
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (t0 + k < ntiles) ? c[t0 + k] : 0u;
+        sum += v[k];
     }
-    for (; t < t1; ++t) sum += c[t];
     uint32_t tot;
     uint32_t run = block_excl_sum<1024>(sum, s_tmp, &tot);
-    t = t0;
-    for (; t + 8u <= t1; t += 8u) {
-        uint32_t v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = c[t + k];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            o[t + k] = run;
-            run += v[k];
+    if (threadIdx.x < 32) {
+        bool ok;
+        // descriptors: one row of 64 chunks per level (level counts of 2^30 nodes fit)
+        const uint32_t ex = lookback_warp<false>(a.desc + (size_t)blockIdx.y * 64, chunk, epoch, tot, a.err, &ok);
+        if (threadIdx.x == 0) {
+            s_prefix = ex;
+            s_ok = ok ? 1 : 0;
         }
     }
-    for (; t < t1; ++t) {
-        const uint32_t v = c[t];
-        o[t] = run;
-        run += v;
+    __syncthreads();
+    if (!s_ok) return;
+    run += s_prefix;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (t0 + k < ntiles) o[t0 + k] = run;
+        run += v[k];
     }
-    if (threadIdx.x == 0 && tot != m->n[l]) atomicOr(a.err, kErrBounds);  // counts disagree
+    if (chunk == nchunks - 1 && threadIdx.x == 0 && s_prefix + tot != m->n[l])
+        atomicOr(a.err, kErrBounds);  // counts disagree with the level size
 }
 
 // Byte-wise arithmetic on a meta word holding four nodes (height in bits 0-5, delete
@@ -631,8 +651,6 @@ cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
-    (void)epoch;
-    (void)num_sms;
     static bool attr_set = false;
     const int dyn = (int)(kKeyBytes + kMetaBytes + 8 * kWarpNodes * 4);
     if (!attr_set) {
@@ -641,8 +659,10 @@ cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s
         attr_set = true;
     }
     const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
-    k_rebuild_count<<<(tiles + 7) / 8, 256, 0, s>>>(a);
-    k_rebuild_scan<<<kLevelSlots - 2, 1024, 0, s>>>(a);
+    const uint32_t cb = (tiles + 7) / 8, ccap = (uint32_t)num_sms * 4u;
+    k_rebuild_count<<<cb < ccap ? cb : ccap, 256, 0, s>>>(a);  // exits at once unless recounting
+    const uint32_t chunks = (tiles + kScanChunk - 1) / kScanChunk;
+    k_rebuild_scan<<<dim3(chunks, kLevelSlots - 2), 1024, 0, s>>>(a, ++epoch);
     k_rebuild_write<<<tiles, kThreads, dyn, s>>>(a);
     return cudaGetLastError();
 }
