@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
         }
     }
     // New nodes: staged in this tile's slice of the staging arrays, in key order.
-    uint32_t tile_new;
-    uint32_t slot = block_excl_sum<kThreads>(new_here, s_tmp, &tile_new);
+    uint32_t tile_new = 0, slot = 0;
+    if (__syncthreads_or(new_here != 0)) slot = block_excl_sum<kThreads>(new_here, s_tmp, &tile_new);
     if (new_mask) {
         const uint32_t so = tile * kApplyTile;
 #pragma unroll

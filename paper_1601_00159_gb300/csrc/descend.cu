@@ -174,51 +174,65 @@ __global__ void __launch_bounds__(kThreads) k_distinct(DescendArgs a) {
 
 // One CTA: dense index of every sub-tile's first distinct key (exclusive sum of the
 // counts), the number of distinct keys, and the apply tiles' exclusive max prefixes.
+// Each thread takes a contiguous run of entries, so there is one block scan per array.
 __global__ void __launch_bounds__(1024) k_dscan(DescendArgs a) {
     __shared__ uint32_t s_tmp[33];
-    __shared__ uint32_t s_carry;
     if (block_sees_error(&a.m->error)) return;
-    const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (uint32_t b0 = 0; b0 < nsub; b0 += 1024) {
-        const uint32_t i = b0 + threadIdx.x;
-        const uint32_t v = i < nsub ? a.sub_cnt[i] : 0u;
+    {
+        const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
+        const uint32_t per = (nsub + 1023u) / 1024u;
+        const uint32_t t0 = min(threadIdx.x * per, nsub), t1 = min(t0 + per, nsub);
+        uint32_t sum = 0;
+        for (uint32_t t = t0; t < t1; ++t) sum += a.sub_cnt[t];
         uint32_t tot;
-        const uint32_t ex = block_excl_sum<1024>(v, s_tmp, &tot);
-        if (i < nsub) a.sub_pref[i] = s_carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += tot;
-        __syncthreads();
+        uint32_t run = block_excl_sum<1024>(sum, s_tmp, &tot);
+        for (uint32_t t = t0; t < t1; ++t) {
+            const uint32_t v = a.sub_cnt[t];
+            a.sub_pref[t] = run;
+            run += v;
+        }
+        if (threadIdx.x == 0) a.bm->distinct = tot;
     }
-    if (threadIdx.x == 0) a.bm->distinct = s_carry;
-    const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (uint32_t b0 = 0; b0 < ntiles; b0 += 1024) {
-        const uint32_t i = b0 + threadIdx.x;
-        const uint32_t v = i < ntiles ? a.tile_max[i] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_excl_max<1024>(v, s_tmp, &tot);
-        if (i < ntiles) a.tile_pref[i] = max(s_carry, ex);
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry = max(s_carry, tot);
-        __syncthreads();
+    {
+        const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
+        const uint32_t per = (ntiles + 1023u) / 1024u;
+        const uint32_t t0 = min(threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
+        uint32_t mx = 0;
+        for (uint32_t t = t0; t < t1; ++t) mx = max(mx, a.tile_max[t]);
+        uint32_t run = block_excl_max<1024>(mx, s_tmp, nullptr);
+        for (uint32_t t = t0; t < t1; ++t) {
+            a.tile_pref[t] = run;
+            run = max(run, a.tile_max[t]);
+        }
     }
 }
 
-// Dense keys and their start position below the pinned levels. One warp per sub-tile.
+// Dense distinct keys: one warp copies each sub-tile's keys to their dense place.
+__global__ void __launch_bounds__(kThreads) k_dpack(DescendArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
+    const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
+    const uint32_t sub = blockIdx.x * (kThreads / 32) + warp;
+    if (sub >= nsub) return;
+    const uint32_t c = a.sub_cnt[sub], d0 = a.sub_pref[sub];
+    for (uint32_t j = (uint32_t)lane; j < c; j += 32u) a.dq[d0 + j] = a.hq[sub * kSubTile + j];
+}
+
+// Start position below the pinned levels for every distinct key (one per thread): one
+// binary search of the lowest pinned level (in shared memory, copied per CTA by TMA
+// bulk copies), then a walk of the levels down to top_launched + 1.
 __global__ void __launch_bounds__(kThreads) k_top(DescendArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
     uint32_t* s_d = reinterpret_cast<uint32_t*>(s_dyn + (kSmemTopMax + kPad) * sizeof(uint64_t));
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ int s_fail;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const DevMeta* m = a.m;
     if (block_sees_error(&m->error)) return;
     const uint32_t H = m->H, Ls = m->Ls, Lb = m->Lb, E = m->smem_entries;
-    const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
+    const uint32_t D = a.bm->distinct;
+    if (blockIdx.x * kThreads >= D) return;
     if (tid == 0) s_fail = 0;
     if (E > 0) {
         if (tid == 0) {
@@ -238,27 +252,22 @@ __global__ void __launch_bounds__(kThreads) k_top(DescendArgs a) {
         }
     }
     const uint32_t bL = m->base[Ls], nL = m->n[Ls];
-    for (uint32_t sub = blockIdx.x * (kThreads / 32) + warp; sub < nsub; sub += gridDim.x * (kThreads / 32)) {
-        const uint32_t c = a.sub_cnt[sub], d0 = a.sub_pref[sub];
-        for (uint32_t j = (uint32_t)lane; j < c; j += 32u) {
-            const uint64_t q = a.hq[sub * kSubTile + j];
-            uint32_t lo = 0;
-            if (Ls <= H) {
-                const int32_t r = smem_rank(s_k + bL, nL, q);
-                lo = (r >= 0) ? s_d[bL + r] : 0u;
-            }
-            // levels between the pinned ones and the top launched level (only when
-            // the index grew past the host's last view of it): walked here
-            for (int l = (Ls <= H ? (int)Ls - 1 : (int)H); l > a.top_launched && l >= (int)Lb; --l) {
-                int32_t r = -1;
-                uint32_t dn = 0;
-                uint64_t kr = 0;
-                lane_scan<true>(a.lkeys + m->base[l], a.ldown + m->base[l], lo, m->n[l], q, r, dn, kr, a.err);
-                lo = (r >= 0) ? dn : 0u;
-            }
-            a.dq[d0 + j] = q;
-            a.dlo[d0 + j] = lo;
+    for (uint32_t d = blockIdx.x * kThreads + tid; d < D; d += gridDim.x * kThreads) {
+        const uint64_t q = a.dq[d];
+        uint32_t lo = 0;
+        if (Ls <= H) {
+            const int32_t r = smem_rank(s_k + bL, nL, q);
+            lo = (r >= 0) ? s_d[bL + r] : 0u;
         }
+        // levels between the pinned ones and the top launched level: walked here
+        for (int l = (Ls <= H ? (int)Ls - 1 : (int)H); l > a.top_launched && l >= (int)Lb; --l) {
+            int32_t r = -1;
+            uint32_t dn = 0;
+            uint64_t kr = 0;
+            lane_scan<true>(a.lkeys + m->base[l], a.ldown + m->base[l], lo, m->n[l], q, r, dn, kr, a.err);
+            lo = (r >= 0) ? dn : 0u;
+        }
+        a.dlo[d] = lo;
     }
 }
 
@@ -330,12 +339,13 @@ cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
     const uint32_t blocks = (nsub + 7) / 8;
     k_distinct<<<blocks, kThreads, 0, s>>>(a);
     k_dscan<<<1, 1024, 0, s>>>(a);
-    const uint32_t capt = (uint32_t)num_sms * 8u;
-    k_top<<<(int)(blocks < capt ? blocks : capt), kThreads, dyn, s>>>(a);
+    k_dpack<<<blocks, kThreads, 0, s>>>(a);
+    const uint32_t need = (a.n + kThreads - 1) / kThreads;
+    k_top<<<need, kThreads, dyn, s>>>(a);  // CTAs past the distinct keys exit at once
     // one launch per index level from top_launched down to 2; a launch whose level is
     // pinned or not built exits at once, and levels above top_launched that are
     // neither (the index grew) are walked by k_top
-    const uint32_t need = (a.n + kThreads - 1) / kThreads, capg = (uint32_t)num_sms * 16u;
+    const uint32_t capg = (uint32_t)num_sms * 16u;
     const uint32_t gblocks = need < capg ? need : capg;  // grid-stride over the distinct keys
     for (int l = a.top_launched; l >= 2; --l) k_level<<<gblocks, kThreads, 0, s>>>(a, l);
     k_locate<<<gblocks, kThreads, 0, s>>>(a);

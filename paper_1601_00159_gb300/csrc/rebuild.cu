@@ -360,12 +360,13 @@ __device__ __forceinline__ uint32_t members(uint32_t hw, uint32_t l) {
     return ((hw | 0x80808080u) - l * 0x01010101u) & 0x80808080u;
 }
 
-constexpr uint32_t kKeyBytes = (kNodes + 2) * sizeof(uint64_t);
 constexpr uint32_t kMetaBytes = kNodes + 16;
 constexpr uint32_t kWarpNodes = kNodes / 8;  // 512 nodes per warp
 
-// One tile of 4096 nodes per CTA: keys and meta arrive in shared memory by TMA bulk
-// copy. Warp w owns nodes [512 w, 512 w + 512); lane t holds nodes 16t..16t+15 of them.
+// One tile of 4096 nodes per CTA: the tile's meta arrives in shared memory by TMA bulk
+// copy; keys are read from global memory only for the nodes that enter the index layer
+// (about a quarter of them at p = 1/4, so key sectors holding none are never read).
+// Warp w owns nodes [512 w, 512 w + 512); lane t holds nodes 16t..16t+15 of them.
 //  1. per lane, a byte-wise membership test of its nodes for every level gives the
 //     warp's count per level (lane i accumulates level Lb + i); the warps' counts are
 //     prefixed across the tile (one barrier);
@@ -377,9 +378,8 @@ constexpr uint32_t kWarpNodes = kNodes / 8;  // 512 nodes per warp
 //     levels repeat step 3 on the shrinking list.
 __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     extern __shared__ __align__(16) uint8_t s_dyn[];
-    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);                   // kNodes + 2
-    uint8_t* s_meta = s_dyn + kKeyBytes;                                     // kNodes + 16
-    uint32_t* s_list = reinterpret_cast<uint32_t*>(s_dyn + kKeyBytes + kMetaBytes);  // 8 x 512
+    uint8_t* s_meta = s_dyn;                                              // kNodes + 16
+    uint32_t* s_list = reinterpret_cast<uint32_t*>(s_dyn + kMetaBytes);   // 8 x 512
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_wcnt[8][32];
     __shared__ uint32_t s_base[kLevelSlots], s_n[kLevelSlots];
@@ -399,16 +399,15 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     if (tid == 0) {
         s_ok = 1;
         mbar_init(&s_bar, 1);
-        const uint32_t bk = ((cnt * 8u + 15u) / 16u) * 16u;
         const uint32_t bm_ = ((cnt + 15u) / 16u) * 16u;
-        mbar_arrive_expect_tx(&s_bar, bk + bm_);
-        bulk_g2s(s_keys, a.st.keys[cur] + ts, bk, &s_bar);
+        mbar_arrive_expect_tx(&s_bar, bm_);
         bulk_g2s(s_meta, a.st.meta[cur] + ts, bm_, &s_bar);
     }
     if (tid < kLevelSlots) {
         s_base[tid] = m->base[tid];
         s_n[tid] = m->n[tid];
     }
+    const uint64_t* TK = a.st.keys[cur] + ts;  // this tile's keys
     __syncthreads();
     if (!mbar_wait_bounded(&s_bar, 0, a.err)) s_ok = 0;
     const uint32_t w0 = (uint32_t)warp * kWarpNodes;
@@ -493,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
                 const uint32_t p = base + j;
                 if (p < s_n[l]) {
                     const uint32_t g = s_base[l] + p;
-                    a.lkeys[g] = s_keys[node];
+                    a.lkeys[g] = TK[node];
                     a.ldown[g] = (l == Lb) ? ts + node : prev_base + (e >> 16);
                 } else {
                     atomicOr(a.err, kErrBounds);
@@ -652,7 +651,7 @@ cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s) {
 
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
     static bool attr_set = false;
-    const int dyn = (int)(kKeyBytes + kMetaBytes + 8 * kWarpNodes * 4);
+    const int dyn = (int)(kMetaBytes + 8 * kWarpNodes * 4);
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_rebuild_write, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
