@@ -157,6 +157,15 @@ int pi_execute_batch_noalloc(pi_index_t* idx, const uint8_t* ops, const uint64_t
                              const uint64_t* values, uint64_t n, pi_result_t* results,
                              pi_stream_t stream);
 
+/*
+ * pi_flush -- makes `stream` wait (on the device, without blocking the host) until all
+ * work the index has in flight has finished. A batch's index-layer rebuild runs in the
+ * background on a library-owned stream, as the paper's rebuild daemon does (Section
+ * 4.4.4): the next batch, and every other call on the index, waits for it by itself,
+ * so this is needed only to include that work in a caller's own timing or ordering.
+ */
+int pi_flush(pi_index_t* idx, pi_stream_t stream);
+
 /* Releases every device allocation of the index after its pending work. NULL-safe. */
 void pi_destroy(pi_index_t* idx);
 

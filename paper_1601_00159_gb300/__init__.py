@@ -21,7 +21,7 @@ PI_MAX_KEYS = (1 << 30) - 2
 
 EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
             "pi_last_error", "pi_status", "pi_info", "pi_export", "pi_export_level", "pi_profile",
-            "pi_profile_read", "pi_execute_batch_noalloc"]
+            "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush"]
 PI_NOALLOC_MAX_BATCH = 1 << 16
 STAGES = ["sort", "descend", "apply", "merge", "layout", "rebuild"]
 
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH):
     lib.pi_export.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64), vp]
     lib.pi_export_level.restype = i32
     lib.pi_export_level.argtypes = [vp, i32, vp, vp, u64, ctypes.POINTER(u64), vp]
+    lib.pi_flush.restype = i32
+    lib.pi_flush.argtypes = [vp, vp]
     lib.pi_profile.restype = i32
     lib.pi_profile.argtypes = [vp, i32]
     lib.pi_profile_read.restype = i32
@@ -206,6 +208,10 @@ class Index:
         _chk(self.lib.pi_export_level(self._h, level, k.data_ptr(), d.data_ptr(), n.value, ctypes.byref(n),
                                       _stream_handle(stream)), "pi_export_level")
         return k[: n.value], d[: n.value]
+
+    def flush(self, stream=None):
+        """pi_flush: make the stream wait for the index's background work."""
+        _chk(self.lib.pi_flush(self._h, _stream_handle(stream)), "pi_flush")
 
     def profile(self, enable: bool):
         _chk(self.lib.pi_profile(self._h, 1 if enable else 0), "pi_profile")

@@ -65,7 +65,7 @@ struct pi_index {
     uint32_t smem_top = kSmemTopMax;  // pinned-entry cap
     uint32_t test_flags = 0;
     DevMeta* d_meta = nullptr;
-    BatchMeta* d_bm = nullptr;
+    BatchMeta* d_bm = nullptr;  // two per-batch counter blocks, alternating between batches
     uint32_t* d_dofs = nullptr;
     uint32_t* d_count = nullptr;
     Storage st{};
@@ -93,10 +93,16 @@ struct pi_index {
     bool force_rebuild = false;
     // stage timing (pi_profile): events recorded between the pipeline's kernels
     bool prof = false;
-    cudaEvent_t* pev = nullptr;  // kProfSlots batches x (PI_NUM_STAGES + 1) events
+    cudaEvent_t* pev = nullptr;  // kProfSlots batches x kProfEvents events
     uint32_t pused = 0;          // batches recorded but not folded yet
     double pms[PI_NUM_STAGES] = {};
     uint64_t pbatches = 0;
+    // Background rebuild (Section 4.4.4): the index-layer rebuild of a batch runs on its
+    // own stream, overlapping the next batch's sort; the next batch's descent waits for
+    // it (ev_rebuilt), and so does every other use of the index state.
+    cudaStream_t rs = nullptr;
+    cudaEvent_t ev_applied = nullptr, ev_rebuilt = nullptr;
+    bool rebuild_pending = false;
 };
 
 namespace {
@@ -241,15 +247,20 @@ cudaError_t alloc_storage(Storage& st, uint64_t cap) {
     return e;
 }
 
-constexpr uint32_t kProfSlots = 4096;
+constexpr uint32_t kProfSlots = 2048;
+// Per batch: 0 start, 1 after sort, 2 after waiting for the previous rebuild, 3 after
+// descent, 4 after apply, 5 after merge, 6 after layout, 7 rebuild start, 8 rebuild end.
+constexpr int kProfEvents = 9;
 
 void prof_fold(pi_index* x) {
+    static const int from[PI_NUM_STAGES] = {0, 2, 3, 4, 5, 7};
     for (uint32_t b = 0; b < x->pused; ++b) {
-        cudaEvent_t* e = x->pev + (size_t)b * (PI_NUM_STAGES + 1);
-        cudaEventSynchronize(e[PI_NUM_STAGES]);
+        cudaEvent_t* e = x->pev + (size_t)b * kProfEvents;
+        cudaEventSynchronize(e[8]);
+        cudaEventSynchronize(e[6]);
         for (int st = 0; st < PI_NUM_STAGES; ++st) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, e[st], e[st + 1]) == cudaSuccess) x->pms[st] += ms;
+            if (cudaEventElapsedTime(&ms, e[from[st]], e[from[st] + 1]) == cudaSuccess) x->pms[st] += ms;
         }
         x->pbatches++;
     }
@@ -259,7 +270,7 @@ void prof_fold(pi_index* x) {
 // Event for stage boundary k of the batch being enqueued (nullptr when not profiling).
 cudaEvent_t prof_event(pi_index* x, int k) {
     if (!x->prof) return nullptr;
-    return x->pev[(size_t)x->pused * (PI_NUM_STAGES + 1) + k];
+    return x->pev[(size_t)x->pused * kProfEvents + k];
 }
 
 void prof_mark(pi_index* x, int k, cudaStream_t s) {
@@ -271,7 +282,7 @@ void destroy(pi_index* x) {
     cudaSetDevice(x->device);
     cudaDeviceSynchronize();
     if (x->pev) {
-        for (size_t i = 0; i < (size_t)kProfSlots * (PI_NUM_STAGES + 1); ++i) cudaEventDestroy(x->pev[i]);
+        for (size_t i = 0; i < (size_t)kProfSlots * kProfEvents; ++i) cudaEventDestroy(x->pev[i]);
         delete[] x->pev;
     }
     free_scratch(x->sc);
@@ -280,6 +291,9 @@ void destroy(pi_index* x) {
     dfree(x->lkeys); dfree(x->ldown);
     dfree(x->desc); dfree(x->lcnt); dfree(x->loff); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
     if (x->h_mbox) cudaFreeHost(x->h_mbox);
+    if (x->ev_applied) cudaEventDestroy(x->ev_applied);
+    if (x->ev_rebuilt) cudaEventDestroy(x->ev_rebuilt);
+    if (x->rs) cudaStreamDestroy(x->rs);
     for (auto& e : x->ev)
         if (e) cudaEventDestroy(e);
     delete x;
@@ -323,8 +337,15 @@ void refresh_known(pi_index* x) {
     x->pending_n = p;
 }
 
+// Makes `s` wait for the background rebuild still in flight, if any (no host sync).
+void wait_rebuild(pi_index* x, cudaStream_t s) {
+    if (x->rebuild_pending) cudaStreamWaitEvent(s, x->ev_rebuilt, 0);
+}
+
 cudaError_t sync_known(pi_index* x, cudaStream_t s) {
+    wait_rebuild(x, s);
     cudaError_t e = read_meta(x, s, &x->known);
+    if (e == cudaSuccess) x->rebuild_pending = false;
     if (e == cudaSuccess) {
         for (uint64_t b = x->seen; b < x->issued; ++b) cudaEventSynchronize(x->ev[b % kRing]);
         x->seen = x->issued;
@@ -414,12 +435,12 @@ int top_launched_for(const pi_index* x) {
     return l < 2 ? 2 : l;
 }
 
-RebuildArgs rebuild_args(pi_index* x, uint32_t size_ub, uint32_t force) {
+RebuildArgs rebuild_args(pi_index* x, BatchMeta* bm, uint32_t size_ub, uint32_t force) {
     RebuildArgs r{};
     r.st = x->st;
     r.nn = x->sc.nn;
     r.m = x->d_meta;
-    r.bm = x->d_bm;
+    r.bm = bm;
     r.lkeys = x->lkeys;
     r.ldown = x->ldown;
     r.desc = x->desc;
@@ -509,6 +530,104 @@ cudaError_t noalloc_scratch_for(int device, uint8_t** out) {
     return cudaSuccess;
 }
 
+// Enqueues one batch (Algorithm 1) with the given per-batch scratch:
+//   stream s:  pack + sort -> [wait for the previous batch's rebuild] -> descent ->
+//              ownership + apply -> merge -> layout -> meta to the mailbox ring
+//   stream rs: [wait for this batch's layout] -> index-layer rebuild
+// The rebuild thus overlaps the next batch's sort (the paper's background rebuild,
+// Section 4.4.4). Results are complete when `s` completes.
+int enqueue_batch(pi_index* x, const Scratch& sc, const uint8_t* ops, const uint64_t* keys,
+                  const uint64_t* values, uint64_t n, pi_result_t* results, uint64_t size_ub, cudaStream_t s) {
+    cudaError_t e;
+    BatchMeta* bm = x->d_bm + (x->issued & 1u);  // the other block may still be read by the rebuild
+    uint32_t ep = next_epochs(x, 16, s);
+    if (x->prof && x->pused == kProfSlots) prof_fold(x);
+    prof_mark(x, 0, s);
+    cudaMemsetAsync(bm, 0, sizeof(BatchMeta), s);
+    SortBuffers sb = sort_buffers(x, sc);
+    if ((e = launch_sort(ops, keys, (uint32_t)n, sb, bm, &x->d_meta->error, ep, s, x->num_sms)) != cudaSuccess)
+        return map_cuda(e);
+    prof_mark(x, 1, s);
+    wait_rebuild(x, s);
+    prof_mark(x, 2, s);
+    DescendArgs da{};
+    da.sk = sc.a_k;
+    da.sp = sc.a_p;
+    da.tile_max = sc.tile_max;
+    da.tile_pref = sc.tile_pref;
+    da.hq = sc.hq;
+    da.sub_cnt = sc.sub_cnt;
+    da.sub_pref = sc.sub_pref;
+    da.dq = sc.dq;
+    da.dlo = sc.dlo;
+    da.top_launched = top_launched_for(x);
+    da.m = x->d_meta;
+    da.bm = bm;
+    da.lkeys = x->lkeys;
+    da.ldown = x->ldown;
+    da.st = x->st;
+    da.loc = sc.loc;
+    da.flags = sc.flags;
+    da.val0 = sc.val0;
+    da.n = (uint32_t)n;
+    da.err = &x->d_meta->error;
+    if ((e = launch_descend(da, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 3, s);
+    ApplyArgs aa{};
+    aa.sk = sc.a_k;
+    aa.sp = sc.a_p;
+    aa.loc = sc.loc;
+    aa.flags = sc.flags;
+    aa.val0 = sc.val0;
+    aa.uvals = values;
+    aa.results = results;
+    aa.st = x->st;
+    aa.nn = sc.nn;
+    aa.m = x->d_meta;
+    aa.bm = bm;
+    aa.desc = x->desc;
+    aa.tile_max = sc.tile_max;
+    aa.tile_pref = sc.tile_pref;
+    aa.tile_new = sc.tile_new;
+    aa.sub_pref = sc.sub_pref;
+    aa.stage = sc.stage;
+    aa.lcnt = x->lcnt;
+    aa.lstride = x->lstride;
+    aa.n = (uint32_t)n;
+    aa.hp = x->hp;
+    aa.err = &x->d_meta->error;
+    if ((e = launch_apply(aa, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 4, s);
+    RebuildArgs ra = rebuild_args(x, bm, (uint32_t)size_ub, x->force_rebuild ? 1u : 0u);
+    ra.nn = sc.nn;
+    if ((e = launch_merge(ra, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 5, s);
+    if ((e = launch_level_bases(ra, s)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 6, s);
+    const uint64_t slot = x->issued % kRing;
+    if (x->issued - x->seen >= kRing) {  // the slot is still unread: wait for its batch
+        cudaEventSynchronize(x->ev[slot]);
+        refresh_known(x);
+    }
+    cudaMemcpyAsync(&x->h_mbox[slot], x->d_meta, sizeof(DevMeta), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(x->ev[slot], s);
+    // the rebuild, in the background
+    cudaEventRecord(x->ev_applied, s);
+    cudaStreamWaitEvent(x->rs, x->ev_applied, 0);
+    prof_mark(x, 7, x->rs);
+    if ((e = launch_rebuild(ra, ep, x->rs, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 8, x->rs);
+    cudaEventRecord(x->ev_rebuilt, x->rs);
+    x->rebuild_pending = true;
+    if (x->prof) x->pused++;
+    x->epoch = ep;
+    x->force_rebuild = false;
+    x->ring_n[slot] = n;
+    x->issued++;
+    x->pending_n += n;
+    return map_cuda(cudaGetLastError());
+}
+
 }  // namespace
 
 extern "C" {
@@ -562,11 +681,14 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
         if (e != cudaSuccess) break;
         if ((e = cudaMallocHost(reinterpret_cast<void**>(&x->h_mbox), kRing * sizeof(DevMeta))) != cudaSuccess) break;
         if ((e = dalloc(&x->d_meta, 1)) != cudaSuccess) break;
-        if ((e = dalloc(&x->d_bm, 1)) != cudaSuccess) break;
+        if ((e = dalloc(&x->d_bm, 2)) != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&x->rs, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaEventCreateWithFlags(&x->ev_applied, cudaEventDisableTiming)) != cudaSuccess) break;
+        if ((e = cudaEventCreateWithFlags(&x->ev_rebuilt, cudaEventDisableTiming)) != cudaSuccess) break;
         if ((e = dalloc(&x->d_dofs, 8 * 256)) != cudaSuccess) break;
         if ((e = dalloc(&x->d_count, 1)) != cudaSuccess) break;
         cudaMemsetAsync(x->d_meta, 0, sizeof(DevMeta), s);
-        cudaMemsetAsync(x->d_bm, 0, sizeof(BatchMeta), s);
+        cudaMemsetAsync(x->d_bm, 0, 2 * sizeof(BatchMeta), s);
         if ((e = alloc_storage(x->st, st_cap)) != cudaSuccess) break;
         x->st_cap = st_cap;
         if ((e = ensure_tile_cnt(x, st_cap)) != cudaSuccess) break;
@@ -615,7 +737,7 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
         x->idx_cap = icap;
         // 2. lay out and build the index layer
         cudaMemsetAsync(x->d_bm, 0, sizeof(BatchMeta), s);
-        RebuildArgs ra = rebuild_args(x, (uint32_t)hm.size, 2u);
+        RebuildArgs ra = rebuild_args(x, x->d_bm, (uint32_t)hm.size, 2u);
         uint32_t ep = next_epochs(x, 4, s);
         if ((e = launch_merge(ra, ep, s, x->num_sms)) != cudaSuccess) break;
         if ((e = launch_level_bases(ra, s)) != cudaSuccess) break;
@@ -658,7 +780,9 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
     if (int rc = sticky_error(x->known)) return rc;
     // capacities (grow rarely; growing synchronises the stream)
     if (n > x->sc.cap) {
+        wait_rebuild(x, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
+        x->rebuild_pending = false;
         free_scratch(x->sc);
         uint64_t q = n < 4096 ? 4096 : n;
         if ((e = alloc_scratch(x->sc, q)) != cudaSuccess) return map_cuda(e);
@@ -679,83 +803,7 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
         }
         x->known.grow_request = 0;
     }
-    uint32_t ep = next_epochs(x, 16, s);
-    if (x->prof && x->pused == kProfSlots) prof_fold(x);
-    prof_mark(x, 0, s);
-    cudaMemsetAsync(x->d_bm, 0, sizeof(BatchMeta), s);
-    SortBuffers sb = sort_buffers(x, x->sc);
-    if ((e = launch_sort(ops, keys, (uint32_t)n, sb, x->d_bm, &x->d_meta->error, ep, s, x->num_sms)) != cudaSuccess)
-        return map_cuda(e);
-    DescendArgs da{};
-    da.sk = x->sc.a_k;
-    da.sp = x->sc.a_p;
-    da.tile_max = x->sc.tile_max;
-    da.tile_pref = x->sc.tile_pref;
-    da.hq = x->sc.hq;
-    da.sub_cnt = x->sc.sub_cnt;
-    da.sub_pref = x->sc.sub_pref;
-    da.dq = x->sc.dq;
-    da.dlo = x->sc.dlo;
-    da.top_launched = top_launched_for(x);
-    da.m = x->d_meta;
-    da.bm = x->d_bm;
-    da.lkeys = x->lkeys;
-    da.ldown = x->ldown;
-    da.st = x->st;
-    da.loc = x->sc.loc;
-    da.flags = x->sc.flags;
-    da.val0 = x->sc.val0;
-    da.n = (uint32_t)n;
-    da.err = &x->d_meta->error;
-    prof_mark(x, 1, s);
-    if ((e = launch_descend(da, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
-    prof_mark(x, 2, s);
-    ApplyArgs aa{};
-    aa.sk = x->sc.a_k;
-    aa.sp = x->sc.a_p;
-    aa.loc = x->sc.loc;
-    aa.flags = x->sc.flags;
-    aa.val0 = x->sc.val0;
-    aa.uvals = values;
-    aa.results = results;
-    aa.st = x->st;
-    aa.nn = x->sc.nn;
-    aa.m = x->d_meta;
-    aa.bm = x->d_bm;
-    aa.desc = x->desc;
-    aa.tile_max = x->sc.tile_max;
-    aa.tile_pref = x->sc.tile_pref;
-    aa.tile_new = x->sc.tile_new;
-    aa.sub_pref = x->sc.sub_pref;
-    aa.stage = x->sc.stage;
-    aa.lcnt = x->lcnt;
-    aa.lstride = x->lstride;
-    aa.n = (uint32_t)n;
-    aa.hp = x->hp;
-    aa.err = &x->d_meta->error;
-    if ((e = launch_apply(aa, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
-    prof_mark(x, 3, s);
-    RebuildArgs ra = rebuild_args(x, (uint32_t)size_ub, x->force_rebuild ? 1u : 0u);
-    if ((e = launch_merge(ra, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
-    prof_mark(x, 4, s);
-    if ((e = launch_level_bases(ra, s)) != cudaSuccess) return map_cuda(e);
-    prof_mark(x, 5, s);
-    if ((e = launch_rebuild(ra, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
-    prof_mark(x, 6, s);
-    if (x->prof) x->pused++;
-    x->epoch = ep;
-    x->force_rebuild = false;
-    const uint64_t slot = x->issued % kRing;
-    if (x->issued - x->seen >= kRing) {  // the slot is still unread: wait for its batch
-        cudaEventSynchronize(x->ev[slot]);
-        refresh_known(x);
-    }
-    cudaMemcpyAsync(&x->h_mbox[slot], x->d_meta, sizeof(DevMeta), cudaMemcpyDeviceToHost, s);
-    cudaEventRecord(x->ev[slot], s);
-    x->ring_n[slot] = n;
-    x->issued++;
-    x->pending_n += n;
-    return map_cuda(cudaGetLastError());
+    return enqueue_batch(x, x->sc, ops, keys, values, n, results, size_ub, s);
 }
 
 int pi_execute_batch_host(pi_index_t* x, const uint8_t* ops_host, const uint64_t* keys_host,
@@ -810,83 +858,21 @@ int pi_execute_batch_noalloc(pi_index_t* x, const uint8_t* ops, const uint64_t* 
     }
     // An index layer that outgrew its capacity is not grown here: the rebuild then drops
     // its lowest levels and results stay exact.
-    uint32_t ep = next_epochs(x, 16, s);
-    cudaMemsetAsync(x->d_bm, 0, sizeof(BatchMeta), s);
-    SortBuffers sb = sort_buffers(x, sc);
-    if ((e = launch_sort(ops, keys, (uint32_t)n, sb, x->d_bm, &x->d_meta->error, ep, s, x->num_sms)) != cudaSuccess)
-        return map_cuda(e);
-    DescendArgs da{};
-    da.sk = sc.a_k;
-    da.sp = sc.a_p;
-    da.tile_max = sc.tile_max;
-    da.tile_pref = sc.tile_pref;
-    da.hq = sc.hq;
-    da.sub_cnt = sc.sub_cnt;
-    da.sub_pref = sc.sub_pref;
-    da.dq = sc.dq;
-    da.dlo = sc.dlo;
-    da.top_launched = top_launched_for(x);
-    da.m = x->d_meta;
-    da.bm = x->d_bm;
-    da.lkeys = x->lkeys;
-    da.ldown = x->ldown;
-    da.st = x->st;
-    da.loc = sc.loc;
-    da.flags = sc.flags;
-    da.val0 = sc.val0;
-    da.n = (uint32_t)n;
-    da.err = &x->d_meta->error;
-    if ((e = launch_descend(da, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
-    ApplyArgs aa{};
-    aa.sk = sc.a_k;
-    aa.sp = sc.a_p;
-    aa.loc = sc.loc;
-    aa.flags = sc.flags;
-    aa.val0 = sc.val0;
-    aa.uvals = values;
-    aa.results = results;
-    aa.st = x->st;
-    aa.nn = sc.nn;
-    aa.m = x->d_meta;
-    aa.bm = x->d_bm;
-    aa.desc = x->desc;
-    aa.tile_max = sc.tile_max;
-    aa.tile_pref = sc.tile_pref;
-    aa.tile_new = sc.tile_new;
-    aa.sub_pref = sc.sub_pref;
-    aa.stage = sc.stage;
-    aa.lcnt = x->lcnt;
-    aa.lstride = x->lstride;
-    aa.n = (uint32_t)n;
-    aa.hp = x->hp;
-    aa.err = &x->d_meta->error;
-    if ((e = launch_apply(aa, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
-    RebuildArgs ra = rebuild_args(x, (uint32_t)size_ub, x->force_rebuild ? 1u : 0u);
-    ra.nn = sc.nn;
-    if ((e = launch_merge(ra, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
-    if ((e = launch_level_bases(ra, s)) != cudaSuccess) return map_cuda(e);
-    if ((e = launch_rebuild(ra, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
-    x->epoch = ep;
-    x->force_rebuild = false;
-    const uint64_t slot = x->issued % kRing;
-    if (x->issued - x->seen >= kRing) {  // the slot is still unread: wait for its batch
-        cudaEventSynchronize(x->ev[slot]);
-        refresh_known(x);
-    }
-    cudaMemcpyAsync(&x->h_mbox[slot], x->d_meta, sizeof(DevMeta), cudaMemcpyDeviceToHost, s);
-    cudaEventRecord(x->ev[slot], s);
-    x->ring_n[slot] = n;
-    x->issued++;
-    x->pending_n += n;
-    return map_cuda(cudaGetLastError());
+    return enqueue_batch(x, sc, ops, keys, values, n, results, size_ub, s);
 }
 
 void pi_destroy(pi_index_t* x) { destroy(x); }
 
+int pi_flush(pi_index_t* x, pi_stream_t stream) {
+    if (!x) return PI_ERR_INVALID_ARG;
+    wait_rebuild(x, reinterpret_cast<cudaStream_t>(stream));
+    return map_cuda(cudaGetLastError());
+}
+
 int pi_profile(pi_index_t* x, int enable) {
     if (!x) return PI_ERR_INVALID_ARG;
     if (enable && !x->pev) {
-        const size_t cnt = (size_t)kProfSlots * (PI_NUM_STAGES + 1);
+        const size_t cnt = (size_t)kProfSlots * kProfEvents;
         x->pev = new (std::nothrow) cudaEvent_t[cnt];
         if (!x->pev) return PI_ERR_OOM;
         for (size_t i = 0; i < cnt; ++i) {
@@ -907,6 +893,7 @@ int pi_profile(pi_index_t* x, int enable) {
 
 int pi_profile_read(pi_index_t* x, double* stage_ms_host, uint64_t* batches_host, pi_stream_t stream) {
     if (!x || !stage_ms_host || !batches_host) return PI_ERR_INVALID_ARG;
+    wait_rebuild(x, reinterpret_cast<cudaStream_t>(stream));
     cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return map_cuda(e);
     prof_fold(x);
