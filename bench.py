@@ -36,7 +36,9 @@ from paper_1601_00159_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "Mqueries/s and % of HBM roofline on 1 GB300; p50/p99 latency in serving loop"
 UNIT = "Mqueries/s"
-KERNELS_PER_STEP = 17  # pack, plan, 8 radix passes, descend, apply, merge, layout, rebuild count/scan/write
+# ncu DRAM bytes of the rebuild's writer kernel, per storage node, are read from this
+# summary, which also records a digest of the writer's source they were taken with.
+WRITER_PROFILE = os.path.join(ROOT, "profiles", "k_rebuild_write_skewed_2p24.md")
 
 WORKLOADS = {
     "skewed": dict(fn=wl.skewed, n=1 << 27, q=1 << 22,
@@ -48,6 +50,30 @@ WORKLOADS = {
     "tiny": dict(fn=wl.tiny, n=1 << 16, q=1 << 14,
                  desc="plain PI, tiny: 2^16 uint64 keys, p=1/2, one batch of 2^14 searches (half hits)"),
 }
+
+
+def writer_source_digest():
+    """sha256 prefix of the writer kernel's source text (k_rebuild_write and its helpers)."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1601_00159_gb300", "csrc", "rebuild.cu")).read()
+    a, b = src.index("// Byte-wise arithmetic on a meta word"), src.index("// Bulk build:")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+
+
+def writer_traffic_per_node():
+    """(bytes per storage node, note) from the committed ncu summary, or (None, why)."""
+    import re
+    try:
+        text = open(WRITER_PROFILE).read()
+    except OSError:
+        return None, "no ncu summary"
+    m = re.search(r"source digest: `([0-9a-f]{16})`", text)
+    b = re.search(r"DRAM bytes per storage node: `([0-9.]+)`", text)
+    if not (m and b):
+        return None, "summary lacks digest or bytes"
+    if m.group(1) != writer_source_digest():
+        return None, "writer source changed since the ncu capture"
+    return float(b.group(1)), "ncu capture at 2^24 keys, scaled by storage nodes"
 
 
 def measured_peaks():
@@ -296,34 +322,23 @@ def run_ours(args, ws, rank, local):
     e2e_ms = reduce_max(e0.elapsed_time(e1), ws)
     e2e_value = ws * q * e2e_steps / (e2e_ms * 1e-3) / 1e6
 
-    # roofline of the dominant kernel (largest share of the step), from live CUDA events
+    # Roofline of the kernel that moves the most algorithmic bytes, k_rebuild_write (the
+    # rebuild's count and scan launches move a few KB): its duration is the CUDA-event
+    # interval around its launch on the rebuild stream, averaged over the timed batches.
     hbm, peak_kind = measured_peaks()
     per_stage = {k: v / max(nb, 1) for k, v in stage_ms.items()}
     hb = host_batches[0]
     ins = int((hb.ops == wl.OP_INSERT).sum())
-    uk, inv = np.unique(hb.keys, return_inverse=True)
-    distinct = len(uk)
-    live_before = info0["live"]
+    distinct = len(np.unique(hb.keys))
     sizes = info1["level_size"]
     size_after = info1["size"]
     writes = distinct  # upper bound: every distinct key may be written once
     ab = algorithmic_bytes(q, ins, distinct, distinct, writes, size_after, sizes, l2_bytes, 8)
-    stage_bytes = {"sort": ab["sort"] / 8, "rebuild": ab["rebuild"],
-                   "descend": ab["traversal"] + ab["storage"] + q * 12, "apply": ab["io"]}
-    dom = max(per_stage, key=lambda s: per_stage[s])
-    if dom == "sort":
-        launches = 8
-        per_launch_ms = per_stage["sort"] / 8
-        dom_bytes = stage_bytes["sort"]
-        kname = "k_sort_pass"
-    else:
-        launches = 1
-        per_launch_ms = per_stage[dom]
-        dom_bytes = stage_bytes.get(dom, 0.0)
-        kname = {"rebuild": "k_rebuild", "descend": "k_descend", "apply": "k_apply",
-                 "merge": "k_merge", "layout": "k_level_bases"}[dom]
-    achieved = dom_bytes / (per_launch_ms * 1e-3) / 1e9
-    rebuild_gbs = stage_bytes["rebuild"] / (per_stage["rebuild"] * 1e-3) / 1e9 if per_stage["rebuild"] > 0 else None
+    writer_ms = per_stage["rebuild_write"]
+    achieved = ab["rebuild"] / (writer_ms * 1e-3) / 1e9
+    per_node, traffic_note = writer_traffic_per_node()
+    traffic = per_node * size_after if per_node is not None else None
+    low = min(ab["rebuild"], traffic) if traffic is not None else ab["rebuild"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -332,17 +347,19 @@ def run_ours(args, ws, rank, local):
                    f"{args.workload}-keys{len(w.keys)}-batch{q}", "desc": spec["desc"], "keys": len(w.keys), "batch": q,
                    "distinct_batches_cycled": len(dbatches), "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2_flush": "none: storage layer and cycled batch inputs exceed L2"},
-        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_source": peak_kind, "traffic": None,
-                     "launches_per_step": launches, "ms_per_launch": per_launch_ms,
-                     "algorithmic_bytes_per_launch": dom_bytes},
+        "roofline": {"bound": "hbm", "kernel": "k_rebuild_write", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind, "traffic": traffic,
+                     "traffic_note": traffic_note,
+                     "frac_min_of_model_and_traffic": low / (writer_ms * 1e-3) / 1e9 / hbm,
+                     "launches_per_step": 1, "ms_per_launch": writer_ms,
+                     "algorithmic_bytes_per_launch": ab["rebuild"],
+                     "bytes_model": "9 B per storage node (key + meta scan) + 12 B per index entry written"},
         "batch_roofline": {"algorithmic_bytes": ab["total"], "achieved_gbs": ab["total"] / (ms_step * 1e-3) / 1e9,
-                           "frac": ab["total"] / (ms_step * 1e-3) / 1e9 / hbm,
-                           "rebuild_gbs": rebuild_gbs},
+                           "frac": ab["total"] / (ms_step * 1e-3) / 1e9 / hbm},
         "stages_ms": per_stage,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": q * 17, "d2h_bytes_per_step": q * 16,
                 "steps": e2e_steps},
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": info1["kernel_launches"] - info0["kernel_launches"],
         "clocks": clk.summary(),
         "index": {"size": info1["size"], "live": info1["live"], "tombstones": info1["tombstones"],
                   "top_level": info1["top_level"], "rebuilds_in_region": info1["rebuilds"] - info0["rebuilds"],

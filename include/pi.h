@@ -83,6 +83,12 @@ typedef struct {
 /* test_flags bit: give only the lowest index level a launch of its own in the
  * level-synchronous descent, so every other level takes the in-kernel walk. */
 #define PI_TEST_WALK_LEVELS 1u
+/* test_flags bit: sort every batch with all eight radix passes (no prefix fix-up). */
+#define PI_TEST_SORT_FULL 2u
+/* test_flags field (bits 4-6): sort batches with only k = 1..4 radix passes on the most
+ * significant varying key bytes, so the fix-up that orders key-prefix segments sees
+ * many long segments. The default is four passes. */
+#define PI_TEST_SORT_PREFIX(k) ((uint32_t)(k) << 4)
 
 /*
  * pi_create -- bulk-build an index from n (key, value) pairs (Section 3.1: the index
@@ -190,6 +196,7 @@ typedef struct {
     uint64_t index_capacity;
     uint64_t batches;        /* batches executed */
     uint64_t rebuilds;       /* index-layer rebuilds run (counts only when known) */
+    uint64_t kernel_launches; /* CUDA kernels the batch entry points have launched so far */
 } pi_info_t;
 int pi_info(pi_index_t* idx, pi_info_t* out_host, pi_stream_t stream);
 
@@ -207,15 +214,18 @@ int pi_export_level(pi_index_t* idx, int level, uint64_t* keys_out, uint32_t* do
 
 /*
  * Stage timing, for measurement (no counterpart in the paper). While enabled, each
- * pi_execute_batch records CUDA events on its stream between the pipeline's stages:
- *   0 pack + radix sort (K0, K1)        3 storage merge (K6a)
- *   1 descent + storage locate (K2, K3) 4 level layout (K6b)
- *   2 ownership + apply (K4, K5)        5 index-layer rebuild (K6c)
+ * pi_execute_batch records CUDA events between the pipeline's stages, on the stream
+ * each stage runs on:
+ *   0 pack + radix sort (K0, K1)        4 level layout (K6b)
+ *   1 descent + storage locate (K2, K3) 5 index-layer rebuild (K6c; background stream)
+ *   2 ownership + apply (K4, K5)        6 the rebuild's writer kernel alone (part of 5)
+ *   3 storage merge (K6a)
+ * The descent's stage excludes its wait for the previous batch's rebuild.
  * pi_profile(idx, 1) starts (and clears) the accumulation; pi_profile(idx, 0) stops it.
  * pi_profile_read synchronises `stream` and writes the summed milliseconds per stage to
  * stage_ms_host[PI_NUM_STAGES] and the number of batches they cover to *batches_host.
  */
-#define PI_NUM_STAGES 6
+#define PI_NUM_STAGES 7
 int pi_profile(pi_index_t* idx, int enable);
 int pi_profile_read(pi_index_t* idx, double* stage_ms_host, uint64_t* batches_host, pi_stream_t stream);
 

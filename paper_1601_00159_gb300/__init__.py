@@ -23,7 +23,14 @@ EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_h
             "pi_last_error", "pi_status", "pi_info", "pi_export", "pi_export_level", "pi_profile",
             "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush"]
 PI_NOALLOC_MAX_BATCH = 1 << 16
-STAGES = ["sort", "descend", "apply", "merge", "layout", "rebuild"]
+PI_TEST_WALK_LEVELS = 1
+PI_TEST_SORT_FULL = 2
+
+
+def PI_TEST_SORT_PREFIX(k: int) -> int:
+    """test_flags value: sort batches with k = 1..4 radix passes plus the prefix fix-up."""
+    return k << 4
+STAGES = ["sort", "descend", "apply", "merge", "layout", "rebuild", "rebuild_write"]
 
 
 class PiError(RuntimeError):
@@ -45,7 +52,7 @@ class PiInfo(ctypes.Structure):
                 ("smem_low_level", ctypes.c_uint32), ("promote_shift", ctypes.c_uint32),
                 ("level_size", ctypes.c_uint64 * 34), ("storage_capacity", ctypes.c_uint64),
                 ("index_capacity", ctypes.c_uint64), ("batches", ctypes.c_uint64),
-                ("rebuilds", ctypes.c_uint64)]
+                ("rebuilds", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "level_size"}

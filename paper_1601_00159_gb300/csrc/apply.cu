@@ -256,8 +256,11 @@ cudaError_t launch_apply(const ApplyArgs& a, uint32_t& epoch, cudaStream_t s, in
     if (a.n == 0) return cudaSuccess;
     const uint32_t tiles = (a.n + kApplyTile - 1) / kApplyTile;
     k_apply<<<tiles, kThreads, 0, s>>>(a);  // tile prefixes come from the descent's scan
+    ++g_launches;
     k_new_scan<<<1, 1024, 0, s>>>(a);
+    ++g_launches;
     k_new_pack<<<tiles, kThreads, 0, s>>>(a);
+    ++g_launches;
     return cudaGetLastError();
 }
 

@@ -43,17 +43,22 @@ struct DevMeta {
     uint32_t updates;      // node changes since the last rebuild
     uint32_t rebuilds;     // rebuilds run
     uint32_t batches;      // batches run
-    uint32_t pad_[2];
+    uint32_t sort_fix_big; // last batch: queries in key-prefix segments sorted by one CTA
+    uint32_t pad_;
     uint32_t cnt[kLevelSlots];   // live keys with height >= l, kept current every batch
     uint32_t n[kLevelSlots];     // n[l]: size of built level l
     uint32_t base[kLevelSlots];  // built level l occupies [base[l], base[l] + n[l]] (+ sentinel)
 };
 
 struct SortPlan {
+    uint64_t pmask;   // the key bytes the passes sort
     uint32_t npass;
     uint32_t digit[8];
     uint32_t src[8];  // 0 = packed input, 1 = buffer A, 2 = buffer B
     uint32_t dst[8];
+    uint32_t fix;     // 1: segments of equal pmask bytes still need ordering by the full key
+    uint32_t nr;      // the other bytes that can differ inside a segment, ascending in rdig
+    uint32_t rdig[8];
 };
 
 // Per-batch scratch counters, cleared by one memset at the start of every batch.
@@ -70,6 +75,7 @@ struct BatchMeta {
     uint32_t distinct;           // distinct keys of the batch (local run heads)
     uint32_t bmax[8];            // per key byte: its maximum over the batch
     uint32_t bnmin[8];           // per key byte: 255 - its minimum over the batch
+    uint32_t fix_big;            // queries in key-prefix segments longer than one warp
     SortPlan plan;
 };
 
@@ -421,12 +427,15 @@ struct SortBuffers {
     uint32_t* tcnt;      // [tiles][256] per-tile digit counts of the current pass
     uint32_t* toff;      // [tiles][256] per-tile digit offsets of the current pass
     uint8_t* ndig;       // next pass's digit of every element, in the current pass's output order
+    uint32_t* fixmap;    // [ceil(n / 32)] bit per position: start of a segment to reorder
 };
 
 // Radix sort of (key, payload) pairs: result in a_k / a_p, stable, by key.
 // ops may be NULL (all searches). Counts invalid queries into bm->invalid.
+// At most max_passes (1..8) digit passes run, on the most significant bytes that vary;
+// when more bytes vary, runs of equal sorted bytes are then ordered by the rest.
 cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, const SortBuffers& sb,
-                        BatchMeta* bm, uint32_t* err, uint32_t& epoch, cudaStream_t s, int num_sms);
+                        BatchMeta* bm, uint32_t* err, cudaStream_t s, int num_sms, int max_passes);
 
 struct DescendArgs {
     const uint64_t* sk;  // sorted keys
@@ -500,7 +509,13 @@ struct RebuildArgs {
 };
 cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
 cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s);
+// Kernels launched by this host thread (every launcher adds the launches it issues); the
+// batch entry points fold the difference into the index's own count.
+extern thread_local uint64_t g_launches;
+
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
+cudaError_t launch_rebuild_prep(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
+cudaError_t launch_rebuild_write(const RebuildArgs& a, cudaStream_t s);
 
 // Bulk build: sorted (key, payload) -> storage layer (last duplicate wins) + counts.
 struct CreateArgs {

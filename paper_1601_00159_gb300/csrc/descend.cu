@@ -338,17 +338,25 @@ cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
     const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
     const uint32_t blocks = (nsub + 7) / 8;
     k_distinct<<<blocks, kThreads, 0, s>>>(a);
+    ++g_launches;
     k_dscan<<<1, 1024, 0, s>>>(a);
+    ++g_launches;
     k_dpack<<<blocks, kThreads, 0, s>>>(a);
+    ++g_launches;
     const uint32_t need = (a.n + kThreads - 1) / kThreads;
     k_top<<<need, kThreads, dyn, s>>>(a);  // CTAs past the distinct keys exit at once
+    ++g_launches;
     // one launch per index level from top_launched down to 2; a launch whose level is
     // pinned or not built exits at once, and levels above top_launched that are
     // neither (the index grew) are walked by k_top
     const uint32_t capg = (uint32_t)num_sms * 16u;
     const uint32_t gblocks = need < capg ? need : capg;  // grid-stride over the distinct keys
-    for (int l = a.top_launched; l >= 2; --l) k_level<<<gblocks, kThreads, 0, s>>>(a, l);
+    for (int l = a.top_launched; l >= 2; --l) {
+        k_level<<<gblocks, kThreads, 0, s>>>(a, l);
+        ++g_launches;
+    }
     k_locate<<<gblocks, kThreads, 0, s>>>(a);
+    ++g_launches;
     return cudaGetLastError();
 }
 

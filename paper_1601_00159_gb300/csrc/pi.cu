@@ -13,6 +13,10 @@
 
 #include "common.cuh"
 
+namespace pi {
+thread_local uint64_t g_launches = 0;
+}  // namespace pi
+
 using namespace pi;
 
 namespace {
@@ -40,6 +44,7 @@ struct Scratch {
     uint32_t* tcnt = nullptr;  // radix sort: per-tile digit counts
     uint32_t* toff = nullptr;  // radix sort: per-tile digit offsets
     uint8_t* ndig = nullptr;   // radix sort: next pass's digits
+    uint32_t* fixmap = nullptr;  // radix sort: segment marks of the prefix fix-up
     uint64_t* hq = nullptr;    // descent: distinct keys per sub-tile
     uint32_t* sub_cnt = nullptr;
     uint32_t* sub_pref = nullptr;
@@ -64,6 +69,8 @@ struct pi_index {
     uint32_t rebuild_policy = 0, threshold_pct = 15;
     uint32_t smem_top = kSmemTopMax;  // pinned-entry cap
     uint32_t test_flags = 0;
+    uint64_t launches = 0;            // kernels launched by the batch entry points
+    uint32_t full_sort_left = 0;      // batches still sorted with all eight passes
     DevMeta* d_meta = nullptr;
     BatchMeta* d_bm = nullptr;  // two per-batch counter blocks, alternating between batches
     uint32_t* d_dofs = nullptr;
@@ -193,7 +200,7 @@ void free_scratch(Scratch& s) {
     dfree(s.nn.keys); dfree(s.nn.vals); dfree(s.nn.loc); dfree(s.nn.height);
     dfree(s.stage.keys); dfree(s.stage.vals); dfree(s.stage.loc); dfree(s.stage.height);
     dfree(s.tile_max); dfree(s.tile_pref); dfree(s.tile_new);
-    dfree(s.tcnt); dfree(s.toff); dfree(s.ndig);
+    dfree(s.tcnt); dfree(s.toff); dfree(s.ndig); dfree(s.fixmap);
     dfree(s.hq); dfree(s.sub_cnt); dfree(s.sub_pref); dfree(s.dq); dfree(s.dlo);
     s.cap = 0;
 }
@@ -216,6 +223,7 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     const uint64_t stiles = (q + kSortTile - 1) / kSortTile + 1;
     PI_TRY(dalloc(&s.tcnt, stiles * 256)); PI_TRY(dalloc(&s.toff, stiles * 256));
     PI_TRY(dalloc(&s.ndig, stiles * kSortTile + 16));
+    PI_TRY(dalloc(&s.fixmap, c / 32 + 1));
     const uint64_t nsub = (q + kSubTile - 1) / kSubTile + 1;
     PI_TRY(dalloc(&s.hq, nsub * kSubTile)); PI_TRY(dalloc(&s.sub_cnt, nsub)); PI_TRY(dalloc(&s.sub_pref, nsub));
     PI_TRY(dalloc(&s.dq, c)); PI_TRY(dalloc(&s.dlo, c));
@@ -249,18 +257,20 @@ cudaError_t alloc_storage(Storage& st, uint64_t cap) {
 
 constexpr uint32_t kProfSlots = 2048;
 // Per batch: 0 start, 1 after sort, 2 after waiting for the previous rebuild, 3 after
-// descent, 4 after apply, 5 after merge, 6 after layout, 7 rebuild start, 8 rebuild end.
-constexpr int kProfEvents = 9;
+// descent, 4 after apply, 5 after merge, 6 after layout, 7 rebuild start, 8 before the
+// rebuild's writer kernel, 9 rebuild end.
+constexpr int kProfEvents = 10;
 
 void prof_fold(pi_index* x) {
-    static const int from[PI_NUM_STAGES] = {0, 2, 3, 4, 5, 7};
+    static const int from[PI_NUM_STAGES] = {0, 2, 3, 4, 5, 7, 8};
+    static const int to[PI_NUM_STAGES] = {1, 3, 4, 5, 6, 9, 9};
     for (uint32_t b = 0; b < x->pused; ++b) {
         cudaEvent_t* e = x->pev + (size_t)b * kProfEvents;
-        cudaEventSynchronize(e[8]);
+        cudaEventSynchronize(e[9]);
         cudaEventSynchronize(e[6]);
         for (int st = 0; st < PI_NUM_STAGES; ++st) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, e[from[st]], e[from[st] + 1]) == cudaSuccess) x->pms[st] += ms;
+            if (cudaEventElapsedTime(&ms, e[from[st]], e[to[st]]) == cudaSuccess) x->pms[st] += ms;
         }
         x->pbatches++;
     }
@@ -308,6 +318,7 @@ SortBuffers sort_buffers(pi_index* x, const Scratch& s) {
     sb.tcnt = s.tcnt;
     sb.toff = s.toff;
     sb.ndig = s.ndig;
+    sb.fixmap = s.fixmap;
     return sb;
 }
 
@@ -475,6 +486,7 @@ constexpr uint64_t noalloc_bytes(uint64_t q) {
            + 2 * al256(cs * 8) + al256(cs * 4) + al256(cs)        // new-node staging
            + 3 * al256(tiles * 4)                                 // tile max / prefix / new
            + 2 * al256(stiles * 256 * 4) + al256(stiles * kSortTile + 16)  // tcnt, toff, ndig
+           + al256((c / 32 + 1) * 4)                              // fixmap
            + al256(nsub * kSubTile * 8) + 2 * al256(nsub * 4)     // hq, sub_cnt, sub_pref
            + al256(c * 8) + al256(c * 4);                         // dq, dlo
 }
@@ -502,6 +514,7 @@ uint64_t carve_scratch(uint8_t* base, uint64_t q, Scratch& s) {
     take(s.stage.keys, cs * 8); take(s.stage.vals, cs * 8); take(s.stage.loc, cs * 4); take(s.stage.height, cs);
     take(s.tile_max, tiles * 4); take(s.tile_pref, tiles * 4); take(s.tile_new, tiles * 4);
     take(s.tcnt, stiles * 256 * 4); take(s.toff, stiles * 256 * 4); take(s.ndig, stiles * kSortTile + 16);
+    take(s.fixmap, (c / 32 + 1) * 4);
     take(s.hq, nsub * kSubTile * 8); take(s.sub_cnt, nsub * 4); take(s.sub_pref, nsub * 4);
     take(s.dq, c * 8); take(s.dlo, c * 4);
     s.cap = q;
@@ -530,14 +543,34 @@ cudaError_t noalloc_scratch_for(int device, uint8_t** out) {
     return cudaSuccess;
 }
 
+// Radix passes for a batch of n queries. Four passes on the most significant varying
+// key bytes leave only prefix collisions to the fix-up; when the last batch the host
+// knows of had more than n/16 queries in long colliding segments (keys whose leading
+// bytes carry little spread), the next 64 batches take all eight passes instead.
+int sort_passes(pi_index* x, uint64_t n) {
+    const uint32_t forced = (x->test_flags / PI_TEST_SORT_PREFIX(1)) & 7u;
+    if (forced >= 1 && forced <= 4) return (int)forced;
+    if (x->test_flags & PI_TEST_SORT_FULL) return 8;
+    if ((uint64_t)x->known.sort_fix_big * 16u > n) {
+        x->full_sort_left = 64;
+        x->known.sort_fix_big = 0;  // one trigger per snapshot
+    }
+    if (x->full_sort_left > 0) {
+        --x->full_sort_left;
+        return 8;
+    }
+    return 4;
+}
+
 // Enqueues one batch (Algorithm 1) with the given per-batch scratch:
 //   stream s:  pack + sort -> [wait for the previous batch's rebuild] -> descent ->
 //              ownership + apply -> merge -> layout -> meta to the mailbox ring
 //   stream rs: [wait for this batch's layout] -> index-layer rebuild
 // The rebuild thus overlaps the next batch's sort (the paper's background rebuild,
 // Section 4.4.4). Results are complete when `s` completes.
-int enqueue_batch(pi_index* x, const Scratch& sc, const uint8_t* ops, const uint64_t* keys,
-                  const uint64_t* values, uint64_t n, pi_result_t* results, uint64_t size_ub, cudaStream_t s) {
+int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const uint64_t* keys,
+                       const uint64_t* values, uint64_t n, pi_result_t* results, uint64_t size_ub,
+                       cudaStream_t s) {
     cudaError_t e;
     BatchMeta* bm = x->d_bm + (x->issued & 1u);  // the other block may still be read by the rebuild
     uint32_t ep = next_epochs(x, 16, s);
@@ -545,7 +578,8 @@ int enqueue_batch(pi_index* x, const Scratch& sc, const uint8_t* ops, const uint
     prof_mark(x, 0, s);
     cudaMemsetAsync(bm, 0, sizeof(BatchMeta), s);
     SortBuffers sb = sort_buffers(x, sc);
-    if ((e = launch_sort(ops, keys, (uint32_t)n, sb, bm, &x->d_meta->error, ep, s, x->num_sms)) != cudaSuccess)
+    if ((e = launch_sort(ops, keys, (uint32_t)n, sb, bm, &x->d_meta->error, s, x->num_sms, sort_passes(x, n))) !=
+        cudaSuccess)
         return map_cuda(e);
     prof_mark(x, 1, s);
     wait_rebuild(x, s);
@@ -615,8 +649,10 @@ int enqueue_batch(pi_index* x, const Scratch& sc, const uint8_t* ops, const uint
     cudaEventRecord(x->ev_applied, s);
     cudaStreamWaitEvent(x->rs, x->ev_applied, 0);
     prof_mark(x, 7, x->rs);
-    if ((e = launch_rebuild(ra, ep, x->rs, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    if ((e = launch_rebuild_prep(ra, ep, x->rs, x->num_sms)) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 8, x->rs);
+    if ((e = launch_rebuild_write(ra, x->rs)) != cudaSuccess) return map_cuda(e);
+    prof_mark(x, 9, x->rs);
     cudaEventRecord(x->ev_rebuilt, x->rs);
     x->rebuild_pending = true;
     if (x->prof) x->pused++;
@@ -626,6 +662,14 @@ int enqueue_batch(pi_index* x, const Scratch& sc, const uint8_t* ops, const uint
     x->issued++;
     x->pending_n += n;
     return map_cuda(cudaGetLastError());
+}
+
+int enqueue_batch(pi_index* x, const Scratch& sc, const uint8_t* ops, const uint64_t* keys,
+                  const uint64_t* values, uint64_t n, pi_result_t* results, uint64_t size_ub, cudaStream_t s) {
+    const uint64_t l0 = g_launches;
+    const int r = enqueue_batch_body(x, sc, ops, keys, values, n, results, size_ub, s);
+    x->launches += g_launches - l0;
+    return r;
 }
 
 }  // namespace
@@ -698,7 +742,7 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
             if ((e = alloc_scratch(tmp, n)) != cudaSuccess) break;
             SortBuffers sb = sort_buffers(x, tmp);
             uint32_t ep = next_epochs(x, 16, s);
-            if ((e = launch_sort(nullptr, keys, (uint32_t)n, sb, x->d_bm, &x->d_meta->error, ep, s, x->num_sms)) !=
+            if ((e = launch_sort(nullptr, keys, (uint32_t)n, sb, x->d_bm, &x->d_meta->error, s, x->num_sms, 8)) !=
                 cudaSuccess)
                 break;
             x->epoch = ep;
@@ -929,6 +973,7 @@ int pi_info(pi_index_t* x, pi_info_t* out, pi_stream_t stream) {
     out->index_capacity = x->idx_cap;
     out->batches = m.batches;
     out->rebuilds = m.rebuilds;
+    out->kernel_launches = x->launches;
     return sticky_error(m);
 }
 

@@ -177,6 +177,7 @@ __device__ bool level_bases_body(RebuildArgs a) {
     a.st.meta[cur][size] = 0;
     for (int l = 1; l < kLevelSlots; ++l) m->cnt[l] = (uint32_t)((int32_t)m->cnt[l] + bm->delta[l]);
     m->updates += bm->changes;
+    m->sort_fix_big = bm->fix_big;
     if (a.force_rebuild != 2u) m->batches += 1;
 
     bool rebuild = a.force_rebuild || merged;
@@ -641,15 +642,28 @@ cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, 
     const uint32_t tiles = a.size_ub / kNodes + 1;
     const uint32_t cap = (uint32_t)num_sms * 4u;
     k_merge<<<(int)(tiles < cap ? tiles : cap), kThreads, 0, s>>>(a, ++epoch);
+    ++g_launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s) {
     k_level_bases<<<1, 32, 0, s>>>(a);
+    ++g_launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
+cudaError_t launch_rebuild_prep(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
+    const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
+    const uint32_t cb = (tiles + 7) / 8, ccap = (uint32_t)num_sms * 4u;
+    k_rebuild_count<<<cb < ccap ? cb : ccap, 256, 0, s>>>(a);  // exits at once unless recounting
+    ++g_launches;
+    const uint32_t chunks = (tiles + kScanChunk - 1) / kScanChunk;
+    k_rebuild_scan<<<dim3(chunks, kLevelSlots - 2), 1024, 0, s>>>(a, ++epoch);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild_write(const RebuildArgs& a, cudaStream_t s) {
     static bool attr_set = false;
     const int dyn = (int)(kMetaBytes + 8 * kWarpNodes * 4);
     if (!attr_set) {
@@ -658,12 +672,14 @@ cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s
         attr_set = true;
     }
     const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
-    const uint32_t cb = (tiles + 7) / 8, ccap = (uint32_t)num_sms * 4u;
-    k_rebuild_count<<<cb < ccap ? cb : ccap, 256, 0, s>>>(a);  // exits at once unless recounting
-    const uint32_t chunks = (tiles + kScanChunk - 1) / kScanChunk;
-    k_rebuild_scan<<<dim3(chunks, kLevelSlots - 2), 1024, 0, s>>>(a, ++epoch);
     k_rebuild_write<<<tiles, kThreads, dyn, s>>>(a);
+    ++g_launches;
     return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
+    cudaError_t e = launch_rebuild_prep(a, epoch, s, num_sms);
+    return e != cudaSuccess ? e : launch_rebuild_write(a, s);
 }
 
 cudaError_t launch_create_storage(const CreateArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
@@ -671,6 +687,7 @@ cudaError_t launch_create_storage(const CreateArgs& a, uint32_t& epoch, cudaStre
     const uint32_t tiles = (a.n + kNodes - 1) / kNodes;
     const uint32_t cap = (uint32_t)num_sms * 4u;
     k_create_storage<<<(int)(tiles < cap ? tiles : cap), kThreads, 0, s>>>(a, ++epoch);
+    ++g_launches;
     return cudaGetLastError();
 }
 
@@ -681,6 +698,7 @@ cudaError_t launch_export_live(const Storage& st, const DevMeta* m, uint64_t* ke
     const uint32_t c = (uint32_t)num_sms * 4u;
     k_export_live<<<(int)(tiles < c ? tiles : c), kThreads, 0, s>>>(st, m, keys_out, vals_out, cap, count, desc,
                                                                    tile_ctr, ++epoch, err);
+    ++g_launches;
     return cudaGetLastError();
 }
 

@@ -9,10 +9,19 @@
 //   scatter: ranks the tile's elements stably within the tile and writes them to
 //            offset + rank, staged in shared memory so each digit's run is written
 //            contiguously.
-// The up-front histograms of all eight digits (one read of the keys) give the digit
-// bases and let a pass whose digit is the same for every key be skipped. The sort is
-// stable, so equal keys stay in arrival order: the order is (key, arrival index), the
-// reading of Definition 3 for duplicate keys.
+// A pass whose byte is the same in every key is skipped (byte-wise min/max in the pack
+// kernel). The sort is stable, so equal keys stay in arrival order: the order is
+// (key, arrival index), the reading of Definition 3 for duplicate keys.
+//
+// Prefix passes. When more bytes vary than the caller's pass budget (4 for batches),
+// only the most significant varying bytes get passes. Keys that agree on those bytes
+// then form contiguous segments, still in arrival order. Distinct keys share a segment
+// only when they collide on those bytes: about D^2 / 2^33 pairs for D distinct uniform
+// keys under 4 bytes, a few hundred at D = 1.2 M. Two kernels finish the order:
+//   find: marks the start of every segment that holds two different keys;
+//   fix:  orders each marked segment by (key, position). A warp does segments of up to
+//         32 queries by counting ranks. A CTA does longer ones (a hot key that collides)
+//         with a stable LSD pass per remaining byte, through buffer B.
 //
 // Payload word: op << 30 | arrival index. Invalid queries (op > 2 or the reserved key)
 // get the sort key 2^64-1 and so gather at the end of the sorted batch.
@@ -30,10 +39,12 @@ constexpr int kWarpSpan = 32 * kItems;    // 256 consecutive elements per warp
 static_assert(kTile == kSortTile, "tile size shared with the host's descriptor sizing");
 
 // K0: validate and pack. Also finds, per key byte, whether it is the same in every
-// key (byte-wise min and max), which decides the radix passes that can be skipped.
+// valid key (byte-wise min and max), which decides the radix passes that can be skipped.
 __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ ops, const uint64_t* __restrict__ keys,
                                               uint32_t n, uint64_t* __restrict__ sk, uint32_t* __restrict__ sp,
-                                              BatchMeta* bm) {
+                                              uint32_t* __restrict__ fixmap, BatchMeta* bm) {
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < (n + 31u) / 32u; w += gridDim.x * blockDim.x)
+        fixmap[w] = 0;  // segment marks of the prefix fix-up
     uint32_t invalid = 0;
     uint32_t mx[8], mn[8];  // mn holds max of (255 - byte), so zero is the identity
 #pragma unroll
@@ -49,11 +60,13 @@ __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ ops, c
         invalid += valid ? 0u : 1u;
         sk[i] = s;
         sp[i] = ((op & 3u) << 30) | i;
+        if (valid) {
 #pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            const uint32_t b = (uint32_t)(s >> (8 * d)) & 255u;
-            mx[d] = max(mx[d], b);
-            mn[d] = max(mn[d], 255u - b);
+            for (int d = 0; d < 8; ++d) {
+                const uint32_t b = (uint32_t)(s >> (8 * d)) & 255u;
+                mx[d] = max(mx[d], b);
+                mn[d] = max(mn[d], 255u - b);
+            }
         }
     }
     __shared__ uint32_t s_red[17];
@@ -80,25 +93,64 @@ __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ ops, c
     else if (threadIdx.x == 16 && s_red[16]) atomicAdd(&bm->invalid, s_red[16]);
 }
 
-// Pass plan: the passes whose byte varies (at least one), ping-ponging so the last
-// pass writes buffer A.
-__global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, uint32_t* tile_max) {
+// Pass plan. The digit bytes D are the bytes that vary among the valid keys. Invalid
+// queries carry the sort key 2^64-1 and must follow every valid key: when there are
+// some, D also holds the highest byte p whose maximum over the valid keys is below 0xFF
+// (every invalid key is larger there; with no such byte D is every byte). Passes
+// ping-pong so that the last one writes buffer A.
+// With more than max_passes bytes in D, the passes take the most significant
+// max_passes of them (the prefix). The fix-up then orders each segment of equal prefix
+// bytes by the full key; its long-segment path sorts by every other byte that can
+// differ inside a segment (rdig).
+__global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, uint32_t* tile_max,
+                                                   uint32_t max_passes) {
     const int b = threadIdx.x;
     if (tile_max)
         for (uint32_t t = b; t < (n + kApplyTile - 1) / kApplyTile; t += 256) tile_max[t] = 0;
     if (b == 0) {
         SortPlan& P = bm->plan;
+        const bool any_valid = bm->invalid < n;
         uint32_t r = 0;
         uint32_t dig[8];
-        for (int d = 0; d < 8; ++d)
-            if (bm->bmax[d] != 255u - bm->bnmin[d]) dig[r++] = d;  // max byte != min byte
-        if (r == 0) dig[r++] = 0;  // all keys equal: one pass (identity order)
-        P.npass = r;
-        for (uint32_t j = 0; j < r; ++j) {
-            P.digit[j] = dig[j];
-            P.src[j] = (j == 0) ? 0u : P.dst[j - 1];
-            P.dst[j] = ((r - 1 - j) % 2 == 0) ? 1u : 2u;  // the last pass writes buffer A
+        bool varies[8], differs[8];  // among valid keys; between valid and invalid keys
+        int p = -1;                  // highest byte where every valid key is below 0xFF
+        for (int d = 0; d < 8; ++d) {
+            const uint32_t hi = bm->bmax[d], lo = 255u - bm->bnmin[d];
+            varies[d] = any_valid && hi != lo;
+            differs[d] = bm->invalid && any_valid && lo < 255u;
+            if (varies[d]) dig[r++] = (uint32_t)d;
+            if (!any_valid || hi < 255u) p = d;
         }
+        if (bm->invalid) {
+            bool have = false;
+            for (uint32_t j = 0; j < r; ++j) have |= dig[j] == (uint32_t)p;
+            if (p < 0) {  // no single byte separates the invalid key: sort every byte
+                r = 0;
+                for (int d = 0; d < 8; ++d) dig[r++] = (uint32_t)d;
+            } else if (!have) {  // insert p, keeping dig ascending
+                uint32_t j = r++;
+                while (j > 0 && dig[j - 1] > (uint32_t)p) {
+                    dig[j] = dig[j - 1];
+                    --j;
+                }
+                dig[j] = (uint32_t)p;
+            }
+        }
+        if (r == 0) dig[r++] = 0;  // all keys equal: one pass (identity order)
+        const uint32_t skip = r > max_passes ? r - max_passes : 0u;  // D bytes below the prefix
+        P.npass = r - skip;
+        P.pmask = 0;
+        for (uint32_t j = 0; j < P.npass; ++j) {
+            P.digit[j] = dig[skip + j];
+            P.src[j] = (j == 0) ? 0u : P.dst[j - 1];
+            P.dst[j] = ((P.npass - 1 - j) % 2 == 0) ? 1u : 2u;  // the last pass writes buffer A
+            P.pmask |= 0xFFull << (8 * dig[skip + j]);
+        }
+        P.fix = skip ? 1u : 0u;
+        P.nr = 0;
+        if (skip)
+            for (int d = 0; d < 8; ++d)
+                if (!((P.pmask >> (8 * d)) & 1u) && (varies[d] || differs[d])) P.rdig[P.nr++] = (uint32_t)d;
     }
 }
 
@@ -181,6 +233,38 @@ __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t j, uint32_t n, Sort
     }
 }
 
+// Rank within the warp of kItems x 32 elements visited in index order (k, then lane);
+// dig = 256 marks an empty slot. The lanes holding the same digit are found with nine
+// ballots (validity + 8 bits); the lowest of them adds the group's size to the warp's
+// counter for that digit (whist) with one shared-memory atomic, whose old value is the
+// group's base. The __syncwarp orders the atomics of consecutive items, so equal digits
+// keep index order (stability); the bases are gathered only after the loop. On return
+// rank[k] counts the warp's earlier elements with the same digit, and whist[d] the
+// warp's elements with digit d (added to its previous contents).
+__device__ __forceinline__ void warp_digit_ranks(const uint32_t (&dig)[kItems], uint32_t (&rank)[kItems],
+                                                 uint32_t* whist) {
+    const uint32_t lt = lanemask_lt();
+    uint32_t lower[kItems], old[kItems], lead[kItems];
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint32_t d = dig[k];
+        uint32_t peers = __ballot_sync(0xffffffffu, d < 256u);
+        if (d >= 256u) peers = ~peers;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? m : ~m;
+        }
+        lead[k] = (uint32_t)(__ffs(peers) - 1);
+        lower[k] = __popc(peers & lt);
+        old[k] = 0;
+        if (lower[k] == 0 && d < 256u) old[k] = atomicAdd(&whist[d], (uint32_t)__popc(peers));
+        __syncwarp();
+    }
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) rank[k] = __shfl_sync(0xffffffffu, old[k], (int)lead[k]) + lower[k];
+}
+
 __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t n, SortBuffers sb,
                                                            BatchMeta* bm, uint32_t* err) {
     const SortPlan& P = bm->plan;
@@ -217,32 +301,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
         pay[k] = v ? src_p[tbase + li] : 0u;
         dig[k] = v ? (uint32_t)((key[k] >> shift) & 255u) : 256u;
     }
-    // Rank within the warp: elements are visited in index order (k, then lane). The
-    // lanes holding the same digit are found with nine ballots (validity + 8 bits);
-    // the lowest of them adds the group's size to the warp's counter for that digit
-    // with one shared-memory atomic, whose old value is the group's base. The
-    // __syncwarp orders the atomics of consecutive items, so equal digits keep index
-    // order (stability); the bases are gathered only after the loop.
-    const uint32_t lt = lanemask_lt();
-    uint32_t lower[kItems], old[kItems], lead[kItems];
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const uint32_t d = dig[k];
-        uint32_t peers = __ballot_sync(0xffffffffu, d < 256u);
-        if (d >= 256u) peers = ~peers;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? m : ~m;
-        }
-        lead[k] = (uint32_t)(__ffs(peers) - 1);
-        lower[k] = __popc(peers & lt);
-        old[k] = 0;
-        if (lower[k] == 0 && d < 256u) old[k] = atomicAdd(&s_whist[warp][d], (uint32_t)__popc(peers));
-        __syncwarp();
-    }
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) rank[k] = __shfl_sync(0xffffffffu, old[k], (int)lead[k]) + lower[k];
+    warp_digit_ranks(dig, rank, s_whist[warp]);
     __syncthreads();
     // Thread tid owns digit tid: tile total and per-warp exclusive prefix.
     uint32_t total = 0;
@@ -282,14 +341,214 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Prefix fix-up. After the prefix passes buffer A is sorted by key & pmask ("the
+// prefix"), and positions with equal prefix hold their queries in arrival order.
+
+// Marks (in fixmap) the first position of every segment of equal prefix that holds two
+// different keys. A position i whose key differs from key i-1 but whose prefix does not
+// lies inside such a segment; the segment's start is found by a galloping search back
+// from i followed by a binary search, both over the prefix order.
+__global__ void __launch_bounds__(256) k_sort_find(uint32_t n, SortBuffers sb, const BatchMeta* bm) {
+    const SortPlan& P = bm->plan;
+    if (!P.fix) return;
+    const uint64_t pm = P.pmask;
+    const uint64_t* __restrict__ ak = sb.a_k;
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t base = blockIdx.x * 256u; base < n; base += gridDim.x * 256u) {
+        const uint32_t i = base + threadIdx.x;
+        const uint64_t k1 = i < n ? ak[i] : 0ull;
+        uint64_t k0 = __shfl_up_sync(0xffffffffu, k1, 1);
+        if (lane == 0 && i > 0 && i < n) k0 = ak[i - 1];
+        if (i == 0 || i >= n || k0 == k1 || ((k0 ^ k1) & pm) != 0) continue;
+        const uint64_t mk = k1 & pm;
+        uint32_t in = i - 1;  // ak[in] is in the segment
+        uint64_t d = 1;
+        while (d <= in && (ak[in - d] & pm) == mk) {
+            in -= (uint32_t)d;
+            d <<= 1;
+        }
+        uint32_t lo = d <= in ? in - (uint32_t)d + 1 : 0u, hi = in;  // the start lies in [lo, hi]
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo) / 2;
+            if ((ak[mid] & pm) == mk) hi = mid;
+            else lo = mid + 1;
+        }
+        atomicOr(&sb.fixmap[lo >> 5], 1u << (lo & 31u));
+    }
+}
+
+constexpr int kFixSlice = kThreads * 32;  // positions per fix-up CTA: one fixmap word per thread
+
+// Stable LSD sort of the segment [s, e) of buffer A by the bytes P.rdig (ascending),
+// by the whole CTA, through the same range of buffer B. The segment is in arrival
+// order, so the result is in (key, arrival) order.
+__device__ void cta_segment_lsd(uint32_t s, uint32_t e, const SortPlan& P, const SortBuffers& sb,
+                                uint32_t (*s_whist)[256], uint32_t* s_base, uint32_t* s_tmp) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint64_t* src_k = sb.a_k;
+    uint32_t* src_p = sb.a_p;
+    uint64_t* dst_k = sb.b_k;
+    uint32_t* dst_p = sb.b_p;
+    for (uint32_t r = 0; r < P.nr; ++r) {
+        const uint32_t shift = 8u * P.rdig[r];
+        for (int w = 0; w < kWarps; ++w) s_whist[w][tid] = 0;
+        s_base[tid] = 0;
+        __syncthreads();
+        for (uint32_t i = s + tid; i < e; i += kThreads) atomicAdd(&s_base[(uint32_t)(src_k[i] >> shift) & 255u], 1u);
+        __syncthreads();
+        const uint32_t cnt = s_base[tid];
+        __syncthreads();
+        s_base[tid] = s + block_excl_sum<kThreads>(cnt, s_tmp, nullptr);
+        __syncthreads();
+        for (uint32_t c = s; c < e; c += kTile) {
+            uint64_t key[kItems];
+            uint32_t pay[kItems], dig[kItems], rank[kItems];
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                const uint32_t i = c + warp * kWarpSpan + k * 32 + lane;
+                const bool v = i < e;
+                key[k] = v ? src_k[i] : 0ull;
+                pay[k] = v ? src_p[i] : 0u;
+                dig[k] = v ? (uint32_t)((key[k] >> shift) & 255u) : 256u;
+            }
+            warp_digit_ranks(dig, rank, s_whist[warp]);
+            __syncthreads();
+            uint32_t total = 0;  // thread tid owns digit tid: per-warp exclusive prefix
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t cc = s_whist[w][tid];
+                s_whist[w][tid] = total;
+                total += cc;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                const uint32_t d = dig[k];
+                if (d < 256u) {
+                    const uint32_t pos = s_base[d] + s_whist[warp][d] + rank[k];
+                    if (pos >= s && pos < e) {
+                        dst_k[pos] = key[k];
+                        dst_p[pos] = pay[k];
+                    }
+                }
+            }
+            __syncthreads();
+            s_base[tid] += total;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) s_whist[w][tid] = 0;
+            __syncthreads();
+        }
+        uint64_t* tk = src_k; src_k = dst_k; dst_k = tk;
+        uint32_t* tp = src_p; src_p = dst_p; dst_p = tp;
+    }
+    if (src_k != sb.a_k) {  // an odd number of passes left the result in B
+        for (uint32_t i = s + tid; i < e; i += kThreads) {
+            sb.a_k[i] = src_k[i];
+            sb.a_p[i] = src_p[i];
+        }
+    }
+    __syncthreads();
+}
+
+// Orders every marked segment. Each CTA reads kThreads fixmap words (kFixSlice
+// positions) and takes the segments that start there. A warp orders a segment of at
+// most 32 queries: rank = queries with a smaller key, or the same key and an earlier
+// position. Longer segments are queued for the whole CTA.
+__global__ void __launch_bounds__(kThreads) k_sort_fix(uint32_t n, SortBuffers sb, BatchMeta* bm) {
+    const SortPlan& P = bm->plan;
+    if (!P.fix) return;
+    __shared__ uint32_t s_list[kFixSlice / 2];  // segment starts (a segment holds >= 2 queries)
+    __shared__ uint32_t s_big[kFixSlice / 32 + 1];  // starts of segments of more than 32
+    __shared__ uint32_t s_nbig, s_end;
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_whist[kWarps][256];
+    __shared__ uint32_t s_base[256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nwords = (n + 31u) / 32u;
+    const uint32_t wi = blockIdx.x * kThreads + tid;
+    uint32_t w = wi < nwords ? sb.fixmap[wi] : 0u;
+    uint32_t total;
+    uint32_t off = block_excl_sum<kThreads>((uint32_t)__popc(w), s_tmp, &total);
+    while (w) {
+        const uint32_t b = (uint32_t)(__ffs(w) - 1);
+        w &= w - 1;
+        if (off < kFixSlice / 2) s_list[off] = wi * 32u + b;  // starts are >= 2 apart: always true
+        ++off;
+    }
+    if (tid == 0) s_nbig = 0;
+    __syncthreads();
+    if (total == 0) return;
+    if (total > kFixSlice / 2) total = kFixSlice / 2;
+    const uint64_t pm = P.pmask;
+    const uint64_t* ak = sb.a_k;
+    for (uint32_t x = warp; x < total; x += kWarps) {
+        const uint32_t s = s_list[x];
+        const uint64_t mk = ak[s] & pm;
+        const uint32_t i = s + lane;
+        // The segment's queries are the lanes of a prefix of the warp (prefix order).
+        const uint64_t key = i < n ? ak[i] : 0ull;
+        const bool in = i < n && (key & pm) == mk;
+        const uint32_t m = (uint32_t)__popc(__ballot_sync(0xffffffffu, in));
+        const bool longer = m == 32u && s + 32u < n && (ak[s + 32u] & pm) == mk;
+        if (longer) {
+            if (lane == 0) {
+                const uint32_t slot = atomicAdd(&s_nbig, 1u);
+                if (slot < kFixSlice / 32 + 1) s_big[slot] = s;  // starts are > 32 apart: always true
+            }
+            continue;
+        }
+        const uint32_t pay = in ? sb.a_p[i] : 0u;
+        uint32_t rank = 0;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const uint64_t kj = __shfl_sync(0xffffffffu, key, j);
+            rank += ((uint32_t)j < m && (kj < key || (kj == key && j < lane))) ? 1u : 0u;
+        }
+        __syncwarp();
+        if (in) {
+            sb.a_k[s + rank] = key;
+            sb.a_p[s + rank] = pay;
+        }
+    }
+    __syncthreads();
+    const uint32_t nbig = min(s_nbig, (uint32_t)(kFixSlice / 32 + 1));
+    for (uint32_t x = 0; x < nbig; ++x) {
+        const uint32_t s = s_big[x];
+        if (tid == 0) {
+            // end of the segment: gallop forward from s + 32 (in it), then bisect
+            const uint64_t mk = ak[s] & pm;
+            uint32_t in = s + 32u;
+            uint64_t d = 1;
+            while (d < n - in && (ak[in + d] & pm) == mk) {
+                in += (uint32_t)d;
+                d <<= 1;
+            }
+            uint32_t lo = in + 1, hi = (d < n - in) ? in + (uint32_t)d : n;  // the end lies in [lo, hi]
+            while (lo < hi) {
+                const uint32_t mid = lo + (hi - lo) / 2;
+                if ((ak[mid] & pm) == mk) lo = mid + 1;
+                else hi = mid;
+            }
+            s_end = lo;
+            atomicAdd(&bm->fix_big, lo - s);
+        }
+        __syncthreads();
+        cta_segment_lsd(s, s_end, P, sb, s_whist, s_base, s_tmp);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, const SortBuffers& sb,
-                        BatchMeta* bm, uint32_t* err, uint32_t& epoch, cudaStream_t s, int num_sms) {
+                        BatchMeta* bm, uint32_t* err, cudaStream_t s, int num_sms, int max_passes) {
     if (n == 0) return cudaSuccess;
+    if (max_passes < 1 || max_passes > 8) return cudaErrorInvalidValue;
     int grid = min((int)((n + 255) / 256), num_sms * 8);
-    k_pack<<<grid, 256, 0, s>>>(ops, keys, n, sb.in_k, sb.in_p, bm);
-    k_sort_plan<<<1, 256, 0, s>>>(n, bm, sb.tile_max);
+    k_pack<<<grid, 256, 0, s>>>(ops, keys, n, sb.in_k, sb.in_p, sb.fixmap, bm);
+    ++g_launches;
+    k_sort_plan<<<1, 256, 0, s>>>(n, bm, sb.tile_max, (uint32_t)max_passes);
+    ++g_launches;
     static bool attr_set = false;
     const int dyn = kTile * (int)(sizeof(uint64_t) + sizeof(uint32_t));
     if (!attr_set) {
@@ -299,12 +558,23 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
     }
     const uint32_t tiles = (n + kTile - 1) / kTile;
     k_sort_count<<<tiles, kThreads, 0, s>>>(0, n, sb, bm);
-    for (uint32_t j = 0; j < 8; ++j) {
+    ++g_launches;
+    for (uint32_t j = 0; j < (uint32_t)max_passes; ++j) {
         k_sort_scan<<<256, 1024, 0, s>>>(j, n, sb, bm);
+        ++g_launches;
         k_sort_pass<<<tiles, kThreads, dyn, s>>>(j, n, sb, bm, err);
-        if (j + 1 < 8) k_sort_count<<<tiles, kThreads, 0, s>>>(j + 1, n, sb, bm);
+        ++g_launches;
+        if (j + 1 < (uint32_t)max_passes) {
+            k_sort_count<<<tiles, kThreads, 0, s>>>(j + 1, n, sb, bm);
+            ++g_launches;
+        }
     }
-    (void)epoch;
+    if (max_passes < 8) {  // with eight passes every byte is sorted: nothing to fix
+        k_sort_find<<<grid, 256, 0, s>>>(n, sb, bm);
+        ++g_launches;
+        k_sort_fix<<<(n + kFixSlice - 1) / kFixSlice, kThreads, 0, s>>>(n, sb, bm);
+        ++g_launches;
+    }
     return cudaGetLastError();
 }
 
