@@ -229,6 +229,72 @@ int pi_export_level(pi_index_t* idx, int level, uint64_t* keys_out, uint32_t* do
 int pi_profile(pi_index_t* idx, int enable);
 int pi_profile_read(pi_index_t* idx, double* stage_ms_host, uint64_t* batches_host, pi_stream_t stream);
 
+/*
+ * ---------------------------------------------------------------------------------
+ * Batching form: one batch for each of many independent indices in one persistent
+ * launch. Algorithm 1 runs for every index of the set at once: each CTA takes a batch
+ * from a device-side queue (largest first) and runs its whole pipeline. The result of
+ * every batch is exactly what pi_execute_batch gives for it (Section 4.2: arrival-order
+ * semantics per index); the indices stay usable by every single-index entry point.
+ * The paper runs one index per NUMA node (Section 4.4.1); many small indices in one
+ * launch are this library's extension.
+ */
+typedef struct pi_multi pi_multi_t;
+
+/* Kernel configuration of one size class: indices whose storage layer has at most
+ * 2^max_log2_size nodes take CTAs of `warps` warps (8, 16 or 32) and radix digits of
+ * `radix_bits` bits (4 or 8). */
+typedef struct {
+    uint32_t max_log2_size;
+    uint32_t warps;
+    uint32_t radix_bits;
+    uint32_t reserved;
+} pi_multi_class_t;
+
+#define PI_MULTI_MAX_CLASSES 4
+#define PI_MULTI_MAX_BATCH (1u << 20) /* queries per batch in the batching form */
+
+typedef struct {
+    uint32_t struct_size;   /* sizeof(pi_multi_config_t) */
+    uint32_t num_classes;   /* 1..PI_MULTI_MAX_CLASSES, ascending max_log2_size; the
+                               last class takes every larger index */
+    pi_multi_class_t cls[PI_MULTI_MAX_CLASSES];
+} pi_multi_config_t;
+
+/*
+ * pi_multi_create -- group `count` indices (made by pi_create / pi_create_ex on the
+ * current device) for batched execution. The set refers to the indices, it does not own
+ * them: destroy the set before its indices. cfg may be NULL (built-in classes). Returns
+ * NULL on error (pi_last_error: PI_ERR_INVALID_ARG for a NULL or repeated index or a bad
+ * class, PI_ERR_OOM, PI_ERR_CUDA).
+ */
+pi_multi_t* pi_multi_create(pi_index_t* const* indices, uint32_t count, const pi_multi_config_t* cfg);
+
+/* One batch for one index of the set. Arrays as for pi_execute_batch (device memory,
+ * n <= PI_MULTI_MAX_BATCH, results[n] in arrival order). */
+typedef struct {
+    uint32_t index;          /* position in the set */
+    uint32_t reserved;
+    const uint8_t* ops;
+    const uint64_t* keys;
+    const uint64_t* values;
+    uint64_t n;
+    pi_result_t* results;
+} pi_multi_batch_t;
+
+/*
+ * pi_multi_execute -- enqueue `nb` batches (host array of descriptors, at most one per
+ * index) on `stream` as one CUDA-graph launch. Returns PI_ERR_INVALID_ARG for a bad
+ * descriptor (nothing is enqueued), PI_ERR_OOM / PI_ERR_CUDA when growing an index's
+ * capacity fails, or a sticky device error of one of the indices. Results are complete
+ * when `stream` reaches the end of the call. The descriptor array may be reused as soon
+ * as the call returns.
+ */
+int pi_multi_execute(pi_multi_t* set, const pi_multi_batch_t* batches_host, uint32_t nb, pi_stream_t stream);
+
+/* Releases the set's own device and host memory (not the indices). NULL-safe. */
+void pi_multi_destroy(pi_multi_t* set);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,10 @@ PI_MAX_KEYS = (1 << 30) - 2
 
 EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
             "pi_last_error", "pi_status", "pi_info", "pi_export", "pi_export_level", "pi_profile",
-            "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush"]
+            "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush",
+            "pi_multi_create", "pi_multi_execute", "pi_multi_destroy"]
+PI_MULTI_MAX_CLASSES = 4
+PI_MULTI_MAX_BATCH = 1 << 20
 PI_NOALLOC_MAX_BATCH = 1 << 16
 PI_TEST_WALK_LEVELS = 1
 PI_TEST_SORT_FULL = 2
@@ -44,6 +47,22 @@ class PiConfig(ctypes.Structure):
                 ("rebuild_threshold_pct", ctypes.c_uint32), ("smem_top_entries", ctypes.c_uint32),
                 ("storage_capacity", ctypes.c_uint64), ("index_capacity", ctypes.c_uint64),
                 ("test_flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class PiMultiClass(ctypes.Structure):
+    _fields_ = [("max_log2_size", ctypes.c_uint32), ("warps", ctypes.c_uint32),
+                ("radix_bits", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class PiMultiConfig(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("num_classes", ctypes.c_uint32),
+                ("cls", PiMultiClass * 4)]
+
+
+class PiMultiBatch(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("ops", ctypes.c_void_p),
+                ("keys", ctypes.c_void_p), ("values", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("results", ctypes.c_void_p)]
 
 
 class PiInfo(ctypes.Structure):
@@ -100,6 +119,12 @@ def load_library(path: str = LIB_PATH):
     lib.pi_profile.argtypes = [vp, i32]
     lib.pi_profile_read.restype = i32
     lib.pi_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), vp]
+    lib.pi_multi_create.restype = vp
+    lib.pi_multi_create.argtypes = [ctypes.POINTER(vp), ctypes.c_uint32, ctypes.POINTER(PiMultiConfig)]
+    lib.pi_multi_execute.restype = i32
+    lib.pi_multi_execute.argtypes = [vp, ctypes.POINTER(PiMultiBatch), ctypes.c_uint32, vp]
+    lib.pi_multi_destroy.restype = None
+    lib.pi_multi_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -233,6 +258,56 @@ class Index:
     def close(self):
         if getattr(self, "_h", None):
             self.lib.pi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MultiSet:
+    """A set of indices run one batch each per call (pi_multi_create / pi_multi_execute).
+    classes: list of (max_log2_size, warps, radix_bits), or None for the built-in table."""
+
+    def __init__(self, indices, classes=None):
+        lib = load_library()
+        self.indices = list(indices)
+        arr = (ctypes.c_void_p * len(self.indices))(*[ix._h.value for ix in self.indices])
+        cfgp = None
+        if classes is not None:
+            cfg = PiMultiConfig()
+            cfg.struct_size = ctypes.sizeof(PiMultiConfig)
+            cfg.num_classes = len(classes)
+            for i, (lg, w, b) in enumerate(classes):
+                cfg.cls[i] = PiMultiClass(lg, w, b, 0)
+            cfgp = ctypes.byref(cfg)
+        h = lib.pi_multi_create(arr, len(self.indices), cfgp)
+        if not h:
+            raise PiError(lib.pi_last_error(), "pi_multi_create")
+        self._h = ctypes.c_void_p(h)
+        self.lib = lib
+
+    def execute(self, batches, stream=None):
+        """batches: list of (index position, ops u8, keys i64, vals i64, results i64[n, 2]) with
+        CUDA tensors; results are written in place (value bits, status)."""
+        import torch
+        arr = (PiMultiBatch * len(batches))()
+        for i, (ix, ops, keys, vals, res) in enumerate(batches):
+            n = ops.numel()
+            _check_dev(ops, torch.uint8, "ops")
+            _check_dev(keys, torch.int64, "keys")
+            _check_dev(vals, torch.int64, "vals")
+            _check_dev(res, torch.int64, "results")
+            if keys.numel() != n or vals.numel() != n or res.numel() != 2 * n:
+                raise ValueError("batch arrays differ in length")
+            arr[i] = PiMultiBatch(ix, 0, ops.data_ptr(), keys.data_ptr(), vals.data_ptr(), n, res.data_ptr())
+        _chk(self.lib.pi_multi_execute(self._h, arr, len(batches), _stream_handle(stream)), "pi_multi_execute")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.pi_multi_destroy(self._h)
             self._h = None
 
     def __del__(self):

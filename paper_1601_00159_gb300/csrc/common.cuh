@@ -61,6 +61,55 @@ struct SortPlan {
     uint32_t rdig[8];
 };
 
+// Digit plan of a radix sort of n keys (see the sort's description): bmax / bnmin are
+// the per-byte maxima and (255 - minima) over the valid keys, invalid the number of
+// invalid keys (sort key 2^64-1), max_passes the pass budget (1..8).
+__device__ __forceinline__ void plan_digits(const uint32_t* bmax, const uint32_t* bnmin, uint32_t invalid,
+                                            uint32_t n, uint32_t max_passes, SortPlan& P) {
+    const bool any_valid = invalid < n;
+    uint32_t r = 0;
+    uint32_t dig[8];
+    bool varies[8], differs[8];  // among valid keys; between valid and invalid keys
+    int p = -1;                  // highest byte where every valid key is below 0xFF
+    for (int d = 0; d < 8; ++d) {
+        const uint32_t hi = bmax[d], lo = 255u - bnmin[d];
+        varies[d] = any_valid && hi != lo;
+        differs[d] = invalid && any_valid && lo < 255u;
+        if (varies[d]) dig[r++] = (uint32_t)d;
+        if (!any_valid || hi < 255u) p = d;
+    }
+    if (invalid) {
+        bool have = false;
+        for (uint32_t j = 0; j < r; ++j) have |= dig[j] == (uint32_t)p;
+        if (p < 0) {  // no single byte separates the invalid key: sort every byte
+            r = 0;
+            for (int d = 0; d < 8; ++d) dig[r++] = (uint32_t)d;
+        } else if (!have) {  // insert p, keeping dig ascending
+            uint32_t j = r++;
+            while (j > 0 && dig[j - 1] > (uint32_t)p) {
+                dig[j] = dig[j - 1];
+                --j;
+            }
+            dig[j] = (uint32_t)p;
+        }
+    }
+    if (r == 0) dig[r++] = 0;  // all keys equal: one pass (identity order)
+    const uint32_t skip = r > max_passes ? r - max_passes : 0u;  // D bytes below the prefix
+    P.npass = r - skip;
+    P.pmask = 0;
+    for (uint32_t j = 0; j < P.npass; ++j) {
+        P.digit[j] = dig[skip + j];
+        P.src[j] = (j == 0) ? 0u : P.dst[j - 1];
+        P.dst[j] = ((P.npass - 1 - j) % 2 == 0) ? 1u : 2u;  // the last pass writes buffer A
+        P.pmask |= 0xFFull << (8 * dig[skip + j]);
+    }
+    P.fix = skip ? 1u : 0u;
+    P.nr = 0;
+    if (skip)
+        for (int d = 0; d < 8; ++d)
+            if (!((P.pmask >> (8 * d)) & 1u) && (varies[d] || differs[d])) P.rdig[P.nr++] = (uint32_t)d;
+}
+
 // Per-batch scratch counters, cleared by one memset at the start of every batch.
 struct BatchMeta {
     uint32_t tile_ctr[24];       // dynamic tile counters, one per look-back kernel
@@ -378,6 +427,39 @@ __device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t* warp_tm
     return r;
 }
 
+// Stable rank within a warp of kI x 32 elements visited in index order (k, then lane),
+// by a kBits-bit digit; dig = 1 << kBits marks an empty slot. The lanes holding the
+// same digit are found with kBits + 1 ballots (validity + digit bits); the lowest of
+// them adds the group's size to the warp's counter for that digit (whist) with one
+// shared-memory atomic, whose old value is the group's base. The __syncwarp orders the
+// atomics of consecutive items, so equal digits keep index order; the bases are
+// gathered only after the loop. On return rank[k] counts the warp's earlier elements
+// with the same digit, and whist[d] has grown by the warp's elements with digit d.
+template <int kI, int kBits>
+__device__ __forceinline__ void warp_digit_ranks(const uint32_t (&dig)[kI], uint32_t (&rank)[kI], uint32_t* whist) {
+    constexpr uint32_t kEmpty = 1u << kBits;
+    const uint32_t lt = lanemask_lt();
+    uint32_t lower[kI], old[kI], lead[kI];
+#pragma unroll
+    for (int k = 0; k < kI; ++k) {
+        const uint32_t d = dig[k];
+        uint32_t peers = __ballot_sync(0xffffffffu, d < kEmpty);
+        if (d >= kEmpty) peers = ~peers;
+#pragma unroll
+        for (int b = 0; b < kBits; ++b) {
+            const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? m : ~m;
+        }
+        lead[k] = (uint32_t)(__ffs(peers) - 1);
+        lower[k] = __popc(peers & lt);
+        old[k] = 0;
+        if (lower[k] == 0 && d < kEmpty) old[k] = atomicAdd(&whist[d], (uint32_t)__popc(peers));
+        __syncwarp();
+    }
+#pragma unroll
+    for (int k = 0; k < kI; ++k) rank[k] = __shfl_sync(0xffffffffu, old[k], (int)lead[k]) + lower[k];
+}
+
 // Block-wide inclusive max over one value per thread; returns the exclusive max.
 template <int kThreads>
 __device__ __forceinline__ uint32_t block_excl_max(uint32_t v, uint32_t* warp_tmp, uint32_t* total) {
@@ -509,6 +591,45 @@ struct RebuildArgs {
 };
 cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
 cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s);
+// ---------------------------------------------------------------------------------
+// Batching form: a set of indices, one batch each, in one persistent launch.
+struct MIndex {           // one index of the set: its own arrays and device meta
+    DevMeta* m;
+    Storage st;
+    uint64_t* lkeys;
+    uint32_t* ldown;
+    uint32_t st_cap;      // storage nodes per buffer
+    uint32_t idx_cap;     // index-layer entries
+    uint32_t smem_top;    // the plain descent's pinned-entry cap (kept in DevMeta::Ls)
+    uint32_t pad_;
+    HashParams hp;
+};
+
+struct MItem {            // one queued batch
+    const uint8_t* ops;
+    const uint64_t* keys;
+    const uint64_t* vals;
+    pi_result_t* results;
+    uint32_t n;
+    uint32_t index;
+};
+
+struct MultiArgs {
+    const MIndex* idx;
+    const MItem* items;       // the queue, largest work first
+    const uint32_t* nitems;   // queue length (device)
+    uint32_t* head;           // next queue slot (device, 0 at launch)
+    uint8_t* scratch;         // per-CTA scratch, stride bytes each
+    uint64_t stride;
+    uint32_t qcap;            // queries per batch the scratch holds
+    uint32_t pad_;
+    DevMeta* mirror;          // copy of every processed index's meta, by index (may be null)
+};
+
+uint64_t multi_scratch_bytes(uint32_t qcap);
+cudaError_t launch_multi(const MultiArgs& a, int warps, int radix_bits, uint32_t grid, cudaStream_t s);
+cudaError_t multi_occupancy(int warps, int radix_bits, int* blocks);
+
 // Kernels launched by this host thread (every launcher adds the launches it issues); the
 // batch entry points fold the difference into the index's own count.
 extern thread_local uint64_t g_launches;

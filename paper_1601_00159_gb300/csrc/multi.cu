@@ -1,0 +1,848 @@
+// Batching form: many independent indices, each with its own query batch, in one
+// persistent launch (Algorithm 1 applied to every index of a set at once).
+//
+// Small indices and small batches leave the level-synchronous whole-GPU pipeline of a
+// single index (tens of launches, each spread over all SMs) launch-bound. Here a CTA
+// runs the whole pipeline of one index's batch by itself, and the CTAs of a persistent
+// launch take batches from a device-side work queue, largest first:
+//   sort        stable LSD radix sort of (key, arrival) over the varying key bytes,
+//               chunks of kT x kMI queries ranked by warp ballots (kBits-bit digits);
+//   distinct    the run heads of the sorted batch, compacted;
+//   descent     each thread walks kMK distinct keys down the index together (one
+//               independent gather per key per step); the top levels are staged in
+//               shared memory and resolved by a binary search of the lowest staged one;
+//   locate      the storage node with the largest key <= q;
+//   apply       one chunked pass with running carries: a max-scan of write markers
+//               gives every query the state of its key just before it (arrival order),
+//               the last query of each key run owns the node and writes the final state;
+//               keys that are new become a sorted list of new nodes;
+//   merge       live old nodes and new nodes into the other storage buffer, by the
+//               insertion points the descent found;
+//   rebuild     the lowest built level from the storage layer, each higher level from
+//               the one below it (heights recomputed from the seeded key hash).
+// All state lives in the indices' own device arrays and DevMeta blocks, so the single-
+// index entry points (export, info, the plain batch path) see the same index after it.
+// The queue is filled before the launch, so taking an item is one atomicAdd and no CTA
+// ever waits on another.
+
+#include "common.cuh"
+
+namespace pi {
+namespace {
+
+constexpr uint32_t kMSeqMask = (1u << 30) - 1u;
+constexpr int kMI = 8;             // queries or nodes per thread in a chunked pass
+constexpr int kMK = 8;             // distinct keys per thread walked down together
+constexpr uint32_t kMTop = 2048;   // index entries staged in shared memory
+
+__device__ __forceinline__ void mstore_result(pi_result_t* res, uint32_t seq, uint64_t v, uint32_t st) {
+    uint4 w;
+    w.x = (uint32_t)v;
+    w.y = (uint32_t)(v >> 32);
+    w.z = st;
+    w.w = 0u;
+    *reinterpret_cast<uint4*>(res + seq) = w;
+}
+
+struct MShared {
+    uint32_t tmp[33];
+    uint32_t bmax[8], bnmin[8];
+    uint32_t invalid;
+    uint32_t item;
+    uint32_t D, newc, dirty, changes, j1;
+    int32_t tomb_delta;
+    int32_t delta[kLevelSlots];
+    SortPlan plan;
+    DevMeta m;
+};
+
+struct MScratchPtrs {
+    uint64_t *ka, *kb;
+    uint32_t *pa, *pb;
+    uint64_t* dq;   // distinct keys
+    uint32_t* dr;   // storage position + 1 of the largest key <= q
+    uint8_t* df;    // bit 0: exists, bit 1: live
+    uint64_t* dv;   // value when live
+    uint64_t *nk, *nv;
+    uint8_t* nh;
+    uint32_t* ni;   // insertion point (old node the new node precedes)
+};
+
+__device__ __forceinline__ uint64_t al256(uint64_t b) { return (b + 255u) & ~255ull; }
+
+__device__ MScratchPtrs carve(uint8_t* base, uint32_t q) {
+    MScratchPtrs p;
+    uint64_t off = 0;
+    const uint64_t c = (uint64_t)q + kPad;
+    auto take = [&](uint64_t bytes) {
+        uint8_t* r = base + off;
+        off += al256(bytes);
+        return r;
+    };
+    p.ka = reinterpret_cast<uint64_t*>(take(c * 8));
+    p.kb = reinterpret_cast<uint64_t*>(take(c * 8));
+    p.pa = reinterpret_cast<uint32_t*>(take(c * 4));
+    p.pb = reinterpret_cast<uint32_t*>(take(c * 4));
+    p.dq = reinterpret_cast<uint64_t*>(take(c * 8));
+    p.dr = reinterpret_cast<uint32_t*>(take(c * 4));
+    p.df = take(c);
+    p.dv = reinterpret_cast<uint64_t*>(take(c * 8));
+    p.nk = reinterpret_cast<uint64_t*>(take(c * 8));
+    p.nv = reinterpret_cast<uint64_t*>(take(c * 8));
+    p.nh = take(c);
+    p.ni = reinterpret_cast<uint32_t*>(take(c * 4));
+    return p;
+}
+
+// In-place exclusive scan of cnt[0, kR) by kT threads.
+template <int kT, int kR>
+__device__ __forceinline__ void small_excl_scan(uint32_t* cnt, uint32_t* tmp) {
+    constexpr int per = (kR + kT - 1) / kT;
+    uint32_t v[per];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        const int d = threadIdx.x * per + k;
+        v[k] = d < kR ? cnt[d] : 0u;
+        sum += v[k];
+    }
+    uint32_t run = block_excl_sum<kT>(sum, tmp, nullptr);
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        const int d = threadIdx.x * per + k;
+        if (d < kR) cnt[d] = run;
+        run += v[k];
+    }
+    __syncthreads();
+}
+
+// Largest index i in [lo - 1, ...) with K[i] <= q for up to kMK keys at once; K holds a
+// sentinel 2^64-1 at or before index lim and is readable 3 entries past it. A key with
+// K[lo] <= q unknown (lo = 0) may get -1. Each round loads four entries per active key,
+// so the keys' loads are independent and in flight together.
+__device__ __forceinline__ void multi_scan(const uint64_t* K, const uint64_t (&q)[kMK], uint32_t (&pos)[kMK],
+                                           int32_t (&r)[kMK], uint32_t act, uint32_t lim, uint32_t* err) {
+    uint32_t todo = act;
+    while (todo) {
+#pragma unroll
+        for (int k = 0; k < kMK; ++k) {
+            if (!((todo >> k) & 1u)) continue;
+            const uint32_t i = pos[k];
+            if (i > lim) {
+                atomicOr(err, kErrBounds);
+                r[k] = -1;
+                todo &= ~(1u << k);
+                continue;
+            }
+            const uint64_t k0 = K[i], k1 = K[i + 1], k2 = K[i + 2], k3 = K[i + 3];
+            // leading entries <= q (entries past the sentinel belong to other arrays)
+            const uint32_t c0 = k0 <= q[k], c1 = c0 & (k1 <= q[k]), c2 = c1 & (k2 <= q[k]), c3 = c2 & (k3 <= q[k]);
+            const uint32_t c = c0 + c1 + c2 + c3;
+            if (c < 4u) {
+                r[k] = (int32_t)(i + c) - 1;
+                todo &= ~(1u << k);
+            } else {
+                pos[k] = i + 4u;
+            }
+        }
+    }
+}
+
+template <int kT, int kBits>
+__device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& s, uint8_t* dsm, MShared& sh) {
+    constexpr int kW = kT / 32;
+    constexpr int kR = 1 << kBits;
+    constexpr uint32_t kC = (uint32_t)kT * kMI;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const MIndex& X = a.idx[it.index];
+    const uint32_t n = it.n;
+    uint32_t* err = &X.m->error;
+
+    if (tid == 0) {
+        sh.m = *X.m;
+        sh.invalid = 0;
+        sh.newc = 0;
+        sh.dirty = 0;
+        sh.changes = 0;
+        sh.tomb_delta = 0;
+    }
+    if (tid < 8) {
+        sh.bmax[tid] = 0;
+        sh.bnmin[tid] = 0;
+    }
+    if (tid < kLevelSlots) sh.delta[tid] = 0;
+    __syncthreads();
+    if (sh.m.error || n == 0) return;
+    const uint32_t cur = sh.m.cur;
+    uint64_t* SK = X.st.keys[cur];
+    uint64_t* SV = X.st.vals[cur];
+    uint8_t* SM = X.st.meta[cur];
+
+    // ---- pack: sort key (2^64-1 for invalid queries), payload op << 30 | arrival index
+    {
+        uint32_t mx[8], mn[8], inv = 0;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) mx[d] = mn[d] = 0;
+        for (uint32_t i = tid; i < n; i += kT) {
+            const uint32_t op = it.ops[i];
+            const uint64_t k = it.keys[i];
+            const bool valid = op <= 2u && k != kMaxKey;
+            s.ka[i] = valid ? k : kMaxKey;
+            s.pa[i] = ((op & 3u) << 30) | i;
+            inv += valid ? 0u : 1u;
+            if (valid) {
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    const uint32_t b = (uint32_t)(k >> (8 * d)) & 255u;
+                    mx[d] = max(mx[d], b);
+                    mn[d] = max(mn[d], 255u - b);
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            mx[d] = __reduce_max_sync(0xffffffffu, mx[d]);
+            mn[d] = __reduce_max_sync(0xffffffffu, mn[d]);
+        }
+        inv = __reduce_add_sync(0xffffffffu, inv);
+        if (lane == 0) {
+            if (inv) atomicAdd(&sh.invalid, inv);
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                atomicMax(&sh.bmax[d], mx[d]);
+                atomicMax(&sh.bnmin[d], mn[d]);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) plan_digits(sh.bmax, sh.bnmin, sh.invalid, n, 8u, sh.plan);
+        __syncthreads();
+    }
+    const uint32_t qv = n - sh.invalid;
+
+    // ---- sort: one stable pass per kBits-bit digit of every planned byte
+    uint64_t* K = s.ka;
+    uint32_t* P = s.pa;
+    {
+        uint64_t* K2 = s.kb;
+        uint32_t* P2 = s.pb;
+        uint32_t* whist = reinterpret_cast<uint32_t*>(dsm);  // [kW][kR]
+        uint32_t* sbase = whist + kW * kR;                   // [kR]
+        uint32_t* stot = sbase + kR;                         // [kR]
+        const uint32_t npass = sh.plan.npass;
+        for (uint32_t j = 0; j < npass; ++j) {
+            for (int sub = 0; sub < 8 / kBits; ++sub) {
+                const uint32_t shift = 8u * sh.plan.digit[j] + (uint32_t)(sub * kBits);
+                for (int d = tid; d < kW * kR; d += kT) whist[d] = 0;
+                for (int d = tid; d < kR; d += kT) sbase[d] = 0;
+                __syncthreads();
+                for (uint32_t i = tid; i < n; i += kT) atomicAdd(&sbase[(uint32_t)(K[i] >> shift) & (kR - 1)], 1u);
+                __syncthreads();
+                small_excl_scan<kT, kR>(sbase, sh.tmp);
+                for (uint32_t c0 = 0; c0 < n; c0 += kC) {
+                    uint64_t key[kMI];
+                    uint32_t pay[kMI], dig[kMI], rank[kMI];
+#pragma unroll
+                    for (int k = 0; k < kMI; ++k) {
+                        const uint32_t i = c0 + (uint32_t)warp * 32u * kMI + (uint32_t)k * 32u + (uint32_t)lane;
+                        const bool v = i < n;
+                        key[k] = v ? K[i] : 0ull;
+                        pay[k] = v ? P[i] : 0u;
+                        dig[k] = v ? (uint32_t)(key[k] >> shift) & (kR - 1) : (uint32_t)kR;
+                    }
+                    warp_digit_ranks<kMI, kBits>(dig, rank, whist + warp * kR);
+                    __syncthreads();
+                    for (int d = tid; d < kR; d += kT) {
+                        uint32_t total = 0;
+#pragma unroll 4
+                        for (int w = 0; w < kW; ++w) {
+                            const uint32_t cc = whist[w * kR + d];
+                            whist[w * kR + d] = total;
+                            total += cc;
+                        }
+                        stot[d] = total;
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int k = 0; k < kMI; ++k) {
+                        const uint32_t d = dig[k];
+                        if (d < (uint32_t)kR) {
+                            const uint32_t pos = sbase[d] + whist[warp * kR + d] + rank[k];
+                            if (pos < n) {
+                                K2[pos] = key[k];
+                                P2[pos] = pay[k];
+                            } else {
+                                atomicOr(err, kErrBounds);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    for (int d = tid; d < kR; d += kT) {
+                        sbase[d] += stot[d];
+#pragma unroll 4
+                        for (int w = 0; w < kW; ++w) whist[w * kR + d] = 0;
+                    }
+                    __syncthreads();
+                }
+                uint64_t* tk = K; K = K2; K2 = tk;
+                uint32_t* tp = P; P = P2; P2 = tp;
+            }
+        }
+    }
+
+    // ---- distinct keys of the valid prefix [0, qv)
+    {
+        uint32_t carry = 0;
+        for (uint32_t c0 = 0; c0 < qv; c0 += kC) {
+            const uint32_t j0 = c0 + (uint32_t)tid * kMI;
+            uint64_t prev = (j0 > 0 && j0 - 1 < qv) ? K[j0 - 1] : 0ull;
+            uint32_t hm = 0;
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                const uint32_t j = j0 + k;
+                const uint64_t kk = j < qv ? K[j] : 0ull;
+                if (j < qv && (j == 0 || kk != prev)) hm |= 1u << k;
+                prev = kk;
+            }
+            uint32_t tot;
+            uint32_t o = carry + block_excl_sum<kT>((uint32_t)__popc(hm), sh.tmp, &tot);
+#pragma unroll
+            for (int k = 0; k < kMI; ++k)
+                if ((hm >> k) & 1u) s.dq[o++] = K[j0 + k];
+            carry += tot;
+        }
+        if (tid == 0) sh.D = carry;
+        __syncthreads();
+    }
+    const uint32_t D = sh.D;
+
+    // ---- descent + locate for every distinct key
+    {
+        const DevMeta& m = sh.m;
+        const uint32_t H = m.H, Lb = m.Lb, size = m.size;
+        const bool built = Lb <= H && H >= 2;
+        uint32_t Lp = H + 1;  // lowest level staged in shared memory (> H: none)
+        if (built)
+            for (int l = (int)H; l >= (int)Lb; --l) {
+                if (m.base[l] + m.n[l] + 1u <= kMTop) Lp = (uint32_t)l;
+                else break;
+            }
+        uint64_t* tk = reinterpret_cast<uint64_t*>(dsm);
+        uint32_t* td = reinterpret_cast<uint32_t*>(dsm + kMTop * sizeof(uint64_t));
+        const uint32_t nst = (built && Lp <= H) ? m.base[Lp] + m.n[Lp] + 1u : 0u;
+        for (uint32_t i = tid; i < nst; i += kT) {
+            tk[i] = X.lkeys[i];
+            td[i] = X.ldown[i];
+        }
+        __syncthreads();
+        for (uint32_t d0 = 0; d0 < D; d0 += (uint32_t)kT * kMK) {
+            uint64_t q[kMK];
+            uint32_t pos[kMK];
+            int32_t r[kMK];
+            uint32_t act = 0;
+#pragma unroll
+            for (int k = 0; k < kMK; ++k) {
+                const uint32_t d = d0 + (uint32_t)k * kT + (uint32_t)tid;
+                q[k] = d < D ? s.dq[d] : kMaxKey;
+                pos[k] = 0;
+                r[k] = -1;
+                if (d < D) act |= 1u << k;
+            }
+            int l = built ? (int)H : 0;
+            if (built && Lp <= H) {
+                // the staged level Lp holds every key of the levels above it
+                const uint32_t b = m.base[Lp], cnt = m.n[Lp];
+#pragma unroll
+                for (int k = 0; k < kMK; ++k) {
+                    uint32_t lo = 0, hi = cnt;  // first index with key > q
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (tk[b + mid] <= q[k]) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    pos[k] = lo ? td[b + lo - 1] : 0u;
+                }
+                l = (int)Lp - 1;
+            }
+            if (built)
+                for (; l >= (int)Lb; --l) {
+                    const uint32_t b = m.base[l];
+                    multi_scan(X.lkeys + b, q, pos, r, act, m.n[l], err);
+#pragma unroll
+                    for (int k = 0; k < kMK; ++k) pos[k] = r[k] >= 0 ? X.ldown[b + (uint32_t)r[k]] : 0u;
+                }
+            if (built) {
+                multi_scan(SK, q, pos, r, act, size, err);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kMK; ++k) {  // no index level: binary search of the storage layer
+                    uint32_t lo = 0, hi = size;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (SK[mid] <= q[k]) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    r[k] = (int32_t)lo - 1;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kMK; ++k) {
+                if (!((act >> k) & 1u)) continue;
+                const uint32_t d = d0 + (uint32_t)k * kT + (uint32_t)tid;
+                const bool exists = r[k] >= 0 && SK[r[k]] == q[k];
+                const bool live = exists && !(SM[r[k]] & kTomb);
+                s.dr[d] = (uint32_t)(r[k] + 1);
+                s.df[d] = (uint8_t)((exists ? 1u : 0u) | (live ? 2u : 0u));
+                s.dv[d] = live ? SV[r[k]] : 0ull;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- results, ownership and apply: one pass over [0, qv) with running carries
+    {
+        uint32_t cmax = 0, cheads = 0, cnew = 0;
+        for (uint32_t c0 = 0; c0 < qv; c0 += kC) {
+            const uint32_t j0 = c0 + (uint32_t)tid * kMI;
+            uint64_t key[kMI];
+            uint32_t pay[kMI];
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                const uint32_t j = j0 + k;
+                key[k] = j < qv ? K[j] : kMaxKey;
+                pay[k] = j < qv ? P[j] : 0u;
+            }
+            const uint64_t kprev = (j0 > 0 && j0 - 1 < qv) ? K[j0 - 1] : kMaxKey;
+            const uint64_t knext = (j0 + kMI < qv) ? K[j0 + kMI] : kMaxKey;
+            uint32_t agg = 0, hm = 0, om = 0;
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                const uint32_t j = j0 + k;
+                const bool valid = j < qv;
+                const uint64_t prev = k ? key[k - 1] : kprev;
+                const uint64_t next = k + 1 < kMI ? key[k + 1] : knext;
+                const bool head = valid && (j == 0 || key[k] != prev);
+                const bool last = valid && (j + 1 == qv || key[k] != next);
+                const uint32_t op = pay[k] >> 30;
+                const uint32_t e = (valid && (op == 1u || op == 2u)) ? 2u * j + 3u : (head ? 2u * j + 2u : 0u);
+                agg = max(agg, e);
+                hm |= (head ? 1u : 0u) << k;
+                om |= (last ? 1u : 0u) << k;
+            }
+            uint32_t tmax;
+            uint32_t M = max(cmax, block_excl_max<kT>(agg, sh.tmp, &tmax));
+            uint32_t htot;
+            uint32_t hidx = cheads + block_excl_sum<kT>((uint32_t)__popc(hm), sh.tmp, &htot);
+            // First walk: every query's result; the owners' final states.
+            uint32_t nm = 0, wm = 0, lm = 0;  // new node; run wrote; final live
+            uint64_t fval[kMI];
+            uint32_t djs[kMI];
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                const uint32_t j = j0 + k;
+                fval[k] = 0;
+                djs[k] = 0;
+                if (j >= qv) continue;
+                const bool head = (hm >> k) & 1u;
+                hidx += head ? 1u : 0u;
+                const uint32_t dj = hidx - 1u;
+                djs[k] = dj;
+                const uint32_t op = pay[k] >> 30;
+                const uint32_t e = (op == 1u || op == 2u) ? 2u * j + 3u : (head ? 2u * j + 2u : 0u);
+                const uint32_t mex = M;
+                M = max(M, e);
+                const uint8_t fl = s.df[dj];
+                bool pl;
+                uint64_t pv;
+                bool wrote = false;
+                if (!head && (mex & 1u)) {  // the last write before j lies in j's key run
+                    const uint32_t pw = P[(mex - 3u) >> 1];
+                    pl = (pw >> 30) == 1u;
+                    pv = pl ? it.vals[pw & kMSeqMask] : 0ull;
+                    wrote = true;
+                } else {
+                    pl = (fl & 2u) != 0;
+                    pv = s.dv[dj];
+                }
+                mstore_result(it.results, pay[k] & kMSeqMask, pl ? pv : 0ull, pl ? PI_R_PRESENT : PI_R_ABSENT);
+                if (!((om >> k) & 1u)) continue;
+                bool flive = pl;
+                uint64_t fv = pv;
+                if (op == 1u) {
+                    flive = true;
+                    fv = it.vals[pay[k] & kMSeqMask];
+                    wrote = true;
+                } else if (op == 2u) {
+                    flive = false;
+                    fv = 0;
+                    wrote = true;
+                }
+                fval[k] = fv;
+                if (wrote) wm |= 1u << k;
+                if (flive) lm |= 1u << k;
+                if (wrote && !(fl & 1u) && flive) nm |= 1u << k;
+            }
+            uint32_t ntot;
+            uint32_t slot = cnew + block_excl_sum<kT>((uint32_t)__popc(nm), sh.tmp, &ntot);
+            // Second walk: the owners whose run wrote update their node or add a new one.
+            int32_t tomb_d = 0;
+            uint32_t chg = 0, dirty = 0;
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                if (!((wm >> k) & 1u)) continue;
+                const uint32_t dj = djs[k];
+                const uint8_t fl = s.df[dj];
+                const bool flive = (lm >> k) & 1u;
+                const bool live0 = (fl & 2u) != 0;
+                if (fl & 1u) {
+                    const uint32_t r = s.dr[dj] - 1u;
+                    const uint8_t meta = SM[r];
+                    const uint32_t h = meta & 0x3Fu;
+                    if (flive) SV[r] = fval[k];
+                    SM[r] = (uint8_t)(h | (flive ? 0u : kTomb));
+                    if (flive != live0) {
+                        tomb_d += flive ? -1 : 1;
+                        ++chg;
+                        if (h >= 2u) dirty = 1;
+                        for (uint32_t l = 1; l <= h && l < (uint32_t)kLevelSlots; ++l)
+                            atomicAdd(&sh.delta[l], flive ? 1 : -1);
+                    }
+                } else if (flive) {
+                    const uint32_t h = tower_height(key[k], X.hp);
+                    s.nk[slot] = key[k];
+                    s.nv[slot] = fval[k];
+                    s.nh[slot] = (uint8_t)h;
+                    s.ni[slot] = s.dr[dj];
+                    ++slot;
+                    ++chg;
+                    dirty = 1;
+                    for (uint32_t l = 1; l <= h && l < (uint32_t)kLevelSlots; ++l) atomicAdd(&sh.delta[l], 1);
+                }
+            }
+            if (tomb_d) atomicAdd(&sh.tomb_delta, tomb_d);
+            if (chg) atomicAdd(&sh.changes, chg);
+            if (dirty) sh.dirty = 1;
+            cmax = max(cmax, tmax);
+            cheads += htot;
+            cnew += ntot;
+        }
+        // invalid queries
+        for (uint32_t j = qv + tid; j < n; j += kT) mstore_result(it.results, P[j] & kMSeqMask, 0ull, PI_R_INVALID);
+        if (tid == 0) sh.newc = cnew;
+        __syncthreads();
+        if (tid == 0) {
+            DevMeta& m = sh.m;
+            m.tombs = (uint32_t)((int32_t)m.tombs + sh.tomb_delta);
+            for (int l = 1; l < kLevelSlots; ++l) m.cnt[l] = (uint32_t)((int32_t)m.cnt[l] + sh.delta[l]);
+            m.updates += sh.changes;
+            m.batches += 1;
+        }
+        __syncthreads();
+    }
+
+    // ---- merge: live old nodes and the new nodes into the other storage buffer
+    const uint32_t M = sh.newc;
+    const bool merged = M > 0 || (sh.m.tombs > 0 && (uint64_t)sh.m.tombs * 8u > sh.m.size);
+    if (merged) {
+        const uint32_t size = sh.m.size;
+        const uint32_t dst = cur ^ 1u;
+        uint64_t* DK = X.st.keys[dst];
+        uint64_t* DV = X.st.vals[dst];
+        uint8_t* DM = X.st.meta[dst];
+        uint32_t* lp = reinterpret_cast<uint32_t*>(dsm);  // live nodes before each chunk position
+        uint32_t carry = 0, j0 = 0;
+        for (uint32_t c0 = 0; c0 < size; c0 += kC) {
+            const uint32_t i0 = c0 + (uint32_t)tid * kMI;
+            uint32_t lmask = 0;
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                const uint32_t i = i0 + k;
+                if (i < size && !(SM[i] & kTomb)) lmask |= 1u << k;
+            }
+            uint32_t tot;
+            uint32_t lb = carry + block_excl_sum<kT>((uint32_t)__popc(lmask), sh.tmp, &tot);
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                lp[tid * kMI + k] = lb;
+                lb += (lmask >> k) & 1u;
+            }
+            if (tid == 0) {  // new nodes placed before an old node of this chunk: [j0, j1)
+                uint32_t lo = j0, hi = M;
+                const uint32_t lim = c0 + kC < size ? c0 + kC : size;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s.ni[mid] < lim) lo = mid + 1;
+                    else hi = mid;
+                }
+                sh.j1 = lo;
+            }
+            __syncthreads();
+            const uint32_t j1 = sh.j1;
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                if (!((lmask >> k) & 1u)) continue;
+                const uint32_t i = i0 + k;
+                uint32_t lo = j0, hi = j1;  // new nodes with insertion point <= i
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s.ni[mid] <= i) lo = mid + 1;
+                    else hi = mid;
+                }
+                const uint32_t o = lp[tid * kMI + k] + lo;
+                DK[o] = SK[i];
+                DV[o] = SV[i];
+                DM[o] = (uint8_t)(SM[i] & 0x3Fu);
+            }
+            for (uint32_t j = j0 + tid; j < j1; j += kT) {
+                const uint32_t o = j + lp[s.ni[j] - c0];
+                DK[o] = s.nk[j];
+                DV[o] = s.nv[j];
+                DM[o] = s.nh[j];
+            }
+            carry += tot;
+            j0 = j1;
+            __syncthreads();
+        }
+        for (uint32_t j = j0 + tid; j < M; j += kT) {  // after the last old node
+            const uint32_t o = j + carry;
+            DK[o] = s.nk[j];
+            DV[o] = s.nv[j];
+            DM[o] = s.nh[j];
+        }
+        const uint32_t nsize = carry + M;
+        if (tid == 0) {
+            if (nsize > X.st_cap) atomicOr(err, kErrBounds);
+            DK[nsize] = kMaxKey;
+            DV[nsize] = 0;
+            DM[nsize] = 0;
+            sh.m.size = nsize;
+            sh.m.tombs = 0;
+            sh.m.cur = dst;
+        }
+        __syncthreads();
+    }
+
+    // ---- rebuild the index layer when the membership of any level changed
+    if (merged || sh.dirty) {
+        if (tid == 0) {
+            DevMeta& m = sh.m;
+            uint32_t H = 1;
+            for (int l = 2; l < kLevelSlots; ++l)
+                if (m.cnt[l] > 0) H = (uint32_t)l;
+            uint64_t need = 0;
+            for (uint32_t l = 2; l <= H; ++l) need += (uint64_t)m.cnt[l] + 1u;
+            uint32_t Lb = 2;
+            uint64_t fit = need;
+            while (Lb <= H && fit > X.idx_cap) {
+                fit -= (uint64_t)m.cnt[Lb] + 1u;
+                ++Lb;
+            }
+            m.index_need = (uint32_t)need;
+            m.grow_request = (Lb > 2) ? 1u : 0u;
+            for (int l = 0; l < kLevelSlots; ++l) {
+                m.n[l] = 0;
+                m.base[l] = 0;
+            }
+            uint32_t off = 0;
+            for (int l = (int)H; l >= (int)Lb; --l) {
+                m.base[l] = off;
+                m.n[l] = m.cnt[l];
+                off += m.cnt[l] + 1u;
+            }
+            m.H = H;
+            m.Lb = Lb;
+            m.index_total = off;
+            uint32_t Ls = H + 1;
+            for (int l = (int)H; l >= (int)Lb; --l) {
+                if (m.base[l] + m.n[l] + 1u <= X.smem_top) Ls = (uint32_t)l;
+                else break;
+            }
+            m.Ls = Ls;
+            m.smem_entries = (Ls <= H) ? m.base[Ls] + m.n[Ls] + 1u : 0u;
+            m.updates = 0;
+            m.rebuilds += 1;
+        }
+        __syncthreads();
+        const DevMeta& m = sh.m;
+        const uint32_t H = m.H, Lb = m.Lb, size = m.size;
+        const uint32_t ncur = m.cur;
+        const uint64_t* RK = X.st.keys[ncur];
+        const uint8_t* RM = X.st.meta[ncur];
+        if (Lb <= H) {
+            // level Lb from the storage layer: live nodes of height >= Lb
+            uint32_t carry = 0;
+            for (uint32_t c0 = 0; c0 < size; c0 += kC) {
+                const uint32_t i0 = c0 + (uint32_t)tid * kMI;
+                uint32_t mm = 0;
+#pragma unroll
+                for (int k = 0; k < kMI; ++k) {
+                    const uint32_t i = i0 + k;
+                    if (i < size) {
+                        const uint8_t mt = RM[i];
+                        if (!(mt & kTomb) && (mt & 0x3Fu) >= Lb) mm |= 1u << k;
+                    }
+                }
+                uint32_t tot;
+                uint32_t o = carry + block_excl_sum<kT>((uint32_t)__popc(mm), sh.tmp, &tot);
+#pragma unroll
+                for (int k = 0; k < kMI; ++k) {
+                    if (!((mm >> k) & 1u)) continue;
+                    if (o < m.n[Lb]) {
+                        X.lkeys[m.base[Lb] + o] = RK[i0 + k];
+                        X.ldown[m.base[Lb] + o] = i0 + k;
+                    }
+                    ++o;
+                }
+                carry += tot;
+            }
+            if (tid == 0 && carry != m.n[Lb]) atomicOr(err, kErrBounds);
+            __syncthreads();
+            // level l + 1 from level l: its members of height >= l + 1
+            for (uint32_t l = Lb; l < H; ++l) {
+                const uint32_t bl = m.base[l], nl = m.n[l], bu = m.base[l + 1], nu = m.n[l + 1];
+                carry = 0;
+                for (uint32_t c0 = 0; c0 < nl; c0 += kC) {
+                    const uint32_t i0 = c0 + (uint32_t)tid * kMI;
+                    uint32_t mm = 0;
+                    uint64_t kk[kMI];
+#pragma unroll
+                    for (int k = 0; k < kMI; ++k) {
+                        const uint32_t i = i0 + k;
+                        kk[k] = i < nl ? X.lkeys[bl + i] : 0ull;
+                        if (i < nl && tower_height(kk[k], X.hp) >= l + 1u) mm |= 1u << k;
+                    }
+                    uint32_t tot;
+                    uint32_t o = carry + block_excl_sum<kT>((uint32_t)__popc(mm), sh.tmp, &tot);
+#pragma unroll
+                    for (int k = 0; k < kMI; ++k) {
+                        if (!((mm >> k) & 1u)) continue;
+                        if (o < nu) {
+                            X.lkeys[bu + o] = kk[k];
+                            X.ldown[bu + o] = i0 + k;
+                        }
+                        ++o;
+                    }
+                    carry += tot;
+                }
+                if (tid == 0 && carry != nu) atomicOr(err, kErrBounds);
+                __syncthreads();
+            }
+            for (uint32_t l = Lb + tid; l <= H; l += kT) {  // sentinels
+                const uint32_t sidx = m.base[l] + m.n[l];
+                X.lkeys[sidx] = kMaxKey;
+                X.ldown[sidx] = (l > Lb) ? m.n[l - 1] : size;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- publish the index's new state
+    if (tid == 0) {
+        DevMeta* gm = X.m;
+        const DevMeta& m = sh.m;
+        gm->cur = m.cur;
+        gm->size = m.size;
+        gm->tombs = m.tombs;
+        gm->H = m.H;
+        gm->Lb = m.Lb;
+        gm->Ls = m.Ls;
+        gm->smem_entries = m.smem_entries;
+        gm->index_total = m.index_total;
+        gm->index_need = m.index_need;
+        gm->grow_request = m.grow_request;
+        gm->updates = m.updates;
+        gm->rebuilds = m.rebuilds;
+        gm->batches = m.batches;
+        for (int l = 0; l < kLevelSlots; ++l) {
+            gm->cnt[l] = m.cnt[l];
+            gm->n[l] = m.n[l];
+            gm->base[l] = m.base[l];
+        }
+        if (a.mirror) a.mirror[it.index] = *gm;  // the host reads the set's sizes from one copy
+    }
+    __syncthreads();
+}
+
+template <int kW, int kBits>
+__global__ void __launch_bounds__(kW * 32) k_multi(MultiArgs a) {
+    constexpr int kT = kW * 32;
+    extern __shared__ __align__(16) uint8_t dsm[];
+    __shared__ MShared sh;
+    const MScratchPtrs s = carve(a.scratch + (uint64_t)blockIdx.x * a.stride, a.qcap);
+    const uint32_t nitems = *a.nitems;
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(a.head, 1u);
+        __syncthreads();
+        const uint32_t item = sh.item;
+        __syncthreads();
+        if (item >= nitems) break;
+        const MItem it = a.items[item];
+        if (it.n <= a.qcap) m_item<kT, kBits>(a, it, s, dsm, sh);
+        else if (threadIdx.x == 0) atomicOr(&a.idx[it.index].m->error, kErrBounds);
+        __syncthreads();
+    }
+}
+
+template <int kW, int kBits>
+constexpr int multi_smem() {
+    constexpr int kT = kW * 32;
+    constexpr int sort = (kW * (1 << kBits) + 2 * (1 << kBits)) * 4;
+    constexpr int top = (int)kMTop * 12;
+    constexpr int merge = kT * kMI * 4;
+    return sort > top ? (sort > merge ? sort : merge) : (top > merge ? top : merge);
+}
+
+// Sets the kernel's dynamic shared-memory limit (once; before any capture) and returns
+// its resident CTAs per SM.
+template <int kW, int kBits>
+cudaError_t occupancy_t(int* blocks) {
+    constexpr int dyn = multi_smem<kW, kBits>();
+    cudaError_t e = cudaFuncSetAttribute(k_multi<kW, kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_multi<kW, kBits>, kW * 32, dyn);
+}
+
+template <int kW, int kBits>
+cudaError_t launch_multi_t(const MultiArgs& a, uint32_t grid, cudaStream_t s) {
+    k_multi<kW, kBits><<<grid, kW * 32, multi_smem<kW, kBits>(), s>>>(a);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+uint64_t multi_scratch_bytes(uint32_t qcap) {
+    const uint64_t c = (uint64_t)qcap + kPad;
+    auto al = [](uint64_t b) { return (b + 255u) & ~255ull; };
+    return 2 * al(c * 8) + 2 * al(c * 4) + al(c * 8) + al(c * 4) + al(c) + al(c * 8) + 2 * al(c * 8) + al(c) +
+           al(c * 4);
+}
+
+// multi_occupancy must have run for the variant first (it sets the shared-memory limit).
+cudaError_t launch_multi(const MultiArgs& a, int warps, int radix_bits, uint32_t grid, cudaStream_t s) {
+    if (grid == 0) return cudaSuccess;
+    if (radix_bits == 8) {
+        if (warps == 8) return launch_multi_t<8, 8>(a, grid, s);
+        if (warps == 16) return launch_multi_t<16, 8>(a, grid, s);
+        if (warps == 32) return launch_multi_t<32, 8>(a, grid, s);
+    } else if (radix_bits == 4) {
+        if (warps == 8) return launch_multi_t<8, 4>(a, grid, s);
+        if (warps == 16) return launch_multi_t<16, 4>(a, grid, s);
+        if (warps == 32) return launch_multi_t<32, 4>(a, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t multi_occupancy(int warps, int radix_bits, int* blocks) {
+    if (radix_bits == 8) {
+        if (warps == 8) return occupancy_t<8, 8>(blocks);
+        if (warps == 16) return occupancy_t<16, 8>(blocks);
+        if (warps == 32) return occupancy_t<32, 8>(blocks);
+    } else if (radix_bits == 4) {
+        if (warps == 8) return occupancy_t<8, 4>(blocks);
+        if (warps == 16) return occupancy_t<16, 4>(blocks);
+        if (warps == 32) return occupancy_t<32, 4>(blocks);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace pi

@@ -9,7 +9,9 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 
@@ -97,6 +99,7 @@ struct pi_index {
     uint64_t seen = 0;          // batches whose mailbox has been read (a prefix)
     DevMeta known{};       // last mailbox snapshot
     uint64_t pending_n = 0;  // queries issued after that snapshot
+    uint64_t extra_n = 0;    // queries of batching-form calls since the last full sync
     bool force_rebuild = false;
     // stage timing (pi_profile): events recorded between the pipeline's kernels
     bool prof = false;
@@ -361,6 +364,7 @@ cudaError_t sync_known(pi_index* x, cudaStream_t s) {
         for (uint64_t b = x->seen; b < x->issued; ++b) cudaEventSynchronize(x->ev[b % kRing]);
         x->seen = x->issued;
         x->pending_n = 0;
+        x->extra_n = 0;
     }
     return e;
 }
@@ -832,7 +836,7 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
         if ((e = alloc_scratch(x->sc, q)) != cudaSuccess) return map_cuda(e);
         if ((e = ensure_desc(x, desc_need(q, x->st_cap))) != cudaSuccess) return map_cuda(e);
     }
-    uint64_t size_ub = (uint64_t)x->known.size + x->pending_n + n;
+    uint64_t size_ub = (uint64_t)x->known.size + x->pending_n + x->extra_n + n;
     if (size_ub > x->st_cap) {
         if ((e = sync_known(x, s)) != cudaSuccess) return map_cuda(e);
         if (int rc = sticky_error(x->known)) return rc;
@@ -893,7 +897,7 @@ int pi_execute_batch_noalloc(pi_index_t* x, const uint8_t* ops, const uint64_t* 
     if (carve_scratch(base, PI_NOALLOC_MAX_BATCH, sc) != kNoAllocBytes) return PI_ERR_CUDA;
     refresh_known(x);
     if (int rc = sticky_error(x->known)) return rc;
-    uint64_t size_ub = (uint64_t)x->known.size + x->pending_n + n;
+    uint64_t size_ub = (uint64_t)x->known.size + x->pending_n + x->extra_n + n;
     if (size_ub > x->st_cap) {
         if ((e = sync_known(x, s)) != cudaSuccess) return map_cuda(e);
         if (int rc = sticky_error(x->known)) return rc;
@@ -1024,5 +1028,359 @@ int pi_export_level(pi_index_t* x, int level, uint64_t* keys_out, uint32_t* down
     e = cudaStreamSynchronize(s);
     return map_cuda(e);
 }
+
+
+// ---------------------------------------------------------------------------------
+// Batching form (host side). The queue buffer holds, per class, the number of items
+// and the next-item counter, then one slice of `count` items per class; it is filled
+// on the host (pinned, one buffer per call parity) and copied in by the graph's first
+// node. One CUDA graph per parity: copy -> one persistent kernel per size class on
+// parallel branches.
+
+}  // extern "C"
+
+struct pi_multi {
+    int device = 0;
+    int num_sms = 0;
+    std::vector<pi_index*> idx;
+    std::vector<MIndex> h_idx;
+    pi_multi_config_t cfg{};
+    MIndex* d_idx = nullptr;
+    DevMeta* d_mirror = nullptr;
+    uint8_t* d_q = nullptr;
+    uint8_t* h_q[2] = {};
+    uint64_t q_bytes = 0;
+    cudaEvent_t q_free[2] = {};
+    uint64_t calls = 0;
+    uint64_t launches = 0;  // kernels per graph launch
+    uint32_t grid[PI_MULTI_MAX_CLASSES] = {};
+    uint32_t qcap[PI_MULTI_MAX_CLASSES] = {};
+    uint8_t* scratch[PI_MULTI_MAX_CLASSES] = {};
+    uint64_t stride[PI_MULTI_MAX_CLASSES] = {};
+    cudaStream_t cs = nullptr;
+    cudaStream_t ls[PI_MULTI_MAX_CLASSES] = {};
+    cudaEvent_t evf = nullptr;
+    cudaEvent_t evj[PI_MULTI_MAX_CLASSES] = {};
+    cudaGraphExec_t gx[2] = {};
+    bool graph_valid = false;
+};
+
+namespace {
+
+constexpr uint64_t kQHeader = 64;  // counts[PI_MULTI_MAX_CLASSES], heads[PI_MULTI_MAX_CLASSES], pad
+
+MIndex mindex_of(const pi_index* x) {
+    MIndex mi{};
+    mi.m = x->d_meta;
+    mi.st = x->st;
+    mi.lkeys = x->lkeys;
+    mi.ldown = x->ldown;
+    mi.st_cap = (uint32_t)x->st_cap;
+    mi.idx_cap = (uint32_t)(x->idx_cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : x->idx_cap);
+    mi.smem_top = x->smem_top;
+    mi.hp = x->hp;
+    return mi;
+}
+
+void multi_free_graphs(pi_multi* mx) {
+    for (auto& g : mx->gx)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    mx->graph_valid = false;
+}
+
+void multi_destroy(pi_multi* mx) {
+    if (!mx) return;
+    cudaSetDevice(mx->device);
+    for (int p = 0; p < 2; ++p)
+        if (mx->q_free[p]) cudaEventSynchronize(mx->q_free[p]);
+    multi_free_graphs(mx);
+    dfree(mx->d_idx);
+    dfree(mx->d_mirror);
+    dfree(mx->d_q);
+    for (auto& h : mx->h_q)
+        if (h) cudaFreeHost(h);
+    for (auto& sc : mx->scratch) dfree(sc);
+    for (auto& e : mx->q_free)
+        if (e) cudaEventDestroy(e);
+    for (auto& e : mx->evj)
+        if (e) cudaEventDestroy(e);
+    if (mx->evf) cudaEventDestroy(mx->evf);
+    for (auto& st : mx->ls)
+        if (st) cudaStreamDestroy(st);
+    if (mx->cs) cudaStreamDestroy(mx->cs);
+    delete mx;
+}
+
+int class_of(const pi_multi* mx, uint64_t nodes) {
+    uint32_t lg = 0;
+    while (lg < 63 && (1ull << lg) < nodes) ++lg;
+    for (uint32_t c = 0; c + 1 < mx->cfg.num_classes; ++c)
+        if (lg <= mx->cfg.cls[c].max_log2_size) return (int)c;
+    return (int)mx->cfg.num_classes - 1;
+}
+
+cudaError_t multi_build_graphs(pi_multi* mx) {
+    multi_free_graphs(mx);
+    const uint32_t count = (uint32_t)mx->idx.size();
+    uint64_t launches = 0;
+    for (int p = 0; p < 2; ++p) {
+        const uint64_t l0 = g_launches;
+        cudaError_t e = cudaStreamBeginCapture(mx->cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaMemcpyAsync(mx->d_q, mx->h_q[p], mx->q_bytes, cudaMemcpyHostToDevice, mx->cs);
+        cudaEventRecord(mx->evf, mx->cs);
+        const uint32_t* counts = reinterpret_cast<const uint32_t*>(mx->d_q);
+        uint32_t* heads = reinterpret_cast<uint32_t*>(mx->d_q) + PI_MULTI_MAX_CLASSES;
+        const MItem* items = reinterpret_cast<const MItem*>(mx->d_q + kQHeader);
+        cudaError_t le = cudaSuccess;
+        for (uint32_t c = 0; c < mx->cfg.num_classes; ++c) {
+            if (!mx->grid[c] || !mx->qcap[c]) continue;
+            cudaStreamWaitEvent(mx->ls[c], mx->evf, 0);
+            MultiArgs a{};
+            a.idx = mx->d_idx;
+            a.items = items + (uint64_t)c * count;  // class c's slice of the queue
+            a.nitems = counts + c;
+            a.head = heads + c;
+            a.scratch = mx->scratch[c];
+            a.stride = mx->stride[c];
+            a.qcap = mx->qcap[c];
+            a.mirror = mx->d_mirror;
+            cudaError_t r =
+                launch_multi(a, (int)mx->cfg.cls[c].warps, (int)mx->cfg.cls[c].radix_bits, mx->grid[c], mx->ls[c]);
+            if (r != cudaSuccess && le == cudaSuccess) le = r;
+            cudaEventRecord(mx->evj[c], mx->ls[c]);
+            cudaStreamWaitEvent(mx->cs, mx->evj[c], 0);
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(mx->cs, &g);
+        if (e == cudaSuccess && le != cudaSuccess) e = le;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&mx->gx[p], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            multi_free_graphs(mx);
+            return e;
+        }
+        launches = g_launches - l0;
+    }
+    g_launches -= 2 * launches;  // counted per graph launch instead
+    mx->launches = launches;
+    mx->graph_valid = true;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+pi_multi_t* pi_multi_create(pi_index_t* const* indices, uint32_t count, const pi_multi_config_t* cfg) {
+    g_last_error = PI_OK;
+    if (!indices || count == 0) {
+        g_last_error = PI_ERR_INVALID_ARG;
+        return nullptr;
+    }
+    pi_multi_config_t c{};
+    if (cfg) {
+        if (cfg->struct_size != sizeof(pi_multi_config_t) || cfg->num_classes < 1 ||
+            cfg->num_classes > PI_MULTI_MAX_CLASSES) {
+            g_last_error = PI_ERR_INVALID_ARG;
+            return nullptr;
+        }
+        c = *cfg;
+        for (uint32_t k = 0; k < c.num_classes; ++k) {
+            const pi_multi_class_t& q = c.cls[k];
+            const bool ok = (q.warps == 8 || q.warps == 16 || q.warps == 32) &&
+                            (q.radix_bits == 4 || q.radix_bits == 8) &&
+                            (k == 0 || q.max_log2_size > c.cls[k - 1].max_log2_size);
+            if (!ok) {
+                g_last_error = PI_ERR_INVALID_ARG;
+                return nullptr;
+            }
+        }
+    } else {
+        c.struct_size = sizeof(c);
+        c.num_classes = 3;
+        c.cls[0] = {14, 8, 4, 0};
+        c.cls[1] = {17, 16, 8, 0};
+        c.cls[2] = {32, 32, 8, 0};
+    }
+    std::vector<pi_index*> v(indices, indices + count);
+    {
+        std::vector<pi_index*> sorted = v;
+        std::sort(sorted.begin(), sorted.end());
+        if (sorted[0] == nullptr || std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+            g_last_error = PI_ERR_INVALID_ARG;
+            return nullptr;
+        }
+    }
+    for (auto* x : v)
+        if (x->device != v[0]->device) {
+            g_last_error = PI_ERR_INVALID_ARG;
+            return nullptr;
+        }
+    pi_multi* mx = new (std::nothrow) pi_multi();
+    if (!mx) {
+        g_last_error = PI_ERR_OOM;
+        return nullptr;
+    }
+    mx->device = v[0]->device;
+    mx->num_sms = v[0]->num_sms;
+    mx->idx = v;
+    mx->cfg = c;
+    cudaSetDevice(mx->device);
+    cudaError_t e = cudaSuccess;
+    do {
+        for (auto* x : v) mx->h_idx.push_back(mindex_of(x));
+        if ((e = dalloc(&mx->d_idx, count)) != cudaSuccess) break;
+        if ((e = cudaMemcpy(mx->d_idx, mx->h_idx.data(), count * sizeof(MIndex), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            break;
+        if ((e = dalloc(&mx->d_mirror, count)) != cudaSuccess) break;
+        mx->q_bytes = kQHeader + (uint64_t)PI_MULTI_MAX_CLASSES * count * sizeof(MItem);
+        if ((e = dalloc(&mx->d_q, mx->q_bytes)) != cudaSuccess) break;
+        for (int p = 0; p < 2; ++p) {
+            if ((e = cudaMallocHost(reinterpret_cast<void**>(&mx->h_q[p]), mx->q_bytes)) != cudaSuccess) break;
+            std::memset(mx->h_q[p], 0, mx->q_bytes);
+            if ((e = cudaEventCreateWithFlags(&mx->q_free[p], cudaEventDisableTiming)) != cudaSuccess) break;
+        }
+        if (e != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&mx->cs, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaEventCreateWithFlags(&mx->evf, cudaEventDisableTiming)) != cudaSuccess) break;
+        for (uint32_t k = 0; k < c.num_classes && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&mx->ls[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&mx->evj[k], cudaEventDisableTiming);
+            int occ = 0;
+            if (e == cudaSuccess) e = multi_occupancy((int)c.cls[k].warps, (int)c.cls[k].radix_bits, &occ);
+            if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
+            const uint64_t slots = (uint64_t)mx->num_sms * (uint64_t)occ;
+            mx->grid[k] = (uint32_t)(slots < count ? slots : count);
+        }
+    } while (0);
+    if (e != cudaSuccess) {
+        g_last_error = map_cuda(e);
+        multi_destroy(mx);
+        return nullptr;
+    }
+    return mx;
+}
+
+int pi_multi_execute(pi_multi_t* mx, const pi_multi_batch_t* b, uint32_t nb, pi_stream_t stream) {
+    if (!mx) return PI_ERR_INVALID_ARG;
+    if (nb == 0) return PI_OK;
+    const uint32_t count = (uint32_t)mx->idx.size();
+    if (!b || nb > count) return PI_ERR_INVALID_ARG;
+    cudaSetDevice(mx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<uint8_t> seen(count, 0);
+    for (uint32_t i = 0; i < nb; ++i) {
+        const pi_multi_batch_t& q = b[i];
+        if (q.index >= count || seen[q.index] || q.n > PI_MULTI_MAX_BATCH) return PI_ERR_INVALID_ARG;
+        if (q.n && (!q.ops || !q.keys || !q.values || !q.results)) return PI_ERR_INVALID_ARG;
+        seen[q.index] = 1;
+    }
+    cudaError_t e;
+    // Capacities: every index must hold its batch's new keys without growing in the
+    // kernel. Growing (rare) synchronises the stream, as in pi_execute_batch.
+    bool idx_changed = false;
+    for (uint32_t i = 0; i < nb; ++i) {
+        pi_index* x = mx->idx[b[i].index];
+        refresh_known(x);
+        if (int rc = sticky_error(x->known)) return rc;
+        const uint64_t n = b[i].n;
+        uint64_t size_ub = (uint64_t)x->known.size + x->pending_n + x->extra_n + n;
+        bool grew = false;
+        if (size_ub > x->st_cap || x->known.grow_request) {
+            if ((e = sync_known(x, s)) != cudaSuccess) return map_cuda(e);
+            if (int rc = sticky_error(x->known)) return rc;
+            size_ub = (uint64_t)x->known.size + n;
+            if (size_ub > PI_MAX_KEYS) return PI_ERR_INVALID_ARG;
+            if (size_ub > x->st_cap) {
+                if ((e = grow_storage(x, size_ub, s)) != cudaSuccess) return map_cuda(e);
+                grew = true;
+            }
+            if (x->known.grow_request && x->known.index_need + 64ull > x->idx_cap) {
+                if ((e = grow_index(x, x->known.index_need, s)) != cudaSuccess) return map_cuda(e);
+                grew = true;
+            }
+            x->known.grow_request = 0;
+        }
+        if (grew) {
+            mx->h_idx[b[i].index] = mindex_of(x);
+            idx_changed = true;
+        }
+        wait_rebuild(x, s);
+    }
+    if (idx_changed &&
+        (e = cudaMemcpyAsync(mx->d_idx, mx->h_idx.data(), mx->h_idx.size() * sizeof(MIndex),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return map_cuda(e);
+    // the queue: per class, largest estimated work first (longest-processing-time order)
+    std::vector<std::vector<std::pair<uint64_t, uint32_t>>> per(mx->cfg.num_classes);
+    uint32_t need_q[PI_MULTI_MAX_CLASSES] = {};
+    for (uint32_t i = 0; i < nb; ++i) {
+        if (b[i].n == 0) continue;
+        const pi_index* x = mx->idx[b[i].index];
+        const uint64_t nodes = (uint64_t)x->known.size + x->pending_n + x->extra_n;
+        const int c = class_of(mx, nodes);
+        per[c].push_back({nodes + 8 * b[i].n, i});
+        if (b[i].n > need_q[c]) need_q[c] = (uint32_t)b[i].n;
+    }
+    bool rebuild_graphs = !mx->graph_valid;
+    for (uint32_t c = 0; c < mx->cfg.num_classes; ++c) {
+        if (need_q[c] <= mx->qcap[c] || !mx->grid[c]) continue;
+        // grow the class's scratch (rare): wait for the calls that may still use it
+        for (int p = 0; p < 2; ++p) cudaEventSynchronize(mx->q_free[p]);
+        uint32_t q = mx->qcap[c] ? mx->qcap[c] : 4096u;
+        while (q < need_q[c]) q *= 2;
+        dfree(mx->scratch[c]);
+        mx->qcap[c] = 0;
+        mx->stride[c] = multi_scratch_bytes(q);
+        if ((e = dalloc(&mx->scratch[c], mx->stride[c] * mx->grid[c])) != cudaSuccess) {
+            mx->graph_valid = false;
+            return map_cuda(e);
+        }
+        mx->qcap[c] = q;
+        rebuild_graphs = true;
+    }
+    if (rebuild_graphs && (e = multi_build_graphs(mx)) != cudaSuccess) return map_cuda(e);
+    const int p = (int)(mx->calls & 1u);
+    if ((e = cudaEventSynchronize(mx->q_free[p])) != cudaSuccess) return map_cuda(e);
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(mx->h_q[p]);
+    MItem* items = reinterpret_cast<MItem*>(mx->h_q[p] + kQHeader);
+    for (uint32_t c = 0; c < PI_MULTI_MAX_CLASSES; ++c) {
+        hdr[c] = 0;                         // items of class c
+        hdr[PI_MULTI_MAX_CLASSES + c] = 0;  // its next-item counter
+    }
+    for (uint32_t c = 0; c < mx->cfg.num_classes; ++c) {
+        auto& L = per[c];
+        std::sort(L.begin(), L.end(), [](const auto& u, const auto& w) { return u.first > w.first; });
+        hdr[c] = (uint32_t)L.size();
+        MItem* slice = items + (uint64_t)c * count;
+        for (size_t k = 0; k < L.size(); ++k) {
+            const pi_multi_batch_t& q = b[L[k].second];
+            MItem& it = slice[k];
+            it.ops = q.ops;
+            it.keys = q.keys;
+            it.vals = q.values;
+            it.results = q.results;
+            it.n = (uint32_t)q.n;
+            it.index = q.index;
+        }
+    }
+    if ((e = cudaGraphLaunch(mx->gx[p], s)) != cudaSuccess) return map_cuda(e);
+    if ((e = cudaEventRecord(mx->q_free[p], s)) != cudaSuccess) return map_cuda(e);
+    mx->calls++;
+    g_launches += mx->launches;
+    for (uint32_t i = 0; i < nb; ++i) {
+        pi_index* x = mx->idx[b[i].index];
+        x->extra_n += b[i].n;
+        x->force_rebuild = true;  // the plain path recounts its per-tile level counts
+    }
+    return PI_OK;
+}
+
+void pi_multi_destroy(pi_multi_t* mx) { multi_destroy(mx); }
 
 }  // extern "C"

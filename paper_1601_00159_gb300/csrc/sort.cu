@@ -107,51 +107,7 @@ __global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, ui
     const int b = threadIdx.x;
     if (tile_max)
         for (uint32_t t = b; t < (n + kApplyTile - 1) / kApplyTile; t += 256) tile_max[t] = 0;
-    if (b == 0) {
-        SortPlan& P = bm->plan;
-        const bool any_valid = bm->invalid < n;
-        uint32_t r = 0;
-        uint32_t dig[8];
-        bool varies[8], differs[8];  // among valid keys; between valid and invalid keys
-        int p = -1;                  // highest byte where every valid key is below 0xFF
-        for (int d = 0; d < 8; ++d) {
-            const uint32_t hi = bm->bmax[d], lo = 255u - bm->bnmin[d];
-            varies[d] = any_valid && hi != lo;
-            differs[d] = bm->invalid && any_valid && lo < 255u;
-            if (varies[d]) dig[r++] = (uint32_t)d;
-            if (!any_valid || hi < 255u) p = d;
-        }
-        if (bm->invalid) {
-            bool have = false;
-            for (uint32_t j = 0; j < r; ++j) have |= dig[j] == (uint32_t)p;
-            if (p < 0) {  // no single byte separates the invalid key: sort every byte
-                r = 0;
-                for (int d = 0; d < 8; ++d) dig[r++] = (uint32_t)d;
-            } else if (!have) {  // insert p, keeping dig ascending
-                uint32_t j = r++;
-                while (j > 0 && dig[j - 1] > (uint32_t)p) {
-                    dig[j] = dig[j - 1];
-                    --j;
-                }
-                dig[j] = (uint32_t)p;
-            }
-        }
-        if (r == 0) dig[r++] = 0;  // all keys equal: one pass (identity order)
-        const uint32_t skip = r > max_passes ? r - max_passes : 0u;  // D bytes below the prefix
-        P.npass = r - skip;
-        P.pmask = 0;
-        for (uint32_t j = 0; j < P.npass; ++j) {
-            P.digit[j] = dig[skip + j];
-            P.src[j] = (j == 0) ? 0u : P.dst[j - 1];
-            P.dst[j] = ((P.npass - 1 - j) % 2 == 0) ? 1u : 2u;  // the last pass writes buffer A
-            P.pmask |= 0xFFull << (8 * dig[skip + j]);
-        }
-        P.fix = skip ? 1u : 0u;
-        P.nr = 0;
-        if (skip)
-            for (int d = 0; d < 8; ++d)
-                if (!((P.pmask >> (8 * d)) & 1u) && (varies[d] || differs[d])) P.rdig[P.nr++] = (uint32_t)d;
-    }
+    if (b == 0) plan_digits(bm->bmax, bm->bnmin, bm->invalid, n, max_passes, bm->plan);
 }
 
 __device__ __forceinline__ const uint64_t* pass_src_keys(const SortPlan& P, uint32_t j, const SortBuffers& sb) {
@@ -233,38 +189,6 @@ __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t j, uint32_t n, Sort
     }
 }
 
-// Rank within the warp of kItems x 32 elements visited in index order (k, then lane);
-// dig = 256 marks an empty slot. The lanes holding the same digit are found with nine
-// ballots (validity + 8 bits); the lowest of them adds the group's size to the warp's
-// counter for that digit (whist) with one shared-memory atomic, whose old value is the
-// group's base. The __syncwarp orders the atomics of consecutive items, so equal digits
-// keep index order (stability); the bases are gathered only after the loop. On return
-// rank[k] counts the warp's earlier elements with the same digit, and whist[d] the
-// warp's elements with digit d (added to its previous contents).
-__device__ __forceinline__ void warp_digit_ranks(const uint32_t (&dig)[kItems], uint32_t (&rank)[kItems],
-                                                 uint32_t* whist) {
-    const uint32_t lt = lanemask_lt();
-    uint32_t lower[kItems], old[kItems], lead[kItems];
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const uint32_t d = dig[k];
-        uint32_t peers = __ballot_sync(0xffffffffu, d < 256u);
-        if (d >= 256u) peers = ~peers;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? m : ~m;
-        }
-        lead[k] = (uint32_t)(__ffs(peers) - 1);
-        lower[k] = __popc(peers & lt);
-        old[k] = 0;
-        if (lower[k] == 0 && d < 256u) old[k] = atomicAdd(&whist[d], (uint32_t)__popc(peers));
-        __syncwarp();
-    }
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) rank[k] = __shfl_sync(0xffffffffu, old[k], (int)lead[k]) + lower[k];
-}
-
 __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t n, SortBuffers sb,
                                                            BatchMeta* bm, uint32_t* err) {
     const SortPlan& P = bm->plan;
@@ -301,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
         pay[k] = v ? src_p[tbase + li] : 0u;
         dig[k] = v ? (uint32_t)((key[k] >> shift) & 255u) : 256u;
     }
-    warp_digit_ranks(dig, rank, s_whist[warp]);
+    warp_digit_ranks<kItems, 8>(dig, rank, s_whist[warp]);
     __syncthreads();
     // Thread tid owns digit tid: tile total and per-warp exclusive prefix.
     uint32_t total = 0;
@@ -412,7 +336,7 @@ __device__ void cta_segment_lsd(uint32_t s, uint32_t e, const SortPlan& P, const
                 pay[k] = v ? src_p[i] : 0u;
                 dig[k] = v ? (uint32_t)((key[k] >> shift) & 255u) : 256u;
             }
-            warp_digit_ranks(dig, rank, s_whist[warp]);
+            warp_digit_ranks<kItems, 8>(dig, rank, s_whist[warp]);
             __syncthreads();
             uint32_t total = 0;  // thread tid owns digit tid: per-warp exclusive prefix
 #pragma unroll

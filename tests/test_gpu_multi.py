@@ -1,0 +1,159 @@
+"""Batching form (pi_multi_execute) against one oracle per index, bit for bit.
+
+A set of independent indices of uneven sizes (p = 1/4) gets one batch each per call, of
+uneven lengths: searches (half hits), inserts of new and of existing keys, deletes, a
+few invalid queries and a hot key. Every result and every index's final state (live
+pairs and built levels) must equal its oracle's. The class tables cover every kernel
+variant (8, 16 and 32 warps per index; 4- and 8-bit radix digits), and the indices
+stay usable by the single-index batch path before and after.
+"""
+import numpy as np
+import pytest
+
+from paper_1601_00159_gb300 import workloads as wl
+from tests.parity import assert_results_equal, assert_state_equal, make_index, results_np, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TABLES = {
+    "default": None,
+    "a": [(12, 8, 4), (15, 16, 8), (32, 32, 4)],
+    "b": [(12, 8, 8), (15, 16, 4), (32, 32, 8)],
+}
+
+
+@pytest.fixture(scope="module")
+def orc_mod():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    from paper_1601_00159_gb300 import build, load_library
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    return load_library()
+
+
+def log_uniform(seed, tag, count, lo_log, hi_log):
+    u = wl.uniform01(wl.stream_seed(seed, tag), 0, count)
+    return np.floor(2.0 ** (lo_log + u * (hi_log - lo_log))).astype(np.int64)
+
+
+def make_batch(seed, keys, q):
+    s = wl.stream_seed(seed, 77)
+    kind = wl.bounded(s, 0, q, 20)
+    hit = keys[wl.bounded(s, q, q, max(len(keys), 1))] if len(keys) else wl.u64_stream(s, q, q) >> np.uint64(1)
+    miss = wl.u64_stream(s, 2 * q, q) >> np.uint64(1)
+    bkeys = np.where(kind % 2 == 0, hit, miss)
+    bkeys = np.where(kind == 19, hit[0], bkeys)  # a hot key
+    ops = np.where(kind < 12, 0, np.where(kind < 16, 1, 2)).astype(np.uint8)
+    ops = np.where(kind == 13, np.uint8(5), ops)  # invalid op code
+    bkeys = np.where(kind == 15, wl.RESERVED_KEY, bkeys)  # the reserved key
+    return wl.Batch(ops.astype(np.uint8), bkeys.astype(np.uint64), wl.u64_stream(s, 3 * q, q))
+
+
+def build_set(orc_mod, seed, count, lo_log, hi_log, big=None):
+    sizes = log_uniform(seed, 1, count, lo_log, hi_log)
+    if big:
+        sizes[0] = big
+    idxs, orcs, keysets = [], [], []
+    for i, n in enumerate(sizes):
+        keys = wl.distinct_keys(seed * 1000 + i, np.arange(int(n)))
+        vals = wl.splitmix64(keys)
+        hs = int(wl.stream_seed(seed, 500 + i))
+        idxs.append(make_index(keys, vals, 0.25, hs))
+        orcs.append(orc_mod.Oracle(keys, vals, 0.25, hs))
+        keysets.append(keys)
+    return idxs, orcs, keysets
+
+
+def run_rounds(ms, idxs, orcs, keysets, seed, rounds, qlo_log, qhi_log, skip=()):
+    import torch
+    for r in range(rounds):
+        qs = log_uniform(seed, 100 + r, len(idxs), qlo_log, qhi_log)
+        batches, host = [], []
+        for i, q in enumerate(qs):
+            if i in skip:
+                continue
+            b = make_batch(seed * 7919 + r * 131 + i, keysets[i], int(q))
+            res = torch.full((len(b.ops), 2), -1, dtype=torch.int64, device="cuda")
+            batches.append((i, to_dev(b.ops, torch.uint8), to_dev(b.keys, torch.int64),
+                            to_dev(b.vals, torch.int64), res))
+            host.append((i, b, res))
+        ms.execute(batches)
+        torch.cuda.synchronize()
+        for i, b, res in host:
+            exp = orcs[i].execute(b.ops, b.keys, b.vals)
+            assert_results_equal(results_np(res), exp, f"round {r} index {i}")
+
+
+@pytest.mark.parametrize("table", sorted(TABLES))
+def test_multi_matches_oracle_per_index(orc_mod, table):
+    from paper_1601_00159_gb300 import MultiSet
+    seed = 3 + len(table)
+    idxs, orcs, keysets = build_set(orc_mod, seed, 20, 6, 16, big=(1 << 18) + 5)
+    ms = MultiSet(idxs, TABLES[table])
+    run_rounds(ms, idxs, orcs, keysets, seed, 3, 0, 12)
+    for i, (ix, orc) in enumerate(zip(idxs, orcs)):
+        assert_state_equal(ix, orc, f"index {i}")
+    ms.close()
+    for ix, orc in zip(idxs, orcs):
+        ix.close()
+        orc.close()
+
+
+def test_multi_mixed_with_plain_path_and_subsets(orc_mod):
+    """Rounds that leave some indices out, empty batches, the single-index path on the
+    same indices in between, and an index whose storage must grow."""
+    import torch
+    from paper_1601_00159_gb300 import MultiSet
+    from tests.parity import run_batch
+    seed = 17
+    idxs, orcs, keysets = build_set(orc_mod, seed, 9, 4, 13)
+    ms = MultiSet(idxs)
+    run_rounds(ms, idxs, orcs, keysets, seed, 2, 0, 11, skip=(2, 5))
+    for i in (0, 2, 7):  # the plain path after the batching form
+        b = make_batch(900 + i, keysets[i], 3000)
+        assert_results_equal(run_batch(idxs[i], b), orcs[i].execute(b.ops, b.keys, b.vals), f"plain {i}")
+    # an empty batch for index 1 and many new keys for index 3 (its storage grows)
+    empty = (1, torch.zeros(0, dtype=torch.uint8, device="cuda"), torch.zeros(0, dtype=torch.int64, device="cuda"),
+             torch.zeros(0, dtype=torch.int64, device="cuda"), torch.zeros((0, 2), dtype=torch.int64, device="cuda"))
+    q = 20000
+    s = wl.stream_seed(seed, 3)
+    ins = wl.Batch(np.ones(q, np.uint8), wl.u64_stream(s, 0, q) >> np.uint64(1), wl.u64_stream(s, q, q))
+    res = torch.full((q, 2), -1, dtype=torch.int64, device="cuda")
+    ms.execute([empty, (3, to_dev(ins.ops, torch.uint8), to_dev(ins.keys, torch.int64),
+                        to_dev(ins.vals, torch.int64), res)])
+    torch.cuda.synchronize()
+    assert_results_equal(results_np(res), orcs[3].execute(ins.ops, ins.keys, ins.vals), "growth")
+    run_rounds(ms, idxs, orcs, keysets, seed + 1, 2, 0, 11)
+    for i, (ix, orc) in enumerate(zip(idxs, orcs)):
+        assert_state_equal(ix, orc, f"index {i}")
+    ms.close()
+
+
+def test_multi_rejects_bad_sets_and_batches():
+    import torch
+    from paper_1601_00159_gb300 import MultiSet, PiError, PI_ERR_INVALID_ARG
+    keys = wl.distinct_keys(5, np.arange(100))
+    a = make_index(keys, keys, 0.25, 1)
+    with pytest.raises(PiError) as e:
+        MultiSet([a, a])
+    assert e.value.code == PI_ERR_INVALID_ARG
+    with pytest.raises(PiError):
+        MultiSet([a], classes=[(12, 12, 8)])
+    ms = MultiSet([a])
+    z = torch.zeros(4, dtype=torch.int64, device="cuda")
+    ops = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    r = torch.zeros((4, 2), dtype=torch.int64, device="cuda")
+    with pytest.raises(PiError):
+        ms.execute([(1, ops, z, z, r)])  # no such index
+    with pytest.raises(PiError):
+        ms.execute([(0, ops, z, z, r), (0, ops, z, z, r)])  # twice in one call
+    ms.close()
+    a.close()
