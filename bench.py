@@ -49,7 +49,21 @@ WORKLOADS = {
                      "50% insert of new uniform keys, rebuild after each batch"),
     "tiny": dict(fn=wl.tiny, n=1 << 16, q=1 << 14,
                  desc="plain PI, tiny: 2^16 uint64 keys, p=1/2, one batch of 2^14 searches (half hits)"),
+    "batching": dict(fn=wl.batching, n=None, q=None,
+                     desc="batching: 256 independent indices, sizes log-uniform in [2^10,2^20] uint64 keys "
+                          "(p=1/4), each with its own batch of log-uniform [2^8,2^16] queries, 80% search "
+                          "(half hits) / 20% insert of new uniform keys; one CUDA-graph launch per step"),
 }
+TUNING = os.path.join(ROOT, "paper_1601_00159_gb300", "multi_tuning.json")
+
+
+def tuned_classes():
+    """The size-class table the autotuner wrote, or None (built-in table)."""
+    try:
+        with open(TUNING) as f:
+            return [tuple(c) for c in json.load(f)["classes"]]
+    except Exception:
+        return None
 
 
 def writer_source_digest():
@@ -201,9 +215,44 @@ def cpu_baseline(w, batch0, budget_s: float = 20.0):
                       f"({elapsed:.1f} s timed; oracle build {build_s:.1f} s untimed)"}
 
 
+def run_reference_batching(args):
+    """The oracle on the batching workload: the first indices (bounded sample, built
+    untimed), each step applying one round of their batches."""
+    import oracle
+    oracle.build()
+    spec = WORKLOADS["batching"]
+    w = wl.batching()
+    take = 8
+    orcs = [oracle.Oracle(w.keys[i], w.vals[i], w.promote_p, w.hash_seeds[i]) for i in range(take)]
+    rounds = [w.batches(r)[:take] for r in range(2)]
+    for s_ in range(args.warmup):
+        for o, b in zip(orcs, rounds[s_ % 2]):
+            o.execute(b.ops, b.keys, b.vals)
+    t = time.perf_counter()
+    done = 0
+    for s_ in range(args.steps):
+        for o, b in zip(orcs, rounds[(args.warmup + s_) % 2]):
+            o.execute(b.ops, b.keys, b.vals)
+            done += len(b)
+    el = time.perf_counter() - t
+    v = done / el / 1e6
+    for o in orcs:
+        o.close()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": "batching", "desc": spec["desc"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the batches of the first {take} of {len(w.keys)} indices per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
+    if args.workload == "batching":
+        return run_reference_batching(args)
     spec = WORKLOADS[args.workload]
     w = spec["fn"]()
     batches = list(w.batches()) if callable(w.batches) else list(w.batches)
@@ -228,6 +277,186 @@ def run_reference(args, ws, rank):
                              "sample": f"{per_step} queries of each batch, applied in arrival order"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_batching(args, ws, rank, local):
+    """Config 4: one pi_multi_execute per step over every index's batch, beside the same
+    batches run by looping the single-index path over the indices."""
+    import torch
+    from paper_1601_00159_gb300 import Index, MultiSet, build, load_library
+    build.build()
+    load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = WORKLOADS["batching"]
+    t_gen = time.time()
+    w = wl.batching(seed=4 + rank)
+    rounds = 4  # distinct rounds of batches, cycled
+    host_rounds = [w.batches(r) for r in range(rounds)]
+    gen_s = time.time() - t_gen
+    count = len(w.keys)
+    qs = [len(b) for b in host_rounds[0]]
+    qtot = int(sum(qs))
+    loop_steps = 2
+    total_rounds = args.warmup + args.steps + 2 + loop_steps + 2 + min(args.steps, 50) + 4
+    idxs = []
+    t = time.time()
+    for i in range(count):
+        k = torch.from_numpy(w.keys[i].view(np.int64)).to(dev)
+        v = torch.from_numpy(w.vals[i].view(np.int64)).to(dev)
+        cap = len(w.keys[i]) + qs[i] * total_rounds // 4 + 4096
+        idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], {"storage_capacity": cap}))
+    create_s = time.time() - t
+    classes = tuned_classes()
+    ms = MultiSet(idxs, classes)
+
+    def pack(rnd):
+        ops = np.concatenate([b.ops for b in rnd])
+        keys = np.concatenate([b.keys for b in rnd]).view(np.int64)
+        vals = np.concatenate([b.vals for b in rnd]).view(np.int64)
+        return ops, keys, vals
+
+    offs = np.concatenate([[0], np.cumsum(qs)])
+    dev_rounds = []
+    for rnd in host_rounds:
+        o, k, v = pack(rnd)
+        dev_rounds.append((torch.from_numpy(o).to(dev), torch.from_numpy(k).to(dev), torch.from_numpy(v).to(dev)))
+    results = torch.empty((qtot, 2), dtype=torch.int64, device=dev)
+
+    def descs(o, k, v, res):
+        return [(i, o[offs[i]:offs[i + 1]], k[offs[i]:offs[i + 1]], v[offs[i]:offs[i + 1]],
+                 res[offs[i]:offs[i + 1]]) for i in range(count)]
+
+    stream = torch.cuda.current_stream()
+    step_descs = [descs(*dr, results) for dr in dev_rounds]
+    for s_ in range(args.warmup):
+        ms.execute(step_descs[s_ % rounds])
+    torch.cuda.synchronize()
+    launches_per_call = ms.kernels_per_call()
+    barrier(ws)
+    with ClockSampler(local) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for s_ in range(args.steps):
+            ms.execute(step_descs[(args.warmup + s_) % rounds])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    ms_total = reduce_max(ev0.elapsed_time(ev1), ws)
+    ms_step = ms_total / args.steps
+    value = ws * qtot * args.steps / (ms_total * 1e-3) / 1e6
+
+    # the same batches through the single-index path, one index after another
+    for s_ in range(2):
+        for (i, o, k, v, r) in step_descs[s_ % rounds]:
+            idxs[i].execute(o, k, v, r)
+    torch.cuda.synchronize()
+    l0 = [ix.info()["kernel_launches"] for ix in idxs]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s_ in range(loop_steps):
+        for (i, o, k, v, r) in step_descs[(s_ + 2) % rounds]:
+            idxs[i].execute(o, k, v, r)
+    for ix in idxs:
+        ix.flush(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = reduce_max(e0.elapsed_time(e1), ws) / loop_steps
+    loop_launches = (sum(ix.info()["kernel_launches"] for ix in idxs) - sum(l0)) // loop_steps
+    loop_value = ws * qtot / (loop_ms * 1e-3) / 1e6
+
+    # e2e: each step copies its packed round from pinned host memory and reads the results back
+    hp = []
+    for rnd in host_rounds:
+        o, k, v = pack(rnd)
+        hp.append((torch.from_numpy(o).pin_memory(), torch.from_numpy(k.copy()).pin_memory(),
+                   torch.from_numpy(v.copy()).pin_memory()))
+    hres = torch.empty((qtot, 2), dtype=torch.int64).pin_memory()
+    dbuf = [torch.empty_like(dev_rounds[0][j]) for j in range(3)]
+    e2e_descs = descs(dbuf[0], dbuf[1], dbuf[2], results)
+    e2e_steps = max(3, min(args.steps, 50))
+    for s_ in range(2):
+        ms.execute(e2e_descs)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s_ in range(e2e_steps):
+        src = hp[s_ % rounds]
+        for j in range(3):
+            dbuf[j].copy_(src[j], non_blocking=True)
+        ms.execute(e2e_descs)
+        hres.copy_(results, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(e0.elapsed_time(e1), ws) / e2e_steps
+    e2e_value = ws * qtot / (e2e_ms * 1e-3) / 1e6
+
+    # algorithmic bytes of one step (every index: batch I/O, storage accesses, merge of the
+    # new nodes, rebuild), after the timed steps
+    hbm, peak_kind = measured_peaks()
+    infos = [ix.info() for ix in idxs]
+    ins = sum(int((b.ops == wl.OP_INSERT).sum()) for b in host_rounds[0])
+    nodes = sum(inf["size"] for inf in infos)
+    entries = sum(sum(inf["level_size"][2:]) for inf in infos)
+    io = qtot * (1 + 8 + 16) + ins * 8
+    store = qtot * 32 + ins * 96
+    merge = 2 * 17 * nodes
+    rebuild = 9 * nodes + 12 * entries
+    ab = io + store + merge + rebuild
+    achieved = ab / (ms_step * 1e-3) / 1e9
+    for ix in idxs:
+        assert ix.status() == 0, "device error status"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "batching", "desc": spec["desc"], "indices": count, "queries_per_step": qtot,
+                   "keys_total": int(sum(len(k) for k in w.keys)), "classes": classes or "built-in",
+                   "distinct_rounds_cycled": rounds, "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "l2_flush": "none: the indices (0.7 GB of storage) and cycled rounds exceed L2"},
+        "roofline": {"bound": "hbm", "kernel": "k_multi", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_source": peak_kind, "traffic": None,
+                     "launches_per_step": launches_per_call, "ms_per_launch": ms_step,
+                     "algorithmic_bytes_per_launch": ab,
+                     "bytes_model": "per index: Q*25 + Q_ins*8 I/O, Q*32 + Q_ins*96 storage, "
+                                    "2*17 B per node merge, 9 B per node + 12 B per index entry rebuild"},
+        "plain_loop": {"value": loop_value, "unit": UNIT, "ms_per_step": loop_ms,
+                       "gpu_launches_per_step": loop_launches,
+                       "note": "the same batches, pi_execute_batch index after index on one stream"},
+        "speedup_vs_plain_loop": value / loop_value,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": qtot * 17, "d2h_bytes_per_step": qtot * 16,
+                "steps": e2e_steps},
+        "gpu_launches": launches_per_call * args.steps,
+        "clocks": clk.summary(),
+        "index": {"nodes": nodes, "index_entries": entries, "create_s": create_s, "gen_s": gen_s},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_multi(w, host_rounds[0], args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ms.close()
+    for ix in idxs:
+        ix.close()
+
+
+def cpu_baseline_multi(w, rnd, budget_s: float = 20.0):
+    """The oracle on a bounded sample of the batching workload: indices in order, each
+    built (untimed) and then given its batch (timed), until the budget is spent."""
+    import oracle
+    oracle.build()
+    done, elapsed, used = 0, 0.0, 0
+    for i, b in enumerate(rnd):
+        if elapsed >= budget_s:
+            break
+        orc = oracle.Oracle(w.keys[i], w.vals[i], w.promote_p, w.hash_seeds[i])
+        t = time.perf_counter()
+        orc.execute(b.ops, b.keys, b.vals)
+        elapsed += time.perf_counter() - t
+        done += len(b)
+        used += 1
+        orc.close()
+    return {"value": done / elapsed / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the batches of the first {used} of {len(rnd)} indices ({done} queries, "
+                      f"{elapsed:.1f} s timed; builds untimed)"}
 
 
 def run_ours(args, ws, rank, local):
@@ -391,6 +620,8 @@ def main():
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batching":
+        run_batching(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

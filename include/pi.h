@@ -292,6 +292,10 @@ typedef struct {
  */
 int pi_multi_execute(pi_multi_t* set, const pi_multi_batch_t* batches_host, uint32_t nb, pi_stream_t stream);
 
+/* Kernels one pi_multi_execute call launches (one persistent kernel per size class in
+ * use when its graph was built); 0 before the first call or for NULL. */
+uint64_t pi_multi_kernels_per_call(const pi_multi_t* set);
+
 /* Releases the set's own device and host memory (not the indices). NULL-safe. */
 void pi_multi_destroy(pi_multi_t* set);
 

@@ -22,7 +22,7 @@ PI_MAX_KEYS = (1 << 30) - 2
 EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
             "pi_last_error", "pi_status", "pi_info", "pi_export", "pi_export_level", "pi_profile",
             "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush",
-            "pi_multi_create", "pi_multi_execute", "pi_multi_destroy"]
+            "pi_multi_create", "pi_multi_execute", "pi_multi_destroy", "pi_multi_kernels_per_call"]
 PI_MULTI_MAX_CLASSES = 4
 PI_MULTI_MAX_BATCH = 1 << 20
 PI_NOALLOC_MAX_BATCH = 1 << 16
@@ -123,6 +123,8 @@ def load_library(path: str = LIB_PATH):
     lib.pi_multi_create.argtypes = [ctypes.POINTER(vp), ctypes.c_uint32, ctypes.POINTER(PiMultiConfig)]
     lib.pi_multi_execute.restype = i32
     lib.pi_multi_execute.argtypes = [vp, ctypes.POINTER(PiMultiBatch), ctypes.c_uint32, vp]
+    lib.pi_multi_kernels_per_call.restype = u64
+    lib.pi_multi_kernels_per_call.argtypes = [vp]
     lib.pi_multi_destroy.restype = None
     lib.pi_multi_destroy.argtypes = [vp]
     _lib = lib
@@ -304,6 +306,9 @@ class MultiSet:
                 raise ValueError("batch arrays differ in length")
             arr[i] = PiMultiBatch(ix, 0, ops.data_ptr(), keys.data_ptr(), vals.data_ptr(), n, res.data_ptr())
         _chk(self.lib.pi_multi_execute(self._h, arr, len(batches), _stream_handle(stream)), "pi_multi_execute")
+
+    def kernels_per_call(self) -> int:
+        return int(self.lib.pi_multi_kernels_per_call(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

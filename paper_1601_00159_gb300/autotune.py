@@ -1,0 +1,92 @@
+"""Autotuner of the batching form's kernel variants (run on the GPU that will serve).
+
+The batching form (pi_multi_execute) runs each size class of indices with its own
+persistent kernel. This script times every variant -- 8, 16 or 32 warps per index, 4- or
+8-bit radix digits -- on the indices of each class of the batching workload and writes
+the fastest per class to multi_tuning.json beside it, which bench.py and MultiSet
+callers pass to pi_multi_create.
+
+    python -m paper_1601_00159_gb300.autotune [--calls 8]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "multi_tuning.json")
+BOUNDS = [14, 17, 32]  # class upper bounds (log2 of the storage size)
+VARIANTS = [(w, b) for w in (8, 16, 32) for b in (4, 8)]
+
+
+def main():
+    import torch
+    from . import Index, MultiSet, build, load_library
+    from . import workloads as wl
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--calls", type=int, default=8)
+    ap.add_argument("--out", default=OUT)
+    args = ap.parse_args()
+    build.build()
+    load_library()
+    dev = torch.device("cuda")
+    w = wl.batching()
+    rnd = w.batches(0)
+    sizes = np.array([len(k) for k in w.keys])
+    lg = np.ceil(np.log2(np.maximum(sizes, 1))).astype(int)
+    chosen, table = [], {}
+    lo = -1
+    for c, hi in enumerate(BOUNDS):
+        members = [i for i in range(len(sizes)) if lo < lg[i] <= hi]
+        lo = hi
+        if not members:
+            chosen.append((hi, 16, 8))
+            continue
+        batches = []
+        for i in members:
+            b = rnd[i]
+            batches.append((torch.from_numpy(b.ops).to(dev), torch.from_numpy(b.keys.view(np.int64)).to(dev),
+                            torch.from_numpy(b.vals.view(np.int64)).to(dev),
+                            torch.empty((len(b), 2), dtype=torch.int64, device=dev)))
+        timings = {}
+        for (wp, bits) in VARIANTS:
+            idxs = []
+            for i in members:
+                k = torch.from_numpy(w.keys[i].view(np.int64)).to(dev)
+                v = torch.from_numpy(w.vals[i].view(np.int64)).to(dev)
+                cap = len(w.keys[i]) + len(rnd[i]) * (args.calls + 4)
+                idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], {"storage_capacity": cap}))
+            ms = MultiSet(idxs, [(32, wp, bits)])
+            desc = [(j, *batches[j]) for j in range(len(members))]
+            for _ in range(2):
+                ms.execute(desc)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.calls):
+                ms.execute(desc)
+            e1.record()
+            torch.cuda.synchronize()
+            timings[f"{wp}x{bits}"] = e0.elapsed_time(e1) / args.calls
+            ms.close()
+            for ix in idxs:
+                ix.close()
+        best = min(timings, key=timings.get)
+        wp, bits = (int(x) for x in best.split("x"))
+        chosen.append((hi, wp, bits))
+        table[f"class{c} (log2 size <= {hi}, {len(members)} indices)"] = timings
+        print(f"class {c}: {len(members)} indices, ms per call {timings} -> {best}", flush=True)
+    out = {"classes": chosen, "ms_per_call": table, "device": torch.cuda.get_device_name(),
+           "workload": "batching (seed 4): indices of each class, their round-0 batches",
+           "calls_timed": args.calls, "date": time.strftime("%Y-%m-%d")}
+    with open(args.out, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out["classes"]))
+
+
+if __name__ == "__main__":
+    main()

@@ -1381,6 +1381,8 @@ int pi_multi_execute(pi_multi_t* mx, const pi_multi_batch_t* b, uint32_t nb, pi_
     return PI_OK;
 }
 
+uint64_t pi_multi_kernels_per_call(const pi_multi_t* mx) { return mx ? mx->launches : 0; }
+
 void pi_multi_destroy(pi_multi_t* mx) { multi_destroy(mx); }
 
 }  // extern "C"

@@ -257,3 +257,45 @@ def random_small(seed: int, n: int, q: int, key_range: int, p: float = 0.5,
         bkeys = np.where(bad & (which == 1), RESERVED_KEY, bkeys)
         out.append(Batch(ops, bkeys, bvals))
     return Workload("random_small", keys, vals, p, int(stream_seed(seed, 8)), out, True)
+
+
+@dataclasses.dataclass
+class MultiWorkload:
+    name: str
+    keys: list             # per index: initial keys (uint64)
+    vals: list             # per index: initial values (uint64)
+    promote_p: float
+    hash_seeds: list       # per index
+    batch_sizes: np.ndarray
+    batches: object        # callable(round) -> list[Batch], one per index
+
+
+def batching(seed: int = 4, count: int = 256, lo_log: float = 10, hi_log: float = 20,
+             qlo_log: float = 8, qhi_log: float = 16) -> MultiWorkload:
+    """Batching: `count` independent indices with sizes log-uniform in [2^lo, 2^hi]
+    (distinct uniform keys in [0, 2^63), value = splitmix64(key), p = 1/4); each has its
+    own batch, of a size log-uniform in [2^qlo, 2^qhi] fixed per index, with 80% search
+    (half hits over the initial keys, half misses) and 20% insert of new uniform keys."""
+    s = stream_seed(seed, 40)
+    sizes = np.floor(2.0 ** (lo_log + uniform01(s, 0, count) * (hi_log - lo_log))).astype(np.int64)
+    qs = np.floor(2.0 ** (qlo_log + uniform01(s, count, count) * (qhi_log - qlo_log))).astype(np.int64)
+    keys = [distinct_keys(seed * 100003 + i, np.arange(int(n))) for i, n in enumerate(sizes)]
+    vals = [splitmix64(k) for k in keys]
+    seeds = [int(stream_seed(seed, 1000 + i)) for i in range(count)]
+
+    def batches(r: int):
+        out = []
+        for i in range(count):
+            q, n = int(qs[i]), int(sizes[i])
+            sb = stream_seed(seed * 7 + i, 10_000 + r)
+            u = uniform01(sb, 0, q)
+            ops = np.where(u < 0.2, OP_INSERT, OP_SEARCH).astype(np.uint8)
+            hit = keys[i][bounded(sb, q, q, n)]
+            new = distinct_keys(seed * 100003 + i, np.uint64(1 << 40) + np.uint64(r) * np.uint64(1 << 20)
+                                + np.arange(q, dtype=np.uint64))
+            half = bounded(sb, 2 * q, q, 2) == 0
+            bkeys = np.where(ops == OP_INSERT, new, np.where(half, hit, new[::-1]))
+            out.append(Batch(ops, bkeys.astype(np.uint64), u64_stream(sb, 3 * q, q)))
+        return out
+
+    return MultiWorkload("batching", keys, vals, 0.25, seeds, qs, batches)
