@@ -299,6 +299,78 @@ uint64_t pi_multi_kernels_per_call(const pi_multi_t* set);
 /* Releases the set's own device and host memory (not the indices). NULL-safe. */
 void pi_multi_destroy(pi_multi_t* set);
 
+/*
+ * ---------------------------------------------------------------------------------
+ * Serving form: continuous batching of variable-size requests against one resident
+ * index. Clients submit requests (host arrays, copied into a pinned ring at submit: the
+ * ring's size is the admission budget, and submit waits while it is full). A dispatcher
+ * thread coalesces the queued requests, in arrival order, into batches of at most
+ * max_batch queries and keeps up to `slots` batches in flight: batch k+1's inputs are
+ * copied to the device while batch k's kernels run, and batch k's results are copied
+ * back while batch k+1's kernels run. A batch is Algorithm 1 on the concatenated
+ * requests, so every query's result equals the result of running the requests one by
+ * one in arrival order (Section 4.2); coalescing changes no result. This answers the
+ * latency concern the paper raises for batching (Section 3.2, right after
+ * Algorithm 1, and Section 6's batch-size experiments) with a bounded batch and
+ * overlapping stages; the serving loop itself is this library's extension.
+ * While a server exists, its index must not be used by any other call.
+ */
+typedef struct pi_server pi_server_t;
+
+typedef struct {
+    uint32_t struct_size;    /* sizeof(pi_server_config_t) */
+    uint32_t max_batch;      /* queries per coalesced batch, 1..PI_MAX_BATCH (default 2^20) */
+    uint32_t slots;          /* batches in flight, 2..8 (default 3) */
+    uint32_t reserved;
+    uint64_t ring_queries;   /* pinned staging capacity in queries, >= max_batch
+                                (default 8 x max_batch) */
+} pi_server_config_t;
+
+/* Starts a server on `idx` (current device). cfg may be NULL. NULL on error
+ * (pi_last_error: PI_ERR_INVALID_ARG, PI_ERR_OOM, PI_ERR_CUDA). */
+pi_server_t* pi_server_create(pi_index_t* idx, const pi_server_config_t* cfg);
+
+/* Queues one request of n (1..max_batch) queries: host arrays as for pi_execute_batch,
+ * copied before the call returns. Waits while the ring has no room. *ticket_out gets
+ * the request's ticket (consecutive from 1). Returns the server's sticky error, if any. */
+int pi_server_submit(pi_server_t* srv, const uint8_t* ops, const uint64_t* keys, const uint64_t* values,
+                     uint32_t n, uint64_t* ticket_out);
+
+/* Waits for the oldest uncollected request, which must be `ticket` (tickets are
+ * collected in submission order), copies its n results to results_out (host, may be
+ * NULL) and its latency in seconds (submission to results in host memory) to
+ * *latency_s (may be NULL), and frees its ring space. */
+int pi_server_wait(pi_server_t* srv, uint64_t ticket, pi_result_t* results_out, double* latency_s);
+
+typedef struct {
+    uint64_t requests;        /* completed since the last reset */
+    uint64_t queries;
+    uint64_t batches;
+    uint32_t max_in_flight;   /* most batches on the GPU at once */
+    uint32_t reserved;
+    double p50_s, p99_s, max_s;  /* request latency */
+    double mean_batch;        /* queries per batch */
+} pi_server_stats_t;
+
+/* Statistics of the requests completed since the last reset (reset != 0 starts anew). */
+int pi_server_stats(pi_server_t* srv, pi_server_stats_t* out, int reset);
+
+/*
+ * pi_server_replay -- load generator: submits nreq requests, request i being the next
+ * sizes[i] queries of the host arrays, each at arrival_s[i] seconds after the call
+ * starts (non-decreasing), collects them in order on a second thread, and returns when
+ * all are done. A request's latency runs from its scheduled arrival (so a late submit
+ * counts against the server) to its results in host memory; latency_s_out[nreq] and
+ * results_out[sum of sizes] may be NULL.
+ */
+int pi_server_replay(pi_server_t* srv, const uint8_t* ops, const uint64_t* keys, const uint64_t* values,
+                     const uint32_t* sizes, const double* arrival_s, uint32_t nreq, pi_result_t* results_out,
+                     double* latency_s_out);
+
+/* Finishes the queued requests, stops the dispatcher and frees the server (not the
+ * index). NULL-safe. */
+void pi_server_destroy(pi_server_t* srv);
+
 #ifdef __cplusplus
 }
 #endif

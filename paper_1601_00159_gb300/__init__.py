@@ -22,7 +22,9 @@ PI_MAX_KEYS = (1 << 30) - 2
 EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
             "pi_last_error", "pi_status", "pi_info", "pi_export", "pi_export_level", "pi_profile",
             "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush",
-            "pi_multi_create", "pi_multi_execute", "pi_multi_destroy", "pi_multi_kernels_per_call"]
+            "pi_multi_create", "pi_multi_execute", "pi_multi_destroy", "pi_multi_kernels_per_call",
+            "pi_server_create", "pi_server_submit", "pi_server_wait", "pi_server_stats", "pi_server_replay",
+            "pi_server_destroy"]
 PI_MULTI_MAX_CLASSES = 4
 PI_MULTI_MAX_BATCH = 1 << 20
 PI_NOALLOC_MAX_BATCH = 1 << 16
@@ -63,6 +65,17 @@ class PiMultiBatch(ctypes.Structure):
     _fields_ = [("index", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("ops", ctypes.c_void_p),
                 ("keys", ctypes.c_void_p), ("values", ctypes.c_void_p), ("n", ctypes.c_uint64),
                 ("results", ctypes.c_void_p)]
+
+
+class PiServerConfig(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("max_batch", ctypes.c_uint32), ("slots", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("ring_queries", ctypes.c_uint64)]
+
+
+class PiServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("queries", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("max_in_flight", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("p50_s", ctypes.c_double),
+                ("p99_s", ctypes.c_double), ("max_s", ctypes.c_double), ("mean_batch", ctypes.c_double)]
 
 
 class PiInfo(ctypes.Structure):
@@ -125,6 +138,18 @@ def load_library(path: str = LIB_PATH):
     lib.pi_multi_execute.argtypes = [vp, ctypes.POINTER(PiMultiBatch), ctypes.c_uint32, vp]
     lib.pi_multi_kernels_per_call.restype = u64
     lib.pi_multi_kernels_per_call.argtypes = [vp]
+    lib.pi_server_create.restype = vp
+    lib.pi_server_create.argtypes = [vp, ctypes.POINTER(PiServerConfig)]
+    lib.pi_server_submit.restype = i32
+    lib.pi_server_submit.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.POINTER(u64)]
+    lib.pi_server_wait.restype = i32
+    lib.pi_server_wait.argtypes = [vp, u64, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.pi_server_stats.restype = i32
+    lib.pi_server_stats.argtypes = [vp, ctypes.POINTER(PiServerStats), i32]
+    lib.pi_server_replay.restype = i32
+    lib.pi_server_replay.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_uint32, vp, vp]
+    lib.pi_server_destroy.restype = None
+    lib.pi_server_destroy.argtypes = [vp]
     lib.pi_multi_destroy.restype = None
     lib.pi_multi_destroy.argtypes = [vp]
     _lib = lib
@@ -313,6 +338,82 @@ class MultiSet:
     def close(self):
         if getattr(self, "_h", None):
             self.lib.pi_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server over one index (pi_server_*). Host numpy arrays in and
+    out; results come back as int64 [n, 2] (value bits, status)."""
+
+    def __init__(self, index, max_batch: int = 0, slots: int = 0, ring_queries: int = 0):
+        lib = load_library()
+        cfg = PiServerConfig(ctypes.sizeof(PiServerConfig), max_batch, slots, 0, ring_queries)
+        h = lib.pi_server_create(index._h, ctypes.byref(cfg))
+        if not h:
+            raise PiError(lib.pi_last_error(), "pi_server_create")
+        self._h = ctypes.c_void_p(h)
+        self.lib = lib
+        self.index = index
+
+    @staticmethod
+    def _host(a, dtype):
+        import numpy as np
+        a = np.ascontiguousarray(a)
+        if a.dtype != dtype:
+            a = a.astype(dtype) if dtype != np.uint64 else a.view(np.uint64)
+        return a
+
+    def submit(self, ops, keys, vals) -> int:
+        import numpy as np
+        ops = self._host(ops, np.uint8)
+        keys = self._host(keys, np.uint64)
+        vals = self._host(vals, np.uint64)
+        t = ctypes.c_uint64(0)
+        _chk(self.lib.pi_server_submit(self._h, ops.ctypes.data, keys.ctypes.data, vals.ctypes.data, len(ops),
+                                       ctypes.byref(t)), "pi_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, n: int):
+        """(results int64 [n, 2], latency seconds) of the oldest uncollected request."""
+        import numpy as np
+        out = np.empty((n, 2), dtype=np.int64)
+        lat = ctypes.c_double(0)
+        _chk(self.lib.pi_server_wait(self._h, ticket, out.ctypes.data, ctypes.byref(lat)), "pi_server_wait")
+        return out, lat.value
+
+    def stats(self, reset: bool = False) -> dict:
+        st = PiServerStats()
+        _chk(self.lib.pi_server_stats(self._h, ctypes.byref(st), 1 if reset else 0), "pi_server_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+
+    def replay(self, ops, keys, vals, sizes, arrivals, want_results: bool = True):
+        """pi_server_replay: (results int64 [sum(sizes), 2] or None, latencies seconds)."""
+        import numpy as np
+        ops = self._host(ops, np.uint8)
+        keys = self._host(keys, np.uint64)
+        vals = self._host(vals, np.uint64)
+        sizes = np.ascontiguousarray(sizes, dtype=np.uint32)
+        arrivals = np.ascontiguousarray(arrivals, dtype=np.float64)
+        total = int(sizes.sum())
+        if total > len(ops):
+            raise ValueError("sizes exceed the query arrays")
+        res = np.empty((total, 2), dtype=np.int64) if want_results else None
+        lat = np.empty(len(sizes), dtype=np.float64)
+        _chk(self.lib.pi_server_replay(self._h, ops.ctypes.data, keys.ctypes.data, vals.ctypes.data,
+                                       sizes.ctypes.data, arrivals.ctypes.data, len(sizes),
+                                       res.ctypes.data if res is not None else None, lat.ctypes.data),
+             "pi_server_replay")
+        return res, lat
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.pi_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

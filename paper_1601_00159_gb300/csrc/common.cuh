@@ -630,6 +630,9 @@ uint64_t multi_scratch_bytes(uint32_t qcap);
 cudaError_t launch_multi(const MultiArgs& a, int warps, int radix_bits, uint32_t grid, cudaStream_t s);
 cudaError_t multi_occupancy(int warps, int radix_bits, int* blocks);
 
+// Sets the error code pi_last_error reports on this host thread.
+void set_last_error(int code);
+
 // Kernels launched by this host thread (every launcher adds the launches it issues); the
 // batch entry points fold the difference into the index's own count.
 extern thread_local uint64_t g_launches;

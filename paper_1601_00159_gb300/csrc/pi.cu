@@ -1386,3 +1386,7 @@ uint64_t pi_multi_kernels_per_call(const pi_multi_t* mx) { return mx ? mx->launc
 void pi_multi_destroy(pi_multi_t* mx) { multi_destroy(mx); }
 
 }  // extern "C"
+
+namespace pi {
+void set_last_error(int code) { g_last_error = code; }
+}  // namespace pi

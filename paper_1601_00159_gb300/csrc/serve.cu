@@ -1,0 +1,438 @@
+// Serving form: continuous batching of variable-size requests against one resident
+// index (host runtime; every query runs in the batch path's kernels).
+//
+// Data path of a request: the client copies its arrays into a pinned ring (submit);
+// the dispatcher thread coalesces ready requests, in arrival order and contiguous in
+// the ring, into a batch of at most max_batch queries on a free device slot:
+//   h2d stream:     ring -> slot inputs                          (event in)
+//   compute stream: wait in; pi_execute_batch on the slot        (event done)
+//   d2h stream:     wait done; slot results -> the ring          (event out)
+// With several slots in flight, batch k+1's copy in and batch k's copy out overlap
+// batch k's and k+1's kernels. The dispatcher polls the out events in dispatch order
+// and stamps the requests complete; a client collects its results from the ring, which
+// frees the space (collection is in submission order, so the ring is a FIFO).
+// Only public entry points of the library touch the index, from the dispatcher thread.
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+    uint64_t pos;       // ring position (monotone counter; physical index pos % R)
+    uint32_t n;
+    bool ready;         // inputs copied into the ring
+    bool dispatched;
+    bool done;
+    int64_t t_arrive;   // ns
+    int64_t t_done;
+};
+
+struct Slot {
+    uint8_t* d_ops = nullptr;
+    uint64_t* d_keys = nullptr;
+    uint64_t* d_vals = nullptr;
+    pi_result_t* d_res = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_done = nullptr, ev_out = nullptr;
+    uint64_t first = 0;  // ticket of the batch's first request
+    uint32_t nreq = 0;
+    bool busy = false;
+};
+
+int map_err(cudaError_t e) {
+    if (e == cudaSuccess) return PI_OK;
+    return e == cudaErrorMemoryAllocation ? PI_ERR_OOM : PI_ERR_CUDA;
+}
+
+}  // namespace
+
+struct pi_server {
+    pi_index_t* idx = nullptr;
+    int device = 0;
+    uint32_t max_batch = 0, nslots = 0;
+    uint64_t R = 0;  // ring capacity in queries
+    uint8_t* r_ops = nullptr;
+    uint64_t* r_keys = nullptr;
+    uint64_t* r_vals = nullptr;
+    pi_result_t* r_res = nullptr;
+    std::vector<Slot> slots;
+    std::deque<uint32_t> busy_order;  // slots in dispatch order
+    cudaStream_t cs = nullptr, hs = nullptr, ds = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_space, cv_work, cv_done;
+    std::deque<Req> reqs;   // uncollected requests, ticket order; reqs[0] has ticket `first`
+    uint64_t first = 1;     // ticket of reqs.front()
+    uint64_t next_disp = 1; // ticket of the first request not yet dispatched
+    uint64_t tail = 0;      // ring position after the newest request
+    std::thread worker;
+    bool stop = false;
+    int error = PI_OK;
+    // statistics since the last reset
+    std::vector<double> lat;
+    uint64_t n_req = 0, n_q = 0, n_batches = 0;
+    uint32_t inflight = 0, max_inflight = 0;
+
+    Req& at(uint64_t ticket) { return reqs[(size_t)(ticket - first)]; }
+};
+
+namespace {
+
+void run_dispatcher(pi_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        bool progress = false;
+        // retire completed batches, oldest first
+        while (!s->busy_order.empty()) {
+            Slot& sl = s->slots[s->busy_order.front()];
+            const cudaError_t q = cudaEventQuery(sl.ev_out);
+            if (q == cudaErrorNotReady) break;
+            if (q != cudaSuccess && s->error == PI_OK) s->error = map_err(q);
+            const int64_t t = now_ns();
+            for (uint32_t k = 0; k < sl.nreq; ++k) {
+                Req& r = s->at(sl.first + k);
+                r.done = true;
+                r.t_done = t;
+                s->lat.push_back((double)(t - r.t_arrive) * 1e-9);
+                s->n_req++;
+                s->n_q += r.n;
+            }
+            sl.busy = false;
+            s->busy_order.pop_front();
+            s->inflight--;
+            progress = true;
+            s->cv_done.notify_all();
+        }
+        // dispatch the ready requests into a free slot
+        uint32_t free_slot = s->nslots;
+        for (uint32_t i = 0; i < s->nslots; ++i)
+            if (!s->slots[i].busy) {
+                free_slot = i;
+                break;
+            }
+        const uint64_t end_ticket = s->first + s->reqs.size();
+        if (free_slot < s->nslots && s->next_disp < end_ticket && s->at(s->next_disp).ready && s->error == PI_OK) {
+            const uint64_t t0 = s->next_disp;
+            const uint64_t pos0 = s->at(t0).pos;
+            uint64_t pos_end = pos0, t = t0;
+            uint32_t n = 0;
+            while (t < end_ticket) {
+                const Req& r = s->at(t);
+                if (!r.ready || r.pos != pos_end || n + r.n > s->max_batch) break;
+                if ((pos0 % s->R) + (pos_end - pos0) + r.n > s->R) break;  // stays contiguous in the ring
+                n += r.n;
+                pos_end += r.n;
+                ++t;
+            }
+            Slot& sl = s->slots[free_slot];
+            sl.first = t0;
+            sl.nreq = (uint32_t)(t - t0);
+            sl.busy = true;
+            for (uint64_t k = t0; k < t; ++k) s->at(k).dispatched = true;
+            s->next_disp = t;
+            s->busy_order.push_back(free_slot);
+            s->inflight++;
+            s->max_inflight = std::max(s->max_inflight, s->inflight);
+            s->n_batches++;
+            lk.unlock();
+            const uint64_t p = pos0 % s->R;
+            cudaError_t e = cudaMemcpyAsync(sl.d_ops, s->r_ops + p, n, cudaMemcpyHostToDevice, s->hs);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(sl.d_keys, s->r_keys + p, (size_t)n * 8, cudaMemcpyHostToDevice, s->hs);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(sl.d_vals, s->r_vals + p, (size_t)n * 8, cudaMemcpyHostToDevice, s->hs);
+            if (e == cudaSuccess) e = cudaEventRecord(sl.ev_in, s->hs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, sl.ev_in, 0);
+            int rc = e == cudaSuccess ? PI_OK : map_err(e);
+            if (rc == PI_OK)
+                rc = pi_execute_batch(s->idx, sl.d_ops, sl.d_keys, sl.d_vals, n, sl.d_res,
+                                      reinterpret_cast<pi_stream_t>(s->cs));
+            if (rc == PI_OK) {
+                e = cudaEventRecord(sl.ev_done, s->cs);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s->ds, sl.ev_done, 0);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(s->r_res + p, sl.d_res, (size_t)n * sizeof(pi_result_t), cudaMemcpyDeviceToHost,
+                                        s->ds);
+                rc = map_err(e);
+            }
+            // the out event is recorded even after an error, so the batch still retires
+            cudaEventRecord(sl.ev_out, s->ds);
+            lk.lock();
+            if (rc != PI_OK && s->error == PI_OK) s->error = rc;
+            progress = true;
+        }
+        if (s->stop && s->busy_order.empty() && (s->next_disp >= s->first + s->reqs.size() || s->error != PI_OK))
+            break;
+        if (!progress) {
+            if (s->busy_order.empty())
+                s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
+            else
+                s->cv_work.wait_for(lk, std::chrono::microseconds(10));  // polling the GPU
+        }
+    }
+    s->cv_done.notify_all();
+}
+
+void free_server(pi_server* s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    for (auto& sl : s->slots) {
+        cudaFree(sl.d_ops);
+        cudaFree(sl.d_keys);
+        cudaFree(sl.d_vals);
+        cudaFree(sl.d_res);
+        if (sl.ev_in) cudaEventDestroy(sl.ev_in);
+        if (sl.ev_done) cudaEventDestroy(sl.ev_done);
+        if (sl.ev_out) cudaEventDestroy(sl.ev_out);
+    }
+    if (s->r_ops) cudaFreeHost(s->r_ops);
+    if (s->r_keys) cudaFreeHost(s->r_keys);
+    if (s->r_vals) cudaFreeHost(s->r_vals);
+    if (s->r_res) cudaFreeHost(s->r_res);
+    if (s->cs) cudaStreamDestroy(s->cs);
+    if (s->hs) cudaStreamDestroy(s->hs);
+    if (s->ds) cudaStreamDestroy(s->ds);
+    delete s;
+}
+
+int submit_at(pi_server* s, const uint8_t* ops, const uint64_t* keys, const uint64_t* vals, uint32_t n,
+              int64_t t_arrive, uint64_t* ticket_out) {
+    if (!s || !ops || !keys || !vals || n == 0 || n > s->max_batch) return PI_ERR_INVALID_ARG;
+    uint64_t ticket, pos;
+    {
+        // Reserve [pos, pos + n) in the ring: contiguous (a request never wraps), and not
+        // on a physical slot of an uncollected request, i.e. pos + n <= R + the oldest
+        // uncollected position (any place is free when nothing is uncollected).
+        std::unique_lock<std::mutex> lk(s->mu);
+        for (;;) {
+            if (s->error != PI_OK) return s->error;
+            pos = s->tail;
+            if (pos % s->R + n > s->R) pos += s->R - pos % s->R;
+            if (s->reqs.empty() || pos + n <= s->reqs.front().pos + s->R) break;
+            s->cv_space.wait(lk);
+        }
+        ticket = s->first + s->reqs.size();
+        s->reqs.push_back(Req{pos, n, false, false, false, t_arrive, 0});
+        s->tail = pos + n;
+    }
+    const uint64_t p = pos % s->R;
+    std::memcpy(s->r_ops + p, ops, n);
+    std::memcpy(s->r_keys + p, keys, (size_t)n * 8);
+    std::memcpy(s->r_vals + p, vals, (size_t)n * 8);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->at(ticket).ready = true;
+    }
+    s->cv_work.notify_one();
+    s->cv_done.notify_all();  // a collector may be waiting for this ticket to exist
+    if (ticket_out) *ticket_out = ticket;
+    return PI_OK;
+}
+
+double pct(std::vector<double>& v, double q) {
+    if (v.empty()) return 0.0;
+    const size_t k = (size_t)std::min<double>((double)(v.size() - 1), q * (double)(v.size() - 1) + 0.5);
+    std::nth_element(v.begin(), v.begin() + (long)k, v.end());
+    return v[k];
+}
+
+}  // namespace
+
+extern "C" {
+
+pi_server_t* pi_server_create(pi_index_t* idx, const pi_server_config_t* cfg) {
+    pi::set_last_error(PI_OK);
+    pi_server_config_t c{};
+    c.struct_size = sizeof(c);
+    c.max_batch = 1u << 20;
+    c.slots = 3;
+    if (cfg) {
+        if (cfg->struct_size != sizeof(pi_server_config_t)) {
+            pi::set_last_error(PI_ERR_INVALID_ARG);
+            return nullptr;
+        }
+        if (cfg->max_batch) c.max_batch = cfg->max_batch;
+        if (cfg->slots) c.slots = cfg->slots;
+        c.ring_queries = cfg->ring_queries;
+    }
+    if (!c.ring_queries) c.ring_queries = 8ull * c.max_batch;
+    if (!idx || c.max_batch > PI_MAX_BATCH || c.slots < 2 || c.slots > 8 || c.ring_queries < c.max_batch) {
+        pi::set_last_error(PI_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    pi_server* s = new (std::nothrow) pi_server();
+    if (!s) {
+        pi::set_last_error(PI_ERR_OOM);
+        return nullptr;
+    }
+    cudaGetDevice(&s->device);
+    s->idx = idx;
+    s->max_batch = c.max_batch;
+    s->nslots = c.slots;
+    s->R = c.ring_queries;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMallocHost(reinterpret_cast<void**>(&s->r_ops), s->R)) != cudaSuccess) break;
+        if ((e = cudaMallocHost(reinterpret_cast<void**>(&s->r_keys), s->R * 8)) != cudaSuccess) break;
+        if ((e = cudaMallocHost(reinterpret_cast<void**>(&s->r_vals), s->R * 8)) != cudaSuccess) break;
+        if ((e = cudaMallocHost(reinterpret_cast<void**>(&s->r_res), s->R * sizeof(pi_result_t))) != cudaSuccess) break;
+        s->slots.resize(s->nslots);
+        for (auto& sl : s->slots) {
+            if ((e = cudaMalloc(reinterpret_cast<void**>(&sl.d_ops), s->max_batch)) != cudaSuccess) break;
+            if ((e = cudaMalloc(reinterpret_cast<void**>(&sl.d_keys), (size_t)s->max_batch * 8)) != cudaSuccess) break;
+            if ((e = cudaMalloc(reinterpret_cast<void**>(&sl.d_vals), (size_t)s->max_batch * 8)) != cudaSuccess) break;
+            if ((e = cudaMalloc(reinterpret_cast<void**>(&sl.d_res), (size_t)s->max_batch * sizeof(pi_result_t))) !=
+                cudaSuccess)
+                break;
+            if ((e = cudaEventCreateWithFlags(&sl.ev_in, cudaEventDisableTiming)) != cudaSuccess) break;
+            if ((e = cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming)) != cudaSuccess) break;
+            if ((e = cudaEventCreateWithFlags(&sl.ev_out, cudaEventDisableTiming)) != cudaSuccess) break;
+        }
+        if (e != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&s->hs, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&s->ds, cudaStreamNonBlocking)) != cudaSuccess) break;
+        // the index's earlier work (on the legacy default stream or elsewhere) is done first
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) break;
+    } while (0);
+    if (e != cudaSuccess) {
+        pi::set_last_error(map_err(e));
+        free_server(s);
+        return nullptr;
+    }
+    try {
+        s->worker = std::thread(run_dispatcher, s);
+    } catch (...) {
+        pi::set_last_error(PI_ERR_OOM);
+        free_server(s);
+        return nullptr;
+    }
+    return s;
+}
+
+int pi_server_submit(pi_server_t* s, const uint8_t* ops, const uint64_t* keys, const uint64_t* values, uint32_t n,
+                     uint64_t* ticket_out) {
+    return submit_at(s, ops, keys, values, n, now_ns(), ticket_out);
+}
+
+int pi_server_wait(pi_server_t* s, uint64_t ticket, pi_result_t* results_out, double* latency_s) {
+    if (!s) return PI_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (ticket != s->first) return PI_ERR_INVALID_ARG;  // not the oldest uncollected request
+    // the request may not be submitted yet (a collector thread runs ahead of the submitter)
+    s->cv_done.wait(lk, [&] { return !s->reqs.empty() || s->error != PI_OK; });
+    if (s->reqs.empty()) return s->error;
+    s->cv_done.wait(lk, [&] { return s->reqs.front().done || s->error != PI_OK; });
+    Req r = s->reqs.front();
+    if (!r.done) return s->error;
+    lk.unlock();
+    if (results_out) std::memcpy(results_out, s->r_res + r.pos % s->R, (size_t)r.n * sizeof(pi_result_t));
+    if (latency_s) *latency_s = (double)(r.t_done - r.t_arrive) * 1e-9;
+    lk.lock();
+    s->reqs.pop_front();
+    s->first++;
+    lk.unlock();
+    s->cv_space.notify_all();
+    return s->error;
+}
+
+int pi_server_stats(pi_server_t* s, pi_server_stats_t* out, int reset) {
+    if (!s || !out) return PI_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->requests = s->n_req;
+    out->queries = s->n_q;
+    out->batches = s->n_batches;
+    out->max_in_flight = s->max_inflight;
+    std::vector<double> v = s->lat;
+    out->p50_s = pct(v, 0.50);
+    out->p99_s = pct(v, 0.99);
+    out->max_s = v.empty() ? 0.0 : *std::max_element(v.begin(), v.end());
+    out->mean_batch = s->n_batches ? (double)s->n_q / (double)s->n_batches : 0.0;
+    if (reset) {
+        s->lat.clear();
+        s->n_req = s->n_q = s->n_batches = 0;
+        s->max_inflight = s->inflight;
+    }
+    return s->error;
+}
+
+int pi_server_replay(pi_server_t* s, const uint8_t* ops, const uint64_t* keys, const uint64_t* values,
+                     const uint32_t* sizes, const double* arrival_s, uint32_t nreq, pi_result_t* results_out,
+                     double* latency_s_out) {
+    if (!s || !ops || !keys || !values || !sizes || !arrival_s) return PI_ERR_INVALID_ARG;
+    uint64_t first;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        first = s->first + s->reqs.size();
+    }
+    std::atomic<int> rc_collect{PI_OK};
+    std::thread collector([&] {
+        uint64_t off = 0;
+        for (uint32_t i = 0; i < nreq; ++i) {
+            double lat = 0;
+            const int rc = pi_server_wait(s, first + i, results_out ? results_out + off : nullptr, &lat);
+            if (rc != PI_OK) {
+                rc_collect = rc;
+                std::lock_guard<std::mutex> lk(s->mu);  // release a submitter waiting for space
+                if (s->error == PI_OK) s->error = rc;
+                s->cv_space.notify_all();
+                s->cv_done.notify_all();
+                return;
+            }
+            if (latency_s_out) latency_s_out[i] = lat;
+            off += sizes[i];
+        }
+    });
+    int rc = PI_OK;
+    const int64_t t0 = now_ns();
+    uint64_t off = 0;
+    for (uint32_t i = 0; i < nreq && rc == PI_OK; ++i) {
+        const int64_t target = t0 + (int64_t)(arrival_s[i] * 1e9);
+        while (now_ns() < target) {
+            if (target - now_ns() > 200000) std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        uint64_t ticket = 0;
+        rc = submit_at(s, ops + off, keys + off, values + off, sizes[i], target, &ticket);
+        if (rc == PI_OK && ticket != first + i) rc = PI_ERR_INVALID_ARG;  // another client interleaved
+        off += sizes[i];
+    }
+    if (rc != PI_OK) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->error == PI_OK) s->error = rc;
+        s->cv_done.notify_all();
+    }
+    collector.join();
+    return rc != PI_OK ? rc : rc_collect.load();
+}
+
+void pi_server_destroy(pi_server_t* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaStreamSynchronize(s->cs);
+    cudaStreamSynchronize(s->ds);
+    free_server(s);
+}
+
+}  // extern "C"
