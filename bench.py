@@ -53,6 +53,10 @@ WORKLOADS = {
                      desc="batching: 256 independent indices, sizes log-uniform in [2^10,2^20] uint64 keys "
                           "(p=1/4), each with its own batch of log-uniform [2^8,2^16] queries, 80% search "
                           "(half hits) / 20% insert of new uniform keys; one CUDA-graph launch per step"),
+    "serving": dict(fn=wl.serving, n=1 << 26, q=None,
+                    desc="serving: resident 2^26-key uint64 index (p=1/4); Poisson-arrival requests of 1..4096 "
+                         "queries (log-uniform), 95% search / 5% insert, Zipf 0.9 keys; coalesced batches of at "
+                         "most 2^20 queries, 3 in flight; p50/p99 request latency at 70% of the measured capacity"),
 }
 TUNING = os.path.join(ROOT, "paper_1601_00159_gb300", "multi_tuning.json")
 
@@ -248,11 +252,41 @@ def run_reference_batching(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_serving(args):
+    """The oracle on the serving workload: built over the 2^26 keys (untimed), each step
+    applying one bounded slice of the request stream in arrival order."""
+    import oracle
+    oracle.build()
+    spec = WORKLOADS["serving"]
+    w = wl.serving(nreq=4000)
+    orc = oracle.Oracle(w.keys, w.vals, w.promote_p, w.hash_seed)
+    per = min(len(w.ops) // max(args.steps + args.warmup, 1), 1 << 18)
+    t = None
+    for s_ in range(args.warmup + args.steps):
+        if s_ == args.warmup:
+            t = time.perf_counter()
+        a = s_ * per
+        orc.execute(w.ops[a:a + per], w.qkeys[a:a + per], w.qvals[a:a + per])
+    el = time.perf_counter() - t
+    v = args.steps * per / el / 1e6
+    orc.close()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": "serving", "desc": spec["desc"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per} queries of the request stream per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     if args.workload == "batching":
         return run_reference_batching(args)
+    if args.workload == "serving":
+        return run_reference_serving(args)
     spec = WORKLOADS[args.workload]
     w = spec["fn"]()
     batches = list(w.batches()) if callable(w.batches) else list(w.batches)
@@ -436,6 +470,120 @@ def run_batching(args, ws, rank, local):
     ms.close()
     for ix in idxs:
         ix.close()
+
+
+def run_serving(args, ws, rank, local):
+    """Config 5: the server under a saturating burst (capacity), then under Poisson
+    arrivals at 70% of that capacity (latency), beside one request per pi_execute_batch."""
+    import torch
+    from paper_1601_00159_gb300 import Index, Server, build, load_library
+    build.build()
+    load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = WORKLOADS["serving"]
+    t = time.time()
+    nreq = 40000
+    w = wl.serving(seed=5 + rank, nreq=nreq)
+    gen_s = time.time() - t
+    offs = np.concatenate([[0], np.cumsum(w.sizes.astype(np.int64))])
+    t = time.time()
+    idx = Index(torch.from_numpy(w.keys.view(np.int64)).to(dev), torch.from_numpy(w.vals.view(np.int64)).to(dev),
+                w.promote_p, w.hash_seed)
+    torch.cuda.synchronize()
+    create_s = time.time() - t
+    srv = Server(idx, max_batch=1 << 20, slots=3)
+    # warm-up, then capacity: every request arrives at once
+    warm = 2000
+    srv.replay(w.ops, w.qkeys, w.qvals, w.sizes[:warm], np.zeros(warm), want_results=False)
+    srv.stats(reset=True)
+    half = nreq // 2
+    a, b = offs[warm], offs[warm + half]
+    t = time.perf_counter()
+    srv.replay(w.ops[a:b], w.qkeys[a:b], w.qvals[a:b], w.sizes[warm:warm + half], np.zeros(half), want_results=False)
+    sat_s = time.perf_counter() - t
+    sat = srv.stats(reset=True)
+    capacity = (b - a) / sat_s / 1e6
+    # latency: Poisson arrivals at 70% of capacity
+    rest = nreq - warm - half
+    a2, b2 = offs[warm + half], offs[nreq]
+    rate = 0.7 * capacity * 1e6 / float(w.sizes[warm + half:].mean())  # requests per second
+    gaps = -np.log(np.maximum(wl.uniform01(wl.stream_seed(5, 77), 0, rest), 1e-12)) / rate
+    arrivals = np.cumsum(gaps)
+    l0 = idx.info()["kernel_launches"]
+    with ClockSampler(local) as clk:
+        t = time.perf_counter()
+        _, lat = srv.replay(w.ops[a2:b2], w.qkeys[a2:b2], w.qvals[a2:b2], w.sizes[warm + half:], arrivals,
+                            want_results=False)
+        run_s = time.perf_counter() - t
+    st = srv.stats(reset=True)
+    srv.close()
+    launches = idx.info()["kernel_launches"] - l0
+    value = (b2 - a2) / run_s / 1e6
+    # the plain path without coalescing: one request per batch, host buffers, synchronous
+    sample = 300
+    hres = torch.empty((4096, 2), dtype=torch.int64).pin_memory()
+    pops = torch.from_numpy(w.ops[:offs[sample]].copy()).pin_memory()
+    pkeys = torch.from_numpy(w.qkeys[:offs[sample]].view(np.int64).copy()).pin_memory()
+    pvals = torch.from_numpy(w.qvals[:offs[sample]].view(np.int64).copy()).pin_memory()
+    plat = []
+    t = time.perf_counter()
+    for i in range(sample):
+        x, y = offs[i], offs[i + 1]
+        t1 = time.perf_counter()
+        idx.execute_host(pops[x:y], pkeys[x:y], pvals[x:y], hres[: y - x])
+        torch.cuda.synchronize()
+        plat.append(time.perf_counter() - t1)
+    per_req_s = time.perf_counter() - t
+    per_req_value = offs[sample] / per_req_s / 1e6
+    hbm, peak_kind = measured_peaks()
+    info = idx.info()
+    assert idx.status() == 0
+    idx.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": int(rest),
+        "warmup": warm, "ms_per_step": run_s / rest * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serving", "desc": spec["desc"], "keys": len(w.keys), "requests": int(rest),
+                   "queries": int(b2 - a2), "mean_request": float(w.sizes.mean()), "arrival_rate_per_s": rate,
+                   "step": "one request", "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "l2_flush": "none: the 2^26-key index (1.1 GB storage) exceeds L2"},
+        "latency": {"p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
+                    "max_ms": float(lat.max()) * 1e3, "batches": st["batches"], "mean_batch": st["mean_batch"],
+                    "max_in_flight": st["max_in_flight"], "measured_from": "scheduled arrival to results in host memory"},
+        "capacity": {"value": capacity, "unit": UNIT, "batches": sat["batches"], "mean_batch": sat["mean_batch"],
+                     "p99_ms": sat["p99_s"] * 1e3, "note": "every request arriving at once"},
+        "plain_per_request": {"value": per_req_value, "unit": UNIT, "requests": sample,
+                              "p50_ms": float(np.percentile(plat, 50)) * 1e3,
+                              "p99_ms": float(np.percentile(plat, 99)) * 1e3,
+                              "note": "pi_execute_batch_host per request, no coalescing, synchronous"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": float(w.sizes.mean()) * 17,
+                "d2h_bytes_per_step": float(w.sizes.mean()) * 16,
+                "note": "the server path is end to end: host requests in, host results out"},
+        "roofline": None,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "index": {"size": info["size"], "live": info["live"], "create_s": create_s, "gen_s": gen_s},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t = time.time()
+        orc = oracle.Oracle(w.keys, w.vals, w.promote_p, w.hash_seed)
+        build_s = time.time() - t
+        done, el = 0, 0.0
+        while done < offs[-1] and el < args.cpu_budget:
+            c = int(min(1 << 18, offs[-1] - done))
+            t = time.perf_counter()
+            orc.execute(w.ops[done:done + c], w.qkeys[done:done + c], w.qvals[done:done + c])
+            el += time.perf_counter() - t
+            done += c
+        orc.close()
+        line["cpu_baseline"] = {"value": done / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the first {done} queries of the request stream in arrival order "
+                                          f"({el:.1f} s timed; oracle build {build_s:.1f} s untimed)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def cpu_baseline_multi(w, rnd, budget_s: float = 20.0):
@@ -622,6 +770,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "batching":
         run_batching(args, ws, rank, local)
+    elif args.workload == "serving":
+        run_serving(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

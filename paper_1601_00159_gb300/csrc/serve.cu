@@ -84,6 +84,8 @@ struct pi_server {
     uint64_t tail = 0;      // ring position after the newest request
     std::thread worker;
     bool stop = false;
+    bool disp_idle = false;      // the dispatcher sleeps with nothing in flight
+    uint32_t submit_waiters = 0; // collectors waiting for a ticket to be submitted
     int error = PI_OK;
     // statistics since the last reset
     std::vector<double> lat;
@@ -180,10 +182,13 @@ void run_dispatcher(pi_server* s) {
         if (s->stop && s->busy_order.empty() && (s->next_disp >= s->first + s->reqs.size() || s->error != PI_OK))
             break;
         if (!progress) {
-            if (s->busy_order.empty())
+            if (s->busy_order.empty()) {
+                s->disp_idle = true;
                 s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
-            else
+                s->disp_idle = false;
+            } else {
                 s->cv_work.wait_for(lk, std::chrono::microseconds(10));  // polling the GPU
+            }
         }
     }
     s->cv_done.notify_all();
@@ -211,38 +216,56 @@ void free_server(pi_server* s) {
     delete s;
 }
 
-int submit_at(pi_server* s, const uint8_t* ops, const uint64_t* keys, const uint64_t* vals, uint32_t n,
-              int64_t t_arrive, uint64_t* ticket_out) {
-    if (!s || !ops || !keys || !vals || n == 0 || n > s->max_batch) return PI_ERR_INVALID_ARG;
-    uint64_t ticket, pos;
-    {
-        // Reserve [pos, pos + n) in the ring: contiguous (a request never wraps), and not
-        // on a physical slot of an uncollected request, i.e. pos + n <= R + the oldest
-        // uncollected position (any place is free when nothing is uncollected).
-        std::unique_lock<std::mutex> lk(s->mu);
-        for (;;) {
-            if (s->error != PI_OK) return s->error;
-            pos = s->tail;
-            if (pos % s->R + n > s->R) pos += s->R - pos % s->R;
-            if (s->reqs.empty() || pos + n <= s->reqs.front().pos + s->R) break;
-            s->cv_space.wait(lk);
-        }
-        ticket = s->first + s->reqs.size();
-        s->reqs.push_back(Req{pos, n, false, false, false, t_arrive, 0});
-        s->tail = pos + n;
+// Reserves ring space and tickets for count requests back to back (request k has
+// sizes[k] queries): each request contiguous in the ring and off every physical slot of
+// an uncollected request, i.e. the group's end <= R + the oldest uncollected position
+// (anything is free when nothing is uncollected). Waits for space.
+int reserve_group(pi_server* s, const uint32_t* sizes, uint32_t count, const int64_t* t_arrive, uint64_t* pos,
+                  uint64_t* first_ticket) {
+    if (!s || count == 0) return PI_ERR_INVALID_ARG;
+    uint64_t total = 0;
+    for (uint32_t k = 0; k < count; ++k) {
+        if (sizes[k] == 0 || sizes[k] > s->max_batch) return PI_ERR_INVALID_ARG;
+        total += sizes[k];
     }
-    const uint64_t p = pos % s->R;
-    std::memcpy(s->r_ops + p, ops, n);
-    std::memcpy(s->r_keys + p, keys, (size_t)n * 8);
-    std::memcpy(s->r_vals + p, vals, (size_t)n * 8);
+    if (total > s->R) return PI_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        if (s->error != PI_OK) return s->error;
+        uint64_t p = s->tail;
+        for (uint32_t k = 0; k < count; ++k) {
+            if (p % s->R + sizes[k] > s->R) p += s->R - p % s->R;
+            pos[k] = p;
+            p += sizes[k];
+        }
+        if (s->reqs.empty() || p <= s->reqs.front().pos + s->R) break;
+        s->cv_space.wait(lk);
+    }
+    *first_ticket = s->first + s->reqs.size();
+    for (uint32_t k = 0; k < count; ++k) s->reqs.push_back(Req{pos[k], sizes[k], false, false, false, t_arrive[k], 0});
+    s->tail = pos[count - 1] + sizes[count - 1];
+    return PI_OK;
+}
+
+// Copies reserved requests' queries (request k from offset offs[k] of the arrays) into
+// the ring and hands them to the dispatcher.
+void fill_group(pi_server* s, const uint8_t* ops, const uint64_t* keys, const uint64_t* vals, const uint32_t* sizes,
+                const uint64_t* offs, uint32_t count, const uint64_t* pos, uint64_t first_ticket) {
+    for (uint32_t k = 0; k < count; ++k) {
+        const uint64_t p = pos[k] % s->R, o = offs[k], n = sizes[k];
+        std::memcpy(s->r_ops + p, ops + o, n);
+        std::memcpy(s->r_keys + p, keys + o, n * 8);
+        std::memcpy(s->r_vals + p, vals + o, n * 8);
+    }
+    bool wake_disp, wake_coll;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        s->at(ticket).ready = true;
+        for (uint32_t k = 0; k < count; ++k) s->at(first_ticket + k).ready = true;
+        wake_disp = s->disp_idle;
+        wake_coll = s->submit_waiters > 0;
     }
-    s->cv_work.notify_one();
-    s->cv_done.notify_all();  // a collector may be waiting for this ticket to exist
-    if (ticket_out) *ticket_out = ticket;
-    return PI_OK;
+    if (wake_disp) s->cv_work.notify_one();
+    if (wake_coll) s->cv_done.notify_all();  // a collector waits for these tickets to exist
 }
 
 double pct(std::vector<double>& v, double q) {
@@ -328,7 +351,15 @@ pi_server_t* pi_server_create(pi_index_t* idx, const pi_server_config_t* cfg) {
 
 int pi_server_submit(pi_server_t* s, const uint8_t* ops, const uint64_t* keys, const uint64_t* values, uint32_t n,
                      uint64_t* ticket_out) {
-    return submit_at(s, ops, keys, values, n, now_ns(), ticket_out);
+    if (!s || !ops || !keys || !values) return PI_ERR_INVALID_ARG;
+    const uint64_t off = 0;
+    const int64_t t = now_ns();
+    uint64_t pos = 0, ticket = 0;
+    const int rc = reserve_group(s, &n, 1, &t, &pos, &ticket);
+    if (rc != PI_OK) return rc;
+    fill_group(s, ops, keys, values, &n, &off, 1, &pos, ticket);
+    if (ticket_out) *ticket_out = ticket;
+    return PI_OK;
 }
 
 int pi_server_wait(pi_server_t* s, uint64_t ticket, pi_result_t* results_out, double* latency_s) {
@@ -336,7 +367,11 @@ int pi_server_wait(pi_server_t* s, uint64_t ticket, pi_result_t* results_out, do
     std::unique_lock<std::mutex> lk(s->mu);
     if (ticket != s->first) return PI_ERR_INVALID_ARG;  // not the oldest uncollected request
     // the request may not be submitted yet (a collector thread runs ahead of the submitter)
-    s->cv_done.wait(lk, [&] { return !s->reqs.empty() || s->error != PI_OK; });
+    if (s->reqs.empty()) {
+        s->submit_waiters++;
+        s->cv_done.wait(lk, [&] { return !s->reqs.empty() || s->error != PI_OK; });
+        s->submit_waiters--;
+    }
     if (s->reqs.empty()) return s->error;
     s->cv_done.wait(lk, [&] { return s->reqs.front().done || s->error != PI_OK; });
     Req r = s->reqs.front();
@@ -402,17 +437,65 @@ int pi_server_replay(pi_server_t* s, const uint8_t* ops, const uint64_t* keys, c
     });
     int rc = PI_OK;
     const int64_t t0 = now_ns();
-    uint64_t off = 0;
-    for (uint32_t i = 0; i < nreq && rc == PI_OK; ++i) {
-        const int64_t target = t0 + (int64_t)(arrival_s[i] * 1e9);
-        while (now_ns() < target) {
-            if (target - now_ns() > 200000) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    std::vector<uint64_t> offs(nreq + 1, 0);
+    for (uint32_t i = 0; i < nreq; ++i) offs[i + 1] = offs[i] + sizes[i];
+    std::vector<int64_t> target(nreq);
+    for (uint32_t i = 0; i < nreq; ++i) target[i] = t0 + (int64_t)(arrival_s[i] * 1e9);
+    // Copy helpers: the main thread reserves groups in arrival order, the helpers copy
+    // them into the ring (round robin), so submission is not bound by one memcpy stream.
+    struct Job {
+        uint32_t i, k;
+        uint64_t ticket;
+        std::vector<uint64_t> pos;
+    };
+    const uint32_t nhelp = std::max(1u, std::min(4u, std::thread::hardware_concurrency() / 4));
+    std::vector<std::deque<Job>> jobs(nhelp);
+    std::mutex jmu;
+    std::condition_variable jcv;
+    bool jdone = false;
+    std::vector<std::thread> helpers;
+    for (uint32_t h = 0; h < nhelp; ++h)
+        helpers.emplace_back([&, h] {
+            std::unique_lock<std::mutex> lk(jmu);
+            while (true) {
+                jcv.wait(lk, [&] { return jdone || !jobs[h].empty(); });
+                if (jobs[h].empty()) return;
+                Job jb = std::move(jobs[h].front());
+                jobs[h].pop_front();
+                lk.unlock();
+                fill_group(s, ops, keys, values, sizes + jb.i, offs.data() + jb.i, jb.k, jb.pos.data(), jb.ticket);
+                lk.lock();
+            }
+        });
+    uint32_t i = 0, rr = 0;
+    while (i < nreq && rc == PI_OK) {
+        while (now_ns() < target[i]) {
+            if (target[i] - now_ns() > 200000) std::this_thread::sleep_for(std::chrono::microseconds(50));
         }
-        uint64_t ticket = 0;
-        rc = submit_at(s, ops + off, keys + off, values + off, sizes[i], target, &ticket);
-        if (rc == PI_OK && ticket != first + i) rc = PI_ERR_INVALID_ARG;  // another client interleaved
-        off += sizes[i];
+        // every request already due goes in one group (bounded so the ring can hold it)
+        const int64_t now = now_ns();
+        uint32_t k = 1;
+        uint64_t q = sizes[i];
+        while (i + k < nreq && k < 1024 && target[i + k] <= now && q + sizes[i + k] <= s->R / 8) q += sizes[i + k++];
+        Job jb{i, k, 0, std::vector<uint64_t>(k)};
+        rc = reserve_group(s, sizes + i, k, target.data() + i, jb.pos.data(), &jb.ticket);
+        if (rc == PI_OK && jb.ticket != first + i) rc = PI_ERR_INVALID_ARG;  // another client interleaved
+        if (rc == PI_OK) {
+            {
+                std::lock_guard<std::mutex> lk(jmu);
+                jobs[rr].push_back(std::move(jb));
+            }
+            jcv.notify_all();
+            rr = (rr + 1) % nhelp;
+        }
+        i += k;
     }
+    {
+        std::lock_guard<std::mutex> lk(jmu);
+        jdone = true;
+    }
+    jcv.notify_all();
+    for (auto& t : helpers) t.join();
     if (rc != PI_OK) {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->error == PI_OK) s->error = rc;

@@ -299,3 +299,34 @@ def batching(seed: int = 4, count: int = 256, lo_log: float = 10, hi_log: float 
         return out
 
     return MultiWorkload("batching", keys, vals, 0.25, seeds, qs, batches)
+
+
+@dataclasses.dataclass
+class ServeWorkload:
+    name: str
+    keys: np.ndarray
+    vals: np.ndarray
+    promote_p: float
+    hash_seed: int
+    ops: np.ndarray        # the request stream's queries, back to back
+    qkeys: np.ndarray
+    qvals: np.ndarray
+    sizes: np.ndarray      # uint32 request sizes (queries)
+
+
+def serving(seed: int = 5, n: int = 1 << 26, nreq: int = 40000, max_size: int = 4096,
+            theta: float = 0.9) -> ServeWorkload:
+    """Serving: a resident index of n distinct uniform keys (value = splitmix64(key),
+    p = 1/4) and a stream of nreq requests of log-uniform sizes in [1, max_size], their
+    queries 95% search / 5% insert (overwrites) with Zipf(theta) keys over the index
+    (ranks scattered by a seeded bijection). Arrival times are the caller's."""
+    keys = distinct_keys(seed, np.arange(n))
+    vals = splitmix64(keys)
+    s = stream_seed(seed, 50)
+    sizes = np.maximum(1, np.floor(2.0 ** (uniform01(s, 0, nreq) * np.log2(max_size)))).astype(np.uint32)
+    q = int(sizes.sum())
+    z = Zipf(n, theta)
+    qkeys = keys[scramble(z.ranks(uniform01(s, nreq, q)), n, seed)]
+    ops = np.where(uniform01(s, nreq + q, q) < 0.05, OP_INSERT, OP_SEARCH).astype(np.uint8)
+    qvals = u64_stream(s, nreq + 2 * q, q)
+    return ServeWorkload("serving", keys, vals, 0.25, int(stream_seed(seed, 51)), ops, qkeys, qvals, sizes)
