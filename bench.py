@@ -78,8 +78,9 @@ def writer_source_digest():
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
-def writer_traffic_per_node():
-    """(bytes per storage node, note) from the committed ncu summary, or (None, why)."""
+def writer_traffic_per_node(lowest):
+    """(bytes per storage node, note) from the committed ncu summary, or (None, why): the
+    capture must be of the same writer source and the same lowest built level."""
     import re
     try:
         text = open(WRITER_PROFILE).read()
@@ -91,6 +92,9 @@ def writer_traffic_per_node():
         return None, "summary lacks digest or bytes"
     if m.group(1) != writer_source_digest():
         return None, "writer source changed since the ncu capture"
+    lv = re.search(r"lowest built level: `([0-9]+)`", text)
+    if not lv or int(lv.group(1)) != lowest:
+        return None, "the capture built a different lowest level"
     return float(b.group(1)), "ncu capture at 2^24 keys, scaled by storage nodes"
 
 
@@ -106,14 +110,16 @@ def measured_peaks():
 # ---------------------------------------------------------------------------------
 # Algorithmic bytes (the method's own traffic, counted per batch from its inputs and
 # the index sizes; one 32-byte sector per random access).
-def algorithmic_bytes(q, q_ins, distinct, hits, writes, size_after, level_sizes, l2_bytes, sort_passes):
+def algorithmic_bytes(q, q_ins, distinct, hits, writes, size_after, level_sizes, l2_bytes, sort_passes,
+                      lowest=2, inv_p=4):
     io = q * (1 + 8 + 16) + q_ins * 8
     trav = 0
     for l, n_l in enumerate(level_sizes):
-        if l >= 2 and n_l and 12 * n_l > l2_bytes / 2:
+        if l >= lowest and n_l and 12 * n_l > l2_bytes / 2:
             trav += distinct * 64
-    store = distinct * 32 + hits * 32 + writes * 96
-    n_index = sum(level_sizes[2:])
+    gap = inv_p ** (lowest - 1)  # storage nodes between two entries of the lowest built level
+    store = distinct * max(32, 8 * gap) + hits * 32 + writes * 96
+    n_index = sum(level_sizes[lowest:])
     rebuild = 9 * size_after + 12 * n_index
     sort = sort_passes * 24 * q + q * (9 + 12)
     return dict(io=io, traversal=trav, storage=store, rebuild=rebuild, sort=sort,
@@ -430,7 +436,7 @@ def run_batching(args, ws, rank, local):
     infos = [ix.info() for ix in idxs]
     ins = sum(int((b.ops == wl.OP_INSERT).sum()) for b in host_rounds[0])
     nodes = sum(inf["size"] for inf in infos)
-    entries = sum(sum(inf["level_size"][2:]) for inf in infos)
+    entries = sum(sum(inf["level_size"][inf["bottom_built"]:]) for inf in infos)
     io = qtot * (1 + 8 + 16) + ins * 8
     store = qtot * 32 + ins * 96
     merge = 2 * 17 * nodes
@@ -710,10 +716,12 @@ def run_ours(args, ws, rank, local):
     sizes = info1["level_size"]
     size_after = info1["size"]
     writes = distinct  # upper bound: every distinct key may be written once
-    ab = algorithmic_bytes(q, ins, distinct, distinct, writes, size_after, sizes, l2_bytes, 8)
+    lowest = info1["bottom_built"]
+    ab = algorithmic_bytes(q, ins, distinct, distinct, writes, size_after, sizes, l2_bytes, 8, lowest,
+                           int(round(1 / w.promote_p)))
     writer_ms = per_stage["rebuild_write"]
     achieved = ab["rebuild"] / (writer_ms * 1e-3) / 1e9
-    per_node, traffic_note = writer_traffic_per_node()
+    per_node, traffic_note = writer_traffic_per_node(lowest)
     traffic = per_node * size_after if per_node is not None else None
     low = min(ab["rebuild"], traffic) if traffic is not None else ab["rebuild"]
     line = {
@@ -730,7 +738,8 @@ def run_ours(args, ws, rank, local):
                      "frac_min_of_model_and_traffic": low / (writer_ms * 1e-3) / 1e9 / hbm,
                      "launches_per_step": 1, "ms_per_launch": writer_ms,
                      "algorithmic_bytes_per_launch": ab["rebuild"],
-                     "bytes_model": "9 B per storage node (key + meta scan) + 12 B per index entry written"},
+                     "bytes_model": "9 B per storage node (key + meta scan) + 12 B per built index entry",
+                     "lowest_built_level": lowest},
         "batch_roofline": {"algorithmic_bytes": ab["total"], "achieved_gbs": ab["total"] / (ms_step * 1e-3) / 1e9,
                            "frac": ab["total"] / (ms_step * 1e-3) / 1e9 / hbm},
         "stages_ms": per_stage,

@@ -77,7 +77,14 @@ typedef struct {
     uint64_t storage_capacity;   /* initial storage-layer capacity, in nodes */
     uint64_t index_capacity;     /* initial index-layer capacity, in entries */
     uint32_t test_flags;         /* PI_TEST_*: alternative code paths for tests; 0 in use */
-    uint32_t reserved;
+    uint32_t lowest_level;       /* lowest index level to materialise, 2..16. 0: automatic,
+                                    the lowest level l whose expected storage gap (1/P)^(l-1)
+                                    is at least 8 nodes (3 for P = 1/4), since on the GPU a
+                                    descent scans such a gap in one or two wide loads while
+                                    every built level costs a rebuild pass. 2 builds every
+                                    level, as the paper does. Levels below it still count in
+                                    pi_info's level sizes; pi_export_level reports them as
+                                    PI_ERR_NOT_BUILT. */
 } pi_config_t;
 
 /* test_flags bit: give only the lowest index level a launch of its own in the

@@ -48,7 +48,7 @@ class PiConfig(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("rebuild_policy", ctypes.c_uint32),
                 ("rebuild_threshold_pct", ctypes.c_uint32), ("smem_top_entries", ctypes.c_uint32),
                 ("storage_capacity", ctypes.c_uint64), ("index_capacity", ctypes.c_uint64),
-                ("test_flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("test_flags", ctypes.c_uint32), ("lowest_level", ctypes.c_uint32)]
 
 
 class PiMultiClass(ctypes.Structure):

@@ -530,6 +530,7 @@ struct DescendArgs {
     uint64_t* dq;        // dense distinct keys
     uint32_t* dlo;       // their current start position on the level being searched
     int top_launched;    // highest index level given its own launch (see launch_descend)
+    int bottom_launched; // lowest level that can be built (levels below it get no launch)
     const DevMeta* m;
     BatchMeta* bm;
     const uint64_t* lkeys;
@@ -587,6 +588,7 @@ struct RebuildArgs {
     uint32_t force_rebuild;  // 1: rebuild regardless; 2: initial build (not a batch)
     uint32_t st_cap;         // storage capacity (nodes, padding excluded)
     uint32_t smem_top;       // cap on pinned entries (<= kSmemTopMax)
+    uint32_t min_lb;         // lowest index level to build (>= 2)
     uint32_t* err;
 };
 cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
@@ -601,7 +603,7 @@ struct MIndex {           // one index of the set: its own arrays and device met
     uint32_t st_cap;      // storage nodes per buffer
     uint32_t idx_cap;     // index-layer entries
     uint32_t smem_top;    // the plain descent's pinned-entry cap (kept in DevMeta::Ls)
-    uint32_t pad_;
+    uint32_t min_lb;      // lowest index level to build (>= 2)
     HashParams hp;
 };
 

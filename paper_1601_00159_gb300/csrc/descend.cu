@@ -38,8 +38,10 @@ constexpr int kThreads = 256;
 constexpr uint32_t kFull = 0xffffffffu;
 
 // r = largest index >= lo-1 with K[r] <= q (K[lo] <= q unless lo is the head, 0).
-// Also returns D[r] (0 if r < 0 or no down array) and K[r].
-template <bool kDown>
+// Also returns D[r] (0 if r < 0 or no down array) and K[r]. Each round reads kWide
+// consecutive entries: 4 on index levels, 8 on the storage layer, whose gaps below the
+// lowest built level span (1/P)^(Lb-1) nodes.
+template <bool kDown, int kWide>
 __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, uint32_t lo, uint32_t lim,
                                           uint64_t q, int32_t& r_out, uint32_t& d_out, uint64_t& k_out,
                                           uint32_t* err) {
@@ -53,21 +55,25 @@ __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, 
             k_out = 0;
             return;
         }
-        const uint64_t k0 = K[i], k1 = K[i + 1], k2 = K[i + 2], k3 = K[i + 3];
-        uint32_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
-        if (kDown) {
-            d0 = D[i];
-            d1 = D[i + 1];
-            d2 = D[i + 2];
-            d3 = D[i + 3];
+        uint64_t kk[kWide];
+        uint32_t dd[kWide];
+#pragma unroll
+        for (int j = 0; j < kWide; ++j) {
+            kk[j] = K[i + j];
+            dd[j] = kDown ? D[i + j] : 0u;
         }
-        if (k0 > q) { r_out = (int32_t)i - 1; d_out = dprev; k_out = kprev; return; }
-        if (k1 > q) { r_out = (int32_t)i;     d_out = d0;    k_out = k0;    return; }
-        if (k2 > q) { r_out = (int32_t)i + 1; d_out = d1;    k_out = k1;    return; }
-        if (k3 > q) { r_out = (int32_t)i + 2; d_out = d2;    k_out = k2;    return; }
-        dprev = d3;
-        kprev = k3;
-        i += 4;
+#pragma unroll
+        for (int j = 0; j < kWide; ++j) {
+            if (kk[j] > q) {
+                r_out = (int32_t)(i + j) - 1;
+                d_out = j ? dd[j - 1] : dprev;
+                k_out = j ? kk[j - 1] : kprev;
+                return;
+            }
+        }
+        dprev = dd[kWide - 1];
+        kprev = kk[kWide - 1];
+        i += kWide;
     }
 }
 
@@ -116,7 +122,7 @@ __device__ __forceinline__ void warp_search(const uint64_t* K, const uint32_t* D
             }
         }
     }
-    if (scan) lane_scan<kDown>(K, D, lo, lim, q, r, dn, kr, err);
+    if (scan) lane_scan<kDown, kDown ? 4 : 8>(K, D, lo, lim, q, r, dn, kr, err);
 }
 
 // Largest index of K[0..n) (sorted, in shared memory) with key <= q, or -1.
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_top(DescendArgs a) {
             int32_t r = -1;
             uint32_t dn = 0;
             uint64_t kr = 0;
-            lane_scan<true>(a.lkeys + m->base[l], a.ldown + m->base[l], lo, m->n[l], q, r, dn, kr, a.err);
+            lane_scan<true, 4>(a.lkeys + m->base[l], a.ldown + m->base[l], lo, m->n[l], q, r, dn, kr, a.err);
             lo = (r >= 0) ? dn : 0u;
         }
         a.dlo[d] = lo;
@@ -351,7 +357,7 @@ cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
     // neither (the index grew) are walked by k_top
     const uint32_t capg = (uint32_t)num_sms * 16u;
     const uint32_t gblocks = need < capg ? need : capg;  // grid-stride over the distinct keys
-    for (int l = a.top_launched; l >= 2; --l) {
+    for (int l = a.top_launched; l >= a.bottom_launched; --l) {
         k_level<<<gblocks, kThreads, 0, s>>>(a, l);
         ++g_launches;
     }

@@ -70,6 +70,7 @@ struct pi_index {
     HashParams hp{};
     uint32_t rebuild_policy = 0, threshold_pct = 15;
     uint32_t smem_top = kSmemTopMax;  // pinned-entry cap
+    uint32_t min_lb = 2;              // lowest index level built
     uint32_t test_flags = 0;
     uint64_t launches = 0;            // kernels launched by the batch entry points
     uint32_t full_sort_left = 0;      // batches still sorted with all eight passes
@@ -469,6 +470,7 @@ RebuildArgs rebuild_args(pi_index* x, BatchMeta* bm, uint32_t size_ub, uint32_t 
     r.force_rebuild = force;
     r.st_cap = (uint32_t)x->st_cap;
     r.smem_top = x->smem_top;
+    r.min_lb = x->min_lb;
     r.err = &x->d_meta->error;
     return r;
 }
@@ -599,6 +601,7 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     da.dq = sc.dq;
     da.dlo = sc.dlo;
     da.top_launched = top_launched_for(x);
+    da.bottom_launched = (int)x->min_lb;
     da.m = x->d_meta;
     da.bm = bm;
     da.lkeys = x->lkeys;
@@ -714,6 +717,18 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
         if (cfg->rebuild_threshold_pct) x->threshold_pct = cfg->rebuild_threshold_pct;
         if (cfg->smem_top_entries && cfg->smem_top_entries < kSmemTopMax) x->smem_top = cfg->smem_top_entries;
         x->test_flags = cfg->test_flags;
+    }
+    // Lowest index level: the lowest l whose expected storage gap 2^(b (l - 1)) is at
+    // least 8 nodes, unless the caller picks one.
+    x->min_lb = 2;
+    while ((uint32_t)b * (x->min_lb - 1) < 3u) ++x->min_lb;
+    if (cfg && cfg->lowest_level) {
+        if (cfg->lowest_level < 2 || cfg->lowest_level > 16) {
+            g_last_error = PI_ERR_INVALID_ARG;
+            delete x;
+            return nullptr;
+        }
+        x->min_lb = cfg->lowest_level;
     }
     uint64_t st_cap = n + (n / 2 > kMinStorage ? n / 2 : kMinStorage);
     if (cfg && cfg->storage_capacity > st_cap) st_cap = cfg->storage_capacity;
@@ -1078,6 +1093,7 @@ MIndex mindex_of(const pi_index* x) {
     mi.st_cap = (uint32_t)x->st_cap;
     mi.idx_cap = (uint32_t)(x->idx_cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : x->idx_cap);
     mi.smem_top = x->smem_top;
+    mi.min_lb = x->min_lb;
     mi.hp = x->hp;
     return mi;
 }

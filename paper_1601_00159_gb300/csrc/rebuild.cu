@@ -195,16 +195,17 @@ __device__ bool level_bases_body(RebuildArgs a) {
         if (m->cnt[l] > 0) H = (uint32_t)l;
     // Lowest level that fits: drop bottom levels (the descent then scans longer storage
     // gaps) rather than overrun the capacity; the host grows it later.
+    const uint32_t Lb0 = a.min_lb > 2u ? a.min_lb : 2u;
     uint64_t need = 0;
-    for (uint32_t l = 2; l <= H; ++l) need += (uint64_t)m->cnt[l] + 1u;
-    uint32_t Lb = 2;
+    for (uint32_t l = Lb0; l <= H; ++l) need += (uint64_t)m->cnt[l] + 1u;
+    uint32_t Lb = Lb0;
     uint64_t fit = need;
     while (Lb <= H && fit > a.index_cap) {
         fit -= (uint64_t)m->cnt[Lb] + 1u;
         ++Lb;
     }
     m->index_need = (uint32_t)need;
-    m->grow_request = (Lb > 2) ? 1u : 0u;
+    m->grow_request = (Lb > Lb0) ? 1u : 0u;
     for (int l = 0; l < kLevelSlots; ++l) {
         m->n[l] = 0;
         m->base[l] = 0;

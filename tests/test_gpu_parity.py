@@ -103,7 +103,7 @@ def test_index_capacity_overflow_keeps_results_exact(orc_mod):
     """An index layer that does not fit drops its lowest levels (the descent then walks
     longer storage gaps); results stay exact and the capacity grows afterwards."""
     w = wl.random_small(5, 50000, 20000, 1 << 30, p=0.5, n_batches=4)
-    idx = make_index(w.keys, w.vals, w.promote_p, w.hash_seed, {"index_capacity": 3000})
+    idx = make_index(w.keys, w.vals, w.promote_p, w.hash_seed, {"index_capacity": 3000, "lowest_level": 2})
     orc = orc_mod.Oracle(w.keys, w.vals, w.promote_p, w.hash_seed)
     info0 = idx.info()
     assert info0["bottom_built"] > 2
@@ -111,6 +111,19 @@ def test_index_capacity_overflow_keeps_results_exact(orc_mod):
         assert_results_equal(run_batch(idx, batch), orc.execute(batch.ops, batch.keys, batch.vals), f"b{b}")
     info = assert_state_equal(idx, orc, "overflow end")
     assert info["bottom_built"] == 2 and info["index_capacity"] > 3000
+
+
+@pytest.mark.parametrize("lowest", [0, 2, 3, 5])
+@pytest.mark.parametrize("p", [0.5, 0.25])
+def test_lowest_built_level(orc_mod, lowest, p):
+    """Index layers whose lowest materialised level is 2 (every level, as in the paper),
+    3, 5 or the automatic choice: results, live pairs and the built levels stay exact,
+    and the descent scans the longer storage gaps below the lowest level."""
+    w = wl.random_small(60 + lowest, 30000, 20000, 1 << 40, p=p, n_batches=3)
+    cfg = {"lowest_level": lowest} if lowest else None
+    info = run_workload(orc_mod, w, cfg)
+    auto = 3 if p == 0.25 else 4
+    assert info["bottom_built"] == (lowest or auto)
 
 
 def test_edge_cases(orc_mod):
