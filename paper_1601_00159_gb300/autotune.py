@@ -30,7 +30,12 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--calls", type=int, default=8)
     ap.add_argument("--out", default=OUT)
+    ap.add_argument("--only", default="", help="time one variant, e.g. 32x8 (profiling runs)")
     args = ap.parse_args()
+    variants = VARIANTS
+    if args.only:
+        wv, bv = (int(x) for x in args.only.split("x"))
+        variants = [(wv, bv)]
     build.build()
     load_library()
     dev = torch.device("cuda")
@@ -53,7 +58,7 @@ def main():
                             torch.from_numpy(b.vals.view(np.int64)).to(dev),
                             torch.empty((len(b), 2), dtype=torch.int64, device=dev)))
         timings = {}
-        for (wp, bits) in VARIANTS:
+        for (wp, bits) in variants:
             idxs = []
             for i in members:
                 k = torch.from_numpy(w.keys[i].view(np.int64)).to(dev)
