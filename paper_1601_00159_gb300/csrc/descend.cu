@@ -39,14 +39,34 @@ constexpr uint32_t kFull = 0xffffffffu;
 
 // r = largest index >= lo-1 with K[r] <= q (K[lo] <= q unless lo is the head, 0).
 // Also returns D[r] (0 if r < 0 or no down array) and K[r]. Each round reads kWide
-// consecutive entries: 4 on index levels, 8 on the storage layer, whose gaps below the
-// lowest built level span (1/P)^(Lb-1) nodes.
+// consecutive entries with 16-byte loads (keys) and 8-byte loads (downs): 4 on index
+// levels, 8 on the storage layer, whose gaps below the lowest built level span
+// (1/P)^(Lb-1) nodes. The loads need &K[i] 16-byte aligned (K and D come from arrays
+// whose bases are, and a level may start at any entry), so an odd start steps back one
+// entry, which is <= q, or, at the head of a level, tests the head on its own.
 template <bool kDown, int kWide>
 __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, uint32_t lo, uint32_t lim,
                                           uint64_t q, int32_t& r_out, uint32_t& d_out, uint64_t& k_out,
                                           uint32_t* err) {
+    static_assert(kWide % 2 == 0, "whole 16-byte key pairs and 8-byte down pairs");
     uint32_t i = lo, dprev = 0;
     uint64_t kprev = 0;
+    if ((reinterpret_cast<uintptr_t>(K + i) & 15u) != 0) {
+        if (i > 0) {
+            --i;
+        } else {
+            const uint64_t k0 = K[0];
+            if (k0 > q) {
+                r_out = -1;
+                d_out = 0;
+                k_out = 0;
+                return;
+            }
+            kprev = k0;
+            dprev = kDown ? D[0] : 0u;
+            i = 1;
+        }
+    }
     for (;;) {
         if (i > lim) {
             atomicOr(err, kErrBounds);
@@ -57,10 +77,24 @@ __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, 
         }
         uint64_t kk[kWide];
         uint32_t dd[kWide];
+        const ulonglong2* kp = reinterpret_cast<const ulonglong2*>(K + i);
 #pragma unroll
-        for (int j = 0; j < kWide; ++j) {
-            kk[j] = K[i + j];
-            dd[j] = kDown ? D[i + j] : 0u;
+        for (int j = 0; j < kWide / 2; ++j) {
+            const ulonglong2 v = kp[j];
+            kk[2 * j] = v.x;
+            kk[2 * j + 1] = v.y;
+        }
+        if (kDown) {
+            const uint2* dp = reinterpret_cast<const uint2*>(D + i);
+#pragma unroll
+            for (int j = 0; j < kWide / 2; ++j) {
+                const uint2 v = dp[j];
+                dd[2 * j] = v.x;
+                dd[2 * j + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kWide; ++j) dd[j] = 0u;
         }
 #pragma unroll
         for (int j = 0; j < kWide; ++j) {
