@@ -56,6 +56,8 @@ def _load():
         lib.osl_num_levels.argtypes = [vp]
         lib.osl_export_level.restype = u64
         lib.osl_export_level.argtypes = [vp, i32, vp, u64]
+        lib.osl_range.restype = u64
+        lib.osl_range.argtypes = [vp, vp, vp, u64, vp, vp, vp, u64]
         lib.osl_destroy.restype = None
         lib.osl_destroy.argtypes = [vp]
         _lib = lib
@@ -114,6 +116,20 @@ class Oracle:
         v = np.zeros(n, np.uint64)
         _load().osl_export(self._h, _ptr(k), _ptr(v), n)
         return k, v
+
+    def range(self, lo, hi):
+        """Range search: (offsets[n + 1], keys, vals), query i's pairs in key order at
+        [offsets[i], offsets[i + 1])."""
+        lib = _load()
+        lo = np.ascontiguousarray(lo, dtype=np.uint64)
+        hi = np.ascontiguousarray(hi, dtype=np.uint64)
+        n = len(lo)
+        offs = np.zeros(n + 1, np.uint64)
+        total = int(lib.osl_range(self._h, _ptr(lo), _ptr(hi), n, _ptr(offs), None, None, 0))
+        k = np.zeros(total, np.uint64)
+        v = np.zeros(total, np.uint64)
+        lib.osl_range(self._h, _ptr(lo), _ptr(hi), n, _ptr(offs), _ptr(k), _ptr(v), total)
+        return offs, k, v
 
     def num_levels(self) -> int:
         return int(_load().osl_num_levels(self._h))

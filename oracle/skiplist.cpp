@@ -251,6 +251,33 @@ uint64_t osl_execute(void* h, const uint8_t* ops, const uint64_t* keys, const ui
 
 uint64_t osl_size(void* h) { return static_cast<SkipList*>(h)->count; }
 
+// Range search (Section 3.2.5), one query at a time: the live pairs with
+// lo[i] <= key <= hi[i], in key order. The walk finds the last node below lo[i] top-down
+// (its interception), then follows the bottom level until a key exceeds hi[i]; lo > hi
+// is an empty range. Writes offsets[0..n] (query i's pairs are [offsets[i],
+// offsets[i + 1]) of the output) and the first cap pairs; returns the total.
+uint64_t osl_range(void* h, const uint64_t* lo, const uint64_t* hi, uint64_t n, uint64_t* offsets,
+                   uint64_t* keys, uint64_t* vals, uint64_t cap) {
+    SkipList* s = static_cast<SkipList*>(h);
+    uint64_t total = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        offsets[i] = total;
+        if (lo[i] > hi[i]) continue;
+        Node* x = s->head;
+        for (int l = s->hmax - 1; l >= 0; --l)
+            while (x->next[l] && x->next[l]->key < lo[i]) x = x->next[l];
+        for (Node* c = x->next[0]; c && c->key <= hi[i]; c = c->next[0]) {
+            if (total < cap) {
+                keys[total] = c->key;
+                vals[total] = c->value;
+            }
+            ++total;
+        }
+    }
+    offsets[n] = total;
+    return total;
+}
+
 // Writes up to cap live pairs in key order; returns the number of live keys.
 uint64_t osl_export(void* h, uint64_t* keys, uint64_t* vals, uint64_t cap) {
     SkipList* s = static_cast<SkipList*>(h);

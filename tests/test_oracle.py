@@ -259,3 +259,36 @@ def test_distinct_keys_are_distinct_and_below_2_63():
     k = wl.distinct_keys(5, idx)
     assert len(np.unique(k)) == len(idx)
     assert int(k.max()) < (1 << 63)
+
+
+def test_range_search_brute_force(oracle_mod):
+    """Range search (Section 3.2.5) against a brute-force filter of a Python dict that
+    replays the same queries: for every range, the live pairs with lo <= key <= hi in key
+    order. Ranges include empty ones (lo > hi), single keys, the whole key space, bounds at
+    0 and 2^64-1, and bounds inside and outside the key set."""
+    rng = np.random.default_rng(11)
+    for trial in range(60):
+        n = int(rng.integers(0, 300))
+        keys = np.unique(rng.integers(0, 1 << 12, n, dtype=np.uint64))
+        vals = rng.integers(0, 1 << 62, len(keys), dtype=np.uint64)
+        b = wl.random_small(trial, 1, 200, 1 << 12, p=0.5, n_batches=1).batches[0]
+        orc = oracle_mod.Oracle(keys, vals, 0.25 if trial % 2 else 0.5, trial)
+        orc.execute(b.ops, b.keys, b.vals)
+        _, d = replay(keys, vals, [b])
+        live = sorted(d)
+        q = 40
+        lo = rng.integers(0, 1 << 12, q, dtype=np.uint64)
+        width = rng.integers(0, 300, q, dtype=np.uint64)
+        hi = lo + width
+        lo[:4] = [0, 5, 7, 0]
+        hi[:4] = [M64, 4, 7, 0]          # everything, lo > hi, a single key, [0, 0]
+        if live:
+            lo[4] = hi[4] = live[len(live) // 2]  # exactly one live key
+        offs, rk, rv = orc.range(lo, hi)
+        assert offs[0] == 0 and len(offs) == q + 1
+        for i in range(q):
+            exp = [k for k in live if int(lo[i]) <= k <= int(hi[i])]
+            got = rk[offs[i]:offs[i + 1]].tolist()
+            assert got == exp, (trial, i, int(lo[i]), int(hi[i]))
+            assert rv[offs[i]:offs[i + 1]].tolist() == [d[k] for k in exp]
+        orc.close()
