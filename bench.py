@@ -57,6 +57,10 @@ WORKLOADS = {
                     desc="serving: resident 2^26-key uint64 index (p=1/4); Poisson-arrival requests of 1..4096 "
                          "queries (log-uniform), 95% search / 5% insert, Zipf 0.9 keys; coalesced batches of at "
                          "most 2^20 queries, 3 in flight; p50/p99 request latency at 70% of the measured capacity"),
+    "range": dict(fn=None, n=1 << 24, q=None,
+                  desc="range search: 2^24 distinct uniform uint64 keys (p=1/4); batches of 2^16 range queries "
+                       "whose spans hold on average g = 1, 10, 100, 1000 keys (the paper's granularity); "
+                       "value at g = 100"),
 }
 TUNING = os.path.join(ROOT, "paper_1601_00159_gb300", "multi_tuning.json")
 
@@ -286,6 +290,32 @@ def run_reference_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_range(args):
+    """The oracle on the range workload: ranges of granularity 100 over the 2^24 keys
+    (built untimed), a bounded slice of 4096 ranges per step."""
+    import oracle
+    oracle.build()
+    keys = np.sort(wl.distinct_keys(6, np.arange(1 << 24)))
+    orc = oracle.Oracle(keys, wl.splitmix64(keys), 0.25, 6)
+    lo, hi = range_bounds(keys, 4096 * (args.warmup + args.steps), 100, 107)
+    t = None
+    for s_ in range(args.warmup + args.steps):
+        if s_ == args.warmup:
+            t = time.perf_counter()
+        orc.range(lo[s_ * 4096:(s_ + 1) * 4096], hi[s_ * 4096:(s_ + 1) * 4096])
+    el = time.perf_counter() - t
+    v = args.steps * 4096 / el / 1e6
+    orc.close()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mranges/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": "range", "desc": WORKLOADS["range"]["desc"]},
+            "cpu_baseline": {"value": v, "unit": "Mranges/s", "cores": 1, "kind": "oracle",
+                             "sample": "4096 ranges of granularity 100 per step"},
+            "e2e": {"value": v, "unit": "Mranges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -293,6 +323,8 @@ def run_reference(args, ws, rank):
         return run_reference_batching(args)
     if args.workload == "serving":
         return run_reference_serving(args)
+    if args.workload == "range":
+        return run_reference_range(args)
     spec = WORKLOADS[args.workload]
     w = spec["fn"]()
     batches = list(w.batches()) if callable(w.batches) else list(w.batches)
@@ -592,6 +624,101 @@ def run_serving(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def range_bounds(keys_sorted, q, g, seed):
+    """q ranges whose span covers about g consecutive keys: lo uniform over the key space,
+    hi = lo + g * (2^63 / n)."""
+    s = wl.stream_seed(seed, 61)
+    lo = wl.u64_stream(s, 0, q) >> np.uint64(1)
+    span = np.uint64(max(1, int(g * (1 << 63) // len(keys_sorted))))
+    return lo, lo + span
+
+
+def run_range(args, ws, rank, local):
+    """Range search (Section 3.2.5, the paper's granularity experiment): pi_range_search
+    on batches of range queries over a 2^24-key index."""
+    import torch
+    from paper_1601_00159_gb300 import Index, build, load_library
+    build.build()
+    load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = 1 << 24
+    keys = np.sort(wl.distinct_keys(6, np.arange(n)))
+    vals = wl.splitmix64(keys)
+    idx = Index(torch.from_numpy(keys.view(np.int64)).to(dev), torch.from_numpy(vals.view(np.int64)).to(dev),
+                0.25, 6)
+    stream = torch.cuda.current_stream()
+    grid = {}
+    for q in (8192, 1 << 16):
+        for g in (1, 10, 100, 1000):
+            lo, hi = range_bounds(keys, q, g, 7 + g)
+            dlo = torch.from_numpy(lo.view(np.int64)).to(dev)
+            dhi = torch.from_numpy(hi.view(np.int64)).to(dev)
+            cap = q * g * 2 + 4096
+            offs = torch.empty(q + 1, dtype=torch.int64, device=dev)
+            ko = torch.empty(cap, dtype=torch.int64, device=dev)
+            vo = torch.empty(cap, dtype=torch.int64, device=dev)
+
+            def call():
+                rc = idx.lib.pi_range_search(idx._h, dlo.data_ptr(), dhi.data_ptr(), q, offs.data_ptr(),
+                                             ko.data_ptr(), vo.data_ptr(), cap, ctypes_stream(stream))
+                assert rc == 0
+            for _ in range(args.warmup):
+                call()
+            torch.cuda.synchronize()
+            steps = max(3, min(args.steps, 200))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            total = int(offs[q].item())
+            assert total <= cap
+            grid[f"q{q}_g{g}"] = {"ms_per_batch": ms, "Mranges_per_s": q / (ms * 1e-3) / 1e6,
+                                  "Mresults_per_s": total / (ms * 1e-3) / 1e6, "results_per_range": total / q}
+    head = grid["q65536_g100"]
+    hbm, peak_kind = measured_peaks()
+    res = head["results_per_range"] * (1 << 16)
+    ab = res * (16 + 16 + 1) + (1 << 17) * (8 + 8 + 1)  # read pairs + meta, write pairs; bounds in
+    achieved = ab / (head["ms_per_batch"] * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": head["Mranges_per_s"], "unit": "Mranges/s", "n_gpus": ws,
+        "steps": max(3, min(args.steps, 200)), "warmup": args.warmup, "ms_per_step": head["ms_per_batch"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "range", "desc": WORKLOADS["range"]["desc"], "keys": n,
+                   "l2_flush": "none: the 2^24-key index (285 MB storage) exceeds L2"},
+        "grid": grid,
+        "roofline": {"bound": "hbm", "kernel": "pi_range_search call", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind, "traffic": None,
+                     "bytes_model": "per result: 8+8 B read, 1 B meta, 16 B written; per range: its two bounds"},
+        "gpu_launches": None,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        orc = oracle.Oracle(keys, vals, 0.25, 6)
+        lo, hi = range_bounds(keys, 1 << 16, 100, 107)
+        t = time.perf_counter()
+        done = 0
+        while done < len(lo) and time.perf_counter() - t < args.cpu_budget:
+            orc.range(lo[done:done + 4096], hi[done:done + 4096])
+            done += 4096
+        el = time.perf_counter() - t
+        orc.close()
+        line["cpu_baseline"] = {"value": done / el / 1e6, "unit": "Mranges/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{done} ranges of granularity 100 ({el:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    idx.close()
+
+
+def ctypes_stream(stream):
+    import ctypes
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
 def cpu_baseline_multi(w, rnd, budget_s: float = 20.0):
     """The oracle on a bounded sample of the batching workload: indices in order, each
     built (untimed) and then given its batch (timed), until the budget is spent."""
@@ -781,6 +908,8 @@ def main():
         run_batching(args, ws, rank, local)
     elif args.workload == "serving":
         run_serving(args, ws, rank, local)
+    elif args.workload == "range":
+        run_range(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

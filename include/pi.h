@@ -237,6 +237,22 @@ int pi_profile(pi_index_t* idx, int enable);
 int pi_profile_read(pi_index_t* idx, double* stage_ms_host, uint64_t* batches_host, pi_stream_t stream);
 
 /*
+ * pi_range_search -- range queries (Section 3.2.5) on the index as it stands after the
+ * batches enqueued before it on `stream` (read-only: it changes nothing).
+ *   lo, hi: device arrays of n inclusive bounds; lo > hi is an empty range; any 64-bit
+ *     value is a valid bound (2^64-1 as hi means "to the end").
+ *   offsets: device array of n + 1: query i's pairs are [offsets[i], offsets[i + 1]) of
+ *     the output, in key order; offsets[n] is the total.
+ *   keys_out, vals_out: device arrays of cap pairs (may be NULL when cap is 0). The pairs
+ *     of a query are written only when they all fit below cap; the caller reads
+ *     offsets[n] and calls again with room for the total if it exceeds cap.
+ * n <= PI_MAX_BATCH / 2. Errors as for pi_execute_batch. Enqueued on `stream` like a
+ * batch: the arrays are in use until the stream reaches the end of the call.
+ */
+int pi_range_search(pi_index_t* idx, const uint64_t* lo, const uint64_t* hi, uint64_t n, uint64_t* offsets,
+                    uint64_t* keys_out, uint64_t* vals_out, uint64_t cap, pi_stream_t stream);
+
+/*
  * ---------------------------------------------------------------------------------
  * Batching form: one batch for each of many independent indices in one persistent
  * launch. Algorithm 1 runs for every index of the set at once: each CTA takes a batch

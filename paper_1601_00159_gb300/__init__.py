@@ -22,7 +22,7 @@ PI_MAX_KEYS = (1 << 30) - 2
 EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
             "pi_last_error", "pi_status", "pi_info", "pi_export", "pi_export_level", "pi_profile",
             "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush",
-            "pi_multi_create", "pi_multi_execute", "pi_multi_destroy", "pi_multi_kernels_per_call",
+            "pi_range_search", "pi_multi_create", "pi_multi_execute", "pi_multi_destroy", "pi_multi_kernels_per_call",
             "pi_server_create", "pi_server_submit", "pi_server_wait", "pi_server_stats", "pi_server_replay",
             "pi_server_destroy"]
 PI_MULTI_MAX_CLASSES = 4
@@ -132,6 +132,8 @@ def load_library(path: str = LIB_PATH):
     lib.pi_profile.argtypes = [vp, i32]
     lib.pi_profile_read.restype = i32
     lib.pi_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), vp]
+    lib.pi_range_search.restype = i32
+    lib.pi_range_search.argtypes = [vp, vp, vp, u64, vp, vp, vp, u64, vp]
     lib.pi_multi_create.restype = vp
     lib.pi_multi_create.argtypes = [ctypes.POINTER(vp), ctypes.c_uint32, ctypes.POINTER(PiMultiConfig)]
     lib.pi_multi_execute.restype = i32
@@ -267,6 +269,29 @@ class Index:
         _chk(self.lib.pi_export_level(self._h, level, k.data_ptr(), d.data_ptr(), n.value, ctypes.byref(n),
                                       _stream_handle(stream)), "pi_export_level")
         return k[: n.value], d[: n.value]
+
+    def range_search(self, lo, hi, cap=None, stream=None):
+        """pi_range_search on int64 CUDA tensors of bounds: (offsets int64 [n + 1], keys,
+        vals), query i's pairs at [offsets[i], offsets[i + 1]). Calls again with more room
+        when the first capacity is too small (reading offsets[n] synchronises)."""
+        import torch
+        _check_dev(lo, torch.int64, "lo")
+        _check_dev(hi, torch.int64, "hi")
+        n = lo.numel()
+        if hi.numel() != n:
+            raise ValueError("lo and hi differ in length")
+        offs = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        cap = int(cap) if cap is not None else max(1024, 16 * n)
+        for _ in range(2):
+            k = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
+            v = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
+            _chk(self.lib.pi_range_search(self._h, lo.data_ptr(), hi.data_ptr(), n, offs.data_ptr(), k.data_ptr(),
+                                          v.data_ptr(), cap, _stream_handle(stream)), "pi_range_search")
+            total = int(offs[n].item())
+            if total <= cap:
+                return offs, k[:total], v[:total]
+            cap = total
+        raise RuntimeError("range results did not fit after resizing")
 
     def flush(self, stream=None):
         """pi_flush: make the stream wait for the index's background work."""

@@ -628,6 +628,29 @@ struct MultiArgs {
     DevMeta* mirror;          // copy of every processed index's meta, by index (may be null)
 };
 
+// Range search: both bounds of n queries, sorted and descended as 2n point lookups.
+struct RangeArgs {
+    const uint64_t* sk;       // sorted bounds
+    const uint32_t* sp;       // their payload: bound index (lo of query b, or hi of query b - n)
+    const uint32_t* loc;      // per distinct bound: storage nodes with key <= it
+    const uint8_t* flags;     // per distinct bound: bit 0 = a node with this key exists
+    const uint32_t* sub_pref; // descent sub-tile prefixes of the distinct bounds
+    const DevMeta* m;
+    const BatchMeta* bm;
+    Storage st;
+    uint32_t* start;          // [n] first node with key >= lo
+    uint32_t* end;            // [n] first node with key > hi
+    uint32_t* cnt;            // [n] live nodes in [start, end)
+    uint64_t* bsum;           // [n / 256 + 1] per-CTA sums, then their prefix
+    uint64_t* offsets;        // [n + 1] output (caller's)
+    uint64_t* keys_out;       // [cap] output (caller's)
+    uint64_t* vals_out;
+    uint64_t cap;
+    uint32_t n;
+    uint32_t* err;
+};
+cudaError_t launch_range(const RangeArgs& a, cudaStream_t s);
+
 uint64_t multi_scratch_bytes(uint32_t qcap);
 cudaError_t launch_multi(const MultiArgs& a, int warps, int radix_bits, uint32_t grid, cudaStream_t s);
 cudaError_t multi_occupancy(int warps, int radix_bits, int* blocks);

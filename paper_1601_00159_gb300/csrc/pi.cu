@@ -74,6 +74,13 @@ struct pi_index {
     uint32_t test_flags = 0;
     uint64_t launches = 0;            // kernels launched by the batch entry points
     uint32_t full_sort_left = 0;      // batches still sorted with all eight passes
+    // range search: both bounds back to back, per-query storage slices and counts
+    uint64_t* r_bounds = nullptr;
+    uint32_t* r_start = nullptr;
+    uint32_t* r_end = nullptr;
+    uint32_t* r_cnt = nullptr;
+    uint64_t* r_bsum = nullptr;
+    uint64_t r_cap = 0;
     DevMeta* d_meta = nullptr;
     BatchMeta* d_bm = nullptr;  // two per-batch counter blocks, alternating between batches
     uint32_t* d_dofs = nullptr;
@@ -300,6 +307,7 @@ void destroy(pi_index* x) {
         delete[] x->pev;
     }
     free_scratch(x->sc);
+    dfree(x->r_bounds); dfree(x->r_start); dfree(x->r_end); dfree(x->r_cnt); dfree(x->r_bsum);
     dfree(x->stg.ops); dfree(x->stg.keys); dfree(x->stg.vals); dfree(x->stg.res);
     free_storage(x->st);
     dfree(x->lkeys); dfree(x->ldown);
@@ -895,6 +903,93 @@ int pi_execute_batch_host(pi_index_t* x, const uint8_t* ops_host, const uint64_t
     int rc = pi_execute_batch(x, g.ops, g.keys, g.vals, n, g.res, stream);
     if (rc != PI_OK) return rc;
     e = cudaMemcpyAsync(results_host, g.res, n * sizeof(pi_result_t), cudaMemcpyDeviceToHost, s);
+    return map_cuda(e);
+}
+
+int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint64_t n, uint64_t* offsets,
+                    uint64_t* keys_out, uint64_t* vals_out, uint64_t cap, pi_stream_t stream) {
+    if (!x || !offsets) return PI_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n == 0) return map_cuda(cudaMemsetAsync(offsets, 0, sizeof(uint64_t), s));
+    if (!lo || !hi || n > PI_MAX_BATCH / 2 || (cap && (!keys_out || !vals_out))) return PI_ERR_INVALID_ARG;
+    cudaError_t e;
+    refresh_known(x);
+    if (int rc = sticky_error(x->known)) return rc;
+    const uint64_t nb = 2 * n;
+    if (nb > x->sc.cap) {  // sort and descent scratch for the 2n bounds (grows like a batch's)
+        wait_rebuild(x, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
+        x->rebuild_pending = false;
+        free_scratch(x->sc);
+        const uint64_t q = nb < 4096 ? 4096 : nb;
+        if ((e = alloc_scratch(x->sc, q)) != cudaSuccess) return map_cuda(e);
+        if ((e = ensure_desc(x, desc_need(q, x->st_cap))) != cudaSuccess) return map_cuda(e);
+    }
+    if (n > x->r_cap) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
+        dfree(x->r_bounds); dfree(x->r_start); dfree(x->r_end); dfree(x->r_cnt); dfree(x->r_bsum);
+        x->r_cap = 0;
+        if ((e = dalloc(&x->r_bounds, nb)) != cudaSuccess || (e = dalloc(&x->r_start, n)) != cudaSuccess ||
+            (e = dalloc(&x->r_end, n)) != cudaSuccess || (e = dalloc(&x->r_cnt, n)) != cudaSuccess ||
+            (e = dalloc(&x->r_bsum, n / 256 + 2)) != cudaSuccess)
+            return map_cuda(e);
+        x->r_cap = n;
+    }
+    const uint64_t l0 = g_launches;
+    cudaMemcpyAsync(x->r_bounds, lo, n * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(x->r_bounds + n, hi, n * 8, cudaMemcpyDeviceToDevice, s);
+    BatchMeta* bm = x->d_bm + (x->issued & 1u);  // the other block may still be read by the rebuild
+    cudaMemsetAsync(bm, 0, sizeof(BatchMeta), s);
+    const Scratch& sc = x->sc;
+    SortBuffers sb = sort_buffers(x, sc);
+    if ((e = launch_sort(nullptr, x->r_bounds, (uint32_t)nb, sb, bm, &x->d_meta->error, s, x->num_sms,
+                         sort_passes(x, nb))) != cudaSuccess)
+        return map_cuda(e);
+    wait_rebuild(x, s);
+    DescendArgs da{};
+    da.sk = sc.a_k;
+    da.sp = sc.a_p;
+    da.tile_max = sc.tile_max;
+    da.tile_pref = sc.tile_pref;
+    da.hq = sc.hq;
+    da.sub_cnt = sc.sub_cnt;
+    da.sub_pref = sc.sub_pref;
+    da.dq = sc.dq;
+    da.dlo = sc.dlo;
+    da.top_launched = top_launched_for(x);
+    da.bottom_launched = (int)x->min_lb;
+    da.m = x->d_meta;
+    da.bm = bm;
+    da.lkeys = x->lkeys;
+    da.ldown = x->ldown;
+    da.st = x->st;
+    da.loc = sc.loc;
+    da.flags = sc.flags;
+    da.val0 = sc.val0;
+    da.n = (uint32_t)nb;
+    da.err = &x->d_meta->error;
+    if ((e = launch_descend(da, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    RangeArgs ra{};
+    ra.sk = sc.a_k;
+    ra.sp = sc.a_p;
+    ra.loc = sc.loc;
+    ra.flags = sc.flags;
+    ra.sub_pref = sc.sub_pref;
+    ra.m = x->d_meta;
+    ra.bm = bm;
+    ra.st = x->st;
+    ra.start = x->r_start;
+    ra.end = x->r_end;
+    ra.cnt = x->r_cnt;
+    ra.bsum = x->r_bsum;
+    ra.offsets = offsets;
+    ra.keys_out = keys_out;
+    ra.vals_out = vals_out;
+    ra.cap = cap;
+    ra.n = (uint32_t)n;
+    ra.err = &x->d_meta->error;
+    e = launch_range(ra, s);
+    x->launches += g_launches - l0;
     return map_cuda(e);
 }
 
