@@ -85,7 +85,49 @@ def main():
         chosen.append((hi, wp, bits))
         table[f"class{c} (log2 size <= {hi}, {len(members)} indices)"] = timings
         print(f"class {c}: {len(members)} indices, ms per call {timings} -> {best}", flush=True)
-    out = {"classes": chosen, "ms_per_call": table, "device": torch.cuda.get_device_name(),
+    # The classes run concurrently in one call and share the SMs, so the per-class winners
+    # are checked jointly: every table whose classes take one of the two fastest variants
+    # of their class is timed on the whole workload, and the fastest table is kept.
+    joint = {}
+    if not args.only:
+        import itertools
+        tops = []
+        for c, hi in enumerate(BOUNDS):
+            key = next((k for k in table if k.startswith(f"class{c} ")), None)
+            ranked = sorted(table[key], key=table[key].get)[:2] if key else [f"{chosen[c][1]}x{chosen[c][2]}"]
+            tops.append([tuple(int(x) for x in r.split("x")) for r in ranked])
+        all_batches = []
+        for i, b in enumerate(rnd):
+            all_batches.append((i, torch.from_numpy(b.ops).to(dev), torch.from_numpy(b.keys.view(np.int64)).to(dev),
+                                torch.from_numpy(b.vals.view(np.int64)).to(dev),
+                                torch.empty((len(b), 2), dtype=torch.int64, device=dev)))
+        for combo in itertools.product(*tops):
+            cls = [(BOUNDS[c], combo[c][0], combo[c][1]) for c in range(len(BOUNDS))]
+            idxs = []
+            for i in range(len(sizes)):
+                k = torch.from_numpy(w.keys[i].view(np.int64)).to(dev)
+                v = torch.from_numpy(w.vals[i].view(np.int64)).to(dev)
+                cap = len(w.keys[i]) + len(rnd[i]) * (args.calls + 4)
+                idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], {"storage_capacity": cap}))
+            ms = MultiSet(idxs, cls)
+            for _ in range(2):
+                ms.execute(all_batches)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.calls):
+                ms.execute(all_batches)
+            e1.record()
+            torch.cuda.synchronize()
+            joint[json.dumps(cls)] = e0.elapsed_time(e1) / args.calls
+            ms.close()
+            for ix in idxs:
+                ix.close()
+            print(f"joint {cls}: {joint[json.dumps(cls)]:.3f} ms per call", flush=True)
+        best = min(joint, key=joint.get)
+        chosen = [tuple(c) for c in json.loads(best)]
+    out = {"classes": chosen, "ms_per_call": table, "joint_ms_per_call": joint,
+           "device": torch.cuda.get_device_name(),
            "workload": "batching (seed 4): indices of each class, their round-0 batches",
            "calls_timed": args.calls, "date": time.strftime("%Y-%m-%d")}
     with open(args.out, "w") as f:

@@ -34,6 +34,7 @@ constexpr uint32_t kMSeqMask = (1u << 30) - 1u;
 constexpr int kMI = 8;             // queries or nodes per thread in a chunked pass
 constexpr int kMK = 8;             // distinct keys per thread walked down together
 constexpr uint32_t kMTop = 2048;   // index entries staged in shared memory
+constexpr uint32_t kMSeg = 256;    // colliding segments one CTA orders after the prefix passes
 
 __device__ __forceinline__ void mstore_result(pi_result_t* res, uint32_t seq, uint64_t v, uint32_t st) {
     uint4 w;
@@ -50,6 +51,8 @@ struct MShared {
     uint32_t invalid;
     uint32_t item;
     uint32_t D, newc, dirty, changes, j1;
+    uint32_t nseg, overflow;
+    uint32_t seg[kMSeg];  // starts of segments the prefix fix-up orders
     int32_t tomb_delta;
     int32_t delta[kLevelSlots];
     SortPlan plan;
@@ -148,12 +151,76 @@ __device__ __forceinline__ void multi_scan(const uint64_t* K, const uint64_t (&q
     }
 }
 
+// One stable LSD pass over [lo, hi) of (src_k, src_p) by the kBits-bit digit at `shift`,
+// into the same range of (dst_k, dst_p): a histogram, its exclusive scan, then chunks of
+// kT x kMI elements ranked by warp ballots (elements in index order within a chunk).
 template <int kT, int kBits>
-__device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& s, uint8_t* dsm, MShared& sh) {
+__device__ void m_lsd_pass(const uint64_t* src_k, const uint32_t* src_p, uint64_t* dst_k, uint32_t* dst_p,
+                           uint32_t lo, uint32_t hi, uint32_t shift, uint8_t* dsm, uint32_t* tmp, uint32_t* err) {
     constexpr int kW = kT / 32;
     constexpr int kR = 1 << kBits;
     constexpr uint32_t kC = (uint32_t)kT * kMI;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t* whist = reinterpret_cast<uint32_t*>(dsm);  // [kW][kR]
+    uint32_t* sbase = whist + kW * kR;                   // [kR]
+    uint32_t* stot = sbase + kR;                         // [kR]
+    for (int d = tid; d < kW * kR; d += kT) whist[d] = 0;
+    for (int d = tid; d < kR; d += kT) sbase[d] = 0;
+    __syncthreads();
+    for (uint32_t i = lo + tid; i < hi; i += kT) atomicAdd(&sbase[(uint32_t)(src_k[i] >> shift) & (kR - 1)], 1u);
+    __syncthreads();
+    small_excl_scan<kT, kR>(sbase, tmp);
+    for (uint32_t c0 = lo; c0 < hi; c0 += kC) {
+        uint64_t key[kMI];
+        uint32_t pay[kMI], dig[kMI], rank[kMI];
+#pragma unroll
+        for (int k = 0; k < kMI; ++k) {
+            const uint32_t i = c0 + (uint32_t)warp * 32u * kMI + (uint32_t)k * 32u + (uint32_t)lane;
+            const bool v = i < hi;
+            key[k] = v ? src_k[i] : 0ull;
+            pay[k] = v ? src_p[i] : 0u;
+            dig[k] = v ? (uint32_t)(key[k] >> shift) & (kR - 1) : (uint32_t)kR;
+        }
+        warp_digit_ranks<kMI, kBits>(dig, rank, whist + warp * kR);
+        __syncthreads();
+        for (int d = tid; d < kR; d += kT) {
+            uint32_t total = 0;
+#pragma unroll 4
+            for (int w = 0; w < kW; ++w) {
+                const uint32_t cc = whist[w * kR + d];
+                whist[w * kR + d] = total;
+                total += cc;
+            }
+            stot[d] = total;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kMI; ++k) {
+            const uint32_t d = dig[k];
+            if (d < (uint32_t)kR) {
+                const uint32_t pos = lo + sbase[d] + whist[warp * kR + d] + rank[k];
+                if (pos < hi) {
+                    dst_k[pos] = key[k];
+                    dst_p[pos] = pay[k];
+                } else {
+                    atomicOr(err, kErrBounds);
+                }
+            }
+        }
+        __syncthreads();
+        for (int d = tid; d < kR; d += kT) {
+            sbase[d] += stot[d];
+#pragma unroll 4
+            for (int w = 0; w < kW; ++w) whist[w * kR + d] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+template <int kT, int kBits>
+__device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& s, uint8_t* dsm, MShared& sh) {
+    constexpr uint32_t kC = (uint32_t)kT * kMI;
+    const int tid = threadIdx.x, lane = tid & 31;
     const MIndex& X = a.idx[it.index];
     const uint32_t n = it.n;
     uint32_t* err = &X.m->error;
@@ -178,116 +245,157 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
     uint64_t* SV = X.st.vals[cur];
     uint8_t* SM = X.st.meta[cur];
 
-    // ---- pack: sort key (2^64-1 for invalid queries), payload op << 30 | arrival index
-    {
-        uint32_t mx[8], mn[8], inv = 0;
-#pragma unroll
-        for (int d = 0; d < 8; ++d) mx[d] = mn[d] = 0;
-        for (uint32_t i = tid; i < n; i += kT) {
-            const uint32_t op = it.ops[i];
-            const uint64_t k = it.keys[i];
-            const bool valid = op <= 2u && k != kMaxKey;
-            s.ka[i] = valid ? k : kMaxKey;
-            s.pa[i] = ((op & 3u) << 30) | i;
-            inv += valid ? 0u : 1u;
-            if (valid) {
-#pragma unroll
-                for (int d = 0; d < 8; ++d) {
-                    const uint32_t b = (uint32_t)(k >> (8 * d)) & 255u;
-                    mx[d] = max(mx[d], b);
-                    mn[d] = max(mn[d], 255u - b);
-                }
-            }
-        }
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            mx[d] = __reduce_max_sync(0xffffffffu, mx[d]);
-            mn[d] = __reduce_max_sync(0xffffffffu, mn[d]);
-        }
-        inv = __reduce_add_sync(0xffffffffu, inv);
-        if (lane == 0) {
-            if (inv) atomicAdd(&sh.invalid, inv);
-#pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                atomicMax(&sh.bmax[d], mx[d]);
-                atomicMax(&sh.bnmin[d], mn[d]);
-            }
-        }
-        __syncthreads();
-        if (tid == 0) plan_digits(sh.bmax, sh.bnmin, sh.invalid, n, 8u, sh.plan);
-        __syncthreads();
-    }
-    const uint32_t qv = n - sh.invalid;
-
-    // ---- sort: one stable pass per kBits-bit digit of every planned byte
+    // ---- pack + sort. Four passes on the most significant varying bytes, then the
+    // segments of equal leading bytes that hold different keys are ordered by the rest
+    // (as in the single-index sort). With more such segments than the list holds, the
+    // batch is packed again and sorted with every pass.
     uint64_t* K = s.ka;
     uint32_t* P = s.pa;
-    {
+    for (uint32_t budget = 4; budget <= 8; budget += 4) {
+        if (tid < 8) {
+            sh.bmax[tid] = 0;
+            sh.bnmin[tid] = 0;
+        }
+        if (tid == 0) {
+            sh.invalid = 0;
+            sh.nseg = 0;
+            sh.overflow = 0;
+        }
+        __syncthreads();
+        {
+            uint32_t mx[8], mn[8], inv = 0;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) mx[d] = mn[d] = 0;
+            for (uint32_t i = tid; i < n; i += kT) {
+                const uint32_t op = it.ops[i];
+                const uint64_t k = it.keys[i];
+                const bool valid = op <= 2u && k != kMaxKey;
+                s.ka[i] = valid ? k : kMaxKey;
+                s.pa[i] = ((op & 3u) << 30) | i;
+                inv += valid ? 0u : 1u;
+                if (valid) {
+#pragma unroll
+                    for (int d = 0; d < 8; ++d) {
+                        const uint32_t b = (uint32_t)(k >> (8 * d)) & 255u;
+                        mx[d] = max(mx[d], b);
+                        mn[d] = max(mn[d], 255u - b);
+                    }
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                mx[d] = __reduce_max_sync(0xffffffffu, mx[d]);
+                mn[d] = __reduce_max_sync(0xffffffffu, mn[d]);
+            }
+            inv = __reduce_add_sync(0xffffffffu, inv);
+            if (lane == 0) {
+                if (inv) atomicAdd(&sh.invalid, inv);
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    atomicMax(&sh.bmax[d], mx[d]);
+                    atomicMax(&sh.bnmin[d], mn[d]);
+                }
+            }
+            __syncthreads();
+            if (tid == 0) plan_digits(sh.bmax, sh.bnmin, sh.invalid, n, budget, sh.plan);
+            __syncthreads();
+        }
+        K = s.ka;
+        P = s.pa;
         uint64_t* K2 = s.kb;
         uint32_t* P2 = s.pb;
-        uint32_t* whist = reinterpret_cast<uint32_t*>(dsm);  // [kW][kR]
-        uint32_t* sbase = whist + kW * kR;                   // [kR]
-        uint32_t* stot = sbase + kR;                         // [kR]
-        const uint32_t npass = sh.plan.npass;
-        for (uint32_t j = 0; j < npass; ++j) {
+        for (uint32_t j = 0; j < sh.plan.npass; ++j)
             for (int sub = 0; sub < 8 / kBits; ++sub) {
-                const uint32_t shift = 8u * sh.plan.digit[j] + (uint32_t)(sub * kBits);
-                for (int d = tid; d < kW * kR; d += kT) whist[d] = 0;
-                for (int d = tid; d < kR; d += kT) sbase[d] = 0;
-                __syncthreads();
-                for (uint32_t i = tid; i < n; i += kT) atomicAdd(&sbase[(uint32_t)(K[i] >> shift) & (kR - 1)], 1u);
-                __syncthreads();
-                small_excl_scan<kT, kR>(sbase, sh.tmp);
-                for (uint32_t c0 = 0; c0 < n; c0 += kC) {
-                    uint64_t key[kMI];
-                    uint32_t pay[kMI], dig[kMI], rank[kMI];
-#pragma unroll
-                    for (int k = 0; k < kMI; ++k) {
-                        const uint32_t i = c0 + (uint32_t)warp * 32u * kMI + (uint32_t)k * 32u + (uint32_t)lane;
-                        const bool v = i < n;
-                        key[k] = v ? K[i] : 0ull;
-                        pay[k] = v ? P[i] : 0u;
-                        dig[k] = v ? (uint32_t)(key[k] >> shift) & (kR - 1) : (uint32_t)kR;
-                    }
-                    warp_digit_ranks<kMI, kBits>(dig, rank, whist + warp * kR);
-                    __syncthreads();
-                    for (int d = tid; d < kR; d += kT) {
-                        uint32_t total = 0;
-#pragma unroll 4
-                        for (int w = 0; w < kW; ++w) {
-                            const uint32_t cc = whist[w * kR + d];
-                            whist[w * kR + d] = total;
-                            total += cc;
-                        }
-                        stot[d] = total;
-                    }
-                    __syncthreads();
-#pragma unroll
-                    for (int k = 0; k < kMI; ++k) {
-                        const uint32_t d = dig[k];
-                        if (d < (uint32_t)kR) {
-                            const uint32_t pos = sbase[d] + whist[warp * kR + d] + rank[k];
-                            if (pos < n) {
-                                K2[pos] = key[k];
-                                P2[pos] = pay[k];
-                            } else {
-                                atomicOr(err, kErrBounds);
-                            }
-                        }
-                    }
-                    __syncthreads();
-                    for (int d = tid; d < kR; d += kT) {
-                        sbase[d] += stot[d];
-#pragma unroll 4
-                        for (int w = 0; w < kW; ++w) whist[w * kR + d] = 0;
-                    }
-                    __syncthreads();
-                }
+                m_lsd_pass<kT, kBits>(K, P, K2, P2, 0u, n, 8u * sh.plan.digit[j] + (uint32_t)(sub * kBits), dsm,
+                                      sh.tmp, err);
                 uint64_t* tk = K; K = K2; K2 = tk;
                 uint32_t* tp = P; P = P2; P2 = tp;
             }
+        if (!sh.plan.fix) break;
+        // segments of equal leading bytes that hold two keys: their starts, found from
+        // every key change inside one (galloping back, then bisecting)
+        const uint64_t pm = sh.plan.pmask;
+        for (uint32_t i = 1 + tid; i < n; i += kT) {
+            const uint64_t k0 = K[i - 1], k1 = K[i];
+            if (k0 == k1 || ((k0 ^ k1) & pm) != 0) continue;
+            const uint64_t mk = k1 & pm;
+            uint32_t in = i - 1;
+            uint64_t d = 1;
+            while (d <= in && (K[in - d] & pm) == mk) {
+                in -= (uint32_t)d;
+                d <<= 1;
+            }
+            uint32_t lo = d <= in ? in - (uint32_t)d + 1 : 0u, hi = in;
+            while (lo < hi) {
+                const uint32_t mid = lo + (hi - lo) / 2;
+                if ((K[mid] & pm) == mk) hi = mid;
+                else lo = mid + 1;
+            }
+            const uint32_t slot = atomicAdd(&sh.nseg, 1u);
+            if (slot < kMSeg) sh.seg[slot] = lo;
+            else sh.overflow = 1;
         }
+        __syncthreads();
+        if (sh.overflow) continue;  // pack again and sort with every pass
+        if (tid == 0) {  // ascending and unique (several key changes share a segment)
+            uint32_t m = sh.nseg, u = 0;
+            for (uint32_t a = 1; a < m; ++a) {
+                const uint32_t v = sh.seg[a];
+                uint32_t b = a;
+                while (b > 0 && sh.seg[b - 1] > v) {
+                    sh.seg[b] = sh.seg[b - 1];
+                    --b;
+                }
+                sh.seg[b] = v;
+            }
+            for (uint32_t a = 0; a < m; ++a)
+                if (a == 0 || sh.seg[a] != sh.seg[u - 1]) sh.seg[u++] = sh.seg[a];
+            sh.nseg = u;
+        }
+        __syncthreads();
+        const uint32_t nseg = sh.nseg;
+        for (uint32_t x = 0; x < nseg; ++x) {
+            const uint32_t s0 = sh.seg[x];
+            if (tid == 0) {  // the segment's end: gallop forward, then bisect
+                const uint64_t mk = K[s0] & pm;
+                uint32_t in = s0;
+                uint64_t d = 1;
+                while (d < n - in && (K[in + d] & pm) == mk) {
+                    in += (uint32_t)d;
+                    d <<= 1;
+                }
+                uint32_t lo = in + 1, hi = (d < n - in) ? in + (uint32_t)d : n;
+                while (lo < hi) {
+                    const uint32_t mid = lo + (hi - lo) / 2;
+                    if ((K[mid] & pm) == mk) lo = mid + 1;
+                    else hi = mid;
+                }
+                sh.j1 = lo;
+            }
+            __syncthreads();
+            const uint32_t e = sh.j1;
+            // stable passes over the other bytes, ping-ponging through the other buffer
+            uint64_t* A = K;
+            uint32_t* AP = P;
+            uint64_t* B = K2;
+            uint32_t* BP = P2;
+            for (uint32_t r = 0; r < sh.plan.nr; ++r)
+                for (int sub = 0; sub < 8 / kBits; ++sub) {
+                    m_lsd_pass<kT, kBits>(A, AP, B, BP, s0, e, 8u * sh.plan.rdig[r] + (uint32_t)(sub * kBits), dsm,
+                                          sh.tmp, err);
+                    uint64_t* tk = A; A = B; B = tk;
+                    uint32_t* tp = AP; AP = BP; BP = tp;
+                }
+            if (A != K)
+                for (uint32_t i = s0 + tid; i < e; i += kT) {
+                    K[i] = A[i];
+                    P[i] = AP[i];
+                }
+            __syncthreads();
+        }
+        break;
     }
+    const uint32_t qv = n - sh.invalid;
 
     // ---- distinct keys of the valid prefix [0, qv)
     {

@@ -157,3 +157,42 @@ def test_multi_rejects_bad_sets_and_batches():
         ms.execute([(0, ops, z, z, r), (0, ops, z, z, r)])  # twice in one call
     ms.close()
     a.close()
+
+
+@pytest.mark.parametrize("kind", ["few_segments", "overflow"])
+def test_multi_prefix_fixup(orc_mod, kind):
+    """Keys whose four leading varying bytes collide: a few segments of different keys
+    (ordered by the in-CTA fix-up), or so many that the CTA packs the batch again and
+    sorts it with every pass. Exact per index either way."""
+    import torch
+    from paper_1601_00159_gb300 import MultiSet
+    idxs, orcs, batches, host = [], [], [], []
+    for i in range(6):
+        s = wl.stream_seed(70 + i, 1)
+        n, q = 3000 + 500 * i, 20000 + 3000 * i
+        if kind == "few_segments":  # bytes 0..4 vary, byte 4 holds 4 bits: 28-bit prefixes
+            mk = lambda st, o, c: wl.u64_stream(st, o, c) & np.uint64((1 << 36) - 1)
+        else:  # bytes 0 and 4..7 vary, bytes 4..7 take 16 values: every prefix is shared
+            mk = lambda st, o, c: ((wl.u64_stream(st, o, c) & np.uint64(0xFF))
+                                   | ((wl.bounded(st, o + c, c, 16).astype(np.uint64) * np.uint64(0x01010101)) << np.uint64(32)))
+        keys = np.unique(mk(s, 0, n))
+        vals = wl.splitmix64(keys)
+        hs = 900 + i
+        idxs.append(make_index(keys, vals, 0.25, hs))
+        orcs.append(orc_mod.Oracle(keys, vals, 0.25, hs))
+        sb = wl.stream_seed(80 + i, 2)
+        ops = wl.bounded(sb, 0, q, 3).astype(np.uint8)
+        bk = np.where(wl.bounded(sb, q, q, 2) == 0, keys[wl.bounded(sb, 2 * q, q, len(keys))], mk(sb, 3 * q, q))
+        b = wl.Batch(ops, bk.astype(np.uint64), wl.u64_stream(sb, 5 * q, q))
+        res = torch.full((q, 2), -1, dtype=torch.int64, device="cuda")
+        batches.append((i, to_dev(b.ops, torch.uint8), to_dev(b.keys, torch.int64), to_dev(b.vals, torch.int64), res))
+        host.append((i, b, res))
+    for table in (None, [(32, 16, 4)]):
+        ms = MultiSet(idxs, table)
+        ms.execute(batches)
+        torch.cuda.synchronize()
+        for i, b, res in host:
+            assert_results_equal(results_np(res), orcs[i].execute(b.ops, b.keys, b.vals), f"{kind} {table} {i}")
+        ms.close()
+    for i, (ix, orc) in enumerate(zip(idxs, orcs)):
+        assert_state_equal(ix, orc, f"{kind} index {i}")
