@@ -219,19 +219,40 @@ __global__ void __launch_bounds__(1024) k_dscan(DescendArgs a) {
     __shared__ uint32_t s_tmp[33];
     if (block_sees_error(&a.m->error)) return;
     {
+        // Thread t owns sub-tiles [16t, 16t + 16): four 16-byte loads, kept in registers
+        // for the write-back (sub_cnt has room for whole groups of 16).
         const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
-        const uint32_t per = (nsub + 1023u) / 1024u;
-        const uint32_t t0 = min(threadIdx.x * per, nsub), t1 = min(t0 + per, nsub);
-        uint32_t sum = 0;
-        for (uint32_t t = t0; t < t1; ++t) sum += a.sub_cnt[t];
-        uint32_t tot;
-        uint32_t run = block_excl_sum<1024>(sum, s_tmp, &tot);
-        for (uint32_t t = t0; t < t1; ++t) {
-            const uint32_t v = a.sub_cnt[t];
-            a.sub_pref[t] = run;
-            run += v;
+        constexpr uint32_t kPer = 16;
+        uint32_t sum = 0, tot = 0, carry = 0;
+        for (uint32_t g0 = 0; g0 < nsub; g0 += 1024u * kPer) {
+            const uint32_t t0 = g0 + threadIdx.x * kPer;
+            uint32_t v[kPer];
+            if (t0 + kPer <= nsub) {
+                const uint4* p = reinterpret_cast<const uint4*>(a.sub_cnt + t0);
+#pragma unroll
+                for (uint32_t k = 0; k < kPer / 4; ++k) {
+                    const uint4 w = p[k];
+                    v[4 * k] = w.x;
+                    v[4 * k + 1] = w.y;
+                    v[4 * k + 2] = w.z;
+                    v[4 * k + 3] = w.w;
+                }
+            } else {
+#pragma unroll
+                for (uint32_t k = 0; k < kPer; ++k) v[k] = t0 + k < nsub ? a.sub_cnt[t0 + k] : 0u;
+            }
+            sum = 0;
+#pragma unroll
+            for (uint32_t k = 0; k < kPer; ++k) sum += v[k];
+            uint32_t run = carry + block_excl_sum<1024>(sum, s_tmp, &tot);
+#pragma unroll
+            for (uint32_t k = 0; k < kPer; ++k) {
+                if (t0 + k < nsub) a.sub_pref[t0 + k] = run;
+                run += v[k];
+            }
+            carry += tot;
         }
-        if (threadIdx.x == 0) a.bm->distinct = tot;
+        if (threadIdx.x == 0) a.bm->distinct = carry;
     }
     {
         const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
@@ -246,8 +267,6 @@ __global__ void __launch_bounds__(1024) k_dscan(DescendArgs a) {
         }
     }
 }
-
-// Dense distinct keys: one warp copies each sub-tile's keys to their dense place.
 __global__ void __launch_bounds__(kThreads) k_dpack(DescendArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel

@@ -19,6 +19,8 @@
 // deltas, so the layout (level bases, sentinels, staging split) is known before the
 // pass and the pass writes every entry exactly once.
 
+#include <cstddef>
+
 #include "common.cuh"
 
 namespace pi {
@@ -230,20 +232,47 @@ __device__ bool level_bases_body(RebuildArgs a) {
     return true;
 }
 
+// The body reads and writes the device meta and batch counters word by word on one
+// thread; it works on shared-memory copies loaded and stored by the whole warp, so its
+// dependent accesses cost shared-memory latency rather than L2 latency.
 __global__ void k_level_bases(RebuildArgs a) {
+    __shared__ DevMeta s_m;
+    __shared__ BatchMeta s_bm;
     __shared__ int s_go;
+    constexpr int kMW = sizeof(DevMeta) / 4, kBW = sizeof(BatchMeta) / 4;
+    static_assert(sizeof(DevMeta) % 4 == 0 && sizeof(BatchMeta) % 4 == 0, "word copies");
+    constexpr int kErrWord = offsetof(DevMeta, error) / 4;
+    uint32_t* sm = reinterpret_cast<uint32_t*>(&s_m);
+    uint32_t* sb = reinterpret_cast<uint32_t*>(&s_bm);
+    const uint32_t* gm = reinterpret_cast<const uint32_t*>(a.m);
+    const uint32_t* gb = reinterpret_cast<const uint32_t*>(a.bm);
+    for (int w = threadIdx.x; w < kMW; w += blockDim.x) sm[w] = gm[w];
+    for (int w = threadIdx.x; w < kBW; w += blockDim.x) sb[w] = gb[w];
     if (threadIdx.x == 0) s_go = 0;
     __syncthreads();
-    if (threadIdx.x == 0) s_go = level_bases_body(a) ? 1 : 0;
+    if (threadIdx.x == 0) {
+        RebuildArgs b = a;
+        b.m = &s_m;
+        b.bm = &s_bm;
+        s_go = level_bases_body(b) ? 1 : 0;
+    }
     __syncthreads();
+    // write back everything but the error word (errors are raised on the global copy)
+    uint32_t* gmw = reinterpret_cast<uint32_t*>(a.m);
+    for (int w = threadIdx.x; w < kMW; w += blockDim.x)
+        if (w != kErrWord) gmw[w] = sm[w];
+    if (threadIdx.x == 0) {
+        a.bm->merged = s_bm.merged;
+        a.bm->rebuild = s_bm.rebuild;
+    }
     if (!s_go) return;
     // sentinels of the built levels, one lane per level
-    const DevMeta* m = a.m;
-    const int l = (int)m->Lb + (int)threadIdx.x;
-    if (l <= (int)m->H) {
-        const uint32_t sidx = m->base[l] + m->n[l];
+    const DevMeta& m = s_m;
+    const int l = (int)m.Lb + (int)threadIdx.x;
+    if (l <= (int)m.H) {
+        const uint32_t sidx = m.base[l] + m.n[l];
         a.lkeys[sidx] = kMaxKey;
-        a.ldown[sidx] = (l > (int)m->Lb) ? m->n[l - 1] : m->size;
+        a.ldown[sidx] = (l > (int)m.Lb) ? m.n[l - 1] : m.size;
     }
 }
 
