@@ -204,6 +204,8 @@ typedef struct {
     uint64_t batches;        /* batches executed */
     uint64_t rebuilds;       /* index-layer rebuilds run (counts only when known) */
     uint64_t kernel_launches; /* CUDA kernels the batch entry points have launched so far */
+    uint64_t incremental_rebuilds; /* rebuilds that updated the previous levels (no storage
+                                      re-layout) rather than scanning the storage layer */
 } pi_info_t;
 int pi_info(pi_index_t* idx, pi_info_t* out_host, pi_stream_t stream);
 

@@ -84,7 +84,8 @@ class PiInfo(ctypes.Structure):
                 ("smem_low_level", ctypes.c_uint32), ("promote_shift", ctypes.c_uint32),
                 ("level_size", ctypes.c_uint64 * 34), ("storage_capacity", ctypes.c_uint64),
                 ("index_capacity", ctypes.c_uint64), ("batches", ctypes.c_uint64),
-                ("rebuilds", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+                ("rebuilds", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("incremental_rebuilds", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "level_size"}

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpi.so")
-SOURCES = ["sort.cu", "descend.cu", "apply.cu", "rebuild.cu", "range.cu", "multi.cu", "serve.cu", "pi.cu"]
+SOURCES = ["sort.cu", "descend.cu", "apply.cu", "rebuild.cu", "relevel.cu", "range.cu", "multi.cu", "serve.cu", "pi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

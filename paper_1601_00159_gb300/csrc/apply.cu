@@ -47,16 +47,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
     __shared__ int32_t s_delta[kLevelSlots];
     __shared__ int32_t s_tomb;
     __shared__ uint32_t s_changes, s_dirty;
+    __shared__ uint32_t s_chist[kLevelSlots];  // built-level membership changes by height
 
     const int tid = threadIdx.x;
     if (block_sees_error(&a.m->error)) return;
     const uint32_t n = a.n;
     const uint32_t qv = n - a.bm->invalid;
     const uint32_t cur = a.m->cur;
+    const uint32_t Lb = a.m->Lb;  // lowest built index level: changes below it leave the index alone
     uint64_t* SV = a.st.vals[cur];
     uint8_t* SM = a.st.meta[cur];
     const uint32_t tile = blockIdx.x;
-    if (tid < kLevelSlots) s_delta[tid] = 0;
+    if (tid < kLevelSlots) {
+        s_delta[tid] = 0;
+        s_chist[tid] = 0;
+    }
     if (tid == 0) {
         s_tomb = 0;
         s_changes = 0;
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
         }
         hidx = incl - nh + a.sub_pref[base / kSubTile];  // dense index of the next head
     }
-    uint32_t new_here = 0, new_mask = 0;
+    uint32_t new_here = 0, new_mask = 0, chg_here = 0, chg_mask = 0;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const uint32_t i = base + k;
@@ -171,7 +176,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
                     // the rebuild's per-tile count of the node's 4096-node tile
                     atomicAdd(&a.lcnt[(size_t)(l - 2) * a.lstride + (r >> 12)], fin_live ? 1u : 0xFFFFFFFFu);
                 }
-                if (h >= 2) s_dirty = 1;
+                if (h >= Lb) {
+                    s_dirty = 1;
+                    chg_here++;
+                    chg_mask |= 1u << k;
+                }
             }
         } else if (fin_live) {
             new_here++;
@@ -201,8 +210,30 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
             if (h >= 2) s_dirty = 1;
         }
     }
+    // Built-level membership changes: staged the same way, for an incremental rebuild.
+    uint32_t tile_chg = 0, cslot = 0;
+    if (__syncthreads_or(chg_here != 0)) cslot = block_excl_sum<kThreads>(chg_here, s_tmp, &tile_chg);
+    if (chg_mask) {
+        const uint32_t so = tile * kApplyTile;
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            if (!(chg_mask & (1u << k))) continue;
+            const uint32_t r = a.loc[dres[k]] - 1u;
+            const uint8_t mt = SM[r];  // as this kernel left it
+            const uint32_t h = mt & kHeightMask;
+            a.cstage.keys[so + cslot] = key[k];
+            a.cstage.pos[so + cslot] = r;
+            a.cstage.hl[so + cslot] = (uint8_t)(h | ((mt & kTomb) ? 0u : 0x80u));
+            ++cslot;
+            atomicAdd(&s_chist[h < (uint32_t)kLevelSlots ? h : kLevelSlots - 1], 1u);
+        }
+    }
     __syncthreads();
-    if (tid == 0) a.tile_new[tile] = tile_new;
+    if (tid == 0) {
+        a.tile_new[tile] = tile_new;
+        a.tile_chg[tile] = tile_chg;
+    }
+    if (tid < kLevelSlots && s_chist[tid]) atomicAdd(&a.bm->chg_hist[tid], s_chist[tid]);
     if (tid < kLevelSlots && s_delta[tid]) atomicAdd(&a.bm->delta[tid], s_delta[tid]);
     if (tid == 0) {
         if (s_tomb) atomicAdd(&a.bm->tomb_delta, s_tomb);
@@ -211,40 +242,65 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
     }
 }
 
-// Exclusive sum of the per-tile new-node counts (one CTA); total -> bm->new_count.
+// Exclusive sums of the per-tile new-node and level-change counts (one CTA); totals ->
+// bm->new_count and bm->nchg.
 __global__ void __launch_bounds__(1024) k_new_scan(ApplyArgs a) {
     __shared__ uint32_t s_tmp[33];
-    __shared__ uint32_t s_carry;
+    __shared__ uint32_t s_carry, s_ccarry;
     if (block_sees_error(&a.m->error)) return;
     const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
-    if (threadIdx.x == 0) s_carry = 0;
+    if (threadIdx.x == 0) {
+        s_carry = 0;
+        s_ccarry = 0;
+    }
     __syncthreads();
     for (uint32_t b0 = 0; b0 < ntiles; b0 += 1024) {
         const uint32_t i = b0 + threadIdx.x;
         const uint32_t v = i < ntiles ? a.tile_new[i] : 0u;
-        uint32_t tot;
+        const uint32_t c = i < ntiles ? a.tile_chg[i] : 0u;
+        uint32_t tot, ctot;
         const uint32_t ex = block_excl_sum<1024>(v, s_tmp, &tot);
-        if (i < ntiles) a.tile_pref[i] = s_carry + ex;  // tile_pref is free again
+        const uint32_t cex = block_excl_sum<1024>(c, s_tmp, &ctot);
+        if (i < ntiles) {
+            a.tile_pref[i] = s_carry + ex;  // tile_pref is free again
+            a.tile_chg_pref[i] = s_ccarry + cex;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) s_carry += tot;
+        if (threadIdx.x == 0) {
+            s_carry += tot;
+            s_ccarry += ctot;
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) a.bm->new_count = s_carry;
+    if (threadIdx.x == 0) {
+        a.bm->new_count = s_carry;
+        a.bm->nchg = s_ccarry;
+    }
 }
 
-// Packs each tile's staged new nodes to their place in key order.
+// Packs each tile's staged new nodes and level changes to their places in key order.
 __global__ void __launch_bounds__(kThreads) k_new_pack(ApplyArgs a) {
     if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
     const uint32_t tile = blockIdx.x;
-    const uint32_t c = a.tile_new[tile];
-    if (c == 0) return;
-    const uint32_t dst = a.tile_pref[tile];
     const uint32_t so = tile * kApplyTile;
-    for (uint32_t j = threadIdx.x; j < c; j += kThreads) {
-        a.nn.keys[dst + j] = a.stage.keys[so + j];
-        a.nn.vals[dst + j] = a.stage.vals[so + j];
-        a.nn.loc[dst + j] = a.stage.loc[so + j];
-        a.nn.height[dst + j] = a.stage.height[so + j];
+    const uint32_t c = a.tile_new[tile];
+    if (c) {
+        const uint32_t dst = a.tile_pref[tile];
+        for (uint32_t j = threadIdx.x; j < c; j += kThreads) {
+            a.nn.keys[dst + j] = a.stage.keys[so + j];
+            a.nn.vals[dst + j] = a.stage.vals[so + j];
+            a.nn.loc[dst + j] = a.stage.loc[so + j];
+            a.nn.height[dst + j] = a.stage.height[so + j];
+        }
+    }
+    const uint32_t cc = a.tile_chg[tile];
+    if (cc) {
+        const uint32_t dst = a.tile_chg_pref[tile];
+        for (uint32_t j = threadIdx.x; j < cc; j += kThreads) {
+            a.chg.keys[dst + j] = a.cstage.keys[so + j];
+            a.chg.pos[dst + j] = a.cstage.pos[so + j];
+            a.chg.hl[dst + j] = a.cstage.hl[so + j];
+        }
     }
 }
 

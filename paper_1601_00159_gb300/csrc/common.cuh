@@ -44,7 +44,9 @@ struct DevMeta {
     uint32_t rebuilds;     // rebuilds run
     uint32_t batches;      // batches run
     uint32_t sort_fix_big; // last batch: queries in key-prefix segments sorted by one CTA
-    uint32_t pad_;
+    uint32_t lcur;         // which of the two index-layer buffers holds the built levels
+    uint32_t levels_exact; // 1: the built levels hold exactly the live keys of their heights
+    uint32_t inc_rebuilds; // rebuilds that updated the previous levels instead of scanning
     uint32_t cnt[kLevelSlots];   // live keys with height >= l, kept current every batch
     uint32_t n[kLevelSlots];     // n[l]: size of built level l
     uint32_t base[kLevelSlots];  // built level l occupies [base[l], base[l] + n[l]] (+ sentinel)
@@ -126,6 +128,14 @@ struct BatchMeta {
     uint32_t bnmin[8];           // per key byte: 255 - its minimum over the batch
     uint32_t fix_big;            // queries in key-prefix segments longer than one warp
     SortPlan plan;
+    // incremental level rebuild (no storage re-layout): the levels are updated from the
+    // previous buffer and the batch's membership changes
+    uint32_t nchg;                    // packed membership changes
+    uint32_t chg_hist[kLevelSlots];   // changes by height
+    uint32_t inc;                     // 1: this batch's rebuild is incremental
+    uint32_t old_H, old_total;
+    uint32_t old_n[kLevelSlots], old_base[kLevelSlots];
+    uint32_t lst_off[kLevelSlots], lst_n[kLevelSlots];  // per-level change lists
 };
 
 // Storage layer, double buffered: [0] and [1]; DevMeta::cur picks the current one.
@@ -140,6 +150,14 @@ struct NewNodes {
     uint64_t* vals;
     uint32_t* loc;  // storage position + 1 of the largest stored key below it (0: front)
     uint8_t* height;
+};
+
+// Membership changes of the built index levels in one batch, in key order: nodes of
+// height >= the lowest built level whose liveness changed (no storage re-layout).
+struct LevelChanges {
+    uint64_t* keys;
+    uint32_t* pos;  // storage position
+    uint8_t* hl;    // height | 0x80 when the node became live (else it became delete-flagged)
 };
 
 struct HashParams {
@@ -533,8 +551,10 @@ struct DescendArgs {
     int bottom_launched; // lowest level that can be built (levels below it get no launch)
     const DevMeta* m;
     BatchMeta* bm;
-    const uint64_t* lkeys;
+    const uint64_t* lkeys;   // index-layer buffer 0 (DevMeta::lcur picks the one in use)
     const uint32_t* ldown;
+    const uint64_t* lkeys1;  // buffer 1
+    const uint32_t* ldown1;
     Storage st;
     uint32_t* loc;
     uint8_t* flags;
@@ -562,6 +582,10 @@ struct ApplyArgs {
     uint32_t* tile_new;   // per-tile new-node count
     const uint32_t* sub_pref;  // dense index of each 256-query sub-tile's first distinct key
     NewNodes stage;       // per-tile staging of new nodes (kApplyTile slots per tile)
+    LevelChanges cstage;  // per-tile staging of level membership changes
+    LevelChanges chg;     // the changes, packed in key order
+    uint32_t* tile_chg;   // per-tile change count
+    uint32_t* tile_chg_pref;
     uint32_t* lcnt;  // per-level per-tile live counts (see RebuildArgs)
     uint32_t lstride;
     uint32_t n;
@@ -575,8 +599,10 @@ struct RebuildArgs {
     NewNodes nn;
     DevMeta* m;
     BatchMeta* bm;
-    uint64_t* lkeys;
+    uint64_t* lkeys;      // index-layer buffer 0 (DevMeta::lcur picks the one in use)
     uint32_t* ldown;
+    uint64_t* lkeys1;     // buffer 1
+    uint32_t* ldown1;
     uint64_t* desc;       // look-back descriptors: max(tiles_merge, tiles_rebuild * 32)
     uint32_t* lcnt;       // per-level per-tile live counts, level-major, row stride lstride
     uint32_t* loff;       // rebuild: per-level per-tile offsets (scan output)
@@ -590,7 +616,14 @@ struct RebuildArgs {
     uint32_t smem_top;       // cap on pinned entries (<= kSmemTopMax)
     uint32_t min_lb;         // lowest index level to build (>= 2)
     uint32_t* err;
+    LevelChanges chg;        // the batch's level membership changes (key order)
+    uint64_t* lst_keys;      // per-level change lists (level l at bm->lst_off[l])
+    uint32_t* lst_pos;
+    int32_t* lst_pref;       // entries' running (inserts - deletes) before them; one extra at the end
+    uint8_t* lst_ins;
+    uint32_t lst_cap;        // entries the lists hold (an incremental rebuild needs them all)
 };
+cudaError_t launch_relevel(const RebuildArgs& a, cudaStream_t s, int num_sms);
 cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
 cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s);
 // ---------------------------------------------------------------------------------
@@ -598,8 +631,10 @@ cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s);
 struct MIndex {           // one index of the set: its own arrays and device meta
     DevMeta* m;
     Storage st;
-    uint64_t* lkeys;
+    uint64_t* lkeys;      // index-layer buffer 0 (DevMeta::lcur picks the one in use)
     uint32_t* ldown;
+    uint64_t* lkeys1;     // buffer 1
+    uint32_t* ldown1;
     uint32_t st_cap;      // storage nodes per buffer
     uint32_t idx_cap;     // index-layer entries
     uint32_t smem_top;    // the plain descent's pinned-entry cap (kept in DevMeta::Ls)

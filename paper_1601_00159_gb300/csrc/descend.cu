@@ -299,8 +299,8 @@ __global__ void __launch_bounds__(kThreads) k_top(DescendArgs a) {
             const uint32_t bk = ((E * 8u + 15u) / 16u) * 16u;
             const uint32_t bd = ((E * 4u + 15u) / 16u) * 16u;
             mbar_arrive_expect_tx(&s_bar, bk + bd);
-            bulk_g2s(s_k, a.lkeys, bk, &s_bar);
-            bulk_g2s(s_d, a.ldown, bd, &s_bar);
+            bulk_g2s(s_k, m->lcur ? a.lkeys1 : a.lkeys, bk, &s_bar);
+            bulk_g2s(s_d, m->lcur ? a.ldown1 : a.ldown, bd, &s_bar);
         }
         __syncthreads();
         if (!mbar_wait_bounded(&s_bar, 0, a.err)) s_fail = 1;
@@ -323,7 +323,8 @@ __global__ void __launch_bounds__(kThreads) k_top(DescendArgs a) {
             int32_t r = -1;
             uint32_t dn = 0;
             uint64_t kr = 0;
-            lane_scan<true, 4>(a.lkeys + m->base[l], a.ldown + m->base[l], lo, m->n[l], q, r, dn, kr, a.err);
+            lane_scan<true, 4>((m->lcur ? a.lkeys1 : a.lkeys) + m->base[l], (m->lcur ? a.ldown1 : a.ldown) + m->base[l],
+                               lo, m->n[l], q, r, dn, kr, a.err);
             lo = (r >= 0) ? dn : 0u;
         }
         a.dlo[d] = lo;
@@ -339,8 +340,8 @@ __global__ void __launch_bounds__(kThreads) k_level(DescendArgs a, int l) {
     if (l > top || l < (int)Lb) return;  // this level is pinned or not built
     const uint32_t D = a.bm->distinct;
     const uint32_t base = m->base[l], lim = m->n[l];
-    const uint64_t* K = a.lkeys + base;
-    const uint32_t* Dn = a.ldown + base;
+    const uint64_t* K = (m->lcur ? a.lkeys1 : a.lkeys) + base;
+    const uint32_t* Dn = (m->lcur ? a.ldown1 : a.ldown) + base;
     for (uint32_t d0 = blockIdx.x * kThreads; d0 < D; d0 += gridDim.x * kThreads) {
         const uint32_t d = d0 + threadIdx.x;
         const bool active = d < D;

@@ -244,6 +244,8 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
     uint64_t* SK = X.st.keys[cur];
     uint64_t* SV = X.st.vals[cur];
     uint8_t* SM = X.st.meta[cur];
+    uint64_t* LK = sh.m.lcur ? X.lkeys1 : X.lkeys;  // the index layer's buffer in use
+    uint32_t* LD = sh.m.lcur ? X.ldown1 : X.ldown;
 
     // ---- pack + sort. Four passes on the most significant varying bytes, then the
     // segments of equal leading bytes that hold different keys are ordered by the rest
@@ -438,8 +440,8 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
         uint32_t* td = reinterpret_cast<uint32_t*>(dsm + kMTop * sizeof(uint64_t));
         const uint32_t nst = (built && Lp <= H) ? m.base[Lp] + m.n[Lp] + 1u : 0u;
         for (uint32_t i = tid; i < nst; i += kT) {
-            tk[i] = X.lkeys[i];
-            td[i] = X.ldown[i];
+            tk[i] = LK[i];
+            td[i] = LD[i];
         }
         __syncthreads();
         for (uint32_t d0 = 0; d0 < D; d0 += (uint32_t)kT * kMK) {
@@ -474,9 +476,9 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
             if (built)
                 for (; l >= (int)Lb; --l) {
                     const uint32_t b = m.base[l];
-                    multi_scan(X.lkeys + b, q, pos, r, act, m.n[l], err);
+                    multi_scan(LK + b, q, pos, r, act, m.n[l], err);
 #pragma unroll
-                    for (int k = 0; k < kMK; ++k) pos[k] = r[k] >= 0 ? X.ldown[b + (uint32_t)r[k]] : 0u;
+                    for (int k = 0; k < kMK; ++k) pos[k] = r[k] >= 0 ? LD[b + (uint32_t)r[k]] : 0u;
                 }
             if (built) {
                 multi_scan(SK, q, pos, r, act, size, err);
@@ -769,6 +771,7 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
             m.smem_entries = (Ls <= H) ? m.base[Ls] + m.n[Ls] + 1u : 0u;
             m.updates = 0;
             m.rebuilds += 1;
+            m.levels_exact = 1;  // rebuilt in place from the storage layer
         }
         __syncthreads();
         const DevMeta& m = sh.m;
@@ -796,8 +799,8 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
                 for (int k = 0; k < kMI; ++k) {
                     if (!((mm >> k) & 1u)) continue;
                     if (o < m.n[Lb]) {
-                        X.lkeys[m.base[Lb] + o] = RK[i0 + k];
-                        X.ldown[m.base[Lb] + o] = i0 + k;
+                        LK[m.base[Lb] + o] = RK[i0 + k];
+                        LD[m.base[Lb] + o] = i0 + k;
                     }
                     ++o;
                 }
@@ -816,7 +819,7 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
 #pragma unroll
                     for (int k = 0; k < kMI; ++k) {
                         const uint32_t i = i0 + k;
-                        kk[k] = i < nl ? X.lkeys[bl + i] : 0ull;
+                        kk[k] = i < nl ? LK[bl + i] : 0ull;
                         if (i < nl && tower_height(kk[k], X.hp) >= l + 1u) mm |= 1u << k;
                     }
                     uint32_t tot;
@@ -825,8 +828,8 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
                     for (int k = 0; k < kMI; ++k) {
                         if (!((mm >> k) & 1u)) continue;
                         if (o < nu) {
-                            X.lkeys[bu + o] = kk[k];
-                            X.ldown[bu + o] = i0 + k;
+                            LK[bu + o] = kk[k];
+                            LD[bu + o] = i0 + k;
                         }
                         ++o;
                     }
@@ -837,8 +840,8 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
             }
             for (uint32_t l = Lb + tid; l <= H; l += kT) {  // sentinels
                 const uint32_t sidx = m.base[l] + m.n[l];
-                X.lkeys[sidx] = kMaxKey;
-                X.ldown[sidx] = (l > Lb) ? m.n[l - 1] : size;
+                LK[sidx] = kMaxKey;
+                LD[sidx] = (l > Lb) ? m.n[l - 1] : size;
             }
         }
         __syncthreads();
@@ -860,6 +863,7 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
         gm->grow_request = m.grow_request;
         gm->updates = m.updates;
         gm->rebuilds = m.rebuilds;
+        gm->levels_exact = m.levels_exact;
         gm->batches = m.batches;
         for (int l = 0; l < kLevelSlots; ++l) {
             gm->cnt[l] = m.cnt[l];

@@ -47,6 +47,15 @@ struct Scratch {
     uint32_t* toff = nullptr;  // radix sort: per-tile digit offsets
     uint8_t* ndig = nullptr;   // radix sort: next pass's digits
     uint32_t* fixmap = nullptr;  // radix sort: segment marks of the prefix fix-up
+    LevelChanges cstage{};       // apply: per-tile staging of level membership changes
+    LevelChanges chg{};          // apply: the changes, packed in key order
+    uint32_t* tile_chg = nullptr;
+    uint32_t* tile_chg_pref = nullptr;
+    uint64_t* lst_keys = nullptr;  // incremental rebuild: per-level change lists
+    uint32_t* lst_pos = nullptr;
+    int32_t* lst_pref = nullptr;
+    uint8_t* lst_ins = nullptr;
+    uint64_t lst_cap = 0;
     uint64_t* hq = nullptr;    // descent: distinct keys per sub-tile
     uint32_t* sub_cnt = nullptr;
     uint32_t* sub_pref = nullptr;
@@ -87,8 +96,10 @@ struct pi_index {
     uint32_t* d_count = nullptr;
     Storage st{};
     uint64_t st_cap = 0;  // nodes per buffer, padding excluded
-    uint64_t* lkeys = nullptr;
+    uint64_t* lkeys = nullptr;   // index-layer buffer 0
     uint32_t* ldown = nullptr;
+    uint64_t* lkeys1 = nullptr;  // buffer 1 (DevMeta::lcur picks the one in use)
+    uint32_t* ldown1 = nullptr;
     uint64_t idx_cap = 0;  // entries, padding excluded
     Scratch sc;
     Staging stg;
@@ -212,6 +223,9 @@ void free_scratch(Scratch& s) {
     dfree(s.stage.keys); dfree(s.stage.vals); dfree(s.stage.loc); dfree(s.stage.height);
     dfree(s.tile_max); dfree(s.tile_pref); dfree(s.tile_new);
     dfree(s.tcnt); dfree(s.toff); dfree(s.ndig); dfree(s.fixmap);
+    dfree(s.cstage.keys); dfree(s.cstage.pos); dfree(s.cstage.hl); dfree(s.chg.keys); dfree(s.chg.pos); dfree(s.chg.hl);
+    dfree(s.tile_chg); dfree(s.tile_chg_pref);
+    dfree(s.lst_keys); dfree(s.lst_pos); dfree(s.lst_pref); dfree(s.lst_ins);
     dfree(s.hq); dfree(s.sub_cnt); dfree(s.sub_pref); dfree(s.dq); dfree(s.dlo);
     s.cap = 0;
 }
@@ -235,6 +249,12 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     PI_TRY(dalloc(&s.tcnt, stiles * 256)); PI_TRY(dalloc(&s.toff, stiles * 256));
     PI_TRY(dalloc(&s.ndig, stiles * kSortTile + 16));
     PI_TRY(dalloc(&s.fixmap, c / 32 + 1));
+    PI_TRY(dalloc(&s.cstage.keys, cs)); PI_TRY(dalloc(&s.cstage.pos, cs)); PI_TRY(dalloc(&s.cstage.hl, cs));
+    PI_TRY(dalloc(&s.chg.keys, c)); PI_TRY(dalloc(&s.chg.pos, c)); PI_TRY(dalloc(&s.chg.hl, c));
+    PI_TRY(dalloc(&s.tile_chg, tiles)); PI_TRY(dalloc(&s.tile_chg_pref, tiles));
+    s.lst_cap = 2 * c + 64;
+    PI_TRY(dalloc(&s.lst_keys, s.lst_cap)); PI_TRY(dalloc(&s.lst_pos, s.lst_cap));
+    PI_TRY(dalloc(&s.lst_pref, s.lst_cap)); PI_TRY(dalloc(&s.lst_ins, s.lst_cap));
     const uint64_t nsub = (q + kSubTile - 1) / kSubTile + 1;
     PI_TRY(dalloc(&s.hq, nsub * kSubTile)); PI_TRY(dalloc(&s.sub_cnt, nsub)); PI_TRY(dalloc(&s.sub_pref, nsub));
     PI_TRY(dalloc(&s.dq, c)); PI_TRY(dalloc(&s.dlo, c));
@@ -310,7 +330,7 @@ void destroy(pi_index* x) {
     dfree(x->r_bounds); dfree(x->r_start); dfree(x->r_end); dfree(x->r_cnt); dfree(x->r_bsum);
     dfree(x->stg.ops); dfree(x->stg.keys); dfree(x->stg.vals); dfree(x->stg.res);
     free_storage(x->st);
-    dfree(x->lkeys); dfree(x->ldown);
+    dfree(x->lkeys); dfree(x->ldown); dfree(x->lkeys1); dfree(x->ldown1);
     dfree(x->desc); dfree(x->lcnt); dfree(x->loff); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
     if (x->h_mbox) cudaFreeHost(x->h_mbox);
     if (x->ev_applied) cudaEventDestroy(x->ev_applied);
@@ -411,30 +431,37 @@ cudaError_t grow_storage(pi_index* x, uint64_t need, cudaStream_t s) {
 
 cudaError_t grow_index(pi_index* x, uint64_t need, cudaStream_t s) {
     uint64_t cap = need + need / 4 + 4096;
-    uint64_t* nk = nullptr;
-    uint32_t* nd = nullptr;
+    uint64_t *nk = nullptr, *nk1 = nullptr;
+    uint32_t *nd = nullptr, *nd1 = nullptr;
     cudaError_t e = dalloc(&nk, cap + kPad);
     if (e == cudaSuccess) e = dalloc(&nd, cap + kPad);
+    if (e == cudaSuccess) e = dalloc(&nk1, cap + kPad);
+    if (e == cudaSuccess) e = dalloc(&nd1, cap + kPad);
     if (e != cudaSuccess) {
-        dfree(nk);
-        dfree(nd);
+        dfree(nk); dfree(nd); dfree(nk1); dfree(nd1);
         return e;
     }
+    // the levels in use move to buffer 0 of the new arrays (called with `known` current)
     const uint64_t used = x->known.index_total;
-    if (x->lkeys && used) {
-        cudaMemcpyAsync(nk, x->lkeys, used * 8, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(nd, x->ldown, used * 4, cudaMemcpyDeviceToDevice, s);
+    const uint64_t* ok = x->known.lcur ? x->lkeys1 : x->lkeys;
+    const uint32_t* od = x->known.lcur ? x->ldown1 : x->ldown;
+    if (ok && used) {
+        cudaMemcpyAsync(nk, ok, used * 8, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(nd, od, used * 4, cudaMemcpyDeviceToDevice, s);
     }
+    const uint32_t zero = 0;
+    cudaMemcpyAsync(&x->d_meta->lcur, &zero, sizeof(zero), cudaMemcpyHostToDevice, s);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-        dfree(nk);
-        dfree(nd);
+        dfree(nk); dfree(nd); dfree(nk1); dfree(nd1);
         return e;
     }
-    dfree(x->lkeys);
-    dfree(x->ldown);
+    dfree(x->lkeys); dfree(x->ldown); dfree(x->lkeys1); dfree(x->ldown1);
     x->lkeys = nk;
     x->ldown = nd;
+    x->lkeys1 = nk1;
+    x->ldown1 = nd1;
+    x->known.lcur = 0;
     x->idx_cap = cap;
     x->force_rebuild = true;
     return cudaSuccess;
@@ -467,6 +494,8 @@ RebuildArgs rebuild_args(pi_index* x, BatchMeta* bm, uint32_t size_ub, uint32_t 
     r.bm = bm;
     r.lkeys = x->lkeys;
     r.ldown = x->ldown;
+    r.lkeys1 = x->lkeys1;
+    r.ldown1 = x->ldown1;
     r.desc = x->desc;
     r.lcnt = x->lcnt;
     r.loff = x->loff;
@@ -501,6 +530,10 @@ constexpr uint64_t noalloc_bytes(uint64_t q) {
            + 3 * al256(tiles * 4)                                 // tile max / prefix / new
            + 2 * al256(stiles * 256 * 4) + al256(stiles * kSortTile + 16)  // tcnt, toff, ndig
            + al256((c / 32 + 1) * 4)                              // fixmap
+           + al256(cs * 8) + al256(cs * 4) + al256(cs)            // level-change staging
+           + al256(c * 8) + al256(c * 4) + al256(c)               // level changes
+           + 2 * al256(tiles * 4)                                 // per-tile change counts
+           + al256((2 * c + 64) * 8) + 2 * al256((2 * c + 64) * 4) + al256(2 * c + 64)  // lists
            + al256(nsub * kSubTile * 8) + 2 * al256(nsub * 4)     // hq, sub_cnt, sub_pref
            + al256(c * 8) + al256(c * 4);                         // dq, dlo
 }
@@ -529,6 +562,12 @@ uint64_t carve_scratch(uint8_t* base, uint64_t q, Scratch& s) {
     take(s.tile_max, tiles * 4); take(s.tile_pref, tiles * 4); take(s.tile_new, tiles * 4);
     take(s.tcnt, stiles * 256 * 4); take(s.toff, stiles * 256 * 4); take(s.ndig, stiles * kSortTile + 16);
     take(s.fixmap, (c / 32 + 1) * 4);
+    take(s.cstage.keys, cs * 8); take(s.cstage.pos, cs * 4); take(s.cstage.hl, cs);
+    take(s.chg.keys, c * 8); take(s.chg.pos, c * 4); take(s.chg.hl, c);
+    take(s.tile_chg, tiles * 4); take(s.tile_chg_pref, tiles * 4);
+    s.lst_cap = 2 * c + 64;
+    take(s.lst_keys, s.lst_cap * 8); take(s.lst_pos, s.lst_cap * 4); take(s.lst_pref, s.lst_cap * 4);
+    take(s.lst_ins, s.lst_cap);
     take(s.hq, nsub * kSubTile * 8); take(s.sub_cnt, nsub * 4); take(s.sub_pref, nsub * 4);
     take(s.dq, c * 8); take(s.dlo, c * 4);
     s.cap = q;
@@ -614,6 +653,8 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     da.bm = bm;
     da.lkeys = x->lkeys;
     da.ldown = x->ldown;
+    da.lkeys1 = x->lkeys1;
+    da.ldown1 = x->ldown1;
     da.st = x->st;
     da.loc = sc.loc;
     da.flags = sc.flags;
@@ -640,6 +681,10 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     aa.tile_new = sc.tile_new;
     aa.sub_pref = sc.sub_pref;
     aa.stage = sc.stage;
+    aa.cstage = sc.cstage;
+    aa.chg = sc.chg;
+    aa.tile_chg = sc.tile_chg;
+    aa.tile_chg_pref = sc.tile_chg_pref;
     aa.lcnt = x->lcnt;
     aa.lstride = x->lstride;
     aa.n = (uint32_t)n;
@@ -649,6 +694,12 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     prof_mark(x, 4, s);
     RebuildArgs ra = rebuild_args(x, bm, (uint32_t)size_ub, x->force_rebuild ? 1u : 0u);
     ra.nn = sc.nn;
+    ra.chg = sc.chg;
+    ra.lst_keys = sc.lst_keys;
+    ra.lst_pos = sc.lst_pos;
+    ra.lst_pref = sc.lst_pref;
+    ra.lst_ins = sc.lst_ins;
+    ra.lst_cap = (uint32_t)(sc.lst_cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : sc.lst_cap);
     if ((e = launch_merge(ra, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 5, s);
     if ((e = launch_level_bases(ra, s)) != cudaSuccess) return map_cuda(e);
@@ -667,6 +718,7 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     if ((e = launch_rebuild_prep(ra, ep, x->rs, x->num_sms)) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 8, x->rs);
     if ((e = launch_rebuild_write(ra, x->rs)) != cudaSuccess) return map_cuda(e);
+    if ((e = launch_relevel(ra, x->rs, x->num_sms)) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 9, x->rs);
     cudaEventRecord(x->ev_rebuilt, x->rs);
     x->rebuild_pending = true;
@@ -805,6 +857,8 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
         if (cfg && cfg->index_capacity) icap = cfg->index_capacity;
         if ((e = dalloc(&x->lkeys, icap + kPad)) != cudaSuccess) break;
         if ((e = dalloc(&x->ldown, icap + kPad)) != cudaSuccess) break;
+        if ((e = dalloc(&x->lkeys1, icap + kPad)) != cudaSuccess) break;
+        if ((e = dalloc(&x->ldown1, icap + kPad)) != cudaSuccess) break;
         x->idx_cap = icap;
         // 2. lay out and build the index layer
         cudaMemsetAsync(x->d_bm, 0, sizeof(BatchMeta), s);
@@ -962,6 +1016,8 @@ int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint6
     da.bm = bm;
     da.lkeys = x->lkeys;
     da.ldown = x->ldown;
+    da.lkeys1 = x->lkeys1;
+    da.ldown1 = x->ldown1;
     da.st = x->st;
     da.loc = sc.loc;
     da.flags = sc.flags;
@@ -1088,6 +1144,7 @@ int pi_info(pi_index_t* x, pi_info_t* out, pi_stream_t stream) {
     out->batches = m.batches;
     out->rebuilds = m.rebuilds;
     out->kernel_launches = x->launches;
+    out->incremental_rebuilds = m.inc_rebuilds;
     return sticky_error(m);
 }
 
@@ -1132,8 +1189,10 @@ int pi_export_level(pi_index_t* x, int level, uint64_t* keys_out, uint32_t* down
     *n_out_host = cnt;
     const uint64_t c = cnt < cap ? cnt : cap;
     if (c) {
-        cudaMemcpyAsync(keys_out, x->lkeys + m.base[level], c * 8, cudaMemcpyDeviceToDevice, s);
-        if (down_out) cudaMemcpyAsync(down_out, x->ldown + m.base[level], c * 4, cudaMemcpyDeviceToDevice, s);
+        const uint64_t* lk = m.lcur ? x->lkeys1 : x->lkeys;
+        const uint32_t* ld = m.lcur ? x->ldown1 : x->ldown;
+        cudaMemcpyAsync(keys_out, lk + m.base[level], c * 8, cudaMemcpyDeviceToDevice, s);
+        if (down_out) cudaMemcpyAsync(down_out, ld + m.base[level], c * 4, cudaMemcpyDeviceToDevice, s);
     }
     e = cudaStreamSynchronize(s);
     return map_cuda(e);
@@ -1185,6 +1244,8 @@ MIndex mindex_of(const pi_index* x) {
     mi.st = x->st;
     mi.lkeys = x->lkeys;
     mi.ldown = x->ldown;
+    mi.lkeys1 = x->lkeys1;
+    mi.ldown1 = x->ldown1;
     mi.st_cap = (uint32_t)x->st_cap;
     mi.idx_cap = (uint32_t)(x->idx_cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : x->idx_cap);
     mi.smem_top = x->smem_top;

@@ -188,9 +188,20 @@ __device__ bool level_bases_body(RebuildArgs a) {
         else rebuild = (uint64_t)m->updates * 100u >= (uint64_t)a.threshold_pct * (uint64_t)(size ? size : 1u);
     }
     bm->rebuild = rebuild ? 1u : 0u;
-    if (!rebuild) return false;
+    if (!rebuild) {
+        if (bm->index_dirty) m->levels_exact = 0;  // deferred: the levels now lag the storage layer
+        return false;
+    }
     m->updates = 0;
     m->rebuilds += 1;
+    // the layout being replaced, for an incremental rebuild
+    const uint32_t oH = m->H, oLb = m->Lb;
+    bm->old_H = oH;
+    bm->old_total = m->index_total;
+    for (int l = 0; l < kLevelSlots; ++l) {
+        bm->old_n[l] = m->n[l];
+        bm->old_base[l] = m->base[l];
+    }
 
     uint32_t H = 1;
     for (int l = 2; l < kLevelSlots; ++l)
@@ -228,6 +239,25 @@ __device__ bool level_bases_body(RebuildArgs a) {
     }
     m->Ls = Ls;
     m->smem_entries = (Ls <= H) ? m->base[Ls] + m->n[Ls] + 1u : 0u;
+    // Incremental when the storage layer kept its layout and the old levels are exact:
+    // the new levels are the old ones plus the batch's membership changes, written to
+    // the other buffer. The per-level change lists must fit their arrays.
+    bool inc = !merged && a.force_rebuild == 0 && m->levels_exact && Lb == oLb && oLb <= oH && Lb <= H;
+    if (inc) {
+        const uint32_t Hm = H > oH ? H : oH;
+        uint64_t lists = 0, ge = 0;
+        for (int l = kLevelSlots - 1; l >= (int)Lb; --l) {
+            ge += bm->chg_hist[l];
+            if ((uint32_t)l <= Hm) lists += ge + 1u;
+        }
+        inc = lists <= a.lst_cap;
+    }
+    bm->inc = inc ? 1u : 0u;
+    if (inc) {
+        m->lcur ^= 1u;
+        m->inc_rebuilds += 1;
+    }
+    m->levels_exact = 1;
     __threadfence_block();
     return true;
 }
@@ -261,18 +291,16 @@ __global__ void k_level_bases(RebuildArgs a) {
     uint32_t* gmw = reinterpret_cast<uint32_t*>(a.m);
     for (int w = threadIdx.x; w < kMW; w += blockDim.x)
         if (w != kErrWord) gmw[w] = sm[w];
-    if (threadIdx.x == 0) {
-        a.bm->merged = s_bm.merged;
-        a.bm->rebuild = s_bm.rebuild;
-    }
+    uint32_t* gbw = reinterpret_cast<uint32_t*>(a.bm);
+    for (int w = threadIdx.x; w < kBW; w += blockDim.x) gbw[w] = sb[w];  // nothing else runs on it now
     if (!s_go) return;
     // sentinels of the built levels, one lane per level
     const DevMeta& m = s_m;
     const int l = (int)m.Lb + (int)threadIdx.x;
     if (l <= (int)m.H) {
         const uint32_t sidx = m.base[l] + m.n[l];
-        a.lkeys[sidx] = kMaxKey;
-        a.ldown[sidx] = (l > (int)m.Lb) ? m.n[l - 1] : m.size;
+        (m.lcur ? a.lkeys1 : a.lkeys)[sidx] = kMaxKey;
+        (m.lcur ? a.ldown1 : a.ldown)[sidx] = (l > (int)m.Lb) ? m.n[l - 1] : m.size;
     }
 }
 
@@ -339,7 +367,7 @@ __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a, uint32_t e
     __shared__ int s_ok;
     const DevMeta* m = a.m;
     if (block_sees_error(&m->error)) return;
-    if (!a.bm->rebuild) return;
+    if (!a.bm->rebuild || a.bm->inc) return;  // an incremental rebuild needs no tile offsets
     const uint32_t H = m->H, Lb = m->Lb, size = m->size;
     const uint32_t l = Lb + blockIdx.y;
     if (H < Lb || size == 0 || l > H) return;
@@ -419,9 +447,11 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const DevMeta* m = a.m;
     if (block_sees_error(&m->error)) return;
-    if (!a.bm->rebuild) return;
+    if (!a.bm->rebuild || a.bm->inc) return;  // the incremental path writes the levels instead
     const uint32_t H = m->H, Lb = m->Lb, size = m->size, cur = m->cur;
     if (H < Lb || size == 0) return;
+    uint64_t* LK = m->lcur ? a.lkeys1 : a.lkeys;  // the index layer's buffer in use
+    uint32_t* LD = m->lcur ? a.ldown1 : a.ldown;
     const uint32_t ntiles = (size + kNodes - 1) / kNodes;
     const uint32_t tile = blockIdx.x;
     if (tile >= ntiles) return;
@@ -523,8 +553,8 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
                 const uint32_t p = base + j;
                 if (p < s_n[l]) {
                     const uint32_t g = s_base[l] + p;
-                    a.lkeys[g] = TK[node];
-                    a.ldown[g] = (l == Lb) ? ts + node : prev_base + (e >> 16);
+                    LK[g] = TK[node];
+                    LD[g] = (l == Lb) ? ts + node : prev_base + (e >> 16);
                 } else {
                     atomicOr(a.err, kErrBounds);
                 }

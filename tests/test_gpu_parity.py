@@ -196,3 +196,30 @@ def test_create_rejects_bad_arguments():
     k2 = to_dev(np.array([1, 2], np.uint64), torch.int64)
     with pytest.raises(PiError):
         Index(k2, v, 0.3, 1)
+
+
+@pytest.mark.parametrize("lowest,p", [(2, 0.5), (3, 0.25), (0, 0.25)])
+def test_incremental_level_rebuild(orc_mod, lowest, p):
+    """Batches that only delete, revive and overwrite existing keys leave the storage
+    layout alone until delete-flagged nodes pass 1/8 of it, so most rebuilds update the
+    previous levels with the batch's membership changes. Every batch's results, live
+    pairs and built levels (with down pointers) must equal the oracle's."""
+    n = 40000
+    keys = wl.distinct_keys(77, np.arange(n))
+    vals = wl.splitmix64(keys)
+    cfg = {"lowest_level": lowest} if lowest else None
+    idx = make_index(keys, vals, p, 12, cfg)
+    orc = orc_mod.Oracle(keys, vals, p, 12)
+    for b in range(8):
+        s = wl.stream_seed(77, 100 + b)
+        q = 9000
+        u = wl.bounded(s, 0, q, 100)
+        ops = np.where(u < 5, 2, np.where(u < 45, 1, 0)).astype(np.uint8)  # 5% delete, 40% (re)insert
+        bk = keys[wl.bounded(s, q, q, n)]
+        batch = wl.Batch(ops, bk.astype(np.uint64), wl.u64_stream(s, 2 * q, q))
+        assert_results_equal(run_batch(idx, batch), orc.execute(batch.ops, batch.keys, batch.vals), f"b{b}")
+        assert_state_equal(idx, orc, f"b{b}")
+    info = idx.info()
+    assert info["incremental_rebuilds"] >= 4, info["incremental_rebuilds"]
+    idx.close()
+    orc.close()
