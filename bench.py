@@ -754,8 +754,10 @@ def run_ours(args, ws, rank, local):
         kw["n" if args.workload != "mid" else "n0"] = 1 << args.keys_log2
     if args.batch_log2:
         kw["q"] = 1 << args.batch_log2
-    w = spec["fn"](**kw)
     n_distinct_batches = 1 if args.workload == "tiny" else min(args.steps + args.warmup, args.batches)
+    if args.workload in ("mid", "skewed"):
+        kw["n_batches"] = max(n_distinct_batches, 2)
+    w = spec["fn"](**kw)
     gen = w.batches() if callable(w.batches) else iter(w.batches)
     host_batches = [next(gen) for _ in range(n_distinct_batches)]
     gen_s = time.time() - t_gen

@@ -699,7 +699,7 @@ extern thread_local uint64_t g_launches;
 
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
 cudaError_t launch_rebuild_prep(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
-cudaError_t launch_rebuild_write(const RebuildArgs& a, cudaStream_t s);
+cudaError_t launch_rebuild_write(const RebuildArgs& a, cudaStream_t s, int num_sms);
 
 // Bulk build: sorted (key, payload) -> storage layer (last duplicate wins) + counts.
 struct CreateArgs {

@@ -717,7 +717,7 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     prof_mark(x, 7, x->rs);
     if ((e = launch_rebuild_prep(ra, ep, x->rs, x->num_sms)) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 8, x->rs);
-    if ((e = launch_rebuild_write(ra, x->rs)) != cudaSuccess) return map_cuda(e);
+    if ((e = launch_rebuild_write(ra, x->rs, x->num_sms)) != cudaSuccess) return map_cuda(e);
     if ((e = launch_relevel(ra, x->rs, x->num_sms)) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 9, x->rs);
     cudaEventRecord(x->ev_rebuilt, x->rs);

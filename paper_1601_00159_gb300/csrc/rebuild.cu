@@ -446,31 +446,33 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const DevMeta* m = a.m;
+    if (a.bm->inc || !a.bm->rebuild) return;  // the incremental path writes the levels instead
     if (block_sees_error(&m->error)) return;
-    if (!a.bm->rebuild || a.bm->inc) return;  // the incremental path writes the levels instead
     const uint32_t H = m->H, Lb = m->Lb, size = m->size, cur = m->cur;
     if (H < Lb || size == 0) return;
     uint64_t* LK = m->lcur ? a.lkeys1 : a.lkeys;  // the index layer's buffer in use
     uint32_t* LD = m->lcur ? a.ldown1 : a.ldown;
     const uint32_t ntiles = (size + kNodes - 1) / kNodes;
-    const uint32_t tile = blockIdx.x;
-    if (tile >= ntiles) return;
-    const uint32_t ts = tile * kNodes;
-    const uint32_t cnt = min((uint32_t)kNodes, size - ts);
-    if (tid == 0) {
-        s_ok = 1;
-        mbar_init(&s_bar, 1);
-        const uint32_t bm_ = ((cnt + 15u) / 16u) * 16u;
-        mbar_arrive_expect_tx(&s_bar, bm_);
-        bulk_g2s(s_meta, a.st.meta[cur] + ts, bm_, &s_bar);
-    }
     if (tid < kLevelSlots) {
         s_base[tid] = m->base[tid];
         s_n[tid] = m->n[tid];
     }
+    if (tid == 0) mbar_init(&s_bar, 1);
+    // A persistent loop over the tiles: the barrier's phase flips with every tile's copy.
+    uint32_t phase = 0;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, phase ^= 1u) {
+    const uint32_t ts = tile * kNodes;
+    const uint32_t cnt = min((uint32_t)kNodes, size - ts);
+    __syncthreads();  // the previous tile is done with shared memory
+    if (tid == 0) {
+        s_ok = 1;
+        const uint32_t bm_ = ((cnt + 15u) / 16u) * 16u;
+        mbar_arrive_expect_tx(&s_bar, bm_);
+        bulk_g2s(s_meta, a.st.meta[cur] + ts, bm_, &s_bar);
+    }
     const uint64_t* TK = a.st.keys[cur] + ts;  // this tile's keys
     __syncthreads();
-    if (!mbar_wait_bounded(&s_bar, 0, a.err)) s_ok = 0;
+    if (!mbar_wait_bounded(&s_bar, phase, a.err)) s_ok = 0;
     const uint32_t w0 = (uint32_t)warp * kWarpNodes;
     const uint32_t nb = w0 + (uint32_t)lane * 16u;
     uint32_t hw[4];
@@ -505,7 +507,7 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
     }
     __syncthreads();
     if (!s_ok) {
-        if (tid == 0) mbar_wait_bounded(&s_bar, 0, a.err);  // let the copy land
+        if (tid == 0) mbar_wait_bounded(&s_bar, phase, a.err);  // let the copy land
         return;
     }
     uint32_t wbase = 0;  // first position of this warp in level Lb + lane
@@ -566,6 +568,7 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
         nlist = nnext;
         prev_base = base;
     }
+    }  // tiles
 }
 
 // ---------------------------------------------------------------------------------
@@ -723,7 +726,7 @@ cudaError_t launch_rebuild_prep(const RebuildArgs& a, uint32_t& epoch, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_rebuild_write(const RebuildArgs& a, cudaStream_t s) {
+cudaError_t launch_rebuild_write(const RebuildArgs& a, cudaStream_t s, int num_sms) {
     static bool attr_set = false;
     const int dyn = (int)(kMetaBytes + 8 * kWarpNodes * 4);
     if (!attr_set) {
@@ -732,14 +735,15 @@ cudaError_t launch_rebuild_write(const RebuildArgs& a, cudaStream_t s) {
         attr_set = true;
     }
     const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
-    k_rebuild_write<<<tiles, kThreads, dyn, s>>>(a);
+    const uint32_t cap = (uint32_t)num_sms * 8u;  // persistent: the CTAs resident at once
+    k_rebuild_write<<<tiles < cap ? tiles : cap, kThreads, dyn, s>>>(a);
     ++g_launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
     cudaError_t e = launch_rebuild_prep(a, epoch, s, num_sms);
-    return e != cudaSuccess ? e : launch_rebuild_write(a, s);
+    return e != cudaSuccess ? e : launch_rebuild_write(a, s, num_sms);
 }
 
 cudaError_t launch_create_storage(const CreateArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {

@@ -20,7 +20,7 @@ namespace pi {
 namespace {
 
 constexpr int kT = 256;
-constexpr uint32_t kItems = 16;
+constexpr uint32_t kItems = 8;
 constexpr uint32_t kTile = kT * kItems;  // old entries per tile
 constexpr uint32_t kSlice = 512;         // list entries staged in shared memory per tile and level
 
@@ -28,6 +28,25 @@ __device__ __forceinline__ uint32_t ge_count(const BatchMeta* bm, uint32_t l) {
     uint32_t c = 0;
     for (uint32_t h = l; h < (uint32_t)kLevelSlots; ++h) c += bm->chg_hist[h];
     return c;
+}
+
+// Three independent lower bounds advanced in lockstep, so their dependent loads overlap
+// (an insert needs its place in two old levels and in the change list below).
+__device__ __forceinline__ void lb3(const uint64_t* K0, uint32_t n0, const uint64_t* K1, uint32_t n1,
+                                    const uint64_t* K2, uint32_t n2, uint64_t x, uint32_t& r0, uint32_t& r1,
+                                    uint32_t& r2) {
+    uint32_t lo0 = 0, hi0 = n0, lo1 = 0, hi1 = n1, lo2 = 0, hi2 = n2;
+    while (lo0 < hi0 || lo1 < hi1 || lo2 < hi2) {
+        const uint32_t m0 = (lo0 + hi0) >> 1, m1 = (lo1 + hi1) >> 1, m2 = (lo2 + hi2) >> 1;
+        const bool a0 = lo0 < hi0, a1 = lo1 < hi1, a2 = lo2 < hi2;
+        const uint64_t v0 = a0 ? K0[m0] : 0ull, v1 = a1 ? K1[m1] : 0ull, v2 = a2 ? K2[m2] : 0ull;
+        if (a0) { if (v0 < x) lo0 = m0 + 1; else hi0 = m0; }
+        if (a1) { if (v1 < x) lo1 = m1 + 1; else hi1 = m1; }
+        if (a2) { if (v2 < x) lo2 = m2 + 1; else hi2 = m2; }
+    }
+    r0 = lo0;
+    r1 = lo1;
+    r2 = lo2;
 }
 
 // First index of K[0, n) (sorted) whose key is >= x.
@@ -59,17 +78,28 @@ __global__ void __launch_bounds__(1024) k_relevel_lists(RebuildArgs a) {
     }
     __syncthreads();
     const uint32_t off = s_off, nchg = bm->nchg;
+    constexpr uint32_t kPer = 8;  // consecutive changes per thread
     uint32_t carry = 0, icarry = 0;
-    for (uint32_t c0 = 0; c0 < nchg; c0 += 1024u) {
-        const uint32_t i = c0 + threadIdx.x;
-        const uint8_t hl = i < nchg ? a.chg.hl[i] : (uint8_t)0;
-        const bool sel = i < nchg && (uint32_t)(hl & kHeightMask) >= l;
-        const bool ins = sel && (hl & 0x80u);
+    for (uint32_t c0 = 0; c0 < nchg; c0 += 1024u * kPer) {
+        const uint32_t i0 = c0 + threadIdx.x * kPer;
+        uint32_t sm = 0, im = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k) {
+            const uint32_t i = i0 + k;
+            const uint8_t hl = i < nchg ? a.chg.hl[i] : (uint8_t)0;
+            if (i < nchg && (uint32_t)(hl & kHeightMask) >= l) {
+                sm |= 1u << k;
+                if (hl & 0x80u) im |= 1u << k;
+            }
+        }
         uint32_t tot, itot;
-        const uint32_t ex = block_excl_sum<1024>(sel ? 1u : 0u, s_tmp, &tot);
-        const uint32_t iex = block_excl_sum<1024>(ins ? 1u : 0u, s_tmp, &itot);
-        if (sel) {
-            const uint32_t j = carry + ex, ib = icarry + iex;
+        uint32_t j = carry + block_excl_sum<1024>((uint32_t)__popc(sm), s_tmp, &tot);
+        uint32_t ib = icarry + block_excl_sum<1024>((uint32_t)__popc(im), s_tmp, &itot);
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k) {
+            if (!((sm >> k) & 1u)) continue;
+            const uint32_t i = i0 + k;
+            const bool ins = (im >> k) & 1u;
             if (off + j < a.lst_cap) {
                 a.lst_keys[off + j] = a.chg.keys[i];
                 a.lst_pos[off + j] = a.chg.pos[i];
@@ -78,6 +108,8 @@ __global__ void __launch_bounds__(1024) k_relevel_lists(RebuildArgs a) {
             } else {
                 atomicOr(a.err, kErrBounds);
             }
+            ++j;
+            ib += ins ? 1u : 0u;
         }
         carry += tot;
         icarry += itot;
@@ -142,7 +174,7 @@ __device__ __forceinline__ uint32_t slice_rank(const uint64_t* sk, uint32_t len,
     return lo;
 }
 
-__global__ void __launch_bounds__(kT) k_relevel_write(RebuildArgs a) {
+__global__ void __launch_bounds__(kT, 4) k_relevel_write(RebuildArgs a) {
     __shared__ uint32_t s_apref[kLevelSlots + 1], s_bpref[kLevelSlots + 1];
     __shared__ uint32_t s_ta, s_tb;
     __shared__ uint64_t s_k0[kSlice], s_k1[kSlice];
@@ -184,17 +216,15 @@ __global__ void __launch_bounds__(kT) k_relevel_write(RebuildArgs a) {
             const uint32_t off0 = bm->lst_off[l];
             if (c < bm->lst_n[l] && a.lst_ins[off0 + c]) {
                 const uint64_t key = a.lst_keys[off0 + c];
-                const uint32_t lbo = l <= oH ? lb_keys(OK + bm->old_base[l], bm->old_n[l], key) : 0u;
+                // its place among the old entries of level l, and (above the lowest level)
+                // its place in level l - 1: old entries below it plus that list's running count
+                const uint32_t off1 = l > Lb ? bm->lst_off[l - 1] : 0u;
+                uint32_t lbo, j1, lbo1;
+                lb3(OK + bm->old_base[l], l <= oH ? bm->old_n[l] : 0u, a.lst_keys + off1, l > Lb ? bm->lst_n[l - 1] : 0u,
+                    OK + (l > Lb ? bm->old_base[l - 1] : 0u), (l > Lb && l - 1u <= oH) ? bm->old_n[l - 1] : 0u, key,
+                    lbo, j1, lbo1);
                 const uint32_t out = lbo + (uint32_t)a.lst_pref[off0 + c];
-                uint32_t nd;
-                if (l == Lb) {
-                    nd = a.lst_pos[off0 + c];
-                } else {
-                    const uint32_t off1 = bm->lst_off[l - 1];
-                    const uint32_t j1 = lb_keys(a.lst_keys + off1, bm->lst_n[l - 1], key);
-                    const uint32_t lbo1 = (l - 1u) <= oH ? lb_keys(OK + bm->old_base[l - 1], bm->old_n[l - 1], key) : 0u;
-                    nd = lbo1 + (uint32_t)a.lst_pref[off1 + j1];
-                }
+                const uint32_t nd = l == Lb ? a.lst_pos[off0 + c] : lbo1 + (uint32_t)a.lst_pref[off1 + j1];
                 if (l <= H && out < m->n[l]) {
                     NK[m->base[l] + out] = key;
                     ND[m->base[l] + out] = nd;
@@ -224,12 +254,20 @@ __global__ void __launch_bounds__(kT) k_relevel_write(RebuildArgs a) {
         }
         __syncthreads();
         const uint32_t nb = m->base[l], nl = m->n[l];
-#pragma unroll 4
+        uint64_t tk[kItems];
+        uint32_t td[kItems];
+#pragma unroll
+        for (uint32_t k = 0; k < kItems; ++k) {  // every load of the tile in flight at once
+            const uint32_t i = i0 + k * kT + (uint32_t)tid;
+            tk[k] = i < i1 ? OK[ob + i] : 0ull;
+            td[k] = i < i1 ? OD[ob + i] : 0u;
+        }
+#pragma unroll
         for (uint32_t k = 0; k < kItems; ++k) {
             const uint32_t i = i0 + k * kT + (uint32_t)tid;
             if (i >= i1) break;
-            const uint64_t key = OK[ob + i];
-            uint32_t nd = OD[ob + i];
+            const uint64_t key = tk[k];
+            uint32_t nd = td[k];
             bool hit;
             int32_t shift;
             if (st0) {
@@ -264,7 +302,7 @@ __global__ void __launch_bounds__(kT) k_relevel_write(RebuildArgs a) {
 cudaError_t launch_relevel(const RebuildArgs& a, cudaStream_t s, int num_sms) {
     k_relevel_lists<<<kLevelSlots, 1024, 0, s>>>(a);
     ++g_launches;
-    k_relevel_write<<<(uint32_t)num_sms * 8u, kT, 0, s>>>(a);
+    k_relevel_write<<<(uint32_t)num_sms * 4u, kT, 0, s>>>(a);  // the CTAs resident at once
     ++g_launches;
     return cudaGetLastError();
 }
