@@ -40,7 +40,7 @@ constexpr uint32_t kFull = 0xffffffffu;
 // r = largest index >= lo-1 with K[r] <= q (K[lo] <= q unless lo is the head, 0).
 // Also returns D[r] (0 if r < 0 or no down array) and K[r]. Each round reads kWide
 // consecutive entries with 16-byte loads (keys) and 8-byte loads (downs): 4 on index
-// levels, 8 on the storage layer, whose gaps below the lowest built level span
+// levels, 16 (one 128-byte line) on the storage layer, whose gaps below the lowest built level span
 // (1/P)^(Lb-1) nodes. The loads need &K[i] 16-byte aligned (K and D come from arrays
 // whose bases are, and a level may start at any entry), so an odd start steps back one
 // entry, which is <= q, or, at the head of a level, tests the head on its own.
@@ -96,14 +96,24 @@ __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, 
 #pragma unroll
             for (int j = 0; j < kWide; ++j) dd[j] = 0u;
         }
+        uint32_t gt = 0;  // bit j: kk[j] > q (the keys are sorted, so the bits are a suffix)
 #pragma unroll
-        for (int j = 0; j < kWide; ++j) {
-            if (kk[j] > q) {
-                r_out = (int32_t)(i + j) - 1;
-                d_out = j ? dd[j - 1] : dprev;
-                k_out = j ? kk[j - 1] : kprev;
-                return;
+        for (int j = 0; j < kWide; ++j) gt |= (kk[j] > q ? 1u : 0u) << j;
+        if (gt) {
+            const int f = __ffs(gt) - 1;
+            uint32_t dsel = dprev;
+            uint64_t ksel = kprev;
+#pragma unroll
+            for (int j = 1; j < kWide; ++j) {
+                if (j == f) {
+                    dsel = dd[j - 1];
+                    ksel = kk[j - 1];
+                }
             }
+            r_out = (int32_t)(i + (uint32_t)f) - 1;
+            d_out = dsel;
+            k_out = ksel;
+            return;
         }
         dprev = dd[kWide - 1];
         kprev = kk[kWide - 1];
@@ -156,7 +166,7 @@ __device__ __forceinline__ void warp_search(const uint64_t* K, const uint32_t* D
             }
         }
     }
-    if (scan) lane_scan<kDown, kDown ? 4 : 8>(K, D, lo, lim, q, r, dn, kr, err);
+    if (scan) lane_scan<kDown, kDown ? 4 : 16>(K, D, lo, lim, q, r, dn, kr, err);
 }
 
 // Largest index of K[0..n) (sorted, in shared memory) with key <= q, or -1.
