@@ -43,6 +43,8 @@ __device__ __forceinline__ void store_result(pi_result_t* res, uint32_t seq, uin
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_tmp[33];
     __shared__ int32_t s_delta[kLevelSlots];
     __shared__ int32_t s_tomb;
@@ -245,6 +247,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
 // Exclusive sums of the per-tile new-node and level-change counts (one CTA); totals ->
 // bm->new_count and bm->nchg.
 __global__ void __launch_bounds__(1024) k_new_scan(ApplyArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_tmp[33];
     __shared__ uint32_t s_carry, s_ccarry;
     if (block_sees_error(&a.m->error)) return;
@@ -280,6 +284,8 @@ __global__ void __launch_bounds__(1024) k_new_scan(ApplyArgs a) {
 
 // Packs each tile's staged new nodes and level changes to their places in key order.
 __global__ void __launch_bounds__(kThreads) k_new_pack(ApplyArgs a) {
+    pdl_wait();
+    pdl_trigger();
     if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
     const uint32_t tile = blockIdx.x;
     const uint32_t so = tile * kApplyTile;
@@ -311,11 +317,11 @@ cudaError_t launch_apply(const ApplyArgs& a, uint32_t& epoch, cudaStream_t s, in
     (void)num_sms;
     if (a.n == 0) return cudaSuccess;
     const uint32_t tiles = (a.n + kApplyTile - 1) / kApplyTile;
-    k_apply<<<tiles, kThreads, 0, s>>>(a);  // tile prefixes come from the descent's scan
+    launch_dep(k_apply, tiles, kThreads, 0, s, a);  // tile prefixes come from the descent's scan
     ++g_launches;
-    k_new_scan<<<1, 1024, 0, s>>>(a);
+    launch_dep(k_new_scan, 1, 1024, 0, s, a);
     ++g_launches;
-    k_new_pack<<<tiles, kThreads, 0, s>>>(a);
+    launch_dep(k_new_pack, tiles, kThreads, 0, s, a);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -196,6 +196,14 @@ __device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// Programmatic dependent launch. Kernels of the batch path are launched with
+// launch_dep, which lets the next kernel on the stream be scheduled while this one
+// drains. Every such kernel calls pdl_wait() before it touches memory: it returns once
+// the previous kernel on the stream has completed and its writes are visible (at once
+// when there is none). pdl_trigger() then lets the next kernel's CTAs be placed as SMs
+// free up; they wait in their own pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -696,6 +704,24 @@ void set_last_error(int code);
 // Kernels launched by this host thread (every launcher adds the launches it issues); the
 // batch entry points fold the difference into the index's own count.
 extern thread_local uint64_t g_launches;
+
+// kernel<<<grid, block, smem, s>>>(args...) with programmatic dependent launch allowed
+// (the kernel must begin with pdl_wait()).
+template <typename... KP, typename... A>
+inline cudaError_t launch_dep(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              A... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KP>(args)...);
+}
 
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
 cudaError_t launch_rebuild_prep(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);

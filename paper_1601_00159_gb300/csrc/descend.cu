@@ -187,6 +187,8 @@ __device__ __forceinline__ int32_t smem_rank(const uint64_t* K, uint32_t n, uint
 // Per 256-query sub-tile (one warp each): local run heads -> holey key list, count,
 // and the apply tile's maximum ownership marker.
 __global__ void __launch_bounds__(kThreads) k_distinct(DescendArgs a) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
     const uint32_t n = a.n;
@@ -226,6 +228,8 @@ __global__ void __launch_bounds__(kThreads) k_distinct(DescendArgs a) {
 // counts), the number of distinct keys, and the apply tiles' exclusive max prefixes.
 // Each thread takes a contiguous run of entries, so there is one block scan per array.
 __global__ void __launch_bounds__(1024) k_dscan(DescendArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_tmp[33];
     if (block_sees_error(&a.m->error)) return;
     {
@@ -278,6 +282,8 @@ __global__ void __launch_bounds__(1024) k_dscan(DescendArgs a) {
     }
 }
 __global__ void __launch_bounds__(kThreads) k_dpack(DescendArgs a) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
     const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
@@ -291,6 +297,8 @@ __global__ void __launch_bounds__(kThreads) k_dpack(DescendArgs a) {
 // binary search of the lowest pinned level (in shared memory, copied per CTA by TMA
 // bulk copies), then a walk of the levels down to top_launched + 1.
 __global__ void __launch_bounds__(kThreads) k_top(DescendArgs a) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
     uint32_t* s_d = reinterpret_cast<uint32_t*>(s_dyn + (kSmemTopMax + kPad) * sizeof(uint64_t));
@@ -343,6 +351,8 @@ __global__ void __launch_bounds__(kThreads) k_top(DescendArgs a) {
 
 // One global index level: every distinct key scans its gap from its start position.
 __global__ void __launch_bounds__(kThreads) k_level(DescendArgs a, int l) {
+    pdl_wait();
+    pdl_trigger();
     const DevMeta* m = a.m;
     if (*(volatile const uint32_t*)&m->error) return;  // no barrier in this kernel
     const uint32_t H = m->H, Lb = m->Lb, Ls = m->Ls;
@@ -367,6 +377,8 @@ __global__ void __launch_bounds__(kThreads) k_level(DescendArgs a, int l) {
 
 // The storage layer: node with the largest key <= q (exists if equal) and its state.
 __global__ void __launch_bounds__(kThreads) k_locate(DescendArgs a) {
+    pdl_wait();
+    pdl_trigger();
     const DevMeta* m = a.m;
     if (*(volatile const uint32_t*)&m->error) return;  // no barrier in this kernel
     const uint32_t size = m->size, cur = m->cur;
@@ -407,14 +419,14 @@ cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
     if (a.n == 0) return cudaSuccess;
     const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
     const uint32_t blocks = (nsub + 7) / 8;
-    k_distinct<<<blocks, kThreads, 0, s>>>(a);
+    launch_dep(k_distinct, blocks, kThreads, 0, s, a);
     ++g_launches;
-    k_dscan<<<1, 1024, 0, s>>>(a);
+    launch_dep(k_dscan, 1, 1024, 0, s, a);
     ++g_launches;
-    k_dpack<<<blocks, kThreads, 0, s>>>(a);
+    launch_dep(k_dpack, blocks, kThreads, 0, s, a);
     ++g_launches;
     const uint32_t need = (a.n + kThreads - 1) / kThreads;
-    k_top<<<need, kThreads, dyn, s>>>(a);  // CTAs past the distinct keys exit at once
+    launch_dep(k_top, need, kThreads, dyn, s, a);  // CTAs past the distinct keys exit at once
     ++g_launches;
     // one launch per index level from top_launched down to 2; a launch whose level is
     // pinned or not built exits at once, and levels above top_launched that are
@@ -422,10 +434,10 @@ cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
     const uint32_t capg = (uint32_t)num_sms * 16u;
     const uint32_t gblocks = need < capg ? need : capg;  // grid-stride over the distinct keys
     for (int l = a.top_launched; l >= a.bottom_launched; --l) {
-        k_level<<<gblocks, kThreads, 0, s>>>(a, l);
+        launch_dep(k_level, gblocks, kThreads, 0, s, a, l);
         ++g_launches;
     }
-    k_locate<<<gblocks, kThreads, 0, s>>>(a);
+    launch_dep(k_locate, gblocks, kThreads, 0, s, a);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -73,6 +73,8 @@ __device__ __forceinline__ uint32_t live_mask(const uint8_t* meta, uint64_t c, u
 // kItems consecutive sorted bounds, so a warp covers one descent sub-tile and the
 // dense index of a bound's key is its sub-tile's prefix plus the warp's local heads.
 __global__ void __launch_bounds__(kThreads) k_range_ends(RangeArgs a) {
+    pdl_wait();
+    pdl_trigger();
     const DevMeta* m = a.m;
     if (*(volatile const uint32_t*)&m->error) return;
     const uint32_t nb = 2u * a.n, qv = nb - a.bm->invalid, size = m->size;
@@ -119,6 +121,8 @@ __global__ void __launch_bounds__(kThreads) k_range_ends(RangeArgs a) {
 
 // Live nodes per query (a warp per query) and per-CTA totals.
 __global__ void __launch_bounds__(kThreads) k_range_count(RangeArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint64_t s_sum[kThreads / 32];
     const DevMeta* m = a.m;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -149,6 +153,8 @@ __global__ void __launch_bounds__(kThreads) k_range_count(RangeArgs a) {
 
 // Exclusive prefix of the CTA sums in place (one CTA), the grand total in offsets[n].
 __global__ void __launch_bounds__(kThreads) k_range_scan(RangeArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint64_t s_tmp[33];
     const uint32_t nblk = (a.n + kQ - 1) / kQ;
     uint64_t carry = 0;
@@ -165,6 +171,8 @@ __global__ void __launch_bounds__(kThreads) k_range_scan(RangeArgs a) {
 
 // Offsets and pairs. A query whose pairs do not fit below cap gets its offset only.
 __global__ void __launch_bounds__(kThreads) k_range_write(RangeArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint64_t s_tmp[33];
     __shared__ uint64_t s_off[kQ];
     const DevMeta* m = a.m;
@@ -221,14 +229,14 @@ cudaError_t launch_range(const RangeArgs& a, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     const uint32_t nb = 2u * a.n;
     const uint32_t ends_blocks = (nb + kThreads * kItems - 1) / (kThreads * kItems);
-    k_range_ends<<<ends_blocks, kThreads, 0, s>>>(a);
+    launch_dep(k_range_ends, ends_blocks, kThreads, 0, s, a);
     ++g_launches;
     const uint32_t qblocks = (a.n + kQ - 1) / kQ;
-    k_range_count<<<qblocks, kThreads, 0, s>>>(a);
+    launch_dep(k_range_count, qblocks, kThreads, 0, s, a);
     ++g_launches;
-    k_range_scan<<<1, kThreads, 0, s>>>(a);
+    launch_dep(k_range_scan, 1, kThreads, 0, s, a);
     ++g_launches;
-    k_range_write<<<qblocks, kThreads, 0, s>>>(a);
+    launch_dep(k_range_write, qblocks, kThreads, 0, s, a);
     ++g_launches;
     return cudaGetLastError();
 }

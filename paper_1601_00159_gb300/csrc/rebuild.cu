@@ -52,6 +52,8 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t 
 // A new node with loc = x goes right before old node x (after old node x - 1) and is
 // handled by the tile that holds position x; the tiles cover positions [0, size].
 __global__ void __launch_bounds__(kThreads) k_merge(RebuildArgs a, uint32_t epoch) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint16_t s_lp[kNodes + 1];  // live old nodes in [ts, ts + k)
     __shared__ uint32_t s_tmp[33];
     __shared__ uint32_t s_tile, s_prefix, s_jb, s_je;
@@ -266,6 +268,8 @@ __device__ bool level_bases_body(RebuildArgs a) {
 // thread; it works on shared-memory copies loaded and stored by the whole warp, so its
 // dependent accesses cost shared-memory latency rather than L2 latency.
 __global__ void k_level_bases(RebuildArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ DevMeta s_m;
     __shared__ BatchMeta s_bm;
     __shared__ int s_go;
@@ -319,6 +323,8 @@ __global__ void k_level_bases(RebuildArgs a) {
 //          of height >= l writes its key and down pointer to level l at the position
 //          given by the same ballots.
 __global__ void __launch_bounds__(256) k_rebuild_count(RebuildArgs a) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const DevMeta* m = a.m;
     if (*(volatile const uint32_t*)&m->error) return;  // no barrier in this kernel
@@ -362,6 +368,8 @@ __global__ void __launch_bounds__(256) k_rebuild_count(RebuildArgs a) {
 constexpr uint32_t kScanChunk = 4096;
 
 __global__ void __launch_bounds__(1024) k_rebuild_scan(RebuildArgs a, uint32_t epoch) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_tmp[33];
     __shared__ uint32_t s_prefix;
     __shared__ int s_ok;
@@ -436,6 +444,8 @@ constexpr uint32_t kWarpNodes = kNodes / 8;  // 512 nodes per warp
 //     Lb + 1, keeping each one's index in level Lb for its down pointer; the next
 //     levels repeat step 3 on the shrinking list.
 __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint8_t* s_meta = s_dyn;                                              // kNodes + 16
     uint32_t* s_list = reinterpret_cast<uint32_t*>(s_dyn + kMetaBytes);   // 8 x 512
@@ -575,6 +585,8 @@ __global__ void __launch_bounds__(kThreads) k_rebuild_write(RebuildArgs a) {
 // Bulk build: keep the last query of every key run of the sorted input (the last
 // occurrence of a key wins), with its value and tower height; count level sizes.
 __global__ void __launch_bounds__(kThreads) k_create_storage(CreateArgs a, uint32_t epoch) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_tmp[33];
     __shared__ uint32_t s_hist[kLevelSlots];
     __shared__ uint32_t s_tile, s_prefix, s_kept;
@@ -652,6 +664,8 @@ __global__ void __launch_bounds__(kThreads) k_export_live(Storage st, const DevM
                                                           uint64_t* vo, uint64_t cap, uint32_t* count,
                                                           uint64_t* desc, uint32_t* tile_ctr, uint32_t epoch,
                                                           uint32_t* err) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_tmp[33];
     __shared__ uint32_t s_tile, s_prefix;
     __shared__ int s_ok;
@@ -704,13 +718,13 @@ __global__ void __launch_bounds__(kThreads) k_export_live(Storage st, const DevM
 cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
     const uint32_t tiles = a.size_ub / kNodes + 1;
     const uint32_t cap = (uint32_t)num_sms * 4u;
-    k_merge<<<(int)(tiles < cap ? tiles : cap), kThreads, 0, s>>>(a, ++epoch);
+    launch_dep(k_merge, (int)(tiles < cap ? tiles : cap), kThreads, 0, s, a, ++epoch);
     ++g_launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s) {
-    k_level_bases<<<1, 32, 0, s>>>(a);
+    launch_dep(k_level_bases, 1, 32, 0, s, a);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -718,10 +732,10 @@ cudaError_t launch_level_bases(const RebuildArgs& a, cudaStream_t s) {
 cudaError_t launch_rebuild_prep(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
     const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
     const uint32_t cb = (tiles + 7) / 8, ccap = (uint32_t)num_sms * 4u;
-    k_rebuild_count<<<cb < ccap ? cb : ccap, 256, 0, s>>>(a);  // exits at once unless recounting
+    launch_dep(k_rebuild_count, cb < ccap ? cb : ccap, 256, 0, s, a);  // exits at once unless recounting
     ++g_launches;
     const uint32_t chunks = (tiles + kScanChunk - 1) / kScanChunk;
-    k_rebuild_scan<<<dim3(chunks, kLevelSlots - 2), 1024, 0, s>>>(a, ++epoch);
+    launch_dep(k_rebuild_scan, dim3(chunks, kLevelSlots - 2), 1024, 0, s, a, ++epoch);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -736,7 +750,7 @@ cudaError_t launch_rebuild_write(const RebuildArgs& a, cudaStream_t s, int num_s
     }
     const uint32_t tiles = (a.size_ub + kNodes - 1) / kNodes + 1;
     const uint32_t cap = (uint32_t)num_sms * 8u;  // persistent: the CTAs resident at once
-    k_rebuild_write<<<tiles < cap ? tiles : cap, kThreads, dyn, s>>>(a);
+    launch_dep(k_rebuild_write, tiles < cap ? tiles : cap, kThreads, dyn, s, a);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -750,7 +764,7 @@ cudaError_t launch_create_storage(const CreateArgs& a, uint32_t& epoch, cudaStre
     if (a.n == 0) return cudaSuccess;
     const uint32_t tiles = (a.n + kNodes - 1) / kNodes;
     const uint32_t cap = (uint32_t)num_sms * 4u;
-    k_create_storage<<<(int)(tiles < cap ? tiles : cap), kThreads, 0, s>>>(a, ++epoch);
+    launch_dep(k_create_storage, (int)(tiles < cap ? tiles : cap), kThreads, 0, s, a, ++epoch);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -760,7 +774,7 @@ cudaError_t launch_export_live(const Storage& st, const DevMeta* m, uint64_t* ke
                                uint32_t& epoch, uint32_t* err, cudaStream_t s, int num_sms, uint32_t size_ub) {
     const uint32_t tiles = size_ub / kNodes + 1;
     const uint32_t c = (uint32_t)num_sms * 4u;
-    k_export_live<<<(int)(tiles < c ? tiles : c), kThreads, 0, s>>>(st, m, keys_out, vals_out, cap, count, desc,
+    launch_dep(k_export_live, (int)(tiles < c ? tiles : c), kThreads, 0, s, st, m, keys_out, vals_out, cap, count, desc,
                                                                    tile_ctr, ++epoch, err);
     ++g_launches;
     return cudaGetLastError();

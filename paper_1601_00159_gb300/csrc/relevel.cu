@@ -61,6 +61,8 @@ __device__ __forceinline__ uint32_t lb_keys(const uint64_t* K, uint32_t n, uint6
 }
 
 __global__ void __launch_bounds__(1024) k_relevel_lists(RebuildArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_tmp[33];
     __shared__ uint32_t s_off;
     const DevMeta* m = a.m;
@@ -175,6 +177,8 @@ __device__ __forceinline__ uint32_t slice_rank(const uint64_t* sk, uint32_t len,
 }
 
 __global__ void __launch_bounds__(kT, 4) k_relevel_write(RebuildArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_apref[kLevelSlots + 1], s_bpref[kLevelSlots + 1];
     __shared__ uint32_t s_ta, s_tb;
     __shared__ uint64_t s_k0[kSlice], s_k1[kSlice];
@@ -300,9 +304,9 @@ __global__ void __launch_bounds__(kT, 4) k_relevel_write(RebuildArgs a) {
 }  // namespace
 
 cudaError_t launch_relevel(const RebuildArgs& a, cudaStream_t s, int num_sms) {
-    k_relevel_lists<<<kLevelSlots, 1024, 0, s>>>(a);
+    launch_dep(k_relevel_lists, kLevelSlots, 1024, 0, s, a);
     ++g_launches;
-    k_relevel_write<<<(uint32_t)num_sms * 4u, kT, 0, s>>>(a);  // the CTAs resident at once
+    launch_dep(k_relevel_write, (uint32_t)num_sms * 4u, kT, 0, s, a);  // the CTAs resident at once
     ++g_launches;
     return cudaGetLastError();
 }

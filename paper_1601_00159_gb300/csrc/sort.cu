@@ -43,6 +43,8 @@ static_assert(kTile == kSortTile, "tile size shared with the host's descriptor s
 __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ ops, const uint64_t* __restrict__ keys,
                                               uint32_t n, uint64_t* __restrict__ sk, uint32_t* __restrict__ sp,
                                               uint32_t* __restrict__ fixmap, BatchMeta* bm) {
+    pdl_wait();
+    pdl_trigger();
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < (n + 31u) / 32u; w += gridDim.x * blockDim.x)
         fixmap[w] = 0;  // segment marks of the prefix fix-up
     uint32_t invalid = 0;
@@ -104,6 +106,8 @@ __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ ops, c
 // differ inside a segment (rdig).
 __global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, uint32_t* tile_max,
                                                    uint32_t max_passes) {
+    pdl_wait();
+    pdl_trigger();
     const int b = threadIdx.x;
     if (tile_max)
         for (uint32_t t = b; t < (n + kApplyTile - 1) / kApplyTile; t += 256) tile_max[t] = 0;
@@ -117,6 +121,8 @@ __device__ __forceinline__ const uint64_t* pass_src_keys(const SortPlan& P, uint
 // Digit histogram of every tile for pass j. Pass 0 reads the packed keys; later
 // passes read the digit bytes the previous scatter wrote beside its output.
 __global__ void __launch_bounds__(kThreads) k_sort_count(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t h[256];
     const SortPlan& P = bm->plan;
     if (j >= P.npass) return;
@@ -151,6 +157,8 @@ __global__ void __launch_bounds__(kThreads) k_sort_count(uint32_t j, uint32_t n,
 // One CTA per digit: that digit's offset in every tile for pass j, relative to the
 // digit's first slot, and the digit's total (the scatter adds the digit bases).
 __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_tmp[33];
     const SortPlan& P = bm->plan;
     if (j >= P.npass) return;
@@ -191,6 +199,8 @@ __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t j, uint32_t n, Sort
 
 __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t n, SortBuffers sb,
                                                            BatchMeta* bm, uint32_t* err) {
+    pdl_wait();
+    pdl_trigger();
     const SortPlan& P = bm->plan;
     if (j >= P.npass) return;
     const uint32_t shift = 8u * P.digit[j];
@@ -274,6 +284,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
 // lies inside such a segment; the segment's start is found by a galloping search back
 // from i followed by a binary search, both over the prefix order.
 __global__ void __launch_bounds__(256) k_sort_find(uint32_t n, SortBuffers sb, const BatchMeta* bm) {
+    pdl_wait();
+    pdl_trigger();
     const SortPlan& P = bm->plan;
     if (!P.fix) return;
     const uint64_t pm = P.pmask;
@@ -380,6 +392,8 @@ __device__ void cta_segment_lsd(uint32_t s, uint32_t e, const SortPlan& P, const
 // most 32 queries: rank = queries with a smaller key, or the same key and an earlier
 // position. Longer segments are queued for the whole CTA.
 __global__ void __launch_bounds__(kThreads) k_sort_fix(uint32_t n, SortBuffers sb, BatchMeta* bm) {
+    pdl_wait();
+    pdl_trigger();
     const SortPlan& P = bm->plan;
     if (!P.fix) return;
     __shared__ uint32_t s_list[kFixSlice / 2];  // segment starts (a segment holds >= 2 queries)
@@ -469,9 +483,9 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
     if (n == 0) return cudaSuccess;
     if (max_passes < 1 || max_passes > 8) return cudaErrorInvalidValue;
     int grid = min((int)((n + 255) / 256), num_sms * 8);
-    k_pack<<<grid, 256, 0, s>>>(ops, keys, n, sb.in_k, sb.in_p, sb.fixmap, bm);
+    launch_dep(k_pack, grid, 256, 0, s, ops, keys, n, sb.in_k, sb.in_p, sb.fixmap, bm);
     ++g_launches;
-    k_sort_plan<<<1, 256, 0, s>>>(n, bm, sb.tile_max, (uint32_t)max_passes);
+    launch_dep(k_sort_plan, 1, 256, 0, s, n, bm, sb.tile_max, (uint32_t)max_passes);
     ++g_launches;
     static bool attr_set = false;
     const int dyn = kTile * (int)(sizeof(uint64_t) + sizeof(uint32_t));
@@ -481,22 +495,22 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
         attr_set = true;
     }
     const uint32_t tiles = (n + kTile - 1) / kTile;
-    k_sort_count<<<tiles, kThreads, 0, s>>>(0, n, sb, bm);
+    launch_dep(k_sort_count, tiles, kThreads, 0, s, 0, n, sb, bm);
     ++g_launches;
     for (uint32_t j = 0; j < (uint32_t)max_passes; ++j) {
-        k_sort_scan<<<256, 1024, 0, s>>>(j, n, sb, bm);
+        launch_dep(k_sort_scan, 256, 1024, 0, s, j, n, sb, bm);
         ++g_launches;
-        k_sort_pass<<<tiles, kThreads, dyn, s>>>(j, n, sb, bm, err);
+        launch_dep(k_sort_pass, tiles, kThreads, dyn, s, j, n, sb, bm, err);
         ++g_launches;
         if (j + 1 < (uint32_t)max_passes) {
-            k_sort_count<<<tiles, kThreads, 0, s>>>(j + 1, n, sb, bm);
+            launch_dep(k_sort_count, tiles, kThreads, 0, s, j + 1, n, sb, bm);
             ++g_launches;
         }
     }
     if (max_passes < 8) {  // with eight passes every byte is sorted: nothing to fix
-        k_sort_find<<<grid, 256, 0, s>>>(n, sb, bm);
+        launch_dep(k_sort_find, grid, 256, 0, s, n, sb, bm);
         ++g_launches;
-        k_sort_fix<<<(n + kFixSlice - 1) / kFixSlice, kThreads, 0, s>>>(n, sb, bm);
+        launch_dep(k_sort_fix, (n + kFixSlice - 1) / kFixSlice, kThreads, 0, s, n, sb, bm);
         ++g_launches;
     }
     return cudaGetLastError();
