@@ -36,9 +36,9 @@ from paper_1601_00159_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "Mqueries/s and % of HBM roofline on 1 GB300; p50/p99 latency in serving loop"
 UNIT = "Mqueries/s"
-# ncu DRAM bytes of the rebuild's writer kernel, per storage node, are read from this
-# summary, which also records a digest of the writer's source they were taken with.
-WRITER_PROFILE = os.path.join(ROOT, "profiles", "k_rebuild_write_skewed_2p24.md")
+# DRAM bytes per launch and per batch of the default skewed workload, from a full-size
+# ncu capture; the summary records a digest of the sources the capture was taken with.
+DRAM_PROFILE = os.path.join(ROOT, "profiles", "dram_skewed_2p27.md")
 
 WORKLOADS = {
     "skewed": dict(fn=wl.skewed, n=1 << 27, q=1 << 22,
@@ -74,32 +74,37 @@ def tuned_classes():
         return None
 
 
-def writer_source_digest():
-    """sha256 prefix of the writer kernel's source text (k_rebuild_write and its helpers)."""
+def source_digest():
+    """sha256 prefix of the CUDA sources and the C header: a DRAM capture counts only for
+    the kernels it measured."""
     import hashlib
-    src = open(os.path.join(ROOT, "paper_1601_00159_gb300", "csrc", "rebuild.cu")).read()
-    a, b = src.index("// Byte-wise arithmetic on a meta word"), src.index("// Bulk build:")
-    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1601_00159_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "pi.h"), "rb").read())
+    return h.hexdigest()[:16]
 
 
-def writer_traffic_per_node(lowest):
-    """(bytes per storage node, note) from the committed ncu summary, or (None, why): the
-    capture must be of the same writer source and the same lowest built level."""
+def dram_profile(workload):
+    """(per-launch DRAM bytes by kernel, DRAM bytes per batch, note) from the committed
+    full-size ncu capture of this workload, or (None, None, why)."""
     import re
     try:
-        text = open(WRITER_PROFILE).read()
+        text = open(DRAM_PROFILE).read()
     except OSError:
-        return None, "no ncu summary"
-    m = re.search(r"source digest: `([0-9a-f]{16})`", text)
-    b = re.search(r"DRAM bytes per storage node: `([0-9.]+)`", text)
-    if not (m and b):
-        return None, "summary lacks digest or bytes"
-    if m.group(1) != writer_source_digest():
-        return None, "writer source changed since the ncu capture"
-    lv = re.search(r"lowest built level: `([0-9]+)`", text)
-    if not lv or int(lv.group(1)) != lowest:
-        return None, "the capture built a different lowest level"
-    return float(b.group(1)), "ncu capture at 2^24 keys, scaled by storage nodes"
+        return None, None, "no ncu summary"
+    m = re.search(r"```json\n(.*?)\n```", text, re.S)
+    if not m:
+        return None, None, "summary lacks its data block"
+    d = json.loads(m.group(1))
+    if d.get("workload") != workload:
+        return None, None, f"the capture is of workload {d.get('workload')}"
+    if d.get("digest") != source_digest():
+        return None, None, "kernel sources changed since the ncu capture"
+    return d["bytes_per_launch"], d["bytes_per_batch"], "ncu capture of this workload at full size"
 
 
 def measured_peaks():
@@ -835,39 +840,54 @@ def run_ours(args, ws, rank, local):
     e2e_ms = reduce_max(e0.elapsed_time(e1), ws)
     e2e_value = ws * q * e2e_steps / (e2e_ms * 1e-3) / 1e6
 
-    # Roofline of the kernel that moves the most algorithmic bytes, k_rebuild_write (the
-    # rebuild's count and scan launches move a few KB): its duration is the CUDA-event
-    # interval around its launch on the rebuild stream, averaged over the timed batches.
+    # Roofline of the largest launch of a batch, the storage locate (k_locate; the ncu
+    # launch list in profiles/ gives the shares): its duration is the CUDA-event interval
+    # around its launch on the batch stream, averaged over the timed batches. Its
+    # algorithmic bytes per distinct key of the batch: the storage keys of one gap
+    # between two entries of the lowest built level (8 B x (1/P)^(Lb-1)), one 32-byte
+    # sector each for the node's meta byte and value, and the 25 B it streams (query key
+    # and start position in; node position, state and prior value out).
     hbm, peak_kind = measured_peaks()
     per_stage = {k: v / max(nb, 1) for k, v in stage_ms.items()}
-    hb = host_batches[0]
-    ins = int((hb.ops == wl.OP_INSERT).sum())
-    distinct = len(np.unique(hb.keys))
+    used = host_batches[: min(len(host_batches), args.steps)]
+    distinct = float(np.mean([len(np.unique(b.keys)) for b in used]))
+    ins = float(np.mean([int((b.ops == wl.OP_INSERT).sum()) for b in used]))
     sizes = info1["level_size"]
     size_after = info1["size"]
     writes = distinct  # upper bound: every distinct key may be written once
     lowest = info1["bottom_built"]
-    ab = algorithmic_bytes(q, ins, distinct, distinct, writes, size_after, sizes, l2_bytes, 8, lowest,
-                           int(round(1 / w.promote_p)))
+    inv_p = int(round(1 / w.promote_p))
+    ab = algorithmic_bytes(q, ins, distinct, distinct, writes, size_after, sizes, l2_bytes, 8, lowest, inv_p)
+    gap = inv_p ** (lowest - 1)
+    loc_per_key = 8 * gap + 32 + 32 + 25
+    loc_bytes = distinct * loc_per_key
+    loc_ms = per_stage["locate"]
+    achieved = loc_bytes / (loc_ms * 1e-3) / 1e9
+    default_run = not (args.keys_log2 or args.batch_log2) and args.rebuild == "each"
+    per_launch, per_batch, traffic_note = (dram_profile(args.workload) if default_run else
+                                           (None, None, "no ncu capture of this configuration"))
+    loc_traffic = per_launch.get("k_locate") if per_launch else None
+    low = min(loc_bytes, loc_traffic) if loc_traffic is not None else loc_bytes
+    # The rebuild's writer: the incremental one reads and writes each built entry (8 B key
+    # + 4 B down) once; the full one scans the storage layer's keys and meta and writes
+    # every built entry.
     writer_ms = per_stage["rebuild_write"]
     inc_region = info1["incremental_rebuilds"] - info0["incremental_rebuilds"]
     rebuilds_region = info1["rebuilds"] - info0["rebuilds"]
     entries = sum(sizes[lowest:])
     if rebuilds_region and inc_region == rebuilds_region:
-        # every timed rebuild updated the previous levels: it reads and writes each built
-        # entry (8 B key + 4 B down) once, plus the batch's change lists
-        wkernel = "k_relevel_write"
-        wbytes = 24 * entries
+        wkernel, wbytes = "k_relevel_write", 24 * entries
         wmodel = "12 B read + 12 B written per built index entry (incremental rebuild)"
-        per_node, traffic_note = None, "no ncu capture of the incremental writer yet"
     else:
-        wkernel = "k_rebuild_write"
-        wbytes = ab["rebuild"]
+        wkernel, wbytes = "k_rebuild_write", ab["rebuild"]
         wmodel = "9 B per storage node (key + meta scan) + 12 B per built index entry"
-        per_node, traffic_note = writer_traffic_per_node(lowest)
-    achieved = wbytes / (writer_ms * 1e-3) / 1e9
-    traffic = per_node * size_after if per_node is not None else None
-    low = min(wbytes, traffic) if traffic is not None else wbytes
+    w_traffic = per_launch.get(wkernel) if per_launch else None
+    # The whole batch against the same peak: the method's bytes (the paper's model with a
+    # full rebuild), the bytes of the path as built (the incremental rebuild in place of
+    # the full one when every timed rebuild was incremental), and DRAM bytes by ncu.
+    built_bytes = ab["total"] - ab["rebuild"] + (wbytes if wkernel == "k_relevel_write" else ab["rebuild"])
+    step_s = ms_step * 1e-3
+    batch_low = min(x for x in (ab["total"], built_bytes, per_batch) if x is not None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -880,16 +900,25 @@ def run_ours(args, ws, rank, local):
                    "rebuild_policy": args.rebuild, "keys": len(w.keys), "batch": q,
                    "distinct_batches_cycled": len(dbatches), "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2_flush": "none: storage layer and cycled batch inputs exceed L2"},
-        "roofline": {"bound": "hbm", "kernel": wkernel, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind, "traffic": traffic,
+        "roofline": {"bound": "hbm", "kernel": "k_locate", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind, "traffic": loc_traffic,
                      "traffic_note": traffic_note,
-                     "frac_min_of_model_and_traffic": low / (writer_ms * 1e-3) / 1e9 / hbm,
-                     "launches_per_step": 1, "ms_per_launch": writer_ms,
-                     "algorithmic_bytes_per_launch": wbytes, "bytes_model": wmodel,
-                     "lowest_built_level": lowest, "incremental_rebuilds": inc_region,
-                     "rebuilds": rebuilds_region},
-        "batch_roofline": {"algorithmic_bytes": ab["total"], "achieved_gbs": ab["total"] / (ms_step * 1e-3) / 1e9,
-                           "frac": ab["total"] / (ms_step * 1e-3) / 1e9 / hbm},
+                     "frac_min_of_model_and_traffic": low / (loc_ms * 1e-3) / 1e9 / hbm,
+                     "launches_per_step": 1, "ms_per_launch": loc_ms, "share_of_step": loc_ms / ms_step,
+                     "algorithmic_bytes_per_launch": loc_bytes,
+                     "bytes_model": f"{loc_per_key} B per distinct key: 8 B x {gap} storage keys of one "
+                                    "lowest-level gap + meta and value sectors (32 B each) + 25 B streamed",
+                     "distinct_keys_per_batch": distinct, "lowest_built_level": lowest},
+        "rebuild_writer": {"kernel": wkernel, "ms_per_launch": writer_ms,
+                           "algorithmic_bytes_per_launch": wbytes, "bytes_model": wmodel,
+                           "achieved_gbs": wbytes / (writer_ms * 1e-3) / 1e9 if writer_ms else None,
+                           "traffic": w_traffic, "incremental_rebuilds": inc_region, "rebuilds": rebuilds_region,
+                           "note": "runs on the rebuild stream, overlapping the next batch's sort"},
+        "batch_roofline": {"algorithmic_bytes": ab["total"], "built_path_bytes": built_bytes,
+                           "traffic": per_batch, "frac_model": ab["total"] / step_s / 1e9 / hbm,
+                           "frac_built_path": built_bytes / step_s / 1e9 / hbm,
+                           "frac": batch_low / step_s / 1e9 / hbm,
+                           "note": "frac divides the smallest of the model, built-path and ncu bytes"},
         "stages_ms": per_stage,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": q * 17, "d2h_bytes_per_step": q * 16,
                 "steps": e2e_steps},
@@ -897,14 +926,13 @@ def run_ours(args, ws, rank, local):
         "clocks": clk.summary(),
         "index": {"size": info1["size"], "live": info1["live"], "tombstones": info1["tombstones"],
                   "top_level": info1["top_level"], "rebuilds_in_region": info1["rebuilds"] - info0["rebuilds"],
-                  "create_s": create_s, "gen_s": gen_s, "distinct_keys_batch0": distinct},
+                  "create_s": create_s, "gen_s": gen_s, "distinct_keys_per_batch": distinct},
     }
     if args.rebuild == "deferred":
         # most batches skip the rebuild, so the writer's per-batch average is not one launch
-        line["roofline"] = {"bound": "hbm", "kernel": "k_rebuild_write", "achieved": None, "peak": hbm,
-                            "unit": "GB/s", "frac": None, "traffic": None,
-                            "note": "deferred rebuild: the writer runs in "
-                                    f"{info1['rebuilds'] - info0['rebuilds']} of {args.steps} timed batches"}
+        line["rebuild_writer"] = {"kernel": "k_rebuild_write", "ms_per_launch": None,
+                                  "note": "deferred rebuild: the writer runs in "
+                                          f"{rebuilds_region} of {args.steps} timed batches"}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, host_batches[0], args.cpu_budget)
     if rank == 0:

@@ -227,14 +227,14 @@ int pi_export_level(pi_index_t* idx, int level, uint64_t* keys_out, uint32_t* do
  * each stage runs on:
  *   0 pack + radix sort (K0, K1)        4 level layout (K6b)
  *   1 descent + storage locate (K2, K3) 5 index-layer rebuild (K6c; background stream)
- *   2 ownership + apply (K4, K5)        6 the rebuild's writer kernel alone (part of 5)
- *   3 storage merge (K6a)
+ *   2 ownership + apply (K4, K5)        6 the rebuild's writer kernels alone (part of 5)
+ *   3 storage merge (K6a)               7 the storage-locate kernel alone (part of 1)
  * The descent's stage excludes its wait for the previous batch's rebuild.
  * pi_profile(idx, 1) starts (and clears) the accumulation; pi_profile(idx, 0) stops it.
  * pi_profile_read synchronises `stream` and writes the summed milliseconds per stage to
  * stage_ms_host[PI_NUM_STAGES] and the number of batches they cover to *batches_host.
  */
-#define PI_NUM_STAGES 7
+#define PI_NUM_STAGES 8
 int pi_profile(pi_index_t* idx, int enable);
 int pi_profile_read(pi_index_t* idx, double* stage_ms_host, uint64_t* batches_host, pi_stream_t stream);
 

@@ -35,7 +35,7 @@ PI_TEST_SORT_FULL = 2
 def PI_TEST_SORT_PREFIX(k: int) -> int:
     """test_flags value: sort batches with k = 1..4 radix passes plus the prefix fix-up."""
     return k << 4
-STAGES = ["sort", "descend", "apply", "merge", "layout", "rebuild", "rebuild_write"]
+STAGES = ["sort", "descend", "apply", "merge", "layout", "rebuild", "rebuild_write", "locate"]
 
 
 class PiError(RuntimeError):

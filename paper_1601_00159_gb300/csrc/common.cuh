@@ -570,7 +570,8 @@ struct DescendArgs {
     uint32_t n;
     uint32_t* err;
 };
-cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms);
+// before_locate (may be null) is recorded on s just before the storage-locate kernel.
+cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms, cudaEvent_t before_locate = nullptr);
 
 struct ApplyArgs {
     const uint64_t* sk;

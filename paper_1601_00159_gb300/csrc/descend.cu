@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_locate(DescendArgs a) {
 
 }  // namespace
 
-cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
+cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms, cudaEvent_t before_locate) {
     static bool attr_set = false;
     const int dyn = (int)((kSmemTopMax + kPad) * (sizeof(uint64_t) + sizeof(uint32_t)));
     if (!attr_set) {
@@ -437,6 +437,7 @@ cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms) {
         launch_dep(k_level, gblocks, kThreads, 0, s, a, l);
         ++g_launches;
     }
+    if (before_locate) cudaEventRecord(before_locate, s);
     launch_dep(k_locate, gblocks, kThreads, 0, s, a);
     ++g_launches;
     return cudaGetLastError();

@@ -289,12 +289,12 @@ cudaError_t alloc_storage(Storage& st, uint64_t cap) {
 constexpr uint32_t kProfSlots = 2048;
 // Per batch: 0 start, 1 after sort, 2 after waiting for the previous rebuild, 3 after
 // descent, 4 after apply, 5 after merge, 6 after layout, 7 rebuild start, 8 before the
-// rebuild's writer kernel, 9 rebuild end.
-constexpr int kProfEvents = 10;
+// rebuild's writer kernel, 9 rebuild end, 10 before the storage locate.
+constexpr int kProfEvents = 11;
 
 void prof_fold(pi_index* x) {
-    static const int from[PI_NUM_STAGES] = {0, 2, 3, 4, 5, 7, 8};
-    static const int to[PI_NUM_STAGES] = {1, 3, 4, 5, 6, 9, 9};
+    static const int from[PI_NUM_STAGES] = {0, 2, 3, 4, 5, 7, 8, 10};
+    static const int to[PI_NUM_STAGES] = {1, 3, 4, 5, 6, 9, 9, 3};
     for (uint32_t b = 0; b < x->pused; ++b) {
         cudaEvent_t* e = x->pev + (size_t)b * kProfEvents;
         cudaEventSynchronize(e[9]);
@@ -661,7 +661,7 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     da.val0 = sc.val0;
     da.n = (uint32_t)n;
     da.err = &x->d_meta->error;
-    if ((e = launch_descend(da, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    if ((e = launch_descend(da, s, x->num_sms, prof_event(x, 10))) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 3, s);
     ApplyArgs aa{};
     aa.sk = sc.a_k;
