@@ -195,7 +195,8 @@ typedef struct {
     uint64_t live;           /* live keys */
     uint64_t tombstones;     /* delete-flagged nodes still in the storage layer */
     uint32_t top_level;      /* H: highest level holding a key (1 if only storage) */
-    uint32_t bottom_built;   /* lowest materialised index level (2 unless it overflowed) */
+    uint32_t bottom_built;   /* lowest materialised index level (pi_config_t.lowest_level,
+                                raised when the index layer overflows its capacity) */
     uint32_t smem_low_level; /* lowest level staged in shared memory by the descent */
     uint32_t promote_shift;  /* b, with P = 2^-b */
     uint64_t level_size[34]; /* level_size[l] = live keys with height >= l, l = 1..33 */
@@ -208,6 +209,15 @@ typedef struct {
                                       re-layout) rather than scanning the storage layer */
 } pi_info_t;
 int pi_info(pi_index_t* idx, pi_info_t* out_host, pi_stream_t stream);
+
+/* Live keys, i.e. the size of level 1 (Definition 1), after the batches enqueued on
+ * `stream` (synchronises it). Returns PI_OK or, like pi_status, the sticky error. */
+int pi_size(pi_index_t* idx, uint64_t* size_out_host, pi_stream_t stream);
+
+/* H, the number of levels (Definition 1: level 1 is the storage layer, so H = 1 when no
+ * live key reaches level 2), after the batches enqueued on `stream` (synchronises it).
+ * Returns H >= 1, or a negative PI_ERR_* code. */
+int pi_num_levels(pi_index_t* idx, pi_stream_t stream);
 
 /* Live keys (level 1). *n_out_host = live count; up to cap pairs are written, in key
  * order, to the device arrays keys_out / vals_out. Synchronises `stream`. */

@@ -20,7 +20,7 @@ PI_MAX_BATCH = 1 << 28
 PI_MAX_KEYS = (1 << 30) - 2
 
 EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
-            "pi_last_error", "pi_status", "pi_info", "pi_export", "pi_export_level", "pi_profile",
+            "pi_last_error", "pi_status", "pi_info", "pi_size", "pi_num_levels", "pi_export", "pi_export_level", "pi_profile",
             "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush",
             "pi_range_search", "pi_multi_create", "pi_multi_execute", "pi_multi_destroy", "pi_multi_kernels_per_call",
             "pi_server_create", "pi_server_submit", "pi_server_wait", "pi_server_stats", "pi_server_replay",
@@ -123,6 +123,10 @@ def load_library(path: str = LIB_PATH):
     lib.pi_status.argtypes = [vp, vp]
     lib.pi_info.restype = i32
     lib.pi_info.argtypes = [vp, ctypes.POINTER(PiInfo), vp]
+    lib.pi_size.restype = i32
+    lib.pi_size.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), vp]
+    lib.pi_num_levels.restype = i32
+    lib.pi_num_levels.argtypes = [vp, vp]
     lib.pi_export.restype = i32
     lib.pi_export.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64), vp]
     lib.pi_export_level.restype = i32
@@ -245,6 +249,18 @@ class Index:
         out = PiInfo()
         _chk(self.lib.pi_info(self._h, ctypes.byref(out), _stream_handle(stream)), "pi_info")
         return out.as_dict()
+
+    def size(self, stream=None) -> int:
+        """Live keys (pi_size)."""
+        n = ctypes.c_uint64(0)
+        _chk(self.lib.pi_size(self._h, ctypes.byref(n), _stream_handle(stream)), "pi_size")
+        return n.value
+
+    def num_levels(self, stream=None) -> int:
+        """H, the number of levels (pi_num_levels)."""
+        h = self.lib.pi_num_levels(self._h, _stream_handle(stream))
+        _chk(min(h, 0), "pi_num_levels")
+        return h
 
     def export(self, stream=None):
         """Live (keys, vals) in key order as int64 CUDA tensors."""

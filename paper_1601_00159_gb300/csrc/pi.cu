@@ -1148,6 +1148,22 @@ int pi_info(pi_index_t* x, pi_info_t* out, pi_stream_t stream) {
     return sticky_error(m);
 }
 
+int pi_size(pi_index_t* x, uint64_t* out, pi_stream_t stream) {
+    if (!x || !out) return PI_ERR_INVALID_ARG;
+    cudaError_t e = sync_known(x, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return map_cuda(e);
+    *out = x->known.cnt[1];
+    return sticky_error(x->known);
+}
+
+int pi_num_levels(pi_index_t* x, pi_stream_t stream) {
+    if (!x) return PI_ERR_INVALID_ARG;
+    cudaError_t e = sync_known(x, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return map_cuda(e);
+    if (int rc = sticky_error(x->known)) return rc;
+    return (int)x->known.H;
+}
+
 int pi_export(pi_index_t* x, uint64_t* keys_out, uint64_t* vals_out, uint64_t cap, uint64_t* n_out_host,
               pi_stream_t stream) {
     if (!x || !n_out_host || (cap > 0 && (!keys_out || !vals_out))) return PI_ERR_INVALID_ARG;

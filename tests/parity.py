@@ -53,11 +53,13 @@ def assert_state_equal(idx, orc, ctx="", check_levels=True):
     assert np.array_equal(gv, ov), f"{ctx}: values differ"
     info = idx.info()
     assert info["live"] == len(ok)
+    assert idx.size() == len(ok), f"{ctx}: pi_size {idx.size()} vs oracle {len(ok)}"
     assert idx.status() == 0, f"{ctx}: device error status {idx.status()}"
     if not check_levels:
         return info
     top = orc.num_levels()
     assert info["top_level"] == max(top, 1), f"{ctx}: top level {info['top_level']} vs {top}"
+    assert idx.num_levels() == max(top, 1), f"{ctx}: pi_num_levels {idx.num_levels()} vs {top}"
     prev_keys = ok
     for level in range(2, top + 1):
         lv = idx.export_level(level)
