@@ -96,6 +96,11 @@ typedef struct {
  * significant varying key bytes, so the fix-up that orders key-prefix segments sees
  * many long segments. The default is four passes. */
 #define PI_TEST_SORT_PREFIX(k) ((uint32_t)(k) << 4)
+/* test_flags bit: debug check of single ownership (Section 3.2.4). Each batch counts the
+ * writes to every storage node (4 B per node of capacity); a node written twice records
+ * a sticky error (pi_status then returns PI_ERR_CUDA), and pi_info's
+ * owner_checked_writes sums the writes checked. The batching form is not checked. */
+#define PI_TEST_OWNER_CHECK 0x100u
 
 /*
  * pi_create -- bulk-build an index from n (key, value) pairs (Section 3.1: the index
@@ -207,12 +212,27 @@ typedef struct {
     uint64_t kernel_launches; /* CUDA kernels the batch entry points have launched so far */
     uint64_t incremental_rebuilds; /* rebuilds that updated the previous levels (no storage
                                       re-layout) rather than scanning the storage layer */
+    uint64_t owner_checked_writes; /* PI_TEST_OWNER_CHECK: storage-node writes checked */
 } pi_info_t;
 int pi_info(pi_index_t* idx, pi_info_t* out_host, pi_stream_t stream);
 
 /* Live keys, i.e. the size of level 1 (Definition 1), after the batches enqueued on
  * `stream` (synchronises it). Returns PI_OK or, like pi_status, the sticky error. */
 int pi_size(pi_index_t* idx, uint64_t* size_out_host, pi_stream_t stream);
+
+/*
+ * Failure-path support (no counterpart in the paper).
+ * pi_test_fail_allocations: the next `count` device allocations the library makes on the
+ *   calling host thread fail as if the device were out of memory (0 clears). The call
+ *   that hits one returns PI_ERR_OOM and leaves the index as it was.
+ * pi_selftest_wait: launches one CTA that waits, through the bounded look-back the batch
+ *   kernels use, for a predecessor that never publishes. The wait gives up after its
+ *   spin bound (about half a second), records the timeout in a scratch error word, which
+ *   is written to *err_word_host, and the kernel returns. Returns PI_ERR_TIMEOUT when the
+ *   bound worked. Allocates and frees 516 B of device memory; synchronises `stream`.
+ */
+void pi_test_fail_allocations(uint32_t count);
+int pi_selftest_wait(uint32_t* err_word_host, pi_stream_t stream);
 
 /* H, the number of levels (Definition 1: level 1 is the storage layer, so H = 1 when no
  * live key reaches level 2), after the batches enqueued on `stream` (synchronises it).

@@ -20,7 +20,8 @@ PI_MAX_BATCH = 1 << 28
 PI_MAX_KEYS = (1 << 30) - 2
 
 EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
-            "pi_last_error", "pi_status", "pi_info", "pi_size", "pi_num_levels", "pi_export", "pi_export_level", "pi_profile",
+            "pi_last_error", "pi_status", "pi_info", "pi_size", "pi_test_fail_allocations",
+            "pi_selftest_wait", "pi_num_levels", "pi_export", "pi_export_level", "pi_profile",
             "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush",
             "pi_range_search", "pi_multi_create", "pi_multi_execute", "pi_multi_destroy", "pi_multi_kernels_per_call",
             "pi_server_create", "pi_server_submit", "pi_server_wait", "pi_server_stats", "pi_server_replay",
@@ -30,6 +31,7 @@ PI_MULTI_MAX_BATCH = 1 << 20
 PI_NOALLOC_MAX_BATCH = 1 << 16
 PI_TEST_WALK_LEVELS = 1
 PI_TEST_SORT_FULL = 2
+PI_TEST_OWNER_CHECK = 0x100
 
 
 def PI_TEST_SORT_PREFIX(k: int) -> int:
@@ -85,7 +87,7 @@ class PiInfo(ctypes.Structure):
                 ("level_size", ctypes.c_uint64 * 34), ("storage_capacity", ctypes.c_uint64),
                 ("index_capacity", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("rebuilds", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("incremental_rebuilds", ctypes.c_uint64)]
+                ("incremental_rebuilds", ctypes.c_uint64), ("owner_checked_writes", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "level_size"}
@@ -123,6 +125,10 @@ def load_library(path: str = LIB_PATH):
     lib.pi_status.argtypes = [vp, vp]
     lib.pi_info.restype = i32
     lib.pi_info.argtypes = [vp, ctypes.POINTER(PiInfo), vp]
+    lib.pi_test_fail_allocations.restype = None
+    lib.pi_test_fail_allocations.argtypes = [ctypes.c_uint32]
+    lib.pi_selftest_wait.restype = i32
+    lib.pi_selftest_wait.argtypes = [ctypes.POINTER(ctypes.c_uint32), vp]
     lib.pi_size.restype = i32
     lib.pi_size.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), vp]
     lib.pi_num_levels.restype = i32
@@ -178,6 +184,20 @@ def _check_dev(t, dtype, name):
 def _chk(rc: int, what: str):
     if rc != PI_OK:
         raise PiError(rc, what)
+
+
+def test_fail_allocations(count: int) -> None:
+    """The next `count` device allocations of the library on this thread fail as out of
+    memory (pi_test_fail_allocations)."""
+    load_library().pi_test_fail_allocations(count)
+
+
+def selftest_wait(stream=None):
+    """(return code, error word) of pi_selftest_wait: a bounded wait on a flag that nothing
+    sets must give up with PI_ERR_TIMEOUT."""
+    w = ctypes.c_uint32(0)
+    rc = load_library().pi_selftest_wait(ctypes.byref(w), _stream_handle(stream))
+    return rc, w.value
 
 
 class Index:

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
         const bool fin_live = (pw >> 30) == 1u;
         if (exists) {
             const uint32_t r = a.loc[dj] - 1u;
+            if (a.wcount) atomicAdd(&a.wcount[r], 1u);
             const uint8_t mt = SM[r];
             const uint32_t h = mt & kHeightMask;
             if (fin_live) {
@@ -310,6 +311,31 @@ __global__ void __launch_bounds__(kThreads) k_new_pack(ApplyArgs a) {
     }
 }
 
+// Debug check of single ownership (Section 3.2.4): after k_apply, every storage node
+// has been written by at most one query. Counts are summed into DevMeta::owner_writes
+// and cleared for the next batch.
+__global__ void __launch_bounds__(kThreads) k_owner_check(ApplyArgs a) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ uint32_t s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
+    const uint32_t size = a.m->size;
+    uint32_t sum = 0;
+    for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < size; i += gridDim.x * kThreads) {
+        const uint32_t c = a.wcount[i];
+        if (c) {
+            sum += c;
+            if (c > 1u) atomicOr(a.err, kErrOwner);
+            a.wcount[i] = 0u;
+        }
+    }
+    sum = __reduce_add_sync(0xffffffffu, sum);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&s_sum, sum);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_sum) atomicAdd(&a.m->owner_writes, s_sum);
+}
+
 }  // namespace
 
 cudaError_t launch_apply(const ApplyArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
@@ -322,6 +348,13 @@ cudaError_t launch_apply(const ApplyArgs& a, uint32_t& epoch, cudaStream_t s, in
     launch_dep(k_new_scan, 1, 1024, 0, s, a);
     ++g_launches;
     launch_dep(k_new_pack, tiles, kThreads, 0, s, a);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_owner_check(const ApplyArgs& a, cudaStream_t s, int num_sms) {
+    if (!a.wcount) return cudaSuccess;
+    launch_dep(k_owner_check, (uint32_t)num_sms * 8u, kThreads, 0, s, a);
     ++g_launches;
     return cudaGetLastError();
 }

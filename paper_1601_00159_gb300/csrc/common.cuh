@@ -21,6 +21,7 @@ constexpr uint32_t kSubTile = 256;      // sorted queries per descent warp step 
 // Sticky error bits in DevMeta::error.
 constexpr uint32_t kErrTimeout = 1u;  // a bounded wait gave up
 constexpr uint32_t kErrBounds = 2u;   // an internal bound check refused an access
+constexpr uint32_t kErrOwner = 4u;    // debug check: a storage node had two writers in one batch
 
 // Bounded spins: a look-back or barrier wait gives up after this many polls (about
 // half a second with the back-off below) and records kErrTimeout instead of hanging.
@@ -47,6 +48,7 @@ struct DevMeta {
     uint32_t lcur;         // which of the two index-layer buffers holds the built levels
     uint32_t levels_exact; // 1: the built levels hold exactly the live keys of their heights
     uint32_t inc_rebuilds; // rebuilds that updated the previous levels instead of scanning
+    uint32_t owner_writes; // debug check: storage-node writes counted so far
     uint32_t cnt[kLevelSlots];   // live keys with height >= l, kept current every batch
     uint32_t n[kLevelSlots];     // n[l]: size of built level l
     uint32_t base[kLevelSlots];  // built level l occupies [base[l], base[l] + n[l]] (+ sentinel)
@@ -600,8 +602,16 @@ struct ApplyArgs {
     uint32_t n;
     HashParams hp;
     uint32_t* err;
+    uint32_t* wcount;  // debug check (null when off): writes per storage node in this batch
 };
 cudaError_t launch_apply(const ApplyArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);
+// Debug check of single ownership: every storage node written at most once by the
+// batch's apply (sets kErrOwner otherwise); adds the writes to DevMeta::owner_writes and
+// clears the counts.
+cudaError_t launch_owner_check(const ApplyArgs& a, cudaStream_t s, int num_sms);
+// Failure-path self-test: one CTA waits, by the batch kernels' bounded look-back, for a
+// predecessor that never publishes (desc: 64 zeroed words; err: zeroed word).
+cudaError_t launch_wait_selftest(uint64_t* desc, uint32_t* err, cudaStream_t s);
 
 struct RebuildArgs {
     Storage st;

@@ -106,6 +106,8 @@ struct pi_index {
     uint64_t* desc = nullptr;
     uint64_t desc_words = 0;
     uint32_t* lcnt = nullptr;  // per-level per-tile live counts: 32 rows x lstride
+    uint32_t* wcount = nullptr;  // PI_TEST_OWNER_CHECK: writes per storage node in a batch
+    uint64_t wcap = 0;
     uint32_t* loff = nullptr;  // rebuild offsets, same shape
     uint32_t lstride = 0;
     uint32_t epoch = 1;
@@ -136,9 +138,16 @@ struct pi_index {
 
 namespace {
 
+// pi_test_fail_allocations: device allocations of this host thread still to fail.
+thread_local uint32_t g_fail_allocs = 0;
+
 template <typename T>
 cudaError_t dalloc(T** p, uint64_t count) {
     *p = nullptr;
+    if (g_fail_allocs > 0) {  // injected failure, as if the device were out of memory
+        --g_fail_allocs;
+        return cudaErrorMemoryAllocation;
+    }
     if (count == 0) count = 1;
     return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
@@ -203,6 +212,17 @@ cudaError_t ensure_tile_cnt(pi_index* x, uint64_t st_cap) {
     if (e == cudaSuccess) e = cudaMemset(x->lcnt, 0, 32 * stride * sizeof(uint32_t));
     x->lstride = (e == cudaSuccess) ? (uint32_t)stride : 0u;
     x->force_rebuild = true;
+    return e;
+}
+
+// PI_TEST_OWNER_CHECK: one zeroed write counter per storage node.
+cudaError_t ensure_wcount(pi_index* x, uint64_t st_cap) {
+    if (!(x->test_flags & PI_TEST_OWNER_CHECK) || x->wcap >= st_cap) return cudaSuccess;
+    dfree(x->wcount);
+    x->wcap = 0;
+    cudaError_t e = dalloc(&x->wcount, st_cap + 1);
+    if (e == cudaSuccess) e = cudaMemset(x->wcount, 0, (st_cap + 1) * sizeof(uint32_t));
+    if (e == cudaSuccess) x->wcap = st_cap;
     return e;
 }
 
@@ -331,7 +351,7 @@ void destroy(pi_index* x) {
     dfree(x->stg.ops); dfree(x->stg.keys); dfree(x->stg.vals); dfree(x->stg.res);
     free_storage(x->st);
     dfree(x->lkeys); dfree(x->ldown); dfree(x->lkeys1); dfree(x->ldown1);
-    dfree(x->desc); dfree(x->lcnt); dfree(x->loff); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
+    dfree(x->desc); dfree(x->lcnt); dfree(x->loff); dfree(x->wcount); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
     if (x->h_mbox) cudaFreeHost(x->h_mbox);
     if (x->ev_applied) cudaEventDestroy(x->ev_applied);
     if (x->ev_rebuilt) cudaEventDestroy(x->ev_rebuilt);
@@ -426,6 +446,7 @@ cudaError_t grow_storage(pi_index* x, uint64_t need, cudaStream_t s) {
     x->st_cap = cap;
     x->known.cur = 0;
     if ((e = ensure_tile_cnt(x, cap)) != cudaSuccess) return e;
+    if ((e = ensure_wcount(x, cap)) != cudaSuccess) return e;
     return ensure_desc(x, desc_need(x->sc.cap, cap));
 }
 
@@ -690,7 +711,9 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     aa.n = (uint32_t)n;
     aa.hp = x->hp;
     aa.err = &x->d_meta->error;
+    aa.wcount = x->wcount;
     if ((e = launch_apply(aa, ep, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    if ((e = launch_owner_check(aa, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 4, s);
     RebuildArgs ra = rebuild_args(x, bm, (uint32_t)size_ub, x->force_rebuild ? 1u : 0u);
     ra.nn = sc.nn;
@@ -815,6 +838,7 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
         if ((e = alloc_storage(x->st, st_cap)) != cudaSuccess) break;
         x->st_cap = st_cap;
         if ((e = ensure_tile_cnt(x, st_cap)) != cudaSuccess) break;
+        if ((e = ensure_wcount(x, st_cap)) != cudaSuccess) break;
         if ((e = ensure_desc(x, desc_need(n, st_cap))) != cudaSuccess) break;
         // 1. sort (key, arrival) and keep the last of every key run
         if (n > 0) {
@@ -1145,7 +1169,30 @@ int pi_info(pi_index_t* x, pi_info_t* out, pi_stream_t stream) {
     out->rebuilds = m.rebuilds;
     out->kernel_launches = x->launches;
     out->incremental_rebuilds = m.inc_rebuilds;
+    out->owner_checked_writes = m.owner_writes;
     return sticky_error(m);
+}
+
+void pi_test_fail_allocations(uint32_t count) { g_fail_allocs = count; }
+
+int pi_selftest_wait(uint32_t* err_word_host, pi_stream_t stream) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint64_t* desc = nullptr;
+    uint32_t* err = nullptr;
+    cudaError_t e = dalloc(&desc, 64);
+    if (e == cudaSuccess) e = dalloc(&err, 1);
+    uint32_t w = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(desc, 0, 64 * sizeof(uint64_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = launch_wait_selftest(desc, err, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&w, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(desc);
+    dfree(err);
+    if (e != cudaSuccess) return map_cuda(e);
+    if (err_word_host) *err_word_host = w;
+    if (w & kErrTimeout) return PI_ERR_TIMEOUT;
+    return w ? PI_ERR_CUDA : PI_OK;
 }
 
 int pi_size(pi_index_t* x, uint64_t* out, pi_stream_t stream) {

@@ -713,6 +713,13 @@ __global__ void __launch_bounds__(kThreads) k_export_live(Storage st, const DevM
     }
 }
 
+// Failure-path self-test: tile 1 waits for tile 0, which never publishes, so the
+// bounded look-back must give up, record kErrTimeout and return.
+__global__ void k_wait_selftest(uint64_t* desc, uint32_t* err) {
+    bool ok = true;
+    lookback_warp<false>(desc, 1u, 1u, 0u, err, &ok);
+}
+
 }  // namespace
 
 cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
@@ -776,6 +783,12 @@ cudaError_t launch_export_live(const Storage& st, const DevMeta* m, uint64_t* ke
     const uint32_t c = (uint32_t)num_sms * 4u;
     launch_dep(k_export_live, (int)(tiles < c ? tiles : c), kThreads, 0, s, st, m, keys_out, vals_out, cap, count, desc,
                                                                    tile_ctr, ++epoch, err);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(uint64_t* desc, uint32_t* err, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(desc, err);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -223,3 +223,28 @@ def test_incremental_level_rebuild(orc_mod, lowest, p):
     assert info["incremental_rebuilds"] >= 4, info["incremental_rebuilds"]
     idx.close()
     orc.close()
+
+
+def _distinct_writes(batches):
+    """Distinct keys written (valid inserts and deletes) per batch, summed."""
+    total = 0
+    for b in batches:
+        valid = (b.ops == wl.OP_INSERT) | (b.ops == wl.OP_DELETE)
+        valid &= b.keys != np.uint64(0xFFFFFFFFFFFFFFFF)
+        total += len(np.unique(b.keys[valid]))
+    return total
+
+
+@pytest.mark.parametrize("kr", [16, 700, 1 << 40])
+def test_single_owner_per_storage_node(orc_mod, kr):
+    """Section 3.2.4: every storage node is modified by exactly one owner per batch. The
+    debug check counts the writes to every node; a second write would leave a sticky
+    error that the state comparison (pi_status) reports."""
+    from paper_1601_00159_gb300 import PI_TEST_OWNER_CHECK
+    w = wl.random_small(60 + kr % 89, 3000, 30000, kr, p=0.25, n_batches=4)
+    info = run_workload(orc_mod, w, config={"test_flags": PI_TEST_OWNER_CHECK})
+    assert 0 < info["owner_checked_writes"] <= _distinct_writes(w.batches)
+    w2 = wl.skewed(seed=9, n=1 << 18, q=1 << 16, n_batches=3)  # Zipf hot keys: long same-key runs
+    info2 = run_workload(orc_mod, w2, config={"test_flags": PI_TEST_OWNER_CHECK})
+    w2b = w2.batches() if callable(w2.batches) else w2.batches
+    assert 0 < info2["owner_checked_writes"] <= _distinct_writes(list(w2b)[:3])
