@@ -15,10 +15,9 @@
 //    state to the storage node (value, delete flag), or emits a new node when the key
 //    is not in the storage layer and ends up present (Algorithm 4, insertNode).
 //
-// The max-scan is split across kernels so no tile ever waits on another: the descent
-// already walks the sorted batch, leaves each 2048-query tile's maximum e in tile_max
-// and turns those into exclusive tile prefixes (tile_pref); k_apply is then
-// fully data-parallel. The descent stored one result per distinct key -- per local
+// The max-scan is split across kernels so no tile of k_apply ever waits on another:
+// the descent's first kernel already walks the sorted batch and leaves each 2048-query
+// tile's exclusive max prefix of e (tile_pref); k_apply is then fully data-parallel. The descent stored one result per distinct key -- per local
 // run head (a query whose key differs from the previous one, and the first query of
 // every 256-query sub-tile) in sorted order -- so a query's storage-layer state is
 // found at its run head's dense index.

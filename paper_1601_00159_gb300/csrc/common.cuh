@@ -15,6 +15,8 @@ constexpr uint8_t kHeightMask = 0x3F;
 constexpr uint32_t kSmemTopMax = 2048;  // index entries staged in shared memory
 constexpr uint32_t kPad = 64;           // readable entries past every array's end
 constexpr uint32_t kSortTile = 2048;    // elements per radix-sort tile
+constexpr uint32_t kScanGroup = 64;     // radix-sort tiles per group of the count kernel's scan
+constexpr uint32_t kCtrDistinct = 14;   // BatchMeta::tile_ctr slot of the distinct-key kernel
 constexpr uint32_t kApplyTile = 2048;   // sorted queries per apply tile
 constexpr uint32_t kSubTile = 256;      // sorted queries per descent warp step (one apply warp)
 
@@ -531,11 +533,12 @@ struct SortBuffers {
     uint32_t* a_p;
     uint64_t* b_k;
     uint32_t* b_p;
-    uint32_t* dofs;  // [256] digit totals of the current pass
+    uint32_t* dofs;  // [256] digit bases (first output slot of each digit) of the current pass
     uint64_t* desc;  // [tiles][256] look-back descriptors
-    uint32_t* tile_max;  // per-apply-tile max run marker, cleared by the plan kernel (may be null)
     uint32_t* tcnt;      // [tiles][256] per-tile digit counts of the current pass
-    uint32_t* toff;      // [tiles][256] per-tile digit offsets of the current pass
+    uint32_t* toff;      // [tiles][256] per-tile digit offsets within the tile's group
+    uint32_t* gsum;      // [groups][256] per-group digit totals, then the groups' offsets
+    uint32_t* gctr;      // [8][groups + 1] arrival counters of the count kernel's CTAs
     uint8_t* ndig;       // next pass's digit of every element, in the current pass's output order
     uint32_t* fixmap;    // [ceil(n / 32)] bit per position: start of a segment to reorder
 };
@@ -550,11 +553,10 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
 struct DescendArgs {
     const uint64_t* sk;  // sorted keys
     const uint32_t* sp;  // sorted payload (op << 30 | arrival index)
-    uint32_t* tile_max;  // per-apply-tile max of the run markers e_i (atomicMax)
-    uint32_t* tile_pref; // per-apply-tile exclusive max prefix
-    uint64_t* hq;        // distinct keys per 256-query sub-tile (holey, sub * 256 + j)
-    uint32_t* sub_cnt;   // distinct keys per sub-tile
+    uint32_t* tile_pref; // per-apply-tile exclusive max prefix of the run markers e_i
     uint32_t* sub_pref;  // dense index of each sub-tile's first distinct key
+    uint64_t* desc;      // look-back descriptors: [0, tiles) head counts, [tiles, 2 tiles) maxima
+    uint32_t epoch;      // tags this batch's descriptors
     uint64_t* dq;        // dense distinct keys
     uint32_t* dlo;       // their current start position on the level being searched
     int top_launched;    // highest index level given its own launch (see launch_descend)
@@ -588,7 +590,6 @@ struct ApplyArgs {
     DevMeta* m;
     BatchMeta* bm;
     uint64_t* desc;  // unused
-    uint32_t* tile_max;   // per-tile max run marker (from the descent)
     uint32_t* tile_pref;  // per-tile exclusive prefix (max, then reused for new-node sums)
     uint32_t* tile_new;   // per-tile new-node count
     const uint32_t* sub_pref;  // dense index of each 256-query sub-tile's first distinct key

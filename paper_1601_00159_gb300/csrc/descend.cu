@@ -11,11 +11,10 @@
 //
 // The descent is level-synchronous over the whole batch -- the paper's group query
 // processing (Section 4.4.3) with the group being every distinct key of the batch:
-//  k_distinct   per 256-query sub-tile, one warp compacts the distinct keys (run
-//               heads, plus the sub-tile's first query) and records their count; it
-//               also folds the ownership markers into the apply tiles' maxima;
-//  k_dscan      one CTA prefixes the sub-tile counts (dense index of every distinct
-//               key) and the apply tiles' maxima;
+//  k_distinct   per 256-query sub-tile, one warp finds the distinct keys (run heads,
+//               plus the sub-tile's first query); a look-back over the apply tiles
+//               gives their dense index, so they are written densely at once, and the
+//               apply tiles' exclusive max prefixes of the ownership markers;
 //  k_top        the levels pinned in shared memory (copied once per CTA by TMA bulk
 //               copies) are resolved by one binary search of the lowest pinned level,
 //               which holds every key of the levels above it; writes the dense key and
@@ -184,18 +183,12 @@ __device__ __forceinline__ int32_t smem_rank(const uint64_t* K, uint32_t n, uint
     return (int32_t)lo - 1;
 }
 
-// Per 256-query sub-tile (one warp each): local run heads -> holey key list, count,
-// and the apply tile's maximum ownership marker.
-__global__ void __launch_bounds__(kThreads) k_distinct(DescendArgs a) {
-    pdl_wait();
-    pdl_trigger();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
-    const uint32_t n = a.n;
-    const uint32_t qv = n - a.bm->invalid;
-    const uint32_t sub = blockIdx.x * (kThreads / 32) + warp;
-    const uint32_t nsub = (n + kSubTile - 1) / kSubTile;
-    if (sub >= nsub) return;
+// Local run heads of one 256-query sub-tile (a run head, or the sub-tile's first query),
+// by one warp. Pass 0 returns their count and the largest ownership marker e_i (see
+// apply.cu); pass 1 writes the heads' keys to dq from dense index d0 on.
+__device__ __forceinline__ uint32_t subtile_heads(const DescendArgs& a, uint32_t sub, uint32_t qv, bool write,
+                                                  uint32_t d0, uint32_t* emax_out) {
+    const int lane = threadIdx.x & 31;
     const uint32_t sb = sub * kSubTile;
     const uint32_t lt = lanemask_lt();
     uint32_t nq = 0, emax = 0;
@@ -205,92 +198,78 @@ __global__ void __launch_bounds__(kThreads) k_distinct(DescendArgs a) {
         const uint32_t i = sb + (uint32_t)k * 32u + (uint32_t)lane;
         const bool valid = i < qv;
         const uint64_t q = valid ? a.sk[i] : kMaxKey;
-        const uint32_t op = valid ? (a.sp[i] >> 30) : 0u;
         uint64_t prev = __shfl_up_sync(0xffffffffu, q, 1);
         if (lane == 0) prev = carry;
         carry = __shfl_sync(0xffffffffu, q, 31);
         const bool head = valid && (i == 0 || q != prev);
         const bool local = valid && (head || (k == 0 && lane == 0));
-        const uint32_t e = (valid && (op == 1u || op == 2u)) ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
-        emax = max(emax, e);
+        if (!write) {
+            const uint32_t op = valid ? (a.sp[i] >> 30) : 0u;
+            const uint32_t e = (valid && (op == 1u || op == 2u)) ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
+            emax = max(emax, e);
+        }
         const uint32_t b = __ballot_sync(0xffffffffu, local);
-        if (local) a.hq[sb + nq + __popc(b & lt)] = q;
+        if (write && local) a.dq[d0 + nq + __popc(b & lt)] = q;
         nq += __popc(b);
     }
-    emax = __reduce_max_sync(0xffffffffu, emax);
-    if (lane == 0) {
-        if (emax) atomicMax(&a.tile_max[sb / kApplyTile], emax);
-        a.sub_cnt[sub] = nq;
-    }
+    if (emax_out) *emax_out = __reduce_max_sync(0xffffffffu, emax);
+    return nq;
 }
 
-// One CTA: dense index of every sub-tile's first distinct key (exclusive sum of the
-// counts), the number of distinct keys, and the apply tiles' exclusive max prefixes.
-// Each thread takes a contiguous run of entries, so there is one block scan per array.
-__global__ void __launch_bounds__(1024) k_dscan(DescendArgs a) {
+// The distinct keys of the sorted batch, densely (one CTA per 2048-query apply tile,
+// one warp per 256-query sub-tile, tiles taken in CTA start order): each warp counts
+// its sub-tile's local run heads; two warps then look back over the earlier tiles, one
+// for the sum of the counts (the tile's first dense index) and one for the maximum
+// ownership marker (the apply tile's exclusive prefix, so k_apply never waits); each
+// warp then writes its heads' keys to dq and its sub-tile's first dense index to
+// sub_pref. The last tile records the number of distinct keys.
+__global__ void __launch_bounds__(kThreads) k_distinct(DescendArgs a) {
     pdl_wait();
     pdl_trigger();
-    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_tile, s_base, s_mpref;
+    __shared__ uint32_t s_cnt[kThreads / 32], s_max[kThreads / 32];
+    __shared__ bool s_ok;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (block_sees_error(&a.m->error)) return;
-    {
-        // Thread t owns sub-tiles [16t, 16t + 16): four 16-byte loads, kept in registers
-        // for the write-back (sub_cnt has room for whole groups of 16).
-        const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
-        constexpr uint32_t kPer = 16;
-        uint32_t sum = 0, tot = 0, carry = 0;
-        for (uint32_t g0 = 0; g0 < nsub; g0 += 1024u * kPer) {
-            const uint32_t t0 = g0 + threadIdx.x * kPer;
-            uint32_t v[kPer];
-            if (t0 + kPer <= nsub) {
-                const uint4* p = reinterpret_cast<const uint4*>(a.sub_cnt + t0);
-#pragma unroll
-                for (uint32_t k = 0; k < kPer / 4; ++k) {
-                    const uint4 w = p[k];
-                    v[4 * k] = w.x;
-                    v[4 * k + 1] = w.y;
-                    v[4 * k + 2] = w.z;
-                    v[4 * k + 3] = w.w;
-                }
-            } else {
-#pragma unroll
-                for (uint32_t k = 0; k < kPer; ++k) v[k] = t0 + k < nsub ? a.sub_cnt[t0 + k] : 0u;
-            }
-            sum = 0;
-#pragma unroll
-            for (uint32_t k = 0; k < kPer; ++k) sum += v[k];
-            uint32_t run = carry + block_excl_sum<1024>(sum, s_tmp, &tot);
-#pragma unroll
-            for (uint32_t k = 0; k < kPer; ++k) {
-                if (t0 + k < nsub) a.sub_pref[t0 + k] = run;
-                run += v[k];
-            }
-            carry += tot;
-        }
-        if (threadIdx.x == 0) a.bm->distinct = carry;
+    if (tid == 0) {
+        s_tile = atomicAdd(&a.bm->tile_ctr[kCtrDistinct], 1u);
+        s_ok = true;
     }
-    {
-        const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
-        const uint32_t per = (ntiles + 1023u) / 1024u;
-        const uint32_t t0 = min(threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
-        uint32_t mx = 0;
-        for (uint32_t t = t0; t < t1; ++t) mx = max(mx, a.tile_max[t]);
-        uint32_t run = block_excl_max<1024>(mx, s_tmp, nullptr);
-        for (uint32_t t = t0; t < t1; ++t) {
-            a.tile_pref[t] = run;
-            run = max(run, a.tile_max[t]);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t n = a.n, qv = n - a.bm->invalid;
+    const uint32_t nsub = (n + kSubTile - 1) / kSubTile, ntiles = (n + kApplyTile - 1) / kApplyTile;
+    if (tile >= ntiles) return;
+    const uint32_t sub = tile * (kApplyTile / kSubTile) + (uint32_t)warp;
+    uint32_t emax = 0, nq = 0;
+    if (sub < nsub) nq = subtile_heads(a, sub, qv, false, 0u, &emax);
+    if (lane == 0) {
+        s_cnt[warp] = nq;
+        s_max[warp] = emax;
+    }
+    __syncthreads();
+    if (warp < 2) {
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) tot = warp == 0 ? tot + s_cnt[w] : max(tot, s_max[w]);
+        bool ok = true;
+        const uint32_t ex = warp == 0 ? lookback_warp<false>(a.desc, tile, a.epoch, tot, a.err, &ok)
+                                      : lookback_warp<true>(a.desc + ntiles, tile, a.epoch, tot, a.err, &ok);
+        if (lane == 0) {
+            if (warp == 0) s_base = ex;
+            else s_mpref = ex;
+            if (!ok) s_ok = false;
+            if (warp == 0 && tile == ntiles - 1) a.bm->distinct = ex + tot;
         }
     }
-}
-__global__ void __launch_bounds__(kThreads) k_dpack(DescendArgs a) {
-    pdl_wait();
-    pdl_trigger();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
-    const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
-    const uint32_t sub = blockIdx.x * (kThreads / 32) + warp;
+    __syncthreads();
+    if (!s_ok) return;  // a look-back gave up (kErrTimeout is recorded); the batch stops
+    if (tid == 0) a.tile_pref[tile] = s_mpref;
     if (sub >= nsub) return;
-    const uint32_t c = a.sub_cnt[sub], d0 = a.sub_pref[sub];
-    for (uint32_t j = (uint32_t)lane; j < c; j += 32u) a.dq[d0 + j] = a.hq[sub * kSubTile + j];
+    uint32_t d0 = s_base;
+    for (int w = 0; w < warp; ++w) d0 += s_cnt[w];
+    if (lane == 0) a.sub_pref[sub] = d0;
+    subtile_heads(a, sub, qv, true, d0, nullptr);
 }
 
 // Start position below the pinned levels for every distinct key (one per thread): one
@@ -417,13 +396,8 @@ cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms, cu
         attr_set = true;
     }
     if (a.n == 0) return cudaSuccess;
-    const uint32_t nsub = (a.n + kSubTile - 1) / kSubTile;
-    const uint32_t blocks = (nsub + 7) / 8;
-    launch_dep(k_distinct, blocks, kThreads, 0, s, a);
-    ++g_launches;
-    launch_dep(k_dscan, 1, 1024, 0, s, a);
-    ++g_launches;
-    launch_dep(k_dpack, blocks, kThreads, 0, s, a);
+    const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
+    launch_dep(k_distinct, ntiles, kThreads, 0, s, a);
     ++g_launches;
     const uint32_t need = (a.n + kThreads - 1) / kThreads;
     launch_dep(k_top, need, kThreads, dyn, s, a);  // CTAs past the distinct keys exit at once

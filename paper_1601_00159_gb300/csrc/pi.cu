@@ -40,11 +40,12 @@ struct Scratch {
     uint64_t* val0 = nullptr;
     NewNodes nn{};
     NewNodes stage{};
-    uint32_t* tile_max = nullptr;
     uint32_t* tile_pref = nullptr;
     uint32_t* tile_new = nullptr;
     uint32_t* tcnt = nullptr;  // radix sort: per-tile digit counts
     uint32_t* toff = nullptr;  // radix sort: per-tile digit offsets
+    uint32_t* gsum = nullptr;  // radix sort: per-group digit totals / offsets
+    uint32_t* gctr = nullptr;  // radix sort: the count kernels' arrival counters
     uint8_t* ndig = nullptr;   // radix sort: next pass's digits
     uint32_t* fixmap = nullptr;  // radix sort: segment marks of the prefix fix-up
     LevelChanges cstage{};       // apply: per-tile staging of level membership changes
@@ -56,8 +57,6 @@ struct Scratch {
     int32_t* lst_pref = nullptr;
     uint8_t* lst_ins = nullptr;
     uint64_t lst_cap = 0;
-    uint64_t* hq = nullptr;    // descent: distinct keys per sub-tile
-    uint32_t* sub_cnt = nullptr;
     uint32_t* sub_pref = nullptr;
     uint64_t* dq = nullptr;    // descent: dense distinct keys
     uint32_t* dlo = nullptr;   // descent: per-key start position
@@ -241,12 +240,12 @@ void free_scratch(Scratch& s) {
     dfree(s.loc); dfree(s.flags); dfree(s.val0);
     dfree(s.nn.keys); dfree(s.nn.vals); dfree(s.nn.loc); dfree(s.nn.height);
     dfree(s.stage.keys); dfree(s.stage.vals); dfree(s.stage.loc); dfree(s.stage.height);
-    dfree(s.tile_max); dfree(s.tile_pref); dfree(s.tile_new);
-    dfree(s.tcnt); dfree(s.toff); dfree(s.ndig); dfree(s.fixmap);
+    dfree(s.tile_pref); dfree(s.tile_new);
+    dfree(s.tcnt); dfree(s.toff); dfree(s.ndig); dfree(s.fixmap); dfree(s.gsum); dfree(s.gctr);
     dfree(s.cstage.keys); dfree(s.cstage.pos); dfree(s.cstage.hl); dfree(s.chg.keys); dfree(s.chg.pos); dfree(s.chg.hl);
     dfree(s.tile_chg); dfree(s.tile_chg_pref);
     dfree(s.lst_keys); dfree(s.lst_pos); dfree(s.lst_pref); dfree(s.lst_ins);
-    dfree(s.hq); dfree(s.sub_cnt); dfree(s.sub_pref); dfree(s.dq); dfree(s.dlo);
+    dfree(s.sub_pref); dfree(s.dq); dfree(s.dlo);
     s.cap = 0;
 }
 
@@ -264,9 +263,11 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     const uint64_t cs = tiles * kApplyTile;
     PI_TRY(dalloc(&s.stage.keys, cs)); PI_TRY(dalloc(&s.stage.vals, cs));
     PI_TRY(dalloc(&s.stage.loc, cs)); PI_TRY(dalloc(&s.stage.height, cs));
-    PI_TRY(dalloc(&s.tile_max, tiles)); PI_TRY(dalloc(&s.tile_pref, tiles)); PI_TRY(dalloc(&s.tile_new, tiles));
+    PI_TRY(dalloc(&s.tile_pref, tiles)); PI_TRY(dalloc(&s.tile_new, tiles));
     const uint64_t stiles = (q + kSortTile - 1) / kSortTile + 1;
     PI_TRY(dalloc(&s.tcnt, stiles * 256)); PI_TRY(dalloc(&s.toff, stiles * 256));
+    const uint64_t sgroups = stiles / kScanGroup + 1;
+    PI_TRY(dalloc(&s.gsum, sgroups * 256)); PI_TRY(dalloc(&s.gctr, 8 * (sgroups + 1)));
     PI_TRY(dalloc(&s.ndig, stiles * kSortTile + 16));
     PI_TRY(dalloc(&s.fixmap, c / 32 + 1));
     PI_TRY(dalloc(&s.cstage.keys, cs)); PI_TRY(dalloc(&s.cstage.pos, cs)); PI_TRY(dalloc(&s.cstage.hl, cs));
@@ -276,7 +277,7 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     PI_TRY(dalloc(&s.lst_keys, s.lst_cap)); PI_TRY(dalloc(&s.lst_pos, s.lst_cap));
     PI_TRY(dalloc(&s.lst_pref, s.lst_cap)); PI_TRY(dalloc(&s.lst_ins, s.lst_cap));
     const uint64_t nsub = (q + kSubTile - 1) / kSubTile + 1;
-    PI_TRY(dalloc(&s.hq, nsub * kSubTile)); PI_TRY(dalloc(&s.sub_cnt, nsub)); PI_TRY(dalloc(&s.sub_pref, nsub));
+    PI_TRY(dalloc(&s.sub_pref, nsub));
     PI_TRY(dalloc(&s.dq, c)); PI_TRY(dalloc(&s.dlo, c));
 #undef PI_TRY
     s.cap = q;
@@ -366,9 +367,10 @@ SortBuffers sort_buffers(pi_index* x, const Scratch& s) {
     sb.in_k = s.in_k; sb.in_p = s.in_p; sb.a_k = s.a_k; sb.a_p = s.a_p; sb.b_k = s.b_k; sb.b_p = s.b_p;
     sb.dofs = x->d_dofs;
     sb.desc = x->desc;
-    sb.tile_max = s.tile_max;
     sb.tcnt = s.tcnt;
     sb.toff = s.toff;
+    sb.gsum = s.gsum;
+    sb.gctr = s.gctr;
     sb.ndig = s.ndig;
     sb.fixmap = s.fixmap;
     return sb;
@@ -548,14 +550,15 @@ constexpr uint64_t noalloc_bytes(uint64_t q) {
            + al256(c * 4) + al256(c) + al256(c * 8)               // loc, flags, val0
            + 2 * al256(c * 8) + al256(c * 4) + al256(c)           // new nodes
            + 2 * al256(cs * 8) + al256(cs * 4) + al256(cs)        // new-node staging
-           + 3 * al256(tiles * 4)                                 // tile max / prefix / new
+           + 2 * al256(tiles * 4)                                 // tile prefix / new
            + 2 * al256(stiles * 256 * 4) + al256(stiles * kSortTile + 16)  // tcnt, toff, ndig
+           + al256((stiles / kScanGroup + 1) * 256 * 4) + al256(8 * (stiles / kScanGroup + 2) * 4)  // gsum, gctr
            + al256((c / 32 + 1) * 4)                              // fixmap
            + al256(cs * 8) + al256(cs * 4) + al256(cs)            // level-change staging
            + al256(c * 8) + al256(c * 4) + al256(c)               // level changes
            + 2 * al256(tiles * 4)                                 // per-tile change counts
            + al256((2 * c + 64) * 8) + 2 * al256((2 * c + 64) * 4) + al256(2 * c + 64)  // lists
-           + al256(nsub * kSubTile * 8) + 2 * al256(nsub * 4)     // hq, sub_cnt, sub_pref
+           + al256(nsub * 4)                                      // sub_pref
            + al256(c * 8) + al256(c * 4);                         // dq, dlo
 }
 
@@ -580,8 +583,9 @@ uint64_t carve_scratch(uint8_t* base, uint64_t q, Scratch& s) {
     take(s.loc, c * 4); take(s.flags, c); take(s.val0, c * 8);
     take(s.nn.keys, c * 8); take(s.nn.vals, c * 8); take(s.nn.loc, c * 4); take(s.nn.height, c);
     take(s.stage.keys, cs * 8); take(s.stage.vals, cs * 8); take(s.stage.loc, cs * 4); take(s.stage.height, cs);
-    take(s.tile_max, tiles * 4); take(s.tile_pref, tiles * 4); take(s.tile_new, tiles * 4);
+    take(s.tile_pref, tiles * 4); take(s.tile_new, tiles * 4);
     take(s.tcnt, stiles * 256 * 4); take(s.toff, stiles * 256 * 4); take(s.ndig, stiles * kSortTile + 16);
+    take(s.gsum, (stiles / kScanGroup + 1) * 256 * 4); take(s.gctr, 8 * (stiles / kScanGroup + 2) * 4);
     take(s.fixmap, (c / 32 + 1) * 4);
     take(s.cstage.keys, cs * 8); take(s.cstage.pos, cs * 4); take(s.cstage.hl, cs);
     take(s.chg.keys, c * 8); take(s.chg.pos, c * 4); take(s.chg.hl, c);
@@ -589,7 +593,7 @@ uint64_t carve_scratch(uint8_t* base, uint64_t q, Scratch& s) {
     s.lst_cap = 2 * c + 64;
     take(s.lst_keys, s.lst_cap * 8); take(s.lst_pos, s.lst_cap * 4); take(s.lst_pref, s.lst_cap * 4);
     take(s.lst_ins, s.lst_cap);
-    take(s.hq, nsub * kSubTile * 8); take(s.sub_cnt, nsub * 4); take(s.sub_pref, nsub * 4);
+    take(s.sub_pref, nsub * 4);
     take(s.dq, c * 8); take(s.dlo, c * 4);
     s.cap = q;
     return off;
@@ -661,10 +665,8 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     DescendArgs da{};
     da.sk = sc.a_k;
     da.sp = sc.a_p;
-    da.tile_max = sc.tile_max;
     da.tile_pref = sc.tile_pref;
-    da.hq = sc.hq;
-    da.sub_cnt = sc.sub_cnt;
+    da.desc = x->desc;
     da.sub_pref = sc.sub_pref;
     da.dq = sc.dq;
     da.dlo = sc.dlo;
@@ -682,6 +684,7 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     da.val0 = sc.val0;
     da.n = (uint32_t)n;
     da.err = &x->d_meta->error;
+    da.epoch = ++ep;
     if ((e = launch_descend(da, s, x->num_sms, prof_event(x, 10))) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 3, s);
     ApplyArgs aa{};
@@ -697,7 +700,6 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     aa.m = x->d_meta;
     aa.bm = bm;
     aa.desc = x->desc;
-    aa.tile_max = sc.tile_max;
     aa.tile_pref = sc.tile_pref;
     aa.tile_new = sc.tile_new;
     aa.sub_pref = sc.sub_pref;
@@ -1027,10 +1029,8 @@ int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint6
     DescendArgs da{};
     da.sk = sc.a_k;
     da.sp = sc.a_p;
-    da.tile_max = sc.tile_max;
     da.tile_pref = sc.tile_pref;
-    da.hq = sc.hq;
-    da.sub_cnt = sc.sub_cnt;
+    da.desc = x->desc;
     da.sub_pref = sc.sub_pref;
     da.dq = sc.dq;
     da.dlo = sc.dlo;
@@ -1048,6 +1048,9 @@ int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint6
     da.val0 = sc.val0;
     da.n = (uint32_t)nb;
     da.err = &x->d_meta->error;
+    uint32_t ep = next_epochs(x, 4, s);
+    da.epoch = ++ep;
+    x->epoch = ep;
     if ((e = launch_descend(da, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
     RangeArgs ra{};
     ra.sk = sc.a_k;

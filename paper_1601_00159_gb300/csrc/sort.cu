@@ -104,13 +104,12 @@ __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ ops, c
 // max_passes of them (the prefix). The fix-up then orders each segment of equal prefix
 // bytes by the full key; its long-segment path sorts by every other byte that can
 // differ inside a segment (rdig).
-__global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, uint32_t* tile_max,
-                                                   uint32_t max_passes) {
+__global__ void __launch_bounds__(256) k_sort_plan(uint32_t n, BatchMeta* bm, uint32_t* gctr, uint32_t max_passes) {
     pdl_wait();
     pdl_trigger();
     const int b = threadIdx.x;
-    if (tile_max)
-        for (uint32_t t = b; t < (n + kApplyTile - 1) / kApplyTile; t += 256) tile_max[t] = 0;
+    const uint32_t ngroups = ((n + kTile - 1) / kTile + kScanGroup - 1) / kScanGroup;
+    for (uint32_t i = b; i < 8u * (ngroups + 1u); i += 256) gctr[i] = 0;  // the count kernels' arrivals
     if (b == 0) plan_digits(bm->bmax, bm->bnmin, bm->invalid, n, max_passes, bm->plan);
 }
 
@@ -118,12 +117,19 @@ __device__ __forceinline__ const uint64_t* pass_src_keys(const SortPlan& P, uint
     return P.src[j] == 0 ? sb.in_k : (P.src[j] == 1 ? sb.a_k : sb.b_k);
 }
 
-// Digit histogram of every tile for pass j. Pass 0 reads the packed keys; later
-// passes read the digit bytes the previous scatter wrote beside its output.
+// Digit histogram of every tile for pass j, then its scan, by the CTAs that finish
+// last (no CTA waits for another): the last CTA of each group of kScanGroup tiles turns
+// the group's counts into offsets within the group (toff) and the group's digit totals
+// (gsum); the last group to finish turns those totals into the groups' offsets, in
+// place, and the digit totals into digit bases (dofs). A tile's first output slot for
+// digit d is then dofs[d] + gsum[group][d] + toff[tile][d]. Pass 0 reads the packed
+// keys; later passes read the digit bytes the previous scatter wrote beside its output.
 __global__ void __launch_bounds__(kThreads) k_sort_count(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
     pdl_wait();
     pdl_trigger();
     __shared__ uint32_t h[256];
+    __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_last;
     const SortPlan& P = bm->plan;
     if (j >= P.npass) return;
     h[threadIdx.x] = 0;
@@ -151,51 +157,54 @@ __global__ void __launch_bounds__(kThreads) k_sort_count(uint32_t j, uint32_t n,
         }
     }
     __syncthreads();
-    sb.tcnt[(size_t)blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
-}
-
-// One CTA per digit: that digit's offset in every tile for pass j, relative to the
-// digit's first slot, and the digit's total (the scatter adds the digit bases).
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ uint32_t s_tmp[33];
-    const SortPlan& P = bm->plan;
-    if (j >= P.npass) return;
-    const uint32_t d = blockIdx.x;
-    const uint32_t ntiles = (n + kTile - 1) / kTile;
-    const uint32_t per = (ntiles + 1023u) / 1024u;
-    const uint32_t t0 = min(threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
-    uint32_t c[4];
-    uint32_t sum = 0;
-    if (per <= 4) {
+    const uint32_t d = threadIdx.x;
+    const uint32_t tile = blockIdx.x, ntiles = gridDim.x;
+    sb.tcnt[(size_t)tile * 256 + d] = h[d];
+    const uint32_t g = tile / kScanGroup, ngroups = (ntiles + kScanGroup - 1) / kScanGroup;
+    const uint32_t t0 = g * kScanGroup, t1 = min(t0 + kScanGroup, ntiles);
+    uint32_t* ctr = sb.gctr + (size_t)j * (ngroups + 1);
+    __threadfence();  // this CTA's counts, before its arrival is counted
+    __syncthreads();
+    if (d == 0) s_last = atomicAdd(&ctr[g], 1u) == t1 - t0 - 1u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();  // every CTA of the group has arrived: their counts are visible
+    uint32_t run = 0;
+    for (uint32_t t = t0; t < t1; t += 8) {
+        uint32_t c[8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            c[k] = (t0 + k < t1) ? sb.tcnt[(size_t)(t0 + k) * 256 + d] : 0u;
-            sum += c[k];
-        }
-    } else {
-        for (uint32_t t = t0; t < t1; ++t) sum += sb.tcnt[(size_t)t * 256 + d];
-    }
-    uint32_t total;
-    uint32_t run = block_excl_sum<1024>(sum, s_tmp, &total);
-    if (threadIdx.x == 0) sb.dofs[d] = total;  // digit total of this pass
-    if (per <= 4) {
+        for (int k = 0; k < 8; ++k) c[k] = (t + k < t1) ? __ldcg(&sb.tcnt[(size_t)(t + k) * 256 + d]) : 0u;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (t0 + k < t1) {
-                sb.toff[(size_t)(t0 + k) * 256 + d] = run;
+        for (int k = 0; k < 8; ++k) {
+            if (t + k < t1) {
+                sb.toff[(size_t)(t + k) * 256 + d] = run;
                 run += c[k];
             }
         }
-    } else {
-        for (uint32_t t = t0; t < t1; ++t) {
-            const uint32_t cc = sb.tcnt[(size_t)t * 256 + d];
-            sb.toff[(size_t)t * 256 + d] = run;
-            run += cc;
+    }
+    sb.gsum[(size_t)g * 256 + d] = run;
+    __threadfence();
+    __syncthreads();
+    if (d == 0) s_last = atomicAdd(&ctr[ngroups], 1u) == ngroups - 1u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    run = 0;
+    for (uint32_t q = 0; q < ngroups; q += 8) {
+        uint32_t c[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[k] = (q + k < ngroups) ? __ldcg(&sb.gsum[(size_t)(q + k) * 256 + d]) : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (q + k < ngroups) {
+                sb.gsum[(size_t)(q + k) * 256 + d] = run;
+                run += c[k];
+            }
         }
     }
+    sb.dofs[d] = block_excl_sum<kThreads>(run, s_tmp, nullptr);  // digit bases of this pass
 }
+
 
 __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t n, SortBuffers sb,
                                                            BatchMeta* bm, uint32_t* err) {
@@ -245,8 +254,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(uint32_t j, uint32_t 
         s_whist[w][tid] = total;
         total += c;
     }
-    const uint32_t dbase = block_excl_sum<kThreads>(sb.dofs[tid], s_tmp, nullptr);  // digit bases
-    s_gbase[tid] = dbase + sb.toff[(size_t)tile * 256 + tid];
+    s_gbase[tid] = sb.dofs[tid] + sb.gsum[(size_t)(tile / kScanGroup) * 256 + tid] +
+                   sb.toff[(size_t)tile * 256 + tid];
     s_tstart[tid] = block_excl_sum<kThreads>(total, s_tmp, nullptr);
     __syncthreads();
 #pragma unroll
@@ -485,7 +494,7 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
     int grid = min((int)((n + 255) / 256), num_sms * 8);
     launch_dep(k_pack, grid, 256, 0, s, ops, keys, n, sb.in_k, sb.in_p, sb.fixmap, bm);
     ++g_launches;
-    launch_dep(k_sort_plan, 1, 256, 0, s, n, bm, sb.tile_max, (uint32_t)max_passes);
+    launch_dep(k_sort_plan, 1, 256, 0, s, n, bm, sb.gctr, (uint32_t)max_passes);
     ++g_launches;
     static bool attr_set = false;
     const int dyn = kTile * (int)(sizeof(uint64_t) + sizeof(uint32_t));
@@ -498,8 +507,6 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
     launch_dep(k_sort_count, tiles, kThreads, 0, s, 0, n, sb, bm);
     ++g_launches;
     for (uint32_t j = 0; j < (uint32_t)max_passes; ++j) {
-        launch_dep(k_sort_scan, 256, 1024, 0, s, j, n, sb, bm);
-        ++g_launches;
         launch_dep(k_sort_pass, tiles, kThreads, dyn, s, j, n, sb, bm, err);
         ++g_launches;
         if (j + 1 < (uint32_t)max_passes) {
