@@ -16,7 +16,7 @@ constexpr uint32_t kSmemTopMax = 2048;  // index entries staged in shared memory
 constexpr uint32_t kPad = 64;           // readable entries past every array's end
 constexpr uint32_t kSortTile = 2048;    // elements per radix-sort tile
 constexpr uint32_t kScanGroup = 64;     // radix-sort tiles per group of the count kernel's scan
-constexpr uint32_t kCtrDistinct = 14;   // BatchMeta::tile_ctr slot of the distinct-key kernel
+constexpr uint32_t kCtrDistinct = 14;   // BatchMeta::tile_ctr slot: the distinct-key kernel's arrivals
 constexpr uint32_t kApplyTile = 2048;   // sorted queries per apply tile
 constexpr uint32_t kSubTile = 256;      // sorted queries per descent warp step (one apply warp)
 
@@ -555,8 +555,10 @@ struct DescendArgs {
     const uint32_t* sp;  // sorted payload (op << 30 | arrival index)
     uint32_t* tile_pref; // per-apply-tile exclusive max prefix of the run markers e_i
     uint32_t* sub_pref;  // dense index of each sub-tile's first distinct key
-    uint64_t* desc;      // look-back descriptors: [0, tiles) head counts, [tiles, 2 tiles) maxima
-    uint32_t epoch;      // tags this batch's descriptors
+    uint32_t* sub_cnt;   // distinct keys per sub-tile
+    uint32_t* tile_heads;  // distinct keys per apply tile
+    uint32_t* tile_emax;   // largest ownership marker per apply tile
+    uint32_t* tile_base;   // dense index of each apply tile's first distinct key
     uint64_t* dq;        // dense distinct keys
     uint32_t* dlo;       // their current start position on the level being searched
     int top_launched;    // highest index level given its own launch (see launch_descend)

@@ -11,10 +11,10 @@
 //
 // The descent is level-synchronous over the whole batch -- the paper's group query
 // processing (Section 4.4.3) with the group being every distinct key of the batch:
-//  k_distinct   per 256-query sub-tile, one warp finds the distinct keys (run heads,
-//               plus the sub-tile's first query); a look-back over the apply tiles
-//               gives their dense index, so they are written densely at once, and the
-//               apply tiles' exclusive max prefixes of the ownership markers;
+//  k_distinct   per 256-query sub-tile, one warp counts the distinct keys (run heads,
+//               plus the sub-tile's first query); the last CTA to finish scans the
+//               apply tiles' counts (dense index) and ownership-marker maxima;
+//  k_dpack      each warp writes its sub-tile's distinct keys densely;
 //  k_top        the levels pinned in shared memory (copied once per CTA by TMA bulk
 //               copies) are resolved by one binary search of the lowest pinned level,
 //               which holds every key of the levels above it; writes the dense key and
@@ -216,58 +216,88 @@ __device__ __forceinline__ uint32_t subtile_heads(const DescendArgs& a, uint32_t
     return nq;
 }
 
-// The distinct keys of the sorted batch, densely (one CTA per 2048-query apply tile,
-// one warp per 256-query sub-tile, tiles taken in CTA start order): each warp counts
-// its sub-tile's local run heads; two warps then look back over the earlier tiles, one
-// for the sum of the counts (the tile's first dense index) and one for the maximum
-// ownership marker (the apply tile's exclusive prefix, so k_apply never waits); each
-// warp then writes its heads' keys to dq and its sub-tile's first dense index to
-// sub_pref. The last tile records the number of distinct keys.
+// The distinct keys of the sorted batch, in two launches with no CTA waiting for
+// another. k_distinct: one CTA per 2048-query apply tile, one warp per 256-query
+// sub-tile, counts the local run heads and the largest ownership marker e_i; the last
+// CTA to finish scans the tiles' totals into each tile's first dense index (sum) and
+// its exclusive prefix of markers (max), so k_apply never waits. k_dpack: each warp
+// writes its sub-tile's heads densely from the tile's index on.
 __global__ void __launch_bounds__(kThreads) k_distinct(DescendArgs a) {
     pdl_wait();
     pdl_trigger();
-    __shared__ uint32_t s_tile, s_base, s_mpref;
+    constexpr uint32_t kPer = 8;  // tiles per thread in the final scan
     __shared__ uint32_t s_cnt[kThreads / 32], s_max[kThreads / 32];
-    __shared__ bool s_ok;
+    __shared__ uint32_t s_tmp[33], s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (block_sees_error(&a.m->error)) return;
-    if (tid == 0) {
-        s_tile = atomicAdd(&a.bm->tile_ctr[kCtrDistinct], 1u);
-        s_ok = true;
-    }
-    __syncthreads();
-    const uint32_t tile = s_tile;
+    const uint32_t tile = blockIdx.x, ntiles = gridDim.x;
     const uint32_t n = a.n, qv = n - a.bm->invalid;
-    const uint32_t nsub = (n + kSubTile - 1) / kSubTile, ntiles = (n + kApplyTile - 1) / kApplyTile;
-    if (tile >= ntiles) return;
+    const uint32_t nsub = (n + kSubTile - 1) / kSubTile;
     const uint32_t sub = tile * (kApplyTile / kSubTile) + (uint32_t)warp;
     uint32_t emax = 0, nq = 0;
     if (sub < nsub) nq = subtile_heads(a, sub, qv, false, 0u, &emax);
     if (lane == 0) {
         s_cnt[warp] = nq;
         s_max[warp] = emax;
+        if (sub < nsub) a.sub_cnt[sub] = nq;
     }
     __syncthreads();
-    if (warp < 2) {
-        uint32_t tot = 0;
+    if (tid == 0) {
+        uint32_t c = 0, mx = 0;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) tot = warp == 0 ? tot + s_cnt[w] : max(tot, s_max[w]);
-        bool ok = true;
-        const uint32_t ex = warp == 0 ? lookback_warp<false>(a.desc, tile, a.epoch, tot, a.err, &ok)
-                                      : lookback_warp<true>(a.desc + ntiles, tile, a.epoch, tot, a.err, &ok);
-        if (lane == 0) {
-            if (warp == 0) s_base = ex;
-            else s_mpref = ex;
-            if (!ok) s_ok = false;
-            if (warp == 0 && tile == ntiles - 1) a.bm->distinct = ex + tot;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            c += s_cnt[w];
+            mx = max(mx, s_max[w]);
         }
+        a.tile_heads[tile] = c;
+        a.tile_emax[tile] = mx;
+        __threadfence();  // the totals, before this CTA's arrival is counted
+        s_last = atomicAdd(&a.bm->tile_ctr[kCtrDistinct], 1u) == ntiles - 1u;
     }
     __syncthreads();
-    if (!s_ok) return;  // a look-back gave up (kErrTimeout is recorded); the batch stops
-    if (tid == 0) a.tile_pref[tile] = s_mpref;
+    if (!s_last) return;
+    __threadfence();  // every tile has arrived: their totals are visible
+    uint32_t csum = 0, cmax = 0;
+    for (uint32_t g0 = 0; g0 < ntiles; g0 += kThreads * kPer) {
+        const uint32_t t0 = g0 + (uint32_t)tid * kPer;
+        uint32_t c[kPer], m[kPer], sum = 0, mx = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k) {
+            c[k] = t0 + k < ntiles ? __ldcg(&a.tile_heads[t0 + k]) : 0u;
+            m[k] = t0 + k < ntiles ? __ldcg(&a.tile_emax[t0 + k]) : 0u;
+            sum += c[k];
+            mx = max(mx, m[k]);
+        }
+        uint32_t tsum, tmax;
+        uint32_t rs = csum + block_excl_sum<kThreads>(sum, s_tmp, &tsum);
+        uint32_t rm = max(cmax, block_excl_max<kThreads>(mx, s_tmp, &tmax));
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k) {
+            if (t0 + k < ntiles) {
+                a.tile_base[t0 + k] = rs;
+                a.tile_pref[t0 + k] = rm;
+            }
+            rs += c[k];
+            rm = max(rm, m[k]);
+        }
+        csum += tsum;
+        cmax = max(cmax, tmax);
+    }
+    if (tid == 0) a.bm->distinct = csum;
+}
+
+__global__ void __launch_bounds__(kThreads) k_dpack(DescendArgs a) {
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
+    const uint32_t n = a.n, qv = n - a.bm->invalid;
+    const uint32_t nsub = (n + kSubTile - 1) / kSubTile;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t s0 = tile * (kApplyTile / kSubTile), sub = s0 + (uint32_t)warp;
     if (sub >= nsub) return;
-    uint32_t d0 = s_base;
-    for (int w = 0; w < warp; ++w) d0 += s_cnt[w];
+    uint32_t d0 = a.tile_base[tile];
+    for (uint32_t t = s0; t < sub; ++t) d0 += a.sub_cnt[t];
     if (lane == 0) a.sub_pref[sub] = d0;
     subtile_heads(a, sub, qv, true, d0, nullptr);
 }
@@ -398,6 +428,8 @@ cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms, cu
     if (a.n == 0) return cudaSuccess;
     const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
     launch_dep(k_distinct, ntiles, kThreads, 0, s, a);
+    ++g_launches;
+    launch_dep(k_dpack, ntiles, kThreads, 0, s, a);
     ++g_launches;
     const uint32_t need = (a.n + kThreads - 1) / kThreads;
     launch_dep(k_top, need, kThreads, dyn, s, a);  // CTAs past the distinct keys exit at once

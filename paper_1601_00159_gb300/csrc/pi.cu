@@ -41,6 +41,10 @@ struct Scratch {
     NewNodes nn{};
     NewNodes stage{};
     uint32_t* tile_pref = nullptr;
+    uint32_t* tile_heads = nullptr;  // descent: distinct keys per apply tile
+    uint32_t* tile_emax = nullptr;   // descent: largest ownership marker per apply tile
+    uint32_t* tile_base = nullptr;   // descent: dense index of each apply tile's first key
+    uint32_t* sub_cnt = nullptr;     // descent: distinct keys per sub-tile
     uint32_t* tile_new = nullptr;
     uint32_t* tcnt = nullptr;  // radix sort: per-tile digit counts
     uint32_t* toff = nullptr;  // radix sort: per-tile digit offsets
@@ -240,12 +244,12 @@ void free_scratch(Scratch& s) {
     dfree(s.loc); dfree(s.flags); dfree(s.val0);
     dfree(s.nn.keys); dfree(s.nn.vals); dfree(s.nn.loc); dfree(s.nn.height);
     dfree(s.stage.keys); dfree(s.stage.vals); dfree(s.stage.loc); dfree(s.stage.height);
-    dfree(s.tile_pref); dfree(s.tile_new);
+    dfree(s.tile_pref); dfree(s.tile_new); dfree(s.tile_heads); dfree(s.tile_emax); dfree(s.tile_base);
     dfree(s.tcnt); dfree(s.toff); dfree(s.ndig); dfree(s.fixmap); dfree(s.gsum); dfree(s.gctr);
     dfree(s.cstage.keys); dfree(s.cstage.pos); dfree(s.cstage.hl); dfree(s.chg.keys); dfree(s.chg.pos); dfree(s.chg.hl);
     dfree(s.tile_chg); dfree(s.tile_chg_pref);
     dfree(s.lst_keys); dfree(s.lst_pos); dfree(s.lst_pref); dfree(s.lst_ins);
-    dfree(s.sub_pref); dfree(s.dq); dfree(s.dlo);
+    dfree(s.sub_pref); dfree(s.sub_cnt); dfree(s.dq); dfree(s.dlo);
     s.cap = 0;
 }
 
@@ -264,6 +268,7 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     PI_TRY(dalloc(&s.stage.keys, cs)); PI_TRY(dalloc(&s.stage.vals, cs));
     PI_TRY(dalloc(&s.stage.loc, cs)); PI_TRY(dalloc(&s.stage.height, cs));
     PI_TRY(dalloc(&s.tile_pref, tiles)); PI_TRY(dalloc(&s.tile_new, tiles));
+    PI_TRY(dalloc(&s.tile_heads, tiles)); PI_TRY(dalloc(&s.tile_emax, tiles)); PI_TRY(dalloc(&s.tile_base, tiles));
     const uint64_t stiles = (q + kSortTile - 1) / kSortTile + 1;
     PI_TRY(dalloc(&s.tcnt, stiles * 256)); PI_TRY(dalloc(&s.toff, stiles * 256));
     const uint64_t sgroups = stiles / kScanGroup + 1;
@@ -277,7 +282,7 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     PI_TRY(dalloc(&s.lst_keys, s.lst_cap)); PI_TRY(dalloc(&s.lst_pos, s.lst_cap));
     PI_TRY(dalloc(&s.lst_pref, s.lst_cap)); PI_TRY(dalloc(&s.lst_ins, s.lst_cap));
     const uint64_t nsub = (q + kSubTile - 1) / kSubTile + 1;
-    PI_TRY(dalloc(&s.sub_pref, nsub));
+    PI_TRY(dalloc(&s.sub_pref, nsub)); PI_TRY(dalloc(&s.sub_cnt, nsub));
     PI_TRY(dalloc(&s.dq, c)); PI_TRY(dalloc(&s.dlo, c));
 #undef PI_TRY
     s.cap = q;
@@ -550,7 +555,7 @@ constexpr uint64_t noalloc_bytes(uint64_t q) {
            + al256(c * 4) + al256(c) + al256(c * 8)               // loc, flags, val0
            + 2 * al256(c * 8) + al256(c * 4) + al256(c)           // new nodes
            + 2 * al256(cs * 8) + al256(cs * 4) + al256(cs)        // new-node staging
-           + 2 * al256(tiles * 4)                                 // tile prefix / new
+           + 5 * al256(tiles * 4)                                 // tile prefix / new / heads / emax / base
            + 2 * al256(stiles * 256 * 4) + al256(stiles * kSortTile + 16)  // tcnt, toff, ndig
            + al256((stiles / kScanGroup + 1) * 256 * 4) + al256(8 * (stiles / kScanGroup + 2) * 4)  // gsum, gctr
            + al256((c / 32 + 1) * 4)                              // fixmap
@@ -558,7 +563,7 @@ constexpr uint64_t noalloc_bytes(uint64_t q) {
            + al256(c * 8) + al256(c * 4) + al256(c)               // level changes
            + 2 * al256(tiles * 4)                                 // per-tile change counts
            + al256((2 * c + 64) * 8) + 2 * al256((2 * c + 64) * 4) + al256(2 * c + 64)  // lists
-           + al256(nsub * 4)                                      // sub_pref
+           + 2 * al256(nsub * 4)                                  // sub_pref, sub_cnt
            + al256(c * 8) + al256(c * 4);                         // dq, dlo
 }
 
@@ -584,6 +589,7 @@ uint64_t carve_scratch(uint8_t* base, uint64_t q, Scratch& s) {
     take(s.nn.keys, c * 8); take(s.nn.vals, c * 8); take(s.nn.loc, c * 4); take(s.nn.height, c);
     take(s.stage.keys, cs * 8); take(s.stage.vals, cs * 8); take(s.stage.loc, cs * 4); take(s.stage.height, cs);
     take(s.tile_pref, tiles * 4); take(s.tile_new, tiles * 4);
+    take(s.tile_heads, tiles * 4); take(s.tile_emax, tiles * 4); take(s.tile_base, tiles * 4);
     take(s.tcnt, stiles * 256 * 4); take(s.toff, stiles * 256 * 4); take(s.ndig, stiles * kSortTile + 16);
     take(s.gsum, (stiles / kScanGroup + 1) * 256 * 4); take(s.gctr, 8 * (stiles / kScanGroup + 2) * 4);
     take(s.fixmap, (c / 32 + 1) * 4);
@@ -593,7 +599,7 @@ uint64_t carve_scratch(uint8_t* base, uint64_t q, Scratch& s) {
     s.lst_cap = 2 * c + 64;
     take(s.lst_keys, s.lst_cap * 8); take(s.lst_pos, s.lst_cap * 4); take(s.lst_pref, s.lst_cap * 4);
     take(s.lst_ins, s.lst_cap);
-    take(s.sub_pref, nsub * 4);
+    take(s.sub_pref, nsub * 4); take(s.sub_cnt, nsub * 4);
     take(s.dq, c * 8); take(s.dlo, c * 4);
     s.cap = q;
     return off;
@@ -666,7 +672,10 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     da.sk = sc.a_k;
     da.sp = sc.a_p;
     da.tile_pref = sc.tile_pref;
-    da.desc = x->desc;
+    da.sub_cnt = sc.sub_cnt;
+    da.tile_heads = sc.tile_heads;
+    da.tile_emax = sc.tile_emax;
+    da.tile_base = sc.tile_base;
     da.sub_pref = sc.sub_pref;
     da.dq = sc.dq;
     da.dlo = sc.dlo;
@@ -684,7 +693,6 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     da.val0 = sc.val0;
     da.n = (uint32_t)n;
     da.err = &x->d_meta->error;
-    da.epoch = ++ep;
     if ((e = launch_descend(da, s, x->num_sms, prof_event(x, 10))) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 3, s);
     ApplyArgs aa{};
@@ -1030,7 +1038,10 @@ int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint6
     da.sk = sc.a_k;
     da.sp = sc.a_p;
     da.tile_pref = sc.tile_pref;
-    da.desc = x->desc;
+    da.sub_cnt = sc.sub_cnt;
+    da.tile_heads = sc.tile_heads;
+    da.tile_emax = sc.tile_emax;
+    da.tile_base = sc.tile_base;
     da.sub_pref = sc.sub_pref;
     da.dq = sc.dq;
     da.dlo = sc.dlo;
@@ -1048,9 +1059,6 @@ int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint6
     da.val0 = sc.val0;
     da.n = (uint32_t)nb;
     da.err = &x->d_meta->error;
-    uint32_t ep = next_epochs(x, 4, s);
-    da.epoch = ++ep;
-    x->epoch = ep;
     if ((e = launch_descend(da, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
     RangeArgs ra{};
     ra.sk = sc.a_k;
