@@ -56,7 +56,7 @@ WORKLOADS = {
     "serving": dict(fn=wl.serving, n=1 << 26, q=None,
                     desc="serving: resident 2^26-key uint64 index (p=1/4); Poisson-arrival requests of 1..4096 "
                          "queries (log-uniform), 95% search / 5% insert, Zipf 0.9 keys; coalesced batches of at "
-                         "most 2^20 queries, 3 in flight; p50/p99 request latency at 70% of the measured capacity"),
+                         "most 2^20 queries, 3 in flight; p50/p99 request latency at 50% and 90% of the measured capacity"),
     "range": dict(fn=None, n=1 << 24, q=None,
                   desc="range search: 2^24 distinct uniform uint64 keys (p=1/4); batches of 2^16 range queries "
                        "whose spans hold on average g = 1, 10, 100, 1000 keys (the paper's granularity); "
@@ -74,16 +74,20 @@ def tuned_classes():
         return None
 
 
+# The sources of the single-index batch path (the kernels a capture of the skewed
+# workload measures, and the host code that launches them).
+BATCH_PATH_SOURCES = ("common.cuh", "sort.cu", "descend.cu", "apply.cu", "rebuild.cu", "relevel.cu", "pi.cu")
+
+
 def source_digest():
-    """sha256 prefix of the CUDA sources and the C header: a DRAM capture counts only for
-    the kernels it measured."""
+    """sha256 prefix of the batch path's CUDA sources and the C header: a DRAM capture
+    counts only for the kernels it measured."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_00159_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            h.update(name.encode())
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in BATCH_PATH_SOURCES:
+        h.update(name.encode())
+        h.update(open(os.path.join(csrc, name), "rb").read())
     h.update(open(os.path.join(ROOT, "include", "pi.h"), "rb").read())
     return h.hexdigest()[:16]
 
@@ -517,7 +521,8 @@ def run_batching(args, ws, rank, local):
 
 def run_serving(args, ws, rank, local):
     """Config 5: the server under a saturating burst (capacity), then under Poisson
-    arrivals at 70% of that capacity (latency), beside one request per pi_execute_batch."""
+    arrivals at 50% and 90% of that capacity (latency), beside one request per
+    pi_execute_batch."""
     import torch
     from paper_1601_00159_gb300 import Index, Server, build, load_library
     build.build()
@@ -547,22 +552,30 @@ def run_serving(args, ws, rank, local):
     sat_s = time.perf_counter() - t
     sat = srv.stats(reset=True)
     capacity = (b - a) / sat_s / 1e6
-    # latency: Poisson arrivals at 70% of capacity
+    # latency: Poisson arrivals at 50% and then 90% of capacity, each on half the rest
     rest = nreq - warm - half
-    a2, b2 = offs[warm + half], offs[nreq]
-    rate = 0.7 * capacity * 1e6 / float(w.sizes[warm + half:].mean())  # requests per second
-    gaps = -np.log(np.maximum(wl.uniform01(wl.stream_seed(5, 77), 0, rest), 1e-12)) / rate
-    arrivals = np.cumsum(gaps)
     l0 = idx.info()["kernel_launches"]
+    runs = {}
+    r0 = warm + half
     with ClockSampler(local) as clk:
-        t = time.perf_counter()
-        _, lat = srv.replay(w.ops[a2:b2], w.qkeys[a2:b2], w.qvals[a2:b2], w.sizes[warm + half:], arrivals,
-                            want_results=False)
-        run_s = time.perf_counter() - t
-    st = srv.stats(reset=True)
+        for frac, r1 in ((0.5, warm + half + rest // 2), (0.9, nreq)):
+            a2, b2 = offs[r0], offs[r1]
+            rate = frac * capacity * 1e6 / float(w.sizes[r0:r1].mean())  # requests per second
+            gaps = -np.log(np.maximum(wl.uniform01(wl.stream_seed(5, 77 + int(frac * 10)), 0, r1 - r0), 1e-12)) / rate
+            t = time.perf_counter()
+            _, lat = srv.replay(w.ops[a2:b2], w.qkeys[a2:b2], w.qvals[a2:b2], w.sizes[r0:r1], np.cumsum(gaps),
+                                want_results=False)
+            run_s = time.perf_counter() - t
+            st = srv.stats(reset=True)
+            runs[frac] = dict(value=(b2 - a2) / run_s / 1e6, requests=r1 - r0, queries=int(b2 - a2), rate=rate,
+                              run_s=run_s, p50_ms=float(np.percentile(lat, 50)) * 1e3,
+                              p99_ms=float(np.percentile(lat, 99)) * 1e3, max_ms=float(lat.max()) * 1e3,
+                              batches=st["batches"], mean_batch=st["mean_batch"], max_in_flight=st["max_in_flight"])
+            r0 = r1
     srv.close()
     launches = idx.info()["kernel_launches"] - l0
-    value = (b2 - a2) / run_s / 1e6
+    hi = runs[0.9]
+    value = hi["value"]
     # the plain path without coalescing: one request per batch, host buffers, synchronous
     sample = 300
     hres = torch.empty((4096, 2), dtype=torch.int64).pin_memory()
@@ -584,16 +597,18 @@ def run_serving(args, ws, rank, local):
     assert idx.status() == 0
     idx.close()
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": int(rest),
-        "warmup": warm, "ms_per_step": run_s / rest * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "serving", "desc": spec["desc"], "keys": len(w.keys), "requests": int(rest),
-                   "queries": int(b2 - a2), "mean_request": float(w.sizes.mean()), "arrival_rate_per_s": rate,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": int(hi["requests"]),
+        "warmup": warm, "ms_per_step": hi["run_s"] / hi["requests"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serving", "desc": spec["desc"], "keys": len(w.keys), "requests": int(hi["requests"]),
+                   "queries": hi["queries"], "mean_request": float(w.sizes.mean()), "arrival_rate_per_s": hi["rate"],
+                   "load": "90% of the capacity measured under a burst (value); 50% in latency_50",
                    "step": "one request", "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2_flush": "none: the 2^26-key index (1.1 GB storage) exceeds L2"},
-        "latency": {"p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
-                    "max_ms": float(lat.max()) * 1e3, "batches": st["batches"], "mean_batch": st["mean_batch"],
-                    "max_in_flight": st["max_in_flight"], "measured_from": "scheduled arrival to results in host memory"},
+        "latency": {"p50_ms": hi["p50_ms"], "p99_ms": hi["p99_ms"], "max_ms": hi["max_ms"], "batches": hi["batches"],
+                    "mean_batch": hi["mean_batch"], "max_in_flight": hi["max_in_flight"], "load": 0.9,
+                    "measured_from": "scheduled arrival to results in host memory"},
+        "latency_50": dict(runs[0.5], load=0.5),
         "capacity": {"value": capacity, "unit": UNIT, "batches": sat["batches"], "mean_batch": sat["mean_batch"],
                      "p99_ms": sat["p99_s"] * 1e3, "note": "every request arriving at once"},
         "plain_per_request": {"value": per_req_value, "unit": UNIT, "requests": sample,
