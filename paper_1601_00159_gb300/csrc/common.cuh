@@ -628,6 +628,7 @@ struct RebuildArgs {
     uint64_t* desc;       // look-back descriptors: max(tiles_merge, tiles_rebuild * 32)
     uint32_t* lcnt;       // per-level per-tile live counts, level-major, row stride lstride
     uint32_t* loff;       // rebuild: per-level per-tile offsets (scan output)
+    uint32_t* mcnt;       // merge: live old nodes per tile [0, lstride), their prefix [lstride, 2 lstride)
     uint32_t lstride;     // tiles per row of lcnt (storage capacity / 4096 + 2)
     uint32_t index_cap;   // entries (without padding)
     uint32_t size_ub;     // upper bound of the storage size after the batch

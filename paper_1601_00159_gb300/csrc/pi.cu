@@ -109,6 +109,7 @@ struct pi_index {
     uint64_t* desc = nullptr;
     uint64_t desc_words = 0;
     uint32_t* lcnt = nullptr;  // per-level per-tile live counts: 32 rows x lstride
+    uint32_t* mcnt = nullptr;  // merge: per-tile live counts and their prefix, 2 x lstride
     uint32_t* wcount = nullptr;  // PI_TEST_OWNER_CHECK: writes per storage node in a batch
     uint64_t wcap = 0;
     uint32_t* loff = nullptr;  // rebuild offsets, same shape
@@ -210,8 +211,10 @@ cudaError_t ensure_tile_cnt(pi_index* x, uint64_t st_cap) {
     if (stride <= x->lstride) return cudaSuccess;
     dfree(x->lcnt);
     dfree(x->loff);
+    dfree(x->mcnt);
     cudaError_t e = dalloc(&x->lcnt, 32 * stride);
     if (e == cudaSuccess) e = dalloc(&x->loff, 32 * stride);
+    if (e == cudaSuccess) e = dalloc(&x->mcnt, 2 * stride);
     if (e == cudaSuccess) e = cudaMemset(x->lcnt, 0, 32 * stride * sizeof(uint32_t));
     x->lstride = (e == cudaSuccess) ? (uint32_t)stride : 0u;
     x->force_rebuild = true;
@@ -357,7 +360,7 @@ void destroy(pi_index* x) {
     dfree(x->stg.ops); dfree(x->stg.keys); dfree(x->stg.vals); dfree(x->stg.res);
     free_storage(x->st);
     dfree(x->lkeys); dfree(x->ldown); dfree(x->lkeys1); dfree(x->ldown1);
-    dfree(x->desc); dfree(x->lcnt); dfree(x->loff); dfree(x->wcount); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
+    dfree(x->desc); dfree(x->lcnt); dfree(x->loff); dfree(x->mcnt); dfree(x->wcount); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
     if (x->h_mbox) cudaFreeHost(x->h_mbox);
     if (x->ev_applied) cudaEventDestroy(x->ev_applied);
     if (x->ev_rebuilt) cudaEventDestroy(x->ev_rebuilt);
@@ -527,6 +530,7 @@ RebuildArgs rebuild_args(pi_index* x, BatchMeta* bm, uint32_t size_ub, uint32_t 
     r.desc = x->desc;
     r.lcnt = x->lcnt;
     r.loff = x->loff;
+    r.mcnt = x->mcnt;
     r.lstride = x->lstride;
     r.index_cap = (uint32_t)(x->idx_cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : x->idx_cap);
     r.size_ub = size_ub;

@@ -47,17 +47,140 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t 
     return lo;
 }
 
+// The same count by a whole warp (every lane calls it and gets the result): each round
+// probes 32 evenly spaced entries of the remaining interval at once, so a search of n
+// entries takes about log32(n) rounds of one load per lane instead of log2(n) dependent
+// loads.
+__device__ __forceinline__ uint32_t warp_lower_bound_u32(const uint32_t* a, uint32_t n, uint32_t x) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t lo = 0, hi = n;  // the count lies in [lo, hi]
+    while (hi - lo > 32u) {
+        const uint32_t step = (hi - lo + 31u) / 32u;
+        const uint32_t p = lo + lane * step;
+        const bool lt = p < hi && a[p] < x;
+        const uint32_t c = (uint32_t)__popc(__ballot_sync(0xffffffffu, lt));  // probes below x
+        if (c == 0) return lo;
+        const uint32_t nlo = lo + (c - 1u) * step + 1u;
+        const uint32_t pc = lo + c * step;
+        hi = (c < 32u && pc < hi) ? pc : hi;
+        lo = nlo;
+    }
+    const uint32_t p = lo + lane;
+    return lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, p < hi && a[p] < x));
+}
+
 // ---------------------------------------------------------------------------------
 // Merge: old live nodes + new nodes -> the other storage buffer, in key order.
 // A new node with loc = x goes right before old node x (after old node x - 1) and is
 // handled by the tile that holds position x; the tiles cover positions [0, size].
-__global__ void __launch_bounds__(kThreads) k_merge(RebuildArgs a, uint32_t epoch) {
+// Block-wide exclusive sum of 64-bit values (kThreads threads); total in *total.
+__device__ __forceinline__ uint64_t block_excl_sum64(uint64_t v, uint64_t* tmp, uint64_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t w = lane < kThreads / 32 ? tmp[lane] : 0ull;
+        uint64_t t = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kThreads / 32) tmp[lane] = t - w;
+        if (lane == kThreads / 32 - 1) tmp[32] = t;
+    }
+    __syncthreads();
+    const uint64_t r = tmp[warp] + x - v;
+    if (total) *total = tmp[32];
+    __syncthreads();
+    return r;
+}
+
+// Live old nodes of every 4096-node tile (the meta bytes, 16 per thread in one 16-byte
+// load; the storage arrays are padded by a whole tile), then, by the last CTA to finish,
+// the tiles' exclusive prefix. No CTA waits for another.
+__global__ void __launch_bounds__(kThreads) k_merge_count(RebuildArgs a) {
     pdl_wait();
     pdl_trigger();
-    __shared__ uint16_t s_lp[kNodes + 1];  // live old nodes in [ts, ts + k)
-    __shared__ uint32_t s_tmp[33];
-    __shared__ uint32_t s_tile, s_prefix, s_jb, s_je;
-    __shared__ int s_ok;
+    constexpr uint32_t kScan = 8;  // tiles per thread in the final scan
+    __shared__ uint32_t s_tmp[33], s_warp[kThreads / 32], s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const DevMeta* m = a.m;
+    if (block_sees_error(&m->error)) return;
+    if (!merge_needed(m, a.bm)) return;
+    const uint32_t size = m->size, ntiles = size / kNodes + 1;
+    const uint8_t* M0 = a.st.meta[m->cur];
+    uint32_t* live = a.mcnt;
+    uint32_t* pref = a.mcnt + a.lstride;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t ts = tile * kNodes;
+        const uint32_t cnt = (size > ts) ? min((uint32_t)kNodes, size - ts) : 0u;
+        const uint32_t b0 = (uint32_t)tid * kPer;
+        const uint4 mw = *reinterpret_cast<const uint4*>(M0 + ts + b0);
+        const uint32_t words[4] = {mw.x, mw.y, mw.z, mw.w};
+        uint32_t lc = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const uint32_t mt = (words[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+            lc += (b0 + k < cnt && !(mt & kTomb)) ? 1u : 0u;
+        }
+        lc = __reduce_add_sync(0xffffffffu, lc);
+        if (lane == 0) s_warp[warp] = lc;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t t = 0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) t += s_warp[w];
+            live[tile] = t;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        __threadfence();  // this CTA's counts, before its arrival is counted
+        s_last = atomicAdd(&a.bm->tile_ctr[kCtrMerge], 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();  // every CTA has arrived: all counts are visible
+    uint32_t carry = 0;
+    for (uint32_t g0 = 0; g0 < ntiles; g0 += kThreads * kScan) {
+        const uint32_t t0 = g0 + (uint32_t)tid * kScan;
+        uint32_t c[kScan], sum = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < kScan; ++k) {
+            c[k] = t0 + k < ntiles ? __ldcg(&live[t0 + k]) : 0u;
+            sum += c[k];
+        }
+        uint32_t tot;
+        uint32_t r = carry + block_excl_sum<kThreads>(sum, s_tmp, &tot);
+#pragma unroll
+        for (uint32_t k = 0; k < kScan; ++k) {
+            if (t0 + k < ntiles) pref[t0 + k] = r;
+            r += c[k];
+        }
+        carry += tot;
+    }
+}
+
+// One 4096-node tile per step: a blocked pass (16 consecutive positions per thread)
+// counts the live old nodes and the new nodes inserted at each position, and one block
+// scan of both counts gives every position its output offset within the tile (the
+// tile's own offset is the count kernel's prefix plus the new nodes of earlier tiles);
+// a striped pass then copies the old live nodes with coalesced loads and stores, and
+// the new nodes go to their slots.
+__global__ void __launch_bounds__(kThreads) k_merge(RebuildArgs a) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ uint16_t s_lp[kNodes + 1];  // live old nodes before each position of the tile
+    __shared__ uint32_t s_nl[kNodes];      // new nodes at or before each position
+    __shared__ uint64_t s_tmp[33];
+    __shared__ uint32_t s_jb, s_je;
     const int tid = threadIdx.x;
     const DevMeta* m = a.m;
     if (block_sees_error(&m->error)) return;
@@ -71,76 +194,91 @@ __global__ void __launch_bounds__(kThreads) k_merge(RebuildArgs a, uint32_t epoc
     uint64_t* K1 = a.st.keys[dst];
     uint64_t* V1 = a.st.vals[dst];
     uint8_t* M1 = a.st.meta[dst];
-    if (tid == 0) s_ok = 1;
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_tile = atomicAdd(&a.bm->tile_ctr[kCtrMerge], 1u);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint32_t ts = tile * kNodes;
+        __syncthreads();  // the previous tile's readers of s_nl and s_lp are done
+        if (tid < 64) {  // warp 0: the tile's first new node; warp 1: the next tile's
+            const uint32_t r = warp_lower_bound_u32(a.nn.loc, newc, tid < 32 ? ts : ts + kNodes);
+            if (tid == 0) s_jb = r;
+            if (tid == 32) s_je = r;
+        }
+        for (int x = tid; x < kNodes; x += kThreads) s_nl[x] = 0u;
+        __syncthreads();
         const uint32_t cnt = (size > ts) ? min((uint32_t)kNodes, size - ts) : 0u;
-        const uint32_t b0 = tid * kPer;
-        uint32_t live_bits = 0, lc = 0;
+        const uint32_t jb = s_jb, je = s_je;
+        // new nodes per insertion position (loc - ts is in [0, kNodes))
+        for (uint32_t j = jb + tid; j < je; j += kThreads) {
+            const uint32_t x = a.nn.loc[j] - ts;
+            if (x < (uint32_t)kNodes) atomicAdd(&s_nl[x], 1u);
+            else atomicOr(a.err, kErrBounds);
+        }
+        __syncthreads();
+        // blocked pass: positions [16 tid, 16 tid + 16); the storage arrays are padded by
+        // a whole tile, so the 16-byte meta load stays in bounds past the last node
+        const uint32_t b0 = (uint32_t)tid * kPer;
+        const uint4 mw = *reinterpret_cast<const uint4*>(M0 + ts + b0);
+        const uint32_t words[4] = {mw.x, mw.y, mw.z, mw.w};
+        uint32_t live_bits = 0, lc = 0, nc = 0;
+        uint32_t nat[kPer];
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
-            const uint32_t li = b0 + k;
-            const bool lv = li < cnt && !(M0[ts + li] & kTomb);
+            const uint32_t mt = (words[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+            const bool lv = b0 + k < cnt && !(mt & kTomb);
             live_bits |= (lv ? 1u : 0u) << k;
             lc += lv ? 1u : 0u;
+            nat[k] = s_nl[b0 + k];
+            nc += nat[k];
         }
-        uint32_t tile_live;
-        uint32_t excl = block_excl_sum<kThreads>(lc, s_tmp, &tile_live);
+        uint64_t tot;
+        const uint64_t ex = block_excl_sum64((uint64_t)lc | ((uint64_t)nc << 32), s_tmp, &tot);
+        const uint32_t tile_live = (uint32_t)tot;
         {
-            uint32_t run = excl;
+            uint32_t rl = (uint32_t)ex, rn = (uint32_t)(ex >> 32);
 #pragma unroll
             for (int k = 0; k < kPer; ++k) {
-                s_lp[b0 + k] = (uint16_t)run;
-                run += (live_bits >> k) & 1u;
+                s_lp[b0 + k] = (uint16_t)rl;
+                rl += (live_bits >> k) & 1u;
+                rn += nat[k];
+                s_nl[b0 + k] = rn;
             }
-            if (tid == kThreads - 1) s_lp[kNodes] = (uint16_t)run;
+            if (tid == kThreads - 1) s_lp[kNodes] = (uint16_t)rl;
         }
-        if (tid < 32) {
-            bool ok;
-            const uint32_t ex = lookback_warp<false>(a.desc, tile, epoch, tile_live, a.err, &ok);
-            if (tid == 0) {
-                s_prefix = ex;
-                if (!ok) s_ok = 0;
-                s_jb = lower_bound_u32(a.nn.loc, newc, ts);
-                s_je = lower_bound_u32(a.nn.loc, newc, ts + kNodes);
-            }
-        }
+        if (tid == 0 && tile_live != a.mcnt[tile]) atomicOr(a.err, kErrBounds);  // the two counts agree
         __syncthreads();
-        if (!s_ok) break;
-        const uint32_t jb = s_jb, je = s_je;
-        const uint32_t out_base = s_prefix + jb;
-        // old live nodes
-        {
-            uint32_t ptr = jb + (je > jb ? lower_bound_u32(a.nn.loc + jb, je - jb, ts + b0 + 1) : 0u);
-            uint32_t run = excl;
+        const uint32_t out_base = a.mcnt[a.lstride + tile] + jb;
+        // striped pass: old live nodes, coalesced; four positions per round, their loads
+        // issued together (the source buffer is read-only here)
+        for (uint32_t x0 = (uint32_t)tid; x0 < cnt; x0 += 4u * kThreads) {
+            uint32_t mt[4];
+            uint64_t kv[4], vv[4];
 #pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                const uint32_t li = b0 + k;
-                if (li >= cnt) break;
-                while (ptr < je && a.nn.loc[ptr] <= ts + li) ++ptr;
-                if ((live_bits >> k) & 1u) {
-                    const uint32_t o = out_base + run + (ptr - jb);
-                    if (o >= a.st_cap) {
-                        atomicOr(a.err, kErrBounds);
-                        break;
-                    }
-                    K1[o] = K0[ts + li];
-                    V1[o] = V0[ts + li];
-                    M1[o] = M0[ts + li];
-                    ++run;
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t x = x0 + (uint32_t)u * kThreads;
+                const bool in = x < cnt;
+                mt[u] = in ? (uint32_t)__ldg(M0 + ts + x) : (uint32_t)kTomb;
+                kv[u] = in ? __ldg(K0 + ts + x) : 0ull;
+                vv[u] = in ? __ldg(V0 + ts + x) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (mt[u] & kTomb) continue;
+                const uint32_t x = x0 + (uint32_t)u * kThreads;
+                const uint32_t o = out_base + s_lp[x] + s_nl[x];
+                if (o >= a.st_cap) {
+                    atomicOr(a.err, kErrBounds);
+                    continue;
                 }
+                K1[o] = kv[u];
+                V1[o] = vv[u];
+                M1[o] = (uint8_t)mt[u];
             }
         }
-        // new nodes of this tile
+        // new nodes of this tile, before the old node at their position
         for (uint32_t j = jb + tid; j < je; j += kThreads) {
-            const uint32_t x = a.nn.loc[j] - ts;  // in [0, kNodes]
+            const uint32_t x = a.nn.loc[j] - ts;
+            if (x >= (uint32_t)kNodes) continue;  // recorded above
             const uint32_t o = out_base + s_lp[x] + (j - jb);
-            if (x > (uint32_t)kNodes || o >= a.st_cap) {
+            if (o >= a.st_cap) {
                 atomicOr(a.err, kErrBounds);
                 continue;
             }
@@ -723,9 +861,12 @@ __global__ void k_wait_selftest(uint64_t* desc, uint32_t* err) {
 }  // namespace
 
 cudaError_t launch_merge(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms) {
+    (void)epoch;  // the merge has no look-back
     const uint32_t tiles = a.size_ub / kNodes + 1;
-    const uint32_t cap = (uint32_t)num_sms * 4u;
-    launch_dep(k_merge, (int)(tiles < cap ? tiles : cap), kThreads, 0, s, a, ++epoch);
+    const uint32_t ccap = (uint32_t)num_sms * 8u, cap = (uint32_t)num_sms * 5u;  // the CTAs resident at once
+    launch_dep(k_merge_count, tiles < ccap ? tiles : ccap, kThreads, 0, s, a);
+    ++g_launches;
+    launch_dep(k_merge, tiles < cap ? tiles : cap, kThreads, 0, s, a);
     ++g_launches;
     return cudaGetLastError();
 }
