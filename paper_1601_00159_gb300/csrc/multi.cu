@@ -47,6 +47,7 @@ __device__ __forceinline__ void mstore_result(pi_result_t* res, uint32_t seq, ui
 
 struct MShared {
     uint32_t tmp[33];
+    uint64_t tmp64[33];
     uint32_t bmax[8], bnmin[8];
     uint32_t invalid;
     uint32_t item;
@@ -117,6 +118,54 @@ __device__ __forceinline__ void small_excl_scan(uint32_t* cnt, uint32_t* tmp) {
         run += v[k];
     }
     __syncthreads();
+}
+
+// Block-wide exclusive sum of 64-bit values over kT threads; total in *total.
+template <int kT>
+__device__ __forceinline__ uint64_t block_excl_sum64(uint64_t v, uint64_t* tmp, uint64_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t w = lane < kT / 32 ? tmp[lane] : 0ull;
+        uint64_t t = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kT / 32) tmp[lane] = t - w;
+        if (lane == kT / 32 - 1) tmp[32] = t;
+    }
+    __syncthreads();
+    const uint64_t r = tmp[warp] + x - v;
+    if (total) *total = tmp[32];
+    __syncthreads();
+    return r;
+}
+
+// Entries of the sorted a[0, n) below x, by a whole warp: each round probes 32 evenly
+// spaced entries of the remaining interval, about log32(n) rounds of one load per lane.
+__device__ __forceinline__ uint32_t warp_count_below(const uint32_t* a, uint32_t n, uint32_t x) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t lo = 0, hi = n;  // the count lies in [lo, hi]
+    while (hi - lo > 32u) {
+        const uint32_t step = (hi - lo + 31u) / 32u;
+        const uint32_t p = lo + lane * step;
+        const uint32_t c = (uint32_t)__popc(__ballot_sync(0xffffffffu, p < hi && a[p] < x));
+        if (c == 0) return lo;
+        const uint32_t pc = lo + c * step;
+        hi = (c < 32u && pc < hi) ? pc : hi;
+        lo = lo + (c - 1u) * step + 1u;
+    }
+    const uint32_t p = lo + lane;
+    return lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, p < hi && a[p] < x));
 }
 
 // Largest index i in [lo - 1, ...) with K[i] <= q for up to kMK keys at once; K holds a
@@ -658,49 +707,76 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
         uint64_t* DK = X.st.keys[dst];
         uint64_t* DV = X.st.vals[dst];
         uint8_t* DM = X.st.meta[dst];
-        uint32_t* lp = reinterpret_cast<uint32_t*>(dsm);  // live nodes before each chunk position
+        uint32_t* lp = reinterpret_cast<uint32_t*>(dsm);  // live old nodes before each chunk position
+        uint32_t* nl = lp + kC;                             // new nodes at or before each chunk position
         uint32_t carry = 0, j0 = 0;
         for (uint32_t c0 = 0; c0 < size; c0 += kC) {
-            const uint32_t i0 = c0 + (uint32_t)tid * kMI;
-            uint32_t lmask = 0;
-#pragma unroll
-            for (int k = 0; k < kMI; ++k) {
-                const uint32_t i = i0 + k;
-                if (i < size && !(SM[i] & kTomb)) lmask |= 1u << k;
+            const uint32_t lim = c0 + kC < size ? c0 + kC : size;
+            if (tid < 32) {  // new nodes placed before an old node of this chunk: [j0, j1)
+                const uint32_t r = j0 + warp_count_below(s.ni + j0, M - j0, lim);
+                if (tid == 0) sh.j1 = r;
             }
-            uint32_t tot;
-            uint32_t lb = carry + block_excl_sum<kT>((uint32_t)__popc(lmask), sh.tmp, &tot);
-#pragma unroll
-            for (int k = 0; k < kMI; ++k) {
-                lp[tid * kMI + k] = lb;
-                lb += (lmask >> k) & 1u;
-            }
-            if (tid == 0) {  // new nodes placed before an old node of this chunk: [j0, j1)
-                uint32_t lo = j0, hi = M;
-                const uint32_t lim = c0 + kC < size ? c0 + kC : size;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (s.ni[mid] < lim) lo = mid + 1;
-                    else hi = mid;
-                }
-                sh.j1 = lo;
-            }
+            for (uint32_t x = tid; x < kC; x += kT) nl[x] = 0u;
             __syncthreads();
             const uint32_t j1 = sh.j1;
+            for (uint32_t j = j0 + tid; j < j1; j += kT) atomicAdd(&nl[s.ni[j] - c0], 1u);
+            __syncthreads();
+            // blocked: positions [kMI tid, kMI tid + kMI) of the chunk
+            const uint32_t b0 = (uint32_t)tid * kMI, i0 = c0 + b0;
+            uint32_t lmask = 0, nsum = 0;
+            uint32_t nat[kMI];
+            if (i0 + kMI <= size) {
+                const uint2 w8 = *reinterpret_cast<const uint2*>(SM + i0);  // i0 is a multiple of 8
+#pragma unroll
+                for (int k = 0; k < kMI; ++k) {
+                    const uint32_t mt = ((k < 4 ? w8.x : w8.y) >> (8 * (k & 3))) & 0xFFu;
+                    if (!(mt & kTomb)) lmask |= 1u << k;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kMI; ++k)
+                    if (i0 + k < size && !(SM[i0 + k] & kTomb)) lmask |= 1u << k;
+            }
 #pragma unroll
             for (int k = 0; k < kMI; ++k) {
-                if (!((lmask >> k) & 1u)) continue;
-                const uint32_t i = i0 + k;
-                uint32_t lo = j0, hi = j1;  // new nodes with insertion point <= i
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (s.ni[mid] <= i) lo = mid + 1;
-                    else hi = mid;
+                nat[k] = nl[b0 + k];
+                nsum += nat[k];
+            }
+            uint64_t tot;
+            const uint64_t ex = block_excl_sum64<kT>((uint64_t)__popc(lmask) | ((uint64_t)nsum << 32), sh.tmp64, &tot);
+            {
+                uint32_t rl = carry + (uint32_t)ex, rn = j0 + (uint32_t)(ex >> 32);
+#pragma unroll
+                for (int k = 0; k < kMI; ++k) {
+                    lp[b0 + k] = rl;
+                    rl += (lmask >> k) & 1u;
+                    rn += nat[k];
+                    nl[b0 + k] = rn;
                 }
-                const uint32_t o = lp[tid * kMI + k] + lo;
-                DK[o] = SK[i];
-                DV[o] = SV[i];
-                DM[o] = (uint8_t)(SM[i] & 0x3Fu);
+            }
+            __syncthreads();
+            // striped: the chunk's live old nodes, coalesced, four positions per round
+            const uint32_t cnt = lim - c0;
+            for (uint32_t x0 = tid; x0 < cnt; x0 += 4u * kT) {
+                uint32_t mt[4];
+                uint64_t kv[4], vv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t x = x0 + (uint32_t)u * kT;
+                    const bool in = x < cnt;
+                    mt[u] = in ? (uint32_t)SM[c0 + x] : (uint32_t)kTomb;
+                    kv[u] = in ? SK[c0 + x] : 0ull;
+                    vv[u] = in ? SV[c0 + x] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (mt[u] & kTomb) continue;
+                    const uint32_t x = x0 + (uint32_t)u * kT;
+                    const uint32_t o = lp[x] + nl[x];
+                    DK[o] = kv[u];
+                    DV[o] = vv[u];
+                    DM[o] = (uint8_t)(mt[u] & 0x3Fu);
+                }
             }
             for (uint32_t j = j0 + tid; j < j1; j += kT) {
                 const uint32_t o = j + lp[s.ni[j] - c0];
@@ -708,7 +784,7 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
                 DV[o] = s.nv[j];
                 DM[o] = s.nh[j];
             }
-            carry += tot;
+            carry += (uint32_t)tot;
             j0 = j1;
             __syncthreads();
         }
@@ -900,7 +976,7 @@ constexpr int multi_smem() {
     constexpr int kT = kW * 32;
     constexpr int sort = (kW * (1 << kBits) + 2 * (1 << kBits)) * 4;
     constexpr int top = (int)kMTop * 12;
-    constexpr int merge = kT * kMI * 4;
+    constexpr int merge = kT * kMI * 8;  // live and new-node prefixes per chunk position
     return sort > top ? (sort > merge ? sort : merge) : (top > merge ? top : merge);
 }
 
