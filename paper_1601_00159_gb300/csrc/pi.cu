@@ -1556,8 +1556,13 @@ int pi_multi_execute(pi_multi_t* mx, const pi_multi_batch_t* b, uint32_t nb, pi_
             }
             x->known.grow_request = 0;
         }
-        if (grew) {
-            mx->h_idx[b[i].index] = mindex_of(x);
+        (void)grew;
+        // The single-index path may have grown this index's arrays since the set last
+        // looked (a plain batch with new keys): the device table must hold the arrays in
+        // use, never freed ones.
+        const MIndex now = mindex_of(x);
+        if (std::memcmp(&now, &mx->h_idx[b[i].index], sizeof(MIndex)) != 0) {
+            mx->h_idx[b[i].index] = now;
             idx_changed = true;
         }
         wait_rebuild(x, s);

@@ -137,6 +137,32 @@ def test_multi_mixed_with_plain_path_and_subsets(orc_mod):
     ms.close()
 
 
+def test_multi_after_the_plain_path_grew_an_index(orc_mod):
+    """A plain batch of new keys grows an index's storage (its arrays are reallocated);
+    the set's next calls must use the new arrays."""
+    from paper_1601_00159_gb300 import MultiSet
+    from tests.parity import run_batch
+    seed = 29
+    idxs, orcs, keysets = build_set(orc_mod, seed, 6, 4, 12)
+    ms = MultiSet(idxs)
+    run_rounds(ms, idxs, orcs, keysets, seed, 1, 0, 10)
+    cap0 = idxs[2].info()["storage_capacity"]
+    q = 90000  # more new keys than the storage layer's headroom
+    s = wl.stream_seed(seed, 5)
+    ins = wl.Batch(np.ones(q, np.uint8), wl.u64_stream(s, 0, q) >> np.uint64(1), wl.u64_stream(s, q, q))
+    icap0 = idxs[2].info()["index_capacity"]
+    assert_results_equal(run_batch(idxs[2], ins), orcs[2].execute(ins.ops, ins.keys, ins.vals), "plain growth")
+    # the next plain batch grows the index layer the larger storage layer needs
+    b = make_batch(31, keysets[2], 500)
+    assert_results_equal(run_batch(idxs[2], b), orcs[2].execute(b.ops, b.keys, b.vals), "plain after growth")
+    info = idxs[2].info()
+    assert info["storage_capacity"] > cap0 and info["index_capacity"] > icap0
+    run_rounds(ms, idxs, orcs, keysets, seed + 1, 3, 0, 12)
+    for i, (ix, orc) in enumerate(zip(idxs, orcs)):
+        assert_state_equal(ix, orc, f"index {i}")
+    ms.close()
+
+
 def test_multi_rejects_bad_sets_and_batches():
     import torch
     from paper_1601_00159_gb300 import MultiSet, PiError, PI_ERR_INVALID_ARG
