@@ -698,117 +698,11 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
         __syncthreads();
     }
 
-    // ---- merge: live old nodes and the new nodes into the other storage buffer
+    // ---- the new level layout (before the merge, which may write the lowest level)
     const uint32_t M = sh.newc;
     const bool merged = M > 0 || (sh.m.tombs > 0 && (uint64_t)sh.m.tombs * 8u > sh.m.size);
-    if (merged) {
-        const uint32_t size = sh.m.size;
-        const uint32_t dst = cur ^ 1u;
-        uint64_t* DK = X.st.keys[dst];
-        uint64_t* DV = X.st.vals[dst];
-        uint8_t* DM = X.st.meta[dst];
-        uint32_t* lp = reinterpret_cast<uint32_t*>(dsm);  // live old nodes before each chunk position
-        uint32_t* nl = lp + kC;                             // new nodes at or before each chunk position
-        uint32_t carry = 0, j0 = 0;
-        for (uint32_t c0 = 0; c0 < size; c0 += kC) {
-            const uint32_t lim = c0 + kC < size ? c0 + kC : size;
-            if (tid < 32) {  // new nodes placed before an old node of this chunk: [j0, j1)
-                const uint32_t r = j0 + warp_count_below(s.ni + j0, M - j0, lim);
-                if (tid == 0) sh.j1 = r;
-            }
-            for (uint32_t x = tid; x < kC; x += kT) nl[x] = 0u;
-            __syncthreads();
-            const uint32_t j1 = sh.j1;
-            for (uint32_t j = j0 + tid; j < j1; j += kT) atomicAdd(&nl[s.ni[j] - c0], 1u);
-            __syncthreads();
-            // blocked: positions [kMI tid, kMI tid + kMI) of the chunk
-            const uint32_t b0 = (uint32_t)tid * kMI, i0 = c0 + b0;
-            uint32_t lmask = 0, nsum = 0;
-            uint32_t nat[kMI];
-            if (i0 + kMI <= size) {
-                const uint2 w8 = *reinterpret_cast<const uint2*>(SM + i0);  // i0 is a multiple of 8
-#pragma unroll
-                for (int k = 0; k < kMI; ++k) {
-                    const uint32_t mt = ((k < 4 ? w8.x : w8.y) >> (8 * (k & 3))) & 0xFFu;
-                    if (!(mt & kTomb)) lmask |= 1u << k;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kMI; ++k)
-                    if (i0 + k < size && !(SM[i0 + k] & kTomb)) lmask |= 1u << k;
-            }
-#pragma unroll
-            for (int k = 0; k < kMI; ++k) {
-                nat[k] = nl[b0 + k];
-                nsum += nat[k];
-            }
-            uint64_t tot;
-            const uint64_t ex = block_excl_sum64<kT>((uint64_t)__popc(lmask) | ((uint64_t)nsum << 32), sh.tmp64, &tot);
-            {
-                uint32_t rl = carry + (uint32_t)ex, rn = j0 + (uint32_t)(ex >> 32);
-#pragma unroll
-                for (int k = 0; k < kMI; ++k) {
-                    lp[b0 + k] = rl;
-                    rl += (lmask >> k) & 1u;
-                    rn += nat[k];
-                    nl[b0 + k] = rn;
-                }
-            }
-            __syncthreads();
-            // striped: the chunk's live old nodes, coalesced, four positions per round
-            const uint32_t cnt = lim - c0;
-            for (uint32_t x0 = tid; x0 < cnt; x0 += 4u * kT) {
-                uint32_t mt[4];
-                uint64_t kv[4], vv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t x = x0 + (uint32_t)u * kT;
-                    const bool in = x < cnt;
-                    mt[u] = in ? (uint32_t)SM[c0 + x] : (uint32_t)kTomb;
-                    kv[u] = in ? SK[c0 + x] : 0ull;
-                    vv[u] = in ? SV[c0 + x] : 0ull;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (mt[u] & kTomb) continue;
-                    const uint32_t x = x0 + (uint32_t)u * kT;
-                    const uint32_t o = lp[x] + nl[x];
-                    DK[o] = kv[u];
-                    DV[o] = vv[u];
-                    DM[o] = (uint8_t)(mt[u] & 0x3Fu);
-                }
-            }
-            for (uint32_t j = j0 + tid; j < j1; j += kT) {
-                const uint32_t o = j + lp[s.ni[j] - c0];
-                DK[o] = s.nk[j];
-                DV[o] = s.nv[j];
-                DM[o] = s.nh[j];
-            }
-            carry += (uint32_t)tot;
-            j0 = j1;
-            __syncthreads();
-        }
-        for (uint32_t j = j0 + tid; j < M; j += kT) {  // after the last old node
-            const uint32_t o = j + carry;
-            DK[o] = s.nk[j];
-            DV[o] = s.nv[j];
-            DM[o] = s.nh[j];
-        }
-        const uint32_t nsize = carry + M;
-        if (tid == 0) {
-            if (nsize > X.st_cap) atomicOr(err, kErrBounds);
-            DK[nsize] = kMaxKey;
-            DV[nsize] = 0;
-            DM[nsize] = 0;
-            sh.m.size = nsize;
-            sh.m.tombs = 0;
-            sh.m.cur = dst;
-        }
-        __syncthreads();
-    }
-
-    // ---- rebuild the index layer when the membership of any level changed
-    if (merged || sh.dirty) {
+    const bool relevel = merged || sh.dirty;
+    if (relevel) {
         if (tid == 0) {
             DevMeta& m = sh.m;
             uint32_t H = 1;
@@ -850,14 +744,183 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
             m.levels_exact = 1;  // rebuilt in place from the storage layer
         }
         __syncthreads();
+    }
+    // A merge rewrites the storage layer in key order, so it also writes the lowest built
+    // level: each member's key and new storage position, at its rank among the members.
+    const bool fused = merged && sh.m.Lb <= sh.m.H;
+
+    // ---- merge: live old nodes and the new nodes into the other storage buffer
+    if (merged) {
+        const uint32_t size = sh.m.size;
+        const uint32_t dst = cur ^ 1u;
+        uint64_t* DK = X.st.keys[dst];
+        uint64_t* DV = X.st.vals[dst];
+        uint8_t* DM = X.st.meta[dst];
+        const uint32_t Lb = sh.m.Lb, lbase = sh.m.base[Lb];
+        uint32_t* nmp = s.dr;  // members among the first j new nodes (the descent's output is dead)
+        if (fused) {
+            uint32_t run = 0;
+            for (uint32_t g0 = 0; g0 < M; g0 += kC) {
+                const uint32_t i0 = g0 + (uint32_t)tid * kMI;
+                uint32_t mm = 0;
+#pragma unroll
+                for (int k = 0; k < kMI; ++k)
+                    if (i0 + k < M && s.nh[i0 + k] >= Lb) mm |= 1u << k;
+                uint32_t tot;
+                uint32_t r = run + block_excl_sum<kT>((uint32_t)__popc(mm), sh.tmp, &tot);
+#pragma unroll
+                for (int k = 0; k < kMI; ++k) {
+                    if (i0 + k < M) nmp[i0 + k] = r;
+                    r += (mm >> k) & 1u;
+                }
+                run += tot;
+            }
+            if (tid == 0) nmp[M] = run;
+            __syncthreads();
+        }
+        uint32_t* lp = reinterpret_cast<uint32_t*>(dsm);  // live old nodes before each chunk position
+        uint32_t* nl = lp + kC;                             // new nodes at or before each chunk position
+        uint32_t* ob = nl + kC;                             // old members of level Lb before each position
+        uint32_t carry = 0, cmem = 0, j0 = 0;
+        for (uint32_t c0 = 0; c0 < size; c0 += kC) {
+            const uint32_t lim = c0 + kC < size ? c0 + kC : size;
+            if (tid < 32) {  // new nodes placed before an old node of this chunk: [j0, j1)
+                const uint32_t r = j0 + warp_count_below(s.ni + j0, M - j0, lim);
+                if (tid == 0) sh.j1 = r;
+            }
+            for (uint32_t x = tid; x < kC; x += kT) nl[x] = 0u;
+            __syncthreads();
+            const uint32_t j1 = sh.j1;
+            for (uint32_t j = j0 + tid; j < j1; j += kT) atomicAdd(&nl[s.ni[j] - c0], 1u);
+            __syncthreads();
+            // blocked: positions [kMI tid, kMI tid + kMI) of the chunk
+            const uint32_t b0 = (uint32_t)tid * kMI, i0 = c0 + b0;
+            uint32_t lmask = 0, omask = 0, nsum = 0;
+            uint32_t nat[kMI];
+            uint32_t hb[kMI];
+            if (i0 + kMI <= size) {
+                const uint2 w8 = *reinterpret_cast<const uint2*>(SM + i0);  // i0 is a multiple of 8
+#pragma unroll
+                for (int k = 0; k < kMI; ++k) hb[k] = ((k < 4 ? w8.x : w8.y) >> (8 * (k & 3))) & 0xFFu;
+            } else {
+#pragma unroll
+                for (int k = 0; k < kMI; ++k) hb[k] = i0 + k < size ? (uint32_t)SM[i0 + k] : (uint32_t)kTomb;
+            }
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                if (!(hb[k] & kTomb)) {
+                    lmask |= 1u << k;
+                    if (fused && (hb[k] & 0x3Fu) >= Lb) omask |= 1u << k;
+                }
+                nat[k] = nl[b0 + k];
+                nsum += nat[k];
+            }
+            // one scan of three counts: live (bits 0-15), old members (16-31), new (32-63)
+            uint64_t tot;
+            const uint64_t ex = block_excl_sum64<kT>(
+                (uint64_t)__popc(lmask) | ((uint64_t)__popc(omask) << 16) | ((uint64_t)nsum << 32), sh.tmp64, &tot);
+            {
+                uint32_t rl = carry + (uint32_t)(ex & 0xFFFFu), ro = cmem + (uint32_t)((ex >> 16) & 0xFFFFu);
+                uint32_t rn = j0 + (uint32_t)(ex >> 32);
+#pragma unroll
+                for (int k = 0; k < kMI; ++k) {
+                    lp[b0 + k] = rl;
+                    ob[b0 + k] = ro;
+                    rl += (lmask >> k) & 1u;
+                    ro += (omask >> k) & 1u;
+                    rn += nat[k];
+                    nl[b0 + k] = rn;
+                }
+            }
+            __syncthreads();
+            // striped: the chunk's live old nodes, coalesced, four positions per round
+            const uint32_t cnt = lim - c0;
+            for (uint32_t x0 = tid; x0 < cnt; x0 += 4u * kT) {
+                uint32_t mt[4];
+                uint64_t kv[4], vv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t x = x0 + (uint32_t)u * kT;
+                    const bool in = x < cnt;
+                    mt[u] = in ? (uint32_t)SM[c0 + x] : (uint32_t)kTomb;
+                    kv[u] = in ? SK[c0 + x] : 0ull;
+                    vv[u] = in ? SV[c0 + x] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (mt[u] & kTomb) continue;
+                    const uint32_t x = x0 + (uint32_t)u * kT;
+                    const uint32_t o = lp[x] + nl[x];
+                    DK[o] = kv[u];
+                    DV[o] = vv[u];
+                    DM[o] = (uint8_t)(mt[u] & 0x3Fu);
+                    if (fused && (mt[u] & 0x3Fu) >= Lb) {
+                        const uint32_t r = ob[x] + nmp[nl[x]];
+                        if (r < sh.m.n[Lb]) {
+                            LK[lbase + r] = kv[u];
+                            LD[lbase + r] = o;
+                        }
+                    }
+                }
+            }
+            for (uint32_t j = j0 + tid; j < j1; j += kT) {
+                const uint32_t x = s.ni[j] - c0;
+                const uint32_t o = j + lp[x];
+                DK[o] = s.nk[j];
+                DV[o] = s.nv[j];
+                DM[o] = s.nh[j];
+                if (fused && s.nh[j] >= Lb) {
+                    const uint32_t r = ob[x] + nmp[j];
+                    if (r < sh.m.n[Lb]) {
+                        LK[lbase + r] = s.nk[j];
+                        LD[lbase + r] = o;
+                    }
+                }
+            }
+            carry += (uint32_t)(tot & 0xFFFFu);
+            cmem += (uint32_t)((tot >> 16) & 0xFFFFu);
+            j0 = j1;
+            __syncthreads();
+        }
+        for (uint32_t j = j0 + tid; j < M; j += kT) {  // after the last old node
+            const uint32_t o = j + carry;
+            DK[o] = s.nk[j];
+            DV[o] = s.nv[j];
+            DM[o] = s.nh[j];
+            if (fused && s.nh[j] >= Lb) {
+                const uint32_t r = cmem + nmp[j];
+                if (r < sh.m.n[Lb]) {
+                    LK[lbase + r] = s.nk[j];
+                    LD[lbase + r] = o;
+                }
+            }
+        }
+        const uint32_t nsize = carry + M;
+        if (tid == 0) {
+            if (nsize > X.st_cap) atomicOr(err, kErrBounds);
+            if (fused && cmem + nmp[M] != sh.m.n[Lb]) atomicOr(err, kErrBounds);
+            DK[nsize] = kMaxKey;
+            DV[nsize] = 0;
+            DM[nsize] = 0;
+            sh.m.size = nsize;
+            sh.m.tombs = 0;
+            sh.m.cur = dst;
+        }
+        __syncthreads();
+    }
+
+    // ---- rebuild the index layer when the membership of any level changed
+    if (relevel) {
+        __syncthreads();
         const DevMeta& m = sh.m;
         const uint32_t H = m.H, Lb = m.Lb, size = m.size;
         const uint32_t ncur = m.cur;
         const uint64_t* RK = X.st.keys[ncur];
         const uint8_t* RM = X.st.meta[ncur];
         if (Lb <= H) {
-            // level Lb from the storage layer: live nodes of height >= Lb
+            // level Lb from the storage layer: live nodes of height >= Lb (a merge wrote it)
             uint32_t carry = 0;
+            if (!fused) {
             for (uint32_t c0 = 0; c0 < size; c0 += kC) {
                 const uint32_t i0 = c0 + (uint32_t)tid * kMI;
                 uint32_t mm = 0;
@@ -883,6 +946,7 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
                 carry += tot;
             }
             if (tid == 0 && carry != m.n[Lb]) atomicOr(err, kErrBounds);
+            }
             __syncthreads();
             // level l + 1 from level l: its members of height >= l + 1
             for (uint32_t l = Lb; l < H; ++l) {
@@ -976,7 +1040,7 @@ constexpr int multi_smem() {
     constexpr int kT = kW * 32;
     constexpr int sort = (kW * (1 << kBits) + 2 * (1 << kBits)) * 4;
     constexpr int top = (int)kMTop * 12;
-    constexpr int merge = kT * kMI * 8;  // live and new-node prefixes per chunk position
+    constexpr int merge = kT * kMI * 12;  // live, new-node and member prefixes per chunk position
     return sort > top ? (sort > merge ? sort : merge) : (top > merge ? top : merge);
 }
 
