@@ -120,6 +120,11 @@ __device__ __forceinline__ void small_excl_scan(uint32_t* cnt, uint32_t* tmp) {
     __syncthreads();
 }
 
+// TMA bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+    if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Block-wide exclusive sum of 64-bit values over kT threads; total in *total.
 template <int kT>
 __device__ __forceinline__ uint64_t block_excl_sum64(uint64_t v, uint64_t* tmp, uint64_t* total) {
@@ -784,6 +789,14 @@ __device__ void m_item(const MultiArgs& a, const MItem& it, const MScratchPtrs& 
         uint32_t carry = 0, cmem = 0, j0 = 0;
         for (uint32_t c0 = 0; c0 < size; c0 += kC) {
             const uint32_t lim = c0 + kC < size ? c0 + kC : size;
+            if (tid == 0 && lim < size) {  // the next chunk's nodes into L2 while this one is copied
+                const uint32_t nx = lim, nn = (size - nx < kC ? size - nx : kC);
+                // nx is a multiple of the chunk, so every start is 16-byte aligned; sizes
+                // round up to 16 bytes (the storage arrays are padded past their end)
+                l2_prefetch(SK + nx, (nn * 8u + 15u) & ~15u);
+                l2_prefetch(SV + nx, (nn * 8u + 15u) & ~15u);
+                l2_prefetch(SM + nx, (nn + 15u) & ~15u);
+            }
             if (tid < 32) {  // new nodes placed before an old node of this chunk: [j0, j1)
                 const uint32_t r = j0 + warp_count_below(s.ni + j0, M - j0, lim);
                 if (tid == 0) sh.j1 = r;
