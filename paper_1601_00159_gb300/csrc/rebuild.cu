@@ -37,17 +37,8 @@ __device__ __forceinline__ bool merge_needed(const DevMeta* m, const BatchMeta* 
     return bm->new_count > 0 || (tombs > 0 && (uint64_t)tombs * 8u > size);
 }
 
-// Number of entries of a[0..n) that are < x (a sorted).
-__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t n, uint32_t x) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// The same count by a whole warp (every lane calls it and gets the result): each round
+// Entries of the sorted a[0, n) below x, by a whole warp (every lane calls it and gets
+// the result): each round
 // probes 32 evenly spaced entries of the remaining interval at once, so a search of n
 // entries takes about log32(n) rounds of one load per lane instead of log2(n) dependent
 // loads.

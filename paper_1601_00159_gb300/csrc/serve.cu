@@ -268,6 +268,41 @@ void fill_group(pi_server* s, const uint8_t* ops, const uint64_t* keys, const ui
     if (wake_coll) s->cv_done.notify_all();  // a collector waits for these tickets to exist
 }
 
+// Collects, in ticket order from `ticket` on (the oldest uncollected request), every
+// request that is done, at most `limit`, waiting for the first one: request j's results
+// go to results_out + offs[j] (results_out may be null) and its latency to lat_out[j]
+// (may be null); their ring space is freed at once. One lock round per group instead
+// of one per request. Returns how many were collected (>= 1), or a negative error code.
+int64_t collect_group(pi_server* s, uint64_t ticket, uint32_t limit, pi_result_t* results_out, const uint64_t* offs,
+                      double* lat_out) {
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (ticket != s->first || limit == 0) return PI_ERR_INVALID_ARG;
+    if (s->reqs.empty()) {  // the collector may run ahead of the submitter
+        s->submit_waiters++;
+        s->cv_done.wait(lk, [&] { return !s->reqs.empty() || s->error != PI_OK; });
+        s->submit_waiters--;
+    }
+    if (s->reqs.empty()) return s->error != PI_OK ? s->error : PI_ERR_INVALID_ARG;
+    s->cv_done.wait(lk, [&] { return s->reqs.front().done || s->error != PI_OK; });
+    if (!s->reqs.front().done) return s->error;
+    uint32_t k = 0;
+    while (k < limit && k < s->reqs.size() && s->reqs[k].done) ++k;
+    std::vector<Req> rs(s->reqs.begin(), s->reqs.begin() + k);
+    lk.unlock();
+    for (uint32_t j = 0; j < k; ++j) {
+        const Req& r = rs[j];
+        if (results_out)
+            std::memcpy(results_out + offs[j], s->r_res + r.pos % s->R, (size_t)r.n * sizeof(pi_result_t));
+        if (lat_out) lat_out[j] = (double)(r.t_done - r.t_arrive) * 1e-9;
+    }
+    lk.lock();
+    s->reqs.erase(s->reqs.begin(), s->reqs.begin() + k);
+    s->first += k;
+    lk.unlock();
+    s->cv_space.notify_all();
+    return (int64_t)k;
+}
+
 double pct(std::vector<double>& v, double q) {
     if (v.empty()) return 0.0;
     const size_t k = (size_t)std::min<double>((double)(v.size() - 1), q * (double)(v.size() - 1) + 0.5);
@@ -417,13 +452,16 @@ int pi_server_replay(pi_server_t* s, const uint8_t* ops, const uint64_t* keys, c
         std::lock_guard<std::mutex> lk(s->mu);
         first = s->first + s->reqs.size();
     }
+    std::vector<uint64_t> offs(nreq + 1, 0);
+    for (uint32_t i = 0; i < nreq; ++i) offs[i + 1] = offs[i] + sizes[i];
     std::atomic<int> rc_collect{PI_OK};
     std::thread collector([&] {
-        uint64_t off = 0;
-        for (uint32_t i = 0; i < nreq; ++i) {
-            double lat = 0;
-            const int rc = pi_server_wait(s, first + i, results_out ? results_out + off : nullptr, &lat);
-            if (rc != PI_OK) {
+        uint32_t i = 0;
+        while (i < nreq) {  // every finished request at once, in ticket order
+            const int64_t k = collect_group(s, first + i, nreq - i, results_out, offs.data() + i,
+                                            latency_s_out ? latency_s_out + i : nullptr);
+            if (k <= 0) {
+                const int rc = k < 0 ? (int)k : PI_ERR_INVALID_ARG;
                 rc_collect = rc;
                 std::lock_guard<std::mutex> lk(s->mu);  // release a submitter waiting for space
                 if (s->error == PI_OK) s->error = rc;
@@ -431,14 +469,11 @@ int pi_server_replay(pi_server_t* s, const uint8_t* ops, const uint64_t* keys, c
                 s->cv_done.notify_all();
                 return;
             }
-            if (latency_s_out) latency_s_out[i] = lat;
-            off += sizes[i];
+            i += (uint32_t)k;
         }
     });
     int rc = PI_OK;
     const int64_t t0 = now_ns();
-    std::vector<uint64_t> offs(nreq + 1, 0);
-    for (uint32_t i = 0; i < nreq; ++i) offs[i + 1] = offs[i] + sizes[i];
     std::vector<int64_t> target(nreq);
     for (uint32_t i = 0; i < nreq; ++i) target[i] = t0 + (int64_t)(arrival_s[i] * 1e9);
     // Copy helpers: the main thread reserves groups in arrival order, the helpers copy
