@@ -227,7 +227,7 @@ int pi_size(pi_index_t* idx, uint64_t* size_out_host, pi_stream_t stream);
  *   that hits one returns PI_ERR_OOM and leaves the index as it was.
  * pi_selftest_wait: launches one CTA that waits, through the bounded look-back the batch
  *   kernels use, for a predecessor that never publishes. The wait gives up after its
- *   spin bound (about half a second), records the timeout in a scratch error word, which
+ *   spin bound (on a GB300 about 1.4 s), records the timeout in a scratch error word, which
  *   is written to *err_word_host, and the kernel returns. Returns PI_ERR_TIMEOUT when the
  *   bound worked. Allocates and frees 516 B of device memory; synchronises `stream`.
  */

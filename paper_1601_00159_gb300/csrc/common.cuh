@@ -26,7 +26,7 @@ constexpr uint32_t kErrBounds = 2u;   // an internal bound check refused an acce
 constexpr uint32_t kErrOwner = 4u;    // debug check: a storage node had two writers in one batch
 
 // Bounded spins: a look-back or barrier wait gives up after this many polls (about
-// half a second with the back-off below) and records kErrTimeout instead of hanging.
+// 1.4 s on a GB300 with the back-off below) and records kErrTimeout instead of hanging.
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Persistent device state of one index (one allocation, lives with the index).
