@@ -203,6 +203,39 @@ def test_height_known_structure(oracle_mod):
     assert found > 100
 
 
+def test_height_cap_known_answers(oracle_mod):
+    """The cap of the height rule: Hmax - 1 levels above the storage level at most, and a
+    hash of 0 counted as 64 trailing zeros. The keys are built to hit chosen hashes by
+    inverting splitmix64 (tests/hashkeys.py), and the expected heights are the
+    hand-derived table tests/golden/height_cap.txt."""
+    from tests.hashkeys import hash_with_trailing_zeros, key_with_hash, splitmix64_inverse
+    sm = oracle_mod.splitmix64
+    rows = [tuple(int(x) for x in r) for r in read_golden_table("height_cap.txt")]
+    assert len(rows) >= 20
+    for seed in (0, 7, 2024):
+        mix = sm(seed)
+        for b, tz, expected in rows:
+            for salt in (0, 12345, M64 >> 3):
+                h = hash_with_trailing_zeros(tz, salt)
+                assert sm(splitmix64_inverse(h)) == h
+                key = key_with_hash(h, mix)
+                assert sm(key ^ mix) == h
+                if key == M64:
+                    continue
+                assert oracle_mod.height(seed, b, key) == expected, (seed, b, tz, salt)
+    # Built into an index, such keys set its number of levels: Hmax for every b.
+    for b, hmax in ((1, 32), (2, 32), (3, 21), (4, 16)):
+        seed = 100 + b
+        mix = sm(seed)
+        capped = sorted({key_with_hash(0, mix), key_with_hash(1 << 63, mix)} - {M64})
+        keys = capped + [int(k) for k in wl.distinct_keys(b, np.arange(200))]
+        keys = np.array(sorted(set(keys)), np.uint64)
+        o = oracle_mod.Oracle(keys, np.arange(len(keys), dtype=np.uint64), 2.0 ** -b, seed)
+        assert o.num_levels() == hmax
+        assert o.level(hmax).tolist() == capped
+        o.close()
+
+
 def test_create_duplicates_last_wins_and_rejects_reserved(oracle_mod):
     keys = np.array([5, 3, 5, 9, 3, 5], np.uint64)
     vals = np.array([1, 2, 3, 4, 5, 6], np.uint64)
