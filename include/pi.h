@@ -156,19 +156,25 @@ int pi_execute_batch_host(pi_index_t* idx, const uint8_t* ops_host, const uint64
  * allocator (cudaMalloc/cudaFree can synchronise the device, which a latency-bound
  * serving loop cannot afford) and code running where a memory budget is fixed up front.
  * The per-batch scratch of up to PI_NOALLOC_MAX_BATCH queries comes from one
- * file-scope device array of a fixed size (about 9 MB), held by every GPU that loads
- * the library until the process exits; this call allocates nothing.
+ * file-scope device array of a fixed size (10,911,488 bytes, about 10.9 MB), held by
+ * every GPU that loads the library until the process exits; this call allocates nothing.
  *   - n > PI_NOALLOC_MAX_BATCH returns PI_ERR_INVALID_ARG.
  *   - A batch that could need the storage layer to grow returns PI_ERR_OOM with the
  *     index unchanged (create the index with enough storage_capacity, or use
  *     pi_execute_batch for that batch). An index layer that outgrows its capacity is not
  *     grown: its lowest levels are dropped and the results stay exact.
- *   - The first call on a device looks up the array's device address (with that device
- *     current); make that first call before any stream capture.
- *   - Every call shares the one array: calls whose work overlaps on the GPU (other
- *     streams, other indices) race and must be serialised by the caller. Nothing in the
- *     array needs to start at zero; each batch writes what it later reads.
- * Results and index updates are identical to pi_execute_batch's.
+ *   - The first call on a device looks up the array's device address and creates one
+ *     event (with that device current); make that first call before any stream capture.
+ *   - Every call shares the one array. Calls issued in order on one stream are safe, on
+ *     one index or alternating between indices: a call on another index than the
+ *     previous call's first makes its stream wait for that call's background rebuild,
+ *     which still reads the array. Calls whose work overlaps on the GPU (issued on
+ *     different streams without ordering between them) race and must be serialised by
+ *     the caller. Nothing in the array needs to start at zero; each batch writes what it
+ *     later reads.
+ * Results and the resulting key/value set are identical to pi_execute_batch's. The
+ * index layer's shape can differ after pi_execute_batch would have grown its capacity
+ * (its lowest levels are then dropped here); searches stay exact either way.
  */
 #define PI_NOALLOC_MAX_BATCH (1u << 16)
 int pi_execute_batch_noalloc(pi_index_t* idx, const uint8_t* ops, const uint64_t* keys,
@@ -250,6 +256,16 @@ int pi_export(pi_index_t* idx, uint64_t* keys_out, uint64_t* vals_out, uint64_t 
  * PI_ERR_NOT_BUILT if the level is not materialised. Synchronises `stream`. */
 int pi_export_level(pi_index_t* idx, int level, uint64_t* keys_out, uint32_t* down_out,
                     uint64_t cap, uint64_t* n_out_host, pi_stream_t stream);
+
+/* Test support: the storage layer as it is stored (Definition 1's level 1 with the
+ * delete-flagged nodes of Algorithm 4 still in place), positions 0 .. size-1, so a test
+ * can check the lowest built level's down pointers (its storage positions) while
+ * delete-flagged nodes exist. Up to cap keys and meta bytes (bits 0-5: tower height;
+ * bit 7: delete flag) are written to the device arrays keys_out / meta_out (meta_out may
+ * be NULL); *n_out_host = size. Synchronises `stream`. Returns PI_OK or the sticky
+ * error, like pi_status. */
+int pi_export_storage(pi_index_t* idx, uint64_t* keys_out, uint8_t* meta_out, uint64_t cap,
+                      uint64_t* n_out_host, pi_stream_t stream);
 
 /*
  * Stage timing, for measurement (no counterpart in the paper). While enabled, each

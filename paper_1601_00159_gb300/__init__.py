@@ -21,7 +21,7 @@ PI_MAX_KEYS = (1 << 30) - 2
 
 EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
             "pi_last_error", "pi_status", "pi_info", "pi_size", "pi_test_fail_allocations",
-            "pi_selftest_wait", "pi_num_levels", "pi_export", "pi_export_level", "pi_profile",
+            "pi_selftest_wait", "pi_num_levels", "pi_export", "pi_export_level", "pi_export_storage", "pi_profile",
             "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush",
             "pi_range_search", "pi_multi_create", "pi_multi_execute", "pi_multi_destroy", "pi_multi_kernels_per_call",
             "pi_server_create", "pi_server_submit", "pi_server_wait", "pi_server_stats", "pi_server_replay",
@@ -137,6 +137,8 @@ def load_library(path: str = LIB_PATH):
     lib.pi_export.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64), vp]
     lib.pi_export_level.restype = i32
     lib.pi_export_level.argtypes = [vp, i32, vp, vp, u64, ctypes.POINTER(u64), vp]
+    lib.pi_export_storage.restype = i32
+    lib.pi_export_storage.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64), vp]
     lib.pi_flush.restype = i32
     lib.pi_flush.argtypes = [vp, vp]
     lib.pi_profile.restype = i32
@@ -306,6 +308,19 @@ class Index:
         _chk(self.lib.pi_export_level(self._h, level, k.data_ptr(), d.data_ptr(), n.value, ctypes.byref(n),
                                       _stream_handle(stream)), "pi_export_level")
         return k[: n.value], d[: n.value]
+
+    def export_storage(self, stream=None):
+        """(keys int64, meta uint8) of the storage layer as stored, delete-flagged nodes
+        included (pi_export_storage)."""
+        import torch
+        n = ctypes.c_uint64(0)
+        _chk(self.lib.pi_export_storage(self._h, None, None, 0, ctypes.byref(n), _stream_handle(stream)),
+             "pi_export_storage")
+        k = torch.empty(max(n.value, 1), dtype=torch.int64, device="cuda")
+        m = torch.empty(max(n.value, 1), dtype=torch.uint8, device="cuda")
+        _chk(self.lib.pi_export_storage(self._h, k.data_ptr(), m.data_ptr(), n.value, ctypes.byref(n),
+                                        _stream_handle(stream)), "pi_export_storage")
+        return k[: n.value], m[: n.value]
 
     def range_search(self, lo, hi, cap=None, stream=None):
         """pi_range_search on int64 CUDA tensors of bounds: (offsets int64 [n + 1], keys,

@@ -609,25 +609,38 @@ uint64_t carve_scratch(uint8_t* base, uint64_t q, Scratch& s) {
     return off;
 }
 
-// Device address of the array, looked up once per device with that device current.
+// Per device: the array's device address, looked up once with that device current, and
+// the hand-over between calls on different indices. A batch's index-layer rebuild runs
+// on its index's own stream and reads its part of the array (new nodes, level changes,
+// change lists) after the caller's stream has moved on. A call on another index would
+// overwrite those parts from its first kernels, so its stream first waits for the last
+// call's rebuild (`rebuilt`, recorded after it). Calls on one index need no such wait:
+// only the sort runs before a batch waits for the previous rebuild, and the sort's
+// buffers are not among the parts the rebuild reads.
+struct NoAllocDevice {
+    uint8_t* ptr = nullptr;
+    cudaEvent_t rebuilt = nullptr;
+    const pi_index* last = nullptr;  // index of the last call on this device
+};
 std::mutex g_noalloc_mu;
-uint8_t* g_noalloc_ptr[64] = {};
+NoAllocDevice g_noalloc[64];
 
-cudaError_t noalloc_scratch_for(int device, uint8_t** out) {
+cudaError_t noalloc_scratch_for(int device, NoAllocDevice** out) {
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
+    NoAllocDevice& d = g_noalloc[device];
+    if (!d.ptr) {
         int prev = -1;
         cudaError_t e = cudaGetDevice(&prev);
         if (e != cudaSuccess) return e;
         if (prev != device && (e = cudaSetDevice(device)) != cudaSuccess) return e;
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e == cudaSuccess && !d.rebuilt) e = cudaEventCreateWithFlags(&d.rebuilt, cudaEventDisableTiming);
         if (prev != device) cudaSetDevice(prev);
         if (e != cudaSuccess) return e;
-        g_noalloc_ptr[device] = static_cast<uint8_t*>(p);
+        d.ptr = static_cast<uint8_t*>(p);
     }
-    *out = g_noalloc_ptr[device];
+    *out = &d;
     return cudaSuccess;
 }
 
@@ -1096,10 +1109,11 @@ int pi_execute_batch_noalloc(pi_index_t* x, const uint8_t* ops, const uint64_t* 
     if (n > PI_NOALLOC_MAX_BATCH) return PI_ERR_INVALID_ARG;  // beyond the static scratch
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
-    uint8_t* base = nullptr;
-    if ((e = noalloc_scratch_for(x->device, &base)) != cudaSuccess) return map_cuda(e);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocDevice* nd = nullptr;
+    if ((e = noalloc_scratch_for(x->device, &nd)) != cudaSuccess) return map_cuda(e);
     Scratch sc{};
-    if (carve_scratch(base, PI_NOALLOC_MAX_BATCH, sc) != kNoAllocBytes) return PI_ERR_CUDA;
+    if (carve_scratch(nd->ptr, PI_NOALLOC_MAX_BATCH, sc) != kNoAllocBytes) return PI_ERR_CUDA;
     refresh_known(x);
     if (int rc = sticky_error(x->known)) return rc;
     uint64_t size_ub = (uint64_t)x->known.size + x->pending_n + x->extra_n + n;
@@ -1109,9 +1123,16 @@ int pi_execute_batch_noalloc(pi_index_t* x, const uint8_t* ops, const uint64_t* 
         size_ub = (uint64_t)x->known.size + n;
         if (size_ub > x->st_cap) return PI_ERR_OOM;  // the storage layer would have to grow
     }
+    // the previous call was on another index: its rebuild may still read the array
+    if (nd->last && nd->last != x && (e = cudaStreamWaitEvent(s, nd->rebuilt, 0)) != cudaSuccess) return map_cuda(e);
     // An index layer that outgrew its capacity is not grown here: the rebuild then drops
     // its lowest levels and results stay exact.
-    return enqueue_batch(x, sc, ops, keys, values, n, results, size_ub, s);
+    const int rc = enqueue_batch(x, sc, ops, keys, values, n, results, size_ub, s);
+    if (rc == PI_OK) {
+        if ((e = cudaEventRecord(nd->rebuilt, x->rs)) != cudaSuccess) return map_cuda(e);
+        nd->last = x;
+    }
+    return rc;
 }
 
 void pi_destroy(pi_index_t* x) { destroy(x); }
@@ -1246,6 +1267,23 @@ int pi_export(pi_index_t* x, uint64_t* keys_out, uint64_t* vals_out, uint64_t ca
     if (e != cudaSuccess) return map_cuda(e);
     *n_out_host = c;
     return PI_OK;
+}
+
+int pi_export_storage(pi_index_t* x, uint64_t* keys_out, uint8_t* meta_out, uint64_t cap, uint64_t* n_out_host,
+                      pi_stream_t stream) {
+    if (!x || !n_out_host || (cap > 0 && !keys_out)) return PI_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = sync_known(x, s);
+    if (e != cudaSuccess) return map_cuda(e);
+    if (int rc = sticky_error(x->known)) return rc;
+    const DevMeta& m = x->known;
+    *n_out_host = m.size;
+    const uint64_t c = m.size < cap ? m.size : cap;
+    if (c) {
+        cudaMemcpyAsync(keys_out, x->st.keys[m.cur], c * 8, cudaMemcpyDeviceToDevice, s);
+        if (meta_out) cudaMemcpyAsync(meta_out, x->st.meta[m.cur], c, cudaMemcpyDeviceToDevice, s);
+    }
+    return map_cuda(cudaStreamSynchronize(s));
 }
 
 int pi_export_level(pi_index_t* x, int level, uint64_t* keys_out, uint32_t* down_out, uint64_t cap,

@@ -55,6 +55,17 @@ def assert_state_equal(idx, orc, ctx="", check_levels=True):
     assert info["live"] == len(ok)
     assert idx.size() == len(ok), f"{ctx}: pi_size {idx.size()} vs oracle {len(ok)}"
     assert idx.status() == 0, f"{ctx}: device error status {idx.status()}"
+    # The storage layer as stored: sorted, its live nodes exactly the oracle's keys, and
+    # as many delete-flagged nodes as pi_info reports.
+    st_k, st_m = idx.export_storage()
+    sk = st_k.cpu().numpy().view(np.uint64)
+    sm = st_m.cpu().numpy()
+    assert len(sk) == info["size"], f"{ctx}: storage export size"
+    assert np.all(sk[1:] > sk[:-1]), f"{ctx}: storage layer not strictly increasing"
+    live = (sm & 0x80) == 0
+    assert int((~live).sum()) == info["tombstones"], f"{ctx}: delete-flagged node count"
+    assert np.array_equal(sk[live], ok), f"{ctx}: live storage nodes differ from the oracle's keys"
+    del live, sm
     if not check_levels:
         return info
     top = orc.num_levels()
@@ -74,7 +85,9 @@ def assert_state_equal(idx, orc, ctx="", check_levels=True):
         assert np.array_equal(lk, exp), f"{ctx}: level {level} differs"
         if level > info["bottom_built"]:
             assert np.array_equal(prev_keys[ld], lk), f"{ctx}: down pointers of level {level} wrong"
-        elif info["tombstones"] == 0:
-            assert np.array_equal(ok[ld], lk), f"{ctx}: storage down pointers of level {level} wrong"
+        else:
+            # the lowest built level points at storage positions, delete-flagged nodes
+            # included (Section 3.1: each level a subsequence of the one below)
+            assert np.array_equal(sk[ld], lk), f"{ctx}: storage down pointers of level {level} wrong"
         prev_keys = exp
     return info

@@ -248,3 +248,44 @@ def test_single_owner_per_storage_node(orc_mod, kr):
     info2 = run_workload(orc_mod, w2, config={"test_flags": PI_TEST_OWNER_CHECK})
     w2b = w2.batches() if callable(w2.batches) else w2.batches
     assert 0 < info2["owner_checked_writes"] <= _distinct_writes(list(w2b)[:3])
+
+
+def _capped_workload(b: int, seed: int):
+    """Keys whose hash reaches the height cap (built by inverting splitmix64), among
+    random keys, then batches that insert more of them (new keys: a re-layout and a full
+    rebuild), delete some (delete-flagged nodes at the top levels: an incremental
+    rebuild), and revive them."""
+    from tests.hashkeys import hash_with_trailing_zeros, key_with_hash
+    mix = int(wl.splitmix64(np.uint64(seed)))
+    hmax = min(32, 64 // b)
+    tz_near = [64, 63, b * (hmax - 1), b * (hmax - 1) - 1, b * (hmax - 2)]
+    capped = []
+    for j, tz in enumerate(tz_near * 4):
+        k = key_with_hash(hash_with_trailing_zeros(tz, 1000 * j + b), mix)
+        if k != (1 << 64) - 1 and k not in capped:
+            capped.append(k)
+    base = [int(k) for k in wl.distinct_keys(b + 50, np.arange(3000))]
+    init = np.array(sorted(set(base + capped[: len(capped) // 2])), np.uint64)
+    later = np.array(capped[len(capped) // 2:], np.uint64)
+    early = np.array(capped[: len(capped) // 2], np.uint64)
+    z = np.zeros
+    b1 = wl.Batch(np.ones(len(later), np.uint8), later, np.arange(len(later), dtype=np.uint64) + 7)
+    b2 = wl.Batch(np.full(len(early), 2, np.uint8), early, z(len(early), np.uint64))
+    rev = early[:3]
+    b3 = wl.Batch(np.concatenate([np.ones(len(rev), np.uint8), z(len(capped), np.uint8)]),
+                  np.concatenate([rev, np.array(capped, np.uint64)]),
+                  np.concatenate([np.arange(len(rev), dtype=np.uint64) + 11, z(len(capped), np.uint64)]))
+    return wl.Workload(f"capped-b{b}", init, wl.splitmix64(init), 2.0 ** -b, seed, [b1, b2, b3]), hmax
+
+
+@pytest.mark.parametrize("b", [1, 2, 3, 4])
+@pytest.mark.parametrize("lowest", [0, 2])
+def test_height_cap_keys(orc_mod, b, lowest):
+    """Keys at the height cap (hash 0, whose trailing-zero count is 64, and hashes with
+    b * (Hmax - 1) or more trailing zeros) give an index of exactly Hmax levels; every
+    level, its down pointers and the results match the oracle through create, insert,
+    delete and revive batches."""
+    w, hmax = _capped_workload(b, 900 + b)
+    info = run_workload(orc_mod, w, config={"lowest_level": lowest} if lowest else None)
+    assert info["top_level"] == hmax
+    assert info["level_size"][hmax] >= 1

@@ -7,7 +7,8 @@ front -- so the library offers a variant whose per-batch scratch lives in a fixe
 device array. This file checks, through the C ABI, that two indices built from the same
 pairs and fed the same two batches in a row, one through each entry point, return
 identical results and end in identical states (the path is integer-exact, so the
-tolerance is zero). It also checks the size limit. It is named to run after every other
+tolerance is zero); the same for two indices whose calls alternate on one stream without
+synchronisation, with a batch of exactly the size limit. It also checks the limit. It is named to run after every other
 test, and it passes alone in a fresh process as well.
 """
 import numpy as np
@@ -58,6 +59,47 @@ def test_noalloc_matches_regular_entry_point_on_two_calls():
         assert i1["level_size"] == i2["level_size"] and i1["top_level"] == i2["top_level"]
     regular.close()
     static.close()
+
+
+def test_noalloc_alternating_indices_on_one_stream():
+    """Calls that alternate between two indices on one stream, with no synchronisation
+    between them, share the one scratch array while each index's background rebuild still
+    reads its part of it. Batch sizes include exactly PI_NOALLOC_MAX_BATCH. Results and
+    final states must equal those of the regular entry point on twin indices."""
+    import torch
+    from paper_1601_00159_gb300 import Index, PI_NOALLOC_MAX_BATCH
+    wa = wl.random_small(51, 40000, PI_NOALLOC_MAX_BATCH, 1 << 40, p=0.25, n_batches=3)
+    wb = wl.random_small(52, 20000, 30000, 1 << 20, p=0.5, n_batches=3)
+    cfg = {"storage_capacity": 400000}
+
+    def twins(w):
+        mk = lambda: Index(_dev(w.keys, torch.int64), _dev(w.vals, torch.int64), w.promote_p, w.hash_seed, cfg)
+        return mk(), mk()
+
+    (ra, sa), (rb, sb) = twins(wa), twins(wb)
+    assert len(wa.batches[0]) == PI_NOALLOC_MAX_BATCH
+    inputs = []
+    for j in range(3):
+        for w in (wa, wb):
+            bt = w.batches[j]
+            inputs.append((_dev(bt.ops, torch.uint8), _dev(bt.keys, torch.int64), _dev(bt.vals, torch.int64)))
+    torch.cuda.synchronize()
+    outs = []
+    for c, (ops, keys, vals) in enumerate(inputs):  # A1 B1 A2 B2 A3 B3, one stream, no sync
+        out = torch.full((ops.numel(), 2), -1, dtype=torch.int64, device="cuda")
+        (sa if c % 2 == 0 else sb).execute_noalloc(ops, keys, vals, out)
+        outs.append(out)
+    expected = [(ra if c % 2 == 0 else rb).execute(*inp) for c, inp in enumerate(inputs)]
+    torch.cuda.synchronize()
+    for c, (got, exp) in enumerate(zip(outs, expected)):
+        assert torch.equal(got, exp), f"call {c}: results differ"
+    for reg, sta in ((ra, sa), (rb, sb)):
+        assert reg.status() == 0 and sta.status() == 0
+        k1, v1 = reg.export()
+        k2, v2 = sta.export()
+        assert torch.equal(k1, k2) and torch.equal(v1, v2), "final states differ"
+        reg.close()
+        sta.close()
 
 
 def test_noalloc_rejects_batches_over_the_limit():
