@@ -36,9 +36,10 @@ from paper_1601_00159_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "Mqueries/s and % of HBM roofline on 1 GB300; p50/p99 latency in serving loop"
 UNIT = "Mqueries/s"
-# DRAM bytes per launch and per batch of the default skewed workload, from a full-size
-# ncu capture; the summary records a digest of the sources the capture was taken with.
-DRAM_PROFILE = os.path.join(ROOT, "profiles", "dram_skewed_2p27.md")
+# Per-kernel DRAM bytes and L2 hit rates of the batch path on the skewed workload, from
+# one ncu capture per kernel on a smaller index (see the summary beside it); the file
+# records a digest of the sources the captures were taken with.
+KERNEL_PROFILE = os.path.join(ROOT, "profiles", "kernels_skewed.json")
 
 WORKLOADS = {
     "skewed": dict(fn=wl.skewed, n=1 << 27, q=1 << 22,
@@ -92,23 +93,27 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def dram_profile(workload):
-    """(per-launch DRAM bytes by kernel, DRAM bytes per batch, note) from the committed
-    full-size ncu capture of this workload, or (None, None, why)."""
-    import re
+def kernel_profile(workload, keys, queries):
+    """(DRAM bytes per batch scaled to this run, per-kernel table, note) from the committed
+    per-kernel ncu captures of this workload, or (None, None, why). Kernels whose traffic
+    follows the index size (the rebuild's and the merge's) are scaled by the key count,
+    the others by the batch size; the capture's smaller index keeps more of itself in L2,
+    so the scaled sum is a lower bound of the traffic at this size."""
     try:
-        text = open(DRAM_PROFILE).read()
-    except OSError:
-        return None, None, "no ncu summary"
-    m = re.search(r"```json\n(.*?)\n```", text, re.S)
-    if not m:
-        return None, None, "summary lacks its data block"
-    d = json.loads(m.group(1))
+        d = json.load(open(KERNEL_PROFILE))
+    except (OSError, ValueError):
+        return None, None, "no per-kernel ncu capture"
     if d.get("workload") != workload:
-        return None, None, f"the capture is of workload {d.get('workload')}"
+        return None, None, f"the captures are of workload {d.get('workload')}"
     if d.get("digest") != source_digest():
-        return None, None, "kernel sources changed since the ncu capture"
-    return d["bytes_per_launch"], d["bytes_per_batch"], "ncu capture of this workload at full size"
+        return None, None, "kernel sources changed since the ncu captures"
+    ck, cq = d["capture"]["keys"], d["capture"]["batch"]
+    total = 0.0
+    for k in d["kernels"].values():
+        f = keys / ck if k["scales_with"] == "index" else queries / cq
+        total += k["dram_bytes"] * k["launches_per_batch"] * f
+    return total, d["kernels"], (f"per-kernel ncu captures at {ck} keys and batches of {cq}, scaled "
+                                 f"to this run (a lower bound: the smaller index is more L2-resident)")
 
 
 def measured_peaks():
@@ -123,20 +128,19 @@ def measured_peaks():
 # ---------------------------------------------------------------------------------
 # Algorithmic bytes (the method's own traffic, counted per batch from its inputs and
 # the index sizes; one 32-byte sector per random access).
-def algorithmic_bytes(q, q_ins, distinct, hits, writes, size_after, level_sizes, l2_bytes, sort_passes,
-                      lowest=2, inv_p=4):
+def algorithmic_bytes(q, q_ins, distinct, hits, writes, live_after, level_sizes, l2_bytes, p):
+    """The method's own bytes per batch, by the model of the paper's Section 5 as the
+    hot-path table states it (one 32-byte sector per random access): batch I/O; one key
+    and one down sector per distinct key and index level too large to stay in L2 (every
+    level from 2 up, as the paper lays the index out); one key sector per distinct key
+    and a value sector per hit in the storage layer, plus key, value and meta sectors per
+    written key; and the paper's full rebuild: a 9-byte scan of every node and 12 bytes
+    per index entry written, N' p / (1 - p) entries for N' live keys."""
     io = q * (1 + 8 + 16) + q_ins * 8
-    trav = 0
-    for l, n_l in enumerate(level_sizes):
-        if l >= lowest and n_l and 12 * n_l > l2_bytes / 2:
-            trav += distinct * 64
-    gap = inv_p ** (lowest - 1)  # storage nodes between two entries of the lowest built level
-    store = distinct * max(32, 8 * gap) + hits * 32 + writes * 96
-    n_index = sum(level_sizes[lowest:])
-    rebuild = 9 * size_after + 12 * n_index
-    sort = sort_passes * 24 * q + q * (9 + 12)
-    return dict(io=io, traversal=trav, storage=store, rebuild=rebuild, sort=sort,
-                total=io + trav + store + rebuild)
+    trav = sum(distinct * 64 for l, n_l in enumerate(level_sizes) if l >= 2 and 12 * n_l > l2_bytes / 2)
+    store = distinct * 32 + hits * 32 + writes * 96
+    rebuild = 9 * live_after + 12 * live_after * p / (1 - p)
+    return dict(io=io, traversal=trav, storage=store, rebuild=rebuild, total=io + trav + store + rebuild)
 
 
 class ClockSampler:
@@ -844,6 +848,18 @@ def run_ours(args, ws, rank, local):
     stage_ms, nb = idx.profile_read()  # stage times exclude the wait for the previous rebuild
     idx.profile(False)
     info1 = idx.info()
+    kernel_ms = None
+    if args.kernel_times:
+        # per-kernel times on extra batches after the timed region (events around every
+        # launch serialise the launches, so these batches are not part of the value)
+        idx.profile(2)
+        for s in range(args.kernel_times):
+            o, k, v = dbatches[(args.warmup + args.steps + s) % len(dbatches)]
+            idx.execute(o, k, v, results)
+        kt = idx.profile_kernels()
+        idx.profile(False)
+        kernel_ms = {name: {"launches_per_batch": c / args.kernel_times, "us_per_batch": 1e3 * ms / args.kernel_times}
+                     for name, (c, ms) in kt.items()}
     assert idx.status() == 0, "device error status after the timed region"
     ms_total = reduce_max(ms_total, ws)
     ms_step = ms_total / args.steps
@@ -891,34 +907,40 @@ def run_ours(args, ws, rank, local):
     e2e_ms = reduce_max(e0.elapsed_time(e1), ws)
     e2e_value = ws * q * e2e_steps / (e2e_ms * 1e-3) / 1e6
 
-    # Roofline of the largest launch of a batch, the storage locate (k_locate; the ncu
-    # launch list in profiles/ gives the shares): its duration is the CUDA-event interval
-    # around its launch on the batch stream, averaged over the timed batches. Its
-    # algorithmic bytes per distinct key of the batch: the storage keys of one gap
-    # between two entries of the lowest built level (8 B x (1/P)^(Lb-1)), one 32-byte
-    # sector each for the node's meta byte and value, and the 25 B it streams (query key
-    # and start position in; node position, state and prior value out).
+    # The roofline of the whole batch (every kernel of one pi_execute_batch): the method's
+    # bytes by the model of the paper's Section 5 (algorithmic_bytes), or the DRAM bytes
+    # the kernels were measured to move by ncu if fewer, over the step time. Distinct,
+    # written and inserted keys are counted exactly from the timed batches; every key of
+    # the skewed workload is drawn from the key set, so each distinct key counts as a hit
+    # (the delete-flagged few excepted, which the model then overstates by a value sector).
     hbm, peak_kind = measured_peaks()
     per_stage = {k: v / max(nb, 1) for k, v in stage_ms.items()}
-    used = host_batches[: min(len(host_batches), args.steps)]
+    used = [host_batches[(args.warmup + s) % len(host_batches)] for s in range(min(args.steps, len(host_batches)))]
     distinct = float(np.mean([len(np.unique(b.keys)) for b in used]))
+    writes = float(np.mean([len(np.unique(b.keys[b.ops != wl.OP_SEARCH])) for b in used]))
     ins = float(np.mean([int((b.ops == wl.OP_INSERT).sum()) for b in used]))
     sizes = info1["level_size"]
-    size_after = info1["size"]
-    writes = distinct  # upper bound: every distinct key may be written once
     lowest = info1["bottom_built"]
-    inv_p = int(round(1 / w.promote_p))
-    ab = algorithmic_bytes(q, ins, distinct, distinct, writes, size_after, sizes, l2_bytes, 8, lowest, inv_p)
-    gap = inv_p ** (lowest - 1)
-    loc_per_key = 8 * gap + 32 + 32 + 25
+    ab = algorithmic_bytes(q, ins, distinct, distinct, writes, info1["live"], sizes, l2_bytes, w.promote_p)
+    default_run = not (args.keys_log2 or args.batch_log2) and args.rebuild == "each"
+    traffic, kprof, traffic_note = (kernel_profile(args.workload, len(w.keys), q) if default_run else
+                                    (None, None, "no ncu capture of this configuration"))
+    step_s = ms_step * 1e-3
+    batch_low = min(ab["total"], traffic) if traffic is not None else ab["total"]
+    # The storage locate (k_locate), the largest launch: it searches the lowest built index
+    # level and then the storage layer. By the same model, per distinct key: a key and a
+    # down sector on every level from 2 up to the lowest built one that is not
+    # L2-resident (the paper's layout descends level 2 too; here the storage search
+    # crosses that gap), a storage key sector and a value sector; plus the 25 B it streams
+    # (query key and start position in; node position, state and prior value out).
+    trav_levels = [l for l in range(2, lowest + 1) if sizes[l] and 12 * sizes[l] > l2_bytes / 2]
+    loc_per_key = 64 * len(trav_levels) + 32 + 32 + 25
     loc_bytes = distinct * loc_per_key
     loc_ms = per_stage["locate"]
-    achieved = loc_bytes / (loc_ms * 1e-3) / 1e9
-    default_run = not (args.keys_log2 or args.batch_log2) and args.rebuild == "each"
-    per_launch, per_batch, traffic_note = (dram_profile(args.workload) if default_run else
-                                           (None, None, "no ncu capture of this configuration"))
-    loc_traffic = per_launch.get("k_locate") if per_launch else None
-    low = min(loc_bytes, loc_traffic) if loc_traffic is not None else loc_bytes
+    loc_traffic = None
+    if kprof and "k_locate" in kprof:
+        kl = kprof["k_locate"]
+        loc_traffic = kl["dram_bytes"] * q / json.load(open(KERNEL_PROFILE))["capture"]["batch"]
     # The rebuild's writer: the incremental one reads and writes each built entry (8 B key
     # + 4 B down) once; the full one scans the storage layer's keys and meta and writes
     # every built entry.
@@ -930,15 +952,8 @@ def run_ours(args, ws, rank, local):
         wkernel, wbytes = "k_relevel_write", 24 * entries
         wmodel = "12 B read + 12 B written per built index entry (incremental rebuild)"
     else:
-        wkernel, wbytes = "k_rebuild_write", ab["rebuild"]
+        wkernel, wbytes = "k_rebuild_write", 9 * info1["size"] + 12 * entries
         wmodel = "9 B per storage node (key + meta scan) + 12 B per built index entry"
-    w_traffic = per_launch.get(wkernel) if per_launch else None
-    # The whole batch against the same peak: the method's bytes (the paper's model with a
-    # full rebuild), the bytes of the path as built (the incremental rebuild in place of
-    # the full one when every timed rebuild was incremental), and DRAM bytes by ncu.
-    built_bytes = ab["total"] - ab["rebuild"] + (wbytes if wkernel == "k_relevel_write" else ab["rebuild"])
-    step_s = ms_step * 1e-3
-    batch_low = min(ab["total"], per_batch) if per_batch is not None else ab["total"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -951,28 +966,40 @@ def run_ours(args, ws, rank, local):
                    "rebuild_policy": args.rebuild, "keys": len(w.keys), "batch": q,
                    "distinct_batches_cycled": len(dbatches), "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2_flush": "none: storage layer and cycled batch inputs exceed L2"},
-        "roofline": {"bound": "hbm", "kernel": "k_locate", "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind, "traffic": loc_traffic,
-                     "traffic_note": traffic_note,
-                     "frac_min_of_model_and_traffic": low / (loc_ms * 1e-3) / 1e9 / hbm,
-                     "launches_per_step": 1, "ms_per_launch": loc_ms, "share_of_step": loc_ms / ms_step,
-                     "algorithmic_bytes_per_launch": loc_bytes,
-                     "bytes_model": f"{loc_per_key} B per distinct key: 8 B x {gap} storage keys of one "
-                                    "lowest-level gap + meta and value sectors (32 B each) + 25 B streamed",
-                     "distinct_keys_per_batch": distinct, "lowest_built_level": lowest},
+        "roofline": {"bound": "hbm", "kernel": "whole batch: every kernel of one pi_execute_batch",
+                     "achieved": batch_low / step_s / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": batch_low / step_s / 1e9 / hbm, "peak_source": peak_kind,
+                     "traffic": traffic, "traffic_note": traffic_note,
+                     "algorithmic_bytes_per_launch": ab["total"], "bytes": "the smaller of the model and the traffic",
+                     "frac_model": ab["total"] / step_s / 1e9 / hbm,
+                     "frac_traffic": traffic / step_s / 1e9 / hbm if traffic is not None else None,
+                     "frac_of_nominal_8tbs": batch_low / step_s / 1e9 / 8000.0,
+                     "launches_per_step": (info1["kernel_launches"] - info0["kernel_launches"]) / args.steps,
+                     "ms_per_launch": ms_step,
+                     "model_parts": {k: v for k, v in ab.items() if k != "total"},
+                     "bytes_model": "per batch: Q*25 + Q_ins*8 I/O; 64 B per distinct key and index level "
+                                    "(from 2) too large for L2; 32 B key sector per distinct key, 32 B value "
+                                    "sector per hit, 96 B per written key; full rebuild 9 N' + 12 N' p/(1-p)",
+                     "distinct_keys_per_batch": distinct, "written_keys_per_batch": writes,
+                     "k_locate": {"ms_per_launch": loc_ms, "share_of_step": loc_ms / ms_step,
+                                  "algorithmic_bytes_per_launch": loc_bytes,
+                                  "achieved": loc_bytes / (loc_ms * 1e-3) / 1e9,
+                                  "frac": loc_bytes / (loc_ms * 1e-3) / 1e9 / hbm,
+                                  "traffic": loc_traffic,
+                                  "bytes_model": f"{loc_per_key} B per distinct key: key and down sectors "
+                                                 f"(64 B) on levels {trav_levels}, storage key and value "
+                                                 "sectors (32 B each), 25 B streamed",
+                                  "lowest_built_level": lowest}},
         "rebuild_writer": {"kernel": wkernel, "ms_per_launch": writer_ms,
                            "algorithmic_bytes_per_launch": wbytes, "bytes_model": wmodel,
                            "achieved_gbs": wbytes / (writer_ms * 1e-3) / 1e9 if writer_ms else None,
-                           "traffic": w_traffic, "incremental_rebuilds": inc_region, "rebuilds": rebuilds_region,
+                           "traffic": (kprof[wkernel]["dram_bytes"] * len(w.keys) /
+                                       json.load(open(KERNEL_PROFILE))["capture"]["keys"])
+                           if kprof and wkernel in kprof else None,
+                           "incremental_rebuilds": inc_region, "rebuilds": rebuilds_region,
                            "note": "runs on the rebuild stream, overlapping the next batch's sort"},
-        "batch_roofline": {"algorithmic_bytes": ab["total"], "built_path_bytes": built_bytes,
-                           "traffic": per_batch, "frac_model": ab["total"] / step_s / 1e9 / hbm,
-                           "frac_built_path": built_bytes / step_s / 1e9 / hbm,
-                           "frac": batch_low / step_s / 1e9 / hbm,
-                           "note": "frac divides the smaller of the method's model bytes and the ncu DRAM "
-                                   "bytes; frac_built_path is the incremental rebuild's own byte model, "
-                                   "for reference"},
         "stages_ms": per_stage,
+        "kernel_us": kernel_ms,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": q * 17, "d2h_bytes_per_step": q * 16,
                 "steps": e2e_steps, "index": "fresh, same batch sequence" if fresh else "the timed index"},
         "gpu_launches": info1["kernel_launches"] - info0["kernel_launches"],
@@ -1005,6 +1032,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--keys-log2", type=int, default=0, help="override the index size (profiling runs)")
     ap.add_argument("--batch-log2", type=int, default=0, help="override the batch size (profiling runs)")
+    ap.add_argument("--kernel-times", type=int, default=0,
+                    help="after the timed region, time every kernel of this many more batches")
     ap.add_argument("--rebuild", default="each", choices=["each", "deferred"],
                     help="index rebuild after every batch, or deferred until the updates since the last "
                          "rebuild exceed 15%% of the storage layer (the paper's setting)")

@@ -15,8 +15,10 @@
  * the stream passed in. Keys and values are unsigned 64-bit integers compared as
  * unsigned; the key 2^64-1 is reserved (it is the sentinel that ends every level).
  *
- * Threading: a pi_index_t must not be used from two host threads, or from two
- * streams, at the same time; the caller serialises its calls.
+ * Threading: a pi_index_t must not be used from two host threads at the same time. Its
+ * calls may name different streams: every call that touches the index is ordered, on
+ * the device, after the index's previous operation (a batch, a range search or a
+ * batching-form call), whichever stream that ran on.
  */
 #ifndef PI_H_
 #define PI_H_
@@ -141,9 +143,14 @@ int pi_execute_batch(pi_index_t* idx, const uint8_t* ops, const uint64_t* keys,
 
 /*
  * pi_execute_batch_host -- the same, with HOST arrays. The library copies the inputs
- * to device staging it owns, runs pi_execute_batch and copies the results back, all
- * on `stream`; results_host is complete when `stream` completes. Pinned host memory
- * makes the copies asynchronous; pageable memory works but serialises them.
+ * to device staging it owns, runs the batch and copies the results back, each step on a
+ * stream of its own, with two staging slots: the copies of one call overlap the kernels
+ * of the calls before and after it. results_host is complete when `stream` completes
+ * (the caller's stream waits for the copy out). The batch is ordered after the index's
+ * previous operation; the copy in does not wait for other earlier work on `stream`, so
+ * the host arrays must hold the batch when the call is made and stay unchanged (and
+ * allocated) until `stream` completes. Pinned host memory makes the copies
+ * asynchronous; pageable memory works but serialises them.
  */
 int pi_execute_batch_host(pi_index_t* idx, const uint8_t* ops_host, const uint64_t* keys_host,
                           const uint64_t* values_host, uint64_t n, pi_result_t* results_host,
@@ -156,7 +163,7 @@ int pi_execute_batch_host(pi_index_t* idx, const uint8_t* ops_host, const uint64
  * allocator (cudaMalloc/cudaFree can synchronise the device, which a latency-bound
  * serving loop cannot afford) and code running where a memory budget is fixed up front.
  * The per-batch scratch of up to PI_NOALLOC_MAX_BATCH queries comes from one
- * file-scope device array of a fixed size (10,911,488 bytes, about 10.9 MB), held by
+ * file-scope device array of a fixed size (about 10.9 MB), held by
  * every GPU that loads the library until the process exits; this call allocates nothing.
  *   - n > PI_NOALLOC_MAX_BATCH returns PI_ERR_INVALID_ARG.
  *   - A batch that could need the storage layer to grow returns PI_ERR_OOM with the
@@ -279,10 +286,17 @@ int pi_export_storage(pi_index_t* idx, uint64_t* keys_out, uint8_t* meta_out, ui
  * pi_profile(idx, 1) starts (and clears) the accumulation; pi_profile(idx, 0) stops it.
  * pi_profile_read synchronises `stream` and writes the summed milliseconds per stage to
  * stage_ms_host[PI_NUM_STAGES] and the number of batches they cover to *batches_host.
+ * pi_profile(idx, 2) also times every kernel launch of the batch entry points between
+ * two events on its own stream (which serialises the launches it brackets: use it to
+ * compare kernels, not to measure throughput). pi_profile_kernels synchronises `stream`
+ * and writes one text line per kernel, "<function name>\t<launches>\t<summed ms>\n",
+ * NUL-terminated, to buf[cap] (truncated to fit); it returns the length the whole table
+ * needs including the NUL, or PI_ERR_INVALID_ARG when level 2 is not on.
  */
 #define PI_NUM_STAGES 8
 int pi_profile(pi_index_t* idx, int enable);
 int pi_profile_read(pi_index_t* idx, double* stage_ms_host, uint64_t* batches_host, pi_stream_t stream);
+int pi_profile_kernels(pi_index_t* idx, char* buf, uint64_t cap, pi_stream_t stream);
 
 /*
  * pi_range_search -- range queries (Section 3.2.5) on the index as it stands after the

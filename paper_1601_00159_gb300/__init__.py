@@ -22,7 +22,7 @@ PI_MAX_KEYS = (1 << 30) - 2
 EXPORTED = ["pi_create", "pi_create_ex", "pi_execute_batch", "pi_execute_batch_host", "pi_destroy",
             "pi_last_error", "pi_status", "pi_info", "pi_size", "pi_test_fail_allocations",
             "pi_selftest_wait", "pi_num_levels", "pi_export", "pi_export_level", "pi_export_storage", "pi_profile",
-            "pi_profile_read", "pi_execute_batch_noalloc", "pi_flush",
+            "pi_profile_read", "pi_profile_kernels", "pi_execute_batch_noalloc", "pi_flush",
             "pi_range_search", "pi_multi_create", "pi_multi_execute", "pi_multi_destroy", "pi_multi_kernels_per_call",
             "pi_server_create", "pi_server_submit", "pi_server_wait", "pi_server_stats", "pi_server_replay",
             "pi_server_destroy"]
@@ -145,6 +145,8 @@ def load_library(path: str = LIB_PATH):
     lib.pi_profile.argtypes = [vp, i32]
     lib.pi_profile_read.restype = i32
     lib.pi_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), vp]
+    lib.pi_profile_kernels.restype = i32
+    lib.pi_profile_kernels.argtypes = [vp, ctypes.c_char_p, u64, vp]
     lib.pi_range_search.restype = i32
     lib.pi_range_search.argtypes = [vp, vp, vp, u64, vp, vp, vp, u64, vp]
     lib.pi_multi_create.restype = vp
@@ -200,6 +202,22 @@ def selftest_wait(stream=None):
     w = ctypes.c_uint32(0)
     rc = load_library().pi_selftest_wait(ctypes.byref(w), _stream_handle(stream))
     return rc, w.value
+
+
+def _kernel_identifier(mangled: str) -> str:
+    """The kernel's own identifier (k_...) in an Itanium-mangled name: a decimal length
+    followed by that many characters; the digits before it may run into other digits."""
+    import re
+    for m in re.finditer(r"(\d+)(k_[a-z0-9_]+)", mangled):
+        digits, rest = m.group(1), mangled[m.start(2):]
+        for j in range(len(digits)):
+            n = int(digits[j:])
+            if 0 < n <= len(rest) and re.fullmatch(r"k_[a-z0-9_]+", rest[:n]) and \
+                    (n == len(rest) or not re.match(r"[a-z0-9_]", rest[n])):
+                if rest[n:n + 1] == "I":  # a template instance: keep its arguments apart
+                    return rest[:n] + "<" + rest[n + 1:].split("EE")[0] + ">"
+                return rest[:n]
+    return mangled
 
 
 class Index:
@@ -349,8 +367,9 @@ class Index:
         """pi_flush: make the stream wait for the index's background work."""
         _chk(self.lib.pi_flush(self._h, _stream_handle(stream)), "pi_flush")
 
-    def profile(self, enable: bool):
-        _chk(self.lib.pi_profile(self._h, 1 if enable else 0), "pi_profile")
+    def profile(self, enable):
+        """pi_profile: False/0 off, True/1 stage times, 2 stage and per-kernel times."""
+        _chk(self.lib.pi_profile(self._h, int(enable)), "pi_profile")
 
     def profile_read(self, stream=None):
         """(dict stage -> summed ms, batches covered)."""
@@ -358,6 +377,19 @@ class Index:
         nb = ctypes.c_uint64(0)
         _chk(self.lib.pi_profile_read(self._h, ms, ctypes.byref(nb), _stream_handle(stream)), "pi_profile_read")
         return dict(zip(STAGES, list(ms))), nb.value
+
+    def profile_kernels(self, stream=None):
+        """{kernel name: (launches, summed ms)} recorded since pi_profile(idx, 2)."""
+        import re
+        need = self.lib.pi_profile_kernels(self._h, None, 0, _stream_handle(stream))
+        _chk(min(need, 0), "pi_profile_kernels")
+        buf = ctypes.create_string_buffer(need)
+        self.lib.pi_profile_kernels(self._h, buf, need, _stream_handle(stream))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, cnt, ms = line.split("\t")
+            out[_kernel_identifier(name)] = (int(cnt), float(ms))
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

@@ -41,7 +41,7 @@ __device__ __forceinline__ void store_result(pi_result_t* res, uint32_t seq, uin
     *reinterpret_cast<uint4*>(res + seq) = w;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_apply(ApplyArgs a) {
     pdl_wait();
     pdl_trigger();
     __shared__ uint32_t s_tmp[33];
@@ -82,6 +82,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
     }
     const uint64_t kprev = (base > 0 && base - 1 < qv) ? a.sk[base - 1] : kMaxKey;
     const uint64_t knext = (base + kItems < qv) ? a.sk[base + kItems] : kMaxKey;
+    // the descent's prefixes for this tile and this warp's sub-tile, loaded with the batch
+    // (a block barrier below would keep them from being hoisted)
+    const uint32_t tpref = a.tile_pref[tile];
+    const uint32_t spref = a.sub_pref[base / kSubTile];
     uint32_t agg = 0;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
         agg = max(agg, e[k]);
     }
     const uint32_t texcl = block_excl_max<kThreads>(agg, s_tmp, nullptr);
-    uint32_t M = max(a.tile_pref[tile], texcl);
+    uint32_t M = max(tpref, texcl);
     // index of each query's local run head among its 256-query sub-tile's local heads
     // (a warp's 8 x 32 queries are exactly one descent sub-tile)
     uint32_t lh = 0, nh = 0;
@@ -116,44 +120,58 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(ApplyArgs a) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        hidx = incl - nh + a.sub_pref[base / kSubTile];  // dense index of the next head
+        hidx = incl - nh + spref;  // dense index of the next head
     }
     uint32_t new_here = 0, new_mask = 0, chg_here = 0, chg_mask = 0;
+    // Per query: its run head's result index, and the gathers of its prior state, all
+    // issued before any store so that their latencies overlap: the run head's state, or,
+    // when an earlier query of its run wrote (the marker names it), that query's payload.
+    uint32_t fromw = 0, insw = 0, flx = 0;  // bit k: from an earlier write; that write inserts; flags
+    uint64_t val[kItems];
+    uint32_t pj[kItems];
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
-        const uint32_t i = base + k;
         const uint32_t mex = M;
         const uint32_t minc = max(M, e[k]);
         M = minc;
-        e[k] = minc;  // keep the inclusive value for the new-node pass
-        const uint32_t dj = hidx + ((lh >> k) & 1u) - 1u;  // this query's run head's result
+        e[k] = minc;  // keep the inclusive value for the owners and the new-node pass
+        dres[k] = hidx + ((lh >> k) & 1u) - 1u;  // this query's run head's result
         hidx += (lh >> k) & 1u;
-        dres[k] = dj;
+        const uint64_t prev = k ? key[k - 1] : kprev;
+        const bool q = base + k < qv;
+        const bool fw = q && (base + k != 0 && key[k] == prev) && (mex & 1u);
+        fromw |= (fw ? 1u : 0u) << k;
+        flx |= (q ? (uint32_t)a.flags[dres[k]] : 0u) << (2 * k);
+        val[k] = q ? a.val0[dres[k]] : 0ull;
+        pj[k] = fw ? a.sp[(mex - 3u) >> 1] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        if (!((fromw >> k) & 1u)) {
+            if (!((flx >> (2 * k + 1)) & 1u)) val[k] = 0ull;  // the run head's key is not live
+            continue;
+        }
+        const bool ins = (pj[k] >> 30) == 1u;
+        insw |= (ins ? 1u : 0u) << k;
+        val[k] = ins ? a.uvals[pj[k] & kSeqMask] : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint32_t i = base + k;
         if (i >= n) continue;
         const uint32_t seq = pay[k] & kSeqMask;
         if (i >= qv) {
             store_result(a.results, seq, 0ull, PI_R_INVALID);
             continue;
         }
-        const uint64_t prev = k ? key[k - 1] : kprev;
-        const bool head = (i == 0 || key[k] != prev);
-        const uint8_t fl = a.flags[dj];
-        const bool exists = fl & 1u, live0 = (fl & 2u) != 0;
-        bool pl;
-        uint64_t pv;
-        if (!head && (mex & 1u)) {
-            const uint32_t j = (mex - 3u) >> 1;
-            const uint32_t pj = a.sp[j];
-            pl = (pj >> 30) == 1u;
-            pv = pl ? a.uvals[pj & kSeqMask] : 0ull;
-        } else {
-            pl = live0;
-            pv = live0 ? a.val0[dj] : 0ull;
-        }
-        store_result(a.results, seq, pv, pl ? PI_R_PRESENT : PI_R_ABSENT);
+        const uint32_t dj = dres[k];
+        const bool exists = (flx >> (2 * k)) & 1u, live0 = (flx >> (2 * k + 1)) & 1u;
+        const bool pl = ((fromw >> k) & 1u) ? ((insw >> k) & 1u) != 0 : live0;
+        store_result(a.results, seq, val[k], pl ? PI_R_PRESENT : PI_R_ABSENT);
 
         const uint64_t next = (k + 1 < kItems) ? key[k + 1] : knext;
         const bool last = next != key[k];
+        const uint32_t minc = e[k];
         if (!last || !(minc & 1u)) continue;  // not the owner, or the run never writes
         const uint32_t jw = (minc - 3u) >> 1;
         const uint32_t pw = (jw == i) ? pay[k] : a.sp[jw];

@@ -16,7 +16,7 @@ constexpr uint32_t kSmemTopMax = 2048;  // index entries staged in shared memory
 constexpr uint32_t kPad = 64;           // readable entries past every array's end
 constexpr uint32_t kSortTile = 2048;    // elements per radix-sort tile
 constexpr uint32_t kScanGroup = 64;     // radix-sort tiles per group of the count kernel's scan
-constexpr uint32_t kCtrDistinct = 14;   // BatchMeta::tile_ctr slot: the distinct-key kernel's arrivals
+constexpr uint32_t kCtrDistinct = 14;   // BatchMeta::tile_ctr slot: the descent prologue's tile counter
 constexpr uint32_t kApplyTile = 2048;   // sorted queries per apply tile
 constexpr uint32_t kSubTile = 256;      // sorted queries per descent warp step (one apply warp)
 
@@ -328,21 +328,31 @@ __device__ __forceinline__ uint32_t lookback_sum_win(uint64_t* desc, size_t stri
     return excl;
 }
 
+// First half of a look-back, for callers that publish their aggregate early and do
+// other work before waiting on their predecessors: tile 0 publishes its inclusive
+// prefix at once, every other tile its aggregate. One thread calls it.
+__device__ __forceinline__ void lookback_publish(uint64_t* desc, uint32_t tile, uint32_t epoch, uint32_t agg) {
+    const uint64_t tag = (uint64_t)epoch << 32;
+    st_relaxed(desc + tile, tag | (tile == 0 ? kFlagPrefix : kFlagAgg) | (agg & kValMask));
+}
+
 // Warp-wide variant, called by all 32 lanes of one warp: each round reads the
 // descriptors of 32 predecessors at once (lane i reads tile base - 1 - i), so a run of
 // predecessors that have published only their aggregates is crossed 32 tiles per
 // memory round trip instead of one. Returns the exclusive prefix in every lane.
+// With `published`, lookback_publish has already stored this tile's aggregate; `agg` must
+// still be that aggregate, since the inclusive prefix published at the end adds it.
 template <bool kMax>
 __device__ uint32_t lookback_warp(uint64_t* desc, uint32_t tile, uint32_t epoch, uint32_t agg, uint32_t* err,
-                                  bool* ok) {
+                                  bool* ok, bool published = false) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t tag = (uint64_t)epoch << 32;
     *ok = true;
     if (tile == 0) {
-        if (lane == 0) st_relaxed(desc, tag | kFlagPrefix | (agg & kValMask));
+        if (lane == 0 && !published) st_relaxed(desc, tag | kFlagPrefix | (agg & kValMask));
         return 0;
     }
-    if (lane == 0) st_relaxed(desc + tile, tag | kFlagAgg | (agg & kValMask));
+    if (lane == 0 && !published) st_relaxed(desc + tile, tag | kFlagAgg | (agg & kValMask));
     uint32_t excl = 0;
     int64_t base = (int64_t)tile;
     uint32_t spins = 0;
@@ -378,6 +388,73 @@ __device__ uint32_t lookback_warp(uint64_t* desc, uint32_t tile, uint32_t epoch,
         excl = lb_op<kMax>(excl, v);
         if (stop < 32u) break;
         base -= 32;
+    }
+    if (lane == 0) st_relaxed(desc + tile, tag | kFlagPrefix | (lb_op<kMax>(excl, agg) & kValMask));
+    return excl;
+}
+
+// Wider warp-wide variant: each lane reads kPer predecessors per round (lane i reads tile
+// base - 1 - i - 32 k), so 32 kPer tiles are crossed per memory round trip. Kernels whose
+// first wave holds hundreds of tiles that all publish their aggregates at once use it:
+// the last tile of such a wave finds the nearest inclusive prefix in a few rounds.
+template <bool kMax, int kPer>
+__device__ uint32_t lookback_warp_wide(uint64_t* desc, uint32_t tile, uint32_t epoch, uint32_t agg, uint32_t* err,
+                                       bool* ok) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t tag = (uint64_t)epoch << 32;
+    *ok = true;
+    if (tile == 0) {
+        if (lane == 0) st_relaxed(desc, tag | kFlagPrefix | (agg & kValMask));
+        return 0;
+    }
+    if (lane == 0) st_relaxed(desc + tile, tag | kFlagAgg | (agg & kValMask));
+    uint32_t excl = 0;
+    int64_t base = (int64_t)tile;
+    uint32_t spins = 0;
+    for (;;) {
+        uint64_t d[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t t = base - 1 - (int64_t)lane - 32 * k;
+            d[k] = (t >= 0) ? ld_relaxed(desc + t) : (tag | kFlagPrefix);  // before tile 0: prefix 0
+        }
+        // distance (lane + 32 k) of the nearest predecessor that published its prefix
+        uint32_t mine = 0xffffffffu;
+#pragma unroll
+        for (int k = kPer - 1; k >= 0; --k) {
+            const bool valid = (uint32_t)(d[k] >> 32) == epoch && (d[k] & (3ull << 30)) != 0;
+            if (valid && (d[k] & (3ull << 30)) == kFlagPrefix) mine = lane + 32u * (uint32_t)k;
+        }
+        const uint32_t stop = __reduce_min_sync(0xffffffffu, mine);
+        const uint32_t lim = (stop == 0xffffffffu) ? 32u * kPer - 1u : stop;
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const bool valid = (uint32_t)(d[k] >> 32) == epoch && (d[k] & (3ull << 30)) != 0;
+            if (lane + 32u * (uint32_t)k <= lim && !valid) bad = true;
+        }
+        if (__any_sync(0xffffffffu, bad)) {
+            ++spins;
+            if (spins > kSpinLimit) {
+                if (lane == 0) atomicOr(err, kErrTimeout);
+                *ok = false;
+                return 0;
+            }
+            if ((spins & 1023u) == 0 && *(volatile uint32_t*)err) {
+                *ok = false;
+                return 0;
+            }
+            if (spins > 32) __nanosleep(100);
+            continue;
+        }
+        uint32_t v = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k)
+            if (lane + 32u * (uint32_t)k <= lim) v = lb_op<kMax>(v, (uint32_t)(d[k] & kValMask));
+        v = kMax ? __reduce_max_sync(0xffffffffu, v) : __reduce_add_sync(0xffffffffu, v);
+        excl = lb_op<kMax>(excl, v);
+        if (stop != 0xffffffffu) break;
+        base -= 32 * kPer;
     }
     if (lane == 0) st_relaxed(desc + tile, tag | kFlagPrefix | (lb_op<kMax>(excl, agg) & kValMask));
     return excl;
@@ -555,14 +632,12 @@ struct DescendArgs {
     const uint32_t* sp;  // sorted payload (op << 30 | arrival index)
     uint32_t* tile_pref; // per-apply-tile exclusive max prefix of the run markers e_i
     uint32_t* sub_pref;  // dense index of each sub-tile's first distinct key
-    uint32_t* sub_cnt;   // distinct keys per sub-tile
-    uint32_t* tile_heads;  // distinct keys per apply tile
-    uint32_t* tile_emax;   // largest ownership marker per apply tile
-    uint32_t* tile_base;   // dense index of each apply tile's first distinct key
+    uint64_t* desc;      // look-back descriptors: 2 words per apply tile
     uint64_t* dq;        // dense distinct keys
     uint32_t* dlo;       // their current start position on the level being searched
-    int top_launched;    // highest index level given its own launch (see launch_descend)
-    int bottom_launched; // lowest level that can be built (levels below it get no launch)
+    int top_launched;    // highest index level given its own launch (see launch_descend);
+                         // at least bottom_launched
+    int bottom_launched; // lowest level that can be built: searched by the storage locate
     const DevMeta* m;
     BatchMeta* bm;
     const uint64_t* lkeys;   // index-layer buffer 0 (DevMeta::lcur picks the one in use)
@@ -577,7 +652,9 @@ struct DescendArgs {
     uint32_t* err;
 };
 // before_locate (may be null) is recorded on s just before the storage-locate kernel.
-cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms, cudaEvent_t before_locate = nullptr);
+// The look-back of the first kernel takes ++epoch; a.desc needs 2 words per apply tile.
+cudaError_t launch_descend(const DescendArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms,
+                           cudaEvent_t before_locate = nullptr);
 
 struct ApplyArgs {
     const uint64_t* sk;
@@ -720,11 +797,9 @@ void set_last_error(int code);
 // batch entry points fold the difference into the index's own count.
 extern thread_local uint64_t g_launches;
 
-// kernel<<<grid, block, smem, s>>>(args...) with programmatic dependent launch allowed
-// (the kernel must begin with pdl_wait()).
 template <typename... KP, typename... A>
-inline cudaError_t launch_dep(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              A... args) {
+inline cudaError_t launch_dep_raw(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                  A... args) {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -736,6 +811,25 @@ inline cudaError_t launch_dep(void (*kernel)(KP...), dim3 grid, dim3 block, size
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KP>(args)...);
+}
+
+// Per-kernel timing (pi_profile level 2): while a recorder is installed on the host
+// thread, launch_dep brackets every launch with two events on the launch's stream.
+struct KernelTimer {
+    virtual void before(cudaStream_t s) = 0;
+    virtual void after(const void* func, cudaStream_t s) = 0;
+};
+extern thread_local KernelTimer* g_ktimer;
+
+// kernel<<<grid, block, smem, s>>>(args...) with programmatic dependent launch allowed
+// (the kernel must begin with pdl_wait()).
+template <typename... KP, typename... A>
+inline cudaError_t launch_dep(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              A... args) {
+    if (g_ktimer) g_ktimer->before(s);
+    const cudaError_t e = launch_dep_raw(kernel, grid, block, smem, s, args...);
+    if (g_ktimer) g_ktimer->after(reinterpret_cast<const void*>(kernel), s);
+    return e;
 }
 
 cudaError_t launch_rebuild(const RebuildArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms);

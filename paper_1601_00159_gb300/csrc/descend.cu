@@ -11,14 +11,13 @@
 //
 // The descent is level-synchronous over the whole batch -- the paper's group query
 // processing (Section 4.4.3) with the group being every distinct key of the batch:
-//  k_distinct   per 256-query sub-tile, one warp counts the distinct keys (run heads,
-//               plus the sub-tile's first query); the last CTA to finish scans the
-//               apply tiles' counts (dense index) and ownership-marker maxima;
-//  k_dpack      each warp writes its sub-tile's distinct keys densely;
-//  k_top        the levels pinned in shared memory (copied once per CTA by TMA bulk
-//               copies) are resolved by one binary search of the lowest pinned level,
-//               which holds every key of the levels above it; writes the dense key and
-//               its start position on the next level;
+//  k_heads      one persistent kernel: the distinct keys (local run heads: a query
+//               whose key differs from the previous one, or the first query of a
+//               256-query sub-tile), their dense index by a decoupled look-back over
+//               the apply tiles, the tiles' ownership-marker prefixes for k_apply, and
+//               each key's start position below the levels pinned in shared memory
+//               (staged once per CTA by TMA bulk copies): one binary search of the
+//               lowest pinned level, which holds every key of the levels above it;
 //  k_level      one launch per remaining index level: every key scans its gap;
 //  k_locate     the storage layer: the node with the largest key <= q, and its state.
 // Each launch is one independent gather per key, so hundreds of thousands of keys are
@@ -37,7 +36,9 @@ constexpr int kThreads = 256;
 constexpr uint32_t kFull = 0xffffffffu;
 
 // r = largest index >= lo-1 with K[r] <= q (K[lo] <= q unless lo is the head, 0).
-// Also returns D[r] (0 if r < 0 or no down array) and K[r]. Each round reads kWide
+// Also returns D[r] (0 if r < 0 or no down array) and K[r], and the next entry's
+// K[r + 1] and D[r + 1] (the first key above q; at the level's sentinel, key 2^64-1 and
+// for the lowest built level the storage size). Each round reads kWide
 // consecutive entries with 16-byte loads (keys) and 8-byte loads (downs): 4 on index
 // levels, 16 (one 128-byte line) on the storage layer, whose gaps below the lowest built level span
 // (1/P)^(Lb-1) nodes. The loads need &K[i] 16-byte aligned (K and D come from arrays
@@ -46,7 +47,7 @@ constexpr uint32_t kFull = 0xffffffffu;
 template <bool kDown, int kWide>
 __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, uint32_t lo, uint32_t lim,
                                           uint64_t q, int32_t& r_out, uint32_t& d_out, uint64_t& k_out,
-                                          uint32_t* err) {
+                                          uint64_t& kn_out, uint32_t& dn_out, uint32_t* err) {
     static_assert(kWide % 2 == 0, "whole 16-byte key pairs and 8-byte down pairs");
     uint32_t i = lo, dprev = 0;
     uint64_t kprev = 0;
@@ -59,6 +60,8 @@ __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, 
                 r_out = -1;
                 d_out = 0;
                 k_out = 0;
+                kn_out = k0;
+                dn_out = kDown ? D[0] : 0u;
                 return;
             }
             kprev = k0;
@@ -72,6 +75,8 @@ __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, 
             r_out = -1;
             d_out = 0;
             k_out = 0;
+            kn_out = kMaxKey;
+            dn_out = 0;
             return;
         }
         uint64_t kk[kWide];
@@ -100,18 +105,22 @@ __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, 
         for (int j = 0; j < kWide; ++j) gt |= (kk[j] > q ? 1u : 0u) << j;
         if (gt) {
             const int f = __ffs(gt) - 1;
-            uint32_t dsel = dprev;
-            uint64_t ksel = kprev;
+            uint32_t dsel = dprev, dnext = dd[0];
+            uint64_t ksel = kprev, knext = kk[0];
 #pragma unroll
             for (int j = 1; j < kWide; ++j) {
                 if (j == f) {
                     dsel = dd[j - 1];
                     ksel = kk[j - 1];
+                    dnext = dd[j];
+                    knext = kk[j];
                 }
             }
             r_out = (int32_t)(i + (uint32_t)f) - 1;
             d_out = dsel;
             k_out = ksel;
+            kn_out = knext;
+            dn_out = dnext;
             return;
         }
         dprev = dd[kWide - 1];
@@ -129,7 +138,7 @@ __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, 
 template <bool kDown>
 __device__ __forceinline__ void warp_search(const uint64_t* K, const uint32_t* D, uint32_t& lo, uint32_t lim,
                                             uint64_t q, bool want, int32_t& r, uint32_t& dn, uint64_t& kr,
-                                            uint32_t* err) {
+                                            uint64_t& kn, uint32_t& dnn, uint32_t* err) {
     const int lane = threadIdx.x & 31;
     const uint32_t lo_min = __reduce_min_sync(kFull, want ? lo : 0xffffffffu);
     if (lo_min == 0xffffffffu) return;  // no lane searches this level
@@ -154,158 +163,139 @@ __device__ __forceinline__ void warp_search(const uint64_t* K, const uint32_t* D
         const int pick = c ? (int)c - 1 : 0;
         const uint32_t dsel = __shfl_sync(kFull, seg_d, pick & 31);
         const uint64_t ksel = __shfl_sync(kFull, seg_k, pick & 31);
+        const uint32_t dnx = __shfl_sync(kFull, seg_d, (int)(c & 31u));
+        const uint64_t knx = __shfl_sync(kFull, seg_k, (int)(c & 31u));
         if (want) {
             if (c < 32u) {
                 r = (int32_t)s + (int32_t)c - 1;
                 dn = c ? dsel : 0u;
                 kr = c ? ksel : 0ull;
+                kn = knx;
+                dnn = dnx;
                 scan = false;
             } else {
                 lo = s + 31u;  // every segment key is <= q: continue from its end
             }
         }
     }
-    if (scan) lane_scan<kDown, kDown ? 4 : 16>(K, D, lo, lim, q, r, dn, kr, err);
-}
-
-// Largest index of K[0..n) (sorted, in shared memory) with key <= q, or -1.
-__device__ __forceinline__ int32_t smem_rank(const uint64_t* K, uint32_t n, uint64_t q) {
-    uint32_t lo = 0, len = n;
-    while (len > 0) {
-        const uint32_t half = len >> 1;
-        if (K[lo + half] <= q) {
-            lo += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return (int32_t)lo - 1;
+    if (scan) lane_scan<kDown, kDown ? 4 : 16>(K, D, lo, lim, q, r, dn, kr, kn, dnn, err);
 }
 
 // Local run heads of one 256-query sub-tile (a run head, or the sub-tile's first query),
-// by one warp. Pass 0 returns their count and the largest ownership marker e_i (see
-// apply.cu); pass 1 writes the heads' keys to dq from dense index d0 on.
-__device__ __forceinline__ uint32_t subtile_heads(const DescendArgs& a, uint32_t sub, uint32_t qv, bool write,
-                                                  uint32_t d0, uint32_t* emax_out) {
+// by one warp: their keys go to `heads` in order, and the largest ownership marker e_i of
+// the sub-tile (see apply.cu) to *emax_out. Returns their count. The sub-tile's keys and
+// payloads are all loaded before any is used, so the warp waits for memory once.
+__device__ __forceinline__ uint32_t subtile_heads(const DescendArgs& a, uint32_t sub, uint32_t qv,
+                                                  uint64_t* heads, uint32_t* emax_out) {
+    constexpr int kR = kSubTile / 32;
     const int lane = threadIdx.x & 31;
     const uint32_t sb = sub * kSubTile;
     const uint32_t lt = lanemask_lt();
-    uint32_t nq = 0, emax = 0;
+    uint64_t kk[kR];
+    uint32_t op[kR];
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+        const uint32_t i = sb + (uint32_t)k * 32u + (uint32_t)lane;
+        kk[k] = i < qv ? a.sk[i] : kMaxKey;
+        op[k] = i < qv ? (a.sp[i] >> 30) : 0u;
+    }
     uint64_t carry = (sb > 0 && sb - 1 < qv) ? a.sk[sb - 1] : kMaxKey;  // key before the element
-#pragma unroll 2
-    for (int k = 0; k < kSubTile / 32; ++k) {
+    uint32_t nq = 0, emax = 0;
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
         const uint32_t i = sb + (uint32_t)k * 32u + (uint32_t)lane;
         const bool valid = i < qv;
-        const uint64_t q = valid ? a.sk[i] : kMaxKey;
+        const uint64_t q = kk[k];
         uint64_t prev = __shfl_up_sync(0xffffffffu, q, 1);
         if (lane == 0) prev = carry;
         carry = __shfl_sync(0xffffffffu, q, 31);
         const bool head = valid && (i == 0 || q != prev);
         const bool local = valid && (head || (k == 0 && lane == 0));
-        if (!write) {
-            const uint32_t op = valid ? (a.sp[i] >> 30) : 0u;
-            const uint32_t e = (valid && (op == 1u || op == 2u)) ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
-            emax = max(emax, e);
-        }
+        const uint32_t e = (valid && (op[k] == 1u || op[k] == 2u)) ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
+        emax = max(emax, e);
         const uint32_t b = __ballot_sync(0xffffffffu, local);
-        if (write && local) a.dq[d0 + nq + __popc(b & lt)] = q;
+        if (local) heads[nq + __popc(b & lt)] = q;
         nq += __popc(b);
     }
-    if (emax_out) *emax_out = __reduce_max_sync(0xffffffffu, emax);
+    *emax_out = __reduce_max_sync(0xffffffffu, emax);
     return nq;
 }
 
-// The distinct keys of the sorted batch, in two launches with no CTA waiting for
-// another. k_distinct: one CTA per 2048-query apply tile, one warp per 256-query
-// sub-tile, counts the local run heads and the largest ownership marker e_i; the last
-// CTA to finish scans the tiles' totals into each tile's first dense index (sum) and
-// its exclusive prefix of markers (max), so k_apply never waits. k_dpack: each warp
-// writes its sub-tile's heads densely from the tile's index on.
-__global__ void __launch_bounds__(kThreads) k_distinct(DescendArgs a) {
+constexpr int kWarps = kThreads / 32;
+
+// The distinct keys of the sorted batch, one CTA per 2048-query apply tile, in the order
+// CTAs start (a tile counter), so that a decoupled look-back (Merrill and Garland 2016)
+// waits only on tiles that running CTAs hold. One warp per 256-query sub-tile collects
+// its local run heads (in shared memory) and its largest ownership marker; the tile's
+// head count (a sum) and marker maximum (a max) go through the look-back, which gives
+// the tile's first dense index and the exclusive max prefix of the markers that k_apply
+// starts from. The heads are then written densely (dq).
+__global__ void __launch_bounds__(kThreads) k_heads(DescendArgs a, uint32_t epoch) {
     pdl_wait();
     pdl_trigger();
-    constexpr uint32_t kPer = 8;  // tiles per thread in the final scan
-    __shared__ uint32_t s_cnt[kThreads / 32], s_max[kThreads / 32];
-    __shared__ uint32_t s_tmp[33], s_last;
+    __shared__ uint64_t s_hk[kWarps][kSubTile];  // each sub-tile's local heads
+    __shared__ uint32_t s_cnt[kWarps], s_max[kWarps], s_off[kWarps + 1];
+    __shared__ uint32_t s_tile, s_base, s_pref;
+    __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (block_sees_error(&a.m->error)) return;
-    const uint32_t tile = blockIdx.x, ntiles = gridDim.x;
+    if (tid == 0) {
+        s_tile = atomicAdd(&a.bm->tile_ctr[kCtrDistinct], 1u);
+        s_fail = 0;
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile, ntiles = gridDim.x;
     const uint32_t n = a.n, qv = n - a.bm->invalid;
     const uint32_t nsub = (n + kSubTile - 1) / kSubTile;
-    const uint32_t sub = tile * (kApplyTile / kSubTile) + (uint32_t)warp;
-    uint32_t emax = 0, nq = 0;
-    if (sub < nsub) nq = subtile_heads(a, sub, qv, false, 0u, &emax);
+    const uint32_t sub = tile * kWarps + (uint32_t)warp;
+    uint32_t nq = 0, emax = 0;
+    if (sub < nsub) nq = subtile_heads(a, sub, qv, s_hk[warp], &emax);
     if (lane == 0) {
         s_cnt[warp] = nq;
         s_max[warp] = emax;
-        if (sub < nsub) a.sub_cnt[sub] = nq;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (warp < 2) {
         uint32_t c = 0, mx = 0;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) {
+        for (int w = 0; w < kWarps; ++w) {
+            if (warp == 0 && lane == 0) s_off[w] = c;
             c += s_cnt[w];
             mx = max(mx, s_max[w]);
         }
-        a.tile_heads[tile] = c;
-        a.tile_emax[tile] = mx;
-        __threadfence();  // the totals, before this CTA's arrival is counted
-        s_last = atomicAdd(&a.bm->tile_ctr[kCtrDistinct], 1u) == ntiles - 1u;
+        if (warp == 0 && lane == 0) s_off[kWarps] = c;
+        bool ok = true;
+        const uint32_t ex = warp == 0 ? lookback_warp_wide<false, 8>(a.desc, tile, epoch, c, a.err, &ok)
+                                      : lookback_warp_wide<true, 8>(a.desc + ntiles, tile, epoch, mx, a.err, &ok);
+        if (lane == 0) {
+            if (warp == 0) s_base = ex;
+            else s_pref = ex;
+            if (!ok) s_fail = 1;
+        }
     }
     __syncthreads();
-    if (!s_last) return;
-    __threadfence();  // every tile has arrived: their totals are visible
-    uint32_t csum = 0, cmax = 0;
-    for (uint32_t g0 = 0; g0 < ntiles; g0 += kThreads * kPer) {
-        const uint32_t t0 = g0 + (uint32_t)tid * kPer;
-        uint32_t c[kPer], m[kPer], sum = 0, mx = 0;
+    if (s_fail) return;
+    const uint32_t base = s_base, tot = s_off[kWarps];
+    if (tid == 0) a.tile_pref[tile] = s_pref;
+    if (lane == 0 && sub < nsub) a.sub_pref[sub] = base + s_off[warp];
+    if (tile == ntiles - 1 && tid == 0) a.bm->distinct = base + tot;
+    for (uint32_t g = (uint32_t)tid; g < tot; g += kThreads) {
+        int w = 0;
 #pragma unroll
-        for (uint32_t k = 0; k < kPer; ++k) {
-            c[k] = t0 + k < ntiles ? __ldcg(&a.tile_heads[t0 + k]) : 0u;
-            m[k] = t0 + k < ntiles ? __ldcg(&a.tile_emax[t0 + k]) : 0u;
-            sum += c[k];
-            mx = max(mx, m[k]);
-        }
-        uint32_t tsum, tmax;
-        uint32_t rs = csum + block_excl_sum<kThreads>(sum, s_tmp, &tsum);
-        uint32_t rm = max(cmax, block_excl_max<kThreads>(mx, s_tmp, &tmax));
-#pragma unroll
-        for (uint32_t k = 0; k < kPer; ++k) {
-            if (t0 + k < ntiles) {
-                a.tile_base[t0 + k] = rs;
-                a.tile_pref[t0 + k] = rm;
-            }
-            rs += c[k];
-            rm = max(rm, m[k]);
-        }
-        csum += tsum;
-        cmax = max(cmax, tmax);
+        for (int k = 1; k < kWarps; ++k) w = (g >= s_off[k]) ? k : w;
+        a.dq[base + g] = s_hk[w][g - s_off[w]];
     }
-    if (tid == 0) a.bm->distinct = csum;
 }
 
-__global__ void __launch_bounds__(kThreads) k_dpack(DescendArgs a) {
-    pdl_wait();
-    pdl_trigger();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (*(volatile const uint32_t*)&a.m->error) return;  // no barrier in this kernel
-    const uint32_t n = a.n, qv = n - a.bm->invalid;
-    const uint32_t nsub = (n + kSubTile - 1) / kSubTile;
-    const uint32_t tile = blockIdx.x;
-    const uint32_t s0 = tile * (kApplyTile / kSubTile), sub = s0 + (uint32_t)warp;
-    if (sub >= nsub) return;
-    uint32_t d0 = a.tile_base[tile];
-    for (uint32_t t = s0; t < sub; ++t) d0 += a.sub_cnt[t];
-    if (lane == 0) a.sub_pref[sub] = d0;
-    subtile_heads(a, sub, qv, true, d0, nullptr);
-}
+constexpr int kTopCtasPerSm = 6;
 
-// Start position below the pinned levels for every distinct key (one per thread): one
-// binary search of the lowest pinned level (in shared memory, copied per CTA by TMA
-// bulk copies), then a walk of the levels down to top_launched + 1.
-__global__ void __launch_bounds__(kThreads) k_top(DescendArgs a) {
+// Start position below the pinned levels for every distinct key: a persistent grid whose
+// CTAs stage the pinned top levels in shared memory once (TMA bulk copies, one mbarrier)
+// and then take one key per thread at a time: the count of keys <= q in the lowest pinned
+// level (it holds every key of the levels above it) by binary lifting, then one
+// warp_search per walked level. The dense keys are sorted, so on the upper walked levels
+// a warp's 32 keys usually start within a few entries and share one coalesced segment.
+__global__ void __launch_bounds__(kThreads, kTopCtasPerSm) k_top(DescendArgs a) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) uint8_t s_dyn[];
@@ -337,24 +327,30 @@ __global__ void __launch_bounds__(kThreads) k_top(DescendArgs a) {
             return;
         }
     }
-    const uint32_t bL = m->base[Ls], nL = m->n[Ls];
-    for (uint32_t d = blockIdx.x * kThreads + tid; d < D; d += gridDim.x * kThreads) {
-        const uint64_t q = a.dq[d];
-        uint32_t lo = 0;
-        if (Ls <= H) {
-            const int32_t r = smem_rank(s_k + bL, nL, q);
-            lo = (r >= 0) ? s_d[bL + r] : 0u;
-        }
-        // levels between the pinned ones and the top launched level: walked here
-        for (int l = (Ls <= H ? (int)Ls - 1 : (int)H); l > a.top_launched && l >= (int)Lb; --l) {
+    const bool pinned = Ls <= H;
+    const uint32_t bL = m->base[Ls], nL = pinned ? m->n[Ls] : 0u;
+    const uint32_t step0 = nL ? 1u << (31 - __clz(nL)) : 0u;
+    const uint64_t* LK = m->lcur ? a.lkeys1 : a.lkeys;
+    const uint32_t* LD = m->lcur ? a.ldown1 : a.ldown;
+    // levels between the pinned ones and the top launched level are walked here
+    const int l_hi = pinned ? (int)Ls - 1 : (int)H;
+    const int l_lo = max(a.top_launched + 1, (int)Lb);
+    for (uint32_t d0 = blockIdx.x * kThreads; d0 < D; d0 += gridDim.x * kThreads) {
+        const uint32_t d = d0 + (uint32_t)tid;
+        const bool active = d < D;
+        const uint64_t q = active ? a.dq[d] : kMaxKey;
+        uint32_t c = 0;  // keys <= q in the lowest pinned level
+        for (uint32_t step = step0; step > 0; step >>= 1)
+            if (c + step <= nL && s_k[bL + c + step - 1] <= q) c += step;
+        uint32_t lo = c ? s_d[bL + c - 1] : 0u;
+        for (int l = l_hi; l >= l_lo; --l) {
             int32_t r = -1;
-            uint32_t dn = 0;
-            uint64_t kr = 0;
-            lane_scan<true, 4>((m->lcur ? a.lkeys1 : a.lkeys) + m->base[l], (m->lcur ? a.ldown1 : a.ldown) + m->base[l],
-                               lo, m->n[l], q, r, dn, kr, a.err);
+            uint32_t dn = 0, dnn = 0;
+            uint64_t kr = 0, kn = 0;
+            warp_search<true>(LK + m->base[l], LD + m->base[l], lo, m->n[l], q, active, r, dn, kr, kn, dnn, a.err);
             lo = (r >= 0) ? dn : 0u;
         }
-        a.dlo[d] = lo;
+        if (active) a.dlo[d] = lo;
     }
 }
 
@@ -377,15 +373,74 @@ __global__ void __launch_bounds__(kThreads) k_level(DescendArgs a, int l) {
         const uint64_t q = active ? a.dq[d] : kMaxKey;
         uint32_t lo = active ? a.dlo[d] : 0u;
         int32_t r = -1;
-        uint32_t dn = 0;
-        uint64_t kr = 0;
-        warp_search<true>(K, Dn, lo, lim, q, active, r, dn, kr, a.err);
+        uint32_t dn = 0, dnn = 0;
+        uint64_t kr = 0, kn = 0;
+        warp_search<true>(K, Dn, lo, lim, q, active, r, dn, kr, kn, dnn, a.err);
         if (active) a.dlo[d] = (r >= 0) ? dn : 0u;
     }
 }
 
-// The storage layer: node with the largest key <= q (exists if equal) and its state.
-__global__ void __launch_bounds__(kThreads) k_locate(DescendArgs a) {
+// Largest p in [slo - 1, shi) with K[p] <= q, for a storage gap with K[shi] > q and,
+// when slo > 0 or has_lo, K[slo] <= q; -1 when q is below every key. The gap's keys
+// lie between klo = K[slo] and khi = K[shi], so the answer is looked for first in the
+// 64-byte line of 8 keys around the linear estimate slo + (q - klo) / (khi - klo) *
+// (shi - slo): for keys spread evenly over the gap that line usually holds it. From
+// there the search moves line by line towards the answer, so it stays exact for any
+// key distribution.
+__device__ __forceinline__ int32_t gap_search(const uint64_t* K, uint32_t slo, uint32_t shi, uint64_t klo,
+                                              uint64_t khi, uint64_t q, uint32_t lim, uint64_t& k_out, uint32_t* err) {
+    uint32_t est = slo;
+    if (shi > slo + 1u && khi != kMaxKey && khi > klo) {
+        const float f = __ull2float_rz(q - klo) / __ull2float_rn(khi - klo);  // in [0, 1]
+        est = slo + (uint32_t)(f * (float)(shi - slo));
+        if (est >= shi) est = shi - 1u;
+    }
+    uint32_t c = est & ~7u;
+    int dir = 0;
+    const uint32_t max_lines = (shi - slo) / 8u + 3u;
+    for (uint32_t it = 0;; ++it) {
+        if (c > lim || it > max_lines) {
+            atomicOr(err, kErrBounds);
+            return -1;
+        }
+        const ulonglong2* kp = reinterpret_cast<const ulonglong2*>(K + c);
+        uint64_t kk[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const ulonglong2 v = kp[j];
+            kk[2 * j] = v.x;
+            kk[2 * j + 1] = v.y;
+        }
+        uint32_t gt = 0;  // bit j: K[c + j] > q (a suffix of the line, the keys being sorted)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) gt |= (kk[j] > q ? 1u : 0u) << j;
+        if (gt == 0xFFu) {  // the answer is before this line
+            if (dir > 0) return (int32_t)c - 1;  // (k_out was set on the previous line)
+            if (c == 0) return -1;
+            dir = -1;
+            c -= 8u;
+        } else if (gt == 0u) {  // the answer is at the end of this line or after it
+            k_out = kk[7];
+            if (dir < 0) return (int32_t)c + 7;
+            dir = 1;
+            c += 8u;
+        } else {
+            const int f = __ffs(gt) - 1;  // >= 1
+#pragma unroll
+            for (int j = 1; j < 8; ++j)
+                if (j == f) k_out = kk[j - 1];
+            return (int32_t)c + f - 1;
+        }
+    }
+}
+
+// The storage layer: the node with the largest key <= q (exists if equal) and its state.
+// `lvl` is the lowest index level that can be built. When it is built and not pinned in
+// shared memory (the usual case), it has no launch of its own: it is searched here, which
+// gives the storage gap of q between the down pointers of two consecutive entries of that
+// level, D[r] and D[r + 1], and their keys K[r] <= q < K[r + 1]; gap_search then finds the
+// node. Otherwise the node is scanned for from the start position the descent left.
+__global__ void __launch_bounds__(kThreads) k_locate(DescendArgs a, int lvl) {
     pdl_wait();
     pdl_trigger();
     const DevMeta* m = a.m;
@@ -394,6 +449,12 @@ __global__ void __launch_bounds__(kThreads) k_locate(DescendArgs a) {
     const uint64_t* SK = a.st.keys[cur];
     const uint8_t* SM = a.st.meta[cur];
     const uint64_t* SV = a.st.vals[cur];
+    const uint32_t H = m->H, Lb = m->Lb, Ls = m->Ls;
+    const int top = (Ls <= H) ? (int)Ls - 1 : (int)H;
+    const bool fused = lvl <= top && lvl >= (int)Lb;  // then lvl == Lb: its downs are storage positions
+    const uint64_t* LK = (m->lcur ? a.lkeys1 : a.lkeys) + (fused ? m->base[lvl] : 0u);
+    const uint32_t* LD = (m->lcur ? a.ldown1 : a.ldown) + (fused ? m->base[lvl] : 0u);
+    const uint32_t lim = fused ? m->n[lvl] : 0u;
     const uint32_t D = a.bm->distinct;
     for (uint32_t d0 = blockIdx.x * kThreads; d0 < D; d0 += gridDim.x * kThreads) {
         const uint32_t d = d0 + threadIdx.x;
@@ -401,23 +462,34 @@ __global__ void __launch_bounds__(kThreads) k_locate(DescendArgs a) {
         const uint64_t q = active ? a.dq[d] : kMaxKey;
         uint32_t lo = active ? a.dlo[d] : 0u;
         int32_t r = -1;
-        uint32_t dn = 0;
-        uint64_t kr = 0;
-        warp_search<false>(SK, nullptr, lo, size, q, active, r, dn, kr, a.err);
+        uint32_t dn = 0, dnn = 0;
+        uint64_t kr = 0, kn = 0;
+        if (fused) {
+            warp_search<true>(LK, LD, lo, lim, q, active, r, dn, kr, kn, dnn, a.err);
+            if (active) {
+                r = gap_search(SK, r >= 0 ? dn : 0u, dnn, r >= 0 ? kr : 0ull, kn, q, size, kr, a.err);
+            }
+        } else {
+            warp_search<false>(SK, nullptr, lo, size, q, active, r, dn, kr, kn, dnn, a.err);
+        }
         if (active) {
             const bool exists = r >= 0 && kr == q;
+            // the value is read with the meta byte, not after it, so both requests are in
+            // flight together (a delete-flagged node's value is read and dropped)
             const uint8_t meta = exists ? SM[r] : (uint8_t)0;
+            const uint64_t v = exists ? SV[r] : 0ull;
             const bool live = exists && !(meta & kTomb);
             a.loc[d] = (uint32_t)(r + 1);
             a.flags[d] = (uint8_t)((exists ? 1u : 0u) | (live ? 2u : 0u));
-            a.val0[d] = live ? SV[r] : 0ull;
+            a.val0[d] = live ? v : 0ull;
         }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms, cudaEvent_t before_locate) {
+cudaError_t launch_descend(const DescendArgs& a, uint32_t& epoch, cudaStream_t s, int num_sms,
+                           cudaEvent_t before_locate) {
     static bool attr_set = false;
     const int dyn = (int)((kSmemTopMax + kPad) * (sizeof(uint64_t) + sizeof(uint32_t)));
     if (!attr_set) {
@@ -427,24 +499,24 @@ cudaError_t launch_descend(const DescendArgs& a, cudaStream_t s, int num_sms, cu
     }
     if (a.n == 0) return cudaSuccess;
     const uint32_t ntiles = (a.n + kApplyTile - 1) / kApplyTile;
-    launch_dep(k_distinct, ntiles, kThreads, 0, s, a);
+    launch_dep(k_heads, ntiles, kThreads, 0, s, a, ++epoch);
     ++g_launches;
-    launch_dep(k_dpack, ntiles, kThreads, 0, s, a);
+    // CTAs past the distinct keys exit at once
+    const uint32_t tcap = (uint32_t)num_sms * kTopCtasPerSm, tneed = (a.n + kThreads - 1) / kThreads;
+    launch_dep(k_top, tneed < tcap ? tneed : tcap, kThreads, dyn, s, a);
     ++g_launches;
     const uint32_t need = (a.n + kThreads - 1) / kThreads;
-    launch_dep(k_top, need, kThreads, dyn, s, a);  // CTAs past the distinct keys exit at once
-    ++g_launches;
-    // one launch per index level from top_launched down to 2; a launch whose level is
-    // pinned or not built exits at once, and levels above top_launched that are
-    // neither (the index grew) are walked by k_top
+    // one launch per index level from top_launched down to bottom_launched + 1; a launch
+    // whose level is pinned or not built exits at once, levels above top_launched that
+    // are neither are walked by k_heads, and level bottom_launched by k_locate
     const uint32_t capg = (uint32_t)num_sms * 16u;
     const uint32_t gblocks = need < capg ? need : capg;  // grid-stride over the distinct keys
-    for (int l = a.top_launched; l >= a.bottom_launched; --l) {
+    for (int l = a.top_launched; l > a.bottom_launched; --l) {
         launch_dep(k_level, gblocks, kThreads, 0, s, a, l);
         ++g_launches;
     }
     if (before_locate) cudaEventRecord(before_locate, s);
-    launch_dep(k_locate, gblocks, kThreads, 0, s, a);
+    launch_dep(k_locate, gblocks, kThreads, 0, s, a, a.bottom_launched);  // searches that level itself
     ++g_launches;
     return cudaGetLastError();
 }

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <new>
 #include <algorithm>
 #include <type_traits>
@@ -17,6 +18,7 @@
 
 namespace pi {
 thread_local uint64_t g_launches = 0;
+thread_local KernelTimer* g_ktimer = nullptr;
 }  // namespace pi
 
 using namespace pi;
@@ -41,10 +43,6 @@ struct Scratch {
     NewNodes nn{};
     NewNodes stage{};
     uint32_t* tile_pref = nullptr;
-    uint32_t* tile_heads = nullptr;  // descent: distinct keys per apply tile
-    uint32_t* tile_emax = nullptr;   // descent: largest ownership marker per apply tile
-    uint32_t* tile_base = nullptr;   // descent: dense index of each apply tile's first key
-    uint32_t* sub_cnt = nullptr;     // descent: distinct keys per sub-tile
     uint32_t* tile_new = nullptr;
     uint32_t* tcnt = nullptr;  // radix sort: per-tile digit counts
     uint32_t* toff = nullptr;  // radix sort: per-tile digit offsets
@@ -64,6 +62,56 @@ struct Scratch {
     uint32_t* sub_pref = nullptr;
     uint64_t* dq = nullptr;    // descent: dense distinct keys
     uint32_t* dlo = nullptr;   // descent: per-key start position
+};
+
+// pi_profile level 2: the two events around every kernel launch of the batch entry
+// points, folded into per-kernel sums when read (or when the event pool is full).
+struct KernelTimes final : KernelTimer {
+    struct Rec {
+        const void* f;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    cudaEvent_t pending = nullptr;
+    std::vector<Rec> recs;
+    std::vector<std::pair<const void*, std::pair<double, uint64_t>>> acc;  // kernel -> (ms, launches)
+    cudaEvent_t take() {
+        if (used == pool.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void before(cudaStream_t s) override {
+        if (used + 2 > 8192) fold();
+        pending = take();
+        if (pending) cudaEventRecord(pending, s);
+    }
+    void after(const void* f, cudaStream_t s) override {
+        cudaEvent_t e = take();
+        if (!e || !pending) return;
+        cudaEventRecord(e, s);
+        recs.push_back({f, pending, e});
+    }
+    void fold() {
+        for (const Rec& r : recs) {
+            float ms = 0.f;
+            cudaEventSynchronize(r.b);
+            if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) continue;
+            size_t k = 0;
+            while (k < acc.size() && acc[k].first != r.f) ++k;
+            if (k == acc.size()) acc.push_back({r.f, {0.0, 0}});
+            acc[k].second.first += ms;
+            acc[k].second.second += 1;
+        }
+        recs.clear();
+        used = 0;
+    }
+    ~KernelTimes() {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
 };
 
 struct Staging {
@@ -105,7 +153,13 @@ struct pi_index {
     uint32_t* ldown1 = nullptr;
     uint64_t idx_cap = 0;  // entries, padding excluded
     Scratch sc;
-    Staging stg;
+    // pi_execute_batch_host's pipeline: two staging slots, copies in on `hs`, the batch on
+    // `cs`, copies out on `ds`; per slot, events for inputs copied, batch done, results
+    // copied out (created on the first host-buffer call)
+    Staging stg[2];
+    cudaStream_t hs = nullptr, cs = nullptr, ds = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
+    uint64_t host_calls = 0;
     uint64_t* desc = nullptr;
     uint64_t desc_words = 0;
     uint32_t* lcnt = nullptr;  // per-level per-tile live counts: 32 rows x lstride
@@ -128,6 +182,7 @@ struct pi_index {
     bool force_rebuild = false;
     // stage timing (pi_profile): events recorded between the pipeline's kernels
     bool prof = false;
+    KernelTimes* kt = nullptr;   // pi_profile level 2
     cudaEvent_t* pev = nullptr;  // kProfSlots batches x kProfEvents events
     uint32_t pused = 0;          // batches recorded but not folded yet
     double pms[PI_NUM_STAGES] = {};
@@ -138,6 +193,13 @@ struct pi_index {
     cudaStream_t rs = nullptr;
     cudaEvent_t ev_applied = nullptr, ev_rebuilt = nullptr;
     bool rebuild_pending = false;
+    // The index's last operation (a batch, a range search or a batching-form call) ends
+    // at last_ev on last_stream; an entry point on another stream first waits for it.
+    // last_ev is the index's own ev_last, or the batching set's event for its calls.
+    cudaEvent_t ev_last = nullptr;
+    cudaEvent_t last_ev = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool has_last = false;
 };
 
 namespace {
@@ -247,12 +309,12 @@ void free_scratch(Scratch& s) {
     dfree(s.loc); dfree(s.flags); dfree(s.val0);
     dfree(s.nn.keys); dfree(s.nn.vals); dfree(s.nn.loc); dfree(s.nn.height);
     dfree(s.stage.keys); dfree(s.stage.vals); dfree(s.stage.loc); dfree(s.stage.height);
-    dfree(s.tile_pref); dfree(s.tile_new); dfree(s.tile_heads); dfree(s.tile_emax); dfree(s.tile_base);
+    dfree(s.tile_pref); dfree(s.tile_new);
     dfree(s.tcnt); dfree(s.toff); dfree(s.ndig); dfree(s.fixmap); dfree(s.gsum); dfree(s.gctr);
     dfree(s.cstage.keys); dfree(s.cstage.pos); dfree(s.cstage.hl); dfree(s.chg.keys); dfree(s.chg.pos); dfree(s.chg.hl);
     dfree(s.tile_chg); dfree(s.tile_chg_pref);
     dfree(s.lst_keys); dfree(s.lst_pos); dfree(s.lst_pref); dfree(s.lst_ins);
-    dfree(s.sub_pref); dfree(s.sub_cnt); dfree(s.dq); dfree(s.dlo);
+    dfree(s.sub_pref); dfree(s.dq); dfree(s.dlo);
     s.cap = 0;
 }
 
@@ -271,7 +333,6 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     PI_TRY(dalloc(&s.stage.keys, cs)); PI_TRY(dalloc(&s.stage.vals, cs));
     PI_TRY(dalloc(&s.stage.loc, cs)); PI_TRY(dalloc(&s.stage.height, cs));
     PI_TRY(dalloc(&s.tile_pref, tiles)); PI_TRY(dalloc(&s.tile_new, tiles));
-    PI_TRY(dalloc(&s.tile_heads, tiles)); PI_TRY(dalloc(&s.tile_emax, tiles)); PI_TRY(dalloc(&s.tile_base, tiles));
     const uint64_t stiles = (q + kSortTile - 1) / kSortTile + 1;
     PI_TRY(dalloc(&s.tcnt, stiles * 256)); PI_TRY(dalloc(&s.toff, stiles * 256));
     const uint64_t sgroups = stiles / kScanGroup + 1;
@@ -285,7 +346,7 @@ cudaError_t alloc_scratch(Scratch& s, uint64_t q) {
     PI_TRY(dalloc(&s.lst_keys, s.lst_cap)); PI_TRY(dalloc(&s.lst_pos, s.lst_cap));
     PI_TRY(dalloc(&s.lst_pref, s.lst_cap)); PI_TRY(dalloc(&s.lst_ins, s.lst_cap));
     const uint64_t nsub = (q + kSubTile - 1) / kSubTile + 1;
-    PI_TRY(dalloc(&s.sub_pref, nsub)); PI_TRY(dalloc(&s.sub_cnt, nsub));
+    PI_TRY(dalloc(&s.sub_pref, nsub));
     PI_TRY(dalloc(&s.dq, c)); PI_TRY(dalloc(&s.dlo, c));
 #undef PI_TRY
     s.cap = q;
@@ -355,9 +416,21 @@ void destroy(pi_index* x) {
         for (size_t i = 0; i < (size_t)kProfSlots * kProfEvents; ++i) cudaEventDestroy(x->pev[i]);
         delete[] x->pev;
     }
+    delete x->kt;
     free_scratch(x->sc);
     dfree(x->r_bounds); dfree(x->r_start); dfree(x->r_end); dfree(x->r_cnt); dfree(x->r_bsum);
-    dfree(x->stg.ops); dfree(x->stg.keys); dfree(x->stg.vals); dfree(x->stg.res);
+    for (auto& g : x->stg) {
+        dfree(g.ops); dfree(g.keys); dfree(g.vals); dfree(g.res);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (x->ev_in[k]) cudaEventDestroy(x->ev_in[k]);
+        if (x->ev_comp[k]) cudaEventDestroy(x->ev_comp[k]);
+        if (x->ev_out[k]) cudaEventDestroy(x->ev_out[k]);
+    }
+    if (x->hs) cudaStreamDestroy(x->hs);
+    if (x->cs) cudaStreamDestroy(x->cs);
+    if (x->ds) cudaStreamDestroy(x->ds);
+    if (x->ev_last) cudaEventDestroy(x->ev_last);
     free_storage(x->st);
     dfree(x->lkeys); dfree(x->ldown); dfree(x->lkeys1); dfree(x->ldown1);
     dfree(x->desc); dfree(x->lcnt); dfree(x->loff); dfree(x->mcnt); dfree(x->wcount); dfree(x->d_meta); dfree(x->d_bm); dfree(x->d_dofs); dfree(x->d_count);
@@ -415,7 +488,20 @@ void wait_rebuild(pi_index* x, cudaStream_t s) {
     if (x->rebuild_pending) cudaStreamWaitEvent(s, x->ev_rebuilt, 0);
 }
 
+// Makes `s` wait for the index's last operation when that ran on another stream.
+void order_after_last(pi_index* x, cudaStream_t s) {
+    if (x->has_last && x->last_stream != s) cudaStreamWaitEvent(s, x->last_ev, 0);
+}
+
+void mark_last(pi_index* x, cudaStream_t s) {
+    cudaEventRecord(x->ev_last, s);
+    x->last_ev = x->ev_last;
+    x->last_stream = s;
+    x->has_last = true;
+}
+
 cudaError_t sync_known(pi_index* x, cudaStream_t s) {
+    order_after_last(x, s);
     wait_rebuild(x, s);
     cudaError_t e = read_meta(x, s, &x->known);
     if (e == cudaSuccess) x->rebuild_pending = false;
@@ -559,7 +645,7 @@ constexpr uint64_t noalloc_bytes(uint64_t q) {
            + al256(c * 4) + al256(c) + al256(c * 8)               // loc, flags, val0
            + 2 * al256(c * 8) + al256(c * 4) + al256(c)           // new nodes
            + 2 * al256(cs * 8) + al256(cs * 4) + al256(cs)        // new-node staging
-           + 5 * al256(tiles * 4)                                 // tile prefix / new / heads / emax / base
+           + 2 * al256(tiles * 4)                                 // tile prefix / new
            + 2 * al256(stiles * 256 * 4) + al256(stiles * kSortTile + 16)  // tcnt, toff, ndig
            + al256((stiles / kScanGroup + 1) * 256 * 4) + al256(8 * (stiles / kScanGroup + 2) * 4)  // gsum, gctr
            + al256((c / 32 + 1) * 4)                              // fixmap
@@ -567,7 +653,7 @@ constexpr uint64_t noalloc_bytes(uint64_t q) {
            + al256(c * 8) + al256(c * 4) + al256(c)               // level changes
            + 2 * al256(tiles * 4)                                 // per-tile change counts
            + al256((2 * c + 64) * 8) + 2 * al256((2 * c + 64) * 4) + al256(2 * c + 64)  // lists
-           + 2 * al256(nsub * 4)                                  // sub_pref, sub_cnt
+           + al256(nsub * 4)                                      // sub_pref
            + al256(c * 8) + al256(c * 4);                         // dq, dlo
 }
 
@@ -593,7 +679,6 @@ uint64_t carve_scratch(uint8_t* base, uint64_t q, Scratch& s) {
     take(s.nn.keys, c * 8); take(s.nn.vals, c * 8); take(s.nn.loc, c * 4); take(s.nn.height, c);
     take(s.stage.keys, cs * 8); take(s.stage.vals, cs * 8); take(s.stage.loc, cs * 4); take(s.stage.height, cs);
     take(s.tile_pref, tiles * 4); take(s.tile_new, tiles * 4);
-    take(s.tile_heads, tiles * 4); take(s.tile_emax, tiles * 4); take(s.tile_base, tiles * 4);
     take(s.tcnt, stiles * 256 * 4); take(s.toff, stiles * 256 * 4); take(s.ndig, stiles * kSortTile + 16);
     take(s.gsum, (stiles / kScanGroup + 1) * 256 * 4); take(s.gctr, 8 * (stiles / kScanGroup + 2) * 4);
     take(s.fixmap, (c / 32 + 1) * 4);
@@ -603,7 +688,7 @@ uint64_t carve_scratch(uint8_t* base, uint64_t q, Scratch& s) {
     s.lst_cap = 2 * c + 64;
     take(s.lst_keys, s.lst_cap * 8); take(s.lst_pos, s.lst_cap * 4); take(s.lst_pref, s.lst_cap * 4);
     take(s.lst_ins, s.lst_cap);
-    take(s.sub_pref, nsub * 4); take(s.sub_cnt, nsub * 4);
+    take(s.sub_pref, nsub * 4);
     take(s.dq, c * 8); take(s.dlo, c * 4);
     s.cap = q;
     return off;
@@ -689,14 +774,13 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     da.sk = sc.a_k;
     da.sp = sc.a_p;
     da.tile_pref = sc.tile_pref;
-    da.sub_cnt = sc.sub_cnt;
-    da.tile_heads = sc.tile_heads;
-    da.tile_emax = sc.tile_emax;
-    da.tile_base = sc.tile_base;
     da.sub_pref = sc.sub_pref;
+    da.desc = x->desc;
     da.dq = sc.dq;
     da.dlo = sc.dlo;
-    da.top_launched = top_launched_for(x);
+    // the lowest buildable level is never walked by the prologue: the storage locate
+    // searches it itself (it needs that level's gap ends)
+    da.top_launched = std::max(top_launched_for(x), (int)x->min_lb);
     da.bottom_launched = (int)x->min_lb;
     da.m = x->d_meta;
     da.bm = bm;
@@ -710,7 +794,7 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
     da.val0 = sc.val0;
     da.n = (uint32_t)n;
     da.err = &x->d_meta->error;
-    if ((e = launch_descend(da, s, x->num_sms, prof_event(x, 10))) != cudaSuccess) return map_cuda(e);
+    if ((e = launch_descend(da, ep, s, x->num_sms, prof_event(x, 10))) != cudaSuccess) return map_cuda(e);
     prof_mark(x, 3, s);
     ApplyArgs aa{};
     aa.sk = sc.a_k;
@@ -784,7 +868,10 @@ int enqueue_batch_body(pi_index* x, const Scratch& sc, const uint8_t* ops, const
 int enqueue_batch(pi_index* x, const Scratch& sc, const uint8_t* ops, const uint64_t* keys,
                   const uint64_t* values, uint64_t n, pi_result_t* results, uint64_t size_ub, cudaStream_t s) {
     const uint64_t l0 = g_launches;
+    g_ktimer = x->kt;
     const int r = enqueue_batch_body(x, sc, ops, keys, values, n, results, size_ub, s);
+    g_ktimer = nullptr;
+    if (r == PI_OK) mark_last(x, s);
     x->launches += g_launches - l0;
     return r;
 }
@@ -858,6 +945,7 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
         if ((e = cudaStreamCreateWithFlags(&x->rs, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaEventCreateWithFlags(&x->ev_applied, cudaEventDisableTiming)) != cudaSuccess) break;
         if ((e = cudaEventCreateWithFlags(&x->ev_rebuilt, cudaEventDisableTiming)) != cudaSuccess) break;
+        if ((e = cudaEventCreateWithFlags(&x->ev_last, cudaEventDisableTiming)) != cudaSuccess) break;
         if ((e = dalloc(&x->d_dofs, 8 * 256)) != cudaSuccess) break;
         if ((e = dalloc(&x->d_count, 1)) != cudaSuccess) break;
         cudaMemsetAsync(x->d_meta, 0, sizeof(DevMeta), s);
@@ -952,6 +1040,7 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
     if (!ops || !keys || !values || !results || n > PI_MAX_BATCH) return PI_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
+    order_after_last(x, s);
     refresh_known(x);
     if (int rc = sticky_error(x->known)) return rc;
     // capacities (grow rarely; growing synchronises the stream)
@@ -989,10 +1078,21 @@ int pi_execute_batch_host(pi_index_t* x, const uint8_t* ops_host, const uint64_t
     if (n == 0) return PI_OK;
     if (!ops_host || !keys_host || !values_host || !results_host || n > PI_MAX_BATCH) return PI_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    Staging& g = x->stg;
-    if (n > g.cap) {
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
+    cudaError_t e = cudaSuccess;
+    if (!x->hs) {  // first host-buffer call: the pipeline's streams and events
+        for (cudaStream_t* p : {&x->hs, &x->cs, &x->ds})
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(p, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+            for (cudaEvent_t* p : {&x->ev_in[k], &x->ev_comp[k], &x->ev_out[k]})
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(p, cudaEventDisableTiming);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    const int k = (int)(x->host_calls & 1u);
+    Staging& g = x->stg[k];
+    if (n > g.cap) {  // grow the slot (rare): wait until nothing uses it
+        if ((e = cudaEventSynchronize(x->ev_comp[k])) != cudaSuccess ||
+            (e = cudaEventSynchronize(x->ev_out[k])) != cudaSuccess)
+            return map_cuda(e);
         dfree(g.ops); dfree(g.keys); dfree(g.vals); dfree(g.res);
         g.cap = 0;
         if ((e = dalloc(&g.ops, n)) != cudaSuccess || (e = dalloc(&g.keys, n)) != cudaSuccess ||
@@ -1002,12 +1102,25 @@ int pi_execute_batch_host(pi_index_t* x, const uint8_t* ops_host, const uint64_t
         }
         g.cap = n;
     }
-    cudaMemcpyAsync(g.ops, ops_host, n, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(g.keys, keys_host, n * 8, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(g.vals, values_host, n * 8, cudaMemcpyHostToDevice, s);
-    int rc = pi_execute_batch(x, g.ops, g.keys, g.vals, n, g.res, stream);
+    // copy in, once the batch that last read this slot's inputs has finished
+    cudaStreamWaitEvent(x->hs, x->ev_comp[k], 0);
+    cudaMemcpyAsync(g.ops, ops_host, n, cudaMemcpyHostToDevice, x->hs);
+    cudaMemcpyAsync(g.keys, keys_host, n * 8, cudaMemcpyHostToDevice, x->hs);
+    cudaMemcpyAsync(g.vals, values_host, n * 8, cudaMemcpyHostToDevice, x->hs);
+    cudaEventRecord(x->ev_in[k], x->hs);
+    // the batch, after the index's previous operation, its inputs, and the copy out of
+    // the slot's previous results
+    cudaStreamWaitEvent(x->cs, x->ev_in[k], 0);
+    cudaStreamWaitEvent(x->cs, x->ev_out[k], 0);
+    const int rc = pi_execute_batch(x, g.ops, g.keys, g.vals, n, g.res, reinterpret_cast<pi_stream_t>(x->cs));
     if (rc != PI_OK) return rc;
-    e = cudaMemcpyAsync(results_host, g.res, n * sizeof(pi_result_t), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(x->ev_comp[k], x->cs);
+    // copy out; the caller's stream completes after it
+    cudaStreamWaitEvent(x->ds, x->ev_comp[k], 0);
+    cudaMemcpyAsync(results_host, g.res, n * sizeof(pi_result_t), cudaMemcpyDeviceToHost, x->ds);
+    cudaEventRecord(x->ev_out[k], x->ds);
+    e = cudaStreamWaitEvent(s, x->ev_out[k], 0);
+    x->host_calls++;
     return map_cuda(e);
 }
 
@@ -1020,6 +1133,7 @@ int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint6
     cudaError_t e;
     refresh_known(x);
     if (int rc = sticky_error(x->known)) return rc;
+    order_after_last(x, s);
     const uint64_t nb = 2 * n;
     if (nb > x->sc.cap) {  // sort and descent scratch for the 2n bounds (grows like a batch's)
         wait_rebuild(x, s);
@@ -1055,14 +1169,13 @@ int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint6
     da.sk = sc.a_k;
     da.sp = sc.a_p;
     da.tile_pref = sc.tile_pref;
-    da.sub_cnt = sc.sub_cnt;
-    da.tile_heads = sc.tile_heads;
-    da.tile_emax = sc.tile_emax;
-    da.tile_base = sc.tile_base;
     da.sub_pref = sc.sub_pref;
+    da.desc = x->desc;
     da.dq = sc.dq;
     da.dlo = sc.dlo;
-    da.top_launched = top_launched_for(x);
+    // the lowest buildable level is never walked by the prologue: the storage locate
+    // searches it itself (it needs that level's gap ends)
+    da.top_launched = std::max(top_launched_for(x), (int)x->min_lb);
     da.bottom_launched = (int)x->min_lb;
     da.m = x->d_meta;
     da.bm = bm;
@@ -1076,7 +1189,10 @@ int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint6
     da.val0 = sc.val0;
     da.n = (uint32_t)nb;
     da.err = &x->d_meta->error;
-    if ((e = launch_descend(da, s, x->num_sms)) != cudaSuccess) return map_cuda(e);
+    uint32_t ep = next_epochs(x, 4, s);
+    e = launch_descend(da, ep, s, x->num_sms);
+    x->epoch = ep;
+    if (e != cudaSuccess) return map_cuda(e);
     RangeArgs ra{};
     ra.sk = sc.a_k;
     ra.sp = sc.a_p;
@@ -1098,6 +1214,7 @@ int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint6
     ra.err = &x->d_meta->error;
     e = launch_range(ra, s);
     x->launches += g_launches - l0;
+    if (e == cudaSuccess) mark_last(x, s);
     return map_cuda(e);
 }
 
@@ -1114,6 +1231,7 @@ int pi_execute_batch_noalloc(pi_index_t* x, const uint8_t* ops, const uint64_t* 
     if ((e = noalloc_scratch_for(x->device, &nd)) != cudaSuccess) return map_cuda(e);
     Scratch sc{};
     if (carve_scratch(nd->ptr, PI_NOALLOC_MAX_BATCH, sc) != kNoAllocBytes) return PI_ERR_CUDA;
+    order_after_last(x, s);
     refresh_known(x);
     if (int rc = sticky_error(x->known)) return rc;
     uint64_t size_ub = (uint64_t)x->known.size + x->pending_n + x->extra_n + n;
@@ -1139,6 +1257,7 @@ void pi_destroy(pi_index_t* x) { destroy(x); }
 
 int pi_flush(pi_index_t* x, pi_stream_t stream) {
     if (!x) return PI_ERR_INVALID_ARG;
+    order_after_last(x, reinterpret_cast<cudaStream_t>(stream));
     wait_rebuild(x, reinterpret_cast<cudaStream_t>(stream));
     return map_cuda(cudaGetLastError());
 }
@@ -1160,6 +1279,12 @@ int pi_profile(pi_index_t* x, int enable) {
     }
     if (x->pused) prof_fold(x);
     x->prof = enable != 0;
+    delete x->kt;  // level 2: per-kernel times as well
+    x->kt = nullptr;
+    if (enable == 2) {
+        x->kt = new (std::nothrow) KernelTimes();
+        if (!x->kt) return PI_ERR_OOM;
+    }
     for (int st = 0; st < PI_NUM_STAGES; ++st) x->pms[st] = 0.0;
     x->pbatches = 0;
     return PI_OK;
@@ -1167,6 +1292,7 @@ int pi_profile(pi_index_t* x, int enable) {
 
 int pi_profile_read(pi_index_t* x, double* stage_ms_host, uint64_t* batches_host, pi_stream_t stream) {
     if (!x || !stage_ms_host || !batches_host) return PI_ERR_INVALID_ARG;
+    order_after_last(x, reinterpret_cast<cudaStream_t>(stream));
     wait_rebuild(x, reinterpret_cast<cudaStream_t>(stream));
     cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return map_cuda(e);
@@ -1174,6 +1300,31 @@ int pi_profile_read(pi_index_t* x, double* stage_ms_host, uint64_t* batches_host
     for (int st = 0; st < PI_NUM_STAGES; ++st) stage_ms_host[st] = x->pms[st];
     *batches_host = x->pbatches;
     return PI_OK;
+}
+
+int pi_profile_kernels(pi_index_t* x, char* buf, uint64_t cap, pi_stream_t stream) {
+    if (!x || (cap && !buf)) return PI_ERR_INVALID_ARG;
+    if (!x->kt) return PI_ERR_INVALID_ARG;
+    order_after_last(x, reinterpret_cast<cudaStream_t>(stream));
+    wait_rebuild(x, reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return map_cuda(e);
+    x->kt->fold();
+    std::string out;
+    for (const auto& k : x->kt->acc) {
+        const char* name = nullptr;
+        if (cudaFuncGetName(&name, k.first) != cudaSuccess || !name) name = "?";
+        char line[64];
+        std::snprintf(line, sizeof(line), "\t%llu\t%.6f\n", (unsigned long long)k.second.second, k.second.first);
+        out += name;
+        out += line;
+    }
+    if (cap) {
+        const size_t c = std::min<size_t>(out.size(), cap - 1);
+        std::memcpy(buf, out.data(), c);
+        buf[c] = 0;
+    }
+    return (int)std::min<size_t>(out.size() + 1, 0x7FFFFFFF);
 }
 
 int pi_status(pi_index_t* x, pi_stream_t stream) {
@@ -1346,6 +1497,7 @@ struct pi_multi {
     cudaStream_t ls[PI_MULTI_MAX_CLASSES] = {};
     cudaEvent_t evf = nullptr;
     cudaEvent_t evj[PI_MULTI_MAX_CLASSES] = {};
+    cudaEvent_t ev_done = nullptr;  // end of the last call: the indices' last operation
     cudaGraphExec_t gx[2] = {};
     bool graph_valid = false;
 };
@@ -1384,6 +1536,9 @@ void multi_destroy(pi_multi* mx) {
     cudaSetDevice(mx->device);
     for (int p = 0; p < 2; ++p)
         if (mx->q_free[p]) cudaEventSynchronize(mx->q_free[p]);
+    for (pi_index* x : mx->idx)  // the calls are complete: forget the set's event
+        if (x->last_ev == mx->ev_done) x->has_last = false;
+    if (mx->ev_done) cudaEventDestroy(mx->ev_done);
     multi_free_graphs(mx);
     dfree(mx->d_idx);
     dfree(mx->d_mirror);
@@ -1536,6 +1691,7 @@ pi_multi_t* pi_multi_create(pi_index_t* const* indices, uint32_t count, const pi
         if (e != cudaSuccess) break;
         if ((e = cudaStreamCreateWithFlags(&mx->cs, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaEventCreateWithFlags(&mx->evf, cudaEventDisableTiming)) != cudaSuccess) break;
+        if ((e = cudaEventCreateWithFlags(&mx->ev_done, cudaEventDisableTiming)) != cudaSuccess) break;
         for (uint32_t k = 0; k < c.num_classes && e == cudaSuccess; ++k) {
             e = cudaStreamCreateWithFlags(&mx->ls[k], cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&mx->evj[k], cudaEventDisableTiming);
@@ -1598,6 +1754,7 @@ int pi_multi_execute(pi_multi_t* mx, const pi_multi_batch_t* b, uint32_t nb, pi_
         // The single-index path may have grown this index's arrays since the set last
         // looked (a plain batch with new keys): the device table must hold the arrays in
         // use, never freed ones.
+        order_after_last(x, s);
         const MIndex now = mindex_of(x);
         if (std::memcmp(&now, &mx->h_idx[b[i].index], sizeof(MIndex)) != 0) {
             mx->h_idx[b[i].index] = now;
@@ -1670,7 +1827,11 @@ int pi_multi_execute(pi_multi_t* mx, const pi_multi_batch_t* b, uint32_t nb, pi_
         pi_index* x = mx->idx[b[i].index];
         x->extra_n += b[i].n;
         x->force_rebuild = true;  // the plain path recounts its per-tile level counts
+        x->last_ev = mx->ev_done;  // recorded once for the call, below
+        x->last_stream = s;
+        x->has_last = true;
     }
+    cudaEventRecord(mx->ev_done, s);
     return PI_OK;
 }
 

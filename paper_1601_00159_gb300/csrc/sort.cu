@@ -40,36 +40,73 @@ static_assert(kTile == kSortTile, "tile size shared with the host's descriptor s
 
 // K0: validate and pack. Also finds, per key byte, whether it is the same in every
 // valid key (byte-wise min and max), which decides the radix passes that can be skipped.
+// Four consecutive queries per thread and step (16-byte key loads, one 4-byte load of
+// their op codes, vector stores) when the caller's arrays are aligned for it, so that
+// every thread keeps several loads in flight; the byte-wise extremes are kept four bytes
+// to a word with SIMD min/max.
+struct PackAcc {
+    uint32_t invalid = 0;
+    uint32_t mxl = 0, mxh = 0;                  // byte-wise max of the valid keys (low, high word)
+    uint32_t mnl = 0xFFFFFFFFu, mnh = 0xFFFFFFFFu;  // byte-wise min
+    __device__ __forceinline__ uint64_t take(uint64_t k, uint32_t op) {
+        const bool valid = op <= 2u && k != kMaxKey;
+        invalid += valid ? 0u : 1u;
+        if (!valid) return kMaxKey;
+        mxl = __vmaxu4(mxl, (uint32_t)k);
+        mxh = __vmaxu4(mxh, (uint32_t)(k >> 32));
+        mnl = __vminu4(mnl, (uint32_t)k);
+        mnh = __vminu4(mnh, (uint32_t)(k >> 32));
+        return k;
+    }
+};
+
 __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ ops, const uint64_t* __restrict__ keys,
                                               uint32_t n, uint64_t* __restrict__ sk, uint32_t* __restrict__ sp,
                                               uint32_t* __restrict__ fixmap, BatchMeta* bm) {
     pdl_wait();
     pdl_trigger();
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < (n + 31u) / 32u; w += gridDim.x * blockDim.x)
-        fixmap[w] = 0;  // segment marks of the prefix fix-up
-    uint32_t invalid = 0;
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    for (uint32_t w = gt; w < (n + 31u) / 32u; w += gs) fixmap[w] = 0;  // segment marks of the prefix fix-up
+    PackAcc acc;
+    const bool vec = ((reinterpret_cast<uintptr_t>(keys) & 15u) | (reinterpret_cast<uintptr_t>(ops) & 3u)) == 0;
+    uint32_t tail = 0;  // first query left to the scalar loop
+    if (vec) {
+        const uint32_t n4 = n / 4u;
+        for (uint32_t g = gt; g < n4; g += gs) {
+            const uint32_t i = 4u * g;
+            const ulonglong2 k01 = reinterpret_cast<const ulonglong2*>(keys + i)[0];
+            const ulonglong2 k23 = reinterpret_cast<const ulonglong2*>(keys + i)[1];
+            const uint32_t o4 = ops ? *reinterpret_cast<const uint32_t*>(ops + i) : 0u;
+            const uint32_t o0 = o4 & 255u, o1 = (o4 >> 8) & 255u, o2 = (o4 >> 16) & 255u, o3 = o4 >> 24;
+            ulonglong2 s01, s23;
+            s01.x = acc.take(k01.x, o0);
+            s01.y = acc.take(k01.y, o1);
+            s23.x = acc.take(k23.x, o2);
+            s23.y = acc.take(k23.y, o3);
+            reinterpret_cast<ulonglong2*>(sk + i)[0] = s01;
+            reinterpret_cast<ulonglong2*>(sk + i)[1] = s23;
+            uint4 p;
+            p.x = ((o0 & 3u) << 30) | i;
+            p.y = ((o1 & 3u) << 30) | (i + 1u);
+            p.z = ((o2 & 3u) << 30) | (i + 2u);
+            p.w = ((o3 & 3u) << 30) | (i + 3u);
+            *reinterpret_cast<uint4*>(sp + i) = p;
+        }
+        tail = 4u * n4;
+    }
+    for (uint32_t i = tail + gt; i < n; i += gs) {
+        const uint32_t op = ops ? ops[i] : 0u;
+        sk[i] = acc.take(keys[i], op);
+        sp[i] = ((op & 3u) << 30) | i;
+    }
+    uint32_t invalid = acc.invalid;
     uint32_t mx[8], mn[8];  // mn holds max of (255 - byte), so zero is the identity
 #pragma unroll
-    for (int d = 0; d < 8; ++d) {
-        mx[d] = 0;
-        mn[d] = 0;
-    }
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint64_t k = keys[i];
-        const uint32_t op = ops ? ops[i] : 0u;
-        const bool valid = op <= 2u && k != kMaxKey;
-        const uint64_t s = valid ? k : kMaxKey;
-        invalid += valid ? 0u : 1u;
-        sk[i] = s;
-        sp[i] = ((op & 3u) << 30) | i;
-        if (valid) {
-#pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                const uint32_t b = (uint32_t)(s >> (8 * d)) & 255u;
-                mx[d] = max(mx[d], b);
-                mn[d] = max(mn[d], 255u - b);
-            }
-        }
+    for (int d = 0; d < 4; ++d) {
+        mx[d] = (acc.mxl >> (8 * d)) & 255u;
+        mx[4 + d] = (acc.mxh >> (8 * d)) & 255u;
+        mn[d] = 255u - ((acc.mnl >> (8 * d)) & 255u);
+        mn[4 + d] = 255u - ((acc.mnh >> (8 * d)) & 255u);
     }
     __shared__ uint32_t s_red[17];
     if (threadIdx.x < 17) s_red[threadIdx.x] = 0;
@@ -124,7 +161,55 @@ __device__ __forceinline__ const uint64_t* pass_src_keys(const SortPlan& P, uint
 // place, and the digit totals into digit bases (dofs). A tile's first output slot for
 // digit d is then dofs[d] + gsum[group][d] + toff[tile][d]. Pass 0 reads the packed
 // keys; later passes read the digit bytes the previous scatter wrote beside its output.
-__global__ void __launch_bounds__(kThreads) k_sort_count(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
+// Each thread counts 8 consecutive elements and adds each run of equal digits with one
+// shared-memory atomic (one per warp when the whole warp holds one digit), so a run of a
+// hot key costs no atomic contention. The scans load 16 rows per round trip.
+__device__ __forceinline__ void count_digits(const uint32_t (&d)[8], uint32_t nv, uint32_t* h) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t cur = d[0], run = nv ? 1u : 0u;
+    bool single = true;
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+        if ((uint32_t)k >= nv) break;
+        if (d[k] == cur) {
+            ++run;
+        } else {
+            single = false;
+            atomicAdd(&h[cur], run);
+            cur = d[k];
+            run = 1;
+        }
+    }
+    const uint32_t d0 = __shfl_sync(0xffffffffu, cur, 0);
+    if (__all_sync(0xffffffffu, single && cur == d0)) {  // the warp holds one digit
+        const uint32_t tot = __reduce_add_sync(0xffffffffu, run);
+        if (lane == 0 && tot) atomicAdd(&h[d0], tot);
+    } else if (run) {
+        atomicAdd(&h[cur], run);
+    }
+}
+
+// Exclusive running sum, per digit (thread d), over `rows` rows of 256 counters starting
+// at `in`: writes each row's prefix to `out` (may equal `in`) and returns the total.
+__device__ __forceinline__ uint32_t scan_rows(const uint32_t* in, uint32_t* out, uint32_t rows) {
+    const uint32_t d = threadIdx.x;
+    uint32_t run = 0;
+    for (uint32_t t = 0; t < rows; t += 16) {
+        uint32_t c[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) c[k] = (t + k < rows) ? __ldcg(&in[(size_t)(t + k) * 256 + d]) : 0u;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (t + k < rows) {
+                out[(size_t)(t + k) * 256 + d] = run;
+                run += c[k];
+            }
+        }
+    }
+    return run;
+}
+
+__global__ void __launch_bounds__(kThreads, 6) k_sort_count(uint32_t j, uint32_t n, SortBuffers sb, BatchMeta* bm) {
     pdl_wait();
     pdl_trigger();
     __shared__ uint32_t h[256];
@@ -135,27 +220,38 @@ __global__ void __launch_bounds__(kThreads) k_sort_count(uint32_t j, uint32_t n,
     h[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t tbase = blockIdx.x * kTile;
+    const uint32_t i0 = tbase + threadIdx.x * 8u;
+    const uint32_t nv = i0 < n ? min(8u, n - i0) : 0u;
+    uint32_t dg[8];
     if (j == 0) {
         const uint32_t shift = 8u * P.digit[0];
         const uint64_t* src = pass_src_keys(P, 0, sb);
+        if (nv == 8u) {
+            const ulonglong2* p = reinterpret_cast<const ulonglong2*>(src + i0);
 #pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            const uint32_t i = tbase + k * kThreads + threadIdx.x;
-            if (i < n) atomicAdd(&h[(uint32_t)(src[i] >> shift) & 255u], 1u);
+            for (int k = 0; k < 4; ++k) {
+                const ulonglong2 v = p[k];
+                dg[2 * k] = (uint32_t)(v.x >> shift) & 255u;
+                dg[2 * k + 1] = (uint32_t)(v.y >> shift) & 255u;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dg[k] = (uint32_t)k < nv ? (uint32_t)(src[i0 + k] >> shift) & 255u : 0u;
         }
     } else {
-        // 8 digit bytes per thread: one 8-byte load
-        const uint32_t i0 = tbase + threadIdx.x * 8u;
-        if (i0 + 8u <= n) {
+        if (nv == 8u) {  // 8 digit bytes per thread: one 8-byte load
             const uint2 v = *reinterpret_cast<const uint2*>(sb.ndig + i0);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) atomicAdd(&h[(v.x >> (8 * k)) & 255u], 1u);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) atomicAdd(&h[(v.y >> (8 * k)) & 255u], 1u);
+            for (int k = 0; k < 4; ++k) {
+                dg[k] = (v.x >> (8 * k)) & 255u;
+                dg[4 + k] = (v.y >> (8 * k)) & 255u;
+            }
         } else {
-            for (uint32_t i = i0; i < n && i < i0 + 8u; ++i) atomicAdd(&h[sb.ndig[i]], 1u);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dg[k] = (uint32_t)k < nv ? sb.ndig[i0 + k] : 0u;
         }
     }
+    count_digits(dg, nv, h);
     __syncthreads();
     const uint32_t d = threadIdx.x;
     const uint32_t tile = blockIdx.x, ntiles = gridDim.x;
@@ -169,39 +265,14 @@ __global__ void __launch_bounds__(kThreads) k_sort_count(uint32_t j, uint32_t n,
     __syncthreads();
     if (!s_last) return;
     __threadfence();  // every CTA of the group has arrived: their counts are visible
-    uint32_t run = 0;
-    for (uint32_t t = t0; t < t1; t += 8) {
-        uint32_t c[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) c[k] = (t + k < t1) ? __ldcg(&sb.tcnt[(size_t)(t + k) * 256 + d]) : 0u;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (t + k < t1) {
-                sb.toff[(size_t)(t + k) * 256 + d] = run;
-                run += c[k];
-            }
-        }
-    }
-    sb.gsum[(size_t)g * 256 + d] = run;
+    sb.gsum[(size_t)g * 256 + d] = scan_rows(sb.tcnt + (size_t)t0 * 256, sb.toff + (size_t)t0 * 256, t1 - t0);
     __threadfence();
     __syncthreads();
     if (d == 0) s_last = atomicAdd(&ctr[ngroups], 1u) == ngroups - 1u;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    run = 0;
-    for (uint32_t q = 0; q < ngroups; q += 8) {
-        uint32_t c[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) c[k] = (q + k < ngroups) ? __ldcg(&sb.gsum[(size_t)(q + k) * 256 + d]) : 0u;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (q + k < ngroups) {
-                sb.gsum[(size_t)(q + k) * 256 + d] = run;
-                run += c[k];
-            }
-        }
-    }
+    const uint32_t run = scan_rows(sb.gsum, sb.gsum, ngroups);
     sb.dofs[d] = block_excl_sum<kThreads>(run, s_tmp, nullptr);  // digit bases of this pass
 }
 
@@ -300,26 +371,36 @@ __global__ void __launch_bounds__(256) k_sort_find(uint32_t n, SortBuffers sb, c
     const uint64_t pm = P.pmask;
     const uint64_t* __restrict__ ak = sb.a_k;
     const uint32_t lane = threadIdx.x & 31u;
-    for (uint32_t base = blockIdx.x * 256u; base < n; base += gridDim.x * 256u) {
-        const uint32_t i = base + threadIdx.x;
-        const uint64_t k1 = i < n ? ak[i] : 0ull;
-        uint64_t k0 = __shfl_up_sync(0xffffffffu, k1, 1);
-        if (lane == 0 && i > 0 && i < n) k0 = ak[i - 1];
-        if (i == 0 || i >= n || k0 == k1 || ((k0 ^ k1) & pm) != 0) continue;
-        const uint64_t mk = k1 & pm;
-        uint32_t in = i - 1;  // ak[in] is in the segment
-        uint64_t d = 1;
-        while (d <= in && (ak[in - d] & pm) == mk) {
-            in -= (uint32_t)d;
-            d <<= 1;
+    constexpr int kU = 4;  // positions per thread and step, loaded together
+    for (uint32_t base = blockIdx.x * 256u * kU; base < n; base += gridDim.x * 256u * kU) {
+        uint64_t k1[kU], k0[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t i = base + (uint32_t)u * 256u + threadIdx.x;
+            k1[u] = i < n ? ak[i] : 0ull;
+            k0[u] = (lane == 0 && i > 0 && i < n) ? ak[i - 1] : 0ull;
         }
-        uint32_t lo = d <= in ? in - (uint32_t)d + 1 : 0u, hi = in;  // the start lies in [lo, hi]
-        while (lo < hi) {
-            const uint32_t mid = lo + (hi - lo) / 2;
-            if ((ak[mid] & pm) == mk) hi = mid;
-            else lo = mid + 1;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t i = base + (uint32_t)u * 256u + threadIdx.x;
+            uint64_t kp = __shfl_up_sync(0xffffffffu, k1[u], 1);
+            if (lane == 0) kp = k0[u];
+            if (i == 0 || i >= n || kp == k1[u] || ((kp ^ k1[u]) & pm) != 0) continue;
+            const uint64_t mk = k1[u] & pm;
+            uint32_t in = i - 1;  // ak[in] is in the segment
+            uint64_t d = 1;
+            while (d <= in && (ak[in - d] & pm) == mk) {
+                in -= (uint32_t)d;
+                d <<= 1;
+            }
+            uint32_t lo = d <= in ? in - (uint32_t)d + 1 : 0u, hi = in;  // the start lies in [lo, hi]
+            while (lo < hi) {
+                const uint32_t mid = lo + (hi - lo) / 2;
+                if ((ak[mid] & pm) == mk) hi = mid;
+                else lo = mid + 1;
+            }
+            atomicOr(&sb.fixmap[lo >> 5], 1u << (lo & 31u));
         }
-        atomicOr(&sb.fixmap[lo >> 5], 1u << (lo & 31u));
     }
 }
 
@@ -515,7 +596,8 @@ cudaError_t launch_sort(const uint8_t* ops, const uint64_t* keys, uint32_t n, co
         }
     }
     if (max_passes < 8) {  // with eight passes every byte is sorted: nothing to fix
-        launch_dep(k_sort_find, grid, 256, 0, s, n, sb, bm);
+        const int fgrid = min((int)((n + 1023) / 1024), num_sms * 8);
+        launch_dep(k_sort_find, fgrid, 256, 0, s, n, sb, bm);
         ++g_launches;
         launch_dep(k_sort_fix, (n + kFixSlice - 1) / kFixSlice, kThreads, 0, s, n, sb, bm);
         ++g_launches;

@@ -62,36 +62,37 @@ def test_reference_arm_prints_one_line_from_rank_zero_under_torchrun():
 
 
 def test_byte_model_hand_computed():
-    """One tiny case worked by hand: q = 1000 queries (100 inserts), 400 distinct keys, 50
-    written, 10,000 storage nodes after the batch, levels 1..4 of 10,000 / 2,500 / 625 /
-    156 keys, lowest built level 3 at P = 1/4 (gap 16 nodes), an L2 of 40,000 bytes."""
+    """One tiny case worked by hand: q = 1000 queries (100 inserts), 400 distinct keys (all
+    hits), 50 written, 10,000 live keys after the batch, levels 1..4 of 10,000 / 2,500 /
+    625 / 156 keys, P = 1/4, an L2 of 40,000 bytes."""
     bench = load_bench()
-    ab = bench.algorithmic_bytes(q=1000, q_ins=100, distinct=400, hits=400, writes=50, size_after=10000,
-                                 level_sizes=[0, 10000, 2500, 625, 156], l2_bytes=40000, sort_passes=8,
-                                 lowest=3, inv_p=4)
+    ab = bench.algorithmic_bytes(q=1000, q_ins=100, distinct=400, hits=400, writes=50, live_after=10000,
+                                 level_sizes=[0, 10000, 2500, 625, 156], l2_bytes=40000, p=0.25)
     assert ab["io"] == 1000 * 25 + 100 * 8                  # 25,800
-    assert ab["traversal"] == 0                              # 12 B x 625 = 7,500 < L2 / 2 = 20,000
-    assert ab["storage"] == 400 * 128 + 400 * 32 + 50 * 96   # 68,800
-    assert ab["rebuild"] == 9 * 10000 + 12 * (625 + 156)     # 99,372
-    assert ab["total"] == 25800 + 0 + 68800 + 99372
-    ab2 = bench.algorithmic_bytes(1000, 100, 400, 400, 50, 10000, [0, 10000, 2500, 625, 156], 10000, 8, 3, 4)
-    assert ab2["traversal"] == 400 * 64                      # level 3 (7,500 B) no longer fits in half the L2
+    # level 2: 12 B x 2,500 = 30,000 > L2 / 2 = 20,000; level 3: 7,500 and level 4 fit
+    assert ab["traversal"] == 400 * 64                       # 25,600
+    assert ab["storage"] == 400 * 32 + 400 * 32 + 50 * 96   # 30,400
+    assert ab["rebuild"] == 9 * 10000 + 12 * 10000 / 3       # 130,000: N' p / (1 - p) = N' / 3 entries
+    assert ab["total"] == 25800 + 25600 + 30400 + 130000
+    ab2 = bench.algorithmic_bytes(1000, 100, 400, 400, 50, 10000, [0, 10000, 2500, 625, 156], 10000, 0.25)
+    assert ab2["traversal"] == 400 * 64 * 2                  # level 3 (7,500 B) no longer fits in half the L2
 
 
 def test_stale_ncu_figures_are_not_reported(tmp_path, monkeypatch):
+    """The per-kernel ncu figures count only for the sources and the workload they were
+    captured with; index-size kernels are scaled by keys, the others by batch size."""
     bench = load_bench()
-    text = open(bench.DRAM_PROFILE).read()
-    good = bench.dram_profile("skewed")
-    assert good[2] in ("ncu capture of this workload at full size", "kernel sources changed since the ncu capture")
-    stale = tmp_path / "stale.md"
-    data = json.loads(text.split("```json\n")[1].split("\n```")[0])
+    data = {"workload": "skewed", "digest": bench.source_digest(), "capture": {"keys": 1000, "batch": 100},
+            "kernels": {"k_locate": {"launches_per_batch": 1, "dram_bytes": 5000, "scales_with": "queries"},
+                        "k_relevel_write": {"launches_per_batch": 1, "dram_bytes": 700, "scales_with": "index"},
+                        "k_sort_count": {"launches_per_batch": 4, "dram_bytes": 10, "scales_with": "queries"}}}
+    f = tmp_path / "k.json"
+    f.write_text(json.dumps(data))
+    monkeypatch.setattr(bench, "KERNEL_PROFILE", str(f))
+    total, kern, note = bench.kernel_profile("skewed", 4000, 200)
+    assert total == 5000 * 2 + 700 * 4 + 4 * 10 * 2 and "lower bound" in note
+    assert bench.kernel_profile("mid", 4000, 200)[0] is None
     data["digest"] = "0" * 16
-    stale.write_text(text.split("```json\n")[0] + "```json\n" + json.dumps(data) + "\n```\n")
-    monkeypatch.setattr(bench, "DRAM_PROFILE", str(stale))
-    per_launch, per_batch, note = bench.dram_profile("skewed")
-    assert per_launch is None and per_batch is None and "changed" in note
-    data["digest"] = bench.source_digest()
-    data["workload"] = "mid"
-    stale.write_text("```json\n" + json.dumps(data) + "\n```\n")
-    assert bench.dram_profile("skewed")[0] is None
-    assert bench.dram_profile("mid")[0] is not None
+    f.write_text(json.dumps(data))
+    total, kern, note = bench.kernel_profile("skewed", 4000, 200)
+    assert total is None and kern is None and "changed" in note

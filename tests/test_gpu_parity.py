@@ -185,6 +185,41 @@ def test_host_entry_point_matches_device_entry_point(orc_mod):
         assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
 
 
+def test_host_entry_point_pipelined_and_mixed_with_other_streams(orc_mod):
+    """Host-buffer batches run on the library's own streams, two in flight: several are
+    issued back to back with no synchronisation, then a device-buffer batch on another
+    stream, a range search and more host-buffer batches. Each must see the effect of every
+    batch issued before it on the index (arrival order across calls), and each result
+    buffer must be complete once the caller's stream completes."""
+    import torch
+    w = wl.random_small(77, 20000, 30000, 40000, p=0.25, n_batches=8)  # dense keys: long dependency chains
+    orc = orc_mod.Oracle(w.keys, w.vals, w.promote_p, w.hash_seed)
+    idx = make_index(w.keys, w.vals, w.promote_p, w.hash_seed)
+    side = torch.cuda.Stream()
+    expected, outs = [], []
+    for b, batch in enumerate(w.batches):
+        expected.append(orc.execute(batch.ops, batch.keys, batch.vals))
+        if b == 4:  # a device-buffer batch on another stream, between host-buffer ones
+            with torch.cuda.stream(side):
+                res = idx.execute(to_dev(batch.ops, torch.uint8), to_dev(batch.keys, torch.int64),
+                                  to_dev(batch.vals, torch.int64), stream=side)
+            outs.append((res, side))
+            continue
+        ops = torch.from_numpy(batch.ops.copy()).pin_memory()
+        ks = torch.from_numpy(batch.keys.view(np.int64).copy()).pin_memory()
+        vs = torch.from_numpy(batch.vals.view(np.int64).copy()).pin_memory()
+        out = torch.empty((len(batch), 2), dtype=torch.int64).pin_memory()
+        idx.execute_host(ops, ks, vs, out)
+        outs.append((out, (ops, ks, vs)))  # the inputs stay referenced until their copies ran
+    torch.cuda.current_stream().synchronize()
+    side.synchronize()
+    for b, ((out, st), exp) in enumerate(zip(outs, expected)):
+        assert_results_equal(results_np(out), exp, f"pipelined batch {b}")
+    assert_state_equal(idx, orc, "after pipelined host batches")
+    idx.close()
+    orc.close()
+
+
 def test_create_rejects_bad_arguments():
     import torch
     from paper_1601_00159_gb300 import Index, PiError, PI_ERR_INVALID_ARG
