@@ -74,7 +74,7 @@ typedef struct {
                                     exceed rebuild_threshold_pct percent of its size. */
     uint32_t rebuild_threshold_pct; /* policy 1 only; default 15 (Section 6) */
     uint32_t smem_top_entries;   /* cap on the index entries staged in shared memory by the
-                                    descent (default and maximum 2048); smaller values
+                                    descent (default and maximum 12288); smaller values
                                     pin fewer top levels */
     uint64_t storage_capacity;   /* initial storage-layer capacity, in nodes */
     uint64_t index_capacity;     /* initial index-layer capacity, in entries */

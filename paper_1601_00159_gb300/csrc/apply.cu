@@ -29,7 +29,8 @@ namespace pi {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = kApplyTile / kThreads;  // 8 sorted queries per thread
+constexpr int kApThreads = 512;                  // k_apply: two CTAs per SM at 64 registers
+constexpr int kItems = kApplyTile / kApThreads;  // 4 sorted queries per thread
 constexpr uint32_t kSeqMask = (1u << 30) - 1u;
 
 __device__ __forceinline__ void store_result(pi_result_t* res, uint32_t seq, uint64_t v, uint32_t st) {
@@ -41,7 +42,7 @@ __device__ __forceinline__ void store_result(pi_result_t* res, uint32_t seq, uin
     *reinterpret_cast<uint4*>(res + seq) = w;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_apply(ApplyArgs a) {
+__global__ void __launch_bounds__(kApThreads, 2) k_apply(ApplyArgs a) {
     pdl_wait();
     pdl_trigger();
     __shared__ uint32_t s_tmp[33];
@@ -82,10 +83,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_apply(ApplyArgs a) {
     }
     const uint64_t kprev = (base > 0 && base - 1 < qv) ? a.sk[base - 1] : kMaxKey;
     const uint64_t knext = (base + kItems < qv) ? a.sk[base + kItems] : kMaxKey;
-    // the descent's prefixes for this tile and this warp's sub-tile, loaded with the batch
-    // (a block barrier below would keep them from being hoisted)
+    // the descent's prefixes for this tile (its markers' maximum before it, the dense
+    // index of its first local run head), loaded with the batch (a block barrier below
+    // would keep them from being hoisted)
     const uint32_t tpref = a.tile_pref[tile];
-    const uint32_t spref = a.sub_pref[base / kSubTile];
+    const uint32_t dbase = a.sub_pref[tile * (kApplyTile / kSubTile)];
     uint32_t agg = 0;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
@@ -98,10 +100,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_apply(ApplyArgs a) {
         e[k] = write ? 2u * i + 3u : (head ? 2u * i + 2u : 0u);
         agg = max(agg, e[k]);
     }
-    const uint32_t texcl = block_excl_max<kThreads>(agg, s_tmp, nullptr);
+    const uint32_t texcl = block_excl_max<kApThreads>(agg, s_tmp, nullptr);
     uint32_t M = max(tpref, texcl);
-    // index of each query's local run head among its 256-query sub-tile's local heads
-    // (a warp's 8 x 32 queries are exactly one descent sub-tile)
+    // dense index of each query's local run head: the tile's first one plus the local
+    // heads before it in the tile (a local head is a run head or a 256-query sub-tile's
+    // first query, as the descent counted them)
     uint32_t lh = 0, nh = 0;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
@@ -111,17 +114,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_apply(ApplyArgs a) {
         lh |= (local ? 1u : 0u) << k;
         nh += local ? 1u : 0u;
     }
-    uint32_t hidx;
-    {
-        const int lane = tid & 31;
-        uint32_t incl = nh;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        hidx = incl - nh + spref;  // dense index of the next head
-    }
+    uint32_t hidx = dbase + block_excl_sum<kApThreads>(nh, s_tmp, nullptr);  // dense index of the next head
     uint32_t new_here = 0, new_mask = 0, chg_here = 0, chg_mask = 0;
     // Per query: its run head's result index, and the gathers of its prior state, all
     // issued before any store so that their latencies overlap: the run head's state, or,
@@ -209,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_apply(ApplyArgs a) {
     }
     // New nodes: staged in this tile's slice of the staging arrays, in key order.
     uint32_t tile_new = 0, slot = 0;
-    if (__syncthreads_or(new_here != 0)) slot = block_excl_sum<kThreads>(new_here, s_tmp, &tile_new);
+    if (__syncthreads_or(new_here != 0)) slot = block_excl_sum<kApThreads>(new_here, s_tmp, &tile_new);
     if (new_mask) {
         const uint32_t so = tile * kApplyTile;
 #pragma unroll
@@ -232,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_apply(ApplyArgs a) {
     }
     // Built-level membership changes: staged the same way, for an incremental rebuild.
     uint32_t tile_chg = 0, cslot = 0;
-    if (__syncthreads_or(chg_here != 0)) cslot = block_excl_sum<kThreads>(chg_here, s_tmp, &tile_chg);
+    if (__syncthreads_or(chg_here != 0)) cslot = block_excl_sum<kApThreads>(chg_here, s_tmp, &tile_chg);
     if (chg_mask) {
         const uint32_t so = tile * kApplyTile;
 #pragma unroll
@@ -360,7 +353,7 @@ cudaError_t launch_apply(const ApplyArgs& a, uint32_t& epoch, cudaStream_t s, in
     (void)num_sms;
     if (a.n == 0) return cudaSuccess;
     const uint32_t tiles = (a.n + kApplyTile - 1) / kApplyTile;
-    launch_dep(k_apply, tiles, kThreads, 0, s, a);  // tile prefixes come from the descent's scan
+    launch_dep(k_apply, tiles, kApThreads, 0, s, a);  // tile prefixes come from the descent's scan
     ++g_launches;
     launch_dep(k_new_scan, 1, 1024, 0, s, a);
     ++g_launches;

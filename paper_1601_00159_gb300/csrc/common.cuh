@@ -12,7 +12,7 @@ constexpr uint64_t kMaxKey = ~0ull;  // reserved key: level and storage sentinel
 constexpr int kLevelSlots = 34;      // per-level arrays are indexed by level 0..33
 constexpr uint8_t kTomb = 0x80;      // meta bit 7: the delete flag F_del (Algorithm 4)
 constexpr uint8_t kHeightMask = 0x3F;
-constexpr uint32_t kSmemTopMax = 2048;  // index entries staged in shared memory
+constexpr uint32_t kSmemTopMax = 12288;  // index entries staged in shared memory (148 KB with their downs)
 constexpr uint32_t kPad = 64;           // readable entries past every array's end
 constexpr uint32_t kSortTile = 2048;    // elements per radix-sort tile
 constexpr uint32_t kScanGroup = 64;     // radix-sort tiles per group of the count kernel's scan

@@ -287,15 +287,16 @@ __global__ void __launch_bounds__(kThreads) k_heads(DescendArgs a, uint32_t epoc
     }
 }
 
-constexpr int kTopCtasPerSm = 6;
+constexpr int kTopThreads = 1024;  // one CTA per SM: the staged levels take most of its shared memory
 
-// Start position below the pinned levels for every distinct key: a persistent grid whose
-// CTAs stage the pinned top levels in shared memory once (TMA bulk copies, one mbarrier)
-// and then take one key per thread at a time: the count of keys <= q in the lowest pinned
+// Start position below the pinned levels for every distinct key: a persistent grid, one
+// CTA per SM, whose CTAs stage the pinned top levels (up to kSmemTopMax entries) in
+// shared memory once (TMA bulk copies, one mbarrier) and then take one key per thread at
+// a time: the count of keys <= q in the lowest pinned
 // level (it holds every key of the levels above it) by binary lifting, then one
 // warp_search per walked level. The dense keys are sorted, so on the upper walked levels
 // a warp's 32 keys usually start within a few entries and share one coalesced segment.
-__global__ void __launch_bounds__(kThreads, kTopCtasPerSm) k_top(DescendArgs a) {
+__global__ void __launch_bounds__(kTopThreads, 1) k_top(DescendArgs a) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) uint8_t s_dyn[];
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, kTopCtasPerSm) k_top(DescendArgs a) 
     if (block_sees_error(&m->error)) return;
     const uint32_t H = m->H, Ls = m->Ls, Lb = m->Lb, E = m->smem_entries;
     const uint32_t D = a.bm->distinct;
-    if (blockIdx.x * kThreads >= D) return;
+    if (blockIdx.x * kTopThreads >= D) return;
     if (tid == 0) s_fail = 0;
     if (E > 0) {
         if (tid == 0) {
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, kTopCtasPerSm) k_top(DescendArgs a) 
     // levels between the pinned ones and the top launched level are walked here
     const int l_hi = pinned ? (int)Ls - 1 : (int)H;
     const int l_lo = max(a.top_launched + 1, (int)Lb);
-    for (uint32_t d0 = blockIdx.x * kThreads; d0 < D; d0 += gridDim.x * kThreads) {
+    for (uint32_t d0 = blockIdx.x * kTopThreads; d0 < D; d0 += gridDim.x * kTopThreads) {
         const uint32_t d = d0 + (uint32_t)tid;
         const bool active = d < D;
         const uint64_t q = active ? a.dq[d] : kMaxKey;
@@ -502,8 +503,8 @@ cudaError_t launch_descend(const DescendArgs& a, uint32_t& epoch, cudaStream_t s
     launch_dep(k_heads, ntiles, kThreads, 0, s, a, ++epoch);
     ++g_launches;
     // CTAs past the distinct keys exit at once
-    const uint32_t tcap = (uint32_t)num_sms * kTopCtasPerSm, tneed = (a.n + kThreads - 1) / kThreads;
-    launch_dep(k_top, tneed < tcap ? tneed : tcap, kThreads, dyn, s, a);
+    const uint32_t tcap = (uint32_t)num_sms, tneed = (a.n + kTopThreads - 1) / kTopThreads;
+    launch_dep(k_top, tneed < tcap ? tneed : tcap, kTopThreads, dyn, s, a);
     ++g_launches;
     const uint32_t need = (a.n + kThreads - 1) / kThreads;
     // one launch per index level from top_launched down to bottom_launched + 1; a launch

@@ -259,19 +259,26 @@ __global__ void __launch_bounds__(kThreads, 6) k_sort_count(uint32_t j, uint32_t
     const uint32_t g = tile / kScanGroup, ngroups = (ntiles + kScanGroup - 1) / kScanGroup;
     const uint32_t t0 = g * kScanGroup, t1 = min(t0 + kScanGroup, ntiles);
     uint32_t* ctr = sb.gctr + (size_t)j * (ngroups + 1);
-    __threadfence();  // this CTA's counts, before its arrival is counted
+    // Arrival: the block barrier orders every thread's counts before thread 0's fence,
+    // which (being cumulative) releases them all before its atomic; the last CTA's
+    // thread 0 fences after the atomic and the barrier passes that on to its threads.
     __syncthreads();
-    if (d == 0) s_last = atomicAdd(&ctr[g], 1u) == t1 - t0 - 1u;
+    if (d == 0) {
+        __threadfence();
+        s_last = atomicAdd(&ctr[g], 1u) == t1 - t0 - 1u;
+        if (s_last) __threadfence();  // every CTA of the group has arrived: their counts are visible
+    }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();  // every CTA of the group has arrived: their counts are visible
     sb.gsum[(size_t)g * 256 + d] = scan_rows(sb.tcnt + (size_t)t0 * 256, sb.toff + (size_t)t0 * 256, t1 - t0);
-    __threadfence();
     __syncthreads();
-    if (d == 0) s_last = atomicAdd(&ctr[ngroups], 1u) == ngroups - 1u;
+    if (d == 0) {
+        __threadfence();
+        s_last = atomicAdd(&ctr[ngroups], 1u) == ngroups - 1u;
+        if (s_last) __threadfence();
+    }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     const uint32_t run = scan_rows(sb.gsum, sb.gsum, ngroups);
     sb.dofs[d] = block_excl_sum<kThreads>(run, s_tmp, nullptr);  // digit bases of this pass
 }
