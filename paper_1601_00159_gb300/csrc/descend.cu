@@ -130,11 +130,13 @@ __device__ __forceinline__ void lane_scan(const uint64_t* K, const uint32_t* D, 
 }
 
 // Called by all 32 lanes. Lanes with `want` search level (K, D) from their `lo`.
-// When the searching lanes start within 8 entries of each other (the usual case on
+// When the searching lanes start within 24 entries of each other (the usual case on
 // the upper levels, since the batch is sorted), the warp loads one 32-key segment
-// with one coalesced access and each lane finds its rank in it by a five-step binary
-// search over the lanes; a lane whose answer lies past the segment, and every lane
-// when the starts are spread out (the lower levels), scans on its own.
+// from the lowest start with one coalesced access and each lane finds its rank in it by
+// a five-step binary search over the lanes (every key before a lane's start is <= its
+// q, so the rank is right from any start inside the segment); a lane whose answer lies
+// past the segment, and every lane when the starts are spread out (the lower levels),
+// scans on its own.
 template <bool kDown>
 __device__ __forceinline__ void warp_search(const uint64_t* K, const uint32_t* D, uint32_t& lo, uint32_t lim,
                                             uint64_t q, bool want, int32_t& r, uint32_t& dn, uint64_t& kr,
@@ -144,7 +146,7 @@ __device__ __forceinline__ void warp_search(const uint64_t* K, const uint32_t* D
     if (lo_min == 0xffffffffu) return;  // no lane searches this level
     const uint32_t lo_max = __reduce_max_sync(kFull, want ? lo : 0u);
     bool scan = want;
-    if (lo_max - lo_min < 8u && lo_min <= lim) {
+    if (lo_max - lo_min < 24u && lo_min <= lim) {
         const uint32_t s = lo_min;
         uint64_t seg_k = K[s + lane];
         const uint32_t seg_d = kDown ? D[s + lane] : 0u;
