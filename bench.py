@@ -75,6 +75,37 @@ def tuned_classes():
         return None
 
 
+def tuned_lowest(nodes):
+    """The batching form's tuned lowest built level for an index of `nodes` keys (its size
+    class's), or 0 (the library's automatic choice)."""
+    try:
+        with open(TUNING) as f:
+            d = json.load(f)
+        lg = max(0, int(np.ceil(np.log2(max(nodes, 1)))))
+        for hi in sorted(int(h) for h in d.get("lowest_level", {})):
+            if lg <= hi:
+                return int(d["lowest_level"][str(hi)])
+    except Exception:
+        pass
+    return 0
+
+
+PLAIN_TUNING = os.path.join(ROOT, "paper_1601_00159_gb300", "plain_tuning.json")
+
+
+def tuned_plain(keys):
+    """The plain path's tuned configuration for an index of `keys` keys: the class of the
+    nearest tuned size, or {} (defaults)."""
+    try:
+        with open(PLAIN_TUNING) as f:
+            cl = json.load(f)["classes"]
+        lg = float(np.log2(max(keys, 1)))
+        best = min(cl, key=lambda c: abs(c["log2_keys"] - lg))
+        return dict(best["chosen"]) if abs(best["log2_keys"] - lg) <= 1 else {}
+    except Exception:
+        return {}
+
+
 # The sources of the single-index batch path (the kernels a capture of the skewed
 # workload measures, and the host code that launches them).
 BATCH_PATH_SOURCES = ("common.cuh", "sort.cu", "descend.cu", "apply.cu", "rebuild.cu", "relevel.cu", "pi.cu")
@@ -401,7 +432,11 @@ def run_batching(args, ws, rank, local):
         k = torch.from_numpy(w.keys[i].view(np.int64)).to(dev)
         v = torch.from_numpy(w.vals[i].view(np.int64)).to(dev)
         cap = len(w.keys[i]) + qs[i] * total_rounds // 4 + 4096
-        idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], {"storage_capacity": cap}))
+        cfg = {"storage_capacity": cap}
+        low = tuned_lowest(len(w.keys[i]))
+        if low:
+            cfg["lowest_level"] = low
+        idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], cfg))
     create_s = time.time() - t
     classes = tuned_classes()
     ms = MultiSet(idxs, classes)
@@ -615,6 +650,26 @@ def run_serving(args, ws, rank, local):
         plat.append(time.perf_counter() - t1)
     per_req_s = time.perf_counter() - t
     per_req_value = offs[sample] / per_req_s / 1e6
+    # the plain path on batches of the size the server coalesced under the burst: the same
+    # request stream cut into batches of that many queries, through the host-buffer entry
+    # point (which overlaps one batch's copies with the next one's kernels)
+    cb = int(max(1, round(sat["mean_batch"])))
+    nb_c = max(3, min(20, int(offs[-1] // cb) - 1))
+    cops = torch.from_numpy(w.ops[:cb * (nb_c + 2)].copy()).pin_memory()
+    ckeys = torch.from_numpy(w.qkeys[:cb * (nb_c + 2)].view(np.int64).copy()).pin_memory()
+    cvals = torch.from_numpy(w.qvals[:cb * (nb_c + 2)].view(np.int64).copy()).pin_memory()
+    cres = torch.empty((cb * (nb_c + 2), 2), dtype=torch.int64).pin_memory()
+    for j in range(2):
+        idx.execute_host(cops[j * cb:(j + 1) * cb], ckeys[j * cb:(j + 1) * cb], cvals[j * cb:(j + 1) * cb],
+                         cres[j * cb:(j + 1) * cb])
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for j in range(2, nb_c + 2):
+        idx.execute_host(cops[j * cb:(j + 1) * cb], ckeys[j * cb:(j + 1) * cb], cvals[j * cb:(j + 1) * cb],
+                         cres[j * cb:(j + 1) * cb])
+    idx.flush()
+    torch.cuda.synchronize()
+    coalesced_value = nb_c * cb / (time.perf_counter() - t) / 1e6
     hbm, peak_kind = measured_peaks()
     info = idx.info()
     assert idx.status() == 0
@@ -634,6 +689,9 @@ def run_serving(args, ws, rank, local):
         "latency_50": dict(runs[0.5], load=0.5),
         "capacity": {"value": capacity, "unit": UNIT, "batches": sat["batches"], "mean_batch": sat["mean_batch"],
                      "p99_ms": sat["p99_s"] * 1e3, "note": "every request arriving at once"},
+        "plain_coalesced": {"value": coalesced_value, "unit": UNIT, "batch": cb, "batches": nb_c,
+                            "note": "pi_execute_batch_host on the request stream cut into batches of the size the "
+                                    "server coalesced under the burst (host arrays, pipelined copies)"},
         "plain_per_request": {"value": per_req_value, "unit": UNIT, "requests": sample,
                               "p50_ms": float(np.percentile(plat, 50)) * 1e3,
                               "p99_ms": float(np.percentile(plat, 99)) * 1e3,
@@ -818,6 +876,8 @@ def run_ours(args, ws, rank, local):
     cfg = {"storage_capacity": len(w.keys) + q * (total_steps + 4) if args.workload == "mid" else 0,
            "rebuild_policy": 1 if args.rebuild == "deferred" else 0}
     cfg = {k: v for k, v in cfg.items() if v}
+    tuned = tuned_plain(len(w.keys)) if args.workload == "skewed" else {}
+    cfg.update(tuned)
     torch.cuda.synchronize()
     t = time.time()
     idx = Index(keys_d, vals_d, w.promote_p, w.hash_seed, cfg or None)
@@ -964,6 +1024,7 @@ def run_ours(args, ws, rank, local):
                    "desc": spec["desc"] + ("; index rebuilt only when the updates since the last rebuild "
                                            "exceed 15% of the storage layer" if args.rebuild == "deferred" else ""),
                    "rebuild_policy": args.rebuild, "keys": len(w.keys), "batch": q,
+                   "tuned": tuned or "defaults (the tuner's choice for this size, or no table)",
                    "distinct_batches_cycled": len(dbatches), "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2_flush": "none: storage layer and cycled batch inputs exceed L2"},
         "roofline": {"bound": "hbm", "kernel": "whole batch: every kernel of one pi_execute_batch",

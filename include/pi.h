@@ -81,12 +81,23 @@ typedef struct {
     uint32_t test_flags;         /* PI_TEST_*: alternative code paths for tests; 0 in use */
     uint32_t lowest_level;       /* lowest index level to materialise, 2..16. 0: automatic,
                                     the lowest level l whose expected storage gap (1/P)^(l-1)
-                                    is at least 8 nodes (3 for P = 1/4), since on the GPU a
-                                    descent scans such a gap in one or two wide loads while
-                                    every built level costs a rebuild pass. 2 builds every
-                                    level, as the paper does. Levels below it still count in
+                                    is at least 32 nodes (4 for P = 1/4), since on the GPU the
+                                    storage search interpolates within a gap and reads about
+                                    one 64-byte line of it, while every built level costs a
+                                    rebuild pass and a descent step. 2 builds every level, as
+                                    the paper does. Levels below it still count in
                                     pi_info's level sizes; pi_export_level reports them as
                                     PI_ERR_NOT_BUILT. */
+    uint32_t sort_passes;        /* radix passes per batch. 0: automatic, four on the most
+                                    significant key bytes that vary in the batch, then an
+                                    ordering of the queries whose keys agree on those bytes
+                                    (all eight for the next batches while such queries
+                                    exceed 1/16 of a batch). 1..4: that many passes on the
+                                    most significant varying bytes, then that ordering.
+                                    8: every varying byte. Every choice gives the same
+                                    results. (Callers built against the header without this
+                                    field pass a smaller struct_size; it then reads as 0.) */
+    uint32_t reserved;           /* 0 */
 } pi_config_t;
 
 /* test_flags bit: give only the lowest index level a launch of its own in the

@@ -50,7 +50,8 @@ class PiConfig(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("rebuild_policy", ctypes.c_uint32),
                 ("rebuild_threshold_pct", ctypes.c_uint32), ("smem_top_entries", ctypes.c_uint32),
                 ("storage_capacity", ctypes.c_uint64), ("index_capacity", ctypes.c_uint64),
-                ("test_flags", ctypes.c_uint32), ("lowest_level", ctypes.c_uint32)]
+                ("test_flags", ctypes.c_uint32), ("lowest_level", ctypes.c_uint32),
+                ("sort_passes", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class PiMultiClass(ctypes.Structure):
@@ -232,7 +233,7 @@ class Index:
             raise ValueError("keys and vals differ in length")
         torch.cuda.current_stream().synchronize()
         if config:
-            cfg = PiConfig(ctypes.sizeof(PiConfig), 0, 0, 0, 0, 0, 0, 0)
+            cfg = PiConfig(ctypes.sizeof(PiConfig), 0, 0, 0, 0, 0, 0, 0, 0, 0)
             for k, v in config.items():
                 setattr(cfg, k, v)
             h = lib.pi_create_ex(keys.data_ptr(), vals.data_ptr(), keys.numel(), float(promote_p),

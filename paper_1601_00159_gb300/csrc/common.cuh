@@ -796,6 +796,8 @@ cudaError_t multi_occupancy(int warps, int radix_bits, int* blocks);
 
 // Sets the error code pi_last_error reports on this host thread.
 void set_last_error(int code);
+// Sizes an index's per-batch scratch for batches of n queries (serving runtime).
+int reserve_batch(pi_index_t* idx, uint64_t n, cudaStream_t s);
 
 // Kernels launched by this host thread (every launcher adds the launches it issues); the
 // batch entry points fold the difference into the index's own count.

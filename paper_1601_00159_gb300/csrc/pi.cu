@@ -6,6 +6,7 @@
 //   when a bound could be exceeded).
 
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -132,6 +133,7 @@ struct pi_index {
     uint32_t smem_top = kSmemTopMax;  // pinned-entry cap
     uint32_t min_lb = 2;              // lowest index level built
     uint32_t test_flags = 0;
+    uint32_t sort_cfg = 0;            // pi_config_t.sort_passes
     uint64_t launches = 0;            // kernels launched by the batch entry points
     uint32_t full_sort_left = 0;      // batches still sorted with all eight passes
     // range search: both bounds back to back, per-query storage slices and counts
@@ -584,6 +586,21 @@ cudaError_t grow_index(pi_index* x, uint64_t need, cudaStream_t s) {
     return cudaSuccess;
 }
 
+// Per-batch scratch for at least n queries (synchronises `s`: the scratch is in use until
+// the batches before have finished). It grows to 1.5 times the old capacity at least, so
+// a stream of growing batches reallocates a few times, not once per batch.
+cudaError_t grow_scratch(pi_index* x, uint64_t n, cudaStream_t s) {
+    wait_rebuild(x, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    x->rebuild_pending = false;
+    uint64_t q = std::max<uint64_t>(n, x->sc.cap + x->sc.cap / 2);
+    q = std::min<uint64_t>(std::max<uint64_t>(q, 4096), std::max<uint64_t>(n, PI_MAX_BATCH));
+    free_scratch(x->sc);
+    if ((e = alloc_scratch(x->sc, q)) != cudaSuccess) return e;
+    return ensure_desc(x, desc_need(q, x->st_cap));
+}
+
 // The descent walks the levels below the pinned ones inside its top kernel, one key
 // per thread, as long as they are small (about 24 MB of entries: L2-resident); the
 // levels below get one launch each. Taken from the host's last view of the index; any
@@ -737,6 +754,8 @@ int sort_passes(pi_index* x, uint64_t n) {
     const uint32_t forced = (x->test_flags / PI_TEST_SORT_PREFIX(1)) & 7u;
     if (forced >= 1 && forced <= 4) return (int)forced;
     if (x->test_flags & PI_TEST_SORT_FULL) return 8;
+    if (x->sort_cfg == 8) return 8;
+    const int prefix = x->sort_cfg ? (int)x->sort_cfg : 4;
     if ((uint64_t)x->known.sort_fix_big * 16u > n) {
         x->full_sort_left = 64;
         x->known.sort_fix_big = 0;  // one trigger per snapshot
@@ -745,7 +764,7 @@ int sort_passes(pi_index* x, uint64_t n) {
         --x->full_sort_left;
         return 8;
     }
-    return 4;
+    return prefix;
 }
 
 // Enqueues one batch (Algorithm 1) with the given per-batch scratch:
@@ -890,10 +909,14 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
         g_last_error = PI_ERR_INVALID_ARG;
         return nullptr;
     }
-    if (cfg && cfg->struct_size != 0 && cfg->struct_size < sizeof(pi_config_t)) {
+    // the fields up to lowest_level are required; later ones read as 0 when struct_size
+    // does not reach them (callers built against an older header)
+    constexpr size_t kCfgBase = offsetof(pi_config_t, sort_passes);
+    if (cfg && cfg->struct_size != 0 && cfg->struct_size < kCfgBase) {
         g_last_error = PI_ERR_INVALID_ARG;
         return nullptr;
     }
+    const bool cfg_full = cfg && (cfg->struct_size == 0 || cfg->struct_size >= sizeof(pi_config_t));
     pi_index* x = new (std::nothrow) pi_index();
     if (!x) {
         g_last_error = PI_ERR_OOM;
@@ -914,11 +937,23 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
         if (cfg->rebuild_threshold_pct) x->threshold_pct = cfg->rebuild_threshold_pct;
         if (cfg->smem_top_entries && cfg->smem_top_entries < kSmemTopMax) x->smem_top = cfg->smem_top_entries;
         x->test_flags = cfg->test_flags;
+        if (cfg_full) {
+            const uint32_t sp = cfg->sort_passes;
+            if (sp > 8 || (sp > 4 && sp < 8)) {
+                g_last_error = PI_ERR_INVALID_ARG;
+                delete x;
+                return nullptr;
+            }
+            x->sort_cfg = sp;
+        }
     }
     // Lowest index level: the lowest l whose expected storage gap 2^(b (l - 1)) is at
-    // least 8 nodes, unless the caller picks one.
+    // least 32 nodes, unless the caller picks one. The storage search interpolates within
+    // the gap, so a wide gap costs about one 64-byte line, while every built level costs
+    // rebuild work and a descent step; the autotuner measured level 4 fastest at P = 1/4
+    // (64-node gaps) for indices of 2^24 to 2^27 keys.
     x->min_lb = 2;
-    while ((uint32_t)b * (x->min_lb - 1) < 3u) ++x->min_lb;
+    while ((uint32_t)b * (x->min_lb - 1) < 5u) ++x->min_lb;
     if (cfg && cfg->lowest_level) {
         if (cfg->lowest_level < 2 || cfg->lowest_level > 16) {
             g_last_error = PI_ERR_INVALID_ARG;
@@ -1044,15 +1079,7 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
     refresh_known(x);
     if (int rc = sticky_error(x->known)) return rc;
     // capacities (grow rarely; growing synchronises the stream)
-    if (n > x->sc.cap) {
-        wait_rebuild(x, s);
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
-        x->rebuild_pending = false;
-        free_scratch(x->sc);
-        uint64_t q = n < 4096 ? 4096 : n;
-        if ((e = alloc_scratch(x->sc, q)) != cudaSuccess) return map_cuda(e);
-        if ((e = ensure_desc(x, desc_need(q, x->st_cap))) != cudaSuccess) return map_cuda(e);
-    }
+    if (n > x->sc.cap && (e = grow_scratch(x, n, s)) != cudaSuccess) return map_cuda(e);
     uint64_t size_ub = (uint64_t)x->known.size + x->pending_n + x->extra_n + n;
     if (size_ub > x->st_cap) {
         if ((e = sync_known(x, s)) != cudaSuccess) return map_cuda(e);
@@ -1135,15 +1162,8 @@ int pi_range_search(pi_index_t* x, const uint64_t* lo, const uint64_t* hi, uint6
     if (int rc = sticky_error(x->known)) return rc;
     order_after_last(x, s);
     const uint64_t nb = 2 * n;
-    if (nb > x->sc.cap) {  // sort and descent scratch for the 2n bounds (grows like a batch's)
-        wait_rebuild(x, s);
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
-        x->rebuild_pending = false;
-        free_scratch(x->sc);
-        const uint64_t q = nb < 4096 ? 4096 : nb;
-        if ((e = alloc_scratch(x->sc, q)) != cudaSuccess) return map_cuda(e);
-        if ((e = ensure_desc(x, desc_need(q, x->st_cap))) != cudaSuccess) return map_cuda(e);
-    }
+    // sort and descent scratch for the 2n bounds (grows like a batch's)
+    if (nb > x->sc.cap && (e = grow_scratch(x, nb, s)) != cudaSuccess) return map_cuda(e);
     if (n > x->r_cap) {
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
         dfree(x->r_bounds); dfree(x->r_start); dfree(x->r_end); dfree(x->r_cnt); dfree(x->r_bsum);
@@ -1843,4 +1863,13 @@ void pi_multi_destroy(pi_multi_t* mx) { multi_destroy(mx); }
 
 namespace pi {
 void set_last_error(int code) { g_last_error = code; }
+
+// Makes the index's per-batch scratch hold batches of n queries (the serving runtime
+// sizes it for its largest coalesced batch up front). Synchronises `s`.
+int reserve_batch(pi_index* x, uint64_t n, cudaStream_t s) {
+    if (!x || n > PI_MAX_BATCH) return PI_ERR_INVALID_ARG;
+    order_after_last(x, s);
+    if (n <= x->sc.cap) return PI_OK;
+    return map_cuda(grow_scratch(x, n, s));
+}
 }  // namespace pi

@@ -368,6 +368,12 @@ pi_server_t* pi_server_create(pi_index_t* idx, const pi_server_config_t* cfg) {
         if ((e = cudaStreamCreateWithFlags(&s->ds, cudaStreamNonBlocking)) != cudaSuccess) break;
         // the index's earlier work (on the legacy default stream or elsewhere) is done first
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) break;
+        // the index's per-batch scratch, sized for the largest coalesced batch now: growing
+        // it later synchronises and reallocates in the middle of the first bursts
+        if (pi::reserve_batch(idx, s->max_batch, s->cs) != PI_OK) {
+            e = cudaErrorMemoryAllocation;
+            break;
+        }
     } while (0);
     if (e != cudaSuccess) {
         pi::set_last_error(map_err(e));
@@ -483,7 +489,7 @@ int pi_server_replay(pi_server_t* s, const uint8_t* ops, const uint64_t* keys, c
         uint64_t ticket;
         std::vector<uint64_t> pos;
     };
-    const uint32_t nhelp = std::max(1u, std::min(4u, std::thread::hardware_concurrency() / 4));
+    const uint32_t nhelp = std::max(1u, std::min(8u, std::thread::hardware_concurrency() / 2));
     std::vector<std::deque<Job>> jobs(nhelp);
     std::mutex jmu;
     std::condition_variable jcv;

@@ -57,7 +57,7 @@ def make_batch(seed, keys, q):
     return wl.Batch(ops.astype(np.uint8), bkeys.astype(np.uint64), wl.u64_stream(s, 3 * q, q))
 
 
-def build_set(orc_mod, seed, count, lo_log, hi_log, big=None):
+def build_set(orc_mod, seed, count, lo_log, hi_log, big=None, configs=None):
     sizes = log_uniform(seed, 1, count, lo_log, hi_log)
     if big:
         sizes[0] = big
@@ -66,7 +66,7 @@ def build_set(orc_mod, seed, count, lo_log, hi_log, big=None):
         keys = wl.distinct_keys(seed * 1000 + i, np.arange(int(n)))
         vals = wl.splitmix64(keys)
         hs = int(wl.stream_seed(seed, 500 + i))
-        idxs.append(make_index(keys, vals, 0.25, hs))
+        idxs.append(make_index(keys, vals, 0.25, hs, (configs or {}).get(i)))
         orcs.append(orc_mod.Oracle(keys, vals, 0.25, hs))
         keysets.append(keys)
     return idxs, orcs, keysets
@@ -143,7 +143,9 @@ def test_multi_after_the_plain_path_grew_an_index(orc_mod):
     from paper_1601_00159_gb300 import MultiSet
     from tests.parity import run_batch
     seed = 29
-    idxs, orcs, keysets = build_set(orc_mod, seed, 6, 4, 12)
+    # index 2 builds every level (lowest level 2), so the burst of new keys below also
+    # outgrows its index layer's capacity
+    idxs, orcs, keysets = build_set(orc_mod, seed, 6, 4, 12, configs={2: {"lowest_level": 2}})
     ms = MultiSet(idxs)
     run_rounds(ms, idxs, orcs, keysets, seed, 1, 0, 10)
     cap0 = idxs[2].info()["storage_capacity"]
