@@ -460,7 +460,8 @@ def run_batching(args, ws, rank, local):
                  res[offs[i]:offs[i + 1]]) for i in range(count)]
 
     stream = torch.cuda.current_stream()
-    step_descs = [descs(*dr, results) for dr in dev_rounds]
+    # descriptor arrays built (and checked) once per round, outside the timed region
+    step_descs = [ms.prepare(descs(*dr, results)) for dr in dev_rounds]
     for s_ in range(args.warmup):
         ms.execute(step_descs[s_ % timed_rounds])
     torch.cuda.synchronize()
@@ -509,7 +510,7 @@ def run_batching(args, ws, rank, local):
     hres = torch.empty((qtot, 2), dtype=torch.int64).pin_memory()
     dbuf = [torch.empty(qtot, dtype=torch.uint8, device=dev), torch.empty(qtot, dtype=torch.int64, device=dev),
             torch.empty(qtot, dtype=torch.int64, device=dev)]
-    e2e_descs = descs(dbuf[0], dbuf[1], dbuf[2], results)
+    e2e_descs = ms.prepare(descs(dbuf[0], dbuf[1], dbuf[2], results))
     for s_ in range(2):
         for j in range(3):
             dbuf[j].copy_(hp[s_][j])
@@ -856,11 +857,16 @@ def run_ours(args, ws, rank, local):
     if args.batch_log2:
         kw["q"] = 1 << args.batch_log2
     n_distinct_batches = 1 if args.workload == "tiny" else min(args.steps + args.warmup, args.batches)
+    # the stage profile runs on further batches after the timed region: the mid workload's
+    # inserts must be new keys there too, so it gets batches of its own
+    prof_steps = min(args.steps, 16)
+    n_prof_batches = prof_steps if args.workload == "mid" else 0
     if args.workload in ("mid", "skewed"):
-        kw["n_batches"] = max(n_distinct_batches, 2)
+        kw["n_batches"] = max(n_distinct_batches + n_prof_batches, 2)
     w = spec["fn"](**kw)
     gen = w.batches() if callable(w.batches) else iter(w.batches)
     host_batches = [next(gen) for _ in range(n_distinct_batches)]
+    prof_host = [next(gen) for _ in range(n_prof_batches)]
     gen_s = time.time() - t_gen
     q = len(host_batches[0])
 
@@ -873,7 +879,7 @@ def run_ours(args, ws, rank, local):
     keys_d = torch.from_numpy(w.keys.view(np.int64)).to(dev)
     vals_d = torch.from_numpy(w.vals.view(np.int64)).to(dev)
     total_steps = args.warmup + args.steps
-    cfg = {"storage_capacity": len(w.keys) + q * (total_steps + 4) if args.workload == "mid" else 0,
+    cfg = {"storage_capacity": len(w.keys) + q * (total_steps + n_prof_batches + 4) if args.workload == "mid" else 0,
            "rebuild_policy": 1 if args.rebuild == "deferred" else 0}
     cfg = {k: v for k, v in cfg.items() if v}
     tuned = tuned_plain(len(w.keys)) if args.workload == "skewed" else {}
@@ -891,7 +897,6 @@ def run_ours(args, ws, rank, local):
         idx.execute(o, k, v, results)
     torch.cuda.synchronize()
     info0 = idx.info()
-    idx.profile(True)
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -905,9 +910,21 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
     barrier(ws)
     ms_total = ev0.elapsed_time(ev1)
-    stage_ms, nb = idx.profile_read()  # stage times exclude the wait for the previous rebuild
-    idx.profile(False)
     info1 = idx.info()
+    routed = info1["routed_batches"] - info0["routed_batches"]
+    # Stage times on further batches after the timed region (the events between stages
+    # cost host time; a profiled batch also keeps the level-synchronous pipeline, so a run
+    # whose batches took the small-batch route reports none).
+    stage_ms, nb = {}, 0
+    if routed < args.steps:
+        prof_batches = [dev_batch(b) for b in prof_host] or dbatches
+        idx.profile(True)
+        for s in range(prof_steps):
+            o, k, v = prof_batches[(s if prof_host else args.warmup + args.steps + s) % len(prof_batches)]
+            idx.execute(o, k, v, results)
+        idx.flush(stream)
+        stage_ms, nb = idx.profile_read()  # stage times exclude the wait for the previous rebuild
+        idx.profile(False)
     kernel_ms = None
     if args.kernel_times:
         # per-kernel times on extra batches after the timed region (events around every
@@ -996,7 +1013,7 @@ def run_ours(args, ws, rank, local):
     trav_levels = [l for l in range(2, lowest + 1) if sizes[l] and 12 * sizes[l] > l2_bytes / 2]
     loc_per_key = 64 * len(trav_levels) + 32 + 32 + 25
     loc_bytes = distinct * loc_per_key
-    loc_ms = per_stage["locate"]
+    loc_ms = per_stage.get("locate")
     loc_traffic = None
     if kprof and "k_locate" in kprof:
         kl = kprof["k_locate"]
@@ -1004,7 +1021,7 @@ def run_ours(args, ws, rank, local):
     # The rebuild's writer: the incremental one reads and writes each built entry (8 B key
     # + 4 B down) once; the full one scans the storage layer's keys and meta and writes
     # every built entry.
-    writer_ms = per_stage["rebuild_write"]
+    writer_ms = per_stage.get("rebuild_write")
     inc_region = info1["incremental_rebuilds"] - info0["incremental_rebuilds"]
     rebuilds_region = info1["rebuilds"] - info0["rebuilds"]
     entries = sum(sizes[lowest:])
@@ -1042,15 +1059,17 @@ def run_ours(args, ws, rank, local):
                                     "(from 2) too large for L2; 32 B key sector per distinct key, 32 B value "
                                     "sector per hit, 96 B per written key; full rebuild 9 N' + 12 N' p/(1-p)",
                      "distinct_keys_per_batch": distinct, "written_keys_per_batch": writes,
-                     "k_locate": {"ms_per_launch": loc_ms, "share_of_step": loc_ms / ms_step,
-                                  "algorithmic_bytes_per_launch": loc_bytes,
-                                  "achieved": loc_bytes / (loc_ms * 1e-3) / 1e9,
-                                  "frac": loc_bytes / (loc_ms * 1e-3) / 1e9 / hbm,
-                                  "traffic": loc_traffic,
-                                  "bytes_model": f"{loc_per_key} B per distinct key: key and down sectors "
-                                                 f"(64 B) on levels {trav_levels}, storage key and value "
-                                                 "sectors (32 B each), 25 B streamed",
-                                  "lowest_built_level": lowest}},
+                     "k_locate": ({"ms_per_launch": loc_ms, "share_of_step": loc_ms / ms_step,
+                                   "algorithmic_bytes_per_launch": loc_bytes,
+                                   "achieved": loc_bytes / (loc_ms * 1e-3) / 1e9,
+                                   "frac": loc_bytes / (loc_ms * 1e-3) / 1e9 / hbm,
+                                   "traffic": loc_traffic,
+                                   "bytes_model": f"{loc_per_key} B per distinct key: key and down sectors "
+                                                  f"(64 B) on levels {trav_levels}, storage key and value "
+                                                  "sectors (32 B each), 25 B streamed",
+                                   "lowest_built_level": lowest} if loc_ms else
+                                  {"note": "no k_locate launch: every timed batch took the small-batch "
+                                           "route (one thread-block-cluster launch)"})},
         "rebuild_writer": {"kernel": wkernel, "ms_per_launch": writer_ms,
                            "algorithmic_bytes_per_launch": wbytes, "bytes_model": wmodel,
                            "achieved_gbs": wbytes / (writer_ms * 1e-3) / 1e9 if writer_ms else None,
@@ -1064,6 +1083,7 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": q * 17, "d2h_bytes_per_step": q * 16,
                 "steps": e2e_steps, "index": "fresh, same batch sequence" if fresh else "the timed index"},
         "gpu_launches": info1["kernel_launches"] - info0["kernel_launches"],
+        "routed_batches": routed,
         "clocks": clk.summary(),
         "index": {"size": info1["size"], "live": info1["live"], "tombstones": info1["tombstones"],
                   "top_level": info1["top_level"], "rebuilds_in_region": info1["rebuilds"] - info0["rebuilds"],

@@ -97,7 +97,14 @@ typedef struct {
                                     8: every varying byte. Every choice gives the same
                                     results. (Callers built against the header without this
                                     field pass a smaller struct_size; it then reads as 0.) */
-    uint32_t reserved;           /* 0 */
+    uint32_t small_batches;      /* 0: automatic. A batch of at most 2^16 queries on an index
+                                    of at most 2^20 nodes (its new keys included) runs as one
+                                    launch: the batching form's pipeline on a thread-block
+                                    cluster of 16 CTAs (8 where 16 do not fit), with the same
+                                    results as the level-synchronous pipeline, which needs
+                                    tens of dependent launches. Not taken while profiling,
+                                    with test_flags or with the deferred rebuild policy.
+                                    1: every batch takes the level-synchronous pipeline. */
 } pi_config_t;
 
 /* test_flags bit: give only the lowest index level a launch of its own in the
@@ -237,6 +244,8 @@ typedef struct {
     uint64_t incremental_rebuilds; /* rebuilds that updated the previous levels (no storage
                                       re-layout) rather than scanning the storage layer */
     uint64_t owner_checked_writes; /* PI_TEST_OWNER_CHECK: storage-node writes checked */
+    uint64_t routed_batches; /* batches that took the small-batch route (one cluster
+                                launch each; pi_config_t.small_batches) */
 } pi_info_t;
 int pi_info(pi_index_t* idx, pi_info_t* out_host, pi_stream_t stream);
 
@@ -328,8 +337,9 @@ int pi_range_search(pi_index_t* idx, const uint64_t* lo, const uint64_t* hi, uin
 /*
  * ---------------------------------------------------------------------------------
  * Batching form: one batch for each of many independent indices in one persistent
- * launch. Algorithm 1 runs for every index of the set at once: each CTA takes a batch
- * from a device-side queue (largest first) and runs its whole pipeline. The result of
+ * launch. Algorithm 1 runs for every index of the set at once: each CTA (or, for a size
+ * class configured so, each thread-block cluster) takes a batch from a device-side queue
+ * (largest first) and runs its whole pipeline. The result of
  * every batch is exactly what pi_execute_batch gives for it (Section 4.2: arrival-order
  * semantics per index); the indices stay usable by every single-index entry point.
  * The paper runs one index per NUMA node (Section 4.4.1); many small indices in one
@@ -339,12 +349,15 @@ typedef struct pi_multi pi_multi_t;
 
 /* Kernel configuration of one size class: indices whose storage layer has at most
  * 2^max_log2_size nodes take CTAs of `warps` warps (8, 16 or 32) and radix digits of
- * `radix_bits` bits (4 or 8). */
+ * `radix_bits` bits (4 or 8). `cluster` is the number of CTAs that share one batch:
+ * 0 or 1 gives each batch one CTA; 2, 4, 8 or 16 give it a thread-block cluster of
+ * that many CTAs (on as many SMs), which splits every stage of the batch into one span
+ * per CTA and needs warps = 32 and radix_bits = 8. */
 typedef struct {
     uint32_t max_log2_size;
     uint32_t warps;
     uint32_t radix_bits;
-    uint32_t reserved;
+    uint32_t cluster;
 } pi_multi_class_t;
 
 #define PI_MULTI_MAX_CLASSES 4

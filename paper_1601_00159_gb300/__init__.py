@@ -51,12 +51,12 @@ class PiConfig(ctypes.Structure):
                 ("rebuild_threshold_pct", ctypes.c_uint32), ("smem_top_entries", ctypes.c_uint32),
                 ("storage_capacity", ctypes.c_uint64), ("index_capacity", ctypes.c_uint64),
                 ("test_flags", ctypes.c_uint32), ("lowest_level", ctypes.c_uint32),
-                ("sort_passes", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("sort_passes", ctypes.c_uint32), ("small_batches", ctypes.c_uint32)]
 
 
 class PiMultiClass(ctypes.Structure):
     _fields_ = [("max_log2_size", ctypes.c_uint32), ("warps", ctypes.c_uint32),
-                ("radix_bits", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("radix_bits", ctypes.c_uint32), ("cluster", ctypes.c_uint32)]
 
 
 class PiMultiConfig(ctypes.Structure):
@@ -88,7 +88,8 @@ class PiInfo(ctypes.Structure):
                 ("level_size", ctypes.c_uint64 * 34), ("storage_capacity", ctypes.c_uint64),
                 ("index_capacity", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("rebuilds", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("incremental_rebuilds", ctypes.c_uint64), ("owner_checked_writes", ctypes.c_uint64)]
+                ("incremental_rebuilds", ctypes.c_uint64), ("owner_checked_writes", ctypes.c_uint64),
+                ("routed_batches", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "level_size"}
@@ -404,9 +405,17 @@ class Index:
             pass
 
 
+class _Prepared:
+    """A checked descriptor array for MultiSet.execute (from MultiSet.prepare)."""
+
+    def __init__(self, arr, count, refs):
+        self.arr, self.count, self._refs = arr, count, refs
+
+
 class MultiSet:
     """A set of indices run one batch each per call (pi_multi_create / pi_multi_execute).
-    classes: list of (max_log2_size, warps, radix_bits), or None for the built-in table."""
+    classes: list of (max_log2_size, warps, radix_bits[, cluster]), or None for the
+    built-in table; cluster > 1 gives each batch of the class that many CTAs."""
 
     def __init__(self, indices, classes=None):
         lib = load_library()
@@ -417,8 +426,9 @@ class MultiSet:
             cfg = PiMultiConfig()
             cfg.struct_size = ctypes.sizeof(PiMultiConfig)
             cfg.num_classes = len(classes)
-            for i, (lg, w, b) in enumerate(classes):
-                cfg.cls[i] = PiMultiClass(lg, w, b, 0)
+            for i, c in enumerate(classes):
+                lg, w, b = c[:3]
+                cfg.cls[i] = PiMultiClass(lg, w, b, c[3] if len(c) > 3 else 0)
             cfgp = ctypes.byref(cfg)
         h = lib.pi_multi_create(arr, len(self.indices), cfgp)
         if not h:
@@ -426,9 +436,10 @@ class MultiSet:
         self._h = ctypes.c_void_p(h)
         self.lib = lib
 
-    def execute(self, batches, stream=None):
-        """batches: list of (index position, ops u8, keys i64, vals i64, results i64[n, 2]) with
-        CUDA tensors; results are written in place (value bits, status)."""
+    def prepare(self, batches):
+        """The descriptor array of a list of batches (see execute), checked once, for calls
+        that reuse it: pi_multi_execute reads the descriptors only during the call. The
+        result keeps the tensors referenced."""
         import torch
         arr = (PiMultiBatch * len(batches))()
         for i, (ix, ops, keys, vals, res) in enumerate(batches):
@@ -440,7 +451,14 @@ class MultiSet:
             if keys.numel() != n or vals.numel() != n or res.numel() != 2 * n:
                 raise ValueError("batch arrays differ in length")
             arr[i] = PiMultiBatch(ix, 0, ops.data_ptr(), keys.data_ptr(), vals.data_ptr(), n, res.data_ptr())
-        _chk(self.lib.pi_multi_execute(self._h, arr, len(batches), _stream_handle(stream)), "pi_multi_execute")
+        return _Prepared(arr, len(batches), list(batches))
+
+    def execute(self, batches, stream=None):
+        """batches: list of (index position, ops u8, keys i64, vals i64, results i64[n, 2]) with
+        CUDA tensors, or the result of prepare(); results are written in place (value bits,
+        status)."""
+        p = batches if isinstance(batches, _Prepared) else self.prepare(batches)
+        _chk(self.lib.pi_multi_execute(self._h, p.arr, p.count, _stream_handle(stream)), "pi_multi_execute")
 
     def kernels_per_call(self) -> int:
         return int(self.lib.pi_multi_kernels_per_call(self._h))

@@ -2,7 +2,8 @@
 
 Batching form (default mode): pi_multi_execute runs each size class of indices with its
 own persistent kernel. This mode times every variant -- 8, 16 or 32 warps per index, 4-
-or 8-bit radix digits -- on the indices of each class of the batching workload, then the
+or 8-bit radix digits, and for 32 warps with 8-bit digits thread-block clusters of 2, 4,
+8 or 16 CTAs per batch -- on the indices of each class of the batching workload, then the
 node fan-out of each class (the lowest built index level, i.e. the storage nodes one
 entry of the lowest level spans), and writes the fastest per class to multi_tuning.json
 beside it, which bench.py and MultiSet callers pass to pi_multi_create / pi_create_ex.
@@ -29,7 +30,19 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "multi_tuning.json")
 PLAIN_OUT = os.path.join(HERE, "plain_tuning.json")
 BOUNDS = [14, 17, 32]  # class upper bounds (log2 of the storage size)
-VARIANTS = [(w, b) for w in (8, 16, 32) for b in (4, 8)]
+VARIANTS = [(w, b, 1) for w in (8, 16, 32) for b in (4, 8)] + [(32, 8, c) for c in (2, 4, 8, 16)]
+
+
+def kernel_name(v):
+    """'32x8' for one CTA per batch, '32x8c4' for clusters of 4 CTAs."""
+    w, b, c = v
+    return f"{w}x{b}" + (f"c{c}" if c > 1 else "")
+
+
+def parse_kernel(name):
+    wb, _, c = name.partition("c")
+    w, b = (int(x) for x in wb.split("x"))
+    return (w, b, int(c) if c else 1)
 
 
 def variant_name(cfg):
@@ -127,7 +140,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--calls", type=int, default=8)
     ap.add_argument("--out", default=OUT)
-    ap.add_argument("--only", default="", help="time one variant, e.g. 32x8 (profiling runs)")
+    ap.add_argument("--only", default="", help="time one variant, e.g. 32x8 or 32x8c8 (profiling runs)")
     ap.add_argument("--plain", action="store_true", help="tune the plain path instead of the batching form")
     ap.add_argument("--sizes", type=int, nargs="*", default=[24, 26, 27], help="--plain: log2 index sizes")
     ap.add_argument("--plain-out", default=PLAIN_OUT)
@@ -136,8 +149,7 @@ def main():
         return tune_plain(args)
     variants = VARIANTS
     if args.only:
-        wv, bv = (int(x) for x in args.only.split("x"))
-        variants = [(wv, bv)]
+        variants = [parse_kernel(args.only)]
     build.build()
     load_library()
     dev = torch.device("cuda")
@@ -155,21 +167,21 @@ def main():
         members = [i for i in range(len(sizes)) if lo < lg[i] <= hi]
         lo = hi
         if not members:
-            chosen.append((hi, 16, 8))
+            chosen.append((hi, 16, 8, 1))
             continue
         batches = [[(torch.from_numpy(rd[i].ops).to(dev), torch.from_numpy(rd[i].keys.view(np.int64)).to(dev),
                      torch.from_numpy(rd[i].vals.view(np.int64)).to(dev),
                      torch.empty((len(rd[i]), 2), dtype=torch.int64, device=dev)) for i in members] for rd in rounds]
         timings = {}
-        for (wp, bits) in variants:
+        for var in variants:
             idxs = []
             for i in members:
                 k = torch.from_numpy(w.keys[i].view(np.int64)).to(dev)
                 v = torch.from_numpy(w.vals[i].view(np.int64)).to(dev)
                 cap = len(w.keys[i]) + len(rnd[i]) * (nr + 4)
                 idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], {"storage_capacity": cap}))
-            ms = MultiSet(idxs, [(32, wp, bits)])
-            descs = [[(j, *bj[j]) for j in range(len(members))] for bj in batches]
+            ms = MultiSet(idxs, [(32, *var)])
+            descs = [ms.prepare([(j, *bj[j]) for j in range(len(members))]) for bj in batches]
             for r in range(2):
                 ms.execute(descs[r])
             torch.cuda.synchronize()
@@ -179,13 +191,12 @@ def main():
                 ms.execute(descs[2 + r])
             e1.record()
             torch.cuda.synchronize()
-            timings[f"{wp}x{bits}"] = e0.elapsed_time(e1) / args.calls
+            timings[kernel_name(var)] = e0.elapsed_time(e1) / args.calls
             ms.close()
             for ix in idxs:
                 ix.close()
         best = min(timings, key=timings.get)
-        wp, bits = (int(x) for x in best.split("x"))
-        chosen.append((hi, wp, bits))
+        chosen.append((hi, *parse_kernel(best)))
         table[f"class{c} (log2 size <= {hi}, {len(members)} indices)"] = timings
         print(f"class {c}: {len(members)} indices, ms per call {timings} -> {best}", flush=True)
     # The classes run concurrently in one call and share the SMs, so the per-class winners
@@ -197,14 +208,14 @@ def main():
         tops = []
         for c, hi in enumerate(BOUNDS):
             key = next((k for k in table if k.startswith(f"class{c} ")), None)
-            ranked = sorted(table[key], key=table[key].get)[:2] if key else [f"{chosen[c][1]}x{chosen[c][2]}"]
-            tops.append([tuple(int(x) for x in r.split("x")) for r in ranked])
+            ranked = sorted(table[key], key=table[key].get)[:2] if key else [kernel_name(chosen[c][1:])]
+            tops.append([parse_kernel(r) for r in ranked])
         all_batches = [[(i, torch.from_numpy(b.ops).to(dev), torch.from_numpy(b.keys.view(np.int64)).to(dev),
                          torch.from_numpy(b.vals.view(np.int64)).to(dev),
                          torch.empty((len(b), 2), dtype=torch.int64, device=dev)) for i, b in enumerate(rd)]
                        for rd in rounds]
         for combo in itertools.product(*tops):
-            cls = [(BOUNDS[c], combo[c][0], combo[c][1]) for c in range(len(BOUNDS))]
+            cls = [(BOUNDS[c], *combo[c]) for c in range(len(BOUNDS))]
             idxs = []
             for i in range(len(sizes)):
                 k = torch.from_numpy(w.keys[i].view(np.int64)).to(dev)
@@ -212,13 +223,14 @@ def main():
                 cap = len(w.keys[i]) + len(rnd[i]) * (nr + 4)
                 idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], {"storage_capacity": cap}))
             ms = MultiSet(idxs, cls)
+            prepared = [ms.prepare(b) for b in all_batches]
             for r in range(2):
-                ms.execute(all_batches[r])
+                ms.execute(prepared[r])
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for r in range(args.calls):
-                ms.execute(all_batches[2 + r])
+                ms.execute(prepared[2 + r])
             e1.record()
             torch.cuda.synchronize()
             joint[json.dumps(cls)] = e0.elapsed_time(e1) / args.calls
@@ -253,14 +265,15 @@ def main():
                 if low:
                     cfg["lowest_level"] = low
                 idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], cfg))
-            ms = MultiSet(idxs, [(32, chosen[c][1], chosen[c][2])])
+            ms = MultiSet(idxs, [(32, *chosen[c][1:])])
+            prepared = [ms.prepare(b) for b in batches]
             for r in range(2):
-                ms.execute(batches[r])
+                ms.execute(prepared[r])
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for r in range(args.calls):
-                ms.execute(batches[2 + r])
+                ms.execute(prepared[2 + r])
             e1.record()
             torch.cuda.synchronize()
             times[f"lowest_level={low or 'auto'}"] = e0.elapsed_time(e1) / args.calls

@@ -791,8 +791,11 @@ struct RangeArgs {
 cudaError_t launch_range(const RangeArgs& a, cudaStream_t s);
 
 uint64_t multi_scratch_bytes(uint32_t qcap);
-cudaError_t launch_multi(const MultiArgs& a, int warps, int radix_bits, uint32_t grid, cudaStream_t s);
-cudaError_t multi_occupancy(int warps, int radix_bits, int* blocks);
+// A kernel variant: warps per CTA, radix digit bits, CTAs per batch (cluster; <= 1: one).
+bool multi_variant_ok(int warps, int radix_bits, int cluster);
+cudaError_t launch_multi(const MultiArgs& a, int warps, int radix_bits, int cluster, uint32_t grid, cudaStream_t s);
+// The variant's largest resident grid in CTAs (sets its shared-memory limit first).
+cudaError_t multi_grid(int warps, int radix_bits, int cluster, int num_sms, uint32_t* grid);
 
 // Sets the error code pi_last_error reports on this host thread.
 void set_last_error(int code);

@@ -182,6 +182,12 @@ struct pi_index {
     uint64_t pending_n = 0;  // queries issued after that snapshot
     uint64_t extra_n = 0;    // queries of batching-form calls since the last full sync
     bool force_rebuild = false;
+    // Small batches (Q <= kSmallBatch on at most kSmallIndex nodes) run through a one-index
+    // batching set whose batch takes a thread-block cluster: one launch instead of the
+    // level-synchronous pipeline's tens. Created on first use; small_mode 1 turns it off.
+    pi_multi* small = nullptr;
+    uint32_t small_mode = 0;
+    uint64_t routed = 0;  // batches that took the route
     // stage timing (pi_profile): events recorded between the pipeline's kernels
     bool prof = false;
     KernelTimes* kt = nullptr;   // pi_profile level 2
@@ -410,10 +416,17 @@ void prof_mark(pi_index* x, int k, cudaStream_t s) {
     if (cudaEvent_t e = prof_event(x, k)) cudaEventRecord(e, s);
 }
 
+void multi_destroy(pi_multi* mx);
+bool small_route(const pi_index* x, uint64_t n, uint64_t size_ub);
+int execute_small(pi_index* x, const uint8_t* ops, const uint64_t* keys, const uint64_t* values, uint64_t n,
+                  pi_result_t* results, cudaStream_t s);
+constexpr int kNoRoute = 1;  // execute_small: no cluster fits; the caller takes the plain path
+
 void destroy(pi_index* x) {
     if (!x) return;
     cudaSetDevice(x->device);
     cudaDeviceSynchronize();
+    if (x->small) multi_destroy(x->small);
     if (x->pev) {
         for (size_t i = 0; i < (size_t)kProfSlots * kProfEvents; ++i) cudaEventDestroy(x->pev[i]);
         delete[] x->pev;
@@ -945,6 +958,12 @@ pi_index_t* pi_create_ex(const uint64_t* keys, const uint64_t* values, uint64_t 
                 return nullptr;
             }
             x->sort_cfg = sp;
+            if (cfg->small_batches > 1) {
+                g_last_error = PI_ERR_INVALID_ARG;
+                delete x;
+                return nullptr;
+            }
+            x->small_mode = cfg->small_batches;
         }
     }
     // Lowest index level: the lowest l whose expected storage gap 2^(b (l - 1)) is at
@@ -1094,6 +1113,11 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
             if ((e = grow_index(x, x->known.index_need, s)) != cudaSuccess) return map_cuda(e);
         }
         x->known.grow_request = 0;
+    }
+    if (small_route(x, n, size_ub)) {
+        const int rc = execute_small(x, ops, keys, values, n, results, s);
+        if (rc != kNoRoute) return rc;
+        x->small_mode = 1;  // no cluster of the needed size fits this device: plain path
     }
     return enqueue_batch(x, x->sc, ops, keys, values, n, results, size_ub, s);
 }
@@ -1377,6 +1401,7 @@ int pi_info(pi_index_t* x, pi_info_t* out, pi_stream_t stream) {
     out->kernel_launches = x->launches;
     out->incremental_rebuilds = m.inc_rebuilds;
     out->owner_checked_writes = m.owner_writes;
+    out->routed_batches = x->routed;
     return sticky_error(m);
 }
 
@@ -1611,8 +1636,9 @@ cudaError_t multi_build_graphs(pi_multi* mx) {
             a.stride = mx->stride[c];
             a.qcap = mx->qcap[c];
             a.mirror = mx->d_mirror;
+            const pi_multi_class_t& q = mx->cfg.cls[c];
             cudaError_t r =
-                launch_multi(a, (int)mx->cfg.cls[c].warps, (int)mx->cfg.cls[c].radix_bits, mx->grid[c], mx->ls[c]);
+                launch_multi(a, (int)q.warps, (int)q.radix_bits, (int)q.cluster, mx->grid[c], mx->ls[c]);
             if (r != cudaSuccess && le == cudaSuccess) le = r;
             cudaEventRecord(mx->evj[c], mx->ls[c]);
             cudaStreamWaitEvent(mx->cs, mx->evj[c], 0);
@@ -1654,8 +1680,7 @@ pi_multi_t* pi_multi_create(pi_index_t* const* indices, uint32_t count, const pi
         c = *cfg;
         for (uint32_t k = 0; k < c.num_classes; ++k) {
             const pi_multi_class_t& q = c.cls[k];
-            const bool ok = (q.warps == 8 || q.warps == 16 || q.warps == 32) &&
-                            (q.radix_bits == 4 || q.radix_bits == 8) &&
+            const bool ok = multi_variant_ok((int)q.warps, (int)q.radix_bits, (int)q.cluster) &&
                             (k == 0 || q.max_log2_size > c.cls[k - 1].max_log2_size);
             if (!ok) {
                 g_last_error = PI_ERR_INVALID_ARG;
@@ -1715,11 +1740,14 @@ pi_multi_t* pi_multi_create(pi_index_t* const* indices, uint32_t count, const pi
         for (uint32_t k = 0; k < c.num_classes && e == cudaSuccess; ++k) {
             e = cudaStreamCreateWithFlags(&mx->ls[k], cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&mx->evj[k], cudaEventDisableTiming);
-            int occ = 0;
-            if (e == cudaSuccess) e = multi_occupancy((int)c.cls[k].warps, (int)c.cls[k].radix_bits, &occ);
-            if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
-            const uint64_t slots = (uint64_t)mx->num_sms * (uint64_t)occ;
-            mx->grid[k] = (uint32_t)(slots < count ? slots : count);
+            const pi_multi_class_t& q = c.cls[k];
+            const uint32_t per = q.cluster > 1 ? q.cluster : 1u;  // CTAs per batch
+            uint32_t slots = 0;
+            if (e == cudaSuccess) e = multi_grid((int)q.warps, (int)q.radix_bits, (int)q.cluster, mx->num_sms, &slots);
+            if (e == cudaSuccess && slots < per) e = cudaErrorInvalidConfiguration;
+            // no more batch slots (CTAs or clusters) than indices in the set
+            const uint64_t units = std::min<uint64_t>(slots / per, count);
+            mx->grid[k] = (uint32_t)(units * per);
         }
     } while (0);
     if (e != cudaSuccess) {
@@ -1730,13 +1758,36 @@ pi_multi_t* pi_multi_create(pi_index_t* const* indices, uint32_t count, const pi
     return mx;
 }
 
+}  // extern "C"
+
+namespace {
+int multi_execute(pi_multi* mx, const pi_multi_batch_t* b, uint32_t nb, cudaStream_t s, pi_index* single);
+}  // namespace
+
+extern "C" {
+
 int pi_multi_execute(pi_multi_t* mx, const pi_multi_batch_t* b, uint32_t nb, pi_stream_t stream) {
     if (!mx) return PI_ERR_INVALID_ARG;
+    return multi_execute(mx, b, nb, reinterpret_cast<cudaStream_t>(stream), nullptr);
+}
+
+uint64_t pi_multi_kernels_per_call(const pi_multi_t* mx) { return mx ? mx->launches : 0; }
+
+void pi_multi_destroy(pi_multi_t* mx) { multi_destroy(mx); }
+
+}  // extern "C"
+
+namespace {
+
+// One call of a batching set. `single`: the set is an index's small-batch route, and the
+// call is that index's batch for pi_execute_batch, which has already checked the
+// capacities; its bookkeeping is then a plain batch's (the mailbox ring and the index's
+// last-operation event) so the host's view of the sizes stays current without a sync.
+int multi_execute(pi_multi* mx, const pi_multi_batch_t* b, uint32_t nb, cudaStream_t s, pi_index* single) {
     if (nb == 0) return PI_OK;
     const uint32_t count = (uint32_t)mx->idx.size();
     if (!b || nb > count) return PI_ERR_INVALID_ARG;
     cudaSetDevice(mx->device);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::vector<uint8_t> seen(count, 0);
     for (uint32_t i = 0; i < nb; ++i) {
         const pi_multi_batch_t& q = b[i];
@@ -1807,7 +1858,8 @@ int pi_multi_execute(pi_multi_t* mx, const pi_multi_batch_t* b, uint32_t nb, pi_
         dfree(mx->scratch[c]);
         mx->qcap[c] = 0;
         mx->stride[c] = multi_scratch_bytes(q);
-        if ((e = dalloc(&mx->scratch[c], mx->stride[c] * mx->grid[c])) != cudaSuccess) {
+        const uint32_t units = mx->grid[c] / (mx->cfg.cls[c].cluster > 1 ? mx->cfg.cls[c].cluster : 1u);
+        if ((e = dalloc(&mx->scratch[c], mx->stride[c] * units)) != cudaSuccess) {
             mx->graph_valid = false;
             return map_cuda(e);
         }
@@ -1843,6 +1895,24 @@ int pi_multi_execute(pi_multi_t* mx, const pi_multi_batch_t* b, uint32_t nb, pi_
     if ((e = cudaEventRecord(mx->q_free[p], s)) != cudaSuccess) return map_cuda(e);
     mx->calls++;
     g_launches += mx->launches;
+    if (single) {
+        pi_index* x = single;
+        const uint64_t slot = x->issued % kRing;
+        if (x->issued - x->seen >= kRing) {  // the slot is still unread: wait for its batch
+            cudaEventSynchronize(x->ev[slot]);
+            refresh_known(x);
+        }
+        cudaMemcpyAsync(&x->h_mbox[slot], x->d_meta, sizeof(DevMeta), cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(x->ev[slot], s);
+        x->ring_n[slot] = b[0].n;
+        x->issued++;
+        x->pending_n += b[0].n;
+        x->force_rebuild = true;  // the plain path recounts its per-tile level counts
+        x->launches += mx->launches;
+        x->routed++;
+        mark_last(x, s);
+        return map_cuda(cudaGetLastError());
+    }
     for (uint32_t i = 0; i < nb; ++i) {
         pi_index* x = mx->idx[b[i].index];
         x->extra_n += b[i].n;
@@ -1855,11 +1925,43 @@ int pi_multi_execute(pi_multi_t* mx, const pi_multi_batch_t* b, uint32_t nb, pi_
     return PI_OK;
 }
 
-uint64_t pi_multi_kernels_per_call(const pi_multi_t* mx) { return mx ? mx->launches : 0; }
+constexpr uint64_t kSmallBatch = 1ull << 16;  // queries
+constexpr uint64_t kSmallIndex = 1ull << 20;  // storage nodes, the batch's new keys included
 
-void pi_multi_destroy(pi_multi_t* mx) { multi_destroy(mx); }
+bool small_route(const pi_index* x, uint64_t n, uint64_t size_ub) {
+    return x->small_mode == 0 && n <= kSmallBatch && size_ub <= kSmallIndex && !x->prof && !x->kt &&
+           x->test_flags == 0 && x->rebuild_policy == 0;
+}
 
-}  // extern "C"
+// A small batch as a one-item batching-form call on a thread-block cluster (16 CTAs, or 8
+// where 16 do not fit). Returns kNoRoute when no cluster size fits this device.
+int execute_small(pi_index* x, const uint8_t* ops, const uint64_t* keys, const uint64_t* values, uint64_t n,
+                  pi_result_t* results, cudaStream_t s) {
+    if (!x->small) {
+        const int saved = g_last_error;  // an internal set: pi_last_error stays the caller's
+        for (uint32_t cl : {16u, 8u}) {
+            pi_multi_config_t c{};
+            c.struct_size = sizeof(c);
+            c.num_classes = 1;
+            c.cls[0] = {32, 32, 8, cl};
+            pi_index_t* one = x;
+            x->small = pi_multi_create(&one, 1, &c);
+            if (x->small) break;
+        }
+        g_last_error = saved;
+        if (!x->small) return kNoRoute;
+    }
+    pi_multi_batch_t b{};
+    b.index = 0;
+    b.ops = ops;
+    b.keys = keys;
+    b.values = values;
+    b.n = n;
+    b.results = results;
+    return multi_execute(x->small, &b, 1, s, x);
+}
+
+}  // namespace
 
 namespace pi {
 void set_last_error(int code) { g_last_error = code; }

@@ -53,5 +53,5 @@ def test_result_struct_layout():
 def test_info_struct_matches_binding():
     import paper_1601_00159_gb300 as pkg
     # 3 u64 + 4 u32 + 34 u64 + 6 u64
-    assert ctypes.sizeof(pkg.PiInfo) == 3 * 8 + 4 * 4 + 34 * 8 + 7 * 8
+    assert ctypes.sizeof(pkg.PiInfo) == 3 * 8 + 4 * 4 + 34 * 8 + 8 * 8
     assert ctypes.sizeof(pkg.PiConfig) == 4 * 4 + 2 * 8 + 4 * 4

@@ -19,6 +19,9 @@ TABLES = {
     "default": None,
     "a": [(12, 8, 4), (15, 16, 8), (32, 32, 4)],
     "b": [(12, 8, 8), (15, 16, 4), (32, 32, 8)],
+    # thread-block clusters: 2, 4, 8 and 16 CTAs per batch
+    "c": [(12, 8, 4), (15, 32, 8, 2), (32, 32, 8, 8)],
+    "d": [(14, 32, 8, 4), (32, 32, 8, 16)],
 }
 
 
@@ -175,6 +178,10 @@ def test_multi_rejects_bad_sets_and_batches():
     assert e.value.code == PI_ERR_INVALID_ARG
     with pytest.raises(PiError):
         MultiSet([a], classes=[(12, 12, 8)])
+    with pytest.raises(PiError):
+        MultiSet([a], classes=[(32, 16, 8, 4)])  # a cluster takes 32-warp CTAs
+    with pytest.raises(PiError):
+        MultiSet([a], classes=[(32, 32, 8, 3)])  # cluster sizes 2, 4, 8, 16
     ms = MultiSet([a])
     z = torch.zeros(4, dtype=torch.int64, device="cuda")
     ops = torch.zeros(4, dtype=torch.uint8, device="cuda")
@@ -215,7 +222,7 @@ def test_multi_prefix_fixup(orc_mod, kind):
         res = torch.full((q, 2), -1, dtype=torch.int64, device="cuda")
         batches.append((i, to_dev(b.ops, torch.uint8), to_dev(b.keys, torch.int64), to_dev(b.vals, torch.int64), res))
         host.append((i, b, res))
-    for table in (None, [(32, 16, 4)]):
+    for table in (None, [(32, 16, 4)], [(32, 32, 8, 4)]):
         ms = MultiSet(idxs, table)
         ms.execute(batches)
         torch.cuda.synchronize()
@@ -224,3 +231,48 @@ def test_multi_prefix_fixup(orc_mod, kind):
         ms.close()
     for i, (ix, orc) in enumerate(zip(idxs, orcs)):
         assert_state_equal(ix, orc, f"{kind} index {i}")
+
+
+def test_multi_full_batching_workload(orc_mod):
+    """The batching workload at full size: 256 indices of 2^10..2^20 keys, batches of
+    2^8..2^16 queries (20% inserts of new keys), two rounds through the tuned class table
+    (thread-block clusters for the largest class), against 256 oracles; then every
+    index's live pairs and levels."""
+    import json
+    import os
+    import torch
+    from paper_1601_00159_gb300 import MultiSet
+    w = wl.batching()
+    root = os.path.join(os.path.dirname(__file__), "..", "paper_1601_00159_gb300", "multi_tuning.json")
+    with open(root) as f:
+        tuning = json.load(f)
+    classes = [tuple(c) for c in tuning["classes"]]
+    lowest = {int(h): int(l) for h, l in tuning.get("lowest_level", {}).items()}
+    idxs, orcs = [], []
+    for i, keys in enumerate(w.keys):
+        lg = int(np.ceil(np.log2(max(len(keys), 1))))
+        low = next((lowest[h] for h in sorted(lowest) if lg <= h), 0)
+        cfg = {"storage_capacity": len(keys) + 4 * int(w.batch_sizes[i]) + 4096}
+        if low:
+            cfg["lowest_level"] = low
+        idxs.append(make_index(keys, w.vals[i], w.promote_p, w.hash_seeds[i], cfg))
+        orcs.append(orc_mod.Oracle(keys, w.vals[i], w.promote_p, w.hash_seeds[i]))
+    ms = MultiSet(idxs, classes)
+    for r in range(2):
+        rnd = w.batches(r)
+        batches = []
+        for i, b in enumerate(rnd):
+            res = torch.full((len(b), 2), -1, dtype=torch.int64, device="cuda")
+            batches.append((i, to_dev(b.ops, torch.uint8), to_dev(b.keys, torch.int64), to_dev(b.vals, torch.int64),
+                            res))
+        ms.execute(batches)
+        torch.cuda.synchronize()
+        for i, b in enumerate(rnd):
+            assert_results_equal(results_np(batches[i][4]), orcs[i].execute(b.ops, b.keys, b.vals),
+                                 f"round {r} index {i} ({len(w.keys[i])} keys, {len(b)} queries)")
+    for i, (ix, orc) in enumerate(zip(idxs, orcs)):
+        assert_state_equal(ix, orc, f"index {i}")
+    ms.close()
+    for ix, orc in zip(idxs, orcs):
+        ix.close()
+        orc.close()

@@ -31,8 +31,8 @@ def lib():
     return load_library()
 
 
-def run_workload(orc_mod, w, config=None, check_levels_every=1, batches=None, check_levels=True):
-    idx = make_index(w.keys, w.vals, w.promote_p, w.hash_seed, config)
+def run_workload(orc_mod, w, config=None, check_levels_every=1, batches=None, check_levels=True, route=False):
+    idx = make_index(w.keys, w.vals, w.promote_p, w.hash_seed, config, route=route)
     orc = orc_mod.Oracle(w.keys, w.vals, w.promote_p, w.hash_seed)
     assert_state_equal(idx, orc, f"{w.name} after create")
     bl = w.batches() if callable(w.batches) else w.batches
@@ -50,23 +50,27 @@ def run_workload(orc_mod, w, config=None, check_levels_every=1, batches=None, ch
     return info
 
 
-def test_tiny_config_full_size(orc_mod):
-    """2^16 keys, p = 1/2, one all-search batch of 2^14 (half hits, half misses)."""
+@pytest.mark.parametrize("route", [False, True])
+def test_tiny_config_full_size(orc_mod, route):
+    """2^16 keys, p = 1/2, one all-search batch of 2^14 (half hits, half misses); on the
+    level-synchronous pipeline and on the small-batch route."""
     w = wl.tiny()
-    info = run_workload(orc_mod, w)
+    info = run_workload(orc_mod, w, route=route)
     assert info["rebuilds"] == 1  # only the initial build: a search batch changes nothing
 
 
+@pytest.mark.parametrize("route", [False, True])
 @pytest.mark.parametrize("seed", range(40))
-def test_random_small_dense(orc_mod, seed):
-    """Tiny key ranges: long same-key runs, revivals, delete/insert chains, invalid ops."""
+def test_random_small_dense(orc_mod, seed, route):
+    """Tiny key ranges: long same-key runs, revivals, delete/insert chains, invalid ops;
+    on the level-synchronous pipeline and on the small-batch route (one cluster launch)."""
     rng = np.random.default_rng(seed)
     n = int(rng.integers(0, 3000))
     q = int(rng.integers(1, 9000))
     kr = int(rng.choice([5, 64, 700, 5000, 1 << 40]))
     p = float(rng.choice([0.5, 0.25, 0.125, 0.0625]))
     w = wl.random_small(1000 + seed, n, q, kr, p=p, n_batches=4)
-    run_workload(orc_mod, w)
+    run_workload(orc_mod, w, route=route)
 
 
 def test_mid_shape_scaled(orc_mod):
@@ -113,24 +117,26 @@ def test_index_capacity_overflow_keeps_results_exact(orc_mod):
     assert info["bottom_built"] == 2 and info["index_capacity"] > 3000
 
 
+@pytest.mark.parametrize("route", [False, True])
 @pytest.mark.parametrize("lowest", [0, 2, 3, 5])
 @pytest.mark.parametrize("p", [0.5, 0.25])
-def test_lowest_built_level(orc_mod, lowest, p):
+def test_lowest_built_level(orc_mod, lowest, p, route):
     """Index layers whose lowest materialised level is 2 (every level, as in the paper),
     3, 5 or the automatic choice: results, live pairs and the built levels stay exact,
     and the descent scans the longer storage gaps below the lowest level."""
     w = wl.random_small(60 + lowest, 30000, 20000, 1 << 40, p=p, n_batches=3)
     cfg = {"lowest_level": lowest} if lowest else None
-    info = run_workload(orc_mod, w, cfg)
+    info = run_workload(orc_mod, w, cfg, route=route)
     auto = 4 if p == 0.25 else 6  # the lowest level whose expected storage gap is >= 32 nodes
     assert info["bottom_built"] == (lowest or auto)
 
 
-def test_edge_cases(orc_mod):
+@pytest.mark.parametrize("route", [False, True])
+def test_edge_cases(orc_mod, route):
     import torch
     M = (1 << 64) - 1
     # empty index, then inserts; empty batch; all-invalid batch; extreme keys
-    idx = make_index(np.zeros(0, np.uint64), np.zeros(0, np.uint64), 0.25, 3)
+    idx = make_index(np.zeros(0, np.uint64), np.zeros(0, np.uint64), 0.25, 3, route=route)
     orc = orc_mod.Oracle(np.zeros(0, np.uint64), np.zeros(0, np.uint64), 0.25, 3)
     assert_state_equal(idx, orc, "empty")
     empty = torch.empty(0, dtype=torch.int64, device="cuda")
@@ -185,7 +191,8 @@ def test_host_entry_point_matches_device_entry_point(orc_mod):
         assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
 
 
-def test_host_entry_point_pipelined_and_mixed_with_other_streams(orc_mod):
+@pytest.mark.parametrize("route", [False, True])
+def test_host_entry_point_pipelined_and_mixed_with_other_streams(orc_mod, route):
     """Host-buffer batches run on the library's own streams, two in flight: several are
     issued back to back with no synchronisation, then a device-buffer batch on another
     stream, a range search and more host-buffer batches. Each must see the effect of every
@@ -194,7 +201,7 @@ def test_host_entry_point_pipelined_and_mixed_with_other_streams(orc_mod):
     import torch
     w = wl.random_small(77, 20000, 30000, 40000, p=0.25, n_batches=8)  # dense keys: long dependency chains
     orc = orc_mod.Oracle(w.keys, w.vals, w.promote_p, w.hash_seed)
-    idx = make_index(w.keys, w.vals, w.promote_p, w.hash_seed)
+    idx = make_index(w.keys, w.vals, w.promote_p, w.hash_seed, route=route)
     side = torch.cuda.Stream()
     expected, outs = [], []
     for b, batch in enumerate(w.batches):
@@ -324,3 +331,48 @@ def test_height_cap_keys(orc_mod, b, lowest):
     info = run_workload(orc_mod, w, config={"lowest_level": lowest} if lowest else None)
     assert info["top_level"] == hmax
     assert info["level_size"][hmax] >= 1
+
+
+def test_small_route_alternates_with_plain_path(orc_mod):
+    """One index takes routed batches (at most 2^16 queries, one cluster launch) and
+    level-synchronous ones (larger batches) in turn, with a range search and a no-alloc
+    batch between them, inserts that make it outgrow 2^20 keys (after which every batch
+    takes the level-synchronous pipeline) and deletes past 1/8 of the storage layer.
+    Every result, the live pairs and the built levels match the oracle throughout."""
+    import torch
+    n0 = (1 << 20) - 100000
+    keys = wl.distinct_keys(41, np.arange(n0))
+    vals = wl.splitmix64(keys)
+    idx = make_index(keys, vals, 0.25, 41, route=True)
+    orc = orc_mod.Oracle(keys, vals, 0.25, 41)
+    s = wl.stream_seed(41, 7)
+    off = 0
+    for b, q in enumerate([1 << 14, 1 << 17, 60000, 5000, (1 << 16) + 1, 3000, 200000, 1 << 16, 1 << 15]):
+        kind = wl.bounded(s, off, q, 10)
+        old = keys[wl.bounded(s, off + q, q, len(keys))]
+        new = wl.u64_stream(s, off + 2 * q, q) >> np.uint64(1)
+        ops = np.where(kind < 3, 0, np.where(kind < 8, 1, 2)).astype(np.uint8)
+        bk = np.where(kind % 2 == 0, old, new).astype(np.uint64)
+        batch = wl.Batch(ops, bk, wl.u64_stream(s, off + 3 * q, q))
+        off += 4 * q
+        if b == 3:  # the no-alloc entry point between routed batches
+            res = torch.full((q, 2), -1, dtype=torch.int64, device="cuda")
+            idx.execute_noalloc(to_dev(batch.ops, torch.uint8), to_dev(batch.keys, torch.int64),
+                                to_dev(batch.vals, torch.int64), res)
+            got = results_np(res)
+        else:
+            got = run_batch(idx, batch)
+        assert_results_equal(got, orc.execute(batch.ops, batch.keys, batch.vals), f"batch {b} ({q} queries)")
+        assert_state_equal(idx, orc, f"batch {b}")
+        if b == 4:  # a range search sees every batch before it
+            lo = np.sort(keys[:64])
+            hi = lo + np.uint64(1 << 40)
+            offs, rk, rv = idx.range_search(to_dev(lo, torch.int64), to_dev(hi, torch.int64))
+            ok, ov = orc.export()
+            for j in range(len(lo)):
+                sel = (ok >= lo[j]) & (ok <= hi[j])
+                a, e = int(offs[j]), int(offs[j + 1])
+                assert np.array_equal(rk[a:e].cpu().numpy().view(np.uint64), ok[sel]), f"range {j}"
+    assert idx.info()["size"] > (1 << 20)
+    idx.close()
+    orc.close()
