@@ -97,14 +97,17 @@ typedef struct {
                                     8: every varying byte. Every choice gives the same
                                     results. (Callers built against the header without this
                                     field pass a smaller struct_size; it then reads as 0.) */
-    uint32_t small_batches;      /* 0: automatic. A batch of at most 2^16 queries on an index
-                                    of at most 2^20 nodes (its new keys included) runs as one
-                                    launch: the batching form's pipeline on a thread-block
-                                    cluster of 16 CTAs (8 where 16 do not fit), with the same
-                                    results as the level-synchronous pipeline, which needs
-                                    tens of dependent launches. Not taken while profiling,
-                                    with test_flags or with the deferred rebuild policy.
-                                    1: every batch takes the level-synchronous pipeline. */
+    uint32_t small_batches;      /* 0: every batch takes the level-synchronous pipeline
+                                    (default). 1: a batch of at most 2^16 queries on an
+                                    index of at most 2^20 nodes (its new keys included)
+                                    runs as one launch, the batching form's pipeline on a
+                                    thread-block cluster of 16 CTAs of 16 warps (8 where 16
+                                    do not fit), with the same results. Measured on a
+                                    GB300 it is about as fast as the default for such
+                                    batches (98 against 99 us for 2^14 searches on 2^16
+                                    keys; faster on the smallest batches, slower on 2^12
+                                    queries on 2^18 keys). Not taken while profiling, with
+                                    test_flags or with the deferred rebuild policy. */
 } pi_config_t;
 
 /* test_flags bit: give only the lowest index level a launch of its own in the
@@ -352,7 +355,7 @@ typedef struct pi_multi pi_multi_t;
  * `radix_bits` bits (4 or 8). `cluster` is the number of CTAs that share one batch:
  * 0 or 1 gives each batch one CTA; 2, 4, 8 or 16 give it a thread-block cluster of
  * that many CTAs (on as many SMs), which splits every stage of the batch into one span
- * per CTA and needs warps = 32 and radix_bits = 8. */
+ * per CTA and needs warps = 16 or 32 and radix_bits = 8. */
 typedef struct {
     uint32_t max_log2_size;
     uint32_t warps;

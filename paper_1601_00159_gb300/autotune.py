@@ -2,8 +2,8 @@
 
 Batching form (default mode): pi_multi_execute runs each size class of indices with its
 own persistent kernel. This mode times every variant -- 8, 16 or 32 warps per index, 4-
-or 8-bit radix digits, and for 32 warps with 8-bit digits thread-block clusters of 2, 4,
-8 or 16 CTAs per batch -- on the indices of each class of the batching workload, then the
+or 8-bit radix digits, and for 16 or 32 warps with 8-bit digits thread-block clusters of
+2, 4, 8 or 16 CTAs per batch -- on the indices of each class of the batching workload, then the
 node fan-out of each class (the lowest built index level, i.e. the storage nodes one
 entry of the lowest level spans), and writes the fastest per class to multi_tuning.json
 beside it, which bench.py and MultiSet callers pass to pi_multi_create / pi_create_ex.
@@ -30,7 +30,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "multi_tuning.json")
 PLAIN_OUT = os.path.join(HERE, "plain_tuning.json")
 BOUNDS = [14, 17, 32]  # class upper bounds (log2 of the storage size)
-VARIANTS = [(w, b, 1) for w in (8, 16, 32) for b in (4, 8)] + [(32, 8, c) for c in (2, 4, 8, 16)]
+VARIANTS = [(w, b, 1) for w in (8, 16, 32) for b in (4, 8)] + [(w, 8, c) for w in (16, 32) for c in (2, 4, 8, 16)]
 
 
 def kernel_name(v):

@@ -44,6 +44,9 @@ constexpr uint32_t kMTop = 2048;   // index entries staged in shared memory
 constexpr uint32_t kMSeg = 256;    // colliding segments one CTA orders after the prefix passes
 constexpr int kXMax = 40;          // values one cluster exchange carries
 constexpr uint32_t kJbWin = 256;   // merge chunks whose new-node bounds are found together
+// The radix scatter's chunk staging starts after the digit counters of the largest
+// variant (32 warps x 256 digits + three 256-entry arrays, 4 B each).
+constexpr uint32_t kSortStage = (32u * 256u + 3u * 256u) * 4u;
 
 __device__ __forceinline__ void mstore_result(pi_result_t* res, uint32_t seq, uint64_t v, uint32_t st) {
     uint4 w;
@@ -224,19 +227,26 @@ __device__ __forceinline__ void multi_bsearch(const uint64_t* K, const uint64_t 
 
 // Scatter of [lo, hi) of (src_k, src_p) by the kBits-bit digit at `shift`. On entry
 // sbase[d] (after the per-warp counters in dsm) holds the first destination of digit d
-// for this range; chunks of kT x kMI elements are ranked by warp ballots (elements in
-// index order within a chunk), so the scatter is stable. Destinations at or past dlim
-// are refused (kErrBounds).
+// for this range. Chunks of kT x kMI elements are ranked by warp ballots (elements in
+// index order within a chunk), so the scatter is stable; each chunk is first placed in
+// shared memory in digit order and then written out in runs, so consecutive threads
+// store consecutive addresses of one digit's run (a chunk scattered straight to global
+// memory costs one L2 request per element). Destinations at or past dlim are refused
+// (kErrBounds).
 template <int kT, int kBits>
 __device__ void m_scatter(const uint64_t* src_k, const uint32_t* src_p, uint64_t* dst_k, uint32_t* dst_p,
-                          uint32_t lo, uint32_t hi, uint32_t shift, uint32_t dlim, uint8_t* dsm, uint32_t* err) {
+                          uint32_t lo, uint32_t hi, uint32_t shift, uint32_t dlim, uint8_t* dsm, uint32_t* tmp,
+                          uint32_t* err) {
     constexpr int kW = kT / 32;
     constexpr int kR = 1 << kBits;
     constexpr uint32_t kC = (uint32_t)kT * kMI;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t* whist = reinterpret_cast<uint32_t*>(dsm);  // [kW][kR]
     uint32_t* sbase = whist + kW * kR;                   // [kR]
-    uint32_t* stot = sbase + kR;                         // [kR]
+    uint32_t* stot = sbase + kR;                         // [kR] the chunk's count per digit
+    uint32_t* loff = stot + kR;                          // [kR] the chunk's first slot per digit
+    uint64_t* sk = reinterpret_cast<uint64_t*>(dsm + kSortStage);  // [kC] the chunk in digit order
+    uint32_t* sp = reinterpret_cast<uint32_t*>(sk + kC);           // [kC]
     for (int d = tid; d < kW * kR; d += kT) whist[d] = 0;
     __syncthreads();
     for (uint32_t c0 = lo; c0 < hi; c0 += kC) {
@@ -261,19 +271,30 @@ __device__ void m_scatter(const uint64_t* src_k, const uint32_t* src_p, uint64_t
                 total += cc;
             }
             stot[d] = total;
+            loff[d] = total;
         }
         __syncthreads();
+        small_excl_scan<kT, kR>(loff, tmp);
 #pragma unroll
         for (int k = 0; k < kMI; ++k) {
             const uint32_t d = dig[k];
             if (d < (uint32_t)kR) {
-                const uint32_t pos = sbase[d] + whist[warp * kR + d] + rank[k];
-                if (pos < dlim) {
-                    dst_k[pos] = key[k];
-                    dst_p[pos] = pay[k];
-                } else {
-                    atomicOr(err, kErrBounds);
-                }
+                const uint32_t l = loff[d] + whist[warp * kR + d] + rank[k];
+                sk[l] = key[k];
+                sp[l] = pay[k];
+            }
+        }
+        __syncthreads();
+        const uint32_t cnt = hi - c0 < kC ? hi - c0 : kC;
+        for (uint32_t i = tid; i < cnt; i += kT) {
+            const uint64_t k = sk[i];
+            const uint32_t d = (uint32_t)(k >> shift) & (kR - 1);
+            const uint32_t pos = sbase[d] + (i - loff[d]);
+            if (pos < dlim) {
+                dst_k[pos] = k;
+                dst_p[pos] = sp[i];
+            } else {
+                atomicOr(err, kErrBounds);
             }
         }
         __syncthreads();
@@ -283,6 +304,25 @@ __device__ void m_scatter(const uint64_t* src_k, const uint32_t* src_p, uint64_t
             for (int w = 0; w < kW; ++w) whist[w * kR + d] = 0;
         }
         __syncthreads();
+    }
+}
+
+// Adds the kBits-bit digits at `shift` of src_k[lo, hi) to the counters h. Each thread
+// loads kMI keys before its first atomic, so the loads are in flight together.
+template <int kT, int kBits>
+__device__ __forceinline__ void m_histogram(const uint64_t* src_k, uint32_t lo, uint32_t hi, uint32_t shift,
+                                            uint32_t* h) {
+    constexpr uint32_t kR = 1u << kBits;
+    for (uint32_t b0 = lo; b0 < hi; b0 += (uint32_t)kT * kMI) {
+        uint32_t dg[kMI];
+#pragma unroll
+        for (int u = 0; u < kMI; ++u) {
+            const uint32_t i = b0 + (uint32_t)u * kT + threadIdx.x;
+            dg[u] = i < hi ? (uint32_t)(src_k[i] >> shift) & (kR - 1u) : kR;
+        }
+#pragma unroll
+        for (int u = 0; u < kMI; ++u)
+            if (dg[u] < kR) atomicAdd(&h[dg[u]], 1u);
     }
 }
 
@@ -297,11 +337,11 @@ __device__ void m_lsd_pass(const uint64_t* src_k, const uint32_t* src_p, uint64_
     uint32_t* sbase = reinterpret_cast<uint32_t*>(dsm) + kW * kR;
     for (int d = tid; d < kR; d += kT) sbase[d] = 0;
     __syncthreads();
-    for (uint32_t i = lo + tid; i < hi; i += kT) atomicAdd(&sbase[(uint32_t)(src_k[i] >> shift) & (kR - 1)], 1u);
+    m_histogram<kT, kBits>(src_k, lo, hi, shift, sbase);
     __syncthreads();
     small_excl_scan<kT, kR>(sbase, tmp);
     for (int d = tid; d < kR; d += kT) sbase[d] += lo;
-    m_scatter<kT, kBits>(src_k, src_p, dst_k, dst_p, lo, hi, shift, hi, dsm, err);
+    m_scatter<kT, kBits>(src_k, src_p, dst_k, dst_p, lo, hi, shift, hi, dsm, tmp, err);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1014,19 +1054,32 @@ __device__ void m_pack(const MItem& it, const MScratchPtrs& s, uint32_t lo, uint
     uint32_t mx[8], mn[8], inv = 0;
 #pragma unroll
     for (int d = 0; d < 8; ++d) mx[d] = mn[d] = 0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += kT) {
-        const uint32_t op = it.ops[i];
-        const uint64_t k = it.keys[i];
-        const bool valid = op <= 2u && k != kMaxKey;
-        s.ka[i] = valid ? k : kMaxKey;
-        s.pa[i] = ((op & 3u) << 30) | i;
-        inv += valid ? 0u : 1u;
-        if (valid) {
+    constexpr int kU = 4;  // queries a thread loads before it stores any
+    for (uint32_t b0 = lo; b0 < hi; b0 += (uint32_t)kT * kU) {
+        uint32_t op[kU];
+        uint64_t kk[kU];
 #pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                const uint32_t b = (uint32_t)(k >> (8 * d)) & 255u;
-                mx[d] = max(mx[d], b);
-                mn[d] = max(mn[d], 255u - b);
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t i = b0 + (uint32_t)u * kT + threadIdx.x;
+            op[u] = i < hi ? (uint32_t)it.ops[i] : 0xFFu;
+            kk[u] = i < hi ? it.keys[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t i = b0 + (uint32_t)u * kT + threadIdx.x;
+            if (i >= hi) continue;
+            const uint64_t k = kk[u];
+            const bool valid = op[u] <= 2u && k != kMaxKey;
+            s.ka[i] = valid ? k : kMaxKey;
+            s.pa[i] = ((op[u] & 3u) << 30) | i;
+            inv += valid ? 0u : 1u;
+            if (valid) {
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    const uint32_t b = (uint32_t)(k >> (8 * d)) & 255u;
+                    mx[d] = max(mx[d], b);
+                    mn[d] = max(mn[d], 255u - b);
+                }
             }
         }
     }
@@ -1370,7 +1423,7 @@ __device__ void cl_lsd_pass(const cg::cluster_group& cl, CXShared& cx, uint32_t&
     ++hph;
     for (int d = tid; d < kR; d += kT) h[d] = 0;
     __syncthreads();
-    for (uint32_t i = lo + tid; i < hi; i += kT) atomicAdd(&h[(uint32_t)(src_k[i] >> shift) & (kR - 1)], 1u);
+    m_histogram<kT, kBits>(src_k, lo, hi, shift, h);
     cl.sync();
     uint32_t pre = 0;
     if (tid < kR) {
@@ -1389,7 +1442,7 @@ __device__ void cl_lsd_pass(const cg::cluster_group& cl, CXShared& cx, uint32_t&
     __syncthreads();
     small_excl_scan<kT, kR>(stot, tmp);
     if (tid < kR) sbase[tid] = stot[tid] + pre;
-    m_scatter<kT, kBits>(src_k, src_p, dst_k, dst_p, lo, hi, shift, n, dsm, err);
+    m_scatter<kT, kBits>(src_k, src_p, dst_k, dst_p, lo, hi, shift, n, dsm, tmp, err);
     cl.sync();
 }
 
@@ -1415,12 +1468,12 @@ __device__ void m_item_cl(const cg::cluster_group& cl, const MultiArgs& a, const
     uint64_t* LK = sh.m.lcur ? X.lkeys1 : X.lkeys;
     uint32_t* LD = sh.m.lcur ? X.ldown1 : X.ldown;
 
-    // ---- pack + sort. A batch of at most one chunk is sorted by rank 0 alone (four
-    // passes and the prefix fix-up; a cluster pass costs two cluster barriers); a larger
-    // one by the cluster, every varying key byte a pass (no prefix fix-up).
+    // ---- pack + sort. A batch of at most two chunks is sorted by rank 0 alone (a cluster
+    // pass costs two cluster barriers and an exchange, more than a chunk's ranking); a
+    // larger one by the cluster.
     uint64_t* K = s.ka;
     uint32_t* P = s.pa;
-    if (n <= kC) {
+    if (n <= 2 * kC) {
         if (me == 0) m_sort_cta<kT, kBits>(it, s, dsm, sh, err, K, P);
         if (tid == 0) {
             sh.xs[0] = (me == 0 && K != s.ka) ? 1u : 0u;  // rank 0's result buffer
@@ -1710,7 +1763,7 @@ __global__ void __launch_bounds__(kW * 32) k_multi_cl(MultiArgs a) {
 template <int kW, int kBits>
 constexpr int multi_smem() {
     constexpr int kT = kW * 32;
-    constexpr int sort = (kW * (1 << kBits) + 2 * (1 << kBits)) * 4;
+    constexpr int sort = (int)kSortStage + kT * kMI * 12;  // counters, then the staged chunk
     constexpr int top = (int)kMTop * 12;
     constexpr int merge = kT * kMI * 12;  // live, new-node and member prefixes per chunk position
     return sort > top ? (sort > merge ? sort : merge) : (top > merge ? top : merge);
@@ -1730,8 +1783,8 @@ cudaError_t grid_t(int cluster, int num_sms, uint32_t* grid) {
         *grid = (uint32_t)(blocks > 0 ? blocks : 0) * (uint32_t)num_sms;
         return e;
     }
-    if constexpr (kW != 32 || kBits != 8) {
-        return cudaErrorInvalidValue;  // clusters run the 32-warp, 8-bit variant only
+    if constexpr ((kW != 16 && kW != 32) || kBits != 8) {
+        return cudaErrorInvalidValue;  // clusters run the 16- and 32-warp, 8-bit variants only
     } else {
     cudaError_t e = cudaFuncSetAttribute(k_multi_cl<kW, kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e == cudaSuccess && cluster > 8)
@@ -1759,7 +1812,7 @@ template <int kW, int kBits>
 cudaError_t launch_t(const MultiArgs& a, int cluster, uint32_t grid, cudaStream_t s) {
     if (cluster <= 1) {
         k_multi<kW, kBits><<<grid, kW * 32, multi_smem<kW, kBits>(), s>>>(a);
-    } else if constexpr (kW != 32 || kBits != 8) {
+    } else if constexpr ((kW != 16 && kW != 32) || kBits != 8) {
         return cudaErrorInvalidValue;
     } else {
         cudaLaunchConfig_t cfg = {};
@@ -1793,14 +1846,15 @@ uint64_t multi_scratch_bytes(uint32_t qcap) {
 bool multi_variant_ok(int warps, int radix_bits, int cluster) {
     const bool base = (warps == 8 || warps == 16 || warps == 32) && (radix_bits == 4 || radix_bits == 8);
     if (cluster <= 1) return base;
-    return warps == 32 && radix_bits == 8 && (cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16);
+    return (warps == 16 || warps == 32) && radix_bits == 8 &&
+           (cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16);
 }
 
 // multi_grid must have run for the variant first (it sets the shared-memory limit).
 cudaError_t launch_multi(const MultiArgs& a, int warps, int radix_bits, int cluster, uint32_t grid, cudaStream_t s) {
     if (grid == 0) return cudaSuccess;
     if (!multi_variant_ok(warps, radix_bits, cluster)) return cudaErrorInvalidValue;
-    if (cluster > 1) return launch_t<32, 8>(a, cluster, grid, s);
+    if (cluster > 1) return warps == 16 ? launch_t<16, 8>(a, cluster, grid, s) : launch_t<32, 8>(a, cluster, grid, s);
     if (radix_bits == 8) {
         if (warps == 8) return launch_t<8, 8>(a, 1, grid, s);
         if (warps == 16) return launch_t<16, 8>(a, 1, grid, s);
@@ -1814,7 +1868,7 @@ cudaError_t launch_multi(const MultiArgs& a, int warps, int radix_bits, int clus
 cudaError_t multi_grid(int warps, int radix_bits, int cluster, int num_sms, uint32_t* grid) {
     *grid = 0;
     if (!multi_variant_ok(warps, radix_bits, cluster)) return cudaErrorInvalidValue;
-    if (cluster > 1) return grid_t<32, 8>(cluster, num_sms, grid);
+    if (cluster > 1) return warps == 16 ? grid_t<16, 8>(cluster, num_sms, grid) : grid_t<32, 8>(cluster, num_sms, grid);
     if (radix_bits == 8) {
         if (warps == 8) return grid_t<8, 8>(1, num_sms, grid);
         if (warps == 16) return grid_t<16, 8>(1, num_sms, grid);

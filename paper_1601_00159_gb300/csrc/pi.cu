@@ -182,9 +182,9 @@ struct pi_index {
     uint64_t pending_n = 0;  // queries issued after that snapshot
     uint64_t extra_n = 0;    // queries of batching-form calls since the last full sync
     bool force_rebuild = false;
-    // Small batches (Q <= kSmallBatch on at most kSmallIndex nodes) run through a one-index
-    // batching set whose batch takes a thread-block cluster: one launch instead of the
-    // level-synchronous pipeline's tens. Created on first use; small_mode 1 turns it off.
+    // With small_mode 1, small batches (Q <= kSmallBatch on at most kSmallIndex nodes) run
+    // through a one-index batching set whose batch takes a thread-block cluster: one
+    // launch instead of the level-synchronous pipeline's tens. Created on first use.
     pi_multi* small = nullptr;
     uint32_t small_mode = 0;
     uint64_t routed = 0;  // batches that took the route
@@ -1117,7 +1117,7 @@ int pi_execute_batch(pi_index_t* x, const uint8_t* ops, const uint64_t* keys, co
     if (small_route(x, n, size_ub)) {
         const int rc = execute_small(x, ops, keys, values, n, results, s);
         if (rc != kNoRoute) return rc;
-        x->small_mode = 1;  // no cluster of the needed size fits this device: plain path
+        x->small_mode = 0;  // no cluster of the needed size fits this device: plain path
     }
     return enqueue_batch(x, x->sc, ops, keys, values, n, results, size_ub, s);
 }
@@ -1929,12 +1929,13 @@ constexpr uint64_t kSmallBatch = 1ull << 16;  // queries
 constexpr uint64_t kSmallIndex = 1ull << 20;  // storage nodes, the batch's new keys included
 
 bool small_route(const pi_index* x, uint64_t n, uint64_t size_ub) {
-    return x->small_mode == 0 && n <= kSmallBatch && size_ub <= kSmallIndex && !x->prof && !x->kt &&
+    return x->small_mode == 1 && n <= kSmallBatch && size_ub <= kSmallIndex && !x->prof && !x->kt &&
            x->test_flags == 0 && x->rebuild_policy == 0;
 }
 
-// A small batch as a one-item batching-form call on a thread-block cluster (16 CTAs, or 8
-// where 16 do not fit). Returns kNoRoute when no cluster size fits this device.
+// A small batch as a one-item batching-form call on a thread-block cluster of 16 CTAs of
+// 16 warps (8 CTAs where 16 do not fit; 16-warp CTAs keep the pipeline's registers
+// unspilled). Returns kNoRoute when no cluster size fits this device.
 int execute_small(pi_index* x, const uint8_t* ops, const uint64_t* keys, const uint64_t* values, uint64_t n,
                   pi_result_t* results, cudaStream_t s) {
     if (!x->small) {
@@ -1943,7 +1944,7 @@ int execute_small(pi_index* x, const uint8_t* ops, const uint64_t* keys, const u
             pi_multi_config_t c{};
             c.struct_size = sizeof(c);
             c.num_classes = 1;
-            c.cls[0] = {32, 32, 8, cl};
+            c.cls[0] = {32, 16, 8, cl};
             pi_index_t* one = x;
             x->small = pi_multi_create(&one, 1, &c);
             if (x->small) break;

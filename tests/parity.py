@@ -21,16 +21,15 @@ def results_np(res):
 
 
 def make_index(keys, vals, p, seed, config=None, route=False):
-    """An index on the GPU. route=False keeps every batch on the level-synchronous
-    pipeline (small_batches = 1), so the tests exercise its kernels at small sizes too;
-    route=True leaves the library's default, under which batches of at most 2^16 queries
-    on indices of at most 2^20 keys run as one thread-block-cluster launch."""
+    """An index on the GPU (the library's defaults: every batch on the level-synchronous
+    pipeline). route=True sets small_batches = 1: batches of at most 2^16 queries on
+    indices of at most 2^20 keys then run as one thread-block-cluster launch."""
     import torch
     from paper_1601_00159_gb300 import Index
     cfg = dict(config or {})
-    if not route:
+    if route:
         cfg.setdefault("small_batches", 1)
-    return Index(to_dev(keys, torch.int64), to_dev(vals, torch.int64), p, seed, cfg)
+    return Index(to_dev(keys, torch.int64), to_dev(vals, torch.int64), p, seed, cfg or None)
 
 
 def run_batch(idx, batch):

@@ -22,6 +22,7 @@ TABLES = {
     # thread-block clusters: 2, 4, 8 and 16 CTAs per batch
     "c": [(12, 8, 4), (15, 32, 8, 2), (32, 32, 8, 8)],
     "d": [(14, 32, 8, 4), (32, 32, 8, 16)],
+    "e": [(12, 16, 8, 8), (32, 16, 8, 2)],
 }
 
 
@@ -179,7 +180,7 @@ def test_multi_rejects_bad_sets_and_batches():
     with pytest.raises(PiError):
         MultiSet([a], classes=[(12, 12, 8)])
     with pytest.raises(PiError):
-        MultiSet([a], classes=[(32, 16, 8, 4)])  # a cluster takes 32-warp CTAs
+        MultiSet([a], classes=[(32, 8, 8, 4)])  # a cluster takes 16- or 32-warp CTAs
     with pytest.raises(PiError):
         MultiSet([a], classes=[(32, 32, 8, 3)])  # cluster sizes 2, 4, 8, 16
     ms = MultiSet([a])
