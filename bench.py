@@ -398,7 +398,7 @@ def run_reference(args, ws, rank):
 
 
 def run_batching(args, ws, rank, local):
-    """Config 4: one pi_multi_execute per step over every index's batch, beside the same
+    """The batching workload: one pi_multi_execute per step over every index's batch, beside the same
     batches run by looping the single-index path over the indices."""
     import torch
     from paper_1601_00159_gb300 import Index, MultiSet, build, load_library
@@ -603,7 +603,7 @@ def run_batching(args, ws, rank, local):
 
 
 def run_serving(args, ws, rank, local):
-    """Config 5: the server under a saturating burst (capacity), then under Poisson
+    """The serving workload: the server under a saturating burst (capacity), then under Poisson
     arrivals at 50% and 90% of that capacity (latency), beside one request per
     pi_execute_batch."""
     import torch
