@@ -52,6 +52,30 @@ def test_result_struct_layout():
 
 def test_info_struct_matches_binding():
     import paper_1601_00159_gb300 as pkg
-    # 3 u64 + 4 u32 + 34 u64 + 6 u64
+    # 3 u64 + 4 u32 + 34 u64 + 8 u64
     assert ctypes.sizeof(pkg.PiInfo) == 3 * 8 + 4 * 4 + 34 * 8 + 8 * 8
     assert ctypes.sizeof(pkg.PiConfig) == 4 * 4 + 2 * 8 + 4 * 4
+
+
+def _header_fields(name):
+    """(type, field) pairs of `typedef struct {...} name;` in include/pi.h."""
+    src = open(os.path.join(ROOT, "include", "pi.h")).read()
+    m = re.search(r"typedef struct \{((?:[^{}])*?)\} " + name + ";", src, flags=re.S)
+    body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+    out = []
+    for decl in body.split(";"):
+        parts = decl.split()
+        if not parts:
+            continue
+        field = re.sub(r"\[.*\]", "", parts[-1])
+        out.append((" ".join(parts[:-1]), field))
+    return out
+
+
+def test_config_structs_match_binding():
+    """The binding's ctypes structs name the header's fields in the header's order."""
+    import paper_1601_00159_gb300 as pkg
+    for cname, cls in (("pi_config_t", pkg.PiConfig), ("pi_multi_class_t", pkg.PiMultiClass),
+                       ("pi_info_t", pkg.PiInfo)):
+        hdr = [f for _, f in _header_fields(cname)]
+        assert hdr == [f for f, _ in cls._fields_], cname

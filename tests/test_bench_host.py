@@ -96,3 +96,32 @@ def test_stale_ncu_figures_are_not_reported(tmp_path, monkeypatch):
     f.write_text(json.dumps(data))
     total, kern, note = bench.kernel_profile("skewed", 4000, 200)
     assert total is None and kern is None and "changed" in note
+
+
+def test_tuned_tables_are_well_formed():
+    """The committed tuning tables hold a valid kernel variant per size class (clusters
+    only with 16 or 32 warps and 8-bit digits) and a lowest level per class, and the
+    bench reads the plain path's table for the sizes it tuned."""
+    bench = load_bench()
+    classes = bench.tuned_classes()
+    assert classes and [c[0] for c in classes] == sorted(c[0] for c in classes)
+    for c in classes:
+        hi, warps, bits = c[:3]
+        cluster = c[3] if len(c) > 3 else 1
+        assert warps in (8, 16, 32) and bits in (4, 8)
+        assert cluster in (0, 1, 2, 4, 8, 16)
+        if cluster > 1:
+            assert warps in (16, 32) and bits == 8
+    for n in (1 << 12, 1 << 16, 1 << 20, 1 << 26):
+        assert bench.tuned_lowest(n) in (0, 2, 3, 4, 5, 6)
+    plain = bench.tuned_plain(1 << 27)
+    assert plain.get("lowest_level") in (2, 3, 4, 5) and plain.get("sort_passes") in (0, 1, 2, 3, 4, 8)
+    assert bench.tuned_plain(1 << 16) == {}  # no tuned size within a factor of two
+
+
+def test_autotune_variant_names_round_trip():
+    from paper_1601_00159_gb300 import autotune
+    for v in autotune.VARIANTS:
+        assert autotune.parse_kernel(autotune.kernel_name(v)) == v
+    assert autotune.kernel_name((32, 8, 1)) == "32x8" and autotune.parse_kernel("16x8c4") == (16, 8, 4)
+    assert all(w in (16, 32) and b == 8 for (w, b, c) in autotune.VARIANTS if c > 1)
