@@ -200,22 +200,39 @@ def main():
         table[f"class{c} (log2 size <= {hi}, {len(members)} indices)"] = timings
         print(f"class {c}: {len(members)} indices, ms per call {timings} -> {best}", flush=True)
     # The classes run concurrently in one call and share the SMs, so the per-class winners
-    # are checked jointly: every table whose classes take one of the two fastest variants
-    # of their class is timed on the whole workload, and the fastest table is kept.
+    # are checked jointly on the whole workload: every table whose classes take one of the
+    # three fastest variants of their class, and the tables with fewer classes (two classes
+    # split at 2^14 or 2^17 nodes, or one) whose classes take one of the fastest variants
+    # of the classes they merge. The fastest table is kept.
     joint = {}
     if not args.only:
         import itertools
         tops = []
         for c, hi in enumerate(BOUNDS):
             key = next((k for k in table if k.startswith(f"class{c} ")), None)
-            ranked = sorted(table[key], key=table[key].get)[:2] if key else [kernel_name(chosen[c][1:])]
+            ranked = sorted(table[key], key=table[key].get)[:3] if key else [kernel_name(chosen[c][1:])]
             tops.append([parse_kernel(r) for r in ranked])
         all_batches = [[(i, torch.from_numpy(b.ops).to(dev), torch.from_numpy(b.keys.view(np.int64)).to(dev),
                          torch.from_numpy(b.vals.view(np.int64)).to(dev),
                          torch.empty((len(b), 2), dtype=torch.int64, device=dev)) for i, b in enumerate(rd)]
                        for rd in rounds]
-        for combo in itertools.product(*tops):
-            cls = [(BOUNDS[c], *combo[c]) for c in range(len(BOUNDS))]
+
+        def merged(cs):  # the fastest variants of the classes cs, without repeats
+            out = []
+            for c in cs:
+                for v in tops[c]:
+                    if v not in out:
+                        out.append(v)
+            return out
+
+        tables = [[(BOUNDS[c], *combo[c]) for c in range(len(BOUNDS))] for combo in itertools.product(*tops)]
+        for split in range(len(BOUNDS) - 1):  # two classes: [0, split] and (split, last]
+            for lo_v in merged(range(split + 1)):
+                for hi_v in merged(range(split + 1, len(BOUNDS))):
+                    tables.append([(BOUNDS[split], *lo_v), (BOUNDS[-1], *hi_v)])
+        for v in merged(range(len(BOUNDS))):
+            tables.append([(BOUNDS[-1], *v)])
+        for cls in tables:
             idxs = []
             for i in range(len(sizes)):
                 k = torch.from_numpy(w.keys[i].view(np.int64)).to(dev)
@@ -245,8 +262,8 @@ def main():
     # class's indices; 0 is the library's automatic choice.
     fanout, lowest = {}, {}
     lo = -1
-    for c, hi in enumerate(BOUNDS):
-        members = [i for i in range(len(sizes)) if lo < lg[i] <= hi]
+    for c, hi in enumerate(cb[0] for cb in chosen):
+        members = [i for i in range(len(sizes)) if lo < lg[i] <= hi or (c == len(chosen) - 1 and lg[i] > hi)]
         lo = hi
         if not members or args.only:
             continue

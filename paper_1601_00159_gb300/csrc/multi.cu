@@ -1195,6 +1195,87 @@ __device__ void m_fix_segments(uint64_t* K, uint32_t* P, uint64_t* K2, uint32_t*
     }
 }
 
+// The plan's radix passes over one chunk (n <= kT x kMI) held in registers and shared
+// memory: the chunk is read from (K, P) once, every pass ranks it by warp ballots and
+// places it in digit order in shared memory, the next pass reads it back from there, and
+// the result is written to (K, P) once. Stable, like the passes through global memory.
+template <int kT, int kBits>
+__device__ void m_sort_chunk_smem(uint64_t* K, uint32_t* P, uint32_t n, const SortPlan& plan, uint8_t* dsm,
+                                  uint32_t* tmp) {
+    constexpr int kW = kT / 32;
+    constexpr int kR = 1 << kBits;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t* whist = reinterpret_cast<uint32_t*>(dsm);  // [kW][kR]
+    uint32_t* stot = whist + kW * kR + kR;               // [kR] (the layout of m_scatter)
+    uint32_t* loff = stot + kR;                          // [kR]
+    uint64_t* sk = reinterpret_cast<uint64_t*>(dsm + kSortStage);
+    uint32_t* sp = reinterpret_cast<uint32_t*>(sk + (uint32_t)kT * kMI);
+    uint64_t key[kMI];
+    uint32_t pay[kMI];
+#pragma unroll
+    for (int k = 0; k < kMI; ++k) {
+        const uint32_t i = (uint32_t)warp * 32u * kMI + (uint32_t)k * 32u + (uint32_t)lane;
+        key[k] = i < n ? K[i] : 0ull;
+        pay[k] = i < n ? P[i] : 0u;
+    }
+    for (int d = tid; d < kW * kR; d += kT) whist[d] = 0;
+    __syncthreads();
+    for (uint32_t j = 0; j < plan.npass; ++j)
+        for (int sub = 0; sub < 8 / kBits; ++sub) {
+            const uint32_t shift = 8u * plan.digit[j] + (uint32_t)(sub * kBits);
+            uint32_t dig[kMI], rank[kMI];
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                const uint32_t i = (uint32_t)warp * 32u * kMI + (uint32_t)k * 32u + (uint32_t)lane;
+                dig[k] = i < n ? (uint32_t)(key[k] >> shift) & (kR - 1) : (uint32_t)kR;
+            }
+            warp_digit_ranks<kMI, kBits>(dig, rank, whist + warp * kR);
+            __syncthreads();
+            for (int d = tid; d < kR; d += kT) {
+                uint32_t total = 0;
+#pragma unroll 4
+                for (int w = 0; w < kW; ++w) {
+                    const uint32_t cc = whist[w * kR + d];
+                    whist[w * kR + d] = total;
+                    total += cc;
+                }
+                stot[d] = total;
+                loff[d] = total;
+            }
+            __syncthreads();
+            small_excl_scan<kT, kR>(loff, tmp);
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                const uint32_t d = dig[k];
+                if (d < (uint32_t)kR) {
+                    const uint32_t l = loff[d] + whist[warp * kR + d] + rank[k];
+                    sk[l] = key[k];
+                    sp[l] = pay[k];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kMI; ++k) {
+                const uint32_t i = (uint32_t)warp * 32u * kMI + (uint32_t)k * 32u + (uint32_t)lane;
+                if (i < n) {
+                    key[k] = sk[i];
+                    pay[k] = sp[i];
+                }
+            }
+            for (int d = tid; d < kW * kR; d += kT) whist[d] = 0;
+            __syncthreads();
+        }
+#pragma unroll
+    for (int k = 0; k < kMI; ++k) {
+        const uint32_t i = (uint32_t)warp * 32u * kMI + (uint32_t)k * 32u + (uint32_t)lane;
+        if (i < n) {
+            K[i] = key[k];
+            P[i] = pay[k];
+        }
+    }
+    __syncthreads();
+}
+
 // Pack + sort of a whole batch by one CTA. Four passes on the most significant varying
 // bytes, then the segments of equal leading bytes that hold different keys are ordered
 // by the rest (as in the single-index sort). With more such segments than the list
@@ -1225,13 +1306,17 @@ __device__ void m_sort_cta(const MItem& it, const MScratchPtrs& s, uint8_t* dsm,
         P = s.pa;
         uint64_t* K2 = s.kb;
         uint32_t* P2 = s.pb;
-        for (uint32_t j = 0; j < sh.plan.npass; ++j)
-            for (int sub = 0; sub < 8 / kBits; ++sub) {
-                m_lsd_pass<kT, kBits>(K, P, K2, P2, 0u, n, 8u * sh.plan.digit[j] + (uint32_t)(sub * kBits), dsm,
-                                      sh.tmp, err);
-                uint64_t* tk = K; K = K2; K2 = tk;
-                uint32_t* tp = P; P = P2; P2 = tp;
-            }
+        if (n <= (uint32_t)kT * kMI) {
+            m_sort_chunk_smem<kT, kBits>(K, P, n, sh.plan, dsm, sh.tmp);  // sorted in place
+        } else {
+            for (uint32_t j = 0; j < sh.plan.npass; ++j)
+                for (int sub = 0; sub < 8 / kBits; ++sub) {
+                    m_lsd_pass<kT, kBits>(K, P, K2, P2, 0u, n, 8u * sh.plan.digit[j] + (uint32_t)(sub * kBits),
+                                          dsm, sh.tmp, err);
+                    uint64_t* tk = K; K = K2; K2 = tk;
+                    uint32_t* tp = P; P = P2; P2 = tp;
+                }
+        }
         if (!sh.plan.fix) break;
         m_find_segments<kT>(K, sh.plan.pmask, 1u, n, &sh.nseg, sh.seg, &sh.overflow);
         __syncthreads();
