@@ -38,7 +38,7 @@ namespace pi {
 namespace {
 
 constexpr uint32_t kMSeqMask = (1u << 30) - 1u;
-constexpr int kMI = 8;             // queries or nodes per thread in a chunked pass
+constexpr int kMI = 4;             // queries or nodes per thread in a chunked pass
 constexpr int kMK = 8;             // distinct keys per thread walked down together
 constexpr uint32_t kMTop = 2048;   // index entries staged in shared memory
 constexpr uint32_t kMSeg = 256;    // colliding segments one CTA orders after the prefix passes
@@ -759,9 +759,18 @@ __device__ void m_merge_span(const MScratchPtrs& s, const uint64_t* SK, const ui
         uint32_t nat[kMI];
         uint32_t hb[kMI];
         if (i0 + kMI <= size) {
-            const uint2 w8 = *reinterpret_cast<const uint2*>(SM + i0);  // i0 is a multiple of 8
+            static_assert(kMI == 4 || kMI == 8, "one 4- or 8-byte load of a thread's meta bytes");
+            uint32_t w[2];
+            if constexpr (kMI == 8) {
+                const uint2 w8 = *reinterpret_cast<const uint2*>(SM + i0);  // i0 is a multiple of 8
+                w[0] = w8.x;
+                w[1] = w8.y;
+            } else {
+                w[0] = *reinterpret_cast<const uint32_t*>(SM + i0);  // i0 is a multiple of 4
+                w[1] = 0;
+            }
 #pragma unroll
-            for (int k = 0; k < kMI; ++k) hb[k] = ((k < 4 ? w8.x : w8.y) >> (8 * (k & 3))) & 0xFFu;
+            for (int k = 0; k < kMI; ++k) hb[k] = (w[k >> 2] >> (8 * (k & 3))) & 0xFFu;
         } else {
 #pragma unroll
             for (int k = 0; k < kMI; ++k) hb[k] = i0 + k < size ? (uint32_t)SM[i0 + k] : (uint32_t)kTomb;
