@@ -139,6 +139,9 @@ def main():
     from . import workloads as wl
     ap = argparse.ArgumentParser()
     ap.add_argument("--calls", type=int, default=8)
+    ap.add_argument("--warm", type=int, default=16,
+                    help="untimed calls first: every call inserts new keys, so the indices grow "
+                         "towards the sizes a long run reaches")
     ap.add_argument("--out", default=OUT)
     ap.add_argument("--only", default="", help="time one variant, e.g. 32x8 or 32x8c8 (profiling runs)")
     ap.add_argument("--plain", action="store_true", help="tune the plain path instead of the batching form")
@@ -156,7 +159,8 @@ def main():
     w = wl.batching()
     # every call takes a round no call has applied before, so its inserts are new keys
     # (every index merges and rebuilds), as in the batching workload itself
-    nr = 2 + args.calls
+    nw = args.warm
+    nr = nw + args.calls
     rounds = [w.batches(r) for r in range(nr)]
     rnd = rounds[0]
     sizes = np.array([len(k) for k in w.keys])
@@ -182,13 +186,13 @@ def main():
                 idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], {"storage_capacity": cap}))
             ms = MultiSet(idxs, [(32, *var)])
             descs = [ms.prepare([(j, *bj[j]) for j in range(len(members))]) for bj in batches]
-            for r in range(2):
+            for r in range(nw):
                 ms.execute(descs[r])
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for r in range(args.calls):
-                ms.execute(descs[2 + r])
+                ms.execute(descs[nw + r])
             e1.record()
             torch.cuda.synchronize()
             timings[kernel_name(var)] = e0.elapsed_time(e1) / args.calls
@@ -241,13 +245,13 @@ def main():
                 idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], {"storage_capacity": cap}))
             ms = MultiSet(idxs, cls)
             prepared = [ms.prepare(b) for b in all_batches]
-            for r in range(2):
+            for r in range(nw):
                 ms.execute(prepared[r])
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for r in range(args.calls):
-                ms.execute(prepared[2 + r])
+                ms.execute(prepared[nw + r])
             e1.record()
             torch.cuda.synchronize()
             joint[json.dumps(cls)] = e0.elapsed_time(e1) / args.calls
@@ -284,13 +288,13 @@ def main():
                 idxs.append(Index(k, v, w.promote_p, w.hash_seeds[i], cfg))
             ms = MultiSet(idxs, [(32, *chosen[c][1:])])
             prepared = [ms.prepare(b) for b in batches]
-            for r in range(2):
+            for r in range(nw):
                 ms.execute(prepared[r])
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for r in range(args.calls):
-                ms.execute(prepared[2 + r])
+                ms.execute(prepared[nw + r])
             e1.record()
             torch.cuda.synchronize()
             times[f"lowest_level={low or 'auto'}"] = e0.elapsed_time(e1) / args.calls
