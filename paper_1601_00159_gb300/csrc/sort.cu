@@ -484,6 +484,76 @@ __device__ void cta_segment_lsd(uint32_t s, uint32_t e, const SortPlan& P, const
     __syncthreads();
 }
 
+// Orders the segment [s, e) of buffer A by the bytes the prefix passes skipped, for a
+// segment of at most one tile: it is read into registers once, every pass ranks it and
+// places it in shared memory (s_k, s_p: kTile entries) in digit order, the next pass
+// reads it back from there, and the result is written to A once. Stable.
+__device__ void cta_segment_smem(uint32_t s, uint32_t e, const SortPlan& P, const SortBuffers& sb,
+                                 uint64_t* s_k, uint32_t* s_p, uint32_t (*s_whist)[256], uint32_t* s_base,
+                                 uint32_t* s_tmp) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t L = e - s;
+    uint64_t key[kItems];
+    uint32_t pay[kItems];
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint32_t li = (uint32_t)(warp * kWarpSpan + k * 32 + lane);
+        key[k] = li < L ? sb.a_k[s + li] : 0ull;
+        pay[k] = li < L ? sb.a_p[s + li] : 0u;
+    }
+    for (int w = 0; w < kWarps; ++w) s_whist[w][tid] = 0;
+    __syncthreads();
+    for (uint32_t r = 0; r < P.nr; ++r) {
+        const uint32_t shift = 8u * P.rdig[r];
+        uint32_t dig[kItems], rank[kItems];
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const uint32_t li = (uint32_t)(warp * kWarpSpan + k * 32 + lane);
+            dig[k] = li < L ? (uint32_t)((key[k] >> shift) & 255u) : 256u;
+        }
+        warp_digit_ranks<kItems, 8>(dig, rank, s_whist[warp]);
+        __syncthreads();
+        uint32_t total = 0;  // thread tid owns digit tid: per-warp exclusive prefix
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t cc = s_whist[w][tid];
+            s_whist[w][tid] = total;
+            total += cc;
+        }
+        s_base[tid] = block_excl_sum<kThreads>(total, s_tmp, nullptr);  // the digit's first slot
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const uint32_t d = dig[k];
+            if (d < 256u) {
+                const uint32_t pos = s_base[d] + s_whist[warp][d] + rank[k];
+                s_k[pos] = key[k];
+                s_p[pos] = pay[k];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const uint32_t li = (uint32_t)(warp * kWarpSpan + k * 32 + lane);
+            if (li < L) {
+                key[k] = s_k[li];
+                pay[k] = s_p[li];
+            }
+        }
+        for (int w = 0; w < kWarps; ++w) s_whist[w][tid] = 0;
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint32_t li = (uint32_t)(warp * kWarpSpan + k * 32 + lane);
+        if (li < L) {
+            sb.a_k[s + li] = key[k];
+            sb.a_p[s + li] = pay[k];
+        }
+    }
+    __syncthreads();
+}
+
 // Orders every marked segment. Each CTA reads kThreads fixmap words (kFixSlice
 // positions) and takes the segments that start there. A warp orders a segment of at
 // most 32 queries: rank = queries with a smaller key, or the same key and an earlier
@@ -493,7 +563,11 @@ __global__ void __launch_bounds__(kThreads) k_sort_fix(uint32_t n, SortBuffers s
     pdl_trigger();
     const SortPlan& P = bm->plan;
     if (!P.fix) return;
-    __shared__ uint32_t s_list[kFixSlice / 2];  // segment starts (a segment holds >= 2 queries)
+    // segment starts (a segment holds >= 2 queries); then the keys of a long segment
+    // ordered in shared memory
+    __shared__ __align__(16) uint32_t s_list[kFixSlice / 2];
+    __shared__ uint32_t s_pay[kTile];
+    static_assert(kFixSlice / 2 * sizeof(uint32_t) >= kTile * sizeof(uint64_t), "a tile's keys fit s_list");
     __shared__ uint32_t s_big[kFixSlice / 32 + 1];  // starts of segments of more than 32
     __shared__ uint32_t s_nbig, s_end;
     __shared__ uint32_t s_tmp[33];
@@ -550,26 +624,40 @@ __global__ void __launch_bounds__(kThreads) k_sort_fix(uint32_t n, SortBuffers s
     const uint32_t nbig = min(s_nbig, (uint32_t)(kFixSlice / 32 + 1));
     for (uint32_t x = 0; x < nbig; ++x) {
         const uint32_t s = s_big[x];
-        if (tid == 0) {
-            // end of the segment: gallop forward from s + 32 (in it), then bisect
+        if (warp == 0) {
+            // End of the segment, by the first warp: lane l probes s + 32 + 2^l - 1 (a
+            // gallop in one round), then 32-way rounds narrow the bracket. The segment's
+            // positions are a prefix of [s + 32, n), so each round's hits are a prefix.
             const uint64_t mk = ak[s] & pm;
-            uint32_t in = s + 32u;
-            uint64_t d = 1;
-            while (d < n - in && (ak[in + d] & pm) == mk) {
-                in += (uint32_t)d;
-                d <<= 1;
+            const uint32_t base = s + 32u;  // in the segment
+            const uint64_t off = (1ull << lane) - 1ull;
+            const bool hit = base + off < n && (ak[base + off] & pm) == mk;
+            const uint32_t hm = __ballot_sync(0xffffffffu, hit);  // lane 0 always hits
+            const int top = 31 - __clz(hm);
+            uint32_t lo = base + ((1u << top) - 1u) + 1u;  // past the last position known in it
+            const uint64_t qn = (uint64_t)base + (2ull << top) - 1ull;  // the first probe past it
+            uint32_t hi = (top < 31 && qn < (uint64_t)n) ? (uint32_t)qn : n;  // not in it (or n)
+            while (hi > lo) {  // the end lies in [lo, hi]
+                const uint32_t step = (hi - lo + 31u) / 32u;
+                const uint32_t p = lo + lane * step;
+                const bool in = p < hi && (ak[p] & pm) == mk;
+                const uint32_t c = (uint32_t)__popc(__ballot_sync(0xffffffffu, in));
+                if (c == 0) break;  // lo itself is past the segment
+                const uint32_t nlo = lo + (c - 1u) * step + 1u;
+                const uint32_t nhi = lo + c * step;
+                lo = nlo;
+                hi = nhi < hi ? nhi : hi;
             }
-            uint32_t lo = in + 1, hi = (d < n - in) ? in + (uint32_t)d : n;  // the end lies in [lo, hi]
-            while (lo < hi) {
-                const uint32_t mid = lo + (hi - lo) / 2;
-                if ((ak[mid] & pm) == mk) lo = mid + 1;
-                else hi = mid;
+            if (lane == 0) {
+                s_end = lo;
+                atomicAdd(&bm->fix_big, lo - s);
             }
-            s_end = lo;
-            atomicAdd(&bm->fix_big, lo - s);
         }
         __syncthreads();
-        cta_segment_lsd(s, s_end, P, sb, s_whist, s_base, s_tmp);
+        if (s_end - s <= (uint32_t)kTile)
+            cta_segment_smem(s, s_end, P, sb, reinterpret_cast<uint64_t*>(s_list), s_pay, s_whist, s_base, s_tmp);
+        else
+            cta_segment_lsd(s, s_end, P, sb, s_whist, s_base, s_tmp);
     }
 }
 
